@@ -1,0 +1,227 @@
+/*
+ * tpcf.h -- C ABI of the GB300 pair-count / Landy-Szalay / linear-construction
+ * covariance library.
+ *
+ * The library computes, for many mock catalogues at once, the three stages of
+ * the linear-construction (LC) covariance of the two-point correlation
+ * function:
+ *   1. tpcf_count  -- binned pair counts DD, DR_i, RR_i in (s, mu)   (Sect. 2.1, Sect. 4.3)
+ *   2. tpcf_ls     -- the split Landy-Szalay estimator                (Sect. 2.1)
+ *   3. tpcf_lc_cov -- sample covariances and their linear combination
+ *                     (Eqs. bruteforce, R1R2, LCdef)                   (Sect. 2.2-2.3)
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments named as device arrays are CUDA device pointers
+ *     owned by the caller; the library never frees or retains them past the
+ *     call's stream work.  Host arrays are read during the call only.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls validate their arguments synchronously, then enqueue the
+ *     GPU work on `stream` and return without waiting.  Errors found on the
+ *     device (e.g. a position outside the bounding cube) are reported by
+ *     tpcf_sync().
+ *   - Return codes: TPCF_OK (0), a positive warning, or a negative error.
+ *     After an error, tpcf_last_error() gives a one-line description.
+ *   - A context is bound to one CUDA device and is not thread-safe: use one
+ *     context per host thread.
+ */
+#ifndef TPCF_H
+#define TPCF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define TPCF_OK               0
+#define TPCF_WARN_EMPTY_BIN   1   /* some rr = 0: those xi entries are NaN */
+#define TPCF_ERR_ARG         -1   /* invalid argument (NULL pointer, bad size, bad enum) */
+#define TPCF_ERR_RANGE       -2   /* geometry/binning outside the exact-integer range, or a
+                                     position outside the bounding cube (open geometry) */
+#define TPCF_ERR_CUDA        -3   /* a CUDA runtime call failed */
+#define TPCF_ERR_NOMEM       -4   /* device or pinned-host allocation failed */
+#define TPCF_ERR_TIMEOUT     -5   /* a bounded device wait gave up */
+#define TPCF_ERR_STATE       -6   /* context unusable after an earlier CUDA error */
+
+/* ---- enums ------------------------------------------------------------- */
+#define TPCF_PERIODIC   0         /* periodic cube of side box_L, minimum-image separations */
+#define TPCF_OPEN       1         /* non-periodic; all points inside the cube [origin, origin+box_L)^3 */
+
+#define TPCF_LOS_X        0       /* plane-parallel line of sight along x (Sect. 4.1) */
+#define TPCF_LOS_MIDPOINT 1       /* line of sight from the observer to the pair midpoint (open only) */
+
+#define TPCF_DD  1u               /* term mask bits for tpcf_count */
+#define TPCF_DR  2u
+#define TPCF_RR  4u
+
+#define TPCF_BATCHED     0        /* all mocks and terms in one persistent launch (default) */
+#define TPCF_PER_LAUNCH  1        /* one kernel launch per (mock, term, subset): baseline */
+
+#define TPCF_FP64    0            /* covariance arithmetic entirely in float64 */
+#define TPCF_TF32X3  1            /* Gram products on tensor cores, 3-term TF32 split, FP32 accumulate */
+#define TPCF_BF16X3  2            /* Gram products on tensor cores, 3-piece BF16 split, FP32 accumulate */
+
+typedef struct tpcf_ctx tpcf_ctx;
+
+/*
+ * Create a context on CUDA device `cuda_device`.  The context owns the
+ * workspace (grown on demand, reused across calls), the autotuner cache and
+ * a device status word.  *out is set to NULL on failure.
+ * Returns TPCF_OK, TPCF_ERR_ARG, TPCF_ERR_CUDA or TPCF_ERR_NOMEM.
+ */
+int tpcf_create(tpcf_ctx **out, int cuda_device);
+
+/* Release every resource of the context (waits for its outstanding work). NULL is a no-op. */
+void tpcf_destroy(tpcf_ctx *ctx);
+
+/*
+ * Wait for all work the context enqueued on `stream`, then read and clear
+ * the device status word.  Returns TPCF_OK, TPCF_WARN_EMPTY_BIN (from
+ * tpcf_ls), TPCF_ERR_RANGE (a position outside the bounding cube),
+ * TPCF_ERR_TIMEOUT, or TPCF_ERR_CUDA.
+ */
+int tpcf_sync(tpcf_ctx *ctx, void *stream);
+
+/* One-line description of the last error or warning on this context ("" if none). */
+const char *tpcf_last_error(const tpcf_ctx *ctx);
+
+/*
+ * Geometry and binning (Sect. 4.3: bins in separation s and in mu, the
+ * cosine of the angle between the line of sight and the pair separation).
+ *   s bins   : half-open [s_edges[k], s_edges[k+1]), k = 0..n_s-1, edges strictly
+ *              increasing and >= 0 (host array of n_s+1 doubles).
+ *   mu bins  : n_mu uniform bins of |mu| on [0, 1], the top bin closed; n_mu = 1 gives
+ *              s-only counts.  mu = 0 for coincident points.
+ *   histogram index of (k, j) is k * n_mu + j (s-major); nbin = n_s * n_mu.
+ * Positions are quantised to integer grid coordinates (2^32 per box side for
+ * TPCF_PERIODIC, 2^30 per bounding-cube side for TPCF_OPEN) and every bin
+ * decision is exact on those integers.  Limits: n_s <= 256, nbin <= 4096;
+ * periodic boxes need s_max <= box_L / 3 and the x line of sight.
+ */
+typedef struct {
+    int     geometry;        /* TPCF_PERIODIC or TPCF_OPEN */
+    double  box_L;           /* periodic box side, or bounding-cube side */
+    double  origin[3];       /* lower corner of the bounding cube (open); ignored for periodic */
+    int     los;             /* TPCF_LOS_X or TPCF_LOS_MIDPOINT */
+    double  observer[3];     /* observer position for TPCF_LOS_MIDPOINT */
+    int     n_s;             /* number of s bins */
+    const double *s_edges;   /* host, n_s + 1 values */
+    int     n_mu;            /* number of |mu| bins, >= 1 */
+} tpcf_binning;
+
+/*
+ * One mock: a data catalogue D and M random sub-catalogues R_1..R_M (the
+ * split random catalogue of Sect. 2.1).  Give each catalogue either as
+ * float64 positions (`*_xyz`, device, row-major [n][3]) or as pre-quantised
+ * grid coordinates (`*_u32`, device, structure-of-arrays [3][n]); the other
+ * pointer is NULL.  The random points are one array; subset i is the index
+ * range [rand_offsets[i], rand_offsets[i+1]) with rand_offsets a HOST array
+ * of M+1 non-decreasing values starting at 0.
+ */
+typedef struct {
+    const double   *data_xyz;
+    const uint32_t *data_u32;
+    int64_t         n_d;
+    const double   *rand_xyz;
+    const uint32_t *rand_u32;
+    const int64_t  *rand_offsets;   /* host, M + 1 */
+    int             M;
+} tpcf_mock;
+
+/*
+ * Binned pair counts of every mock (Sect. 2.1 DD, DR_i, RR_i; Sect. 4.3 bins).
+ *   DD   : unordered pairs of distinct points of D
+ *   DR_i : all pairs (a in D, b in R_i)
+ *   RR_i : unordered pairs of distinct points of R_i (pairs across
+ *          sub-catalogues are not counted: the split estimator)
+ * Outputs (device, int64, overwritten for the requested terms):
+ *   dd[n_mock][nbin], dr[n_mock][M][nbin], rr[n_mock][M][nbin]
+ * Every mock must have the same M when TPCF_DR or TPCF_RR is requested.
+ * `terms` is a mask of TPCF_DD | TPCF_DR | TPCF_RR; unrequested outputs may
+ * be NULL.  `mode` selects TPCF_BATCHED or TPCF_PER_LAUNCH; both give
+ * identical counts.  Returns TPCF_OK or a negative error (nothing enqueued).
+ */
+int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *binning,
+               unsigned terms, int64_t *dd, int64_t *dr, int64_t *rr, int mode, void *stream);
+
+/*
+ * Split Landy-Szalay estimator of Sect. 2.1 for each mock, over the random
+ * sub-catalogues listed in sel[0..n_sel) (host, indices into 0..M-1):
+ *   dd = DD / (N_d (N_d - 1) / 2)
+ *   dr = (1/n_sel) sum_{i in sel} DR_i / (N_d N_r,i)
+ *   rr = (1/n_sel) sum_{i in sel} RR_i / (N_r,i (N_r,i - 1) / 2)
+ *   xi = (dd - 2 dr) / rr + 1                     (float64; NaN where rr = 0)
+ * With N_r,i = N_d these are the paper's normalisations.  sel = {0} gives
+ * xi(D, R_1); sel = {0, 1} gives xi(D, R_1 u R_2) with the split RR.
+ * Inputs: dd[n_mock][nbin], dr/rr[n_mock][M][nbin] (device int64);
+ * n_d[n_mock], n_r[n_mock][M] (host).  Output xi[n_mock][nbin] (device float64).
+ * Needs N_d >= 2 and N_r,i >= 2.  A bin with rr = 0 makes tpcf_sync return
+ * TPCF_WARN_EMPTY_BIN.
+ */
+int tpcf_ls(tpcf_ctx *ctx, const int64_t *dd, const int64_t *dr, const int64_t *rr,
+            const int64_t *n_d, const int64_t *n_r, int n_mock, int M, int nbin,
+            const int *sel, int n_sel, double *xi, void *stream);
+
+/*
+ * Linear-construction covariance, Eqs. (R1R2) and (LCdef):
+ *   C^a  = (Cov[xi(D,R1)] + Cov[xi(D,R2)]) / 2,  C^b = Cov[xi(D, R1 u R2)]
+ *   A    = 2 C^b - C^a,   B = 2 M_a (C^a - C^b),   C^LC = A + B / M
+ * with Cov the sample covariance over the n_mock mocks, Eq. (bruteforce):
+ * 1/(N-1) sum (xi - mean)(xi - mean)^T.  M = +INFINITY gives C^LC = A.
+ * Inputs xi_a1, xi_a2, xi_b: device float64 [n_mock][nbin].
+ * Outputs: C_lc required; Ca, Cb, A, B may be NULL; all device float64 [nbin][nbin].
+ * `precision`: TPCF_FP64 (all float64), TPCF_TF32X3 or TPCF_BF16X3 (the
+ * centred Gram products on tensor cores in split precision with FP32
+ * accumulation over K-chunks and a float64 sum; means and the final
+ * combination stay float64).  Needs n_mock >= 2, M_a >= 1, M >= M_a.
+ */
+int tpcf_lc_cov(tpcf_ctx *ctx, const double *xi_a1, const double *xi_a2, const double *xi_b,
+                int n_mock, int nbin, int M_a, double M, int precision,
+                double *C_lc, double *Ca, double *Cb, double *A, double *B, void *stream);
+
+/*
+ * The exact integer s-bin thresholds tpcf_count uses (host only, no GPU work):
+ * T[k] = ceil(s_edges[k]^2 q^2) with q = 2^32 / box_L (periodic) or
+ * 2^30 / box_L (open), so that a pair with squared grid separation D2 lies
+ * in s-bin k iff T[k] <= D2 < T[k+1] (Sect. 4.3 bins, half-open).
+ * T_out: host array of n_s + 1 values.  Returns TPCF_OK, TPCF_ERR_ARG or
+ * TPCF_ERR_RANGE (edges beyond the 63-bit range or the geometry's limits).
+ * `ctx` may be NULL.
+ */
+int tpcf_thresholds(tpcf_ctx *ctx, const tpcf_binning *binning, uint64_t *T_out);
+
+/*
+ * Work statistics of the last tpcf_count on this context, valid after
+ * tpcf_sync: candidate pairs tested by the pair-count kernel(s), pairs
+ * that fell in a bin, pairs that needed the exact integer recheck, the
+ * number of work units, and (when timing is enabled) the pair-count
+ * kernels' device time in milliseconds measured with CUDA events on the
+ * launch stream.  Any pointer may be NULL.
+ */
+typedef struct {
+    int64_t n_candidates;
+    int64_t n_binned;
+    int64_t n_exact;
+    int64_t n_units;
+    double  paircount_ms;
+    int     n_paircount_launches;
+    int     cell_subdiv;      /* cells per s_max along an axis, chosen by the planner/autotuner */
+    int     cells_per_axis;
+} tpcf_count_info;
+
+int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info);
+
+/* Enable (1) or disable (0) CUDA-event timing of the pair-count kernels. */
+int tpcf_set_timing(tpcf_ctx *ctx, int enable);
+
+/*
+ * Pin the chaining-mesh subdivision (cells per s_max along an axis, 1..4),
+ * or 0 to let the autotuner choose.  For tests and benchmarks.
+ */
+int tpcf_set_cell_subdiv(tpcf_ctx *ctx, int subdiv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPCF_H */

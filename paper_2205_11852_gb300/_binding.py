@@ -1,0 +1,243 @@
+"""ctypes binding of libtpcf (include/tpcf.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module builds the C
+structs, passes device pointers of torch CUDA tensors (torch supplies the
+device memory and the current stream) and turns return codes into
+exceptions.  There is no CPU fallback: if ``_build/libtpcf.so`` is missing
+the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import pathlib
+
+import torch
+
+_LIBPATH = pathlib.Path(__file__).resolve().parent / "_build" / "libtpcf.so"
+
+TPCF_OK = 0
+TPCF_WARN_EMPTY_BIN = 1
+TPCF_ERR_ARG = -1
+TPCF_ERR_RANGE = -2
+TPCF_ERR_CUDA = -3
+TPCF_ERR_NOMEM = -4
+TPCF_ERR_TIMEOUT = -5
+TPCF_ERR_STATE = -6
+
+TPCF_PERIODIC, TPCF_OPEN = 0, 1
+TPCF_LOS_X, TPCF_LOS_MIDPOINT = 0, 1
+TPCF_DD, TPCF_DR, TPCF_RR = 1, 2, 4
+TPCF_BATCHED, TPCF_PER_LAUNCH = 0, 1
+TPCF_FP64, TPCF_TF32X3, TPCF_BF16X3 = 0, 1, 2
+
+EXPORTED = ("tpcf_create", "tpcf_destroy", "tpcf_sync", "tpcf_last_error", "tpcf_count", "tpcf_ls",
+            "tpcf_lc_cov", "tpcf_last_count_info", "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds")
+
+
+class TpcfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tpcf error {code}: {msg}")
+        self.code = code
+
+
+class tpcf_binning(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int), ("box_L", ctypes.c_double), ("origin", ctypes.c_double * 3),
+                ("los", ctypes.c_int), ("observer", ctypes.c_double * 3), ("n_s", ctypes.c_int),
+                ("s_edges", ctypes.POINTER(ctypes.c_double)), ("n_mu", ctypes.c_int)]
+
+
+class tpcf_mock(ctypes.Structure):
+    _fields_ = [("data_xyz", ctypes.c_void_p), ("data_u32", ctypes.c_void_p), ("n_d", ctypes.c_int64),
+                ("rand_xyz", ctypes.c_void_p), ("rand_u32", ctypes.c_void_p),
+                ("rand_offsets", ctypes.POINTER(ctypes.c_int64)), ("M", ctypes.c_int)]
+
+
+class tpcf_count_info(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int64), ("n_binned", ctypes.c_int64), ("n_exact", ctypes.c_int64),
+                ("n_units", ctypes.c_int64), ("paircount_ms", ctypes.c_double),
+                ("n_paircount_launches", ctypes.c_int), ("cell_subdiv", ctypes.c_int),
+                ("cells_per_axis", ctypes.c_int)]
+
+
+def load_library() -> ctypes.CDLL:
+    """Load libtpcf.so and declare its signatures (no CUDA call is made)."""
+    if not _LIBPATH.exists():
+        raise ImportError(f"{_LIBPATH} is missing: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(str(_LIBPATH))
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.tpcf_create.argtypes = [ctypes.POINTER(P), I]
+    lib.tpcf_destroy.argtypes = [P]
+    lib.tpcf_destroy.restype = None
+    lib.tpcf_sync.argtypes = [P, P]
+    lib.tpcf_last_error.argtypes = [P]
+    lib.tpcf_last_error.restype = ctypes.c_char_p
+    lib.tpcf_count.argtypes = [P, ctypes.POINTER(tpcf_mock), I, ctypes.POINTER(tpcf_binning), ctypes.c_uint,
+                               P, P, P, I, P]
+    lib.tpcf_ls.argtypes = [P, P, P, P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), I, I, I,
+                            ctypes.POINTER(ctypes.c_int), I, P, P]
+    lib.tpcf_lc_cov.argtypes = [P, P, P, P, I, I, I, D, I, P, P, P, P, P, P]
+    lib.tpcf_last_count_info.argtypes = [P, ctypes.POINTER(tpcf_count_info)]
+    lib.tpcf_set_timing.argtypes = [P, I]
+    lib.tpcf_set_cell_subdiv.argtypes = [P, I]
+    lib.tpcf_thresholds.argtypes = [P, ctypes.POINTER(tpcf_binning), ctypes.POINTER(ctypes.c_uint64)]
+    for name in ("tpcf_create", "tpcf_sync", "tpcf_count", "tpcf_ls", "tpcf_lc_cov", "tpcf_last_count_info",
+                 "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_binning(s_edges, n_mu=1, geometry=TPCF_PERIODIC, box_L=1.0, origin=(0.0, 0.0, 0.0), los=TPCF_LOS_X,
+                 observer=(0.0, 0.0, 0.0)):
+    """tpcf_binning; the returned object keeps the edge array alive."""
+    edges = (ctypes.c_double * len(s_edges))(*[float(e) for e in s_edges])
+    b = tpcf_binning(int(geometry), float(box_L), (ctypes.c_double * 3)(*origin), int(los),
+                     (ctypes.c_double * 3)(*observer), len(s_edges) - 1,
+                     ctypes.cast(edges, ctypes.POINTER(ctypes.c_double)), int(n_mu))
+    b._edges = edges
+    return b
+
+
+def tpcf_thresholds(binning) -> list:
+    """Exact integer s-bin thresholds used by tpcf_count (host computation, no GPU)."""
+    T = (ctypes.c_uint64 * (binning.n_s + 1))()
+    rc = lib().tpcf_thresholds(None, ctypes.byref(binning), T)
+    if rc != TPCF_OK:
+        raise TpcfError(rc, "tpcf_thresholds failed")
+    return [int(t) for t in T]
+
+
+class Context:
+    """A libtpcf context on one CUDA device (tpcf_create / tpcf_destroy)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = lib()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        rc = self._lib.tpcf_create(ctypes.byref(h), self.device)
+        if rc != TPCF_OK:
+            raise TpcfError(rc, "tpcf_create failed")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.tpcf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc < 0:
+            raise TpcfError(rc, self._lib.tpcf_last_error(self.handle).decode())
+        return rc
+
+    # -- C entry points, same names -------------------------------------------------
+
+    def tpcf_sync(self, stream=None) -> int:
+        return self._check(self._lib.tpcf_sync(self.handle, _stream(stream)))
+
+    def tpcf_set_timing(self, enable: bool):
+        self._check(self._lib.tpcf_set_timing(self.handle, int(bool(enable))))
+
+    def tpcf_set_cell_subdiv(self, subdiv: int):
+        self._check(self._lib.tpcf_set_cell_subdiv(self.handle, int(subdiv)))
+
+    def tpcf_last_count_info(self) -> dict:
+        info = tpcf_count_info()
+        self._check(self._lib.tpcf_last_count_info(self.handle, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
+    def tpcf_count(self, mocks, binning, terms=TPCF_DD | TPCF_DR | TPCF_RR, mode=TPCF_BATCHED, stream=None,
+                   out=None):
+        """Pair counts of every mock.
+
+        mocks: sequence of dicts with keys
+          'data' (float64 CUDA [n_d,3]) or 'data_u32' (int32/uint32 CUDA [3,n_d]),
+          'randoms' (float64 CUDA [n_r,3]) or 'randoms_u32' ([3,n_r]), 'offsets' (M+1 ints).
+        Returns dict of int64 CUDA tensors dd [n_mock,nbin], dr/rr [n_mock,M,nbin].
+        """
+        n_mock = len(mocks)
+        nbin = binning.n_s * binning.n_mu
+        arr = (tpcf_mock * max(1, n_mock))()
+        keep = []
+        M = 0
+        dev = torch.device("cuda", self.device)
+        for i, m in enumerate(mocks):
+            d = m.get("data")
+            du = m.get("data_u32")
+            r = m.get("randoms")
+            ru = m.get("randoms_u32")
+            offs = m.get("offsets", [0])
+            M = len(offs) - 1
+            o = (ctypes.c_int64 * len(offs))(*[int(x) for x in offs])
+            keep.append(o)
+            for t in (d, du, r, ru):
+                if t is not None and (not t.is_cuda or not t.is_contiguous()):
+                    raise ValueError("catalogues must be contiguous CUDA tensors")
+            n_d = d.shape[0] if d is not None else (du.shape[1] if du is not None else 0)
+            arr[i] = tpcf_mock(_ptr(d), _ptr(du), n_d, _ptr(r), _ptr(ru),
+                               ctypes.cast(o, ctypes.POINTER(ctypes.c_int64)), M)
+        if out is None:
+            out = {"dd": torch.empty((n_mock, nbin), dtype=torch.int64, device=dev),
+                   "dr": torch.empty((n_mock, max(M, 1), nbin), dtype=torch.int64, device=dev),
+                   "rr": torch.empty((n_mock, max(M, 1), nbin), dtype=torch.int64, device=dev)}
+        rc = self._lib.tpcf_count(self.handle, arr, n_mock, ctypes.byref(binning), int(terms),
+                                  _ptr(out["dd"]), _ptr(out["dr"]), _ptr(out["rr"]), int(mode), _stream(stream))
+        self._check(rc)
+        del keep
+        return out
+
+    def tpcf_ls(self, dd, dr, rr, n_d, n_r, sel, stream=None, out=None):
+        """Split Landy-Szalay xi [n_mock, nbin] (float64 CUDA) over random subsets `sel`."""
+        n_mock, nbin = dd.shape
+        M = dr.shape[1]
+        nd = (ctypes.c_int64 * max(1, n_mock))(*[int(x) for x in n_d])
+        flat = [int(x) for row in n_r for x in row]
+        nr = (ctypes.c_int64 * max(1, len(flat)))(*flat)
+        s = (ctypes.c_int * len(sel))(*[int(x) for x in sel])
+        if out is None:
+            out = torch.empty((n_mock, nbin), dtype=torch.float64, device=dd.device)
+        rc = self._lib.tpcf_ls(self.handle, _ptr(dd), _ptr(dr), _ptr(rr), nd, nr, n_mock, M, nbin, s, len(sel),
+                               _ptr(out), _stream(stream))
+        self._check(rc)
+        return out
+
+    def tpcf_lc_cov(self, xi_a1, xi_a2, xi_b, M_a=1, M=math.inf, precision=TPCF_FP64, stream=None,
+                    want_parts=True):
+        """LC covariance (Eqs. R1R2, LCdef); returns dict of float64 CUDA [nbin, nbin] tensors."""
+        n_mock, nbin = xi_a1.shape
+        dev = xi_a1.device
+        mk = lambda: torch.empty((nbin, nbin), dtype=torch.float64, device=dev)
+        out = {"C_lc": mk()}
+        if want_parts:
+            out.update(Ca=mk(), Cb=mk(), A=mk(), B=mk())
+        rc = self._lib.tpcf_lc_cov(self.handle, _ptr(xi_a1), _ptr(xi_a2), _ptr(xi_b), n_mock, nbin, int(M_a),
+                                   float(M), int(precision), _ptr(out["C_lc"]), _ptr(out.get("Ca")),
+                                   _ptr(out.get("Cb")), _ptr(out.get("A")), _ptr(out.get("B")), _stream(stream))
+        self._check(rc)
+        return out

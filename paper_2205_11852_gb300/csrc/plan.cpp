@@ -1,0 +1,318 @@
+// Host-side planning of a pair count: exact integer bin thresholds, the FP32
+// error bands around them, the s-bin lookup table over FP32 bit patterns,
+// and the chaining-mesh neighbourhood.
+//
+// Binning definition (Sect. 4.3 bins; exact on integer grid coordinates):
+// a pair with squared grid separation D2 lies in s-bin k iff
+// T_k <= D2 < T_{k+1}, T_k = ceil(e_k^2 q^2), q = 2^32/L (periodic) or
+// 2^30/L (open).  T_k is computed here in exact integer arithmetic.
+#include "plan.h"
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace tpcf {
+
+namespace {
+
+// Minimal unsigned big integer (little-endian 32-bit limbs), enough for
+// ceil(a * 2^s / b) with a, b < 2^106 and a quotient below 2^64.
+struct Big {
+    static constexpr int N = 14;
+    uint32_t d[N];
+    Big() { std::memset(d, 0, sizeof(d)); }
+    explicit Big(unsigned long long v) : Big() { d[0] = (uint32_t)v; d[1] = (uint32_t)(v >> 32); }
+    static Big mul(unsigned long long a, unsigned long long b)
+    {
+        Big r;
+        const uint32_t x[2] = {(uint32_t)a, (uint32_t)(a >> 32)}, y[2] = {(uint32_t)b, (uint32_t)(b >> 32)};
+        for (int i = 0; i < 2; i++) {
+            unsigned long long carry = 0;
+            for (int j = 0; j < 2; j++) {
+                unsigned long long t = (unsigned long long)x[i] * y[j] + r.d[i + j] + carry;
+                r.d[i + j] = (uint32_t)t;
+                carry = t >> 32;
+            }
+            int k = i + 2;
+            while (carry) {
+                unsigned long long t = (unsigned long long)r.d[k] + carry;
+                r.d[k++] = (uint32_t)t;
+                carry = t >> 32;
+            }
+        }
+        return r;
+    }
+    Big shl(int s) const
+    {
+        Big r;
+        const int w = s / 32, b = s % 32;
+        for (int i = N - 1; i >= 0; i--) {
+            unsigned long long v = 0;
+            if (i - w >= 0) v = (unsigned long long)d[i - w] << b;
+            if (b && i - w - 1 >= 0) v |= (unsigned long long)d[i - w - 1] >> (32 - b);
+            r.d[i] = (uint32_t)v;
+        }
+        return r;
+    }
+    int cmp(const Big &o) const
+    {
+        for (int i = N - 1; i >= 0; i--)
+            if (d[i] != o.d[i]) return d[i] < o.d[i] ? -1 : 1;
+        return 0;
+    }
+    void sub(const Big &o)
+    {
+        long long borrow = 0;
+        for (int i = 0; i < N; i++) {
+            long long t = (long long)d[i] - o.d[i] - borrow;
+            borrow = t < 0;
+            d[i] = (uint32_t)(t + (borrow << 32));
+        }
+    }
+    bool zero() const
+    {
+        for (int i = 0; i < N; i++)
+            if (d[i]) return false;
+        return true;
+    }
+};
+
+// v = m * 2^e with m a 53-bit integer (v > 0, finite)
+void decompose(double v, unsigned long long &m, int &e)
+{
+    int ex;
+    double fr = std::frexp(v, &ex);           // v = fr * 2^ex, fr in [0.5, 1)
+    m = (unsigned long long)std::ldexp(fr, 53);
+    e = ex - 53;
+}
+
+double ulp_f32(double x)
+{
+    if (x <= 0) return std::ldexp(1.0, -149);
+    int ex;
+    std::frexp(x, &ex);                        // x in [2^(ex-1), 2^ex)
+    return std::ldexp(1.0, ex - 1 - 23);
+}
+
+float down_f(double x)
+{
+    float f = (float)x;
+    if ((double)f > x) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+
+float up_f(double x)
+{
+    float f = (float)x;
+    if ((double)f < x) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+}  // namespace
+
+// T = ceil(e^2 * 2^(2 bits) / L^2); returns false if T >= 2^63.
+bool exact_threshold(double e, double L, int bits, unsigned long long &T)
+{
+    if (e == 0.0) { T = 0; return true; }
+    const double est = (e / L) * (e / L) * std::ldexp(1.0, 2 * bits);
+    if (!(est < 4.0e18)) return false;
+    if (est < 0.25) { T = 1; return true; }
+    unsigned long long me, mL;
+    int ee, eL;
+    decompose(e, me, ee);
+    decompose(L, mL, eL);
+    const int s = 2 * ee + 2 * bits - 2 * eL;  // value = me^2 2^s / mL^2
+    Big num = Big::mul(me, me), den = Big::mul(mL, mL);
+    if (s >= 0) num = num.shl(s); else den = den.shl(-s);
+    // long division; the quotient is below 2^64
+    unsigned long long q = 0;
+    for (int i = 63; i >= 0; i--) {
+        Big t = den.shl(i);
+        if (t.cmp(num) <= 0) {
+            num.sub(t);
+            q |= 1ull << i;
+        }
+    }
+    T = q + (num.zero() ? 0 : 1);
+    return T < (1ull << 63);
+}
+
+int build_plan(const tpcf_binning &b, int subdiv, Plan &pl, std::string &err)
+{
+    CountParams &p = pl.prm;
+    std::memset(&p, 0, sizeof(p));
+    p.geometry = b.geometry;
+    p.los = b.los;
+    p.n_s = b.n_s;
+    p.n_mu = b.n_mu;
+    p.nbin = b.n_s * b.n_mu;
+    p.bits = (b.geometry == TPCF_PERIODIC) ? 32 : 30;
+    const double L = b.box_L;
+    const double s_max = b.s_edges[b.n_s];
+
+    // exact thresholds
+    for (int k = 0; k <= b.n_s; k++) {
+        if (!exact_threshold(b.s_edges[k], L, p.bits, p.T[k])) {
+            err = "separation range exceeds the 64-bit squared-distance range";
+            return TPCF_ERR_RANGE;
+        }
+    }
+    const unsigned long long Tmax = p.T[b.n_s];
+    if (Tmax == 0) { err = "s_max must be positive"; return TPCF_ERR_ARG; }
+
+    // mesh
+    int n_c = (int)std::floor(subdiv * L / s_max);
+    n_c = std::max(1, std::min(n_c, MAX_NC));
+    const unsigned long long full = 1ull << p.bits;
+    int K = 0;
+    unsigned long long Wmin = 0, Wmax = 0;
+    for (;;) {
+        Wmin = full / (unsigned long long)n_c;
+        Wmax = (full + n_c - 1) / (unsigned long long)n_c;
+        // largest offset o whose cells can hold points closer than s_max:
+        // ((o - 1) Wmin + 1)^2 < Tmax
+        K = 0;
+        while (true) {
+            const double m = (double)K * (double)Wmin + 1.0;  // bound for offset K+1
+            if (m * m >= (double)Tmax * (1.0 + 1e-12) + 1.0) break;
+            K++;
+            if (K > 4) break;
+        }
+        const bool ok_k = K <= 4;
+        const bool ok_wrap = (b.geometry != TPCF_PERIODIC) || (n_c >= 2 * K + 1);
+        if (ok_k && ok_wrap) break;
+        if (n_c <= 1 || (b.geometry == TPCF_PERIODIC && n_c <= 3)) {
+            err = "periodic box too small for the separation range (need s_max <= L/3)";
+            return TPCF_ERR_RANGE;
+        }
+        n_c = std::max(1, n_c - 1);
+    }
+    p.n_c = n_c;
+    p.n_cells = n_c * n_c * n_c;
+    pl.K = K;
+    pl.subdiv = subdiv;
+    pl.orig.resize(n_c + 1);
+    for (int c = 0; c <= n_c; c++) {
+        const unsigned long long o = ((unsigned long long)c * full + n_c - 1) / n_c;
+        pl.orig[c] = (uint32_t)o;  // 2^32 wraps to 0; only differences are used
+    }
+
+    // neighbour rows (dz, dy) with the x reach of each
+    auto m1 = [&](int o) -> double {
+        if (o == 0) return 0.0;
+        const double m = (double)(std::abs(o) - 1) * (double)Wmin + 1.0;
+        return m * m;
+    };
+    p.n_rows = 0;
+    for (int dz = -K; dz <= K; dz++)
+        for (int dy = -K; dy <= K; dy++) {
+            const double base = m1(dz) + m1(dy);
+            if (base >= (double)Tmax * (1.0 + 1e-12) + 1.0) continue;
+            int kx = 0;
+            while (kx + 1 <= K && base + m1(kx + 1) < (double)Tmax * (1.0 + 1e-12) + 1.0) kx++;
+            p.row_dz[p.n_rows] = (int8_t)dz;
+            p.row_dy[p.n_rows] = (int8_t)dy;
+            p.row_kx[p.n_rows] = (int8_t)kx;
+            p.n_rows++;
+        }
+
+    // FP32 error model.  Coordinates are cell-relative floats; a b-point is
+    // shifted into A's frame by the integer corner difference.  Every value in
+    // the chain stays below (K+2) * Wmax in magnitude, and each of the five
+    // roundings costs at most half an ulp there.
+    const double E = 3.0 * ulp_f32((double)(K + 2) * (double)Wmax);
+    const double u = std::ldexp(1.0, -24);
+    const double g3 = 3.0 * u / (1.0 - 3.0 * u);
+    auto err_at = [&](double T) -> double {
+        const double r = std::sqrt(T);
+        const double a = 2.0 * std::sqrt(3.0) * E * r + 3.0 * E * E;
+        return 2.0 * (a + g3 * (T + a)) + 4.0;   // x2 safety, +4 grid units^2
+    };
+    for (int k = 0; k <= b.n_s; k++) {
+        const double T = (double)p.T[k];
+        if (p.T[k] == 0) {
+            p.lo[k] = 0.0f;
+            p.hi[k] = 0.0f;
+        } else {
+            const double e = err_at(T);
+            p.lo[k] = down_f(T - e);
+            p.hi[k] = up_f(T + e);
+        }
+    }
+    p.hit_max = p.hi[b.n_s];
+    pl.E_delta = E;
+
+    // mu band (see the kernel): |t - t*| <= n_mu (c1 / sqrt(D2) + c3 / |l| + c2)
+    p.inv_nmu2 = 1.0f / (float)(b.n_mu * b.n_mu);
+    if (b.los == TPCF_LOS_X) {
+        p.mu_c1 = (float)(b.n_mu * 1.1 * (1.0 + std::sqrt(3.0)) * E);
+        p.mu_c2 = (float)(b.n_mu * std::ldexp(1.0, -19));
+    } else {
+        // observer in open grid units; l = u_a + u_b - 2 u_obs
+        for (int c = 0; c < 3; c++)
+            p.obs[c] = (long long)std::floor(((b.observer[c] - b.origin[c]) / L) * std::ldexp(1.0, 30));
+        double gmax = 0.0;
+        for (int c = 0; c < 3; c++)
+            gmax = std::max(gmax, 2.0 * std::max(std::fabs((double)p.obs[c]),
+                                                 std::fabs(std::ldexp(1.0, 30) - (double)p.obs[c])));
+        const double lmax = gmax + 2.0 * (K + 2) * (double)Wmax;
+        const double El = 0.5 * ulp_f32(gmax) + 2.0 * E + 2.0 * ulp_f32(lmax);
+        p.mu_c1 = (float)(b.n_mu * 2.2 * std::sqrt(3.0) * E);
+        p.mu_c2 = (float)(b.n_mu * std::ldexp(1.0, -18));
+        p.mu_c3 = (float)(b.n_mu * 2.2 * std::sqrt(3.0) * El);
+    }
+
+    // s-bin table over FP32 bit patterns of d2
+    double vmin = INFINITY;
+    for (int k = 0; k <= b.n_s; k++)
+        if (p.T[k] > 0) vmin = std::min(vmin, (double)p.lo[k]);
+    int mb = 9;
+    for (;; mb--) {
+        const int sh = 23 - mb;
+        double x0 = (vmin > 1e-30) ? std::ldexp(1.0, (int)std::floor(std::log2(vmin)) - 1) : std::ldexp(1.0, -126);
+        x0 = std::max(x0, (double)FLT_MIN);
+        uint32_t k0, ke;
+        float fx0 = (float)x0, fhm = p.hit_max;
+        std::memcpy(&k0, &fx0, 4);
+        std::memcpy(&ke, &fhm, 4);
+        k0 >>= sh;
+        ke >>= sh;
+        const long long n = (long long)ke - (long long)k0 + 1;
+        if (n <= MAX_TABLE || mb <= 4) {
+            p.tab_shift = sh;
+            p.tab_key0 = k0;
+            p.tab_n = (int)std::min<long long>(n, MAX_TABLE);
+            break;
+        }
+    }
+    pl.table.assign(p.tab_n, CODE_AMBIG);
+    for (int i = 0; i < p.tab_n; i++) {
+        const uint32_t key = p.tab_key0 + (uint32_t)i;
+        uint32_t blo = key << p.tab_shift, bhi = (key + 1) << p.tab_shift;
+        float flo, fhi;
+        std::memcpy(&flo, &blo, 4);
+        std::memcpy(&fhi, &bhi, 4);
+        double vlo = (i == 0) ? 0.0 : (double)flo;
+        double vhi = (i == p.tab_n - 1) ? INFINITY : (double)fhi;
+        int passed = 0, slot = 0;
+        for (int k = 0; k <= b.n_s; k++) {
+            if ((double)p.hi[k] <= vlo) passed++;
+            else if ((double)p.lo[k] >= vhi) {}
+            else slot++;
+        }
+        if (slot == 0) {
+            const int bin = passed - 1;
+            pl.table[i] = (bin < 0 || bin >= b.n_s) ? CODE_DISCARD : (uint16_t)bin;
+        } else if (slot == 1) {
+            pl.table[i] = (uint16_t)(CODE_EDGE | passed);
+        } else {
+            pl.table[i] = CODE_AMBIG;
+        }
+    }
+    return TPCF_OK;
+}
+
+}  // namespace tpcf

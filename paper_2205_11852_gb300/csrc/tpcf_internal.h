@@ -1,0 +1,129 @@
+// Internal declarations shared by the CUDA translation units of libtpcf.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tpcf.h"
+
+namespace tpcf {
+
+constexpr int MAX_NS = 256;          // s bins
+constexpr int MAX_NBIN = 4096;       // s bins x mu bins
+constexpr int MAX_NC = 1024;         // mesh cells per axis
+constexpr int MAX_ROWS = 81;         // (2K+1)^2 neighbour rows, K <= 4
+constexpr int MAX_TABLE = 16384;     // s-bin lookup slots
+
+// s-bin lookup codes (uint16): a plain bin, an edge-slot marker, or a sentinel
+constexpr uint16_t CODE_EDGE = 0x8000;      // low 15 bits: edge index e; bin e-1 below, e above
+constexpr uint16_t CODE_DISCARD = 0x7FFE;   // slot lies entirely outside [T_0, T_ns)
+constexpr uint16_t CODE_AMBIG = 0x7FFD;     // slot holds several edges: always recheck exactly
+
+// One pair-count term: histogram of pairs between catalogue A and catalogue B.
+struct Term {
+    int cat_a;
+    int cat_b;
+    int auto_pairs;        // 1: A == B, unordered pairs of distinct points
+    int pad;
+    long long *hist;       // caller's int64 output row [nbin]
+};
+
+// One catalogue in the packed point arrays.
+struct Cat {
+    const double *xyz;     // caller's float64 [n][3], or nullptr
+    const uint32_t *u32;   // caller's pre-quantised [3][n] (row stride n), or nullptr
+    uint32_t p0;           // first index in the packed arrays
+    uint32_t n;            // number of points
+};
+
+// A work unit: a chunk of the points of one mesh cell of catalogue A, paired
+// against the neighbourhood of that cell in catalogue B for term t.
+struct Unit {
+    int term;
+    int cell;              // linear cell index in catalogue A
+    uint32_t a0, a1;       // packed sorted index range of the a-points
+};
+
+// Everything the pair-count kernels need, passed by value.
+struct CountParams {
+    int geometry;          // TPCF_PERIODIC | TPCF_OPEN
+    int los;               // TPCF_LOS_X | TPCF_LOS_MIDPOINT
+    int n_s, n_mu, nbin;
+    int n_c;               // cells per axis
+    int n_cells;           // n_c^3
+    int bits;              // 32 (periodic) or 30 (open)
+    int n_rows;            // neighbour rows (dz, dy) with a non-empty x range
+    int8_t row_dz[MAX_ROWS], row_dy[MAX_ROWS], row_kx[MAX_ROWS];
+    // s-bin lookup over float bit patterns of d2
+    int tab_shift;         // key = bits(d2) >> tab_shift
+    uint32_t tab_key0;     // first key in the table
+    int tab_n;             // table slots
+    float hit_max;         // upper band of T_ns: d2 >= hit_max is never binned
+    float mu_c1, mu_c2;    // mu ambiguity band: beta = mu_c1 / sqrt(d2) + mu_c2 (+ mu_c3 / |l| for the midpoint)
+    float mu_c3;
+    float inv_nmu2;        // 1 / n_mu^2
+    long long obs[3];      // observer in grid units (midpoint line of sight)
+    unsigned long long T[MAX_NS + 1];   // exact squared edges in grid units
+    float lo[MAX_NS + 1], hi[MAX_NS + 1];   // float bands: d2 < lo => D2 < T; d2 >= hi => D2 >= T
+};
+
+// Workspace layout produced by the mesh build and consumed by the counters.
+struct Mesh {
+    const float4 *pf;          // sorted: cell-relative float coords, .w = cell x index (int bits)
+    const uint32_t *us;        // sorted exact grid coords [3][n_total]
+    uint32_t n_total;
+    const uint32_t *cellstart; // [n_cat * n_cells + 1] global sorted start of each (cat, cell)
+    const uint32_t *orig;      // [n_c + 1] integer lower corner of each cell column
+};
+
+// device status bits (written with atomicOr, read by tpcf_sync)
+constexpr int STATUS_RANGE = 1;        // position outside the bounding cube
+constexpr int STATUS_EMPTY_BIN = 2;    // rr == 0 in the LS estimator
+constexpr int STATUS_TIMEOUT = 4;      // bounded wait gave up
+
+// ---- launchers (each returns cudaError_t of the launch) ----
+cudaError_t launch_quantize_keys(const Cat *cats, int n_cat, uint32_t max_n, const CountParams &p,
+                                 double L, const double *origin, uint32_t n_total, uint32_t *uq,
+                                 uint32_t *keys, uint32_t *cellcount, int *status, cudaStream_t s);
+cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, size_t tmp_n,
+                            cudaStream_t s);
+size_t scan_tmp_elems(size_t n);
+cudaError_t launch_scatter(const Cat *cats, int n_cat, uint32_t max_n, const CountParams &p,
+                           const uint32_t *uq, const uint32_t *keys, const uint32_t *cellstart,
+                           uint32_t *cursor, const uint32_t *orig, uint32_t n_total, uint32_t *us,
+                           float4 *pf, cudaStream_t s);
+cudaError_t launch_unit_count(const Term *terms, int n_terms, const Cat *cats, int n_cells,
+                              const uint32_t *cellstart, int chunk, uint32_t *ucount, cudaStream_t s);
+cudaError_t launch_unit_fill(const Term *terms, int n_terms, const Cat *cats, int n_cells,
+                             const uint32_t *cellstart, int chunk, const uint32_t *ustart, Unit *units,
+                             cudaStream_t s);
+
+struct PairLaunch {
+    int blocks;            // grid size
+    int warps_per_block;
+    int persistent;        // 1: claim units from a global counter; 0: one block per cell of one term
+    int term;              // per-launch mode: the term
+    int smem_bytes;
+};
+cudaError_t launch_paircount(const CountParams &p, const Mesh &m, const Term *terms, const Cat *cats,
+                             const Unit *units, const uint32_t *n_units, unsigned *claim,
+                             const uint16_t *table, unsigned long long *stats, int *status,
+                             const PairLaunch &pl, cudaStream_t s);
+int paircount_smem_bytes(const CountParams &p, int warps_per_block);
+cudaError_t paircount_set_attrs(const CountParams &p, int smem_bytes);
+int paircount_max_blocks_per_sm(const CountParams &p, int warps_per_block, int smem_bytes);
+
+// ---- estimator launchers ----
+cudaError_t launch_ls(const long long *dd, const long long *dr, const long long *rr,
+                      const long long *nd_nr /* [n_mock][1+M] */, const int *sel, int n_sel,
+                      int n_mock, int M, int nbin, double *xi, int *status, cudaStream_t s);
+cudaError_t launch_lc_fp64(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock,
+                           int nbin, double *work /* 3*n_mock*nbin + 3*nbin + 3*nbin*nbin */,
+                           int M_a, double M, double *C_lc, double *Ca, double *Cb, double *A, double *B,
+                           cudaStream_t s);
+cudaError_t launch_lc_split(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock,
+                            int nbin, int precision, void *work, size_t work_bytes, int M_a, double M,
+                            double *C_lc, double *Ca, double *Cb, double *A, double *B, cudaStream_t s);
+size_t lc_split_work_bytes(int n_mock, int nbin, int precision);
+
+}  // namespace tpcf

@@ -1,0 +1,340 @@
+"""GPU parity: the CUDA library against the CPU oracle, through the C ABI.
+
+Counts must match bit for bit; float64 estimator steps within 1e-12
+(|x - x_oracle| / (1 + |x_oracle|) for xi; |C - C_oracle| / sqrt(C^a_ii C^a_jj)
+for covariance elements).  Inputs are seeded synthetic catalogues shaped like
+the measurement workloads: Neyman-Scott data with uniform randoms in periodic
+boxes, and a cut-sky octant shell with a midpoint line of sight.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def tp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2205_11852_gb300 as tp
+    return tp
+
+
+@pytest.fixture(scope="module")
+def ctx(tp):
+    c = tp.Context(0)
+    yield c
+    c.close()
+
+
+DEV = "cuda:0"
+
+
+def _mocks_to_device(mocks):
+    out = []
+    for mk in mocks:
+        n_r = [len(r) for r in mk.randoms]
+        offs = [0] + list(np.cumsum(n_r))
+        out.append({"data": torch.from_numpy(np.ascontiguousarray(mk.data)).to(DEV),
+                    "randoms": torch.from_numpy(np.ascontiguousarray(np.concatenate(mk.randoms)
+                                                                     if mk.randoms else np.zeros((0, 3)))).to(DEV),
+                    "offsets": offs})
+    return out
+
+
+def _check_counts(ctx, tp, mocks, tb, ob, modes=(0, 1), terms=7):
+    dm = _mocks_to_device(mocks)
+    for mode in modes:
+        out = ctx.tpcf_count(dm, tb, terms=terms, mode=mode)
+        assert ctx.tpcf_sync() == tp.TPCF_OK
+        info = ctx.tpcf_last_count_info()
+        tot = 0
+        for m, mk in enumerate(mocks):
+            ref = oracle.count_mock(mk.data, mk.randoms, ob)
+            if terms & 1:
+                assert np.array_equal(out["dd"][m].cpu().numpy(), ref["DD"]), (mode, m, "DD")
+                tot += ref["DD"].sum()
+            if terms & 2:
+                assert np.array_equal(out["dr"][m].cpu().numpy(), ref["DR"]), (mode, m, "DR")
+                tot += ref["DR"].sum()
+            if terms & 4:
+                assert np.array_equal(out["rr"][m].cpu().numpy(), ref["RR"]), (mode, m, "RR")
+                tot += ref["RR"].sum()
+        assert info["n_binned"] == tot
+        assert info["n_candidates"] >= tot
+    return out
+
+
+def _periodic(L, edges, n_mu):
+    import paper_2205_11852_gb300 as tp
+    return tp.make_binning(edges, n_mu, tp.TPCF_PERIODIC, L), oracle.Binning(edges, n_mu, oracle.PERIODIC, L)
+
+
+# ---------------------------------------------------------------------------
+# counts
+# ---------------------------------------------------------------------------
+
+def test_counts_periodic_s_only(tp, ctx):
+    """Small-workload shape: Neyman-Scott data, 2 random subsets, 20 linear s bins to s_max = L/5."""
+    L = 500.0
+    mocks = [synth.SMALL.make_mock(m, n_d=2500, M=2) for m in range(3)]
+    tb, ob = _periodic(L, np.linspace(0, 100.0, 21), 1)
+    _check_counts(ctx, tp, mocks, tb, ob)
+
+
+def test_counts_periodic_s_mu(tp, ctx):
+    """Mid-workload shape scaled down: 40 s x 10 mu bins, plane-parallel line of sight."""
+    L = 400.0
+    w = synth.Workload("t", 31, 2, "periodic", L, (0, 0, 0), 3000, 2, 80.0, 40, 10, "x", n_parent=4e-5, sigma=3.0)
+    mocks = [w.make_mock(m) for m in range(2)]
+    tb, ob = _periodic(L, w.s_edges, 10)
+    _check_counts(ctx, tp, mocks, tb, ob)
+
+
+@pytest.mark.parametrize("subdiv", [1, 2, 3, 4])
+def test_counts_any_mesh_subdivision(tp, ctx, subdiv):
+    L = 300.0
+    w = synth.Workload("t", 32, 1, "periodic", L, (0, 0, 0), 1800, 2, 60.0, 12, 5, "x", n_parent=5e-5, sigma=2.0)
+    mocks = [w.make_mock(0)]
+    tb, ob = _periodic(L, w.s_edges, 5)
+    ctx.tpcf_set_cell_subdiv(subdiv)
+    try:
+        _check_counts(ctx, tp, mocks, tb, ob, modes=(0,))
+    finally:
+        ctx.tpcf_set_cell_subdiv(0)
+
+
+def test_counts_open_midpoint(tp, ctx):
+    """Cut-sky octant shell, observer at the origin, midpoint line of sight (batching shape, scaled)."""
+    L = 600.0
+    w = synth.Workload("t", 33, 2, "open", L, (0, 0, 0), 2500, 2, 50.0, 20, 5, "midpoint",
+                       n_parent=2e-5, sigma=3.0, shell=(300.0, 600.0))
+    mocks = [w.make_mock(m) for m in range(2)]
+    edges = np.linspace(0, 50.0, 21)
+    tb = tp.make_binning(edges, 5, tp.TPCF_OPEN, L, los=tp.TPCF_LOS_MIDPOINT, observer=(0, 0, 0))
+    ob = oracle.Binning(edges, 5, oracle.OPEN, L, los=oracle.LOS_MIDPOINT, observer=(0, 0, 0))
+    _check_counts(ctx, tp, mocks, tb, ob)
+
+
+def test_counts_open_plane_parallel_slab(tp, ctx):
+    """Open slab geometry with the x line of sight (the paper's slab setup, Sect. 4.1, scaled)."""
+    L = 300.0
+    rng = synth.rng_for(34, 0, 0)
+    d = rng.random((2000, 3)) * np.array([L, L, L / 5])
+    r = [rng.random((2000, 3)) * np.array([L, L, L / 5]) for _ in range(2)]
+    mocks = [synth.Mock(d, r)]
+    edges = np.linspace(0, 40.0, 17)
+    tb = tp.make_binning(edges, 8, tp.TPCF_OPEN, L, los=tp.TPCF_LOS_X)
+    ob = oracle.Binning(edges, 8, oracle.OPEN, L, los=oracle.LOS_X)
+    _check_counts(ctx, tp, mocks, tb, ob)
+
+
+def test_counts_golden_edge_pairs(tp, ctx):
+    g = json.load(open(os.path.join(GOLDEN, "edge_pairs.json")))
+    for section in ("periodic", "open_midpoint"):
+        s = g[section]
+        if section == "periodic":
+            tb = tp.make_binning(s["s_edges"], s["n_mu"], tp.TPCF_PERIODIC, s["L"])
+        else:
+            tb = tp.make_binning(s["s_edges"], s["n_mu"], tp.TPCF_OPEN, s["L"], los=tp.TPCF_LOS_MIDPOINT,
+                                 observer=s["observer"])
+        nbin = len(s["s_edges"]) - 1
+        nbin *= s["n_mu"]
+        for p in s["pairs"]:
+            a = torch.tensor(np.array(p["a"], dtype=np.uint32).reshape(3, 1).view(np.int32), device=DEV)
+            b = torch.tensor(np.array(p["b"], dtype=np.uint32).reshape(3, 1).view(np.int32), device=DEV)
+            ab = torch.tensor(np.array([p["a"], p["b"]], dtype=np.uint32).T.copy().view(np.int32), device=DEV)
+            # cross: D = {a}, R_1 = {b};  auto: RR of R_2 = {a, b}
+            rr = torch.cat([b, ab], dim=1).contiguous()
+            mk = {"data_u32": a.contiguous(), "randoms_u32": rr, "offsets": [0, 1, 3]}
+            out = ctx.tpcf_count([mk], tb)
+            assert ctx.tpcf_sync() == tp.TPCF_OK
+            exp = np.zeros(nbin, np.int64)
+            if p["bin"] >= 0:
+                exp[p["bin"]] = 1
+            assert np.array_equal(out["dr"][0, 0].cpu().numpy(), exp), p["why"]
+            assert np.array_equal(out["rr"][0, 1].cpu().numpy(), exp), p["why"]
+            assert out["dd"][0].sum().item() == 0 and out["rr"][0, 0].sum().item() == 0
+
+
+def test_counts_duplicates_tiny_and_empty(tp, ctx):
+    L = 200.0
+    rng = np.random.default_rng(1)
+    base = rng.random((40, 3)) * L
+    dup = np.repeat(base, 7, axis=0)                       # 7 coincident copies of each point
+    tiny = base[:1]
+    empty = np.zeros((0, 3))
+    tb, ob = _periodic(L, np.array([0.0, 0.5, 10.0, 30.0, 60.0]), 3)
+    cases = [synth.Mock(dup, [dup[:100], base]), synth.Mock(tiny, [tiny, empty]), synth.Mock(empty, [base, tiny]),
+             synth.Mock(base, [empty, empty])]
+    _check_counts(ctx, tp, cases, tb, ob)
+
+
+def test_u32_input_matches_float_input(tp, ctx):
+    L = 400.0
+    mk = synth.SMALL.make_mock(5, n_d=1500, M=2)
+    tb, ob = _periodic(L, np.linspace(0, 100.0, 11), 4)
+    f = ctx.tpcf_count(_mocks_to_device([mk]), tb)
+    ctx.tpcf_sync()
+    qd = oracle.quantize(mk.data, oracle.PERIODIC, L)
+    qr = np.concatenate([oracle.quantize(r, oracle.PERIODIC, L) for r in mk.randoms], axis=1)
+    m = {"data_u32": torch.from_numpy(qd.view(np.int32).copy()).to(DEV),
+         "randoms_u32": torch.from_numpy(qr.view(np.int32).copy()).to(DEV), "offsets": [0, 1500, 3000]}
+    u = ctx.tpcf_count([m], tb)
+    ctx.tpcf_sync()
+    for k in ("dd", "dr", "rr"):
+        assert torch.equal(f[k], u[k])
+
+
+def test_terms_subset_and_output_untouched(tp, ctx):
+    L = 300.0
+    mk = synth.SMALL.make_mock(6, n_d=800, M=2)
+    tb, ob = _periodic(L, np.linspace(0, 50.0, 6), 1)
+    ref = oracle.count_mock(mk.data, mk.randoms, ob)
+    out = ctx.tpcf_count(_mocks_to_device([mk]), tb, terms=tp.TPCF_DR)
+    ctx.tpcf_sync()
+    assert np.array_equal(out["dr"][0].cpu().numpy(), ref["DR"])
+
+
+def test_open_geometry_position_outside_cube_reports_range(tp, ctx):
+    edges = np.linspace(0, 10.0, 3)
+    tb = tp.make_binning(edges, 1, tp.TPCF_OPEN, 100.0)
+    d = torch.tensor([[1.0, 1.0, 1.0], [150.0, 1.0, 1.0]], dtype=torch.float64, device=DEV)
+    ctx.tpcf_count([{"data": d, "randoms": d.clone(), "offsets": [0, 2]}], tb)
+    with pytest.raises(tp.TpcfError) as e:
+        ctx.tpcf_sync()
+    assert e.value.code == tp.TPCF_ERR_RANGE
+    # the context stays usable
+    d2 = torch.tensor([[1.0, 1.0, 1.0], [5.0, 1.0, 1.0]], dtype=torch.float64, device=DEV)
+    out = ctx.tpcf_count([{"data": d2, "randoms": d2.clone(), "offsets": [0, 2]}], tb)
+    assert ctx.tpcf_sync() == tp.TPCF_OK
+    assert out["dd"][0].tolist() == [1, 0]
+
+
+def test_bad_arguments_rejected(tp, ctx):
+    tb = tp.make_binning([0.0, 10.0], 1, tp.TPCF_PERIODIC, 100.0)
+    d = torch.zeros((3, 3), dtype=torch.float64, device=DEV)
+    with pytest.raises(tp.TpcfError):
+        ctx.tpcf_count([{"data": d, "randoms": d, "offsets": [0, 3]}], tb, terms=0)
+    with pytest.raises(tp.TpcfError):
+        ctx.tpcf_count([{"data": d, "randoms": d, "offsets": [0, 2, 1]}], tb)
+    tbad = tp.make_binning([0.0, 40.0], 1, tp.TPCF_PERIODIC, 100.0)
+    with pytest.raises(tp.TpcfError) as e:
+        ctx.tpcf_count([{"data": d, "randoms": d, "offsets": [0, 3]}], tbad)
+    assert e.value.code == tp.TPCF_ERR_RANGE
+
+
+# ---------------------------------------------------------------------------
+# estimator and covariance
+# ---------------------------------------------------------------------------
+
+def _xi_err(x, r):
+    both_nan = np.isnan(x) & np.isnan(r)
+    e = np.abs(x - r) / (1.0 + np.abs(r))
+    e[both_nan] = 0.0
+    return float(np.nanmax(e)) if e.size else 0.0, bool(np.all(np.isnan(x) == np.isnan(r)))
+
+
+def test_ls_parity(tp, ctx):
+    rng = np.random.default_rng(4)
+    n_mock, M, nbin = 7, 3, 33
+    n_d = rng.integers(50, 5000, n_mock)
+    n_r = rng.integers(50, 9000, (n_mock, M))
+    DD = rng.integers(0, 10 ** 9, (n_mock, nbin))
+    DR = rng.integers(0, 10 ** 9, (n_mock, M, nbin))
+    RR = rng.integers(0, 10 ** 9, (n_mock, M, nbin))
+    RR[2, :, 5] = 0                            # an empty bin -> NaN + warning
+    g = [torch.from_numpy(a).to(DEV) for a in (DD, DR, RR)]
+    for sel in ([0], [1], [0, 1], [0, 1, 2], [2, 0]):
+        xi = ctx.tpcf_ls(*g, n_d, n_r, sel)
+        rc = ctx.tpcf_sync()
+        ref = np.array([oracle.ls(DD[m], DR[m], RR[m], n_d[m], n_r[m], sel) for m in range(n_mock)])
+        err, nan_ok = _xi_err(xi.cpu().numpy(), ref)
+        assert nan_ok and err <= 1e-12, (sel, err)
+        assert rc == tp.TPCF_WARN_EMPTY_BIN
+
+
+@pytest.mark.parametrize("M", [1.0, 2.0, 50.0, math.inf])
+def test_lc_fp64_parity(tp, ctx, M):
+    xa1, xa2, xb = synth.synthetic_xi_variants(41, 120, 37)
+    g = [torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in (xa1, xa2, xb)]
+    out = ctx.tpcf_lc_cov(*g, 1, M, tp.TPCF_FP64)
+    ctx.tpcf_sync()
+    ref = oracle.lc_cov(xa1, xa2, xb, 1, M)
+    d = np.sqrt(np.diag(ref["Ca"]))
+    scale = np.outer(d, d)
+    for k in ("C_lc", "Ca", "Cb", "A", "B"):
+        err = np.max(np.abs(out[k].cpu().numpy() - ref[k]) / scale)
+        assert err <= 1e-12, (k, err)
+
+
+def test_lc_fp64_ragged_large_nbin(tp, ctx):
+    xa1, xa2, xb = synth.synthetic_xi_variants(42, 301, 200)
+    g = [torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in (xa1, xa2, xb)]
+    out = ctx.tpcf_lc_cov(*g, 1, 50.0, tp.TPCF_FP64)
+    ctx.tpcf_sync()
+    ref = oracle.lc_cov(xa1, xa2, xb, 1, 50.0)
+    d = np.sqrt(np.diag(ref["Ca"]))
+    err = np.max(np.abs(out["C_lc"].cpu().numpy() - ref["C_lc"]) / np.outer(d, d))
+    assert err <= 1e-12
+
+
+def test_end_to_end_counts_ls_lc(tp, ctx):
+    """Counts -> split LS (R1, R2, R1 u R2) -> LC covariance, all on the GPU, against the oracle chain."""
+    L = 300.0
+    n, n_mock = 900, 6
+    mocks = [synth.SMALL.make_mock(100 + m, n_d=n, M=2) for m in range(n_mock)]
+    tb, ob = _periodic(L, np.linspace(0, 60.0, 7), 2)
+    out = ctx.tpcf_count(_mocks_to_device(mocks), tb)
+    xs = {}
+    for key, sel in (("a1", [0]), ("a2", [1]), ("b", [0, 1])):
+        xs[key] = ctx.tpcf_ls(out["dd"], out["dr"], out["rr"], [n] * n_mock, [[n, n]] * n_mock, sel)
+    cov = ctx.tpcf_lc_cov(xs["a1"], xs["a2"], xs["b"], 1, 50.0, tp.TPCF_FP64)
+    ctx.tpcf_sync()
+    ref_x = {k: [] for k in xs}
+    for mk in mocks:
+        c = oracle.count_mock(mk.data, mk.randoms, ob)
+        for key, sel in (("a1", [0]), ("a2", [1]), ("b", [0, 1])):
+            ref_x[key].append(oracle.ls(c["DD"], c["DR"], c["RR"], n, [n, n], sel))
+    for key in xs:
+        err, _ = _xi_err(xs[key].cpu().numpy(), np.array(ref_x[key]))
+        assert err <= 1e-12
+    ref = oracle.lc_cov(*(np.array(ref_x[k]) for k in ("a1", "a2", "b")), 1, 50.0)
+    d = np.sqrt(np.abs(np.diag(ref["Ca"])))
+    assert np.max(np.abs(cov["C_lc"].cpu().numpy() - ref["C_lc"]) / np.outer(d, d)) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# full-size mock of the mid workload (1e5 data points, 2 x 1e5 randoms, 40 x 10 bins)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_full_size_mid_mock_bit_exact(tp, ctx):
+    w = synth.MID
+    mk = w.make_mock(0)
+    tb = tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_PERIODIC, w.L)
+    ob = oracle.Binning(w.s_edges, w.n_mu, oracle.PERIODIC, w.L)
+    dm = _mocks_to_device([mk])
+    out = ctx.tpcf_count(dm, tb, mode=tp.TPCF_BATCHED)
+    ctx.tpcf_sync()
+    ref = oracle.count_mock(mk.data, mk.randoms, ob)
+    assert np.array_equal(out["dd"][0].cpu().numpy(), ref["DD"])
+    assert np.array_equal(out["dr"][0].cpu().numpy(), ref["DR"])
+    assert np.array_equal(out["rr"][0].cpu().numpy(), ref["RR"])
+    out2 = ctx.tpcf_count(dm, tb, mode=tp.TPCF_PER_LAUNCH)
+    ctx.tpcf_sync()
+    for k in ("dd", "dr", "rr"):
+        assert torch.equal(out[k], out2[k])
