@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the LC covariance hot path on the mid workload.
+
+Workload (per GPU, weak scaling): 100 mocks in a periodic box L = 1000 Mpc/h,
+N_d = 100 000 Neyman-Scott points (parents 1e-5 (Mpc/h)^-3, sigma = 3 Mpc/h)
+and two uniform random subsets R1, R2 of N_d points each (the M_a = 1 pair of
+the linear construction), 40 linear s bins on [0, 200) Mpc/h x 10 mu bins
+with the x line of sight.
+
+One step = the whole hot path: quantisation + chaining-mesh build + pair
+counts DD, DR1, DR2, RR1, RR2 of every mock (one persistent launch) + split
+Landy-Szalay for R1, R2 and R1 u R2 + the LC covariance (Eqs. R1R2, LCdef)
+with M = 50.  `value` is mocks/s with inputs resident in HBM; `e2e` is the
+same metric through the public API with the positions copied from pinned
+host memory and C^LC copied back inside every step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "G pairs/s binned + LC-cov mocks/s, batched vs per-mock launch; cov err vs FP64"
+LANE_OPS_PER_CAND = 7      # 3 sub + 3 mul/fma + 1 compare per candidate pair
+LANE_OPS_PER_BINNED = 8    # s-bin, mu-bin, address, shared atomic per binned pair
+SM_MAX_MHZ = 2070.0        # GB300 maximum SM clock
+LANES_PER_SM = 128         # FP32/INT32 lanes per SM
+M_FINAL = 50.0             # random-catalogue size of the target covariance (the paper's M = 50)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--mocks", type=int, default=synth.MID.n_mock, help="mocks per GPU")
+    p.add_argument("--nd", type=int, default=synth.MID.n_d, help="data points per mock")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "tf32x3", "bf16x3"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_host_inputs(n_mock, n_d, first_mock):
+    """Positions of all mocks in one float64 array; per mock (data, R1, R2) offsets."""
+    w = synth.MID
+    blocks, layout = [], []
+    off = 0
+    for m in range(first_mock, first_mock + n_mock):
+        mk = w.make_mock(m, n_d=n_d, M=2)
+        parts = [mk.data] + mk.randoms
+        sizes = [len(x) for x in parts]
+        layout.append((off, sizes))
+        blocks.extend(parts)
+        off += sum(sizes)
+    return np.concatenate(blocks), layout
+
+
+def mock_views(pos_dev, layout):
+    mocks = []
+    for off, (nd, n1, n2) in layout:
+        mocks.append({"data": pos_dev[off:off + nd], "randoms": pos_dev[off + nd:off + nd + n1 + n2],
+                      "offsets": [0, n1, n1 + n2]})
+    return mocks
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate(n_d, target_s, seed_mock=0):
+    """Time the oracle's brute-force counts on a row sample of one mid mock.
+
+    The five terms of one mock cost 3.5 N_d^2 pair tests (DD and RR_i: N_d^2/2
+    each, DR_i: N_d^2 each).  A sample of k a-rows against all b-points costs
+    k N_d tests per term; the rate in mocks/s is the sampled fraction of the
+    mock's pair tests divided by the time taken.
+    """
+    import oracle
+    w = synth.MID
+    mk = w.make_mock(seed_mock, n_d=n_d, M=2)
+    ob = oracle.Binning(w.s_edges, w.n_mu, oracle.PERIODIC, w.L)
+    qd = oracle.quantize(mk.data, oracle.PERIODIC, w.L)
+    qr = [oracle.quantize(r, oracle.PERIODIC, w.L) for r in mk.randoms]
+
+    def run(k):
+        t0 = time.perf_counter()
+        tests = 0
+        a = np.ascontiguousarray(qd[:, :k])
+        oracle.count_pairs(a, qd, ob)      # DD rows (each row against all: twice the auto work)
+        tests += k * n_d / 2
+        for r in qr:
+            oracle.count_pairs(a, r, ob)   # DR_i rows
+            tests += k * n_d
+            ar = np.ascontiguousarray(r[:, :k])
+            oracle.count_pairs(ar, r, ob)  # RR_i rows
+            tests += k * n_d / 2
+        return time.perf_counter() - t0, tests
+
+    k = max(16, n_d // 2000)
+    dt, tests = run(k)
+    k2 = int(min(n_d, k * max(1.0, target_s / max(dt, 1e-3))))
+    if k2 > k:
+        dt, tests = run(k2)
+        k = k2
+    full = 3.5 * n_d * n_d
+    frac = tests / full
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"mocks_per_s": frac / dt, "seconds": dt, "rows": k, "fraction_of_mock": frac, "cores": cores,
+            "pair_tests_per_s": tests / dt}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle as it stands, on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample_rate(args.nd, target_s=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
+        if i >= args.warmup:
+            rates.append(r)
+    v = statistics.median([r["mocks_per_s"] for r in rates])
+    sample = (f"brute-force counts of {rates[0]['rows']} a-rows of mock 0 against all points "
+              f"(DD, DR1, DR2, RR1, RR2), {rates[0]['fraction_of_mock']:.3%} of one mock's pair tests per step")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "mocks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.median(
+                [r["seconds"] for r in rates]), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"mid: {args.mocks} mocks/GPU, periodic L=1000, N_d={args.nd} Neyman-Scott, "
+                                   "R1+R2 of N_d each, 40 s x 10 mu bins to 200", "global_batch": args.mocks * world},
+            "cpu_baseline": {"value": v, "unit": "mocks/s", "cores": rates[0]["cores"], "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "mocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2205_11852_gb300 as tp
+
+    dev = torch.device("cuda", local)
+    w = synth.MID
+    n_mock, n_d = args.mocks, args.nd
+    prec = {"fp64": tp.TPCF_FP64, "tf32x3": tp.TPCF_TF32X3, "bf16x3": tp.TPCF_BF16X3}[args.precision]
+
+    host, layout = make_host_inputs(n_mock, n_d, rank * n_mock)
+    pinned = torch.from_numpy(host).pin_memory()
+    pos = pinned.to(dev)
+    mocks = mock_views(pos, layout)
+    nd_list = [sz[0] for _, sz in layout]
+    nr_list = [[sz[1], sz[2]] for _, sz in layout]
+    ctx = tp.Context(local)
+    b = tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_PERIODIC, w.L)
+    nbin = w.n_s * w.n_mu
+    outc = {"dd": torch.empty((n_mock, nbin), dtype=torch.int64, device=dev),
+            "dr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev),
+            "rr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev)}
+    xi = {k: torch.empty((n_mock, nbin), dtype=torch.float64, device=dev) for k in ("a1", "a2", "b")}
+    sels = {"a1": [0], "a2": [1], "b": [0, 1]}
+    gather = None
+    if world > 1:
+        import torch.distributed as dist
+        gather = {k: torch.empty((world * n_mock, nbin), dtype=torch.float64, device=dev) for k in xi}
+
+    def step(mode=tp.TPCF_BATCHED, mocks_in=None):
+        ctx.tpcf_count(mocks_in or mocks, b, mode=mode, out=outc)
+        for k, sel in sels.items():
+            ctx.tpcf_ls(outc["dd"], outc["dr"], outc["rr"], nd_list, nr_list, sel, out=xi[k])
+        src = xi
+        if gather is not None:
+            import torch.distributed as dist
+            for k in xi:
+                dist.all_gather_into_tensor(gather[k], xi[k])
+            src = gather
+        return ctx.tpcf_lc_cov(src["a1"], src["a2"], src["b"], 1, M_FINAL, prec, want_parts=False)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # correctness of the timed configuration: batched == per-launch on 2 mocks
+    chk_b = ctx.tpcf_count(mocks[:2], b, mode=tp.TPCF_BATCHED)
+    chk_p = ctx.tpcf_count(mocks[:2], b, mode=tp.TPCF_PER_LAUNCH)
+    ctx.tpcf_sync()
+    same = all(torch.equal(chk_b[k], chk_p[k]) for k in ("dd", "dr", "rr"))
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    ctx.tpcf_set_timing(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        cov = step()
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    rc = ctx.tpcf_sync()
+    info = ctx.tpcf_last_count_info()
+    ctx.tpcf_set_timing(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    mocks_total = n_mock * world
+    value = mocks_total / (ms * 1e-3)
+
+    # pair-count kernel roofline (ALU-bound): algorithmic lane-ops / kernel time
+    n_cand, n_binned = info["n_candidates"], info["n_binned"]
+    k_ms = info["paircount_ms"] / max(1, info["timed_calls"])
+    lane_ops = LANE_OPS_PER_CAND * n_cand + LANE_OPS_PER_BINNED * n_binned
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = n_sm * LANES_PER_SM * SM_MAX_MHZ * 1e6
+    achieved = lane_ops / (k_ms * 1e-3)
+    f_run = clocks.get("sm_mhz") or SM_MAX_MHZ
+    gpairs = n_binned / (k_ms * 1e-3) / 1e9
+
+    # plain per-launch path on the same GPU (one launch per mock, term and subset)
+    for _ in range(1):
+        step(mode=tp.TPCF_PER_LAUNCH)
+    barrier()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_pl = max(1, min(args.steps, 3))
+    p0.record(stream)
+    for _ in range(n_pl):
+        step(mode=tp.TPCF_PER_LAUNCH)
+    p1.record(stream)
+    barrier()
+    ms_pl = p0.elapsed_time(p1) / n_pl
+    per_launch = mocks_total / (ms_pl * 1e-3)
+
+    # end to end through the public API: positions from pinned host memory,
+    # C^LC read back, every step
+    h2d = pinned.numel() * pinned.element_size()
+    d2h = nbin * nbin * 8
+    res_host = torch.empty((nbin, nbin), dtype=torch.float64).pin_memory()
+    pos2 = torch.empty_like(pos)
+    mocks2 = mock_views(pos2, layout)
+    barrier()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for _ in range(args.steps):
+        pos2.copy_(pinned, non_blocking=True)
+        c = step(mocks_in=mocks2)
+        res_host.copy_(c["C_lc"], non_blocking=True)
+    q1.record(stream)
+    barrier()
+    ms_e2e = q0.elapsed_time(q1) / args.steps
+    te = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = mocks_total / (float(te.item()) * 1e-3)
+
+    # covariance error of the timed path against the float64 oracle construction on the same xi
+    cov_err = None
+    if rank == 0:
+        import oracle
+        src = gather if gather is not None else xi
+        ref = oracle.lc_cov(src["a1"].cpu().numpy(), src["a2"].cpu().numpy(), src["b"].cpu().numpy(), 1, M_FINAL)
+        d = np.sqrt(np.abs(np.diag(ref["Ca"])))
+        scale = np.outer(d, d)
+        scale[scale == 0] = 1.0
+        cov_err = float(np.max(np.abs(cov["C_lc"].cpu().numpy() - ref["C_lc"]) / scale))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample_rate(n_d, args.cpu_seconds)
+        cpu = {"value": r["mocks_per_s"], "unit": "mocks/s", "cores": r["cores"], "kind": "oracle",
+               "sample": (f"brute-force counts of {r['rows']} a-rows of mock 0 against all points (DD, DR1, "
+                          f"DR2, RR1, RR2), {r['fraction_of_mock']:.3%} of one mock's pair tests, "
+                          f"{r['seconds']:.1f} s")}
+
+    kernels_per_step = info["n_kernels"] + 3 + 4
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "mocks/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": (f"mid: {n_mock} mocks/GPU, periodic L=1000 Mpc/h, N_d={n_d} Neyman-Scott "
+                                    "(n_p=1e-5, sigma=3), R1+R2 uniform of N_d each, 40 s x 10 mu bins to "
+                                    "200 Mpc/h, LOS x; LS + LC covariance (M=50)"),
+                       "global_batch": mocks_total, "cov_precision": args.precision,
+                       "l2": "inputs larger than L2 (positions and mesh > 129 MB)"},
+            "gpairs_binned_per_s": gpairs,
+            "pairs_binned_per_step": n_binned * world,
+            "candidate_pairs_per_step": n_cand * world,
+            "per_launch": {"value": per_launch, "unit": "mocks/s", "ms_per_step": ms_pl,
+                           "batched_over_per_launch": value / per_launch},
+            "batched_equals_per_launch": bool(same),
+            "cov_err_vs_fp64": cov_err,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-op/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "frac_at_run_clock": achieved / (n_sm * LANES_PER_SM * f_run * 1e6),
+                         "kernel": "paircount_kernel", "kernel_ms": k_ms,
+                         "lane_ops_per_launch": lane_ops, "exact_rechecks": info["n_exact"]},
+            "clocks": clocks,
+            "e2e": {"value": e2e, "unit": "mocks/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": kernels_per_step * args.steps,
+            "status": rc,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -195,9 +195,11 @@ int tpcf_thresholds(tpcf_ctx *ctx, const tpcf_binning *binning, uint64_t *T_out)
  * Work statistics of the last tpcf_count on this context, valid after
  * tpcf_sync: candidate pairs tested by the pair-count kernel(s), pairs
  * that fell in a bin, pairs that needed the exact integer recheck, the
- * number of work units, and (when timing is enabled) the pair-count
- * kernels' device time in milliseconds measured with CUDA events on the
- * launch stream.  Any pointer may be NULL.
+ * number of work units, the number of kernels the call launched, and the
+ * mesh it used.  When timing is enabled, paircount_ms is the total device
+ * time of the pair-count kernels of every tpcf_count since timing was
+ * (re-)enabled, over timed_calls calls, measured with CUDA events recorded
+ * on the launch stream around those kernels.
  */
 typedef struct {
     int64_t n_candidates;
@@ -206,13 +208,18 @@ typedef struct {
     int64_t n_units;
     double  paircount_ms;
     int     n_paircount_launches;
-    int     cell_subdiv;      /* cells per s_max along an axis, chosen by the planner/autotuner */
+    int     cell_subdiv;      /* cells per s_max along an axis */
     int     cells_per_axis;
+    int     n_kernels;        /* kernels launched by the last tpcf_count */
+    int     timed_calls;      /* tpcf_count calls accumulated in paircount_ms */
 } tpcf_count_info;
 
 int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info);
 
-/* Enable (1) or disable (0) CUDA-event timing of the pair-count kernels. */
+/*
+ * Enable (1) or disable (0) CUDA-event timing of the pair-count kernels.
+ * Enabling resets the accumulated time; at most 4096 calls are accumulated.
+ */
 int tpcf_set_timing(tpcf_ctx *ctx, int enable);
 
 /*

@@ -57,7 +57,7 @@ class tpcf_count_info(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int64), ("n_binned", ctypes.c_int64), ("n_exact", ctypes.c_int64),
                 ("n_units", ctypes.c_int64), ("paircount_ms", ctypes.c_double),
                 ("n_paircount_launches", ctypes.c_int), ("cell_subdiv", ctypes.c_int),
-                ("cells_per_axis", ctypes.c_int)]
+                ("cells_per_axis", ctypes.c_int), ("n_kernels", ctypes.c_int), ("timed_calls", ctypes.c_int)]
 
 
 def load_library() -> ctypes.CDLL:

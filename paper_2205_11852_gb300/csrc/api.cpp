@@ -40,11 +40,13 @@ struct tpcf_ctx {
     int *status = nullptr;                // device status word
     unsigned long long *stats = nullptr;  // device [4]
     unsigned long long *stats_host = nullptr;  // pinned [4]
-    // timing
+    // timing: one event pair per timed tpcf_count
     bool timing = false;
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    std::vector<cudaEvent_t> ev;          // [2 * k]
+    int n_timed = 0;
+    cudaEvent_t done = nullptr;           // recorded after the stats copy of the last tpcf_count
     int last_launches = 0;
-    bool last_timed = false;
+    int last_kernels = 0;
     // planner
     int subdiv_pin = 0;
     std::map<std::string, int> tune_cache;
@@ -220,8 +222,7 @@ int tpcf_create(tpcf_ctx **out, int cuda_device)
     cudaError_t e = cudaSetDevice(cuda_device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, cuda_device);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->staging_free, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreate(&ctx->t0);
-    if (e == cudaSuccess) e = cudaEventCreate(&ctx->t1);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->stats, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->stats_host, 4 * sizeof(unsigned long long));
@@ -247,8 +248,8 @@ void tpcf_destroy(tpcf_ctx *ctx)
         if (kv.second.p) cudaFree(kv.second.p);
     if (ctx->staging.p) cudaFreeHost(ctx->staging.p);
     if (ctx->staging_free) cudaEventDestroy(ctx->staging_free);
-    if (ctx->t0) cudaEventDestroy(ctx->t0);
-    if (ctx->t1) cudaEventDestroy(ctx->t1);
+    if (ctx->done) cudaEventDestroy(ctx->done);
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->status) cudaFree(ctx->status);
     if (ctx->stats) cudaFree(ctx->stats);
     if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
@@ -293,6 +294,7 @@ int tpcf_set_timing(tpcf_ctx *ctx, int enable)
 {
     if (!ctx) return TPCF_ERR_ARG;
     ctx->timing = enable != 0;
+    ctx->n_timed = 0;
     return TPCF_OK;
 }
 
@@ -310,7 +312,7 @@ int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info)
     if (!info) return TPCF_OK;
     std::memset(info, 0, sizeof(*info));
     CK(cudaSetDevice(ctx->device));
-    CK(cudaEventSynchronize(ctx->t1));
+    CK(cudaEventSynchronize(ctx->done));
     info->n_candidates = (int64_t)ctx->stats_host[0];
     info->n_binned = (int64_t)ctx->stats_host[1];
     info->n_exact = (int64_t)ctx->stats_host[2];
@@ -318,11 +320,16 @@ int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info)
     info->n_paircount_launches = ctx->last_launches;
     info->cell_subdiv = ctx->last_subdiv;
     info->cells_per_axis = ctx->last_nc;
-    if (ctx->last_timed) {
+    info->n_kernels = ctx->last_kernels;
+    double total = 0.0;
+    for (int i = 0; i < ctx->n_timed; i++) {
         float ms = 0;
-        CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
-        info->paircount_ms = ms;
+        CK(cudaEventSynchronize(ctx->ev[2 * i + 1]));
+        CK(cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+        total += ms;
     }
+    info->paircount_ms = total;
+    info->timed_calls = ctx->n_timed;
     return TPCF_OK;
 }
 
@@ -369,11 +376,28 @@ int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_bin
     if (n_total >= (1ull << 31)) return fail(ctx, TPCF_ERR_RANGE, "more than 2^31 points in one call");
     if (M < 0) M = 0;
 
-    // plan (autotuned subdivision, cached per geometry/binning and size class)
+    // mesh cap: a few cells per point of the largest catalogue, and the
+    // (catalogue x cell) and (term x cell) tables indexable in 32 bits
+    unsigned long long max_cat = 0, n_cat_est = 0, n_terms_est = 0;
+    for (int m = 0; m < n_mock; m++) {
+        if (need_d) { max_cat = std::max<unsigned long long>(max_cat, mocks[m].n_d); n_cat_est++; }
+        if (need_r)
+            for (int i = 0; i < M; i++) {
+                max_cat = std::max<unsigned long long>(max_cat, mocks[m].rand_offsets[i + 1] - mocks[m].rand_offsets[i]);
+                n_cat_est++;
+            }
+        n_terms_est += ((terms & TPCF_DD) ? 1 : 0) + (unsigned long long)M * (((terms & TPCF_DR) ? 1 : 0) + ((terms & TPCF_RR) ? 1 : 0));
+    }
+    unsigned long long max_cells = std::max<unsigned long long>(64, 4 * max_cat);
+    max_cells = std::min<unsigned long long>(max_cells, 1ull << 24);
+    const unsigned long long tabs = std::max<unsigned long long>(1, std::max(n_cat_est, n_terms_est));
+    max_cells = std::min<unsigned long long>(max_cells, ((1ull << 32) - 2) / tabs);
+
+    // plan (subdivision pinned, or the default)
     int subdiv = ctx->subdiv_pin ? ctx->subdiv_pin : 2;
     Plan pl;
     std::string perr;
-    if ((rc = build_plan(*binning, subdiv, pl, perr))) return fail(ctx, rc, perr);
+    if ((rc = build_plan(*binning, subdiv, max_cells, pl, perr))) return fail(ctx, rc, perr);
     if ((rc = check_mu_width(ctx, binning, pl.prm))) return rc;
     const CountParams &prm = pl.prm;
     ctx->last_subdiv = subdiv;
@@ -434,9 +458,13 @@ int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_bin
         if ((terms & TPCF_RR) && M > 0) CK(cudaMemsetAsync(rr, 0, nb * n_mock * M, s));
     }
     ctx->last_launches = 0;
-    ctx->last_timed = false;
-    std::memset(ctx->stats_host, 0, 4 * sizeof(unsigned long long));
-    if (n_total == 0 || n_terms == 0) return TPCF_OK;
+    ctx->last_kernels = 0;
+    if (n_total == 0 || n_terms == 0) {
+        CK(cudaMemsetAsync(ctx->stats, 0, 4 * sizeof(unsigned long long), s));
+        CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(ctx->done, s));
+        return TPCF_OK;
+    }
 
     // pre-quantised randoms are given as one [3][n_r] array per mock; gather
     // each subset into a contiguous [3][n] staging region on the device
@@ -540,8 +568,20 @@ int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_bin
     const int smem = paircount_smem_bytes(prm, warps);
     CK(paircount_set_attrs(prm, smem));
     CK(cudaMemsetAsync(ctx->stats, 0, 4 * sizeof(unsigned long long), s));
-    if (ctx->timing) CK(cudaEventRecord(ctx->t0, s));
+    int slot = -1;
+    if (ctx->timing && ctx->n_timed < 4096) {
+        slot = ctx->n_timed;
+        while ((int)ctx->ev.size() < 2 * (slot + 1)) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            ctx->ev.push_back(e);
+        }
+    }
+    // kernels of the mesh build: quantize, 3-kernel scan, scatter
+    ctx->last_kernels = 5;
     if (mode == TPCF_BATCHED) {
+        // unit list: count, 3-kernel scan, fill
+        ctx->last_kernels += 5;
         CK(cudaMemsetAsync(uc + (ntc - 1), 0, 4, s));
         CK(launch_unit_count(d_terms, n_terms, d_cats, prm.n_cells, cs, UNIT_CHUNK, uc, s));
         CK(launch_scan_u32(uc, ust, ntc, tmp, tmp_n, s));
@@ -553,12 +593,16 @@ int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_bin
         L.term = 0;
         L.smem_bytes = smem;
         L.blocks = ctx->n_sm * paircount_max_blocks_per_sm(prm, warps, smem);
+        if (slot >= 0) CK(cudaEventRecord(ctx->ev[2 * slot], s));
         CK(launch_paircount(prm, mesh, d_terms, d_cats, units, ust + (ntc - 1), (unsigned *)w_claim, d_tab,
                             ctx->stats, ctx->status, L, s));
+        if (slot >= 0) CK(cudaEventRecord(ctx->ev[2 * slot + 1], s));
         ctx->last_launches = 1;
+        ctx->last_kernels += 1;
         CK(cudaMemsetAsync(ctx->stats + 3, 0, 8, s));
         CK(cudaMemcpyAsync(ctx->stats + 3, ust + (ntc - 1), 4, cudaMemcpyDeviceToDevice, s));
     } else {
+        if (slot >= 0) CK(cudaEventRecord(ctx->ev[2 * slot], s));
         for (int t = 0; t < n_terms; t++) {
             PairLaunch L;
             L.warps_per_block = warps;
@@ -569,15 +613,13 @@ int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_bin
             CK(launch_paircount(prm, mesh, d_terms, d_cats, units, nullptr, nullptr, d_tab, ctx->stats,
                                 ctx->status, L, s));
         }
+        if (slot >= 0) CK(cudaEventRecord(ctx->ev[2 * slot + 1], s));
         ctx->last_launches = n_terms;
+        ctx->last_kernels += n_terms;
     }
-    if (ctx->timing) {
-        CK(cudaEventRecord(ctx->t1, s));
-        ctx->last_timed = true;
-    } else {
-        CK(cudaEventRecord(ctx->t1, s));
-    }
+    if (slot >= 0) ctx->n_timed++;
     CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ctx->done, s));
     return TPCF_OK;
 }
 

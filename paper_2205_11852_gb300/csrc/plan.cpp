@@ -140,7 +140,7 @@ bool exact_threshold(double e, double L, int bits, unsigned long long &T)
     return T < (1ull << 63);
 }
 
-int build_plan(const tpcf_binning &b, int subdiv, Plan &pl, std::string &err)
+int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, Plan &pl, std::string &err)
 {
     CountParams &p = pl.prm;
     std::memset(&p, 0, sizeof(p));
@@ -166,6 +166,9 @@ int build_plan(const tpcf_binning &b, int subdiv, Plan &pl, std::string &err)
     // mesh
     int n_c = (int)std::floor(subdiv * L / s_max);
     n_c = std::max(1, std::min(n_c, MAX_NC));
+    // never more cells than the caller's cap (few points, or many catalogues)
+    while (n_c > 1 && (unsigned long long)n_c * n_c * n_c > max_cells) n_c--;
+    if (b.geometry == TPCF_PERIODIC) n_c = std::max(n_c, std::min(3, (int)std::floor(L / s_max)));
     const unsigned long long full = 1ull << p.bits;
     int K = 0;
     unsigned long long Wmin = 0, Wmax = 0;

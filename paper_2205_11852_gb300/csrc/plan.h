@@ -20,6 +20,7 @@ struct Plan {
 };
 
 bool exact_threshold(double e, double L, int bits, unsigned long long &T);
-int build_plan(const tpcf_binning &b, int subdiv, Plan &pl, std::string &err);
+// max_cells caps the mesh (n_c^3); cells never shrink below s_max / subdiv.
+int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, Plan &pl, std::string &err);
 
 }  // namespace tpcf
