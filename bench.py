@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "tf32x3", "bf16x3"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--count-only", action="store_true",
+                   help="one warm-up and one batched tpcf_count of the workload, then exit (profiler captures)")
     return p.parse_args()
 
 
@@ -146,8 +148,8 @@ def oracle_sample_rate(n_d, target_s, seed_mock=0):
     """Time the oracle's brute-force counts on a row sample of one mid mock.
 
     The five terms of one mock cost 3.5 N_d^2 pair tests (DD and RR_i: N_d^2/2
-    each, DR_i: N_d^2 each).  A sample of k a-rows against all b-points costs
-    k N_d tests per term; the rate in mocks/s is the sampled fraction of the
+    each, DR_i: N_d^2 each).  A sample of k a-rows against all b-points runs
+    k N_d tests per term; the rate in mocks/s is the executed fraction of the
     mock's pair tests divided by the time taken.
     """
     import oracle
@@ -161,14 +163,14 @@ def oracle_sample_rate(n_d, target_s, seed_mock=0):
         t0 = time.perf_counter()
         tests = 0
         a = np.ascontiguousarray(qd[:, :k])
-        oracle.count_pairs(a, qd, ob)      # DD rows (each row against all: twice the auto work)
-        tests += k * n_d / 2
+        oracle.count_pairs(a, qd, ob)      # DD rows against all points
+        tests += k * n_d
         for r in qr:
             oracle.count_pairs(a, r, ob)   # DR_i rows
             tests += k * n_d
             ar = np.ascontiguousarray(r[:, :k])
-            oracle.count_pairs(ar, r, ob)  # RR_i rows
-            tests += k * n_d / 2
+            oracle.count_pairs(ar, r, ob)  # RR_i rows against all points
+            tests += k * n_d
         return time.perf_counter() - t0, tests
 
     k = max(16, n_d // 2000)
@@ -272,6 +274,16 @@ def main():
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize()
+
+    if args.count_only:
+        for _ in range(2):
+            ctx.tpcf_count(mocks, b, mode=tp.TPCF_BATCHED, out=outc)
+        ctx.tpcf_sync()
+        info = ctx.tpcf_last_count_info()
+        print(json.dumps({"count_only": True, "mocks": n_mock, "n_candidates": info["n_candidates"],
+                          "n_binned": info["n_binned"], "n_exact": info["n_exact"]}))
+        ctx.close()
+        return
 
     # correctness of the timed configuration: batched == per-launch on 2 mocks
     chk_b = ctx.tpcf_count(mocks[:2], b, mode=tp.TPCF_BATCHED)
