@@ -480,12 +480,13 @@ int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_bin
         units_bound += n / UNIT_CHUNK + std::min<unsigned long long>(n, prm.n_cells) + 1;
     }
 
-    void *w_uq, *w_keys, *w_us, *w_pf, *w_cc, *w_cs, *w_tmp, *w_uc, *w_ust, *w_units, *w_small, *w_claim;
+    void *w_uq, *w_keys, *w_us, *w_pf, *w_pcx, *w_cc, *w_cs, *w_tmp, *w_uc, *w_ust, *w_units, *w_small, *w_claim;
     const size_t tmp_n = std::max(scan_tmp_elems(ncc), scan_tmp_elems(ntc));
     if ((rc = ensure(ctx, "uq", 3 * NT * 4, &w_uq))) return rc;
     if ((rc = ensure(ctx, "keys", NT * 4, &w_keys))) return rc;
     if ((rc = ensure(ctx, "us", 3 * NT * 4, &w_us))) return rc;
     if ((rc = ensure(ctx, "pf", NT * 16, &w_pf))) return rc;
+    if ((rc = ensure(ctx, "pcx", NT * 2, &w_pcx))) return rc;
     if ((rc = ensure(ctx, "cellcount", ncc * 4, &w_cc))) return rc;
     if ((rc = ensure(ctx, "cellstart", ncc * 4, &w_cs))) return rc;
     if ((rc = ensure(ctx, "scantmp", tmp_n * 4, &w_tmp))) return rc;
@@ -541,7 +542,7 @@ int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_bin
     const Cat *d_cats = (const Cat *)((char *)w_small + o_cats);
     const Term *d_terms = (const Term *)((char *)w_small + o_terms);
     const uint32_t *d_orig = (const uint32_t *)((char *)w_small + o_orig);
-    const uint16_t *d_tab = (const uint16_t *)((char *)w_small + o_tab);
+    const int16_t *d_tab = (const int16_t *)((char *)w_small + o_tab);
 
     uint32_t *uq = (uint32_t *)w_uq, *keys = (uint32_t *)w_keys, *us = (uint32_t *)w_us;
     float4 *pf = (float4 *)w_pf;
@@ -555,16 +556,18 @@ int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_bin
                             cc, ctx->status, s));
     CK(launch_scan_u32(cc, cs, ncc, tmp, tmp_n, s));
     CK(cudaMemsetAsync(cc, 0, ncc * 4, s));
-    CK(launch_scatter(d_cats, n_cat, max_n, prm, uq, keys, cs, cc, d_orig, (uint32_t)NT, us, pf, s));
+    CK(launch_scatter(d_cats, n_cat, max_n, prm, uq, keys, cs, cc, d_orig, (uint32_t)NT, us, pf, (uint16_t *)w_pcx,
+                      s));
 
     Mesh mesh;
     mesh.pf = pf;
+    mesh.pcx = (const uint16_t *)w_pcx;
     mesh.us = us;
     mesh.n_total = (uint32_t)NT;
     mesh.cellstart = cs;
     mesh.orig = d_orig;
 
-    const int warps = 4;
+    const int warps = 8;
     const int smem = paircount_smem_bytes(prm, warps);
     CK(paircount_set_attrs(prm, smem));
     CK(cudaMemsetAsync(ctx->stats, 0, 4 * sizeof(unsigned long long), s));

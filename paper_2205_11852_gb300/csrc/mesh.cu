@@ -94,7 +94,7 @@ __global__ void scatter_kernel(const Cat *__restrict__ cats, int n_cat, int n_c,
                                const uint32_t *__restrict__ uq, const uint32_t *__restrict__ keys,
                                const uint32_t *__restrict__ cellstart, uint32_t *__restrict__ cursor,
                                const uint32_t *__restrict__ orig, uint32_t n_total,
-                               uint32_t *__restrict__ us, float4 *__restrict__ pf)
+                               uint32_t *__restrict__ us, float4 *__restrict__ pf, uint16_t *__restrict__ pcx)
 {
     for (int c = blockIdx.y; c < n_cat; c += gridDim.y) {
     const Cat cat = cats[c];
@@ -109,8 +109,10 @@ __global__ void scatter_kernel(const Cat *__restrict__ cats, int n_cat, int n_c,
         const uint32_t cx = cell_of(ux, n_c, bits), cy = cell_of(uy, n_c, bits),
                        cz = cell_of(uz, n_c, bits);
         // offsets from the cell's integer lower corner are below one cell width
-        pf[pos] = make_float4((float)(ux - orig[cx]), (float)(uy - orig[cy]), (float)(uz - orig[cz]),
-                              __int_as_float((int)cx));
+        const float fx = (float)(ux - orig[cx]), fy = (float)(uy - orig[cy]), fz = (float)(uz - orig[cz]);
+        const float nh = -0.5f * __fmaf_rn(fz, fz, __fmaf_rn(fy, fy, __fmul_rn(fx, fx)));
+        pf[pos] = make_float4(fx, fy, fz, nh);
+        pcx[pos] = (uint16_t)cx;
     }
     }
 }
@@ -269,12 +271,12 @@ cudaError_t launch_quantize_keys(const Cat *cats, int n_cat, uint32_t max_n, con
 cudaError_t launch_scatter(const Cat *cats, int n_cat, uint32_t max_n, const CountParams &p,
                            const uint32_t *uq, const uint32_t *keys, const uint32_t *cellstart,
                            uint32_t *cursor, const uint32_t *orig, uint32_t n_total, uint32_t *us,
-                           float4 *pf, cudaStream_t s)
+                           float4 *pf, uint16_t *pcx, cudaStream_t s)
 {
     if (n_cat == 0 || max_n == 0) return cudaSuccess;
     dim3 grid(grid_for(max_n, 256, 4096), std::min(n_cat, 65535));
     scatter_kernel<<<grid, 256, 0, s>>>(cats, n_cat, p.n_c, p.bits, uq, keys, cellstart, cursor, orig, n_total, us,
-                                        pf);
+                                        pf, pcx);
     return cudaGetLastError();
 }
 

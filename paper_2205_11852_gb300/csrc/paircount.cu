@@ -1,61 +1,79 @@
 // Binned pair counting on the chaining mesh (Sect. 2.1: DD, DR_i, RR_i
 // counts; Sect. 4.3: bins in separation s and in mu).
 //
-// Work decomposition.  A unit is a chunk of the sorted points of one mesh
-// cell A of catalogue a, to be paired with every point of catalogue b in the
-// neighbourhood of A.  A warp owns a unit.  The neighbourhood is walked as
-// rows of cells (dz, dy) whose x-runs are contiguous in the cell-sorted
-// point order; each run is cut into tiles of 32*P b-points, one P-vector per
-// lane, shifted into A's frame once per tile.  The a-points are then
-// broadcast to the warp one at a time (uniform loads served by L1), so one
-// load feeds 32*P pair tests.
+// Work decomposition.  A unit is a chunk of at most 256 sorted points of one
+// mesh cell A of catalogue a, to be paired with every point of catalogue b in
+// the neighbourhood of A.  A thread block owns a unit: the a-chunk and the
+// histogram live in shared memory, and the warps share the b side.  The
+// neighbourhood is walked as rows of cells (dz, dy) whose x-runs are
+// contiguous in the cell-sorted point order; every run is cut into tiles of
+// 32*P b-points, and the tiles are dealt to the warps.  A warp loads its tile
+// once, one P-vector per lane, shifted into A's frame, then streams the
+// a-chunk past it by broadcast shared-memory loads.
 //
-// Per pair: FP32 d^2 from cell-relative coordinates and a compare with the
-// top edge.  Pairs that may be in range are appended to a lane-private queue
-// in shared memory; the queue is binned in bulk so that the binning code
-// runs with every lane busy.  Binning looks up the s bin from the bit
-// pattern of d^2 (each table slot spans at most one bin edge) and the mu bin
-// from n_mu |mu| = n_mu |dx| / sqrt(d^2).  A pair whose d^2 or mu lies within
-// the rigorous FP32 error band of a bin edge is rebinned exactly from the
-// integer grid coordinates (64-bit squared distances, 128-bit mu test), so
-// every count equals the integer definition bit for bit.
-//
-// Histograms are privatised per warp in shared memory (int32) and added to
-// the caller's int64 histogram when the warp finishes a unit.
+// Per pair, a dot-product form of the range test,
+//     a.b' - |a|^2/2  >=  (|b'|^2 - H)/2 - margin,
+// costs three FMAs and one compare (|a|^2/2 is stored with the point,
+// (|b'|^2 - H)/2 is per lane), with a margin that makes it a superset of the
+// direct FP32 test d2 < H.  A passing pair appends a 16-bit entry (a index,
+// b slot) to a lane-private queue in shared memory, branch-free.  Queues are
+// binned in bulk: the direct FP32 d2 and dx are recomputed, the s bin comes
+// from a table indexed by the bit pattern of d2 (one compare against the
+// band of the next edge), the mu bin from n_mu |dx| / sqrt(d2).  A pair whose
+// d2 or mu lies within the rigorous FP32 error band of a bin edge is rebinned
+// exactly from the integer grid coordinates (64-bit squared distances,
+// 128-bit mu test), so every count equals the integer definition bit for bit.
 #include "plan.h"
 
 namespace tpcf {
 
 namespace {
 
-constexpr int P = 4;          // b-points per lane
-constexpr int QN = 16;        // queue slots per lane
-constexpr float FAR = 3.0e18f;
+constexpr int P = 4;            // b-points per lane
+constexpr int TILE = 32 * P;    // b-points per warp tile
+constexpr int QN = 48;          // queue slots per lane (16-bit entries)
+constexpr int WARPS = 8;        // warps per block
+constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 
 typedef unsigned __int128 u128;
 typedef __int128 i128;
 
+struct Seg {
+    uint32_t s0, s1;       // b range
+    uint32_t tile0;        // first tile index of this segment
+    float sy, sz;          // row shift into A's frame
+    int self;              // the run is cell A itself in an auto count
+    int pad;
+};
+
 struct Smem {
-    int *hist;                 // [warps][nbin]
-    float4 *queue;             // [warps][QN][32]
-    uint16_t *table;           // [tab_n]
+    float4 *a;                 // [UNIT_CHUNK]
+    int *hist;                 // [nbin]
+    uint16_t *queue;           // [WARPS][QN][32]
+    float4 *bcopy;             // [WARPS][P][32]
+    int16_t *table;            // [tab_n]
+    float2 *lohi;              // [n_s + 2]
     uint32_t *orig;            // [n_c + 1]
-    float *lo, *hi;            // [n_s + 1]
     unsigned long long *T;     // [n_s + 1]
+    Seg *segs;                 // [MAX_SEGS]
+    int *misc;                 // [4]: unit, n_segs, n_tiles
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t smem_layout(const CountParams &p, int warps, size_t *off)
+__host__ __device__ inline size_t smem_layout(const CountParams &p, size_t *off)
 {
     size_t o = 0;
-    off[0] = o; o = align16(o + sizeof(unsigned long long) * (p.n_s + 1));   // T
-    off[1] = o; o = align16(o + sizeof(float4) * (size_t)warps * QN * 32);    // queue
-    off[2] = o; o = align16(o + sizeof(int) * (size_t)warps * p.nbin);       // hist
-    off[3] = o; o = align16(o + sizeof(float) * (p.n_s + 1));                // lo
-    off[4] = o; o = align16(o + sizeof(float) * (p.n_s + 1));                // hi
-    off[5] = o; o = align16(o + sizeof(uint32_t) * (p.n_c + 1));             // orig
-    off[6] = o; o = align16(o + sizeof(uint16_t) * p.tab_n);                 // table
+    off[0] = o; o = align16(o + sizeof(unsigned long long) * (p.n_s + 1));  // T
+    off[1] = o; o = align16(o + sizeof(float4) * UNIT_CHUNK);              // a chunk
+    off[2] = o; o = align16(o + sizeof(float4) * WARPS * P * 32);           // b copies
+    off[3] = o; o = align16(o + sizeof(uint16_t) * WARPS * QN * 32);        // queues
+    off[4] = o; o = align16(o + sizeof(int) * p.nbin);                      // histogram
+    off[5] = o; o = align16(o + sizeof(float2) * (p.n_s + 2));              // edge bands
+    off[6] = o; o = align16(o + sizeof(uint32_t) * (p.n_c + 1));            // cell corners
+    off[7] = o; o = align16(o + sizeof(int16_t) * p.tab_n);                 // s table
+    off[8] = o; o = align16(o + sizeof(Seg) * MAX_SEGS);                    // segments
+    off[9] = o; o = align16(o + sizeof(int) * 4);
     return o;
 }
 
@@ -112,292 +130,322 @@ __device__ __noinline__ int exact_bin(const CountParams &prm, const unsigned lon
 }
 
 template <bool MU, bool MID>
-struct Warp {
+struct Ctx {
     const CountParams &prm;
     const Smem &sm;
     const Mesh &m;
-    int *hist;         // this warp's histogram
-    float4 *q;         // this warp's queue
-    int lane;
-    // unit state
-    uint32_t a0, a1;
-    float gx, gy, gz;  // 2 (corner(A) - observer), midpoint line of sight
-    unsigned long long n_cand;
+    int lane, warp;
+    uint16_t *q;               // this warp's queue
+    float4 *bc;                // this warp's b copies
+    uint32_t a0, na;           // current unit's a-chunk
+    float gx, gy, gz;          // 2 (corner(A) - observer), midpoint line of sight
     unsigned n_exact, n_binned;
 
-    __device__ Warp(const CountParams &p, const Smem &s, const Mesh &mm, int w, int l)
-        : prm(p), sm(s), m(mm), lane(l), n_cand(0), n_exact(0), n_binned(0)
+    // bin of a queued pair; -1 unbinned, -2 recheck exactly
+    __device__ __forceinline__ int classify(float d2, float dx, const float4 &a, const float4 &b) const
     {
-        hist = s.hist + (size_t)w * p.nbin;
-        q = s.queue + (size_t)w * QN * 32;
-    }
-
-    // Classify a queued pair; returns the bin, -1 (unbinned) or -2 (recheck exactly).
-    __device__ __forceinline__ int classify(float d2, float dx, uint32_t ia, const float (&bx)[P],
-                                            const float (&by)[P], const float (&bz)[P], int p) const
-    {
-        uint32_t key = __float_as_uint(d2) >> prm.tab_shift;
-        key = max(key, prm.tab_key0) - prm.tab_key0;
-        key = min(key, (uint32_t)(prm.tab_n - 1));
-        const uint16_t c = sm.table[key];
-        int k;
-        bool amb = false;
-        if (c & CODE_EDGE) {
-            const int e = c & 0x7FFF;
-            const float hi = sm.hi[e];
-            k = (d2 >= hi) ? e : e - 1;
-            amb = (d2 >= sm.lo[e]) && (d2 < hi);
-        } else if (c == CODE_AMBIG) {
-            return -2;
-        } else {
-            k = c;   // a bin, or CODE_DISCARD (>= n_s)
-        }
-        if (amb) return -2;
-        if (k < 0 || k >= prm.n_s) return -1;
-        if (!MU) return k;
+        const uint32_t key = min((__float_as_uint(__fadd_rn(d2, prm.tab_bias)) >> prm.tab_shift) - prm.tab_key0,
+                                 (uint32_t)(prm.tab_n - 1));
+        int k = sm.table[key];
+        bool amb = (k == CODE_AMBIG);
+        k = amb ? -1 : k;
+        const float2 lh = sm.lohi[k + 1];
+        const bool ge_hi = d2 >= lh.y;
+        amb |= (d2 >= lh.x) && !ge_hi;
+        k += ge_hi ? 1 : 0;
+        if (!MU) return amb ? -2 : ((unsigned)k < (unsigned)prm.n_s ? k : -1);
+        if ((unsigned)k >= (unsigned)prm.n_s && !amb) return -1;
         float t, beta;
         if (!MID) {
-            const float r = rsqrtf(d2);
-            t = fabsf(dx) * r * (float)prm.n_mu;
-            beta = fmaf(prm.mu_c1, r, prm.mu_c2);
+            const float r = rsqrtf(__fmul_rn(d2, prm.inv_nmu2));   // n_mu / sqrt(d2)
+            t = __fmul_rn(fabsf(dx), r);
+            beta = __fmaf_rn(prm.mu_c1, r, prm.mu_c2);
         } else {
-            const float4 a = __ldg(m.pf + ia);
-            float px = 0.f, py = 0.f, pz = 0.f;
-#pragma unroll
-            for (int i = 0; i < P; i++)
-                if (i == p) { px = bx[i]; py = by[i]; pz = bz[i]; }
-            const float ex = a.x - px, ey = a.y - py, ez = a.z - pz;
-            const float lx = gx + a.x + px, ly = gy + a.y + py, lz = gz + a.z + pz;
-            const float dot = fmaf(ez, lz, fmaf(ey, ly, ex * lx));
-            const float l2 = fmaf(lz, lz, fmaf(ly, ly, lx * lx));
+            const float ex = __fsub_rn(a.x, b.x), ey = __fsub_rn(a.y, b.y), ez = __fsub_rn(a.z, b.z);
+            const float lx = __fadd_rn(__fadd_rn(gx, a.x), b.x);
+            const float ly = __fadd_rn(__fadd_rn(gy, a.y), b.y);
+            const float lz = __fadd_rn(__fadd_rn(gz, a.z), b.z);
+            const float dot = __fmaf_rn(ez, lz, __fmaf_rn(ey, ly, __fmul_rn(ex, lx)));
+            const float l2 = __fmaf_rn(lz, lz, __fmaf_rn(ly, ly, __fmul_rn(lx, lx)));
             const float rs = rsqrtf(d2), rl = rsqrtf(l2);
-            t = fabsf(dot) * rs * rl * (float)prm.n_mu;
-            beta = fmaf(prm.mu_c1, rs, fmaf(prm.mu_c3, rl, prm.mu_c2));
+            t = __fmul_rn(__fmul_rn(__fmul_rn(fabsf(dot), rs), rl), (float)prm.n_mu);
+            beta = __fmaf_rn(prm.mu_c1, rs, __fmaf_rn(prm.mu_c3, rl, prm.mu_c2));
         }
-        if (!(beta < 0.05f)) return -2;
-        const float fl = floorf(t);
-        const float f = t - fl;
-        int j = (int)fl;
-        const bool near_lo = !(f >= beta);
-        const bool near_hi = !(f <= 1.0f - beta);
-        if ((near_lo && j >= 1 && j <= prm.n_mu - 1) || (near_hi && j + 1 >= 1 && j + 1 <= prm.n_mu - 1))
-            return -2;
+        // round t to the nearest integer m with the 1.5 * 2^23 trick; the pair
+        // is ambiguous when t is within beta of an interior mu edge 1..n_mu-1
+        const float big = 12582912.0f;
+        const float mf = __fadd_rn(t, big);
+        const int mi = __float_as_int(mf) - 0x4B400000;
+        const float d = __fsub_rn(t, __fsub_rn(mf, big));
+        amb |= !(beta < 0.05f);
+        amb |= (fabsf(d) < beta) && (mi >= 1) && (mi <= prm.n_mu - 1);
+        if (amb) return -2;
+        int j = mi - (d < 0.0f ? 1 : 0);
         j = min(max(j, 0), prm.n_mu - 1);
         return k * prm.n_mu + j;
     }
 
-    __device__ __forceinline__ void flush(int &qn, uint32_t base, const float (&bx)[P], const float (&by)[P],
-                                          const float (&bz)[P])
+    __device__ __forceinline__ void flush(uint32_t &qoff, uint32_t base)
     {
-        const int qmax = __reduce_max_sync(0xffffffffu, (unsigned)qn);
-        for (int k = 0; k < qmax; k++) {
-            if (k < qn) {
-                const float4 e = q[k * 32 + lane];
-                const uint32_t ia = __float_as_uint(e.z);
-                const int p = __float_as_int(e.w);
-                int bin = classify(e.x, e.y, ia, bx, by, bz, p);
+        const uint32_t n = qoff >> 5;
+        const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
+        for (uint32_t k = 0; k < nmax; k++) {
+            if (k < n) {
+                const uint32_t e = q[k * 32 + lane];
+                const uint32_t ai = e & 255u, p = e >> 8;
+                const float4 a = sm.a[ai];
+                const float4 b = bc[p * 32 + lane];
+                const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
+                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                int bin = classify(d2, dx, a, b);
                 if (bin == -2) {
-                    bin = exact_bin(prm, sm.T, m.us, m.n_total, ia, base + lane + 32u * p);
+                    bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + ai, base + lane + 32u * p);
                     n_exact++;
                 }
                 if (bin >= 0) {
-                    atomicAdd(&hist[bin], 1);
+                    atomicAdd(&sm.hist[bin], 1);
                     n_binned++;
                 }
             }
         }
-        qn = 0;
+        qoff = 0;
         __syncwarp();
     }
 
-    // All pairs (a in [a0, a1), b in [s0, s1)); b shifted into A's frame.
-    // self: the b run is cell A itself in an auto count, keep ia < ib only.
-    __device__ void run(uint32_t s0, uint32_t s1, uint32_t orig_ax, float sy, float sz, bool self)
+    // all pairs of the a-chunk with one tile of b-points starting at `base`
+    template <bool SELF>
+    __device__ __forceinline__ void tile(uint32_t base, uint32_t s1, uint32_t orig_ax, float sy, float sz)
     {
-        for (uint32_t base = s0; base < s1; base += 32u * P) {
-            float bx[P], by[P], bz[P];
+        float bx[P], by[P], bz[P], hb[P];
+        const float H = prm.hit_max, mg = prm.dot_margin;
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            const uint32_t i = base + lane + 32u * p;
+            if (i < s1) {
+                const float4 v = __ldg(m.pf + i);
+                const int cx = m.pcx[i];
+                const float sx = (float)(int)(sm.orig[cx] - orig_ax);
+                bx[p] = __fadd_rn(v.x, sx);
+                by[p] = __fadd_rn(v.y, sy);
+                bz[p] = __fadd_rn(v.z, sz);
+                const float b2 = __fmaf_rn(bz[p], bz[p], __fmaf_rn(by[p], by[p], __fmul_rn(bx[p], bx[p])));
+                hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, H)), mg);
+            } else {
+                bx[p] = by[p] = bz[p] = 0.0f;
+                hb[p] = __int_as_float(0x7f800000);   // +inf: never passes
+            }
+            bc[p * 32 + lane] = make_float4(bx[p], by[p], bz[p], 0.0f);
+        }
+        __syncwarp();
+        uint32_t qoff = 0;   // queue write position in slots * 32
+        const uint32_t lim = (uint32_t)(QN - 2 * P) << 5;
+        const uint32_t ib0 = base + lane;
+        uint32_t ai = 0;
+        for (; ai + 1 < na; ai += 2) {
+            const float4 a = sm.a[ai], c = sm.a[ai + 1];
 #pragma unroll
             for (int p = 0; p < P; p++) {
-                const uint32_t i = base + lane + 32u * p;
-                if (i < s1) {
-                    const float4 v = __ldg(m.pf + i);
-                    const int cx = __float_as_int(v.w);
-                    const float sx = (float)(int)(sm.orig[cx] - orig_ax);
-                    bx[p] = __fadd_rn(v.x, sx);
-                    by[p] = __fadd_rn(v.y, sy);
-                    bz[p] = __fadd_rn(v.z, sz);
-                } else {
-                    bx[p] = by[p] = bz[p] = FAR;
-                }
+                const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
+                bool hit = t >= hb[p];
+                if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
+                if (hit) q[qoff + lane] = (uint16_t)(ai | (p << 8));
+                qoff += hit ? 32u : 0u;
             }
-            const uint32_t nb = min(s1 - base, 32u * P);
-            n_cand += (unsigned long long)nb * (a1 - a0);
-            int qn = 0;
-            const float hit_max = prm.hit_max;
-            for (uint32_t ia = a0; ia < a1; ia++) {
-                const float4 a = __ldg(m.pf + ia);
 #pragma unroll
-                for (int p = 0; p < P; p++) {
-                    const float dx = __fsub_rn(a.x, bx[p]);
-                    const float dy = __fsub_rn(a.y, by[p]);
-                    const float dz = __fsub_rn(a.z, bz[p]);
-                    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                    bool hit = d2 < hit_max;
-                    if (self) hit = hit && (ia < base + lane + 32u * p);
-                    if (hit) {
-                        q[qn * 32 + lane] = make_float4(d2, dx, __uint_as_float(ia), __int_as_float(p));
-                        qn++;
-                    }
-                }
-                if (__any_sync(0xffffffffu, qn > QN - P)) flush(qn, base, bx, by, bz);
+            for (int p = 0; p < P; p++) {
+                const float t = __fmaf_rn(c.x, bx[p], __fmaf_rn(c.y, by[p], __fmaf_rn(c.z, bz[p], c.w)));
+                bool hit = t >= hb[p];
+                if (SELF) hit = hit && (a0 + ai + 1 < ib0 + 32u * p);
+                if (hit) q[qoff + lane] = (uint16_t)((ai + 1) | (p << 8));
+                qoff += hit ? 32u : 0u;
             }
-            if (__any_sync(0xffffffffu, qn > 0)) flush(qn, base, bx, by, bz);
+            if (__any_sync(0xffffffffu, qoff > lim)) flush(qoff, base);
         }
-    }
-
-    __device__ void flush_hist(long long *out)
-    {
-        __syncwarp();
-        for (int b = lane; b < prm.nbin; b += 32) {
-            const int v = hist[b];
-            if (v) {
-                atomicAdd((unsigned long long *)&out[b], (unsigned long long)(long long)v);
-                hist[b] = 0;
+        if (ai < na) {
+            const float4 a = sm.a[ai];
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
+                bool hit = t >= hb[p];
+                if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
+                if (hit) q[qoff + lane] = (uint16_t)(ai | (p << 8));
+                qoff += hit ? 32u : 0u;
             }
         }
-        __syncwarp();
-    }
-
-    __device__ void unit(const Unit &un, const Term &tm)
-    {
-        const int n_c = prm.n_c;
-        const int ax = un.cell % n_c, ay = (un.cell / n_c) % n_c, az = un.cell / (n_c * n_c);
-        const bool periodic = prm.geometry == TPCF_PERIODIC;
-        const uint32_t *cs = m.cellstart + (size_t)tm.cat_b * prm.n_cells;
-        a0 = un.a0;
-        a1 = un.a1;
-        const uint32_t oax = sm.orig[ax], oay = sm.orig[ay], oaz = sm.orig[az];
-        if (MID) {
-            gx = 2.0f * (float)((long long)oax - prm.obs[0]);
-            gy = 2.0f * (float)((long long)oay - prm.obs[1]);
-            gz = 2.0f * (float)((long long)oaz - prm.obs[2]);
-        }
-        unsigned long long since_flush = 0;
-        for (int r = 0; r < prm.n_rows; r++) {
-            const int dz = prm.row_dz[r], dy = prm.row_dy[r], kx = prm.row_kx[r];
-            if (tm.auto_pairs && (dz < 0 || (dz == 0 && dy < 0))) continue;
-            int z = az + dz, y = ay + dy;
-            if (periodic) {
-                z = z < 0 ? z + n_c : (z >= n_c ? z - n_c : z);
-                y = y < 0 ? y + n_c : (y >= n_c ? y - n_c : y);
-            } else if (z < 0 || z >= n_c || y < 0 || y >= n_c) {
-                continue;
-            }
-            const float sy = (float)(int)(sm.orig[y] - oay);
-            const float sz = (float)(int)(sm.orig[z] - oaz);
-            const uint32_t rowkey = ((uint32_t)z * n_c + (uint32_t)y) * n_c;
-            int xlo = ax - kx, xhi = ax + kx;
-            const unsigned long long before = n_cand;
-            if (tm.auto_pairs && dz == 0 && dy == 0) {
-                run(cs[rowkey + ax], cs[rowkey + ax + 1], oax, sy, sz, true);
-                xlo = ax + 1;
-            }
-            if (xlo <= xhi) {
-                if (periodic) {
-                    if (xlo < 0) {
-                        run(cs[rowkey + xlo + n_c], cs[rowkey + n_c], oax, sy, sz, false);
-                        run(cs[rowkey], cs[rowkey + xhi + 1], oax, sy, sz, false);
-                    } else if (xhi >= n_c) {
-                        run(cs[rowkey + xlo], cs[rowkey + n_c], oax, sy, sz, false);
-                        run(cs[rowkey], cs[rowkey + xhi - n_c + 1], oax, sy, sz, false);
-                    } else {
-                        run(cs[rowkey + xlo], cs[rowkey + xhi + 1], oax, sy, sz, false);
-                    }
-                } else {
-                    xlo = max(xlo, 0);
-                    xhi = min(xhi, n_c - 1);
-                    if (xlo <= xhi) run(cs[rowkey + xlo], cs[rowkey + xhi + 1], oax, sy, sz, false);
-                }
-            }
-            // int32 per-warp bins: drain well before 2^31 pairs can accumulate
-            since_flush += n_cand - before;
-            if (since_flush > (1ull << 30)) {
-                flush_hist(tm.hist);
-                since_flush = 0;
-            }
-        }
-        flush_hist(tm.hist);
+        if (__any_sync(0xffffffffu, qoff > 0)) flush(qoff, base);
     }
 };
 
+// Build the unit's b segments (thread 0); returns nothing, fills smem.
+__device__ void build_segments(const CountParams &prm, const Smem &sm, const Mesh &m, const Term &tm, int cell)
+{
+    const int n_c = prm.n_c;
+    const int ax = cell % n_c, ay = (cell / n_c) % n_c, az = cell / (n_c * n_c);
+    const bool periodic = prm.geometry == TPCF_PERIODIC;
+    const uint32_t *cs = m.cellstart + (size_t)tm.cat_b * prm.n_cells;
+    const uint32_t oay = sm.orig[ay], oaz = sm.orig[az];
+    int ns = 0;
+    uint32_t tiles = 0;
+    auto add = [&](uint32_t s0, uint32_t s1, float sy, float sz, int self) {
+        if (s1 <= s0) return;
+        Seg g;
+        g.s0 = s0;
+        g.s1 = s1;
+        g.tile0 = tiles;
+        g.sy = sy;
+        g.sz = sz;
+        g.self = self;
+        g.pad = 0;
+        sm.segs[ns++] = g;
+        tiles += (s1 - s0 + TILE - 1) / TILE;
+    };
+    for (int r = 0; r < prm.n_rows; r++) {
+        const int dz = prm.row_dz[r], dy = prm.row_dy[r], kx = prm.row_kx[r];
+        if (tm.auto_pairs && (dz < 0 || (dz == 0 && dy < 0))) continue;
+        int z = az + dz, y = ay + dy;
+        if (periodic) {
+            z = z < 0 ? z + n_c : (z >= n_c ? z - n_c : z);
+            y = y < 0 ? y + n_c : (y >= n_c ? y - n_c : y);
+        } else if (z < 0 || z >= n_c || y < 0 || y >= n_c) {
+            continue;
+        }
+        const float sy = (float)(int)(sm.orig[y] - oay);
+        const float sz = (float)(int)(sm.orig[z] - oaz);
+        const uint32_t rowkey = ((uint32_t)z * n_c + (uint32_t)y) * n_c;
+        int xlo = ax - kx, xhi = ax + kx;
+        if (tm.auto_pairs && dz == 0 && dy == 0) {
+            add(cs[rowkey + ax], cs[rowkey + ax + 1], sy, sz, 1);
+            xlo = ax + 1;
+        }
+        if (xlo > xhi) continue;
+        if (periodic) {
+            if (xlo < 0) {
+                add(cs[rowkey + xlo + n_c], cs[rowkey + n_c], sy, sz, 0);
+                add(cs[rowkey], cs[rowkey + xhi + 1], sy, sz, 0);
+            } else if (xhi >= n_c) {
+                add(cs[rowkey + xlo], cs[rowkey + n_c], sy, sz, 0);
+                add(cs[rowkey], cs[rowkey + xhi - n_c + 1], sy, sz, 0);
+            } else {
+                add(cs[rowkey + xlo], cs[rowkey + xhi + 1], sy, sz, 0);
+            }
+        } else {
+            xlo = max(xlo, 0);
+            xhi = min(xhi, n_c - 1);
+            if (xlo <= xhi) add(cs[rowkey + xlo], cs[rowkey + xhi + 1], sy, sz, 0);
+        }
+    }
+    sm.misc[1] = ns;
+    sm.misc[2] = (int)tiles;
+}
+
 template <bool MU, bool MID>
-__global__ void __launch_bounds__(128) paircount_kernel(const __grid_constant__ CountParams prm, const Mesh m,
-                                                        const Term *__restrict__ terms,
-                                                        const Unit *__restrict__ units,
-                                                        const uint32_t *__restrict__ n_units_p,
-                                                        unsigned *__restrict__ claim,
-                                                        const uint16_t *__restrict__ table_g,
-                                                        unsigned long long *__restrict__ stats,
-                                                        int persistent, int term_pl, int chunk)
+__global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_constant__ CountParams prm, const Mesh m,
+                                                                const Term *__restrict__ terms,
+                                                                const Unit *__restrict__ units,
+                                                                const uint32_t *__restrict__ n_units_p,
+                                                                unsigned *__restrict__ claim,
+                                                                const int16_t *__restrict__ table_g,
+                                                                unsigned long long *__restrict__ stats,
+                                                                int persistent, int term_pl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warps = blockDim.x >> 5;
-    size_t off[7];
-    smem_layout(prm, warps, off);
+    size_t off[10];
+    smem_layout(prm, off);
     Smem sm;
     sm.T = (unsigned long long *)(smem_raw + off[0]);
-    sm.queue = (float4 *)(smem_raw + off[1]);
-    sm.hist = (int *)(smem_raw + off[2]);
-    sm.lo = (float *)(smem_raw + off[3]);
-    sm.hi = (float *)(smem_raw + off[4]);
-    sm.orig = (uint32_t *)(smem_raw + off[5]);
-    sm.table = (uint16_t *)(smem_raw + off[6]);
-    for (int i = threadIdx.x; i <= prm.n_s; i += blockDim.x) {
-        sm.T[i] = prm.T[i];
-        sm.lo[i] = prm.lo[i];
-        sm.hi[i] = prm.hi[i];
+    sm.a = (float4 *)(smem_raw + off[1]);
+    sm.bcopy = (float4 *)(smem_raw + off[2]);
+    sm.queue = (uint16_t *)(smem_raw + off[3]);
+    sm.hist = (int *)(smem_raw + off[4]);
+    sm.lohi = (float2 *)(smem_raw + off[5]);
+    sm.orig = (uint32_t *)(smem_raw + off[6]);
+    sm.table = (int16_t *)(smem_raw + off[7]);
+    sm.segs = (Seg *)(smem_raw + off[8]);
+    sm.misc = (int *)(smem_raw + off[9]);
+    const int tid = threadIdx.x;
+    for (int i = tid; i <= prm.n_s; i += blockDim.x) sm.T[i] = prm.T[i];
+    for (int i = tid; i <= prm.n_s + 1; i += blockDim.x) sm.lohi[i] = make_float2(prm.lo[i], prm.hi[i]);
+    for (int i = tid; i <= prm.n_c; i += blockDim.x) sm.orig[i] = m.orig[i];
+    for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
+    for (int i = tid; i < prm.nbin; i += blockDim.x) sm.hist[i] = 0;
+
+    Ctx<MU, MID> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
+    cx.q = sm.queue + (size_t)cx.warp * QN * 32;
+    cx.bc = sm.bcopy + (size_t)cx.warp * P * 32;
+    unsigned long long n_cand = 0;
+
+    // per-launch mode: this block walks the chunks of one cell of one term
+    const uint32_t n_units = persistent ? *n_units_p : 0u;
+    uint32_t pl_a = 0, pl_end = 0;
+    if (!persistent) {
+        const size_t gk = (size_t)terms[term_pl].cat_a * prm.n_cells + blockIdx.x;
+        pl_a = m.cellstart[gk];
+        pl_end = m.cellstart[gk + 1];
     }
-    for (int i = threadIdx.x; i <= prm.n_c; i += blockDim.x) sm.orig[i] = m.orig[i];
-    for (int i = threadIdx.x; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
-    for (int i = threadIdx.x; i < warps * prm.nbin; i += blockDim.x) sm.hist[i] = 0;
     __syncthreads();
 
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Warp<MU, MID> wp(prm, sm, m, w, lane);
-    if (persistent) {
-        const uint32_t n_units = *n_units_p;
-        for (;;) {
-            uint32_t u = 0;
-            if (lane == 0) u = atomicAdd(claim, 1u);
-            u = __shfl_sync(0xffffffffu, u, 0);
+    for (;;) {
+        Unit un;
+        if (persistent) {
+            if (tid == 0) sm.misc[0] = (int)atomicAdd(claim, 1u);
+            __syncthreads();
+            const uint32_t u = (uint32_t)sm.misc[0];
             if (u >= n_units) break;
-            const Unit un = units[u];
-            wp.unit(un, terms[un.term]);
-        }
-    } else {
-        // one block per cell of catalogue a of one term; warps split the cell's chunks
-        const Term tm = terms[term_pl];
-        const int cell = blockIdx.x;
-        const size_t gk = (size_t)tm.cat_a * prm.n_cells + cell;
-        const uint32_t s0 = m.cellstart[gk], s1 = m.cellstart[gk + 1];
-        for (uint32_t a = s0 + (uint32_t)w * chunk; a < s1; a += (uint32_t)warps * chunk) {
-            Unit un;
+            un = units[u];
+        } else {
+            if (pl_a >= pl_end) break;
             un.term = term_pl;
-            un.cell = cell;
-            un.a0 = a;
-            un.a1 = min(s1, a + (uint32_t)chunk);
-            wp.unit(un, tm);
+            un.cell = blockIdx.x;
+            un.a0 = pl_a;
+            un.a1 = min(pl_end, pl_a + (uint32_t)UNIT_CHUNK);
+            pl_a = un.a1;
         }
+        const Term tm = terms[un.term];
+        cx.a0 = un.a0;
+        cx.na = un.a1 - un.a0;
+        for (uint32_t i = tid; i < cx.na; i += blockDim.x) sm.a[i] = __ldg(m.pf + un.a0 + i);
+        if (tid == 0) build_segments(prm, sm, m, tm, un.cell);
+        const int n_c = prm.n_c;
+        const int ax = un.cell % n_c, ay = (un.cell / n_c) % n_c, az = un.cell / (n_c * n_c);
+        const uint32_t oax = sm.orig[ax];
+        if (MID) {
+            cx.gx = 2.0f * (float)((long long)oax - prm.obs[0]);
+            cx.gy = 2.0f * (float)((long long)sm.orig[ay] - prm.obs[1]);
+            cx.gz = 2.0f * (float)((long long)sm.orig[az] - prm.obs[2]);
+        }
+        __syncthreads();
+        const int ns = sm.misc[1];
+        const uint32_t nt = (uint32_t)sm.misc[2];
+        int sg = 0;
+        for (uint32_t ti = cx.warp; ti < nt; ti += WARPS) {
+            while (sg + 1 < ns && sm.segs[sg + 1].tile0 <= ti) sg++;
+            const Seg g = sm.segs[sg];
+            const uint32_t base = g.s0 + (ti - g.tile0) * TILE;
+            n_cand += (unsigned long long)min(g.s1 - base, (uint32_t)TILE) * cx.na;
+            if (g.self) cx.template tile<true>(base, g.s1, oax, g.sy, g.sz);
+            else cx.template tile<false>(base, g.s1, oax, g.sy, g.sz);
+        }
+        __syncthreads();
+        // drain the block histogram into the term's int64 histogram
+        for (int b = tid; b < prm.nbin; b += blockDim.x) {
+            const int v = sm.hist[b];
+            if (v) {
+                atomicAdd((unsigned long long *)&tm.hist[b], (unsigned long long)(long long)v);
+                sm.hist[b] = 0;
+            }
+        }
+        __syncthreads();
     }
-    // work statistics
-    unsigned long long ex = wp.n_exact, bn = wp.n_binned;
+    // work statistics (per-lane candidate counts are warp-uniform: count lane 0 only)
+    unsigned long long ex = cx.n_exact, bn = cx.n_binned, cd = (cx.lane == 0) ? n_cand : 0ull;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ex += __shfl_down_sync(0xffffffffu, ex, o);
         bn += __shfl_down_sync(0xffffffffu, bn, o);
+        cd += __shfl_down_sync(0xffffffffu, cd, o);
     }
-    if (lane == 0) {
-        atomicAdd(&stats[0], wp.n_cand);
+    if (cx.lane == 0) {
+        atomicAdd(&stats[0], cd);
         atomicAdd(&stats[1], bn);
         atomicAdd(&stats[2], ex);
     }
@@ -422,8 +470,9 @@ void *select_kernel(const CountParams &p)
 
 int paircount_smem_bytes(const CountParams &p, int warps_per_block)
 {
-    size_t off[7];
-    return (int)smem_layout(p, warps_per_block, off);
+    (void)warps_per_block;
+    size_t off[10];
+    return (int)smem_layout(p, off);
 }
 
 cudaError_t paircount_set_attrs(const CountParams &p, int smem_bytes)
@@ -433,26 +482,23 @@ cudaError_t paircount_set_attrs(const CountParams &p, int smem_bytes)
 
 int paircount_max_blocks_per_sm(const CountParams &p, int warps_per_block, int smem_bytes)
 {
+    (void)warps_per_block;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_kernel(p), warps_per_block * 32, smem_bytes) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_kernel(p), WARPS * 32, smem_bytes) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_paircount(const CountParams &p, const Mesh &m, const Term *terms, const Cat *cats,
-                             const Unit *units, const uint32_t *n_units, unsigned *claim,
-                             const uint16_t *table, unsigned long long *stats, int *status,
-                             const PairLaunch &pl, cudaStream_t s)
+                             const Unit *units, const uint32_t *n_units, unsigned *claim, const int16_t *table,
+                             unsigned long long *stats, int *status, const PairLaunch &pl, cudaStream_t s)
 {
     (void)cats;
     (void)status;
-    const int chunk = UNIT_CHUNK;
-    void *args[] = {(void *)&p,      (void *)&m,     (void *)&terms,      (void *)&units,
-                    (void *)&n_units, (void *)&claim, (void *)&table,     (void *)&stats,
-                    (void *)&pl.persistent, (void *)&pl.term, (void *)&chunk};
-    return cudaLaunchKernel(select_kernel(p), dim3(pl.blocks), dim3(pl.warps_per_block * 32), args,
-                            (size_t)pl.smem_bytes, s);
+    void *args[] = {(void *)&p,     (void *)&m,     (void *)&terms,         (void *)&units,   (void *)&n_units,
+                    (void *)&claim, (void *)&table, (void *)&stats,         (void *)&pl.persistent,
+                    (void *)&pl.term};
+    return cudaLaunchKernel(select_kernel(p), dim3(pl.blocks), dim3(WARPS * 32), args, (size_t)pl.smem_bytes, s);
 }
 
 }  // namespace tpcf

@@ -163,36 +163,43 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
     const unsigned long long Tmax = p.T[b.n_s];
     if (Tmax == 0) { err = "s_max must be positive"; return TPCF_ERR_ARG; }
 
-    // mesh
+    // mesh: the largest n_c (cells per axis) whose cells still reach no
+    // further than `subdiv` neighbours, capped by max_cells
+    const unsigned long long full = 1ull << p.bits;
+    const double Tn = (double)Tmax * (1.0 + 1e-12) + 1.0;
+    // reach: largest offset o whose cells can hold a pair closer than s_max,
+    // i.e. ((o - 1) Wmin + 1)^2 < T_ns
+    auto reach = [&](unsigned long long Wmin) {
+        int K = 0;
+        while (K <= 8) {
+            const double m = (double)K * (double)Wmin + 1.0;
+            if (m * m >= Tn) break;
+            K++;
+        }
+        return K;
+    };
     int n_c = (int)std::floor(subdiv * L / s_max);
     n_c = std::max(1, std::min(n_c, MAX_NC));
-    // never more cells than the caller's cap (few points, or many catalogues)
     while (n_c > 1 && (unsigned long long)n_c * n_c * n_c > max_cells) n_c--;
-    if (b.geometry == TPCF_PERIODIC) n_c = std::max(n_c, std::min(3, (int)std::floor(L / s_max)));
-    const unsigned long long full = 1ull << p.bits;
-    int K = 0;
-    unsigned long long Wmin = 0, Wmax = 0;
-    for (;;) {
-        Wmin = full / (unsigned long long)n_c;
-        Wmax = (full + n_c - 1) / (unsigned long long)n_c;
-        // largest offset o whose cells can hold points closer than s_max:
-        // ((o - 1) Wmin + 1)^2 < Tmax
-        K = 0;
-        while (true) {
-            const double m = (double)K * (double)Wmin + 1.0;  // bound for offset K+1
-            if (m * m >= (double)Tmax * (1.0 + 1e-12) + 1.0) break;
-            K++;
-            if (K > 4) break;
+    while (n_c > 1 && reach(full / (unsigned long long)n_c) > subdiv) n_c--;
+    int K = reach(full / (unsigned long long)n_c);
+    if (b.geometry == TPCF_PERIODIC) {
+        // distinct offsets in [-K, K] must map to distinct cells
+        while (n_c < 2 * K + 1 && n_c < MAX_NC) {
+            n_c++;
+            K = reach(full / (unsigned long long)n_c);
         }
-        const bool ok_k = K <= 4;
-        const bool ok_wrap = (b.geometry != TPCF_PERIODIC) || (n_c >= 2 * K + 1);
-        if (ok_k && ok_wrap) break;
-        if (n_c <= 1 || (b.geometry == TPCF_PERIODIC && n_c <= 3)) {
+        if (n_c < 2 * K + 1) {
             err = "periodic box too small for the separation range (need s_max <= L/3)";
             return TPCF_ERR_RANGE;
         }
-        n_c = std::max(1, n_c - 1);
     }
+    if (K > 4) {
+        err = "mesh reach above 4 cells";
+        return TPCF_ERR_RANGE;
+    }
+    const unsigned long long Wmin = full / (unsigned long long)n_c;
+    const unsigned long long Wmax = (full + n_c - 1) / (unsigned long long)n_c;
     p.n_c = n_c;
     p.n_cells = n_c * n_c * n_c;
     pl.K = K;
@@ -213,9 +220,9 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
     for (int dz = -K; dz <= K; dz++)
         for (int dy = -K; dy <= K; dy++) {
             const double base = m1(dz) + m1(dy);
-            if (base >= (double)Tmax * (1.0 + 1e-12) + 1.0) continue;
+            if (base >= Tn) continue;
             int kx = 0;
-            while (kx + 1 <= K && base + m1(kx + 1) < (double)Tmax * (1.0 + 1e-12) + 1.0) kx++;
+            while (kx + 1 <= K && base + m1(kx + 1) < Tn) kx++;
             p.row_dz[p.n_rows] = (int8_t)dz;
             p.row_dy[p.n_rows] = (int8_t)dy;
             p.row_kx[p.n_rows] = (int8_t)kx;
@@ -245,13 +252,26 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
             p.hi[k] = up_f(T + e);
         }
     }
+    p.lo[b.n_s + 1] = INFINITY;
+    p.hi[b.n_s + 1] = INFINITY;
     p.hit_max = p.hi[b.n_s];
     pl.E_delta = E;
 
-    // mu band (see the kernel): |t - t*| <= n_mu (c1 / sqrt(D2) + c3 / |l| + c2)
+    // Dot-product candidate test  a.b' - |a|^2/2 >= (|b'|^2 - H)/2 - margin:
+    // the margin covers the roundings of both sides (|a| <= sqrt3 W,
+    // |b'| <= sqrt3 (K+1) W) and the 3u relative error of the direct d2.
+    {
+        const double W2 = (double)Wmax * (double)Wmax;
+        const double H = (double)p.hit_max;
+        const double k1 = (double)(K + 1);
+        p.dot_margin = up_f(2.0 * u * ((6.0 + 9.0 * k1 + 12.0 * k1 * k1) * W2 + 2.6 * H));
+    }
+
+    // mu band: |t - t*| <= beta with t = n_mu |mu| computed in FP32
     p.inv_nmu2 = 1.0f / (float)(b.n_mu * b.n_mu);
     if (b.los == TPCF_LOS_X) {
-        p.mu_c1 = (float)(b.n_mu * 1.1 * (1.0 + std::sqrt(3.0)) * E);
+        // beta = mu_c1 * r + mu_c2, r = n_mu / sqrt(d2)
+        p.mu_c1 = (float)(1.1 * (1.0 + std::sqrt(3.0)) * E);
         p.mu_c2 = (float)(b.n_mu * std::ldexp(1.0, -19));
     } else {
         // observer in open grid units; l = u_a + u_b - 2 u_obs
@@ -263,23 +283,28 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
                                                  std::fabs(std::ldexp(1.0, 30) - (double)p.obs[c])));
         const double lmax = gmax + 2.0 * (K + 2) * (double)Wmax;
         const double El = 0.5 * ulp_f32(gmax) + 2.0 * E + 2.0 * ulp_f32(lmax);
+        // beta = mu_c1 / sqrt(d2) + mu_c3 / |l| + mu_c2
         p.mu_c1 = (float)(b.n_mu * 2.2 * std::sqrt(3.0) * E);
         p.mu_c2 = (float)(b.n_mu * std::ldexp(1.0, -18));
         p.mu_c3 = (float)(b.n_mu * 2.2 * std::sqrt(3.0) * El);
     }
 
-    // s-bin table over FP32 bit patterns of d2
+    // s-bin table over FP32 bit patterns of d2 + bias.  The bias (a power of
+    // two well below the first positive edge band) keeps every key at or
+    // above the table's first key.
     double vmin = INFINITY;
     for (int k = 0; k <= b.n_s; k++)
         if (p.T[k] > 0) vmin = std::min(vmin, (double)p.lo[k]);
+    double bias = std::isfinite(vmin) && vmin > 0 ? std::ldexp(1.0, (int)std::floor(std::log2(vmin)) - 2)
+                                                  : 1.0;
+    bias = std::max(bias, std::ldexp(1.0, -100));
+    p.tab_bias = (float)bias;
     int mb = 9;
     for (;; mb--) {
         const int sh = 23 - mb;
-        double x0 = (vmin > 1e-30) ? std::ldexp(1.0, (int)std::floor(std::log2(vmin)) - 1) : std::ldexp(1.0, -126);
-        x0 = std::max(x0, (double)FLT_MIN);
         uint32_t k0, ke;
-        float fx0 = (float)x0, fhm = p.hit_max;
-        std::memcpy(&k0, &fx0, 4);
+        float fb = (float)bias, fhm = up_f((double)p.hit_max + bias);
+        std::memcpy(&k0, &fb, 4);
         std::memcpy(&ke, &fhm, 4);
         k0 >>= sh;
         ke >>= sh;
@@ -298,22 +323,17 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
         float flo, fhi;
         std::memcpy(&flo, &blo, 4);
         std::memcpy(&fhi, &bhi, 4);
-        double vlo = (i == 0) ? 0.0 : (double)flo;
-        double vhi = (i == p.tab_n - 1) ? INFINITY : (double)fhi;
+        // d2 values whose rounded d2 + bias lands in this slot
+        const double slack = ulp_f32((double)fhi);
+        const double vlo = (i == 0) ? -INFINITY : (double)flo - bias - slack;
+        const double vhi = (i == p.tab_n - 1) ? INFINITY : (double)fhi - bias + slack;
         int passed = 0, slot = 0;
         for (int k = 0; k <= b.n_s; k++) {
-            if ((double)p.hi[k] <= vlo) passed++;
+            if (p.T[k] == 0 || (double)p.hi[k] <= vlo) passed++;
             else if ((double)p.lo[k] >= vhi) {}
             else slot++;
         }
-        if (slot == 0) {
-            const int bin = passed - 1;
-            pl.table[i] = (bin < 0 || bin >= b.n_s) ? CODE_DISCARD : (uint16_t)bin;
-        } else if (slot == 1) {
-            pl.table[i] = (uint16_t)(CODE_EDGE | passed);
-        } else {
-            pl.table[i] = CODE_AMBIG;
-        }
+        pl.table[i] = (slot <= 1) ? (int16_t)(passed - 1) : CODE_AMBIG;
     }
     return TPCF_OK;
 }

@@ -13,7 +13,7 @@ constexpr int UNIT_CHUNK = 256;   // a-points per work unit
 struct Plan {
     CountParams prm;
     std::vector<uint32_t> orig;     // [n_c + 1] integer cell corners (mod 2^32)
-    std::vector<uint16_t> table;    // s-bin lookup
+    std::vector<int16_t> table;     // s-bin lookup
     int K = 0;                      // neighbour reach in cells
     int subdiv = 2;                 // cells per s_max (requested)
     double E_delta = 0;             // FP32 coordinate-difference error bound (grid units)

@@ -14,10 +14,11 @@ constexpr int MAX_NC = 1024;         // mesh cells per axis
 constexpr int MAX_ROWS = 81;         // (2K+1)^2 neighbour rows, K <= 4
 constexpr int MAX_TABLE = 16384;     // s-bin lookup slots
 
-// s-bin lookup codes (uint16): a plain bin, an edge-slot marker, or a sentinel
-constexpr uint16_t CODE_EDGE = 0x8000;      // low 15 bits: edge index e; bin e-1 below, e above
-constexpr uint16_t CODE_DISCARD = 0x7FFE;   // slot lies entirely outside [T_0, T_ns)
-constexpr uint16_t CODE_AMBIG = 0x7FFD;     // slot holds several edges: always recheck exactly
+// s-bin lookup: each slot of the table holds k, the bin of the slot's d2
+// values below edge k+1 (-1: below the first edge, n_s: beyond the last),
+// after which d2 is compared with the band of edge k+1 only.  CODE_AMBIG
+// marks a slot that spans several edge bands: always recheck exactly.
+constexpr int16_t CODE_AMBIG = 0x7FFF;
 
 // One pair-count term: histogram of pairs between catalogue A and catalogue B.
 struct Term {
@@ -54,22 +55,26 @@ struct CountParams {
     int bits;              // 32 (periodic) or 30 (open)
     int n_rows;            // neighbour rows (dz, dy) with a non-empty x range
     int8_t row_dz[MAX_ROWS], row_dy[MAX_ROWS], row_kx[MAX_ROWS];
-    // s-bin lookup over float bit patterns of d2
-    int tab_shift;         // key = bits(d2) >> tab_shift
+    // s-bin lookup over float bit patterns of d2 + tab_bias
+    int tab_shift;         // key = bits(d2 + tab_bias) >> tab_shift
     uint32_t tab_key0;     // first key in the table
     int tab_n;             // table slots
+    float tab_bias;
     float hit_max;         // upper band of T_ns: d2 >= hit_max is never binned
-    float mu_c1, mu_c2;    // mu ambiguity band: beta = mu_c1 / sqrt(d2) + mu_c2 (+ mu_c3 / |l| for the midpoint)
+    float dot_margin;      // slack of the dot-product candidate test
+    float mu_c1, mu_c2;    // mu ambiguity band (see the kernel)
     float mu_c3;
     float inv_nmu2;        // 1 / n_mu^2
     long long obs[3];      // observer in grid units (midpoint line of sight)
-    unsigned long long T[MAX_NS + 1];   // exact squared edges in grid units
-    float lo[MAX_NS + 1], hi[MAX_NS + 1];   // float bands: d2 < lo => D2 < T; d2 >= hi => D2 >= T
+    unsigned long long T[MAX_NS + 1];        // exact squared edges in grid units
+    float lo[MAX_NS + 2], hi[MAX_NS + 2];    // float bands: d2 < lo => D2 < T; d2 >= hi => D2 >= T;
+                                             // entry n_s+1 is +inf
 };
 
 // Workspace layout produced by the mesh build and consumed by the counters.
 struct Mesh {
-    const float4 *pf;          // sorted: cell-relative float coords, .w = cell x index (int bits)
+    const float4 *pf;          // sorted: cell-relative float coords, .w = -|f|^2 / 2
+    const uint16_t *pcx;       // sorted: cell x index of each point
     const uint32_t *us;        // sorted exact grid coords [3][n_total]
     uint32_t n_total;
     const uint32_t *cellstart; // [n_cat * n_cells + 1] global sorted start of each (cat, cell)
@@ -91,7 +96,7 @@ size_t scan_tmp_elems(size_t n);
 cudaError_t launch_scatter(const Cat *cats, int n_cat, uint32_t max_n, const CountParams &p,
                            const uint32_t *uq, const uint32_t *keys, const uint32_t *cellstart,
                            uint32_t *cursor, const uint32_t *orig, uint32_t n_total, uint32_t *us,
-                           float4 *pf, cudaStream_t s);
+                           float4 *pf, uint16_t *pcx, cudaStream_t s);
 cudaError_t launch_unit_count(const Term *terms, int n_terms, const Cat *cats, int n_cells,
                               const uint32_t *cellstart, int chunk, uint32_t *ucount, cudaStream_t s);
 cudaError_t launch_unit_fill(const Term *terms, int n_terms, const Cat *cats, int n_cells,
@@ -107,7 +112,7 @@ struct PairLaunch {
 };
 cudaError_t launch_paircount(const CountParams &p, const Mesh &m, const Term *terms, const Cat *cats,
                              const Unit *units, const uint32_t *n_units, unsigned *claim,
-                             const uint16_t *table, unsigned long long *stats, int *status,
+                             const int16_t *table, unsigned long long *stats, int *status,
                              const PairLaunch &pl, cudaStream_t s);
 int paircount_smem_bytes(const CountParams &p, int warps_per_block);
 cudaError_t paircount_set_attrs(const CountParams &p, int smem_bytes);
