@@ -31,7 +31,7 @@ namespace {
 
 constexpr int P = 4;            // b-points per lane
 constexpr int TILE = 32 * P;    // b-points per warp tile
-constexpr int QN = 48;          // queue slots per lane (16-bit entries)
+constexpr int QN = 64;          // queue slots per lane (16-bit entries)
 constexpr int WARPS = 8;        // warps per block
 constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 
@@ -237,7 +237,12 @@ struct Ctx {
             bc[p * 32 + lane] = make_float4(bx[p], by[p], bz[p], 0.0f);
         }
         __syncwarp();
-        uint32_t qoff = 0;   // queue write position in slots * 32
+        // queue write position in slots * 32.  Every candidate writes the head
+        // slot; only a hit advances it, so stores stay branch-free.  The head
+        // stays below QN slots: a flush is forced before 2P more pushes could
+        // overflow.
+        uint32_t qoff = 0;
+        uint16_t *const qh = q + lane;
         const uint32_t lim = (uint32_t)(QN - 2 * P) << 5;
         const uint32_t ib0 = base + lane;
         uint32_t ai = 0;
@@ -248,7 +253,7 @@ struct Ctx {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                if (hit) q[qoff + lane] = (uint16_t)(ai | (p << 8));
+                qh[qoff] = (uint16_t)(ai | (p << 8));   // head slot; kept only on a hit
                 qoff += hit ? 32u : 0u;
             }
 #pragma unroll
@@ -256,7 +261,7 @@ struct Ctx {
                 const float t = __fmaf_rn(c.x, bx[p], __fmaf_rn(c.y, by[p], __fmaf_rn(c.z, bz[p], c.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai + 1 < ib0 + 32u * p);
-                if (hit) q[qoff + lane] = (uint16_t)((ai + 1) | (p << 8));
+                qh[qoff] = (uint16_t)((ai + 1) | (p << 8));
                 qoff += hit ? 32u : 0u;
             }
             if (__any_sync(0xffffffffu, qoff > lim)) flush(qoff, base);
@@ -268,7 +273,7 @@ struct Ctx {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                if (hit) q[qoff + lane] = (uint16_t)(ai | (p << 8));
+                qh[qoff] = (uint16_t)(ai | (p << 8));   // head slot; kept only on a hit
                 qoff += hit ? 32u : 0u;
             }
         }
@@ -276,66 +281,105 @@ struct Ctx {
     }
 };
 
-// Build the unit's b segments (thread 0); returns nothing, fills smem.
-__device__ void build_segments(const CountParams &prm, const Smem &sm, const Mesh &m, const Term &tm, int cell)
+__device__ __forceinline__ uint32_t warp_exclusive_sum(uint32_t v, int lane, uint32_t &total)
+{
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+// The unit's b segments, built by one warp (one lane per neighbour row) and
+// stored in row order with their first tile index.
+__device__ void build_segments(const CountParams &prm, const Smem &sm, const Mesh &m, const Term &tm, int cell,
+                               int lane)
 {
     const int n_c = prm.n_c;
     const int ax = cell % n_c, ay = (cell / n_c) % n_c, az = cell / (n_c * n_c);
     const bool periodic = prm.geometry == TPCF_PERIODIC;
     const uint32_t *cs = m.cellstart + (size_t)tm.cat_b * prm.n_cells;
     const uint32_t oay = sm.orig[ay], oaz = sm.orig[az];
-    int ns = 0;
-    uint32_t tiles = 0;
-    auto add = [&](uint32_t s0, uint32_t s1, float sy, float sz, int self) {
-        if (s1 <= s0) return;
-        Seg g;
-        g.s0 = s0;
-        g.s1 = s1;
-        g.tile0 = tiles;
-        g.sy = sy;
-        g.sz = sz;
-        g.self = self;
-        g.pad = 0;
-        sm.segs[ns++] = g;
-        tiles += (s1 - s0 + TILE - 1) / TILE;
-    };
-    for (int r = 0; r < prm.n_rows; r++) {
-        const int dz = prm.row_dz[r], dy = prm.row_dy[r], kx = prm.row_kx[r];
-        if (tm.auto_pairs && (dz < 0 || (dz == 0 && dy < 0))) continue;
-        int z = az + dz, y = ay + dy;
-        if (periodic) {
-            z = z < 0 ? z + n_c : (z >= n_c ? z - n_c : z);
-            y = y < 0 ? y + n_c : (y >= n_c ? y - n_c : y);
-        } else if (z < 0 || z >= n_c || y < 0 || y >= n_c) {
-            continue;
-        }
-        const float sy = (float)(int)(sm.orig[y] - oay);
-        const float sz = (float)(int)(sm.orig[z] - oaz);
-        const uint32_t rowkey = ((uint32_t)z * n_c + (uint32_t)y) * n_c;
-        int xlo = ax - kx, xhi = ax + kx;
-        if (tm.auto_pairs && dz == 0 && dy == 0) {
-            add(cs[rowkey + ax], cs[rowkey + ax + 1], sy, sz, 1);
-            xlo = ax + 1;
-        }
-        if (xlo > xhi) continue;
-        if (periodic) {
-            if (xlo < 0) {
-                add(cs[rowkey + xlo + n_c], cs[rowkey + n_c], sy, sz, 0);
-                add(cs[rowkey], cs[rowkey + xhi + 1], sy, sz, 0);
-            } else if (xhi >= n_c) {
-                add(cs[rowkey + xlo], cs[rowkey + n_c], sy, sz, 0);
-                add(cs[rowkey], cs[rowkey + xhi - n_c + 1], sy, sz, 0);
-            } else {
-                add(cs[rowkey + xlo], cs[rowkey + xhi + 1], sy, sz, 0);
+    uint32_t ns_total = 0, tiles_total = 0;
+    for (int r0 = 0; r0 < prm.n_rows; r0 += 32) {
+        const int r = r0 + lane;
+        uint32_t s0[3], s1[3];
+        int self[3];
+        int nl = 0;
+        float sy = 0.f, sz = 0.f;
+        if (r < prm.n_rows) {
+            const int dz = prm.row_dz[r], dy = prm.row_dy[r], kx = prm.row_kx[r];
+            bool use = !(tm.auto_pairs && (dz < 0 || (dz == 0 && dy < 0)));
+            int z = az + dz, y = ay + dy;
+            if (periodic) {
+                z = z < 0 ? z + n_c : (z >= n_c ? z - n_c : z);
+                y = y < 0 ? y + n_c : (y >= n_c ? y - n_c : y);
+            } else if (z < 0 || z >= n_c || y < 0 || y >= n_c) {
+                use = false;
             }
-        } else {
-            xlo = max(xlo, 0);
-            xhi = min(xhi, n_c - 1);
-            if (xlo <= xhi) add(cs[rowkey + xlo], cs[rowkey + xhi + 1], sy, sz, 0);
+            if (use) {
+                sy = (float)(int)(sm.orig[y] - oay);
+                sz = (float)(int)(sm.orig[z] - oaz);
+                const uint32_t rowkey = ((uint32_t)z * n_c + (uint32_t)y) * n_c;
+                int xlo = ax - kx, xhi = ax + kx;
+                auto add = [&](uint32_t a, uint32_t b, int sf) {
+                    if (b > a) {
+                        s0[nl] = a;
+                        s1[nl] = b;
+                        self[nl] = sf;
+                        nl++;
+                    }
+                };
+                if (tm.auto_pairs && dz == 0 && dy == 0) {
+                    add(cs[rowkey + ax], cs[rowkey + ax + 1], 1);
+                    xlo = ax + 1;
+                }
+                if (xlo <= xhi) {
+                    if (periodic) {
+                        if (xlo < 0) {
+                            add(cs[rowkey + xlo + n_c], cs[rowkey + n_c], 0);
+                            add(cs[rowkey], cs[rowkey + xhi + 1], 0);
+                        } else if (xhi >= n_c) {
+                            add(cs[rowkey + xlo], cs[rowkey + n_c], 0);
+                            add(cs[rowkey], cs[rowkey + xhi - n_c + 1], 0);
+                        } else {
+                            add(cs[rowkey + xlo], cs[rowkey + xhi + 1], 0);
+                        }
+                    } else {
+                        xlo = max(xlo, 0);
+                        xhi = min(xhi, n_c - 1);
+                        if (xlo <= xhi) add(cs[rowkey + xlo], cs[rowkey + xhi + 1], 0);
+                    }
+                }
+            }
         }
+        uint32_t tl = 0;
+        for (int i = 0; i < nl; i++) tl += (s1[i] - s0[i] + TILE - 1) / TILE;
+        uint32_t n_all, t_all;
+        const uint32_t n_ex = warp_exclusive_sum((uint32_t)nl, lane, n_all);
+        uint32_t t_ex = warp_exclusive_sum(tl, lane, t_all);
+        for (int i = 0; i < nl; i++) {
+            Seg g;
+            g.s0 = s0[i];
+            g.s1 = s1[i];
+            g.tile0 = tiles_total + t_ex;
+            g.sy = sy;
+            g.sz = sz;
+            g.self = self[i];
+            g.pad = 0;
+            sm.segs[ns_total + n_ex + i] = g;
+            t_ex += (s1[i] - s0[i] + TILE - 1) / TILE;
+        }
+        ns_total += n_all;
+        tiles_total += t_all;
     }
-    sm.misc[1] = ns;
-    sm.misc[2] = (int)tiles;
+    if (lane == 0) {
+        sm.misc[1] = (int)ns_total;
+        sm.misc[2] = (int)tiles_total;
+    }
 }
 
 template <bool MU, bool MID>
@@ -404,7 +448,7 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
         cx.a0 = un.a0;
         cx.na = un.a1 - un.a0;
         for (uint32_t i = tid; i < cx.na; i += blockDim.x) sm.a[i] = __ldg(m.pf + un.a0 + i);
-        if (tid == 0) build_segments(prm, sm, m, tm, un.cell);
+        if (cx.warp == 0) build_segments(prm, sm, m, tm, un.cell, cx.lane);
         const int n_c = prm.n_c;
         const int ax = un.cell % n_c, ay = (un.cell / n_c) % n_c, az = un.cell / (n_c * n_c);
         const uint32_t oax = sm.orig[ax];
