@@ -31,7 +31,7 @@ namespace {
 
 constexpr int P = 4;            // b-points per lane
 constexpr int TILE = 32 * P;    // b-points per warp tile
-constexpr int QN = 64;          // queue slots per lane (16-bit entries)
+constexpr int QN = 40;          // queue slots per lane (16-bit entries)
 constexpr int WARPS = 8;        // warps per block
 constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 
@@ -50,13 +50,14 @@ struct Smem {
     float4 *a;                 // [UNIT_CHUNK]
     int *hist;                 // [nbin]
     uint16_t *queue;           // [WARPS][QN][32]
+    uint16_t *compact;         // [WARPS][QN * 32]
     float4 *bcopy;             // [WARPS][P][32]
     int16_t *table;            // [tab_n]
     float2 *lohi;              // [n_s + 2]
     uint32_t *orig;            // [n_c + 1]
     unsigned long long *T;     // [n_s + 1]
     Seg *segs;                 // [MAX_SEGS]
-    int *misc;                 // [4]: unit, n_segs, n_tiles
+    int *misc;                 // [4]: unit, n_segs, n_tiles, next tile
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -67,7 +68,7 @@ __host__ __device__ inline size_t smem_layout(const CountParams &p, size_t *off)
     off[0] = o; o = align16(o + sizeof(unsigned long long) * (p.n_s + 1));  // T
     off[1] = o; o = align16(o + sizeof(float4) * UNIT_CHUNK);              // a chunk
     off[2] = o; o = align16(o + sizeof(float4) * WARPS * P * 32);           // b copies
-    off[3] = o; o = align16(o + sizeof(uint16_t) * WARPS * QN * 32);        // queues
+    off[3] = o; o = align16(o + sizeof(uint16_t) * WARPS * QN * 32 * 2);    // queues + compacted copies
     off[4] = o; o = align16(o + sizeof(int) * p.nbin);                      // histogram
     off[5] = o; o = align16(o + sizeof(float2) * (p.n_s + 2));              // edge bands
     off[6] = o; o = align16(o + sizeof(uint32_t) * (p.n_c + 1));            // cell corners
@@ -129,6 +130,18 @@ __device__ __noinline__ int exact_bin(const CountParams &prm, const unsigned lon
     return k * n_mu + j;
 }
 
+__device__ __forceinline__ uint32_t warp_exclusive_sum(uint32_t v, int lane, uint32_t &total)
+{
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
 template <bool MU, bool MID>
 struct Ctx {
     const CountParams &prm;
@@ -136,6 +149,7 @@ struct Ctx {
     const Mesh &m;
     int lane, warp;
     uint16_t *q;               // this warp's queue
+    uint16_t *cq;              // this warp's compacted queue
     float4 *bc;                // this warp's b copies
     uint32_t a0, na;           // current unit's a-chunk
     float gx, gy, gz;          // 2 (corner(A) - observer), midpoint line of sight
@@ -185,27 +199,33 @@ struct Ctx {
         return k * prm.n_mu + j;
     }
 
+    // Bin every queued pair.  The lanes' queues are first packed into one
+    // warp-contiguous list (entry | owner lane << 10), so that the binning
+    // loop runs with all lanes busy whatever the spread of per-lane counts.
     __device__ __forceinline__ void flush(uint32_t &qoff, uint32_t base)
     {
         const uint32_t n = qoff >> 5;
+        uint32_t total;
+        const uint32_t pos = warp_exclusive_sum(n, lane, total);
         const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
-        for (uint32_t k = 0; k < nmax; k++) {
-            if (k < n) {
-                const uint32_t e = q[k * 32 + lane];
-                const uint32_t ai = e & 255u, p = e >> 8;
-                const float4 a = sm.a[ai];
-                const float4 b = bc[p * 32 + lane];
-                const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
-                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                int bin = classify(d2, dx, a, b);
-                if (bin == -2) {
-                    bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + ai, base + lane + 32u * p);
-                    n_exact++;
-                }
-                if (bin >= 0) {
-                    atomicAdd(&sm.hist[bin], 1);
-                    n_binned++;
-                }
+        for (uint32_t k = 0; k < nmax; k++)
+            if (k < n) cq[pos + k] = (uint16_t)(q[k * 32 + lane] | (lane << 10));
+        __syncwarp();
+        for (uint32_t e = lane; e < total; e += 32) {
+            const uint32_t v = cq[e];
+            const uint32_t ai = v & 255u, p = (v >> 8) & 3u, owner = v >> 10;
+            const float4 a = sm.a[ai];
+            const float4 b = bc[p * 32 + owner];
+            const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
+            const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+            int bin = classify(d2, dx, a, b);
+            if (bin == -2) {
+                bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + ai, base + owner + 32u * p);
+                n_exact++;
+            }
+            if (bin >= 0) {
+                atomicAdd(&sm.hist[bin], 1);
+                n_binned++;
             }
         }
         qoff = 0;
@@ -280,18 +300,6 @@ struct Ctx {
         if (__any_sync(0xffffffffu, qoff > 0)) flush(qoff, base);
     }
 };
-
-__device__ __forceinline__ uint32_t warp_exclusive_sum(uint32_t v, int lane, uint32_t &total)
-{
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    total = __shfl_sync(0xffffffffu, x, 31);
-    return x - v;
-}
 
 // The unit's b segments, built by one warp (one lane per neighbour row) and
 // stored in row order with their first tile index.
@@ -413,8 +421,9 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
     for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
     for (int i = tid; i < prm.nbin; i += blockDim.x) sm.hist[i] = 0;
 
-    Ctx<MU, MID> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
-    cx.q = sm.queue + (size_t)cx.warp * QN * 32;
+    Ctx<MU, MID> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
+    cx.q = sm.queue + (size_t)cx.warp * QN * 32 * 2;
+    cx.cq = cx.q + QN * 32;
     cx.bc = sm.bcopy + (size_t)cx.warp * P * 32;
     unsigned long long n_cand = 0;
 
@@ -449,6 +458,7 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
         cx.na = un.a1 - un.a0;
         for (uint32_t i = tid; i < cx.na; i += blockDim.x) sm.a[i] = __ldg(m.pf + un.a0 + i);
         if (cx.warp == 0) build_segments(prm, sm, m, tm, un.cell, cx.lane);
+        if (tid == 0) sm.misc[3] = 0;
         const int n_c = prm.n_c;
         const int ax = un.cell % n_c, ay = (un.cell / n_c) % n_c, az = un.cell / (n_c * n_c);
         const uint32_t oax = sm.orig[ax];
@@ -461,13 +471,18 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
         const int ns = sm.misc[1];
         const uint32_t nt = (uint32_t)sm.misc[2];
         int sg = 0;
-        for (uint32_t ti = cx.warp; ti < nt; ti += WARPS) {
+        // tiles are claimed one at a time from a shared counter (its first
+        // WARPS values are implicit), so warps finish a unit together
+        for (uint32_t ti = cx.warp; ti < nt;) {
             while (sg + 1 < ns && sm.segs[sg + 1].tile0 <= ti) sg++;
             const Seg g = sm.segs[sg];
             const uint32_t base = g.s0 + (ti - g.tile0) * TILE;
             n_cand += (unsigned long long)min(g.s1 - base, (uint32_t)TILE) * cx.na;
             if (g.self) cx.template tile<true>(base, g.s1, oax, g.sy, g.sz);
             else cx.template tile<false>(base, g.s1, oax, g.sy, g.sz);
+            uint32_t nx = 0;
+            if (cx.lane == 0) nx = (uint32_t)atomicAdd(&sm.misc[3], 1) + WARPS;
+            ti = __shfl_sync(0xffffffffu, nx, 0);
         }
         __syncthreads();
         // drain the block histogram into the term's int64 histogram

@@ -299,7 +299,7 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
                                                   : 1.0;
     bias = std::max(bias, std::ldexp(1.0, -100));
     p.tab_bias = (float)bias;
-    int mb = 9;
+    int mb = 8;
     for (;; mb--) {
         const int sh = 23 - mb;
         uint32_t k0, ke;
