@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--nd", type=int, default=synth.MID.n_d, help="data points per mock")
     p.add_argument("--precision", default="fp64", choices=["fp64", "tf32x3", "bf16x3"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--subdiv", type=int, default=0, help="pin the mesh subdivision (0: library choice)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--count-only", action="store_true",
                    help="one warm-up and one batched tpcf_count of the workload, then exit (profiler captures)")
@@ -245,6 +246,8 @@ def main():
     nd_list = [sz[0] for _, sz in layout]
     nr_list = [[sz[1], sz[2]] for _, sz in layout]
     ctx = tp.Context(local)
+    if args.subdiv:
+        ctx.tpcf_set_cell_subdiv(args.subdiv)
     b = tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_PERIODIC, w.L)
     nbin = w.n_s * w.n_mu
     outc = {"dd": torch.empty((n_mock, nbin), dtype=torch.int64, device=dev),

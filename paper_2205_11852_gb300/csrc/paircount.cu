@@ -142,6 +142,15 @@ __device__ __forceinline__ uint32_t warp_exclusive_sum(uint32_t v, int lane, uin
     return x - v;
 }
 
+// MUFU reciprocal square root without denormal handling (relative error
+// within 2 ulp); every use carries that error in its ambiguity band
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <bool MU, bool MID>
 struct Ctx {
     const CountParams &prm;
@@ -155,7 +164,8 @@ struct Ctx {
     float gx, gy, gz;          // 2 (corner(A) - observer), midpoint line of sight
     unsigned n_exact, n_binned;
 
-    // bin of a queued pair; -1 unbinned, -2 recheck exactly
+    // Bin of a queued pair: >= 0, -1 (not binned) or -2 (recheck exactly).
+    // Straight-line code: every lane runs the same instructions.
     __device__ __forceinline__ int classify(float d2, float dx, const float4 &a, const float4 &b) const
     {
         const uint32_t key = min((__float_as_uint(__fadd_rn(d2, prm.tab_bias)) >> prm.tab_shift) - prm.tab_key0,
@@ -167,68 +177,85 @@ struct Ctx {
         const bool ge_hi = d2 >= lh.y;
         amb |= (d2 >= lh.x) && !ge_hi;
         k += ge_hi ? 1 : 0;
-        if (!MU) return amb ? -2 : ((unsigned)k < (unsigned)prm.n_s ? k : -1);
-        if ((unsigned)k >= (unsigned)prm.n_s && !amb) return -1;
-        float t, beta;
-        if (!MID) {
-            const float r = rsqrtf(__fmul_rn(d2, prm.inv_nmu2));   // n_mu / sqrt(d2)
-            t = __fmul_rn(fabsf(dx), r);
-            beta = __fmaf_rn(prm.mu_c1, r, prm.mu_c2);
-        } else {
-            const float ex = __fsub_rn(a.x, b.x), ey = __fsub_rn(a.y, b.y), ez = __fsub_rn(a.z, b.z);
-            const float lx = __fadd_rn(__fadd_rn(gx, a.x), b.x);
-            const float ly = __fadd_rn(__fadd_rn(gy, a.y), b.y);
-            const float lz = __fadd_rn(__fadd_rn(gz, a.z), b.z);
-            const float dot = __fmaf_rn(ez, lz, __fmaf_rn(ey, ly, __fmul_rn(ex, lx)));
-            const float l2 = __fmaf_rn(lz, lz, __fmaf_rn(ly, ly, __fmul_rn(lx, lx)));
-            const float rs = rsqrtf(d2), rl = rsqrtf(l2);
-            t = __fmul_rn(__fmul_rn(__fmul_rn(fabsf(dot), rs), rl), (float)prm.n_mu);
-            beta = __fmaf_rn(prm.mu_c1, rs, __fmaf_rn(prm.mu_c3, rl, prm.mu_c2));
+        const bool valid = (unsigned)k < (unsigned)prm.n_s;
+        int bin = k;
+        if (MU) {
+            float t, beta;
+            if (!MID) {
+                const float r = rsqrt_approx(__fmul_rn(d2, prm.inv_nmu2));   // n_mu / sqrt(d2)
+                t = __fmul_rn(fabsf(dx), r);
+                beta = __fmaf_rn(prm.mu_c1, r, prm.mu_c2);
+            } else {
+                const float ex = __fsub_rn(a.x, b.x), ey = __fsub_rn(a.y, b.y), ez = __fsub_rn(a.z, b.z);
+                const float lx = __fadd_rn(__fadd_rn(gx, a.x), b.x);
+                const float ly = __fadd_rn(__fadd_rn(gy, a.y), b.y);
+                const float lz = __fadd_rn(__fadd_rn(gz, a.z), b.z);
+                const float dot = __fmaf_rn(ez, lz, __fmaf_rn(ey, ly, __fmul_rn(ex, lx)));
+                const float l2 = __fmaf_rn(lz, lz, __fmaf_rn(ly, ly, __fmul_rn(lx, lx)));
+                const float rs = rsqrt_approx(d2), rl = rsqrt_approx(l2);
+                t = __fmul_rn(__fmul_rn(__fmul_rn(fabsf(dot), rs), rl), (float)prm.n_mu);
+                beta = __fmaf_rn(prm.mu_c1, rs, __fmaf_rn(prm.mu_c3, rl, prm.mu_c2));
+            }
+            // round t to the nearest integer mi with the 1.5 * 2^23 trick; the
+            // pair is ambiguous when t lies within beta of an interior mu edge
+            const float big = 12582912.0f;
+            const float mf = __fadd_rn(t, big);
+            const int mi = __float_as_int(mf) - 0x4B400000;
+            const float d = __fsub_rn(t, __fsub_rn(mf, big));
+            amb |= !(beta < 0.05f);
+            amb |= (fabsf(d) < beta) && ((unsigned)(mi - 1) < (unsigned)(prm.n_mu - 1));
+            const int j = min(max(mi - (d < 0.0f ? 1 : 0), 0), prm.n_mu - 1);
+            bin = k * prm.n_mu + j;
         }
-        // round t to the nearest integer m with the 1.5 * 2^23 trick; the pair
-        // is ambiguous when t is within beta of an interior mu edge 1..n_mu-1
-        const float big = 12582912.0f;
-        const float mf = __fadd_rn(t, big);
-        const int mi = __float_as_int(mf) - 0x4B400000;
-        const float d = __fsub_rn(t, __fsub_rn(mf, big));
-        amb |= !(beta < 0.05f);
-        amb |= (fabsf(d) < beta) && (mi >= 1) && (mi <= prm.n_mu - 1);
-        if (amb) return -2;
-        int j = mi - (d < 0.0f ? 1 : 0);
-        j = min(max(j, 0), prm.n_mu - 1);
-        return k * prm.n_mu + j;
+        return amb ? -2 : (valid ? bin : -1);
     }
 
     // Bin every queued pair.  The lanes' queues are first packed into one
     // warp-contiguous list (entry | owner lane << 10), so that the binning
     // loop runs with all lanes busy whatever the spread of per-lane counts.
-    __device__ __forceinline__ void flush(uint32_t &qoff, uint32_t base)
+    // Pairs that need the exact recheck are gathered (in place, behind the
+    // read position) and rechecked after the loop.
+    __device__ __forceinline__ void flush(uint16_t *&head, uint32_t base)
     {
-        const uint32_t n = qoff >> 5;
+        const uint32_t n = (uint32_t)(head - (q + lane)) >> 5;
         uint32_t total;
         const uint32_t pos = warp_exclusive_sum(n, lane, total);
         const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
         for (uint32_t k = 0; k < nmax; k++)
             if (k < n) cq[pos + k] = (uint16_t)(q[k * 32 + lane] | (lane << 10));
         __syncwarp();
-        for (uint32_t e = lane; e < total; e += 32) {
-            const uint32_t v = cq[e];
+        uint32_t n_amb = 0;
+        for (uint32_t w0 = 0; w0 < total; w0 += 32) {
+            const uint32_t e = w0 + lane;
+            const bool live = e < total;
+            const uint32_t v = live ? cq[e] : 0u;
             const uint32_t ai = v & 255u, p = (v >> 8) & 3u, owner = v >> 10;
             const float4 a = sm.a[ai];
             const float4 b = bc[p * 32 + owner];
             const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
             const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-            int bin = classify(d2, dx, a, b);
-            if (bin == -2) {
-                bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + ai, base + owner + 32u * p);
-                n_exact++;
+            const int bin = live ? classify(d2, dx, a, b) : -1;
+            if (bin >= 0) atomicAdd(&sm.hist[bin], 1);
+            n_binned += (bin >= 0) ? 1u : 0u;
+            const unsigned am = __ballot_sync(0xffffffffu, bin == -2);
+            if (am) {
+                __syncwarp();
+                if (bin == -2) cq[n_amb + __popc(am & ((1u << lane) - 1u))] = (uint16_t)v;
+                n_amb += __popc(am);
             }
+        }
+        __syncwarp();
+        for (uint32_t e = lane; e < n_amb; e += 32) {
+            const uint32_t v = cq[e];
+            const uint32_t ai = v & 255u, p = (v >> 8) & 3u, owner = v >> 10;
+            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + ai, base + owner + 32u * p);
+            n_exact++;
             if (bin >= 0) {
                 atomicAdd(&sm.hist[bin], 1);
                 n_binned++;
             }
         }
-        qoff = 0;
+        head = q + lane;
         __syncwarp();
     }
 
@@ -257,13 +284,11 @@ struct Ctx {
             bc[p * 32 + lane] = make_float4(bx[p], by[p], bz[p], 0.0f);
         }
         __syncwarp();
-        // queue write position in slots * 32.  Every candidate writes the head
-        // slot; only a hit advances it, so stores stay branch-free.  The head
-        // stays below QN slots: a flush is forced before 2P more pushes could
-        // overflow.
-        uint32_t qoff = 0;
-        uint16_t *const qh = q + lane;
-        const uint32_t lim = (uint32_t)(QN - 2 * P) << 5;
+        // Every candidate writes the head slot of the lane's queue; only a hit
+        // advances the head, so the stores stay branch-free.  A flush is forced
+        // before 2P more pushes could run past QN slots.
+        uint16_t *head = q + lane;
+        uint16_t *const lim = q + lane + (QN - 2 * P) * 32;
         const uint32_t ib0 = base + lane;
         uint32_t ai = 0;
         for (; ai + 1 < na; ai += 2) {
@@ -273,18 +298,18 @@ struct Ctx {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                qh[qoff] = (uint16_t)(ai | (p << 8));   // head slot; kept only on a hit
-                qoff += hit ? 32u : 0u;
+                *head = (uint16_t)(ai | (p << 8));   // kept only on a hit
+                head += hit ? 32 : 0;
             }
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const float t = __fmaf_rn(c.x, bx[p], __fmaf_rn(c.y, by[p], __fmaf_rn(c.z, bz[p], c.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai + 1 < ib0 + 32u * p);
-                qh[qoff] = (uint16_t)((ai + 1) | (p << 8));
-                qoff += hit ? 32u : 0u;
+                *head = (uint16_t)((ai + 1) | (p << 8));
+                head += hit ? 32 : 0;
             }
-            if (__any_sync(0xffffffffu, qoff > lim)) flush(qoff, base);
+            if (__any_sync(0xffffffffu, head > lim)) flush(head, base);
         }
         if (ai < na) {
             const float4 a = sm.a[ai];
@@ -293,11 +318,11 @@ struct Ctx {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                qh[qoff] = (uint16_t)(ai | (p << 8));   // head slot; kept only on a hit
-                qoff += hit ? 32u : 0u;
+                *head = (uint16_t)(ai | (p << 8));
+                head += hit ? 32 : 0;
             }
         }
-        if (__any_sync(0xffffffffu, qoff > 0)) flush(qoff, base);
+        if (__any_sync(0xffffffffu, head != q + lane)) flush(head, base);
     }
 };
 
