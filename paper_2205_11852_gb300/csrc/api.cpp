@@ -394,7 +394,7 @@ int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_bin
     max_cells = std::min<unsigned long long>(max_cells, ((1ull << 32) - 2) / tabs);
 
     // plan (subdivision pinned, or the default)
-    int subdiv = ctx->subdiv_pin ? ctx->subdiv_pin : 2;
+    int subdiv = ctx->subdiv_pin ? ctx->subdiv_pin : 3;
     Plan pl;
     std::string perr;
     if ((rc = build_plan(*binning, subdiv, max_cells, pl, perr))) return fail(ctx, rc, perr);

@@ -151,7 +151,7 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     return y;
 }
 
-template <bool MU, bool MID>
+template <bool MU, bool MID, bool LIN>
 struct Ctx {
     const CountParams &prm;
     const Smem &sm;
@@ -168,21 +168,38 @@ struct Ctx {
     // Straight-line code: every lane runs the same instructions.
     __device__ __forceinline__ int classify(float d2, float dx, const float4 &a, const float4 &b) const
     {
-        const uint32_t key = min((__float_as_uint(__fadd_rn(d2, prm.tab_bias)) >> prm.tab_shift) - prm.tab_key0,
-                                 (uint32_t)(prm.tab_n - 1));
-        int k = sm.table[key];
-        bool amb = (k == CODE_AMBIG);
-        k = amb ? -1 : k;
-        const float2 lh = sm.lohi[k + 1];
-        const bool ge_hi = d2 >= lh.y;
-        amb |= (d2 >= lh.x) && !ge_hi;
-        k += ge_hi ? 1 : 0;
-        const bool valid = (unsigned)k < (unsigned)prm.n_s;
+        const float big = 12582912.0f;   // 1.5 * 2^23: x + big rounds x to an integer
+        bool amb = false, valid;
+        int k;
+        float r = 0.0f;
+        if (LIN) {
+            // s bin = floor(u), u = sqrt(d2) / (q ds); ambiguous near an interior
+            // edge or near s_max
+            r = rsqrt_approx(__fmul_rn(d2, prm.inv_nmu2));      // n_mu / sqrt(d2)
+            const float u = __fmul_rn(__fmul_rn(d2, r), prm.s_scale);
+            const float mf = __fadd_rn(u, big);
+            const int ki = __float_as_int(mf) - 0x4B400000;
+            const float ds = __fsub_rn(u, __fsub_rn(mf, big));
+            amb = (fabsf(ds) < __fmaf_rn(prm.s_c1, u, prm.s_c0)) && ((unsigned)(ki - 1) < (unsigned)prm.n_s);
+            k = ki - (ds < 0.0f ? 1 : 0);
+            valid = (unsigned)k < (unsigned)prm.n_s;
+        } else {
+            const uint32_t key = min((__float_as_uint(__fadd_rn(d2, prm.tab_bias)) >> prm.tab_shift) - prm.tab_key0,
+                                     (uint32_t)(prm.tab_n - 1));
+            k = sm.table[key];
+            amb = (k == CODE_AMBIG);
+            k = amb ? -1 : k;
+            const float2 lh = sm.lohi[k + 1];
+            const bool ge_hi = d2 >= lh.y;
+            amb |= (d2 >= lh.x) && !ge_hi;
+            k += ge_hi ? 1 : 0;
+            valid = (unsigned)k < (unsigned)prm.n_s;
+        }
         int bin = k;
         if (MU) {
             float t, beta;
             if (!MID) {
-                const float r = rsqrt_approx(__fmul_rn(d2, prm.inv_nmu2));   // n_mu / sqrt(d2)
+                if (!LIN) r = rsqrt_approx(__fmul_rn(d2, prm.inv_nmu2));   // n_mu / sqrt(d2)
                 t = __fmul_rn(fabsf(dx), r);
                 beta = __fmaf_rn(prm.mu_c1, r, prm.mu_c2);
             } else {
@@ -196,9 +213,8 @@ struct Ctx {
                 t = __fmul_rn(__fmul_rn(__fmul_rn(fabsf(dot), rs), rl), (float)prm.n_mu);
                 beta = __fmaf_rn(prm.mu_c1, rs, __fmaf_rn(prm.mu_c3, rl, prm.mu_c2));
             }
-            // round t to the nearest integer mi with the 1.5 * 2^23 trick; the
-            // pair is ambiguous when t lies within beta of an interior mu edge
-            const float big = 12582912.0f;
+            // the pair is ambiguous when t = n_mu |mu| lies within beta of an
+            // interior mu edge 1..n_mu-1
             const float mf = __fadd_rn(t, big);
             const int mi = __float_as_int(mf) - 0x4B400000;
             const float d = __fsub_rn(t, __fsub_rn(mf, big));
@@ -206,12 +222,14 @@ struct Ctx {
             amb |= (fabsf(d) < beta) && ((unsigned)(mi - 1) < (unsigned)(prm.n_mu - 1));
             const int j = min(max(mi - (d < 0.0f ? 1 : 0), 0), prm.n_mu - 1);
             bin = k * prm.n_mu + j;
+        } else if (LIN) {
+            amb |= !(r < 3.0e38f);   // d2 == 0: r = inf, u = NaN
         }
         return amb ? -2 : (valid ? bin : -1);
     }
 
     // Bin every queued pair.  The lanes' queues are first packed into one
-    // warp-contiguous list (entry | owner lane << 10), so that the binning
+    // warp-contiguous list (a index | b copy index << 8), so that the binning
     // loop runs with all lanes busy whatever the spread of per-lane counts.
     // Pairs that need the exact recheck are gathered (in place, behind the
     // read position) and rechecked after the loop.
@@ -222,16 +240,19 @@ struct Ctx {
         const uint32_t pos = warp_exclusive_sum(n, lane, total);
         const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
         for (uint32_t k = 0; k < nmax; k++)
-            if (k < n) cq[pos + k] = (uint16_t)(q[k * 32 + lane] | (lane << 10));
+            if (k < n) {
+                const uint32_t v = q[k * 32 + lane];   // a index | p << 8
+                cq[pos + k] = (uint16_t)((v & 255u) | ((((v >> 8) << 5) | lane) << 8));
+            }
         __syncwarp();
         uint32_t n_amb = 0;
         for (uint32_t w0 = 0; w0 < total; w0 += 32) {
             const uint32_t e = w0 + lane;
             const bool live = e < total;
             const uint32_t v = live ? cq[e] : 0u;
-            const uint32_t ai = v & 255u, p = (v >> 8) & 3u, owner = v >> 10;
+            const uint32_t ai = v & 255u, bi = v >> 8;   // bi = p * 32 + owner lane = ib - base
             const float4 a = sm.a[ai];
-            const float4 b = bc[p * 32 + owner];
+            const float4 b = bc[bi];
             const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
             const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
             const int bin = live ? classify(d2, dx, a, b) : -1;
@@ -247,8 +268,7 @@ struct Ctx {
         __syncwarp();
         for (uint32_t e = lane; e < n_amb; e += 32) {
             const uint32_t v = cq[e];
-            const uint32_t ai = v & 255u, p = (v >> 8) & 3u, owner = v >> 10;
-            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + ai, base + owner + 32u * p);
+            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + (v & 255u), base + (v >> 8));
             n_exact++;
             if (bin >= 0) {
                 atomicAdd(&sm.hist[bin], 1);
@@ -415,7 +435,7 @@ __device__ void build_segments(const CountParams &prm, const Smem &sm, const Mes
     }
 }
 
-template <bool MU, bool MID>
+template <bool MU, bool MID, bool LIN>
 __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_constant__ CountParams prm, const Mesh m,
                                                                 const Term *__restrict__ terms,
                                                                 const Unit *__restrict__ units,
@@ -446,7 +466,7 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
     for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
     for (int i = tid; i < prm.nbin; i += blockDim.x) sm.hist[i] = 0;
 
-    Ctx<MU, MID> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
+    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
     cx.q = sm.queue + (size_t)cx.warp * QN * 32 * 2;
     cx.cq = cx.q + QN * 32;
     cx.bc = sm.bcopy + (size_t)cx.warp * P * 32;
@@ -535,19 +555,20 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
     }
 }
 
-template <bool MU, bool MID>
+template <bool MU, bool MID, bool LIN>
 void *kernel_ptr()
 {
-    return (void *)paircount_kernel<MU, MID>;
+    return (void *)paircount_kernel<MU, MID, LIN>;
 }
 
 void *select_kernel(const CountParams &p)
 {
     const bool mu = p.n_mu > 1;
     const bool mid = mu && p.los == TPCF_LOS_MIDPOINT;
-    if (!mu) return kernel_ptr<false, false>();
-    if (!mid) return kernel_ptr<true, false>();
-    return kernel_ptr<true, true>();
+    const bool lin = p.linear != 0;
+    if (!mu) return lin ? kernel_ptr<false, false, true>() : kernel_ptr<false, false, false>();
+    if (!mid) return lin ? kernel_ptr<true, false, true>() : kernel_ptr<true, false, false>();
+    return lin ? kernel_ptr<true, true, true>() : kernel_ptr<true, true, false>();
 }
 
 }  // namespace

@@ -289,6 +289,21 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
         p.mu_c3 = (float)(b.n_mu * 2.2 * std::sqrt(3.0) * El);
     }
 
+    // Linear bins starting at 0 (e_k = k e_1 exactly): the s bin is
+    // floor(u*), u* = sqrt(D2) / (q e_1), and |u - u*| <= s_c0 + s_c1 u for the
+    // FP32 estimate u (d2 error, 2-ulp rsqrt, three roundings).
+    {
+        bool lin = b.s_edges[0] == 0.0 && b.n_s >= 1;
+        const double e1 = b.s_edges[1];
+        for (int k = 1; lin && k <= b.n_s; k++) lin = std::fma((double)k, e1, -b.s_edges[k]) == 0.0;
+        const double q = std::ldexp(1.0, p.bits) / L;
+        const double qds = q * e1;
+        p.linear = lin ? 1 : 0;
+        p.s_scale = (float)(1.0 / ((double)b.n_mu * qds));
+        p.s_c0 = (float)(1.5 * (std::sqrt(3.0) * E / qds + 1.5 * E * E / (qds * qds)) + 1e-6);
+        p.s_c1 = (float)std::ldexp(1.0, -19);
+    }
+
     // s-bin table over FP32 bit patterns of d2 + bias.  The bias (a power of
     // two well below the first positive edge band) keeps every key at or
     // above the table's first key.

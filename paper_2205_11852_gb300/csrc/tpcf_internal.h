@@ -65,6 +65,9 @@ struct CountParams {
     float mu_c1, mu_c2;    // mu ambiguity band (see the kernel)
     float mu_c3;
     float inv_nmu2;        // 1 / n_mu^2
+    int linear;            // edges e_k = k * ds exactly: s bin = floor(sqrt(D2) / (q ds))
+    float s_scale;         // 1 / (n_mu q ds): u = d2 * (n_mu / sqrt(d2)) * s_scale = sqrt(d2) / (q ds)
+    float s_c0, s_c1;      // s band for the linear path: beta_s = s_c0 + s_c1 * u
     long long obs[3];      // observer in grid units (midpoint line of sight)
     unsigned long long T[MAX_NS + 1];        // exact squared edges in grid units
     float lo[MAX_NS + 2], hi[MAX_NS + 2];    // float bands: d2 < lo => D2 < T; d2 >= hi => D2 >= T;
