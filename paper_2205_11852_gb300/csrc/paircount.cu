@@ -38,12 +38,13 @@ constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 typedef unsigned __int128 u128;
 typedef __int128 i128;
 
+// A run of b-points: cells x0..x1 of one neighbour row, contiguous in the
+// cell-sorted order.  Runs are concatenated, and the concatenation is cut
+// into full tiles, so a tile may span several rows.
 struct Seg {
-    uint32_t s0, s1;       // b range
-    uint32_t tile0;        // first tile index of this segment
+    uint32_t s0;           // first b index
+    uint32_t off0;         // offset of s0 in the concatenation of the unit's runs
     float sy, sz;          // row shift into A's frame
-    int self;              // the run is cell A itself in an auto count
-    int pad;
 };
 
 struct Smem {
@@ -56,8 +57,9 @@ struct Smem {
     float2 *lohi;              // [n_s + 2]
     uint32_t *orig;            // [n_c + 1]
     unsigned long long *T;     // [n_s + 1]
-    Seg *segs;                 // [MAX_SEGS]
-    int *misc;                 // [4]: unit, n_segs, n_tiles, next tile
+    Seg *segs;                 // [MAX_SEGS + 1], the last one a sentinel
+    uint32_t *bidx;            // [WARPS][P][32] b index of every loaded b-point
+    int *misc;                 // [8]: unit, n_segs, packed points, next tile, self s0, self s1
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -73,8 +75,9 @@ __host__ __device__ inline size_t smem_layout(const CountParams &p, size_t *off)
     off[5] = o; o = align16(o + sizeof(float2) * (p.n_s + 2));              // edge bands
     off[6] = o; o = align16(o + sizeof(uint32_t) * (p.n_c + 1));            // cell corners
     off[7] = o; o = align16(o + sizeof(int16_t) * p.tab_n);                 // s table
-    off[8] = o; o = align16(o + sizeof(Seg) * MAX_SEGS);                    // segments
-    off[9] = o; o = align16(o + sizeof(int) * 4);
+    off[8] = o; o = align16(o + sizeof(Seg) * (MAX_SEGS + 1));              // segments
+    off[9] = o; o = align16(o + sizeof(uint32_t) * WARPS * P * 32);         // b indices
+    off[10] = o; o = align16(o + sizeof(int) * 8);
     return o;
 }
 
@@ -160,6 +163,7 @@ struct Ctx {
     uint16_t *q;               // this warp's queue
     uint16_t *cq;              // this warp's compacted queue
     float4 *bc;                // this warp's b copies
+    uint32_t *bix;             // this warp's b indices
     uint32_t a0, na;           // current unit's a-chunk
     float gx, gy, gz;          // 2 (corner(A) - observer), midpoint line of sight
     unsigned n_exact, n_binned;
@@ -233,7 +237,7 @@ struct Ctx {
     // loop runs with all lanes busy whatever the spread of per-lane counts.
     // Pairs that need the exact recheck are gathered (in place, behind the
     // read position) and rechecked after the loop.
-    __device__ __forceinline__ void flush(uint16_t *&head, uint32_t base)
+    __device__ __forceinline__ void flush(uint16_t *&head)
     {
         const uint32_t n = (uint32_t)(head - (q + lane)) >> 5;
         uint32_t total;
@@ -268,7 +272,7 @@ struct Ctx {
         __syncwarp();
         for (uint32_t e = lane; e < n_amb; e += 32) {
             const uint32_t v = cq[e];
-            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + (v & 255u), base + (v >> 8));
+            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + (v & 255u), bix[v >> 8]);
             n_exact++;
             if (bin >= 0) {
                 atomicAdd(&sm.hist[bin], 1);
@@ -279,29 +283,59 @@ struct Ctx {
         __syncwarp();
     }
 
-    // all pairs of the a-chunk with one tile of b-points starting at `base`
+    // Load one b-point into lane registers (shifted into A's frame) and into
+    // the warp's b copies used by the flush.
+    __device__ __forceinline__ void load_b(int p, bool ok, uint32_t i, float sy, float sz, uint32_t orig_ax,
+                                           float (&bx)[P], float (&by)[P], float (&bz)[P], float (&hb)[P]) const
+    {
+        if (ok) {
+            const float4 v = __ldg(m.pf + i);
+            const int cx = m.pcx[i];
+            const float sx = (float)(int)(sm.orig[cx] - orig_ax);
+            bx[p] = __fadd_rn(v.x, sx);
+            by[p] = __fadd_rn(v.y, sy);
+            bz[p] = __fadd_rn(v.z, sz);
+            const float b2 = __fmaf_rn(bz[p], bz[p], __fmaf_rn(by[p], by[p], __fmul_rn(bx[p], bx[p])));
+            hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, prm.hit_max)), prm.dot_margin);
+        } else {
+            bx[p] = by[p] = bz[p] = 0.0f;
+            hb[p] = __int_as_float(0x7f800000);   // +inf: never passes
+            i = 0;
+        }
+        bc[p * 32 + lane] = make_float4(bx[p], by[p], bz[p], 0.0f);
+        bix[p * 32 + lane] = i;
+    }
+
+    // all pairs of the a-chunk with one tile of b-points: the self cell of an
+    // auto count (SELF, indices base..s1) or a packed tile at offset o_base of
+    // the concatenated runs (n_seg runs, total points).
     template <bool SELF>
-    __device__ __forceinline__ void tile(uint32_t base, uint32_t s1, uint32_t orig_ax, float sy, float sz)
+    __device__ __forceinline__ void tile(uint32_t base, uint32_t s1, uint32_t o_base, int n_seg, uint32_t total,
+                                         uint32_t orig_ax)
     {
         float bx[P], by[P], bz[P], hb[P];
-        const float H = prm.hit_max, mg = prm.dot_margin;
+        if (SELF) {
 #pragma unroll
-        for (int p = 0; p < P; p++) {
-            const uint32_t i = base + lane + 32u * p;
-            if (i < s1) {
-                const float4 v = __ldg(m.pf + i);
-                const int cx = m.pcx[i];
-                const float sx = (float)(int)(sm.orig[cx] - orig_ax);
-                bx[p] = __fadd_rn(v.x, sx);
-                by[p] = __fadd_rn(v.y, sy);
-                bz[p] = __fadd_rn(v.z, sz);
-                const float b2 = __fmaf_rn(bz[p], bz[p], __fmaf_rn(by[p], by[p], __fmul_rn(bx[p], bx[p])));
-                hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, H)), mg);
-            } else {
-                bx[p] = by[p] = bz[p] = 0.0f;
-                hb[p] = __int_as_float(0x7f800000);   // +inf: never passes
+            for (int p = 0; p < P; p++) {
+                const uint32_t i = base + lane + 32u * p;
+                load_b(p, i < s1, i, 0.0f, 0.0f, orig_ax, bx, by, bz, hb);
             }
-            bc[p * 32 + lane] = make_float4(bx[p], by[p], bz[p], 0.0f);
+        } else {
+            // locate the run of this lane's first point, then walk forward
+            const uint32_t o0 = o_base + lane;
+            int lo = 0, hi = n_seg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sm.segs[mid].off0 <= o0) lo = mid; else hi = mid - 1;
+            }
+            int g = lo;
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                const uint32_t o = o0 + 32u * p;
+                while (g + 1 < n_seg && sm.segs[g + 1].off0 <= o) g++;
+                const Seg sg = sm.segs[g];
+                load_b(p, o < total, sg.s0 + (o - sg.off0), sg.sy, sg.sz, orig_ax, bx, by, bz, hb);
+            }
         }
         __syncwarp();
         // Every candidate writes the head slot of the lane's queue; only a hit
@@ -309,7 +343,7 @@ struct Ctx {
         // before 2P more pushes could run past QN slots.
         uint16_t *head = q + lane;
         uint16_t *const lim = q + lane + (QN - 2 * P) * 32;
-        const uint32_t ib0 = base + lane;
+        const uint32_t ib0 = base + lane;   // used by SELF tiles only
         uint32_t ai = 0;
         for (; ai + 1 < na; ai += 2) {
             const float4 a = sm.a[ai], c = sm.a[ai + 1];
@@ -329,7 +363,7 @@ struct Ctx {
                 *head = (uint16_t)((ai + 1) | (p << 8));
                 head += hit ? 32 : 0;
             }
-            if (__any_sync(0xffffffffu, head > lim)) flush(head, base);
+            if (__any_sync(0xffffffffu, head > lim)) flush(head);
         }
         if (ai < na) {
             const float4 a = sm.a[ai];
@@ -342,12 +376,13 @@ struct Ctx {
                 head += hit ? 32 : 0;
             }
         }
-        if (__any_sync(0xffffffffu, head != q + lane)) flush(head, base);
+        if (__any_sync(0xffffffffu, head != q + lane)) flush(head);
     }
 };
 
-// The unit's b segments, built by one warp (one lane per neighbour row) and
-// stored in row order with their first tile index.
+// The unit's b runs, built by one warp (one lane per neighbour row): the
+// self cell of an auto count apart, every other run concatenated in row order
+// with its offset in the concatenation.
 __device__ void build_segments(const CountParams &prm, const Smem &sm, const Mesh &m, const Term &tm, int cell,
                                int lane)
 {
@@ -356,11 +391,15 @@ __device__ void build_segments(const CountParams &prm, const Smem &sm, const Mes
     const bool periodic = prm.geometry == TPCF_PERIODIC;
     const uint32_t *cs = m.cellstart + (size_t)tm.cat_b * prm.n_cells;
     const uint32_t oay = sm.orig[ay], oaz = sm.orig[az];
-    uint32_t ns_total = 0, tiles_total = 0;
+    uint32_t ns_total = 0, pts_total = 0;
+    if (lane == 0) {
+        sm.misc[4] = 0;
+        sm.misc[5] = 0;
+    }
+    __syncwarp();
     for (int r0 = 0; r0 < prm.n_rows; r0 += 32) {
         const int r = r0 + lane;
-        uint32_t s0[3], s1[3];
-        int self[3];
+        uint32_t s0[2], s1[2];
         int nl = 0;
         float sy = 0.f, sz = 0.f;
         if (r < prm.n_rows) {
@@ -378,60 +417,57 @@ __device__ void build_segments(const CountParams &prm, const Smem &sm, const Mes
                 sz = (float)(int)(sm.orig[z] - oaz);
                 const uint32_t rowkey = ((uint32_t)z * n_c + (uint32_t)y) * n_c;
                 int xlo = ax - kx, xhi = ax + kx;
-                auto add = [&](uint32_t a, uint32_t b, int sf) {
+                auto add = [&](uint32_t a, uint32_t b) {
                     if (b > a) {
                         s0[nl] = a;
                         s1[nl] = b;
-                        self[nl] = sf;
                         nl++;
                     }
                 };
                 if (tm.auto_pairs && dz == 0 && dy == 0) {
-                    add(cs[rowkey + ax], cs[rowkey + ax + 1], 1);
+                    sm.misc[4] = (int)cs[rowkey + ax];
+                    sm.misc[5] = (int)cs[rowkey + ax + 1];
                     xlo = ax + 1;
                 }
                 if (xlo <= xhi) {
                     if (periodic) {
                         if (xlo < 0) {
-                            add(cs[rowkey + xlo + n_c], cs[rowkey + n_c], 0);
-                            add(cs[rowkey], cs[rowkey + xhi + 1], 0);
+                            add(cs[rowkey + xlo + n_c], cs[rowkey + n_c]);
+                            add(cs[rowkey], cs[rowkey + xhi + 1]);
                         } else if (xhi >= n_c) {
-                            add(cs[rowkey + xlo], cs[rowkey + n_c], 0);
-                            add(cs[rowkey], cs[rowkey + xhi - n_c + 1], 0);
+                            add(cs[rowkey + xlo], cs[rowkey + n_c]);
+                            add(cs[rowkey], cs[rowkey + xhi - n_c + 1]);
                         } else {
-                            add(cs[rowkey + xlo], cs[rowkey + xhi + 1], 0);
+                            add(cs[rowkey + xlo], cs[rowkey + xhi + 1]);
                         }
                     } else {
                         xlo = max(xlo, 0);
                         xhi = min(xhi, n_c - 1);
-                        if (xlo <= xhi) add(cs[rowkey + xlo], cs[rowkey + xhi + 1], 0);
+                        if (xlo <= xhi) add(cs[rowkey + xlo], cs[rowkey + xhi + 1]);
                     }
                 }
             }
         }
-        uint32_t tl = 0;
-        for (int i = 0; i < nl; i++) tl += (s1[i] - s0[i] + TILE - 1) / TILE;
-        uint32_t n_all, t_all;
+        uint32_t pl = 0;
+        for (int i = 0; i < nl; i++) pl += s1[i] - s0[i];
+        uint32_t n_all, p_all;
         const uint32_t n_ex = warp_exclusive_sum((uint32_t)nl, lane, n_all);
-        uint32_t t_ex = warp_exclusive_sum(tl, lane, t_all);
+        uint32_t p_ex = warp_exclusive_sum(pl, lane, p_all);
         for (int i = 0; i < nl; i++) {
             Seg g;
             g.s0 = s0[i];
-            g.s1 = s1[i];
-            g.tile0 = tiles_total + t_ex;
+            g.off0 = pts_total + p_ex;
             g.sy = sy;
             g.sz = sz;
-            g.self = self[i];
-            g.pad = 0;
             sm.segs[ns_total + n_ex + i] = g;
-            t_ex += (s1[i] - s0[i] + TILE - 1) / TILE;
+            p_ex += s1[i] - s0[i];
         }
         ns_total += n_all;
-        tiles_total += t_all;
+        pts_total += p_all;
     }
     if (lane == 0) {
         sm.misc[1] = (int)ns_total;
-        sm.misc[2] = (int)tiles_total;
+        sm.misc[2] = (int)pts_total;
     }
 }
 
@@ -446,7 +482,7 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
                                                                 int persistent, int term_pl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    size_t off[10];
+    size_t off[11];
     smem_layout(prm, off);
     Smem sm;
     sm.T = (unsigned long long *)(smem_raw + off[0]);
@@ -458,7 +494,8 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
     sm.orig = (uint32_t *)(smem_raw + off[6]);
     sm.table = (int16_t *)(smem_raw + off[7]);
     sm.segs = (Seg *)(smem_raw + off[8]);
-    sm.misc = (int *)(smem_raw + off[9]);
+    sm.bidx = (uint32_t *)(smem_raw + off[9]);
+    sm.misc = (int *)(smem_raw + off[10]);
     const int tid = threadIdx.x;
     for (int i = tid; i <= prm.n_s; i += blockDim.x) sm.T[i] = prm.T[i];
     for (int i = tid; i <= prm.n_s + 1; i += blockDim.x) sm.lohi[i] = make_float2(prm.lo[i], prm.hi[i]);
@@ -466,10 +503,12 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
     for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
     for (int i = tid; i < prm.nbin; i += blockDim.x) sm.hist[i] = 0;
 
-    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
+    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f,
+                         0u, 0u};
     cx.q = sm.queue + (size_t)cx.warp * QN * 32 * 2;
     cx.cq = cx.q + QN * 32;
     cx.bc = sm.bcopy + (size_t)cx.warp * P * 32;
+    cx.bix = sm.bidx + (size_t)cx.warp * P * 32;
     unsigned long long n_cand = 0;
 
     // per-launch mode: this block walks the chunks of one cell of one term
@@ -514,17 +553,22 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
         }
         __syncthreads();
         const int ns = sm.misc[1];
-        const uint32_t nt = (uint32_t)sm.misc[2];
-        int sg = 0;
+        const uint32_t total = (uint32_t)sm.misc[2];
+        const uint32_t self0 = (uint32_t)sm.misc[4], self1 = (uint32_t)sm.misc[5];
+        const uint32_t n_self = (self1 - self0 + TILE - 1) / TILE;
+        const uint32_t nt = n_self + (total + TILE - 1) / TILE;
         // tiles are claimed one at a time from a shared counter (its first
         // WARPS values are implicit), so warps finish a unit together
         for (uint32_t ti = cx.warp; ti < nt;) {
-            while (sg + 1 < ns && sm.segs[sg + 1].tile0 <= ti) sg++;
-            const Seg g = sm.segs[sg];
-            const uint32_t base = g.s0 + (ti - g.tile0) * TILE;
-            n_cand += (unsigned long long)min(g.s1 - base, (uint32_t)TILE) * cx.na;
-            if (g.self) cx.template tile<true>(base, g.s1, oax, g.sy, g.sz);
-            else cx.template tile<false>(base, g.s1, oax, g.sy, g.sz);
+            if (ti < n_self) {
+                const uint32_t base = self0 + ti * TILE;
+                n_cand += (unsigned long long)min(self1 - base, (uint32_t)TILE) * cx.na;
+                cx.template tile<true>(base, self1, 0u, ns, total, oax);
+            } else {
+                const uint32_t ob = (ti - n_self) * TILE;
+                n_cand += (unsigned long long)min(total - ob, (uint32_t)TILE) * cx.na;
+                cx.template tile<false>(0u, 0u, ob, ns, total, oax);
+            }
             uint32_t nx = 0;
             if (cx.lane == 0) nx = (uint32_t)atomicAdd(&sm.misc[3], 1) + WARPS;
             ti = __shfl_sync(0xffffffffu, nx, 0);
@@ -576,7 +620,7 @@ void *select_kernel(const CountParams &p)
 int paircount_smem_bytes(const CountParams &p, int warps_per_block)
 {
     (void)warps_per_block;
-    size_t off[10];
+    size_t off[11];
     return (int)smem_layout(p, off);
 }
 
