@@ -52,13 +52,12 @@ struct Smem {
     int *hist;                 // [nbin]
     uint16_t *queue;           // [WARPS][QN][32]
     uint16_t *compact;         // [WARPS][QN * 32]
-    float4 *bcopy;             // [WARPS][P][32]
+    float4 *bcopy;             // [WARPS][P][32]: b' in A's frame, .w = b index (bits)
     int16_t *table;            // [tab_n]
     float2 *lohi;              // [n_s + 2]
     uint32_t *orig;            // [n_c + 1]
     unsigned long long *T;     // [n_s + 1]
     Seg *segs;                 // [MAX_SEGS + 1], the last one a sentinel
-    uint32_t *bidx;            // [WARPS][P][32] b index of every loaded b-point
     int *misc;                 // [8]: unit, n_segs, packed points, next tile, self s0, self s1
 };
 
@@ -74,10 +73,9 @@ __host__ __device__ inline size_t smem_layout(const CountParams &p, size_t *off)
     off[4] = o; o = align16(o + sizeof(int) * p.nbin);                      // histogram
     off[5] = o; o = align16(o + sizeof(float2) * (p.n_s + 2));              // edge bands
     off[6] = o; o = align16(o + sizeof(uint32_t) * (p.n_c + 1));            // cell corners
-    off[7] = o; o = align16(o + sizeof(int16_t) * p.tab_n);                 // s table
+    off[7] = o; o = align16(o + sizeof(int16_t) * (p.linear ? 0 : p.tab_n)); // s table
     off[8] = o; o = align16(o + sizeof(Seg) * (MAX_SEGS + 1));              // segments
-    off[9] = o; o = align16(o + sizeof(uint32_t) * WARPS * P * 32);         // b indices
-    off[10] = o; o = align16(o + sizeof(int) * 8);
+    off[9] = o; o = align16(o + sizeof(int) * 8);
     return o;
 }
 
@@ -162,8 +160,7 @@ struct Ctx {
     int lane, warp;
     uint16_t *q;               // this warp's queue
     uint16_t *cq;              // this warp's compacted queue
-    float4 *bc;                // this warp's b copies
-    uint32_t *bix;             // this warp's b indices
+    float4 *bc;                // this warp's b copies (.w: b index)
     uint32_t a0, na;           // current unit's a-chunk
     float gx, gy, gz;          // 2 (corner(A) - observer), midpoint line of sight
     unsigned n_exact, n_binned;
@@ -272,7 +269,7 @@ struct Ctx {
         __syncwarp();
         for (uint32_t e = lane; e < n_amb; e += 32) {
             const uint32_t v = cq[e];
-            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + (v & 255u), bix[v >> 8]);
+            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + (v & 255u), __float_as_uint(bc[v >> 8].w));
             n_exact++;
             if (bin >= 0) {
                 atomicAdd(&sm.hist[bin], 1);
@@ -302,8 +299,7 @@ struct Ctx {
             hb[p] = __int_as_float(0x7f800000);   // +inf: never passes
             i = 0;
         }
-        bc[p * 32 + lane] = make_float4(bx[p], by[p], bz[p], 0.0f);
-        bix[p * 32 + lane] = i;
+        bc[p * 32 + lane] = make_float4(bx[p], by[p], bz[p], __uint_as_float(i));
     }
 
     // all pairs of the a-chunk with one tile of b-points: the self cell of an
@@ -482,7 +478,7 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
                                                                 int persistent, int term_pl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    size_t off[11];
+    size_t off[10];
     smem_layout(prm, off);
     Smem sm;
     sm.T = (unsigned long long *)(smem_raw + off[0]);
@@ -494,21 +490,19 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
     sm.orig = (uint32_t *)(smem_raw + off[6]);
     sm.table = (int16_t *)(smem_raw + off[7]);
     sm.segs = (Seg *)(smem_raw + off[8]);
-    sm.bidx = (uint32_t *)(smem_raw + off[9]);
-    sm.misc = (int *)(smem_raw + off[10]);
+    sm.misc = (int *)(smem_raw + off[9]);
     const int tid = threadIdx.x;
     for (int i = tid; i <= prm.n_s; i += blockDim.x) sm.T[i] = prm.T[i];
     for (int i = tid; i <= prm.n_s + 1; i += blockDim.x) sm.lohi[i] = make_float2(prm.lo[i], prm.hi[i]);
     for (int i = tid; i <= prm.n_c; i += blockDim.x) sm.orig[i] = m.orig[i];
-    for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
+    if (!LIN)
+        for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
     for (int i = tid; i < prm.nbin; i += blockDim.x) sm.hist[i] = 0;
 
-    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f,
-                         0u, 0u};
+    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
     cx.q = sm.queue + (size_t)cx.warp * QN * 32 * 2;
     cx.cq = cx.q + QN * 32;
     cx.bc = sm.bcopy + (size_t)cx.warp * P * 32;
-    cx.bix = sm.bidx + (size_t)cx.warp * P * 32;
     unsigned long long n_cand = 0;
 
     // per-launch mode: this block walks the chunks of one cell of one term
@@ -620,7 +614,7 @@ void *select_kernel(const CountParams &p)
 int paircount_smem_bytes(const CountParams &p, int warps_per_block)
 {
     (void)warps_per_block;
-    size_t off[11];
+    size_t off[10];
     return (int)smem_layout(p, off);
 }
 
