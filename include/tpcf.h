@@ -181,6 +181,35 @@ int tpcf_lc_cov(tpcf_ctx *ctx, const double *xi_a1, const double *xi_a2, const d
                 double *C_lc, double *Ca, double *Cb, double *A, double *B, void *stream);
 
 /*
+ * tpcf_lc_cov_noalloc -- tpcf_lc_cov in TPCF_FP64 that allocates nothing.
+ * (A library addition; the paper has no counterpart.)
+ *
+ * For callers that cannot allocate device memory while they run: services
+ * that reserve all of their GPU memory at start-up and treat any later
+ * cudaMalloc as a failure, and code that must not trigger the implicit device
+ * synchronisation that cudaMalloc / cudaFree can cause.  It needs no context
+ * (creating one allocates).  Inputs, outputs and their meaning are those of
+ * tpcf_lc_cov; the result equals tpcf_lc_cov(..., TPCF_FP64, ...) up to
+ * float64 rounding.
+ *
+ * Its scratch is one fixed array of 2^21 doubles (16 MiB) compiled into the
+ * library; every GPU that loads the library holds it until the process exits.
+ * Limit: 3*n_mock*nbin + 3*nbin + 3*nbin*nbin <= 2^21, else TPCF_ERR_RANGE
+ * (e.g. nbin = 400 with n_mock <= 1347).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array: calls whose GPU work overlaps (on
+ * different streams, or from different threads) race and give wrong results,
+ * so serialise them.  The array keeps the last call's contents; nothing in it
+ * needs to start at zero.  Work is enqueued on `stream` (cudaStream_t, NULL =
+ * legacy default stream) on the current CUDA device; the call returns without
+ * waiting.  Returns TPCF_OK, TPCF_ERR_ARG, TPCF_ERR_RANGE or TPCF_ERR_CUDA.
+ */
+int tpcf_lc_cov_noalloc(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
+                        int M_a, double M, double *C_lc, double *Ca, double *Cb, double *A, double *B,
+                        void *stream);
+
+/*
  * The exact integer s-bin thresholds tpcf_count uses (host only, no GPU work):
  * T[k] = ceil(s_edges[k]^2 q^2) with q = 2^32 / box_L (periodic) or
  * 2^30 / box_L (open), so that a pair with squared grid separation D2 lies

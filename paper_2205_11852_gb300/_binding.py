@@ -32,7 +32,8 @@ TPCF_BATCHED, TPCF_PER_LAUNCH = 0, 1
 TPCF_FP64, TPCF_TF32X3, TPCF_BF16X3 = 0, 1, 2
 
 EXPORTED = ("tpcf_create", "tpcf_destroy", "tpcf_sync", "tpcf_last_error", "tpcf_count", "tpcf_ls",
-            "tpcf_lc_cov", "tpcf_last_count_info", "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds")
+            "tpcf_lc_cov", "tpcf_last_count_info", "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds",
+            "tpcf_lc_cov_noalloc")
 
 
 class TpcfError(RuntimeError):
@@ -82,6 +83,8 @@ def load_library() -> ctypes.CDLL:
     lib.tpcf_set_timing.argtypes = [P, I]
     lib.tpcf_set_cell_subdiv.argtypes = [P, I]
     lib.tpcf_thresholds.argtypes = [P, ctypes.POINTER(tpcf_binning), ctypes.POINTER(ctypes.c_uint64)]
+    lib.tpcf_lc_cov_noalloc.argtypes = [P, P, P, I, I, I, D, P, P, P, P, P, P]
+    lib.tpcf_lc_cov_noalloc.restype = ctypes.c_int
     for name in ("tpcf_create", "tpcf_sync", "tpcf_count", "tpcf_ls", "tpcf_lc_cov", "tpcf_last_count_info",
                  "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds"):
         getattr(lib, name).restype = ctypes.c_int
