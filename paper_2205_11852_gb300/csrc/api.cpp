@@ -686,7 +686,7 @@ int tpcf_lc_cov(tpcf_ctx *ctx, const double *xi_a1, const double *xi_a2, const d
         void *w;
         if ((rc = ensure(ctx, "lc_split_work", bytes, &w))) return rc;
         cudaError_t e = launch_lc_split(xi_a1, xi_a2, xi_b, n_mock, nbin, precision, w, bytes, M_a, M, C_lc, Ca,
-                                        Cb, A, B, s);
+                                        Cb, A, B, ctx->status, s);
         if (e == cudaErrorNotSupported) return fail(ctx, TPCF_ERR_ARG, "split-precision covariance unavailable");
         CK(e);
         return TPCF_OK;

@@ -171,4 +171,19 @@ cudaError_t launch_lc_fp64(const double *xi_a1, const double *xi_a2, const doubl
     return cudaGetLastError();
 }
 
+cudaError_t launch_means(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
+                         double *mean, cudaStream_t s)
+{
+    mean_kernel<<<dim3(std::max(1, (nbin + 127) / 128), 3), 128, 0, s>>>(xi_a1, xi_a2, xi_b, n_mock, nbin, mean);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const double *G, int nbin, int n_mock, int M_a, double M, double *C_lc, double *Ca,
+                           double *Cb, double *A, double *B, cudaStream_t s)
+{
+    combine_kernel<<<std::max(1, blocks_for((size_t)nbin * nbin, 256)), 256, 0, s>>>(G, nbin, n_mock, M_a, M, C_lc,
+                                                                                     Ca, Cb, A, B);
+    return cudaGetLastError();
+}
+
 }  // namespace tpcf

@@ -1,17 +1,419 @@
-// Split-precision Gram products for the LC covariance on the tensor cores.
+// Split-precision Gram products of the LC covariance on the 5th-generation
+// tensor cores (tcgen05), Eqs. (bruteforce), (R1R2), (LCdef).
+//
+// The sample covariances need G_v = Y_v^T Y_v for the three centred
+// correlation-function variants v (R1, R2, R1 u R2), Y_v = xi_v - mean_v of
+// shape [n_mock][nbin].  Y is split into pieces that the tensor cores take
+// exactly:
+//   TF32X3: y = hi + lo (tf32 each), G ~ hi.hi + hi.lo + lo.hi         (3 products)
+//   BF16X3: y = h + m + l (bf16 each), G ~ hh + hm + mh + hl + lh + mm  (6 products)
+// A CTA owns one 128 x 128 output tile of one variant and one K-slice of 32
+// mocks: its operand tiles arrive by one bulk copy each (cp.async.bulk, the
+// TMA engine, completing on an mbarrier), one thread issues the tcgen05.mma
+// chain into a 128-column FP32 accumulator in tensor memory, and the warps
+// read it back with tcgen05.ld and add it into the float64 Gram with
+// atomics.  The FP32 accumulation therefore spans 32 mocks (times the split
+// products) and every slice is summed in float64.
+//
+// Operand tiles are written by the split kernel directly in the canonical
+// K-major, non-swizzled layout of the tensor-core descriptors: 8-row x
+// 16-byte core matrices, LBO = 128 bytes between core matrices along K and
+// SBO = (32 * elem / 16) * 128 bytes between 8-row groups.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
 #include "tpcf_internal.h"
 
 namespace tpcf {
+namespace {
+
+constexpr int TM = 128;          // rows (bins) per tile, M = N of the MMA
+constexpr int KS = 32;           // mocks per K-slice
+constexpr int GRAM_THREADS = 128;
+constexpr long long SPIN_LIMIT = 1ll << 26;
+
+template <int PREC>
+struct Split;
+
+template <>
+struct Split<TPCF_TF32X3> {
+    static constexpr int ELEM = 4;                           // bytes
+    static constexpr int PIECES = 2;
+    static constexpr int K_MMA = 8;                          // K per tcgen05.mma (kind::tf32)
+    static constexpr int N_PROD = 3;
+    // products hi.hi, hi.lo, lo.hi: piece of A and of B for product q
+    __host__ __device__ static constexpr int pa(int q) { return q == 2 ? 1 : 0; }
+    __host__ __device__ static constexpr int pb(int q) { return q == 1 ? 1 : 0; }
+    static constexpr uint32_t FMT = 2;                       // TF32 operand format
+};
+template <>
+struct Split<TPCF_BF16X3> {
+    static constexpr int ELEM = 2;
+    static constexpr int PIECES = 3;
+    static constexpr int K_MMA = 16;                         // kind::f16
+    static constexpr int N_PROD = 6;
+    // products hh, hm, mh, hl, lh, mm
+    __host__ __device__ static constexpr int pa(int q) { return q == 2 ? 1 : (q == 4 ? 2 : (q == 5 ? 1 : 0)); }
+    __host__ __device__ static constexpr int pb(int q) { return q == 1 ? 1 : (q == 3 ? 2 : (q == 5 ? 1 : 0)); }
+    static constexpr uint32_t FMT = 1;                       // BF16 operand format
+};
+
+template <int PREC>
+__host__ __device__ constexpr int tile_bytes() { return TM * KS * Split<PREC>::ELEM; }
+
+template <int PREC>
+__host__ __device__ constexpr int sbo_bytes() { return (KS * Split<PREC>::ELEM / 16) * 128; }
+
+// byte offset of element (row r, k) inside a K-major non-swizzled tile
+template <int PREC>
+__device__ __forceinline__ uint32_t tile_offset(int r, int k)
+{
+    constexpr int per = 16 / Split<PREC>::ELEM;              // elements per core-matrix row
+    return (uint32_t)((r >> 3) * sbo_bytes<PREC>() + (k / per) * 128 + (r & 7) * 16 + (k % per) * Split<PREC>::ELEM);
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x)
+{
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return y;
+}
+
+// centred residuals, split into pieces, written as operand tiles
+// tiles[v][piece][rb][ks]
+template <int PREC>
+__global__ void split_kernel(const double *__restrict__ x0, const double *__restrict__ x1,
+                             const double *__restrict__ x2, const double *__restrict__ mean, int n_mock, int nbin,
+                             int n_rb, int n_ks, unsigned char *__restrict__ tiles)
+{
+    const int v = blockIdx.z;
+    const double *x = v == 0 ? x0 : (v == 1 ? x1 : x2);
+    const int rb = blockIdx.y, ks = blockIdx.x;
+    constexpr int TB = tile_bytes<PREC>();
+    constexpr int NP = Split<PREC>::PIECES;
+    for (int e = threadIdx.x; e < TM * KS; e += blockDim.x) {
+        const int r = e % TM, k = e / TM;
+        const int i = rb * TM + r, m = ks * KS + k;
+        const double y = (i < nbin && m < n_mock) ? x[(size_t)m * nbin + i] - mean[(size_t)v * nbin + i] : 0.0;
+        const uint32_t off = tile_offset<PREC>(r, k);
+        if (PREC == TPCF_TF32X3) {
+            const uint32_t hi = tf32_rna((float)y);
+            const uint32_t lo = tf32_rna((float)(y - (double)__uint_as_float(hi)));
+            unsigned char *t0 = tiles + ((((size_t)v * NP + 0) * n_rb + rb) * n_ks + ks) * TB;
+            unsigned char *t1 = tiles + ((((size_t)v * NP + 1) * n_rb + rb) * n_ks + ks) * TB;
+            *(uint32_t *)(t0 + off) = hi;
+            *(uint32_t *)(t1 + off) = lo;
+        } else {
+            const __nv_bfloat16 h = __double2bfloat16(y);
+            const double r1 = y - (double)__bfloat162float(h);
+            const __nv_bfloat16 mm = __double2bfloat16(r1);
+            const double r2 = r1 - (double)__bfloat162float(mm);
+            const __nv_bfloat16 l = __double2bfloat16(r2);
+            unsigned char *t0 = tiles + ((((size_t)v * NP + 0) * n_rb + rb) * n_ks + ks) * TB;
+            unsigned char *t1 = tiles + ((((size_t)v * NP + 1) * n_rb + rb) * n_ks + ks) * TB;
+            unsigned char *t2 = tiles + ((((size_t)v * NP + 2) * n_rb + rb) * n_ks + ks) * TB;
+            *(__nv_bfloat16 *)(t0 + off) = h;
+            *(__nv_bfloat16 *)(t1 + off) = mm;
+            *(__nv_bfloat16 *)(t2 + off) = l;
+        }
+    }
+}
+
+// ---- inline PTX: mbarrier, bulk copy, tcgen05 ----
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false if the barrier did not complete within the limit
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit)
+{
+    for (long long i = 0; i < limit; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// non-swizzled K-major shared-memory matrix descriptor
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
+    return d;                 // base offset 0, no swizzle
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    if (PREC == TPCF_TF32X3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// instruction descriptor: FP32 accumulate, K-major A and B, M = N = 128
+template <int PREC>
+__host__ __device__ constexpr uint32_t instr_desc()
+{
+    return (1u << 4)                          // D format: F32
+           | (Split<PREC>::FMT << 7)          // A format
+           | (Split<PREC>::FMT << 10)         // B format
+           | ((uint32_t)(TM >> 3) << 17)      // N / 8
+           | ((uint32_t)(TM >> 4) << 24);     // M / 16
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned char *__restrict__ tiles, int nbin,
+                                                              int n_rb, int n_ks, const int2 *__restrict__ pairs,
+                                                              double *__restrict__ G, int *__restrict__ status)
+{
+    constexpr int TB = tile_bytes<PREC>();
+    constexpr int NP = Split<PREC>::PIECES;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *sA = smem;                       // NP tiles of row block bi
+    unsigned char *sB = smem + NP * TB;             // NP tiles of row block bj
+    uint64_t *bar = (uint64_t *)(smem + 2 * NP * TB);
+    uint32_t *slot = (uint32_t *)(bar + 2);
+    int *flag = (int *)(slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int2 pr = pairs[blockIdx.x];
+    const int bi = pr.x, bj = pr.y;
+    const int v = blockIdx.y, ks = blockIdx.z;
+
+    if (warp == 0) tmem_alloc(slot, TM);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+        *flag = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+
+    if (tid == 0) {
+        mbar_expect_tx(&bar[0], (uint32_t)(2 * NP * TB));
+        for (int p = 0; p < NP; p++) {
+            const unsigned char *ga = tiles + ((((size_t)v * NP + p) * n_rb + bi) * n_ks + ks) * TB;
+            const unsigned char *gb = tiles + ((((size_t)v * NP + p) * n_rb + bj) * n_ks + ks) * TB;
+            bulk_g2s(sA + p * TB, ga, TB, &bar[0]);
+            bulk_g2s(sB + p * TB, gb, TB, &bar[0]);
+        }
+        bool ok = mbar_wait(&bar[0], 0, SPIN_LIMIT);
+        if (!ok) ok = mbar_wait(&bar[0], 0, SPIN_LIMIT);   // give copies in flight one more bounded wait
+        if (ok) {
+            tc_fence_after();
+            constexpr uint32_t idesc = instr_desc<PREC>();
+            constexpr int steps = KS / Split<PREC>::K_MMA;
+            uint32_t acc = 0;
+#pragma unroll
+            for (int q = 0; q < Split<PREC>::N_PROD; q++) {
+                const uint32_t a0 = smem_addr(sA + Split<PREC>::pa(q) * TB);
+                const uint32_t b0 = smem_addr(sB + Split<PREC>::pb(q) * TB);
+#pragma unroll
+                for (int s = 0; s < steps; s++) {
+                    // each MMA step covers two core matrices along K (2 x 128 bytes)
+                    const uint64_t da = smem_desc(a0 + s * 256, 128, sbo_bytes<PREC>());
+                    const uint64_t db = smem_desc(b0 + s * 256, 128, sbo_bytes<PREC>());
+                    mma<PREC>(tmem, da, db, idesc, acc);
+                    acc = 1;
+                }
+            }
+            mma_commit(&bar[1]);
+        } else {
+            *flag = 0;
+        }
+    }
+    __syncthreads();
+    if (*flag) {
+        bool done = mbar_wait(&bar[1], 0, SPIN_LIMIT);
+        if (!done) done = mbar_wait(&bar[1], 0, SPIN_LIMIT);
+        if (done) {
+            tc_fence_after();
+            // warp w reads accumulator rows 32w..32w+31 (its tensor-memory lanes)
+            const int row = bi * TM + warp * 32 + lane;
+            double *g = G + (size_t)v * nbin * nbin;
+#pragma unroll 1
+            for (int c0 = 0; c0 < TM; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+                if (row < nbin) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int col = bj * TM + c0 + j;
+                        if (col < nbin) {
+                            const double val = (double)__uint_as_float(r[j]);
+                            atomicAdd(&g[(size_t)row * nbin + col], val);
+                            if (bi != bj) atomicAdd(&g[(size_t)col * nbin + row], val);
+                        }
+                    }
+                }
+            }
+        } else if (tid == 0) {
+            atomicOr(status, STATUS_TIMEOUT);
+        }
+    } else if (tid == 0) {
+        atomicOr(status, STATUS_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TM);
+}
+
+template <int PREC>
+size_t tiles_bytes(int n_mock, int nbin)
+{
+    const size_t n_rb = (nbin + TM - 1) / TM, n_ks = (n_mock + KS - 1) / KS;
+    return 3 * (size_t)Split<PREC>::PIECES * n_rb * n_ks * tile_bytes<PREC>();
+}
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <int PREC>
+cudaError_t run(const double *x0, const double *x1, const double *x2, int n_mock, int nbin, void *work,
+                size_t work_bytes, int M_a, double M, double *C_lc, double *Ca, double *Cb, double *A, double *B,
+                int *status, cudaStream_t s)
+{
+    const int n_rb = (nbin + TM - 1) / TM, n_ks = (n_mock + KS - 1) / KS;
+    if (n_ks > 65535 || n_rb > 90) return cudaErrorInvalidValue;
+    unsigned char *w = (unsigned char *)work;
+    unsigned char *tiles = w;
+    size_t o = al256(tiles_bytes<PREC>(n_mock, nbin));
+    double *G = (double *)(w + o);
+    o += al256(3 * (size_t)nbin * nbin * 8);
+    double *mean = (double *)(w + o);
+    o += al256(3 * (size_t)nbin * 8);
+    int2 *pairs = (int2 *)(w + o);
+    o += al256((size_t)n_rb * (n_rb + 1) / 2 * sizeof(int2));
+    if (o > work_bytes) return cudaErrorInvalidValue;
+    cudaError_t e = launch_means(x0, x1, x2, n_mock, nbin, mean, s);
+    if (e != cudaSuccess) return e;
+    split_kernel<PREC><<<dim3(n_ks, n_rb, 3), 256, 0, s>>>(x0, x1, x2, mean, n_mock, nbin, n_rb, n_ks, tiles);
+    // upper-triangle tile pairs (bi <= bj)
+    static thread_local int2 host_pairs[4096];
+    int np = 0;
+    for (int i = 0; i < n_rb; i++)
+        for (int j = i; j < n_rb && np < 4096; j++) host_pairs[np++] = make_int2(i, j);
+    if (np != n_rb * (n_rb + 1) / 2) return cudaErrorInvalidValue;
+    e = cudaMemcpyAsync(pairs, host_pairs, np * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(G, 0, 3 * (size_t)nbin * nbin * 8, s);
+    if (e != cudaSuccess) return e;
+    const int smem = 2 * Split<PREC>::PIECES * tile_bytes<PREC>() + 64;
+    e = cudaFuncSetAttribute(gram_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    gram_tc_kernel<PREC><<<dim3(np, 3, n_ks), GRAM_THREADS, smem, s>>>(tiles, nbin, n_rb, n_ks, pairs, G, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_combine(G, nbin, n_mock, M_a, M, C_lc, Ca, Cb, A, B, s);
+}
+
+}  // namespace
 
 size_t lc_split_work_bytes(int n_mock, int nbin, int precision)
 {
-    (void)precision;
-    return 256 + 3 * (size_t)n_mock * nbin * 8 + 3 * (size_t)nbin * 8 + 3 * (size_t)nbin * nbin * 8;
+    const size_t n_rb = (nbin + TM - 1) / TM;
+    const size_t t = precision == TPCF_BF16X3 ? tiles_bytes<TPCF_BF16X3>(n_mock, nbin)
+                                              : tiles_bytes<TPCF_TF32X3>(n_mock, nbin);
+    return al256(t) + al256(3 * (size_t)nbin * nbin * 8) + al256(3 * (size_t)nbin * 8) +
+           al256(n_rb * (n_rb + 1) / 2 * sizeof(int2));
 }
 
-cudaError_t launch_lc_split(const double *, const double *, const double *, int, int, int, void *, size_t, int,
-                            double, double *, double *, double *, double *, double *, cudaStream_t)
+cudaError_t launch_lc_split(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
+                            int precision, void *work, size_t work_bytes, int M_a, double M, double *C_lc,
+                            double *Ca, double *Cb, double *A, double *B, int *status, cudaStream_t s)
 {
+    if (precision == TPCF_TF32X3)
+        return run<TPCF_TF32X3>(xi_a1, xi_a2, xi_b, n_mock, nbin, work, work_bytes, M_a, M, C_lc, Ca, Cb, A, B,
+                                status, s);
+    if (precision == TPCF_BF16X3)
+        return run<TPCF_BF16X3>(xi_a1, xi_a2, xi_b, n_mock, nbin, work, work_bytes, M_a, M, C_lc, Ca, Cb, A, B,
+                                status, s);
     return cudaErrorNotSupported;
 }
 

@@ -131,7 +131,13 @@ cudaError_t launch_lc_fp64(const double *xi_a1, const double *xi_a2, const doubl
                            cudaStream_t s);
 cudaError_t launch_lc_split(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock,
                             int nbin, int precision, void *work, size_t work_bytes, int M_a, double M,
-                            double *C_lc, double *Ca, double *Cb, double *A, double *B, cudaStream_t s);
+                            double *C_lc, double *Ca, double *Cb, double *A, double *B, int *status, cudaStream_t s);
 size_t lc_split_work_bytes(int n_mock, int nbin, int precision);
+// column means mean[3][nbin] of the three xi variants
+cudaError_t launch_means(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
+                         double *mean, cudaStream_t s);
+// LC combination from the three Gram blocks G[3][nbin][nbin] (float64)
+cudaError_t launch_combine(const double *G, int nbin, int n_mock, int M_a, double M, double *C_lc, double *Ca,
+                           double *Cb, double *A, double *B, cudaStream_t s);
 
 }  // namespace tpcf
