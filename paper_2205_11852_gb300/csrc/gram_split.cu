@@ -7,13 +7,15 @@
 // exactly:
 //   TF32X3: y = hi + lo (tf32 each), G ~ hi.hi + hi.lo + lo.hi         (3 products)
 //   BF16X3: y = h + m + l (bf16 each), G ~ hh + hm + mh + hl + lh + mm  (6 products)
-// A CTA owns one 128 x 128 output tile of one variant and one K-slice of 32
+// A CTA owns one 128 x 128 output tile of one variant and one K-slice of 16
 // mocks: its operand tiles arrive by one bulk copy each (cp.async.bulk, the
 // TMA engine, completing on an mbarrier), one thread issues the tcgen05.mma
-// chain into a 128-column FP32 accumulator in tensor memory, and the warps
-// read it back with tcgen05.ld and add it into the float64 Gram with
-// atomics.  The FP32 accumulation therefore spans 32 mocks (times the split
-// products) and every slice is summed in float64.
+// chain into FP32 accumulators in tensor memory, and the warps read them back
+// with tcgen05.ld and add them into the float64 Gram with atomics.  The
+// leading product (hi.hi) and the much smaller correction products go to two
+// separate accumulators, so the FP32 rounding of the leading sum spans only
+// 16 exact products and the corrections do not round against it; every slice
+// is summed in float64.
 //
 // Operand tiles are written by the split kernel directly in the canonical
 // K-major, non-swizzled layout of the tensor-core descriptors: 8-row x
@@ -21,6 +23,7 @@
 // SBO = (32 * elem / 16) * 128 bytes between 8-row groups.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "tpcf_internal.h"
@@ -29,7 +32,9 @@ namespace tpcf {
 namespace {
 
 constexpr int TM = 128;          // rows (bins) per tile, M = N of the MMA
-constexpr int KS = 32;           // mocks per K-slice
+constexpr int KS = 16;           // mocks per K-slice
+constexpr int TMEM_COLS = 2 * TM; // two FP32 accumulators: leading product, corrections
+constexpr int GRAM_SMEM_MIN = 100 * 1024;   // at most two CTAs per SM: their tensor memory fits
 constexpr int GRAM_THREADS = 128;
 constexpr long long SPIN_LIMIT = 1ll << 26;
 
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
     const int bi = pr.x, bj = pr.y;
     const int v = blockIdx.y, ks = blockIdx.z;
 
-    if (warp == 0) tmem_alloc(slot, TM);
+    if (warp == 0) tmem_alloc(slot, TMEM_COLS);
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -290,18 +295,18 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
             tc_fence_after();
             constexpr uint32_t idesc = instr_desc<PREC>();
             constexpr int steps = KS / Split<PREC>::K_MMA;
-            uint32_t acc = 0;
 #pragma unroll
             for (int q = 0; q < Split<PREC>::N_PROD; q++) {
                 const uint32_t a0 = smem_addr(sA + Split<PREC>::pa(q) * TB);
                 const uint32_t b0 = smem_addr(sB + Split<PREC>::pb(q) * TB);
 #pragma unroll
                 for (int s = 0; s < steps; s++) {
-                    // each MMA step covers two core matrices along K (2 x 128 bytes)
+                    // each MMA step covers two core matrices along K (2 x 128 bytes);
+                    // product 0 accumulates in columns [0, 128), the others in [128, 256)
                     const uint64_t da = smem_desc(a0 + s * 256, 128, sbo_bytes<PREC>());
                     const uint64_t db = smem_desc(b0 + s * 256, 128, sbo_bytes<PREC>());
-                    mma<PREC>(tmem, da, db, idesc, acc);
-                    acc = 1;
+                    const uint32_t d = tmem + (q == 0 ? 0u : (uint32_t)TM);
+                    mma<PREC>(d, da, db, idesc, (q == 0 || q == 1) ? (s > 0 ? 1u : 0u) : 1u);
                 }
             }
             mma_commit(&bar[1]);
@@ -320,14 +325,15 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
             double *g = G + (size_t)v * nbin * nbin;
 #pragma unroll 1
             for (int c0 = 0; c0 < TM; c0 += 32) {
-                uint32_t r[32];
+                uint32_t r[32], rc[32];
                 tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(TM + c0), rc);
                 if (row < nbin) {
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
                         const int col = bj * TM + c0 + j;
                         if (col < nbin) {
-                            const double val = (double)__uint_as_float(r[j]);
+                            const double val = (double)__uint_as_float(r[j]) + (double)__uint_as_float(rc[j]);
                             atomicAdd(&g[(size_t)row * nbin + col], val);
                             if (bi != bj) atomicAdd(&g[(size_t)col * nbin + row], val);
                         }
@@ -342,7 +348,7 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TM);
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
 template <int PREC>
@@ -384,7 +390,7 @@ cudaError_t run(const double *x0, const double *x1, const double *x2, int n_mock
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(G, 0, 3 * (size_t)nbin * nbin * 8, s);
     if (e != cudaSuccess) return e;
-    const int smem = 2 * Split<PREC>::PIECES * tile_bytes<PREC>() + 64;
+    const int smem = std::max(2 * Split<PREC>::PIECES * tile_bytes<PREC>() + 64, GRAM_SMEM_MIN);
     e = cudaFuncSetAttribute(gram_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     gram_tc_kernel<PREC><<<dim3(np, 3, n_ks), GRAM_THREADS, smem, s>>>(tiles, nbin, n_rb, n_ks, pairs, G, status);

@@ -338,3 +338,24 @@ def test_full_size_mid_mock_bit_exact(tp, ctx):
     ctx.tpcf_sync()
     for k in ("dd", "dr", "rr"):
         assert torch.equal(out[k], out2[k])
+
+
+# ---------------------------------------------------------------------------
+# split-precision covariance on the tensor cores
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec_name", ["TPCF_TF32X3", "TPCF_BF16X3"])
+@pytest.mark.parametrize("n_mock,nbin", [(2, 5), (64, 37), (301, 200), (3500, 200), (130, 400)])
+def test_lc_split_precision_within_1e6(tp, ctx, prec_name, n_mock, nbin):
+    """Gram products in TF32x3 / BF16x3 with FP32 accumulation: every covariance element
+    within 1e-6 of the float64 oracle, normalised by sqrt(C^a_ii C^a_jj)."""
+    xa1, xa2, xb = synth.synthetic_xi_variants(43, n_mock, nbin)
+    g = [torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in (xa1, xa2, xb)]
+    out = ctx.tpcf_lc_cov(*g, 1, 50.0, getattr(tp, prec_name))
+    assert ctx.tpcf_sync() == tp.TPCF_OK
+    ref = oracle.lc_cov(xa1, xa2, xb, 1, 50.0)
+    d = np.sqrt(np.diag(ref["Ca"]))
+    scale = np.outer(d, d)
+    for k in ("C_lc", "Ca", "Cb", "A", "B"):
+        err = np.max(np.abs(out[k].cpu().numpy() - ref[k]) / scale)
+        assert err <= 1e-6, (k, err)
