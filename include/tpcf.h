@@ -241,6 +241,8 @@ typedef struct {
     int     cells_per_axis;
     int     n_kernels;        /* kernels launched by the last tpcf_count */
     int     timed_calls;      /* tpcf_count calls accumulated in paircount_ms */
+    int     unit_chunk;       /* a-points per work unit, chosen by the autotuner */
+    int     graph_replay;     /* 1: the batched launch was a replay of a captured CUDA graph */
 } tpcf_count_info;
 
 int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info);
@@ -256,6 +258,23 @@ int tpcf_set_timing(tpcf_ctx *ctx, int enable);
  * or 0 to let the autotuner choose.  For tests and benchmarks.
  */
 int tpcf_set_cell_subdiv(tpcf_ctx *ctx, int subdiv);
+
+/*
+ * Options of the batched pair count (both on by default):
+ *   TPCF_OPT_GRAPHS   -- capture the batched tpcf_count (mesh build, work list
+ *                        and the persistent pair-count launch) as a CUDA graph
+ *                        on first use and replay it while the plan, buffers and
+ *                        outputs of the call stay the same.  The first call of
+ *                        a new shape must not itself be under stream capture.
+ *   TPCF_OPT_AUTOTUNE -- on the first batched call of a new workload shape,
+ *                        time candidate mesh subdivisions and work-unit sizes on
+ *                        a few of the mocks and keep the fastest (cached per
+ *                        context).  A pinned subdivision disables it.
+ * Returns TPCF_OK or TPCF_ERR_ARG.
+ */
+#define TPCF_OPT_GRAPHS    1
+#define TPCF_OPT_AUTOTUNE  2
+int tpcf_set_option(tpcf_ctx *ctx, int option, int value);
 
 #ifdef __cplusplus
 }

@@ -30,10 +30,11 @@ TPCF_LOS_X, TPCF_LOS_MIDPOINT = 0, 1
 TPCF_DD, TPCF_DR, TPCF_RR = 1, 2, 4
 TPCF_BATCHED, TPCF_PER_LAUNCH = 0, 1
 TPCF_FP64, TPCF_TF32X3, TPCF_BF16X3 = 0, 1, 2
+TPCF_OPT_GRAPHS, TPCF_OPT_AUTOTUNE = 1, 2
 
 EXPORTED = ("tpcf_create", "tpcf_destroy", "tpcf_sync", "tpcf_last_error", "tpcf_count", "tpcf_ls",
             "tpcf_lc_cov", "tpcf_last_count_info", "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds",
-            "tpcf_lc_cov_noalloc")
+            "tpcf_lc_cov_noalloc", "tpcf_set_option")
 
 
 class TpcfError(RuntimeError):
@@ -58,7 +59,8 @@ class tpcf_count_info(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int64), ("n_binned", ctypes.c_int64), ("n_exact", ctypes.c_int64),
                 ("n_units", ctypes.c_int64), ("paircount_ms", ctypes.c_double),
                 ("n_paircount_launches", ctypes.c_int), ("cell_subdiv", ctypes.c_int),
-                ("cells_per_axis", ctypes.c_int), ("n_kernels", ctypes.c_int), ("timed_calls", ctypes.c_int)]
+                ("cells_per_axis", ctypes.c_int), ("n_kernels", ctypes.c_int), ("timed_calls", ctypes.c_int),
+                ("unit_chunk", ctypes.c_int), ("graph_replay", ctypes.c_int)]
 
 
 def load_library() -> ctypes.CDLL:
@@ -85,6 +87,8 @@ def load_library() -> ctypes.CDLL:
     lib.tpcf_thresholds.argtypes = [P, ctypes.POINTER(tpcf_binning), ctypes.POINTER(ctypes.c_uint64)]
     lib.tpcf_lc_cov_noalloc.argtypes = [P, P, P, I, I, I, D, P, P, P, P, P, P]
     lib.tpcf_lc_cov_noalloc.restype = ctypes.c_int
+    lib.tpcf_set_option.argtypes = [P, I, I]
+    lib.tpcf_set_option.restype = ctypes.c_int
     for name in ("tpcf_create", "tpcf_sync", "tpcf_count", "tpcf_ls", "tpcf_lc_cov", "tpcf_last_count_info",
                  "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds"):
         getattr(lib, name).restype = ctypes.c_int
@@ -169,6 +173,9 @@ class Context:
 
     def tpcf_set_cell_subdiv(self, subdiv: int):
         self._check(self._lib.tpcf_set_cell_subdiv(self.handle, int(subdiv)))
+
+    def tpcf_set_option(self, option: int, value: int):
+        self._check(self._lib.tpcf_set_option(self.handle, int(option), int(value)))
 
     def tpcf_last_count_info(self) -> dict:
         info = tpcf_count_info()

@@ -1,0 +1,567 @@
+// tpcf_count: binned pair counts of many mocks (Sect. 2.1 DD, DR_i, RR_i;
+// Sect. 4.3 (s, mu) bins) -- host orchestration.
+//
+//   prepare()  validates the call and builds, on the host, the plan (exact
+//              thresholds, FP32 bands, mesh), the catalogue and term tables
+//              and the workspace layout;
+//   enqueue()  puts the whole GPU sequence on a stream: quantisation and
+//              cell keys, counting sort by cell, work-unit list, and the pair
+//              count (one persistent launch, or one launch per term);
+//   the batched path captures enqueue() once as a CUDA graph per call shape
+//              and replays it; an autotuner picks the mesh subdivision and
+//              the work-unit size of a new shape by timing candidates on a
+//              few of its mocks.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace tpcf;
+using namespace tpcf::detail;
+
+namespace {
+
+struct RqCopy {
+    uint32_t *dst;
+    const uint32_t *src;
+    size_t n, pitch;
+};
+
+struct Setup {
+    Plan pl;
+    std::vector<Cat> cats;
+    std::vector<Term> terms;
+    std::vector<RqCopy> rq;
+    int M = 0;
+    unsigned mask = 0;
+    size_t NT = 0, ncc = 0, ntc = 0, tmp_n = 0;
+    uint32_t max_n = 0;
+    unsigned long long units_bound = 0;
+    int chunk = UNIT_CHUNK;
+    int smem = 0, blocks = 0;
+    double L = 0, origin[3] = {0, 0, 0};
+    // outputs to clear
+    int64_t *dd = nullptr, *dr = nullptr, *rr = nullptr;
+    size_t n_dd = 0, n_drr = 0;
+    // workspace
+    void *uq = nullptr, *keys = nullptr, *us = nullptr, *pf = nullptr, *pcx = nullptr, *cc = nullptr,
+         *cs = nullptr, *tmp = nullptr, *uc = nullptr, *ust = nullptr, *units = nullptr, *claim = nullptr,
+         *rqbuf = nullptr;
+    // small tables (host bytes and layout)
+    std::vector<unsigned char> small;
+    size_t o_cats = 0, o_terms = 0, o_orig = 0, o_tab = 0;
+};
+
+// Validate and build everything host-side for one call; allocates workspace.
+int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *binning, unsigned terms,
+            int64_t *dd, int64_t *dr, int64_t *rr, int mode, int subdiv, int chunk, Setup &S)
+{
+    int rc;
+    if ((rc = validate_binning(ctx, binning))) return rc;
+    if (n_mock < 0 || (n_mock > 0 && !mocks)) return fail(ctx, TPCF_ERR_ARG, "mocks is NULL");
+    if (terms == 0 || (terms & ~7u)) return fail(ctx, TPCF_ERR_ARG, "terms must be a non-empty mask of DD|DR|RR");
+    if (mode != TPCF_BATCHED && mode != TPCF_PER_LAUNCH) return fail(ctx, TPCF_ERR_ARG, "bad mode");
+    if ((terms & TPCF_DD) && !dd) return fail(ctx, TPCF_ERR_ARG, "dd output is NULL");
+    if ((terms & TPCF_DR) && !dr) return fail(ctx, TPCF_ERR_ARG, "dr output is NULL");
+    if ((terms & TPCF_RR) && !rr) return fail(ctx, TPCF_ERR_ARG, "rr output is NULL");
+    const bool need_d = terms & (TPCF_DD | TPCF_DR);
+    const bool need_r = terms & (TPCF_DR | TPCF_RR);
+    int M = -1;
+    unsigned long long n_total = 0, max_cat = 0, n_cat_est = 0, n_terms_est = 0;
+    for (int m = 0; m < n_mock; m++) {
+        const tpcf_mock &mk = mocks[m];
+        if (need_d) {
+            if (mk.n_d < 0) return fail(ctx, TPCF_ERR_ARG, "n_d < 0");
+            if (mk.n_d > 0 && !mk.data_xyz == !mk.data_u32)
+                return fail(ctx, TPCF_ERR_ARG, "give exactly one of data_xyz / data_u32");
+            n_total += (unsigned long long)mk.n_d;
+            max_cat = std::max<unsigned long long>(max_cat, mk.n_d);
+            n_cat_est++;
+        }
+        if (need_r) {
+            if (mk.M < 1) return fail(ctx, TPCF_ERR_ARG, "M must be >= 1");
+            if (M >= 0 && mk.M != M) return fail(ctx, TPCF_ERR_ARG, "all mocks need the same M");
+            M = mk.M;
+            if (!mk.rand_offsets) return fail(ctx, TPCF_ERR_ARG, "rand_offsets is NULL");
+            if (mk.rand_offsets[0] != 0) return fail(ctx, TPCF_ERR_ARG, "rand_offsets[0] must be 0");
+            for (int i = 0; i < mk.M; i++) {
+                if (mk.rand_offsets[i + 1] < mk.rand_offsets[i])
+                    return fail(ctx, TPCF_ERR_ARG, "rand_offsets must be non-decreasing");
+                max_cat = std::max<unsigned long long>(max_cat, mk.rand_offsets[i + 1] - mk.rand_offsets[i]);
+                n_cat_est++;
+            }
+            const int64_t nr = mk.rand_offsets[mk.M];
+            if (nr > 0 && !mk.rand_xyz == !mk.rand_u32)
+                return fail(ctx, TPCF_ERR_ARG, "give exactly one of rand_xyz / rand_u32");
+            n_total += (unsigned long long)nr;
+        }
+    }
+    if (n_total >= (1ull << 31)) return fail(ctx, TPCF_ERR_RANGE, "more than 2^31 points in one call");
+    if (M < 0) M = 0;
+    S.M = M;
+    S.mask = terms;
+    for (int m = 0; m < n_mock; m++)
+        n_terms_est += ((terms & TPCF_DD) ? 1 : 0) +
+                       (unsigned long long)M * (((terms & TPCF_DR) ? 1 : 0) + ((terms & TPCF_RR) ? 1 : 0));
+
+    // mesh cap: a few cells per point of the largest catalogue, and the
+    // (catalogue x cell) and (term x cell) tables indexable in 32 bits
+    unsigned long long max_cells = std::max<unsigned long long>(64, 4 * max_cat);
+    max_cells = std::min<unsigned long long>(max_cells, 1ull << 24);
+    const unsigned long long tabs = std::max<unsigned long long>(1, std::max(n_cat_est, n_terms_est));
+    max_cells = std::min<unsigned long long>(max_cells, ((1ull << 32) - 2) / tabs);
+
+    std::string perr;
+    if ((rc = build_plan(*binning, subdiv, max_cells, S.pl, perr))) return fail(ctx, rc, perr);
+    if ((rc = check_mu_width(ctx, binning, S.pl.prm))) return rc;
+    const CountParams &prm = S.pl.prm;
+    S.chunk = std::max(32, std::min(chunk, UNIT_CHUNK));
+    S.L = binning->box_L;
+    for (int c = 0; c < 3; c++) S.origin[c] = binning->origin[c];
+
+    // catalogues and terms
+    uint32_t p0 = 0;
+    std::vector<int> rand_cat0(n_mock, -1);
+    for (int m = 0; m < n_mock; m++) {
+        const tpcf_mock &mk = mocks[m];
+        const int cd = (int)S.cats.size();
+        if (need_d) {
+            Cat c;
+            c.xyz = mk.data_xyz;
+            c.u32 = mk.data_xyz ? nullptr : mk.data_u32;
+            c.p0 = p0;
+            c.n = (uint32_t)mk.n_d;
+            p0 += c.n;
+            S.max_n = std::max(S.max_n, c.n);
+            S.cats.push_back(c);
+        }
+        const int cr = (int)S.cats.size();
+        rand_cat0[m] = cr;
+        if (need_r) {
+            for (int i = 0; i < M; i++) {
+                Cat c;
+                const int64_t o0 = mk.rand_offsets[i], o1 = mk.rand_offsets[i + 1];
+                c.xyz = mk.rand_xyz ? mk.rand_xyz + 3 * o0 : nullptr;
+                c.u32 = nullptr;   // pre-quantised subsets are gathered below
+                c.p0 = p0;
+                c.n = (uint32_t)(o1 - o0);
+                p0 += c.n;
+                S.max_n = std::max(S.max_n, c.n);
+                S.cats.push_back(c);
+            }
+        }
+        const int nbin = prm.nbin;
+        if (terms & TPCF_DD) S.terms.push_back(Term{cd, cd, 1, 0, (long long *)dd + (size_t)m * nbin});
+        for (int i = 0; i < M; i++) {
+            if (terms & TPCF_DR)
+                S.terms.push_back(Term{cd, cr + i, 0, 0, (long long *)dr + ((size_t)m * M + i) * nbin});
+            if (terms & TPCF_RR)
+                S.terms.push_back(Term{cr + i, cr + i, 1, 0, (long long *)rr + ((size_t)m * M + i) * nbin});
+        }
+    }
+    S.dd = (terms & TPCF_DD) ? dd : nullptr;
+    S.dr = (terms & TPCF_DR) ? dr : nullptr;
+    S.rr = (terms & TPCF_RR) ? rr : nullptr;
+    S.n_dd = (size_t)n_mock * prm.nbin;
+    S.n_drr = (size_t)n_mock * M * prm.nbin;
+    S.NT = (size_t)n_total;
+    if (S.NT == 0 || S.terms.empty()) return TPCF_OK;
+
+    S.ncc = S.cats.size() * (size_t)prm.n_cells + 1;
+    if (S.ncc >= (1ull << 32)) return fail(ctx, TPCF_ERR_RANGE, "too many catalogues x cells");
+    S.ntc = S.terms.size() * (size_t)prm.n_cells + 1;
+    if (S.ntc >= (1ull << 32)) return fail(ctx, TPCF_ERR_RANGE, "too many terms x cells");
+    for (const Term &t : S.terms) {
+        const unsigned long long n = S.cats[t.cat_a].n;
+        S.units_bound += n / S.chunk + std::min<unsigned long long>(n, prm.n_cells) + 1;
+    }
+    S.tmp_n = std::max(scan_tmp_elems(S.ncc), scan_tmp_elems(S.ntc));
+
+    // workspace
+    const size_t NT = S.NT;
+    if ((rc = ensure(ctx, "uq", 3 * NT * 4, &S.uq))) return rc;
+    if ((rc = ensure(ctx, "keys", NT * 4, &S.keys))) return rc;
+    if ((rc = ensure(ctx, "us", 3 * NT * 4, &S.us))) return rc;
+    if ((rc = ensure(ctx, "pf", NT * 16, &S.pf))) return rc;
+    if ((rc = ensure(ctx, "pcx", NT * 2, &S.pcx))) return rc;
+    if ((rc = ensure(ctx, "cellcount", S.ncc * 4, &S.cc))) return rc;
+    if ((rc = ensure(ctx, "cellstart", S.ncc * 4, &S.cs))) return rc;
+    if ((rc = ensure(ctx, "scantmp", S.tmp_n * 4, &S.tmp))) return rc;
+    if ((rc = ensure(ctx, "ucount", S.ntc * 4, &S.uc))) return rc;
+    if ((rc = ensure(ctx, "ustart", S.ntc * 4, &S.ust))) return rc;
+    if ((rc = ensure(ctx, "units", S.units_bound * sizeof(Unit), &S.units))) return rc;
+    if ((rc = ensure(ctx, "claim", 256, &S.claim))) return rc;
+
+    // pre-quantised randoms: one [3][n_r] array per mock, gathered into a
+    // compact [3][n] block per subset
+    size_t rq_elems = 0;
+    if (need_r)
+        for (int m = 0; m < n_mock; m++)
+            if (!mocks[m].rand_xyz && mocks[m].rand_offsets[M] > 0) rq_elems += 3 * (size_t)mocks[m].rand_offsets[M];
+    if (rq_elems) {
+        if ((rc = ensure(ctx, "rq", rq_elems * 4, &S.rqbuf))) return rc;
+        size_t off = 0;
+        for (int m = 0; m < n_mock; m++) {
+            const tpcf_mock &mk = mocks[m];
+            if (mk.rand_xyz || mk.rand_offsets[M] == 0) continue;
+            const size_t nr = (size_t)mk.rand_offsets[M];
+            for (int i = 0; i < M; i++) {
+                const size_t o0 = (size_t)mk.rand_offsets[i], n = (size_t)(mk.rand_offsets[i + 1] - o0);
+                uint32_t *dst = (uint32_t *)S.rqbuf + off;
+                if (n > 0) S.rq.push_back(RqCopy{dst, mk.rand_u32 + o0, n, nr});
+                S.cats[rand_cat0[m] + i].u32 = dst;
+                off += 3 * n;
+            }
+        }
+    }
+
+    // small tables: cats | terms | orig | table
+    S.o_cats = 0;
+    S.o_terms = al(S.o_cats + S.cats.size() * sizeof(Cat));
+    S.o_orig = al(S.o_terms + S.terms.size() * sizeof(Term));
+    S.o_tab = al(S.o_orig + S.pl.orig.size() * 4);
+    S.small.assign(al(S.o_tab + S.pl.table.size() * 2), 0);
+    std::memcpy(S.small.data() + S.o_cats, S.cats.data(), S.cats.size() * sizeof(Cat));
+    std::memcpy(S.small.data() + S.o_terms, S.terms.data(), S.terms.size() * sizeof(Term));
+    std::memcpy(S.small.data() + S.o_orig, S.pl.orig.data(), S.pl.orig.size() * 4);
+    std::memcpy(S.small.data() + S.o_tab, S.pl.table.data(), S.pl.table.size() * 2);
+
+    // launch shape (host queries, outside any capture)
+    S.smem = paircount_smem_bytes(prm, 8);
+    cudaError_t e = paircount_set_attrs(prm, S.smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "paircount_set_attrs");
+    S.blocks = ctx->n_sm * paircount_max_blocks_per_sm(prm, 8, S.smem);
+    return TPCF_OK;
+}
+
+// Every GPU step of one call, on stream s.  `small` holds S.small on the
+// device.  ev0/ev1 (may be null) are recorded around the pair-count kernels;
+// `external` makes them event-record nodes when the stream is being captured.
+int enqueue(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, void *small, cudaEvent_t ev0, cudaEvent_t ev1,
+            bool external, int &kernels)
+{
+    const CountParams &prm = S.pl.prm;
+    kernels = 0;
+    if (S.dd) CK(cudaMemsetAsync(S.dd, 0, S.n_dd * 8, s));
+    if (S.dr && S.n_drr) CK(cudaMemsetAsync(S.dr, 0, S.n_drr * 8, s));
+    if (S.rr && S.n_drr) CK(cudaMemsetAsync(S.rr, 0, S.n_drr * 8, s));
+    CK(cudaMemsetAsync(ctx->stats, 0, 4 * sizeof(unsigned long long), s));
+    if (S.NT == 0 || S.terms.empty()) {
+        CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        return TPCF_OK;
+    }
+    for (const RqCopy &c : S.rq)
+        CK(cudaMemcpy2DAsync(c.dst, c.n * 4, c.src, c.pitch * 4, c.n * 4, 3, cudaMemcpyDeviceToDevice, s));
+    const Cat *d_cats = (const Cat *)((const char *)small + S.o_cats);
+    const Term *d_terms = (const Term *)((const char *)small + S.o_terms);
+    const uint32_t *d_orig = (const uint32_t *)((const char *)small + S.o_orig);
+    const int16_t *d_tab = (const int16_t *)((const char *)small + S.o_tab);
+    const int n_cat = (int)S.cats.size(), n_terms = (int)S.terms.size();
+    uint32_t *cc = (uint32_t *)S.cc, *cs = (uint32_t *)S.cs, *tmp = (uint32_t *)S.tmp;
+    uint32_t *uc = (uint32_t *)S.uc, *ust = (uint32_t *)S.ust;
+
+    // mesh build: quantise + keys + cell histogram, scan, scatter
+    CK(cudaMemsetAsync(cc, 0, S.ncc * 4, s));
+    CK(launch_quantize_keys(d_cats, n_cat, S.max_n, prm, S.L, S.origin, (uint32_t)S.NT, (uint32_t *)S.uq,
+                            (uint32_t *)S.keys, cc, ctx->status, s));
+    CK(launch_scan_u32(cc, cs, S.ncc, tmp, S.tmp_n, s));
+    CK(cudaMemsetAsync(cc, 0, S.ncc * 4, s));
+    CK(launch_scatter(d_cats, n_cat, S.max_n, prm, (uint32_t *)S.uq, (uint32_t *)S.keys, cs, cc, d_orig,
+                      (uint32_t)S.NT, (uint32_t *)S.us, (float4 *)S.pf, (uint16_t *)S.pcx, s));
+    kernels += 5;
+
+    Mesh mesh;
+    mesh.pf = (const float4 *)S.pf;
+    mesh.pcx = (const uint16_t *)S.pcx;
+    mesh.us = (const uint32_t *)S.us;
+    mesh.n_total = (uint32_t)S.NT;
+    mesh.cellstart = cs;
+    mesh.orig = d_orig;
+    PairLaunch L;
+    L.warps_per_block = 8;
+    L.smem_bytes = S.smem;
+    L.chunk = S.chunk;
+    if (mode == TPCF_BATCHED) {
+        CK(cudaMemsetAsync(uc + (S.ntc - 1), 0, 4, s));
+        CK(launch_unit_count(d_terms, n_terms, d_cats, prm.n_cells, cs, S.chunk, uc, s));
+        CK(launch_scan_u32(uc, ust, S.ntc, tmp, S.tmp_n, s));
+        CK(launch_unit_fill(d_terms, n_terms, d_cats, prm.n_cells, cs, S.chunk, ust, (Unit *)S.units, s));
+        CK(cudaMemsetAsync(S.claim, 0, 4, s));
+        kernels += 5;
+        L.persistent = 1;
+        L.term = 0;
+        L.blocks = S.blocks;
+        if (ev0) CK(cudaEventRecordWithFlags(ev0, s, external ? cudaEventRecordExternal : cudaEventRecordDefault));
+        CK(launch_paircount(prm, mesh, d_terms, d_cats, (const Unit *)S.units, ust + (S.ntc - 1),
+                            (unsigned *)S.claim, d_tab, ctx->stats, ctx->status, L, s));
+        if (ev1) CK(cudaEventRecordWithFlags(ev1, s, external ? cudaEventRecordExternal : cudaEventRecordDefault));
+        kernels += 1;
+        CK(cudaMemcpyAsync(ctx->stats + 3, ust + (S.ntc - 1), 4, cudaMemcpyDeviceToDevice, s));
+    } else {
+        if (ev0) CK(cudaEventRecordWithFlags(ev0, s, external ? cudaEventRecordExternal : cudaEventRecordDefault));
+        for (int t = 0; t < n_terms; t++) {
+            L.persistent = 0;
+            L.term = t;
+            L.blocks = prm.n_cells;
+            CK(launch_paircount(prm, mesh, d_terms, d_cats, nullptr, nullptr, nullptr, d_tab, ctx->stats,
+                                ctx->status, L, s));
+        }
+        if (ev1) CK(cudaEventRecordWithFlags(ev1, s, external ? cudaEventRecordExternal : cudaEventRecordDefault));
+        kernels += n_terms;
+    }
+    CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    return TPCF_OK;
+}
+
+// small tables through the context's pinned staging area (direct path)
+int upload_small(tpcf_ctx *ctx, const Setup &S, cudaStream_t s, void **dev)
+{
+    int rc;
+    if ((rc = ensure(ctx, "small", S.small.size(), dev))) return rc;
+    void *host;
+    if ((rc = staging(ctx, S.small.size(), &host))) return rc;
+    std::memcpy(host, S.small.data(), S.small.size());
+    CK(cudaMemcpyAsync(*dev, host, S.small.size(), cudaMemcpyHostToDevice, s));
+    return staging_done(ctx, s);
+}
+
+// timing slot for this call, or -1
+int timing_slot(tpcf_ctx *ctx)
+{
+    if (!ctx->timing || ctx->n_timed >= 4096) return -1;
+    const int slot = ctx->n_timed;
+    while ((int)ctx->ev.size() < 2 * (slot + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        ctx->ev.push_back(e);
+    }
+    return slot;
+}
+
+std::string graph_key(const Setup &S, int mode, tpcf_ctx *ctx)
+{
+    std::string k;
+    auto put = [&](const void *p, size_t n) { k.append((const char *)p, n); };
+    put(&S.pl.prm, sizeof(CountParams));
+    put(&mode, sizeof(mode));
+    put(&S.chunk, sizeof(S.chunk));
+    put(&S.blocks, sizeof(S.blocks));
+    put(&S.NT, sizeof(S.NT));
+    put(&S.L, sizeof(S.L));
+    put(S.origin, sizeof(S.origin));
+    put(S.small.data(), S.small.size());   // catalogue pointers, sizes, outputs, cell corners, table
+    for (const RqCopy &c : S.rq) put(&c, sizeof(c));
+    const void *ws[] = {S.uq, S.keys, S.us, S.pf, S.pcx, S.cc, S.cs, S.tmp, S.uc, S.ust, S.units, S.claim,
+                        S.rqbuf, S.dd, S.dr, S.rr, ctx->stats, ctx->stats_host, ctx->status};
+    put(ws, sizeof(ws));
+    return k;
+}
+
+int run_graph(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, int slot)
+{
+    const std::string key = graph_key(S, mode, ctx);
+    GraphEntry *g = nullptr;
+    for (GraphEntry &e : ctx->graphs)
+        if (e.key == key) g = &e;
+    if (!g) {
+        if (ctx->graphs.size() >= 8) {
+            auto oldest = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                           [](const GraphEntry &a, const GraphEntry &b) { return a.last_use < b.last_use; });
+            CK(cudaDeviceSynchronize());
+            if (oldest->exec) cudaGraphExecDestroy(oldest->exec);
+            if (oldest->small) cudaFree(oldest->small);
+            ctx->graphs.erase(oldest);
+        }
+        GraphEntry ne;
+        ne.key = key;
+        CK(cudaMalloc(&ne.small, S.small.size()));
+        CK(cudaMemcpy(ne.small, S.small.data(), S.small.size(), cudaMemcpyHostToDevice));
+        // capture on the context's own stream, then replay on the caller's
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int kernels = 0;
+        const int rc = enqueue(ctx, S, mode, ctx->cap_stream, ne.small, ctx->scratch_ev[0], ctx->scratch_ev[1], true,
+                               kernels);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaFree(ne.small);
+            return rc;
+        }
+        if (ec != cudaSuccess) {
+            cudaFree(ne.small);
+            return cuda_fail(ctx, ec, "cudaStreamEndCapture");
+        }
+        ne.kernels = kernels;
+        // the two event-record nodes, in capture order
+        size_t n_nodes = 0;
+        CK(cudaGraphGetNodes(graph, nullptr, &n_nodes));
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        CK(cudaGraphGetNodes(graph, nodes.data(), &n_nodes));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            CK(cudaGraphNodeGetType(nd, &t));
+            if (t == cudaGraphNodeTypeEventRecord) {
+                cudaEvent_t ev;
+                CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+                if (ev == ctx->scratch_ev[0]) ne.ev_node[0] = nd;
+                if (ev == ctx->scratch_ev[1]) ne.ev_node[1] = nd;
+            }
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&ne.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            cudaFree(ne.small);
+            return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+        }
+        ctx->graphs.push_back(std::move(ne));
+        g = &ctx->graphs.back();
+    }
+    g->last_use = ++ctx->use_clock;
+    cudaEvent_t e0 = slot >= 0 ? ctx->ev[2 * slot] : ctx->scratch_ev[0];
+    cudaEvent_t e1 = slot >= 0 ? ctx->ev[2 * slot + 1] : ctx->scratch_ev[1];
+    if (g->ev_node[0]) CK(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_node[0], e0));
+    if (g->ev_node[1]) CK(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_node[1], e1));
+    CK(cudaGraphLaunch(g->exec, s));
+    ctx->last_kernels = g->kernels;
+    ctx->last_graph = true;
+    return TPCF_OK;
+}
+
+int run_direct(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, int slot)
+{
+    void *small = nullptr;
+    int rc;
+    if (!S.small.empty() && (rc = upload_small(ctx, S, s, &small))) return rc;
+    int kernels = 0;
+    rc = enqueue(ctx, S, mode, s, small, slot >= 0 ? ctx->ev[2 * slot] : nullptr,
+                 slot >= 0 ? ctx->ev[2 * slot + 1] : nullptr, false, kernels);
+    if (rc) return rc;
+    ctx->last_kernels = kernels;
+    ctx->last_graph = false;
+    return TPCF_OK;
+}
+
+// Autotuner: time candidate (subdivision, unit size) pairs on a few mocks.
+int autotune(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *binning, unsigned terms,
+             int64_t *dd, int64_t *dr, int64_t *rr, cudaStream_t s, Tuned &best)
+{
+    const int n_try = std::min(n_mock, 6);
+    static const int subdivs[] = {2, 3, 4};
+    static const int chunks[] = {128, 256};
+    cudaEvent_t t0, t1;
+    CK(cudaEventCreate(&t0));
+    CK(cudaEventCreate(&t1));
+    float best_ms = 1e30f;
+    int rc = TPCF_OK;
+    for (int sd : subdivs)
+        for (int ch : chunks) {
+            Setup S;
+            if ((rc = prepare(ctx, mocks, n_try, binning, terms, dd, dr, rr, TPCF_BATCHED, sd, ch, S))) {
+                if (rc == TPCF_ERR_RANGE) { rc = TPCF_OK; continue; }   // mesh not possible at this subdivision
+                break;
+            }
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2 && rc == TPCF_OK; rep++) {
+                CK(cudaEventRecord(t0, s));
+                rc = run_direct(ctx, S, TPCF_BATCHED, s, -1);
+                CK(cudaEventRecord(t1, s));
+                CK(cudaEventSynchronize(t1));
+                float x = 0;
+                CK(cudaEventElapsedTime(&x, t0, t1));
+                ms = std::min(ms, x);
+            }
+            if (rc) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.subdiv = sd;
+                best.chunk = ch;
+            }
+        }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return rc;
+}
+
+std::string tune_key(const tpcf_mock *mocks, int n_mock, const tpcf_binning *b, unsigned terms)
+{
+    std::string k;
+    auto put = [&](const void *p, size_t n) { k.append((const char *)p, n); };
+    put(&b->geometry, sizeof(int));
+    put(&b->box_L, sizeof(double));
+    put(&b->los, sizeof(int));
+    put(&b->n_s, sizeof(int));
+    put(&b->n_mu, sizeof(int));
+    put(b->s_edges, sizeof(double) * (b->n_s + 1));
+    put(&terms, sizeof(terms));
+    // size class: log2 of the mean catalogue size
+    double pts = 0;
+    for (int m = 0; m < n_mock; m++) pts += (double)mocks[m].n_d;
+    const int cls = n_mock > 0 ? (int)std::log2(1.0 + pts / n_mock) : 0;
+    put(&cls, sizeof(cls));
+    return k;
+}
+
+}  // namespace
+
+namespace tpcf {
+namespace detail {
+
+void release_graphs(tpcf_ctx *ctx)
+{
+    for (GraphEntry &e : ctx->graphs) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (e.small) cudaFree(e.small);
+    }
+    ctx->graphs.clear();
+}
+
+}  // namespace detail
+}  // namespace tpcf
+
+extern "C" int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *binning,
+                          unsigned terms, int64_t *dd, int64_t *dr, int64_t *rr, int mode, void *stream)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // shape-level validation first, so that tuning never sees a bad call
+    if ((rc = validate_binning(ctx, binning))) return rc;
+    Tuned cfg;
+    if (ctx->subdiv_pin) {
+        cfg.subdiv = ctx->subdiv_pin;
+    } else if (ctx->autotune && mode == TPCF_BATCHED && n_mock > 0) {
+        const std::string tk = tune_key(mocks, n_mock, binning, terms);
+        auto it = ctx->tune_cache.find(tk);
+        if (it == ctx->tune_cache.end()) {
+            Setup probe;
+            if ((rc = prepare(ctx, mocks, n_mock, binning, terms, dd, dr, rr, mode, cfg.subdiv, cfg.chunk, probe)))
+                return rc;
+            Tuned t;
+            if ((rc = autotune(ctx, mocks, n_mock, binning, terms, dd, dr, rr, s, t))) return rc;
+            it = ctx->tune_cache.emplace(tk, t).first;
+        }
+        cfg = it->second;
+    }
+    Setup S;
+    if ((rc = prepare(ctx, mocks, n_mock, binning, terms, dd, dr, rr, mode, cfg.subdiv, cfg.chunk, S))) return rc;
+    ctx->last_subdiv = cfg.subdiv;
+    ctx->last_nc = S.pl.prm.n_c;
+    ctx->last_chunk = S.chunk;
+    ctx->last_launches = S.terms.empty() || S.NT == 0 ? 0 : (mode == TPCF_BATCHED ? 1 : (int)S.terms.size());
+    const int slot = timing_slot(ctx);
+    if (mode == TPCF_BATCHED && ctx->use_graphs && S.NT > 0 && !S.terms.empty())
+        rc = run_graph(ctx, S, mode, s, slot);
+    else
+        rc = run_direct(ctx, S, mode, s, slot);
+    if (rc) return rc;
+    if (slot >= 0) ctx->n_timed++;
+    CK(cudaEventRecord(ctx->done, s));
+    return TPCF_OK;
+}

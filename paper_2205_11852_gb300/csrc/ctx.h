@@ -1,0 +1,96 @@
+// Private context of libtpcf, shared by the translation units of the C ABI.
+#pragma once
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+namespace tpcf {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct PinBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// One instantiated CUDA graph of a batched tpcf_count, replayed while the
+// call's plan, buffers and outputs stay the same.
+struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ev_node[2] = {nullptr, nullptr};   // event-record nodes around the pair-count kernel
+    void *small = nullptr;                             // the graph's own copy of the small tables
+    int kernels = 0;
+    unsigned long long last_use = 0;
+};
+
+// Autotuned configuration of the batched pair count.
+struct Tuned {
+    int subdiv = 3;
+    int chunk = 256;
+};
+
+}  // namespace tpcf
+
+struct tpcf_ctx {
+    int device = 0;
+    int n_sm = 0;
+    std::string err;
+    bool broken = false;
+    // workspace
+    std::map<std::string, tpcf::DevBuf> bufs;
+    tpcf::PinBuf staging;
+    cudaEvent_t staging_free = nullptr;   // recorded after the last copy out of `staging`
+    bool staging_pending = false;
+    int *status = nullptr;                // device status word
+    unsigned long long *stats = nullptr;  // device [4]
+    unsigned long long *stats_host = nullptr;  // pinned [4]
+    // timing: one event pair per timed tpcf_count
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;          // [2 * k]
+    int n_timed = 0;
+    cudaEvent_t done = nullptr;           // recorded after the stats copy of the last tpcf_count
+    cudaEvent_t scratch_ev[2] = {nullptr, nullptr};   // graph event nodes point here when untimed
+    int last_launches = 0;
+    int last_kernels = 0;
+    bool last_graph = false;
+    // planner and autotuner
+    int subdiv_pin = 0;
+    int use_graphs = 1;
+    int autotune = 1;
+    std::map<std::string, tpcf::Tuned> tune_cache;
+    int last_subdiv = 0, last_nc = 0, last_chunk = 0;
+    // graphs
+    cudaStream_t cap_stream = nullptr;
+    std::vector<tpcf::GraphEntry> graphs;
+    unsigned long long use_clock = 0;
+};
+
+namespace tpcf {
+namespace detail {
+
+int fail(tpcf_ctx *c, int code, const std::string &msg);
+int cuda_fail(tpcf_ctx *c, cudaError_t e, const char *where);
+int ensure(tpcf_ctx *ctx, const char *name, size_t bytes, void **out);
+int staging(tpcf_ctx *ctx, size_t bytes, void **out);
+int staging_done(tpcf_ctx *ctx, cudaStream_t s);
+size_t al(size_t x);
+int check_ctx(tpcf_ctx *ctx);
+int validate_binning(tpcf_ctx *ctx, const tpcf_binning *b);
+int check_mu_width(tpcf_ctx *ctx, const tpcf_binning *b, const CountParams &p);
+void release_graphs(tpcf_ctx *ctx);
+
+}  // namespace detail
+}  // namespace tpcf
+
+#define CK(expr)                                                                       \
+    do {                                                                               \
+        cudaError_t _e = (expr);                                                       \
+        if (_e != cudaSuccess) return ::tpcf::detail::cuda_fail(ctx, _e, #expr);       \
+    } while (0)

@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
                                                                 unsigned *__restrict__ claim,
                                                                 const int16_t *__restrict__ table_g,
                                                                 unsigned long long *__restrict__ stats,
-                                                                int persistent, int term_pl)
+                                                                int persistent, int term_pl, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     size_t off[10];
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
             un.term = term_pl;
             un.cell = blockIdx.x;
             un.a0 = pl_a;
-            un.a1 = min(pl_end, pl_a + (uint32_t)UNIT_CHUNK);
+            un.a1 = min(pl_end, pl_a + (uint32_t)chunk);
             pl_a = un.a1;
         }
         const Term tm = terms[un.term];
@@ -640,7 +640,7 @@ cudaError_t launch_paircount(const CountParams &p, const Mesh &m, const Term *te
     (void)status;
     void *args[] = {(void *)&p,     (void *)&m,     (void *)&terms,         (void *)&units,   (void *)&n_units,
                     (void *)&claim, (void *)&table, (void *)&stats,         (void *)&pl.persistent,
-                    (void *)&pl.term};
+                    (void *)&pl.term, (void *)&pl.chunk};
     return cudaLaunchKernel(select_kernel(p), dim3(pl.blocks), dim3(WARPS * 32), args, (size_t)pl.smem_bytes, s);
 }
 

@@ -112,6 +112,7 @@ struct PairLaunch {
     int persistent;        // 1: claim units from a global counter; 0: one block per cell of one term
     int term;              // per-launch mode: the term
     int smem_bytes;
+    int chunk;             // a-points per work unit (per-launch mode)
 };
 cudaError_t launch_paircount(const CountParams &p, const Mesh &m, const Term *terms, const Cat *cats,
                              const Unit *units, const uint32_t *n_units, unsigned *claim,

@@ -359,3 +359,53 @@ def test_lc_split_precision_within_1e6(tp, ctx, prec_name, n_mock, nbin):
     for k in ("C_lc", "Ca", "Cb", "A", "B"):
         err = np.max(np.abs(out[k].cpu().numpy() - ref[k]) / scale)
         assert err <= 1e-6, (k, err)
+
+
+# ---------------------------------------------------------------------------
+# batched path: CUDA-graph replay and autotuner
+# ---------------------------------------------------------------------------
+
+def test_graph_replay_bit_identical_and_timed(tp):
+    L = 300.0
+    w = synth.Workload("t", 35, 3, "periodic", L, (0, 0, 0), 1200, 2, 60.0, 12, 4, "x", n_parent=5e-5, sigma=2.0)
+    mocks = [w.make_mock(m) for m in range(3)]
+    tb, ob = _periodic(L, w.s_edges, 4)
+    dm = _mocks_to_device(mocks)
+    c = tp.Context(0)
+    c.tpcf_set_option(tp.TPCF_OPT_GRAPHS, 0)
+    ref = c.tpcf_count(dm, tb)
+    c.tpcf_sync()
+    assert c.tpcf_last_count_info()["graph_replay"] == 0
+    c.tpcf_set_option(tp.TPCF_OPT_GRAPHS, 1)
+    out = {k: torch.empty_like(v) for k, v in ref.items()}
+    c.tpcf_count(dm, tb, out=out)            # captures
+    c.tpcf_set_timing(True)
+    for _ in range(3):
+        for v in out.values():
+            v.fill_(-7)                      # replays must rewrite every output
+        c.tpcf_count(dm, tb, out=out)
+    assert c.tpcf_sync() == tp.TPCF_OK
+    info = c.tpcf_last_count_info()
+    assert info["graph_replay"] == 1 and info["timed_calls"] == 3 and info["paircount_ms"] > 0
+    for k in ("dd", "dr", "rr"):
+        assert torch.equal(out[k], ref[k])
+    o = oracle.count_mock(mocks[1].data, mocks[1].randoms, ob)
+    assert np.array_equal(out["rr"][1].cpu().numpy(), o["RR"])
+    c.close()
+
+
+def test_autotuner_choice_is_exact(tp):
+    L = 400.0
+    w = synth.Workload("t", 36, 8, "periodic", L, (0, 0, 0), 1500, 2, 80.0, 20, 5, "x", n_parent=3e-5, sigma=3.0)
+    mocks = [w.make_mock(m) for m in range(8)]
+    tb, ob = _periodic(L, w.s_edges, 5)
+    c = tp.Context(0)
+    out = c.tpcf_count(_mocks_to_device(mocks), tb)
+    c.tpcf_sync()
+    info = c.tpcf_last_count_info()
+    assert info["cell_subdiv"] in (2, 3, 4) and info["unit_chunk"] in (128, 256)
+    for m in (0, 7):
+        o = oracle.count_mock(mocks[m].data, mocks[m].randoms, ob)
+        assert np.array_equal(out["dd"][m].cpu().numpy(), o["DD"])
+        assert np.array_equal(out["dr"][m].cpu().numpy(), o["DR"])
+    c.close()
