@@ -375,6 +375,7 @@ int run_graph(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, int slot)
                                            [](const GraphEntry &a, const GraphEntry &b) { return a.last_use < b.last_use; });
             CK(cudaDeviceSynchronize());
             if (oldest->exec) cudaGraphExecDestroy(oldest->exec);
+            if (oldest->graph) cudaGraphDestroy(oldest->graph);
             if (oldest->small) cudaFree(oldest->small);
             ctx->graphs.erase(oldest);
         }
@@ -415,11 +416,12 @@ int run_graph(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, int slot)
             }
         }
         const cudaError_t ei = cudaGraphInstantiate(&ne.exec, graph, 0);
-        cudaGraphDestroy(graph);
         if (ei != cudaSuccess) {
+            cudaGraphDestroy(graph);
             cudaFree(ne.small);
             return cuda_fail(ctx, ei, "cudaGraphInstantiate");
         }
+        ne.graph = graph;
         ctx->graphs.push_back(std::move(ne));
         g = &ctx->graphs.back();
     }
@@ -517,6 +519,7 @@ void release_graphs(tpcf_ctx *ctx)
 {
     for (GraphEntry &e : ctx->graphs) {
         if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (e.graph) cudaGraphDestroy(e.graph);
         if (e.small) cudaFree(e.small);
     }
     ctx->graphs.clear();

@@ -23,6 +23,7 @@ struct PinBuf {
 // call's plan, buffers and outputs stay the same.
 struct GraphEntry {
     std::string key;
+    cudaGraph_t graph = nullptr;                       // kept: its nodes address the exec's nodes
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t ev_node[2] = {nullptr, nullptr};   // event-record nodes around the pair-count kernel
     void *small = nullptr;                             // the graph's own copy of the small tables
