@@ -51,10 +51,14 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--mocks", type=int, default=synth.MID.n_mock, help="mocks per GPU")
     p.add_argument("--nd", type=int, default=synth.MID.n_d, help="data points per mock")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "tf32x3", "bf16x3"])
+    p.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3"])
+    p.add_argument("--no-precision-config", action="store_true",
+                   help="skip the covariance-only measurement on 3500 mocks x 200 bins")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--subdiv", type=int, default=0, help="pin the mesh subdivision (0: library choice)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--cov-only", action="store_true",
+                   help="two split-precision LC covariances of 3500 mocks x 200 bins, then exit (profiler captures)")
     p.add_argument("--count-only", action="store_true",
                    help="one warm-up and one batched tpcf_count of the workload, then exit (profiler captures)")
     return p.parse_args()
@@ -239,6 +243,16 @@ def main():
     n_mock, n_d = args.mocks, args.nd
     prec = {"fp64": tp.TPCF_FP64, "tf32x3": tp.TPCF_TF32X3, "bf16x3": tp.TPCF_BF16X3}[args.precision]
 
+    if args.cov_only:
+        xs = synth.synthetic_xi_variants(3, 3500, 200)
+        gx = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in xs]
+        ctx0 = tp.Context(local)
+        for _ in range(2):
+            ctx0.tpcf_lc_cov(*gx, 1, M_FINAL, prec, want_parts=False)
+        print(json.dumps({"cov_only": True, "precision": args.precision, "status": ctx0.tpcf_sync()}))
+        ctx0.close()
+        return
+
     host, layout = make_host_inputs(n_mock, n_d, rank * n_mock)
     pinned = torch.from_numpy(host).pin_memory()
     pos = pinned.to(dev)
@@ -386,7 +400,32 @@ def main():
                           f"DR2, RR1, RR2), {r['fraction_of_mock']:.3%} of one mock's pair tests, "
                           f"{r['seconds']:.1f} s")}
 
-    kernels_per_step = info["n_kernels"] + 3 + 4
+    # covariance-only workload: 3500 mocks x 3 variants x 200 (s, mu) bins,
+    # float64 vs split precision on the tensor cores, error against the oracle
+    prec_cfg = None
+    if rank == 0 and not args.no_precision_config:
+        import oracle
+        xs = synth.synthetic_xi_variants(3, 3500, 200)
+        gx = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in xs]
+        ref = oracle.lc_cov(*xs, 1, M_FINAL)
+        d = np.sqrt(np.diag(ref["Ca"]))
+        scale = np.outer(d, d)
+        prec_cfg = {"workload": "3500 mocks x 3 variants x 200 (s, mu) bins, LC covariance with M=50"}
+        for name, pr in (("fp64", tp.TPCF_FP64), ("tf32x3", tp.TPCF_TF32X3), ("bf16x3", tp.TPCF_BF16X3)):
+            for _ in range(3):
+                out = ctx.tpcf_lc_cov(*gx, 1, M_FINAL, pr, want_parts=False)
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            c0.record(stream)
+            for _ in range(reps):
+                out = ctx.tpcf_lc_cov(*gx, 1, M_FINAL, pr, want_parts=False)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            err = float(np.max(np.abs(out["C_lc"].cpu().numpy() - ref["C_lc"]) / scale))
+            prec_cfg[name] = {"ms": c0.elapsed_time(c1) / reps, "max_err_vs_fp64_oracle": err}
+
+    kernels_per_step = info["n_kernels"] + 3 + 4   # count + 3 LS + 4 covariance kernels
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "mocks/s", "n_gpus": world, "steps": args.steps,
@@ -404,6 +443,9 @@ def main():
                            "batched_over_per_launch": value / per_launch},
             "batched_equals_per_launch": bool(same),
             "cov_err_vs_fp64": cov_err,
+            "tuned": {"cell_subdiv": info["cell_subdiv"], "cells_per_axis": info["cells_per_axis"],
+                      "unit_chunk": info["unit_chunk"], "graph_replay": bool(info["graph_replay"])},
+            "precision_config": prec_cfg,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-op/s",
                          "frac": achieved / peak, "traffic": None,
                          "frac_at_run_clock": achieved / (n_sm * LANES_PER_SM * f_run * 1e6),

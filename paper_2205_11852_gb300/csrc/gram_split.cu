@@ -252,8 +252,8 @@ __host__ __device__ constexpr uint32_t instr_desc()
 
 template <int PREC>
 __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned char *__restrict__ tiles, int nbin,
-                                                              int n_rb, int n_ks, const int2 *__restrict__ pairs,
-                                                              double *__restrict__ G, int *__restrict__ status)
+                                                              int n_rb, int n_ks, double *__restrict__ G,
+                                                              int *__restrict__ status)
 {
     constexpr int TB = tile_bytes<PREC>();
     constexpr int NP = Split<PREC>::PIECES;
@@ -265,8 +265,13 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
     int *flag = (int *)(slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int2 pr = pairs[blockIdx.x];
-    const int bi = pr.x, bj = pr.y;
+    // blockIdx.x enumerates the upper-triangle tile pairs (bi <= bj) row by row
+    int bi = 0, rest = (int)blockIdx.x;
+    while (rest >= n_rb - bi) {
+        rest -= n_rb - bi;
+        bi++;
+    }
+    const int bj = bi + rest;
     const int v = blockIdx.y, ks = blockIdx.z;
 
     if (warp == 0) tmem_alloc(slot, TMEM_COLS);
@@ -374,26 +379,17 @@ cudaError_t run(const double *x0, const double *x1, const double *x2, int n_mock
     o += al256(3 * (size_t)nbin * nbin * 8);
     double *mean = (double *)(w + o);
     o += al256(3 * (size_t)nbin * 8);
-    int2 *pairs = (int2 *)(w + o);
-    o += al256((size_t)n_rb * (n_rb + 1) / 2 * sizeof(int2));
     if (o > work_bytes) return cudaErrorInvalidValue;
     cudaError_t e = launch_means(x0, x1, x2, n_mock, nbin, mean, s);
     if (e != cudaSuccess) return e;
     split_kernel<PREC><<<dim3(n_ks, n_rb, 3), 256, 0, s>>>(x0, x1, x2, mean, n_mock, nbin, n_rb, n_ks, tiles);
-    // upper-triangle tile pairs (bi <= bj)
-    static thread_local int2 host_pairs[4096];
-    int np = 0;
-    for (int i = 0; i < n_rb; i++)
-        for (int j = i; j < n_rb && np < 4096; j++) host_pairs[np++] = make_int2(i, j);
-    if (np != n_rb * (n_rb + 1) / 2) return cudaErrorInvalidValue;
-    e = cudaMemcpyAsync(pairs, host_pairs, np * sizeof(int2), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
+    const int np = n_rb * (n_rb + 1) / 2;   // upper-triangle tile pairs
     e = cudaMemsetAsync(G, 0, 3 * (size_t)nbin * nbin * 8, s);
     if (e != cudaSuccess) return e;
     const int smem = std::max(2 * Split<PREC>::PIECES * tile_bytes<PREC>() + 64, GRAM_SMEM_MIN);
     e = cudaFuncSetAttribute(gram_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    gram_tc_kernel<PREC><<<dim3(np, 3, n_ks), GRAM_THREADS, smem, s>>>(tiles, nbin, n_rb, n_ks, pairs, G, status);
+    gram_tc_kernel<PREC><<<dim3(np, 3, n_ks), GRAM_THREADS, smem, s>>>(tiles, nbin, n_rb, n_ks, G, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_combine(G, nbin, n_mock, M_a, M, C_lc, Ca, Cb, A, B, s);
@@ -406,8 +402,8 @@ size_t lc_split_work_bytes(int n_mock, int nbin, int precision)
     const size_t n_rb = (nbin + TM - 1) / TM;
     const size_t t = precision == TPCF_BF16X3 ? tiles_bytes<TPCF_BF16X3>(n_mock, nbin)
                                               : tiles_bytes<TPCF_TF32X3>(n_mock, nbin);
-    return al256(t) + al256(3 * (size_t)nbin * nbin * 8) + al256(3 * (size_t)nbin * 8) +
-           al256(n_rb * (n_rb + 1) / 2 * sizeof(int2));
+    (void)n_rb;
+    return al256(t) + al256(3 * (size_t)nbin * nbin * 8) + al256(3 * (size_t)nbin * 8);
 }
 
 cudaError_t launch_lc_split(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
