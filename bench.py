@@ -180,15 +180,29 @@ def oracle_sample_rate(n_d, target_s, seed_mock=0):
 
     k = max(16, n_d // 2000)
     dt, tests = run(k)
-    k2 = int(min(n_d, k * max(1.0, target_s / max(dt, 1e-3))))
-    if k2 > k:
-        dt, tests = run(k2)
-        k = k2
+    # grow the sample until it takes at least ~70% of the target time (or the whole mock)
+    while dt < 0.7 * target_s and k < n_d:
+        k = int(min(n_d, max(2 * k, k * 0.9 * target_s / max(dt, 1e-3))))
+        dt, tests = run(k)
     full = 3.5 * n_d * n_d
     frac = tests / full
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"mocks_per_s": frac / dt, "seconds": dt, "rows": k, "fraction_of_mock": frac, "cores": cores,
             "pair_tests_per_s": tests / dt}
+
+
+def measured_traffic(n_mock):
+    """DRAM bytes of one pair-count launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "paircount_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2205_11852_gb300", "csrc", "paircount.cu"), "rb").read()
+    except OSError:
+        return None
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("kernel_source_sha256_prefix"):
+        return None
+    return rec["dram_bytes_per_mock"] * n_mock
 
 
 def run_reference(args, rank, world):
@@ -253,7 +267,8 @@ def main():
         ctx0.close()
         return
 
-    host, layout = make_host_inputs(n_mock, n_d, rank * n_mock)
+    from paper_2205_11852_gb300 import multi
+    host, layout = make_host_inputs(n_mock, n_d, multi.mock_range(rank, n_mock).start)
     pinned = torch.from_numpy(host).pin_memory()
     pos = pinned.to(dev)
     mocks = mock_views(pos, layout)
@@ -280,10 +295,9 @@ def main():
             ctx.tpcf_ls(outc["dd"], outc["dr"], outc["rr"], nd_list, nr_list, sel, out=xi[k])
         src = xi
         if gather is not None:
-            import torch.distributed as dist
-            for k in xi:
-                dist.all_gather_into_tensor(gather[k], xi[k])
-            src = gather
+            src = {k: multi.gather_rows(v, world) for k, v in xi.items()}
+            for k in src:
+                gather[k] = src[k]
         return ctx.tpcf_lc_cov(src["a1"], src["a2"], src["b"], 1, M_FINAL, prec, want_parts=False)
 
     def barrier():
@@ -447,7 +461,8 @@ def main():
                       "unit_chunk": info["unit_chunk"], "graph_replay": bool(info["graph_replay"])},
             "precision_config": prec_cfg,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-op/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": measured_traffic(n_mock),
+                         "traffic_note": "ncu DRAM bytes of 2 mocks scaled to the launch's mocks",
                          "frac_at_run_clock": achieved / (n_sm * LANES_PER_SM * f_run * 1e6),
                          "kernel": "paircount_kernel", "kernel_ms": k_ms,
                          "lane_ops_per_launch": lane_ops, "exact_rechecks": info["n_exact"]},
