@@ -16,8 +16,8 @@
 // costs three FMAs and one compare (|a|^2/2 is stored with the point,
 // (|b'|^2 - H)/2 is per lane), with a margin that makes it a superset of the
 // direct FP32 test d2 < H.  A passing pair appends a 16-bit entry (a index,
-// b slot) to the warp's dense queue in shared memory at its ballot rank.
-// Queues are binned in bulk: the direct FP32 d2 and dx are recomputed, the s bin comes
+// b slot) to a lane-private queue in shared memory, branch-free.  Queues are
+// binned in bulk: the direct FP32 d2 and dx are recomputed, the s bin comes
 // from a table indexed by the bit pattern of d2 (one compare against the
 // band of the next edge), the mu bin from n_mu |dx| / sqrt(d2).  A pair whose
 // d2 or mu lies within the rigorous FP32 error band of a bin edge is rebinned
@@ -31,7 +31,7 @@ namespace {
 
 constexpr int P = 4;            // b-points per lane
 constexpr int TILE = 32 * P;    // b-points per warp tile
-constexpr int QCAP = 1024;      // warp queue capacity (16-bit entries)
+constexpr int QN = 40;          // queue slots per lane (16-bit entries)
 constexpr int WARPS = 8;        // warps per block
 constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 
@@ -50,7 +50,8 @@ struct Seg {
 struct Smem {
     float4 *a;                 // [UNIT_CHUNK]
     int *hist;                 // [nbin]
-    uint16_t *queue;           // [WARPS][QCAP]
+    uint16_t *queue;           // [WARPS][QN][32]
+    uint16_t *compact;         // [WARPS][QN * 32]
     float4 *bcopy;             // [WARPS][P][32]: b' in A's frame, .w = b index (bits)
     int16_t *table;            // [tab_n]
     float2 *lohi;              // [n_s + 2]
@@ -68,7 +69,7 @@ __host__ __device__ inline size_t smem_layout(const CountParams &p, size_t *off)
     off[0] = o; o = align16(o + sizeof(unsigned long long) * (p.n_s + 1));  // T
     off[1] = o; o = align16(o + sizeof(float4) * UNIT_CHUNK);              // a chunk
     off[2] = o; o = align16(o + sizeof(float4) * WARPS * P * 32);           // b copies
-    off[3] = o; o = align16(o + sizeof(uint16_t) * WARPS * QCAP);           // warp queues
+    off[3] = o; o = align16(o + sizeof(uint16_t) * WARPS * QN * 32 * 2);    // queues + compacted copies
     off[4] = o; o = align16(o + sizeof(int) * p.nbin);                      // histogram
     off[5] = o; o = align16(o + sizeof(float2) * (p.n_s + 2));              // edge bands
     off[6] = o; o = align16(o + sizeof(uint32_t) * (p.n_c + 1));            // cell corners
@@ -158,6 +159,7 @@ struct Ctx {
     const Mesh &m;
     int lane, warp;
     uint16_t *q;               // this warp's queue
+    uint16_t *cq;              // this warp's compacted queue
     float4 *bc;                // this warp's b copies (.w: b index)
     uint32_t a0, na;           // current unit's a-chunk
     float gx, gy, gz;          // 2 (corner(A) - observer), midpoint line of sight
@@ -227,20 +229,29 @@ struct Ctx {
         return amb ? -2 : (valid ? bin : -1);
     }
 
-    // Bin the warp's queued pairs [0, qn) with every lane busy.  Entries are
-    // (a index | b copy index << 8) in (a, slot, lane) order, so the a loads
-    // mostly broadcast and the b loads are consecutive.  Pairs that need the
-    // exact recheck are gathered (in place, behind the read position) and
-    // rechecked after the loop.
-    __device__ __forceinline__ void flush(uint32_t &qn)
+    // Bin every queued pair.  The lanes' queues are first packed into one
+    // warp-contiguous list (a index | b copy index << 8), so that the binning
+    // loop runs with all lanes busy whatever the spread of per-lane counts.
+    // Pairs that need the exact recheck are gathered (in place, behind the
+    // read position) and rechecked after the loop.
+    __device__ __forceinline__ void flush(uint16_t *&head)
     {
+        const uint32_t n = (uint32_t)(head - (q + lane)) >> 5;
+        uint32_t total;
+        const uint32_t pos = warp_exclusive_sum(n, lane, total);
+        const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
+        for (uint32_t k = 0; k < nmax; k++)
+            if (k < n) {
+                const uint32_t v = q[k * 32 + lane];   // a index | p << 8
+                cq[pos + k] = (uint16_t)((v & 255u) | ((((v >> 8) << 5) | lane) << 8));
+            }
         __syncwarp();
         uint32_t n_amb = 0;
-        for (uint32_t w0 = 0; w0 < qn; w0 += 32) {
+        for (uint32_t w0 = 0; w0 < total; w0 += 32) {
             const uint32_t e = w0 + lane;
-            const bool live = e < qn;
-            const uint32_t v = live ? q[e] : 0u;
-            const uint32_t ai = v & 255u, bi = v >> 8;   // bi = p * 32 + lane of the b-point
+            const bool live = e < total;
+            const uint32_t v = live ? cq[e] : 0u;
+            const uint32_t ai = v & 255u, bi = v >> 8;   // bi = p * 32 + owner lane = ib - base
             const float4 a = sm.a[ai];
             const float4 b = bc[bi];
             const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
@@ -251,13 +262,13 @@ struct Ctx {
             const unsigned am = __ballot_sync(0xffffffffu, bin == -2);
             if (am) {
                 __syncwarp();
-                if (bin == -2) q[n_amb + __popc(am & ((1u << lane) - 1u))] = (uint16_t)v;
+                if (bin == -2) cq[n_amb + __popc(am & ((1u << lane) - 1u))] = (uint16_t)v;
                 n_amb += __popc(am);
             }
         }
         __syncwarp();
         for (uint32_t e = lane; e < n_amb; e += 32) {
-            const uint32_t v = q[e];
+            const uint32_t v = cq[e];
             const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + (v & 255u), __float_as_uint(bc[v >> 8].w));
             n_exact++;
             if (bin >= 0) {
@@ -265,7 +276,7 @@ struct Ctx {
                 n_binned++;
             }
         }
-        qn = 0;
+        head = q + lane;
         __syncwarp();
     }
 
@@ -323,27 +334,45 @@ struct Ctx {
             }
         }
         __syncwarp();
-        // A hit is appended to the warp queue at its rank among the slot's hits
-        // (one ballot per b slot), so the queue stays dense and in (a, slot,
-        // lane) order.  qn is warp-uniform; a flush comes before one more
-        // a-point (32 P entries at most) could overflow the queue.
-        const uint32_t lt = (1u << lane) - 1u;
+        // Every candidate writes the head slot of the lane's queue; only a hit
+        // advances the head, so the stores stay branch-free.  A flush is forced
+        // before 2P more pushes could run past QN slots.
+        uint16_t *head = q + lane;
+        uint16_t *const lim = q + lane + (QN - 2 * P) * 32;
         const uint32_t ib0 = base + lane;   // used by SELF tiles only
-        uint32_t qn = 0;
-        for (uint32_t ai = 0; ai < na; ai++) {
+        uint32_t ai = 0;
+        for (; ai + 1 < na; ai += 2) {
+            const float4 a = sm.a[ai], c = sm.a[ai + 1];
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
+                bool hit = t >= hb[p];
+                if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
+                *head = (uint16_t)(ai | (p << 8));   // kept only on a hit
+                head += hit ? 32 : 0;
+            }
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                const float t = __fmaf_rn(c.x, bx[p], __fmaf_rn(c.y, by[p], __fmaf_rn(c.z, bz[p], c.w)));
+                bool hit = t >= hb[p];
+                if (SELF) hit = hit && (a0 + ai + 1 < ib0 + 32u * p);
+                *head = (uint16_t)((ai + 1) | (p << 8));
+                head += hit ? 32 : 0;
+            }
+            if (__any_sync(0xffffffffu, head > lim)) flush(head);
+        }
+        if (ai < na) {
             const float4 a = sm.a[ai];
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                const uint32_t mk = __ballot_sync(0xffffffffu, hit);
-                if (hit) q[qn + __popc(mk & lt)] = (uint16_t)(ai | ((uint32_t)(p * 32 + lane) << 8));
-                qn += __popc(mk);
+                *head = (uint16_t)(ai | (p << 8));
+                head += hit ? 32 : 0;
             }
-            if (qn > QCAP - 32 * P) flush(qn);
         }
-        if (qn) flush(qn);
+        if (__any_sync(0xffffffffu, head != q + lane)) flush(head);
     }
 };
 
@@ -470,8 +499,9 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
         for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
     for (int i = tid; i < prm.nbin; i += blockDim.x) sm.hist[i] = 0;
 
-    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
-    cx.q = sm.queue + (size_t)cx.warp * QCAP;
+    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
+    cx.q = sm.queue + (size_t)cx.warp * QN * 32 * 2;
+    cx.cq = cx.q + QN * 32;
     cx.bc = sm.bcopy + (size_t)cx.warp * P * 32;
     unsigned long long n_cand = 0;
 
