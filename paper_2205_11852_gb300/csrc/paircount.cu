@@ -152,15 +152,49 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     return y;
 }
 
+// 32-bit shared-memory accesses (addresses from __cvta_generic_to_shared)
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void sts16(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((unsigned short)v) : "memory");
+}
+__device__ __forceinline__ uint32_t lds16(uint32_t a)
+{
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ float4 lds128(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_inc(uint32_t a)
+{
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a) : "memory");
+}
+
+// Binning constants, copied from the launch parameters into registers once.
+struct BinConst {
+    float tab_bias, inv_nmu2, s_scale, s_c0, s_c1, mu_c1, mu_c2, mu_c3, hit_max, dot_margin;
+    uint32_t tab_key0, tab_last;
+    int tab_shift, n_s, n_mu;
+};
+
 template <bool MU, bool MID, bool LIN>
 struct Ctx {
     const CountParams &prm;
     const Smem &sm;
     const Mesh &m;
+    BinConst c;
     int lane, warp;
-    uint16_t *q;               // this warp's queue
-    uint16_t *cq;              // this warp's compacted queue
-    float4 *bc;                // this warp's b copies (.w: b index)
+    uint32_t q;                // this lane's queue column (shared address of slot 0)
+    uint32_t cq;               // this warp's compacted queue (shared address)
+    uint32_t bc;               // this warp's b copies (shared address; .w: b index)
+    uint32_t abase;            // the a-chunk (shared address)
+    uint32_t hbase;            // the block histogram (shared address)
     uint32_t a0, na;           // current unit's a-chunk
     float gx, gy, gz;          // 2 (corner(A) - observer), midpoint line of sight
     unsigned n_exact, n_binned;
@@ -176,17 +210,17 @@ struct Ctx {
         if (LIN) {
             // s bin = floor(u), u = sqrt(d2) / (q ds); ambiguous near an interior
             // edge or near s_max
-            r = rsqrt_approx(__fmul_rn(d2, prm.inv_nmu2));      // n_mu / sqrt(d2)
-            const float u = __fmul_rn(__fmul_rn(d2, r), prm.s_scale);
+            r = rsqrt_approx(__fmul_rn(d2, c.inv_nmu2));      // n_mu / sqrt(d2)
+            const float u = __fmul_rn(__fmul_rn(d2, r), c.s_scale);
             const float mf = __fadd_rn(u, big);
             const int ki = __float_as_int(mf) - 0x4B400000;
             const float ds = __fsub_rn(u, __fsub_rn(mf, big));
-            amb = (fabsf(ds) < __fmaf_rn(prm.s_c1, u, prm.s_c0)) && ((unsigned)(ki - 1) < (unsigned)prm.n_s);
+            amb = (fabsf(ds) < __fmaf_rn(c.s_c1, u, c.s_c0)) && ((unsigned)(ki - 1) < (unsigned)c.n_s);
             k = ki - (ds < 0.0f ? 1 : 0);
-            valid = (unsigned)k < (unsigned)prm.n_s;
+            valid = (unsigned)k < (unsigned)c.n_s;
         } else {
-            const uint32_t key = min((__float_as_uint(__fadd_rn(d2, prm.tab_bias)) >> prm.tab_shift) - prm.tab_key0,
-                                     (uint32_t)(prm.tab_n - 1));
+            const uint32_t key = min((__float_as_uint(__fadd_rn(d2, c.tab_bias)) >> c.tab_shift) - c.tab_key0,
+                                     c.tab_last);
             k = sm.table[key];
             amb = (k == CODE_AMBIG);
             k = amb ? -1 : k;
@@ -194,15 +228,15 @@ struct Ctx {
             const bool ge_hi = d2 >= lh.y;
             amb |= (d2 >= lh.x) && !ge_hi;
             k += ge_hi ? 1 : 0;
-            valid = (unsigned)k < (unsigned)prm.n_s;
+            valid = (unsigned)k < (unsigned)c.n_s;
         }
         int bin = k;
         if (MU) {
             float t, beta;
             if (!MID) {
-                if (!LIN) r = rsqrt_approx(__fmul_rn(d2, prm.inv_nmu2));   // n_mu / sqrt(d2)
+                if (!LIN) r = rsqrt_approx(__fmul_rn(d2, c.inv_nmu2));   // n_mu / sqrt(d2)
                 t = __fmul_rn(fabsf(dx), r);
-                beta = __fmaf_rn(prm.mu_c1, r, prm.mu_c2);
+                beta = __fmaf_rn(c.mu_c1, r, c.mu_c2);
             } else {
                 const float ex = __fsub_rn(a.x, b.x), ey = __fsub_rn(a.y, b.y), ez = __fsub_rn(a.z, b.z);
                 const float lx = __fadd_rn(__fadd_rn(gx, a.x), b.x);
@@ -211,8 +245,8 @@ struct Ctx {
                 const float dot = __fmaf_rn(ez, lz, __fmaf_rn(ey, ly, __fmul_rn(ex, lx)));
                 const float l2 = __fmaf_rn(lz, lz, __fmaf_rn(ly, ly, __fmul_rn(lx, lx)));
                 const float rs = rsqrt_approx(d2), rl = rsqrt_approx(l2);
-                t = __fmul_rn(__fmul_rn(__fmul_rn(fabsf(dot), rs), rl), (float)prm.n_mu);
-                beta = __fmaf_rn(prm.mu_c1, rs, __fmaf_rn(prm.mu_c3, rl, prm.mu_c2));
+                t = __fmul_rn(__fmul_rn(__fmul_rn(fabsf(dot), rs), rl), (float)c.n_mu);
+                beta = __fmaf_rn(c.mu_c1, rs, __fmaf_rn(c.mu_c3, rl, c.mu_c2));
             }
             // the pair is ambiguous when t = n_mu |mu| lies within beta of an
             // interior mu edge 1..n_mu-1
@@ -220,9 +254,9 @@ struct Ctx {
             const int mi = __float_as_int(mf) - 0x4B400000;
             const float d = __fsub_rn(t, __fsub_rn(mf, big));
             amb |= !(beta < 0.05f);
-            amb |= (fabsf(d) < beta) && ((unsigned)(mi - 1) < (unsigned)(prm.n_mu - 1));
-            const int j = min(max(mi - (d < 0.0f ? 1 : 0), 0), prm.n_mu - 1);
-            bin = k * prm.n_mu + j;
+            amb |= (fabsf(d) < beta) && ((unsigned)(mi - 1) < (unsigned)(c.n_mu - 1));
+            const int j = min(max(mi - (d < 0.0f ? 1 : 0), 0), c.n_mu - 1);
+            bin = k * c.n_mu + j;
         } else if (LIN) {
             amb |= !(r < 3.0e38f);   // d2 == 0: r = inf, u = NaN
         }
@@ -233,50 +267,49 @@ struct Ctx {
     // warp-contiguous list (a index | b copy index << 8), so that the binning
     // loop runs with all lanes busy whatever the spread of per-lane counts.
     // Pairs that need the exact recheck are gathered (in place, behind the
-    // read position) and rechecked after the loop.
-    __device__ __forceinline__ void flush(uint16_t *&head)
+    // read position) and rechecked after the loop.  n = this lane's count.
+    __device__ __forceinline__ void flush(uint32_t n)
     {
-        const uint32_t n = (uint32_t)(head - (q + lane)) >> 5;
         uint32_t total;
         const uint32_t pos = warp_exclusive_sum(n, lane, total);
         const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
         for (uint32_t k = 0; k < nmax; k++)
             if (k < n) {
-                const uint32_t v = q[k * 32 + lane];   // a index | p << 8
-                cq[pos + k] = (uint16_t)((v & 255u) | ((((v >> 8) << 5) | lane) << 8));
+                const uint32_t v = lds16(q + k * 64u);   // a index | p << 8
+                sts16(cq + 2u * (pos + k), (v & 255u) | ((((v >> 8) << 5) | (uint32_t)lane) << 8));
             }
         __syncwarp();
         uint32_t n_amb = 0;
         for (uint32_t w0 = 0; w0 < total; w0 += 32) {
             const uint32_t e = w0 + lane;
             const bool live = e < total;
-            const uint32_t v = live ? cq[e] : 0u;
-            const uint32_t ai = v & 255u, bi = v >> 8;   // bi = p * 32 + owner lane = ib - base
-            const float4 a = sm.a[ai];
-            const float4 b = bc[bi];
+            const uint32_t v = live ? lds16(cq + 2u * e) : 0u;
+            const uint32_t ai = v & 255u, bi = v >> 8;   // bi = p * 32 + owner lane
+            const float4 a = lds128(abase + 16u * ai);
+            const float4 b = lds128(bc + 16u * bi);
             const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
             const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
             const int bin = live ? classify(d2, dx, a, b) : -1;
-            if (bin >= 0) atomicAdd(&sm.hist[bin], 1);
+            if (bin >= 0) red_inc(hbase + 4u * (uint32_t)bin);
             n_binned += (bin >= 0) ? 1u : 0u;
             const unsigned am = __ballot_sync(0xffffffffu, bin == -2);
             if (am) {
                 __syncwarp();
-                if (bin == -2) cq[n_amb + __popc(am & ((1u << lane) - 1u))] = (uint16_t)v;
+                if (bin == -2) sts16(cq + 2u * (n_amb + __popc(am & ((1u << lane) - 1u))), v);
                 n_amb += __popc(am);
             }
         }
         __syncwarp();
         for (uint32_t e = lane; e < n_amb; e += 32) {
-            const uint32_t v = cq[e];
-            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + (v & 255u), __float_as_uint(bc[v >> 8].w));
+            const uint32_t v = lds16(cq + 2u * e);
+            const float4 b = lds128(bc + 16u * (v >> 8));
+            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + (v & 255u), __float_as_uint(b.w));
             n_exact++;
             if (bin >= 0) {
-                atomicAdd(&sm.hist[bin], 1);
+                red_inc(hbase + 4u * (uint32_t)bin);
                 n_binned++;
             }
         }
-        head = q + lane;
         __syncwarp();
     }
 
@@ -293,13 +326,15 @@ struct Ctx {
             by[p] = __fadd_rn(v.y, sy);
             bz[p] = __fadd_rn(v.z, sz);
             const float b2 = __fmaf_rn(bz[p], bz[p], __fmaf_rn(by[p], by[p], __fmul_rn(bx[p], bx[p])));
-            hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, prm.hit_max)), prm.dot_margin);
+            hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, c.hit_max)), c.dot_margin);
         } else {
             bx[p] = by[p] = bz[p] = 0.0f;
             hb[p] = __int_as_float(0x7f800000);   // +inf: never passes
             i = 0;
         }
-        bc[p * 32 + lane] = make_float4(bx[p], by[p], bz[p], __uint_as_float(i));
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(bc + 16u * (uint32_t)(p * 32 + lane)),
+                     "f"(bx[p]), "f"(by[p]), "f"(bz[p]), "f"(__uint_as_float(i))
+                     : "memory");
     }
 
     // all pairs of the a-chunk with one tile of b-points: the self cell of an
@@ -334,45 +369,49 @@ struct Ctx {
             }
         }
         __syncwarp();
-        // Every candidate writes the head slot of the lane's queue; only a hit
-        // advances the head, so the stores stay branch-free.  A flush is forced
-        // before 2P more pushes could run past QN slots.
-        uint16_t *head = q + lane;
-        uint16_t *const lim = q + lane + (QN - 2 * P) * 32;
+        // Every candidate writes the head slot of the lane's queue column; only
+        // a hit advances the head (64 bytes: one slot of 32 lanes), so the
+        // stores stay branch-free.  A flush comes before 2P more pushes could
+        // run past QN slots.
+        uint32_t head = q;
+        const uint32_t lim = q + (uint32_t)(QN - 2 * P) * 64u;
         const uint32_t ib0 = base + lane;   // used by SELF tiles only
         uint32_t ai = 0;
         for (; ai + 1 < na; ai += 2) {
-            const float4 a = sm.a[ai], c = sm.a[ai + 1];
+            const float4 a = lds128(abase + 16u * ai), cc = lds128(abase + 16u * (ai + 1));
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                *head = (uint16_t)(ai | (p << 8));   // kept only on a hit
-                head += hit ? 32 : 0;
+                sts16(head, ai | (p << 8));   // kept only on a hit
+                head += hit ? 64u : 0u;
             }
 #pragma unroll
             for (int p = 0; p < P; p++) {
-                const float t = __fmaf_rn(c.x, bx[p], __fmaf_rn(c.y, by[p], __fmaf_rn(c.z, bz[p], c.w)));
+                const float t = __fmaf_rn(cc.x, bx[p], __fmaf_rn(cc.y, by[p], __fmaf_rn(cc.z, bz[p], cc.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai + 1 < ib0 + 32u * p);
-                *head = (uint16_t)((ai + 1) | (p << 8));
-                head += hit ? 32 : 0;
+                sts16(head, (ai + 1) | (p << 8));
+                head += hit ? 64u : 0u;
             }
-            if (__any_sync(0xffffffffu, head > lim)) flush(head);
+            if (__any_sync(0xffffffffu, head > lim)) {
+                flush((head - q) >> 6);
+                head = q;
+            }
         }
         if (ai < na) {
-            const float4 a = sm.a[ai];
+            const float4 a = lds128(abase + 16u * ai);
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                *head = (uint16_t)(ai | (p << 8));
-                head += hit ? 32 : 0;
+                sts16(head, ai | (p << 8));
+                head += hit ? 64u : 0u;
             }
         }
-        if (__any_sync(0xffffffffu, head != q + lane)) flush(head);
+        if (__any_sync(0xffffffffu, head != q)) flush((head - q) >> 6);
     }
 };
 
@@ -499,10 +538,29 @@ __global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_cons
         for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
     for (int i = tid; i < prm.nbin; i += blockDim.x) sm.hist[i] = 0;
 
-    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, nullptr, nullptr, nullptr, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
-    cx.q = sm.queue + (size_t)cx.warp * QN * 32 * 2;
-    cx.cq = cx.q + QN * 32;
-    cx.bc = sm.bcopy + (size_t)cx.warp * P * 32;
+    BinConst bcst;
+    bcst.tab_bias = prm.tab_bias;
+    bcst.inv_nmu2 = prm.inv_nmu2;
+    bcst.s_scale = prm.s_scale;
+    bcst.s_c0 = prm.s_c0;
+    bcst.s_c1 = prm.s_c1;
+    bcst.mu_c1 = prm.mu_c1;
+    bcst.mu_c2 = prm.mu_c2;
+    bcst.mu_c3 = prm.mu_c3;
+    bcst.hit_max = prm.hit_max;
+    bcst.dot_margin = prm.dot_margin;
+    bcst.tab_key0 = prm.tab_key0;
+    bcst.tab_last = (uint32_t)(prm.tab_n - 1);
+    bcst.tab_shift = prm.tab_shift;
+    bcst.n_s = prm.n_s;
+    bcst.n_mu = prm.n_mu;
+    Ctx<MU, MID, LIN> cx{prm, sm, m, bcst, tid & 31, tid >> 5, 0u, 0u, 0u, 0u, 0u, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
+    const uint32_t qw = saddr(sm.queue) + (uint32_t)cx.warp * (QN * 32 * 2 * 2);
+    cx.q = qw + 2u * (uint32_t)cx.lane;
+    cx.cq = qw + QN * 32 * 2;
+    cx.bc = saddr(sm.bcopy) + (uint32_t)cx.warp * (P * 32 * 16);
+    cx.abase = saddr(sm.a);
+    cx.hbase = saddr(sm.hist);
     unsigned long long n_cand = 0;
 
     // per-launch mode: this block walks the chunks of one cell of one term
