@@ -175,6 +175,41 @@ __device__ __forceinline__ void red_inc(uint32_t a)
 {
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a) : "memory");
 }
+// histogram increment when bin >= 0, without a branch
+__device__ __forceinline__ void red_inc_if(uint32_t base, int bin)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .u32 a;\n\t"
+        "setp.ge.s32 p, %1, 0;\n\t"
+        "mad.lo.u32 a, %1, 4, %0;\n\t"
+        "@p red.shared.add.u32 [a], 1;\n\t}" ::"r"(base),
+        "r"(bin)
+        : "memory");
+}
+// 16-bit shared load when live (else 0), without a branch
+__device__ __forceinline__ uint32_t lds16_if(uint32_t a, bool live)
+{
+    unsigned short v;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %2, 0;\n\t"
+        "mov.u16 %0, 0;\n\t"
+        "@p ld.shared.u16 %0, [%1];\n\t}"
+        : "=h"(v)
+        : "r"(a), "r"((int)live)
+        : "memory");
+    return v;
+}
+// 16-bit shared store when pred, without a branch
+__device__ __forceinline__ void sts16_if(uint32_t a, uint32_t v, bool pred)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %2, 0;\n\t"
+        "@p st.shared.u16 [%0], %1;\n\t}" ::"r"(a),
+        "h"((unsigned short)v), "r"((int)pred)
+        : "memory");
+}
 
 // Binning constants, copied from the launch parameters into registers once.
 struct BinConst {
@@ -266,36 +301,39 @@ struct Ctx {
     // Bin every queued pair.  The lanes' queues are first packed into one
     // warp-contiguous list (a index | b copy index << 8), so that the binning
     // loop runs with all lanes busy whatever the spread of per-lane counts.
-    // Pairs that need the exact recheck are gathered (in place, behind the
-    // read position) and rechecked after the loop.  n = this lane's count.
+    // Pairs that need the exact recheck are rechecked at the end.  n = this
+    // lane's count.
     __device__ __forceinline__ void flush(uint32_t n)
     {
         uint32_t total;
         const uint32_t pos = warp_exclusive_sum(n, lane, total);
         const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
-        for (uint32_t k = 0; k < nmax; k++)
-            if (k < n) {
-                const uint32_t v = lds16(q + k * 64u);   // a index | p << 8
-                sts16(cq + 2u * (pos + k), (v & 255u) | ((((v >> 8) << 5) | (uint32_t)lane) << 8));
-            }
+        for (uint32_t k = 0; k < nmax; k++) {
+            const bool mine = k < n;
+            const uint32_t v = lds16_if(q + k * 64u, mine);   // a index | p << 8
+            sts16_if(cq + 2u * (pos + k), (v & 255u) | ((((v >> 8) << 5) | (uint32_t)lane) << 8), mine);
+        }
         __syncwarp();
         uint32_t n_amb = 0;
         for (uint32_t w0 = 0; w0 < total; w0 += 32) {
             const uint32_t e = w0 + lane;
             const bool live = e < total;
-            const uint32_t v = live ? lds16(cq + 2u * e) : 0u;
+            const uint32_t v = lds16_if(cq + 2u * e, live);
             const uint32_t ai = v & 255u, bi = v >> 8;   // bi = p * 32 + owner lane
             const float4 a = lds128(abase + 16u * ai);
             const float4 b = lds128(bc + 16u * bi);
             const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
             const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-            const int bin = live ? classify(d2, dx, a, b) : -1;
-            if (bin >= 0) red_inc(hbase + 4u * (uint32_t)bin);
+            int bin = classify(d2, dx, a, b);
+            bin = live ? bin : -1;
+            red_inc_if(hbase, bin);
             n_binned += (bin >= 0) ? 1u : 0u;
             const unsigned am = __ballot_sync(0xffffffffu, bin == -2);
             if (am) {
+                // rare: keep the entry for the exact recheck, written over
+                // entries this loop has already consumed
                 __syncwarp();
-                if (bin == -2) sts16(cq + 2u * (n_amb + __popc(am & ((1u << lane) - 1u))), v);
+                sts16_if(cq + 2u * (n_amb + __popc(am & ((1u << lane) - 1u))), v, bin == -2);
                 n_amb += __popc(am);
             }
         }
