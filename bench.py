@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--subdiv", type=int, default=0, help="pin the mesh subdivision (0: library choice)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--smp-mocks", type=int, default=4,
+                   help="mocks of the brute-force (Smp, M=50) comparison run; 0 skips it")
     p.add_argument("--cov-only", action="store_true",
                    help="two split-precision LC covariances of 3500 mocks x 200 bins, then exit (profiler captures)")
     p.add_argument("--count-only", action="store_true",
@@ -189,6 +191,46 @@ def oracle_sample_rate(n_d, target_s, seed_mock=0):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"mocks_per_s": frac / dt, "seconds": dt, "rows": k, "fraction_of_mock": frac, "cores": cores,
             "pair_tests_per_s": tests / dt}
+
+
+def smp_measure(tp, ctx, dev, b, prec, n_mock, n_d, M=50, reps=2):
+    """Brute-force (Smp) path on the mid shape: every mock against all M random
+    subsets in one batched launch, LS over all subsets, sample covariance
+    (Eq. bruteforce).  Returns ms per step and the pair totals."""
+    import torch
+    w = synth.MID
+    mks = [w.make_mock(m, n_d=n_d, M=M) for m in range(n_mock)]
+    dm = [{"data": torch.from_numpy(mk.data).to(dev),
+           "randoms": torch.from_numpy(np.concatenate(mk.randoms)).to(dev),
+           "offsets": [i * n_d for i in range(M + 1)]} for mk in mks]
+    nbin = w.n_s * w.n_mu
+    out = {"dd": torch.empty((n_mock, nbin), dtype=torch.int64, device=dev),
+           "dr": torch.empty((n_mock, M, nbin), dtype=torch.int64, device=dev),
+           "rr": torch.empty((n_mock, M, nbin), dtype=torch.int64, device=dev)}
+    xi = torch.empty((n_mock, nbin), dtype=torch.float64, device=dev)
+    sel = list(range(M))
+    n_r = [[n_d] * M for _ in range(n_mock)]
+
+    def step():
+        ctx.tpcf_count(dm, b, mode=tp.TPCF_BATCHED, out=out)
+        ctx.tpcf_ls(out["dd"], out["dr"], out["rr"], [n_d] * n_mock, n_r, sel, out=xi)
+        return ctx.tpcf_sample_cov(xi, prec)
+
+    step()
+    torch.cuda.synchronize()
+    ctx.tpcf_set_timing(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    info = ctx.tpcf_last_count_info()
+    ctx.tpcf_set_timing(False)
+    rc = ctx.tpcf_sync()
+    return {"ms": e0.elapsed_time(e1) / reps, "n_binned": info["n_binned"], "n_candidates": info["n_candidates"],
+            "status": rc}
 
 
 def measured_traffic(n_mock):
@@ -439,6 +481,19 @@ def main():
             err = float(np.max(np.abs(out["C_lc"].cpu().numpy() - ref["C_lc"]) / scale))
             prec_cfg[name] = {"ms": c0.elapsed_time(c1) / reps, "max_err_vs_fp64_oracle": err}
 
+    # brute-force (Smp) comparison: the same mocks' shape with all M = 50 subsets
+    smp = None
+    if rank == 0 and world == 1 and args.smp_mocks >= 2:
+        r = smp_measure(tp, ctx, dev, b, prec, args.smp_mocks, n_d)
+        smp_rate = args.smp_mocks / (r["ms"] * 1e-3)
+        smp = {"workload": (f"{args.smp_mocks} mocks of the mid shape with M=50 random subsets of N_d each: "
+                            "DD, DR_1..50, RR_1..50 in one batched launch, LS over all 50, sample covariance"),
+               "value": smp_rate, "unit": "mocks/s", "ms_per_step": r["ms"],
+               "pairs_binned_per_mock": r["n_binned"] / args.smp_mocks,
+               "lc_over_smp_speed": value / smp_rate,
+               "lc_over_smp_binned_pairs": (r["n_binned"] / args.smp_mocks) / (n_binned / n_mock),
+               "paper_cost_ratio_1p3M_over_7": (1 + 3 * 50) / 7, "status": r["status"]}
+
     kernels_per_step = info["n_kernels"] + 3 + 4   # count + 3 LS + 4 covariance kernels
     if rank == 0:
         line = {
@@ -460,6 +515,7 @@ def main():
             "tuned": {"cell_subdiv": info["cell_subdiv"], "cells_per_axis": info["cells_per_axis"],
                       "unit_chunk": info["unit_chunk"], "graph_replay": bool(info["graph_replay"])},
             "precision_config": prec_cfg,
+            "smp_comparison": smp,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-op/s",
                          "frac": achieved / peak, "traffic": measured_traffic(n_mock),
                          "traffic_note": "ncu DRAM bytes of 2 mocks scaled to the launch's mocks",

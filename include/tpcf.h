@@ -181,6 +181,20 @@ int tpcf_lc_cov(tpcf_ctx *ctx, const double *xi_a1, const double *xi_a2, const d
                 double *C_lc, double *Ca, double *Cb, double *A, double *B, void *stream);
 
 /*
+ * Sample covariance of one correlation-function variant over the mocks,
+ * Eq. (bruteforce): C = 1/(N-1) sum_m (xi_m - mean)(xi_m - mean)^T.  This is
+ * the brute-force (Smp) estimate the LC covariance is compared with: xi from
+ * tpcf_ls over all M random subsets (Sect. 2.1, Sect. 3.2).
+ * Input xi: device float64 [n_mock][nbin]; output C: device float64
+ * [nbin][nbin] (caller-owned, fully overwritten).  `precision` as in
+ * tpcf_lc_cov.  Needs n_mock >= 2 and 1 <= nbin <= 65536 (TPCF_ERR_ARG
+ * otherwise); TPCF_ERR_NOMEM if the workspace cannot grow.  Enqueued on
+ * `stream`; returns without waiting.
+ */
+int tpcf_sample_cov(tpcf_ctx *ctx, const double *xi, int n_mock, int nbin, int precision, double *C,
+                    void *stream);
+
+/*
  * tpcf_lc_cov_noalloc -- tpcf_lc_cov in TPCF_FP64 that allocates nothing.
  * (A library addition; the paper has no counterpart.)
  *

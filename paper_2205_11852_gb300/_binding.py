@@ -34,7 +34,7 @@ TPCF_OPT_GRAPHS, TPCF_OPT_AUTOTUNE = 1, 2
 
 EXPORTED = ("tpcf_create", "tpcf_destroy", "tpcf_sync", "tpcf_last_error", "tpcf_count", "tpcf_ls",
             "tpcf_lc_cov", "tpcf_last_count_info", "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds",
-            "tpcf_lc_cov_noalloc", "tpcf_set_option")
+            "tpcf_lc_cov_noalloc", "tpcf_set_option", "tpcf_sample_cov")
 
 
 class TpcfError(RuntimeError):
@@ -89,6 +89,8 @@ def load_library() -> ctypes.CDLL:
     lib.tpcf_lc_cov_noalloc.restype = ctypes.c_int
     lib.tpcf_set_option.argtypes = [P, I, I]
     lib.tpcf_set_option.restype = ctypes.c_int
+    lib.tpcf_sample_cov.argtypes = [P, P, I, I, I, P, P]
+    lib.tpcf_sample_cov.restype = ctypes.c_int
     for name in ("tpcf_create", "tpcf_sync", "tpcf_count", "tpcf_ls", "tpcf_lc_cov", "tpcf_last_count_info",
                  "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds"):
         getattr(lib, name).restype = ctypes.c_int
@@ -251,3 +253,11 @@ class Context:
                                    _ptr(out.get("Cb")), _ptr(out.get("A")), _ptr(out.get("B")), _stream(stream))
         self._check(rc)
         return out
+
+    def tpcf_sample_cov(self, xi, precision=TPCF_FP64, stream=None):
+        """Sample covariance of xi [n_mock, nbin] over the mocks (Eq. bruteforce); float64 CUDA [nbin, nbin]."""
+        n_mock, nbin = xi.shape
+        C = torch.empty((nbin, nbin), dtype=torch.float64, device=xi.device)
+        self._check(self._lib.tpcf_sample_cov(self.handle, _ptr(xi), n_mock, nbin, int(precision), _ptr(C),
+                                              _stream(stream)))
+        return C

@@ -378,4 +378,31 @@ int tpcf_lc_cov(tpcf_ctx *ctx, const double *xi_a1, const double *xi_a2, const d
     return fail(ctx, TPCF_ERR_ARG, "bad precision");
 }
 
+int tpcf_sample_cov(tpcf_ctx *ctx, const double *xi, int n_mock, int nbin, int precision, double *C, void *stream)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!xi || !C) return fail(ctx, TPCF_ERR_ARG, "NULL argument");
+    if (n_mock < 2) return fail(ctx, TPCF_ERR_ARG, "n_mock must be >= 2");
+    if (nbin < 1 || nbin > 65536) return fail(ctx, TPCF_ERR_ARG, "bad nbin");
+    if (precision == TPCF_FP64) {
+        const size_t elems = (size_t)n_mock * nbin + (size_t)nbin + (size_t)nbin * nbin;
+        void *w;
+        if ((rc = ensure(ctx, "lc_work", elems * 8, &w))) return rc;
+        CK(launch_cov_fp64(xi, n_mock, nbin, (double *)w, C, s));
+        return TPCF_OK;
+    }
+    if (precision == TPCF_TF32X3 || precision == TPCF_BF16X3) {
+        const size_t bytes = lc_split_work_bytes(n_mock, nbin, precision, 1);
+        void *w;
+        if ((rc = ensure(ctx, "lc_split_work", bytes, &w))) return rc;
+        cudaError_t e = launch_cov_split(xi, n_mock, nbin, precision, w, bytes, C, ctx->status, s);
+        if (e == cudaErrorNotSupported) return fail(ctx, TPCF_ERR_ARG, "split-precision covariance unavailable");
+        CK(e);
+        return TPCF_OK;
+    }
+    return fail(ctx, TPCF_ERR_ARG, "bad precision");
+}
+
 }  // extern "C"

@@ -1,5 +1,6 @@
-// Split Landy-Szalay estimator (Sect. 2.1) and the linear-construction
-// covariance (Eqs. bruteforce, R1R2, LCdef) in float64.
+// Split Landy-Szalay estimator (Sect. 2.1), the sample covariance
+// (Eq. bruteforce) and the linear-construction covariance (Eqs. R1R2, LCdef)
+// in float64.
 #include <cmath>
 
 #include "tpcf_internal.h"
@@ -140,7 +141,30 @@ __global__ void combine_kernel(const double *__restrict__ G, int nbin, int n_moc
     }
 }
 
+// sample covariance of one variant, Eq. (bruteforce): C = G / (N - 1)
+__global__ void scale_kernel(const double *__restrict__ G, size_t nn, int n_mock, double *__restrict__ C)
+{
+    const double inv = 1.0 / (double)(n_mock - 1);
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x)
+        C[t] = G[t] * inv;
+}
+
 int blocks_for(size_t n, int threads) { return (int)std::min<size_t>((n + threads - 1) / threads, 152 * 16); }
+
+// float64 Gram products of n_var centred variants; returns G [n_var][nbin][nbin] inside work
+double *gram_fp64(const double *x0, const double *x1, const double *x2, int n_var, int n_mock, int nbin,
+                  double *work, cudaStream_t s)
+{
+    double *Y = work;
+    double *mean = Y + (size_t)n_var * n_mock * nbin;
+    double *G = mean + (size_t)n_var * nbin;
+    mean_kernel<<<dim3(std::max(1, (nbin + 127) / 128), n_var), 128, 0, s>>>(x0, x1, x2, n_mock, nbin, mean);
+    centre_kernel<<<dim3(std::max(1, blocks_for((size_t)n_mock * nbin, 256)), n_var), 256, 0, s>>>(
+        x0, x1, x2, n_mock, nbin, mean, Y);
+    const int nt = (nbin + GT - 1) / GT;
+    gram_fp64_kernel<<<dim3(nt, nt, n_var), 256, 0, s>>>(Y, n_mock, nbin, G);
+    return G;
+}
 
 }  // namespace
 
@@ -158,23 +182,32 @@ cudaError_t launch_lc_fp64(const double *xi_a1, const double *xi_a2, const doubl
                            double *work, int M_a, double M, double *C_lc, double *Ca, double *Cb, double *A,
                            double *B, cudaStream_t s)
 {
-    double *Y = work;
-    double *mean = Y + 3 * (size_t)n_mock * nbin;
-    double *G = mean + 3 * (size_t)nbin;
-    mean_kernel<<<dim3(std::max(1, (nbin + 127) / 128), 3), 128, 0, s>>>(xi_a1, xi_a2, xi_b, n_mock, nbin, mean);
-    centre_kernel<<<dim3(std::max(1, blocks_for((size_t)n_mock * nbin, 256)), 3), 256, 0, s>>>(
-        xi_a1, xi_a2, xi_b, n_mock, nbin, mean, Y);
-    const int nt = (nbin + GT - 1) / GT;
-    gram_fp64_kernel<<<dim3(nt, nt, 3), 256, 0, s>>>(Y, n_mock, nbin, G);
+    const double *G = gram_fp64(xi_a1, xi_a2, xi_b, 3, n_mock, nbin, work, s);
     combine_kernel<<<std::max(1, blocks_for((size_t)nbin * nbin, 256)), 256, 0, s>>>(G, nbin, n_mock, M_a, M, C_lc,
                                                                                      Ca, Cb, A, B);
     return cudaGetLastError();
 }
 
-cudaError_t launch_means(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
-                         double *mean, cudaStream_t s)
+cudaError_t launch_cov_fp64(const double *xi, int n_mock, int nbin, double *work, double *C, cudaStream_t s)
 {
-    mean_kernel<<<dim3(std::max(1, (nbin + 127) / 128), 3), 128, 0, s>>>(xi_a1, xi_a2, xi_b, n_mock, nbin, mean);
+    const double *G = gram_fp64(xi, xi, xi, 1, n_mock, nbin, work, s);
+    scale_kernel<<<std::max(1, blocks_for((size_t)nbin * nbin, 256)), 256, 0, s>>>(G, (size_t)nbin * nbin, n_mock,
+                                                                                  C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_means(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_var, int n_mock,
+                         int nbin, double *mean, cudaStream_t s)
+{
+    mean_kernel<<<dim3(std::max(1, (nbin + 127) / 128), n_var), 128, 0, s>>>(xi_a1, xi_a2, xi_b, n_mock, nbin,
+                                                                              mean);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(const double *G, int nbin, int n_mock, double *C, cudaStream_t s)
+{
+    scale_kernel<<<std::max(1, blocks_for((size_t)nbin * nbin, 256)), 256, 0, s>>>(G, (size_t)nbin * nbin, n_mock,
+                                                                                  C);
     return cudaGetLastError();
 }
 

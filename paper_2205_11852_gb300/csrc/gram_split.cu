@@ -357,16 +357,17 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
 }
 
 template <int PREC>
-size_t tiles_bytes(int n_mock, int nbin)
+size_t tiles_bytes(int n_mock, int nbin, int n_var)
 {
     const size_t n_rb = (nbin + TM - 1) / TM, n_ks = (n_mock + KS - 1) / KS;
-    return 3 * (size_t)Split<PREC>::PIECES * n_rb * n_ks * tile_bytes<PREC>();
+    return (size_t)n_var * Split<PREC>::PIECES * n_rb * n_ks * tile_bytes<PREC>();
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// n_var = 3: the LC covariance of (x0, x1, x2); n_var = 1: the sample covariance of x0 into C_lc
 template <int PREC>
-cudaError_t run(const double *x0, const double *x1, const double *x2, int n_mock, int nbin, void *work,
+cudaError_t run(const double *x0, const double *x1, const double *x2, int n_var, int n_mock, int nbin, void *work,
                 size_t work_bytes, int M_a, double M, double *C_lc, double *Ca, double *Cb, double *A, double *B,
                 int *status, cudaStream_t s)
 {
@@ -374,36 +375,35 @@ cudaError_t run(const double *x0, const double *x1, const double *x2, int n_mock
     if (n_ks > 65535 || n_rb > 90) return cudaErrorInvalidValue;
     unsigned char *w = (unsigned char *)work;
     unsigned char *tiles = w;
-    size_t o = al256(tiles_bytes<PREC>(n_mock, nbin));
+    size_t o = al256(tiles_bytes<PREC>(n_mock, nbin, n_var));
     double *G = (double *)(w + o);
-    o += al256(3 * (size_t)nbin * nbin * 8);
+    o += al256((size_t)n_var * nbin * nbin * 8);
     double *mean = (double *)(w + o);
-    o += al256(3 * (size_t)nbin * 8);
+    o += al256((size_t)n_var * nbin * 8);
     if (o > work_bytes) return cudaErrorInvalidValue;
-    cudaError_t e = launch_means(x0, x1, x2, n_mock, nbin, mean, s);
+    cudaError_t e = launch_means(x0, x1, x2, n_var, n_mock, nbin, mean, s);
     if (e != cudaSuccess) return e;
-    split_kernel<PREC><<<dim3(n_ks, n_rb, 3), 256, 0, s>>>(x0, x1, x2, mean, n_mock, nbin, n_rb, n_ks, tiles);
+    split_kernel<PREC><<<dim3(n_ks, n_rb, n_var), 256, 0, s>>>(x0, x1, x2, mean, n_mock, nbin, n_rb, n_ks, tiles);
     const int np = n_rb * (n_rb + 1) / 2;   // upper-triangle tile pairs
-    e = cudaMemsetAsync(G, 0, 3 * (size_t)nbin * nbin * 8, s);
+    e = cudaMemsetAsync(G, 0, (size_t)n_var * nbin * nbin * 8, s);
     if (e != cudaSuccess) return e;
     const int smem = std::max(2 * Split<PREC>::PIECES * tile_bytes<PREC>() + 64, GRAM_SMEM_MIN);
     e = cudaFuncSetAttribute(gram_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    gram_tc_kernel<PREC><<<dim3(np, 3, n_ks), GRAM_THREADS, smem, s>>>(tiles, nbin, n_rb, n_ks, G, status);
+    gram_tc_kernel<PREC><<<dim3(np, n_var, n_ks), GRAM_THREADS, smem, s>>>(tiles, nbin, n_rb, n_ks, G, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (n_var == 1) return launch_scale(G, nbin, n_mock, C_lc, s);
     return launch_combine(G, nbin, n_mock, M_a, M, C_lc, Ca, Cb, A, B, s);
 }
 
 }  // namespace
 
-size_t lc_split_work_bytes(int n_mock, int nbin, int precision)
+size_t lc_split_work_bytes(int n_mock, int nbin, int precision, int n_var)
 {
-    const size_t n_rb = (nbin + TM - 1) / TM;
-    const size_t t = precision == TPCF_BF16X3 ? tiles_bytes<TPCF_BF16X3>(n_mock, nbin)
-                                              : tiles_bytes<TPCF_TF32X3>(n_mock, nbin);
-    (void)n_rb;
-    return al256(t) + al256(3 * (size_t)nbin * nbin * 8) + al256(3 * (size_t)nbin * 8);
+    const size_t t = precision == TPCF_BF16X3 ? tiles_bytes<TPCF_BF16X3>(n_mock, nbin, n_var)
+                                              : tiles_bytes<TPCF_TF32X3>(n_mock, nbin, n_var);
+    return al256(t) + al256((size_t)n_var * nbin * nbin * 8) + al256((size_t)n_var * nbin * 8);
 }
 
 cudaError_t launch_lc_split(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
@@ -411,11 +411,23 @@ cudaError_t launch_lc_split(const double *xi_a1, const double *xi_a2, const doub
                             double *Ca, double *Cb, double *A, double *B, int *status, cudaStream_t s)
 {
     if (precision == TPCF_TF32X3)
-        return run<TPCF_TF32X3>(xi_a1, xi_a2, xi_b, n_mock, nbin, work, work_bytes, M_a, M, C_lc, Ca, Cb, A, B,
+        return run<TPCF_TF32X3>(xi_a1, xi_a2, xi_b, 3, n_mock, nbin, work, work_bytes, M_a, M, C_lc, Ca, Cb, A, B,
                                 status, s);
     if (precision == TPCF_BF16X3)
-        return run<TPCF_BF16X3>(xi_a1, xi_a2, xi_b, n_mock, nbin, work, work_bytes, M_a, M, C_lc, Ca, Cb, A, B,
+        return run<TPCF_BF16X3>(xi_a1, xi_a2, xi_b, 3, n_mock, nbin, work, work_bytes, M_a, M, C_lc, Ca, Cb, A, B,
                                 status, s);
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_cov_split(const double *xi, int n_mock, int nbin, int precision, void *work, size_t work_bytes,
+                             double *C, int *status, cudaStream_t s)
+{
+    if (precision == TPCF_TF32X3)
+        return run<TPCF_TF32X3>(xi, xi, xi, 1, n_mock, nbin, work, work_bytes, 1, 2.0, C, nullptr, nullptr,
+                                nullptr, nullptr, status, s);
+    if (precision == TPCF_BF16X3)
+        return run<TPCF_BF16X3>(xi, xi, xi, 1, n_mock, nbin, work, work_bytes, 1, 2.0, C, nullptr, nullptr,
+                                nullptr, nullptr, status, s);
     return cudaErrorNotSupported;
 }
 

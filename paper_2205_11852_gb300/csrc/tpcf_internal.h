@@ -133,12 +133,20 @@ cudaError_t launch_lc_fp64(const double *xi_a1, const double *xi_a2, const doubl
 cudaError_t launch_lc_split(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock,
                             int nbin, int precision, void *work, size_t work_bytes, int M_a, double M,
                             double *C_lc, double *Ca, double *Cb, double *A, double *B, int *status, cudaStream_t s);
-size_t lc_split_work_bytes(int n_mock, int nbin, int precision);
-// column means mean[3][nbin] of the three xi variants
-cudaError_t launch_means(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
-                         double *mean, cudaStream_t s);
+// work bytes of the split-precision path for n_var variants (3: LC, 1: one sample covariance)
+size_t lc_split_work_bytes(int n_mock, int nbin, int precision, int n_var = 3);
+// sample covariance C[nbin][nbin] of one variant xi[n_mock][nbin], Eq. (bruteforce)
+cudaError_t launch_cov_fp64(const double *xi, int n_mock, int nbin,
+                            double *work /* n_mock*nbin + nbin + nbin*nbin */, double *C, cudaStream_t s);
+cudaError_t launch_cov_split(const double *xi, int n_mock, int nbin, int precision, void *work, size_t work_bytes,
+                             double *C, int *status, cudaStream_t s);
+// column means mean[n_var][nbin] of the first n_var xi variants
+cudaError_t launch_means(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_var, int n_mock,
+                         int nbin, double *mean, cudaStream_t s);
 // LC combination from the three Gram blocks G[3][nbin][nbin] (float64)
 cudaError_t launch_combine(const double *G, int nbin, int n_mock, int M_a, double M, double *C_lc, double *Ca,
                            double *Cb, double *A, double *B, cudaStream_t s);
+// C = G / (n_mock - 1) for one Gram block
+cudaError_t launch_scale(const double *G, int nbin, int n_mock, double *C, cudaStream_t s);
 
 }  // namespace tpcf
