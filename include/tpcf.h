@@ -195,6 +195,48 @@ int tpcf_sample_cov(tpcf_ctx *ctx, const double *xi, int n_mock, int nbin, int p
                     void *stream);
 
 /*
+ * Linear maps applied before the covariance.  The LC construction holds for
+ * any linear function of the correlation function (Sect. 2.4): multipoles,
+ * the projected function, wider bins.  Apply the same map to xi_a1, xi_a2
+ * and xi_b, then call tpcf_lc_cov; the result is P C^LC P^T.
+ */
+
+/*
+ * Re-binning of pair counts into wider bins (Sect. 4.3: bins combined into
+ * wider ones, and the 1-D function from counts co-added over mu):
+ *   out[r][k'][j'] = sum_{k = f_s k'}^{f_s k' + f_s - 1} sum_{j = f_mu j'}^{f_mu j' + f_mu - 1} in[r][k][j]
+ * `in`: device int64 [rows][n_s][n_mu] (any stack of DD, DR_i, RR_i
+ * histograms, s-major); `out`: device int64 [rows][n_s/f_s][n_mu/f_mu].
+ * With half-open s bins and uniform |mu| bins the result equals counting
+ * with the merged edges directly.  f_s must divide n_s and f_mu divide n_mu
+ * (TPCF_ERR_ARG otherwise).  Enqueued on `stream`.
+ */
+int tpcf_rebin_counts(tpcf_ctx *ctx, const int64_t *in, int64_t rows, int n_s, int n_mu, int f_s, int f_mu,
+                      int64_t *out, void *stream);
+
+/*
+ * y[m][o] = sum_b P[o][b] xi[m][b] in float64: a linear map of every mock's
+ * xi row.  P: device float64 [n_out][nbin]; xi: device float64
+ * [n_mock][nbin]; y: device float64 [n_mock][n_out] (caller-owned, not
+ * aliasing xi).  Needs n_out, nbin >= 1 and 0 <= n_mock <= 2097120
+ * (TPCF_ERR_ARG otherwise).  Enqueued on `stream`.
+ */
+int tpcf_project(tpcf_ctx *ctx, const double *P, int n_out, int nbin, const double *xi, int n_mock, double *y,
+                 void *stream);
+
+/*
+ * Host-side: the matrix of the Legendre multipoles of Sect. 4.3,
+ *   xi_l(s) = (2l+1)/2 int_{-1}^{1} xi(s, mu) P_l(mu) dmu,
+ * for xi binned in n_s s bins x n_mu uniform |mu| bins on [0, 1] (s-major).
+ * Because xi depends on |mu| and l is even, the integral is twice the one
+ * on [0, 1], and over a bin (2l+1) int P_l = [P_{l+1} - P_{l-1}] (l >= 1),
+ * [mu] (l = 0).  Output P: HOST float64 [n_ell * n_s][n_s * n_mu], row
+ * (i, k) = multipole ells[i] at s bin k.  Each ells[i] must be even and in
+ * [0, 64] (odd multipoles vanish for |mu| bins); TPCF_ERR_ARG otherwise.
+ */
+int tpcf_multipole_matrix(int n_s, int n_mu, const int *ells, int n_ell, double *P);
+
+/*
  * tpcf_lc_cov_noalloc -- tpcf_lc_cov in TPCF_FP64 that allocates nothing.
  * (A library addition; the paper has no counterpart.)
  *

@@ -20,6 +20,9 @@ checkability rather than speed:
 * ``sample_cov`` -- the sample covariance, Eq. (bruteforce), two-pass float64.
 * ``lc_cov``     -- the linear construction: Eqs. (R1R2) and (LCdef).
 * ``cov_ab``     -- the two-size decomposition of Eq. (CovAB).
+* ``rebin_counts`` / ``multipole_matrix`` / ``project`` -- the linear maps
+                    applied before the covariance (Sect. 2.4, Sect. 4.3):
+                    bins combined into wider ones, the Legendre multipoles.
 
 Readings of the paper where it is silent (all listed in the design notes):
 bins are half-open [e_k, e_{k+1}); mu is |cos| in [0, 1] with the top bin
@@ -304,3 +307,49 @@ def cov_ab(C_Ma, C_Mb, M_a: float, M_b: float):
     A = (M_b / (M_b - M_a)) * C_Mb - (M_a / (M_b - M_a)) * C_Ma
     B = (M_a * M_b / (M_b - M_a)) * (C_Ma - C_Mb)
     return A, B
+
+
+# ---------------------------------------------------------------------------
+# Linear maps of the correlation function (Sect. 2.4, Sect. 4.3)
+# ---------------------------------------------------------------------------
+
+def rebin_counts(counts, n_s: int, n_mu: int, f_s: int, f_mu: int) -> np.ndarray:
+    """Pair counts [..., n_s * n_mu] combined into wider bins: groups of f_s
+    consecutive s bins and f_mu consecutive mu bins are summed."""
+    c = np.asarray(counts, dtype=np.int64)
+    if n_s % f_s or n_mu % f_mu:
+        raise ValueError("re-binning factors must divide the bin counts")
+    lead = c.shape[:-1]
+    out = np.zeros(lead + (n_s // f_s, n_mu // f_mu), dtype=np.int64)
+    c = c.reshape(lead + (n_s, n_mu))
+    for k in range(n_s):
+        for j in range(n_mu):
+            out[..., k // f_s, j // f_mu] += c[..., k, j]
+    return out.reshape(lead + ((n_s // f_s) * (n_mu // f_mu),))
+
+
+def multipole_matrix(n_s: int, n_mu: int, ells=(0, 2, 4)) -> np.ndarray:
+    """Matrix of the Legendre multipoles xi_l(s) = (2l+1)/2 int_{-1}^{1} xi(s, mu) P_l(mu) dmu
+    (Sect. 4.3) for xi binned in n_s x n_mu uniform |mu| bins on [0, 1].
+
+    xi(s, mu) is constant on each bin and depends on |mu|, so bin j of |mu|
+    covers [mu_j, mu_{j+1}] and [-mu_{j+1}, -mu_j]; the integral of P_l over
+    both pieces comes from numpy's Legendre antiderivative.
+    Rows (ell index, s bin), columns (s bin, mu bin).
+    """
+    from numpy.polynomial import legendre as npl
+    edges = np.arange(n_mu + 1, dtype=np.float64) / n_mu
+    P = np.zeros((len(ells) * n_s, n_s * n_mu))
+    for i, ell in enumerate(ells):
+        anti = npl.Legendre.basis(ell).integ()
+        for j in range(n_mu):
+            a, b = edges[j], edges[j + 1]
+            integral = (anti(b) - anti(a)) + (anti(-a) - anti(-b))
+            for k in range(n_s):
+                P[i * n_s + k, k * n_mu + j] = (2 * ell + 1) / 2.0 * integral
+    return P
+
+
+def project(P, xi) -> np.ndarray:
+    """Every mock's xi row mapped by P: y[m] = P xi[m]."""
+    return np.asarray(xi, dtype=np.float64) @ np.asarray(P, dtype=np.float64).T

@@ -34,7 +34,8 @@ TPCF_OPT_GRAPHS, TPCF_OPT_AUTOTUNE = 1, 2
 
 EXPORTED = ("tpcf_create", "tpcf_destroy", "tpcf_sync", "tpcf_last_error", "tpcf_count", "tpcf_ls",
             "tpcf_lc_cov", "tpcf_last_count_info", "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds",
-            "tpcf_lc_cov_noalloc", "tpcf_set_option", "tpcf_sample_cov")
+            "tpcf_lc_cov_noalloc", "tpcf_set_option", "tpcf_sample_cov", "tpcf_rebin_counts", "tpcf_project",
+            "tpcf_multipole_matrix")
 
 
 class TpcfError(RuntimeError):
@@ -91,6 +92,12 @@ def load_library() -> ctypes.CDLL:
     lib.tpcf_set_option.restype = ctypes.c_int
     lib.tpcf_sample_cov.argtypes = [P, P, I, I, I, P, P]
     lib.tpcf_sample_cov.restype = ctypes.c_int
+    lib.tpcf_rebin_counts.argtypes = [P, P, ctypes.c_int64, I, I, I, I, P, P]
+    lib.tpcf_rebin_counts.restype = ctypes.c_int
+    lib.tpcf_project.argtypes = [P, P, I, I, P, I, P, P]
+    lib.tpcf_project.restype = ctypes.c_int
+    lib.tpcf_multipole_matrix.argtypes = [I, I, P, I, P]
+    lib.tpcf_multipole_matrix.restype = ctypes.c_int
     for name in ("tpcf_create", "tpcf_sync", "tpcf_count", "tpcf_ls", "tpcf_lc_cov", "tpcf_last_count_info",
                  "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds"):
         getattr(lib, name).restype = ctypes.c_int
@@ -135,6 +142,17 @@ def tpcf_thresholds(binning) -> list:
     if rc != TPCF_OK:
         raise TpcfError(rc, "tpcf_thresholds failed")
     return [int(t) for t in T]
+
+
+def tpcf_multipole_matrix(n_s, n_mu, ells=(0, 2, 4)):
+    """Legendre multipole matrix [len(ells) * n_s, n_s * n_mu] (float64 numpy, host computation)."""
+    import numpy as np
+    ls = (ctypes.c_int * len(ells))(*[int(x) for x in ells])
+    P = np.empty((len(ells) * n_s, n_s * n_mu), dtype=np.float64)
+    rc = lib().tpcf_multipole_matrix(int(n_s), int(n_mu), ls, len(ells), ctypes.c_void_p(P.ctypes.data))
+    if rc != TPCF_OK:
+        raise TpcfError(rc, "tpcf_multipole_matrix failed")
+    return P
 
 
 class Context:
@@ -253,6 +271,27 @@ class Context:
                                    _ptr(out.get("Cb")), _ptr(out.get("A")), _ptr(out.get("B")), _stream(stream))
         self._check(rc)
         return out
+
+    def tpcf_rebin_counts(self, counts, n_s, n_mu, f_s, f_mu, stream=None):
+        """Counts [..., n_s * n_mu] (int64 CUDA) summed into [..., (n_s/f_s) * (n_mu/f_mu)] wider bins."""
+        lead = tuple(counts.shape[:-1])
+        rows = 1
+        for d in lead:
+            rows *= int(d)
+        out = torch.empty(lead + ((n_s // max(1, f_s)) * (n_mu // max(1, f_mu)),), dtype=torch.int64,
+                          device=counts.device)
+        self._check(self._lib.tpcf_rebin_counts(self.handle, _ptr(counts), rows, int(n_s), int(n_mu), int(f_s),
+                                                int(f_mu), _ptr(out), _stream(stream)))
+        return out
+
+    def tpcf_project(self, P, xi, stream=None):
+        """xi [n_mock, nbin] mapped by P [n_out, nbin] (float64 CUDA): returns [n_mock, n_out]."""
+        n_out, nbin = P.shape
+        n_mock = xi.shape[0]
+        y = torch.empty((n_mock, n_out), dtype=torch.float64, device=xi.device)
+        self._check(self._lib.tpcf_project(self.handle, _ptr(P), n_out, nbin, _ptr(xi), n_mock, _ptr(y),
+                                           _stream(stream)))
+        return y
 
     def tpcf_sample_cov(self, xi, precision=TPCF_FP64, stream=None):
         """Sample covariance of xi [n_mock, nbin] over the mocks (Eq. bruteforce); float64 CUDA [nbin, nbin]."""

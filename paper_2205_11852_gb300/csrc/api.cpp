@@ -405,4 +405,60 @@ int tpcf_sample_cov(tpcf_ctx *ctx, const double *xi, int n_mock, int nbin, int p
     return fail(ctx, TPCF_ERR_ARG, "bad precision");
 }
 
+int tpcf_rebin_counts(tpcf_ctx *ctx, const int64_t *in, int64_t rows, int n_s, int n_mu, int f_s, int f_mu,
+                      int64_t *out, void *stream)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (rows < 0 || n_s < 1 || n_mu < 1 || f_s < 1 || f_mu < 1 || n_s % f_s || n_mu % f_mu)
+        return fail(ctx, TPCF_ERR_ARG, "bad re-binning shape (factors must divide n_s and n_mu)");
+    if (rows > 0 && (!in || !out)) return fail(ctx, TPCF_ERR_ARG, "NULL argument");
+    CK(launch_rebin((const long long *)in, rows, n_s, n_mu, f_s, f_mu, (long long *)out, (cudaStream_t)stream));
+    return TPCF_OK;
+}
+
+int tpcf_project(tpcf_ctx *ctx, const double *P, int n_out, int nbin, const double *xi, int n_mock, double *y,
+                 void *stream)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (n_out < 1 || nbin < 1 || n_mock < 0 || n_mock > 65535 * 32) return fail(ctx, TPCF_ERR_ARG, "bad shape");
+    if (n_mock > 0 && (!P || !xi || !y)) return fail(ctx, TPCF_ERR_ARG, "NULL argument");
+    CK(launch_project(P, n_out, nbin, xi, n_mock, y, (cudaStream_t)stream));
+    return TPCF_OK;
+}
+
+int tpcf_multipole_matrix(int n_s, int n_mu, const int *ells, int n_ell, double *P)
+{
+    if (n_s < 1 || n_mu < 1 || n_ell < 1 || !ells || !P) return TPCF_ERR_ARG;
+    int lmax = 0;
+    for (int i = 0; i < n_ell; i++) {
+        if (ells[i] < 0 || ells[i] > 64 || (ells[i] & 1)) return TPCF_ERR_ARG;
+        lmax = std::max(lmax, ells[i]);
+    }
+    // Legendre values P_0 .. P_{lmax+1} at the n_mu + 1 uniform |mu| edges (Bonnet recurrence)
+    std::vector<double> leg((size_t)(n_mu + 1) * (lmax + 2));
+    for (int j = 0; j <= n_mu; j++) {
+        const double x = (double)j / n_mu;
+        double *L = &leg[(size_t)j * (lmax + 2)];
+        L[0] = 1.0;
+        if (lmax + 1 >= 1) L[1] = x;
+        for (int n = 1; n + 1 <= lmax + 1; n++) L[n + 1] = ((2.0 * n + 1.0) * x * L[n] - n * L[n - 1]) / (n + 1.0);
+    }
+    // xi_l(s_k) = (2l+1)/2 int_{-1}^{1} xi P_l dmu = (2l+1) sum_j xi_kj int_{mu_j}^{mu_j+1} P_l dmu (even l),
+    // with (2l+1) int P_l = [P_{l+1} - P_{l-1}] for l >= 1 and [mu] for l = 0
+    const size_t nbin = (size_t)n_s * n_mu;
+    std::fill(P, P + (size_t)n_ell * n_s * nbin, 0.0);
+    for (int i = 0; i < n_ell; i++) {
+        const int l = ells[i];
+        for (int j = 0; j < n_mu; j++) {
+            const double *L0 = &leg[(size_t)j * (lmax + 2)], *L1 = &leg[(size_t)(j + 1) * (lmax + 2)];
+            const double w = l == 0 ? (double)(j + 1) / n_mu - (double)j / n_mu
+                                    : (L1[l + 1] - L0[l + 1]) - (L1[l - 1] - L0[l - 1]);
+            for (int k = 0; k < n_s; k++) P[((size_t)i * n_s + k) * nbin + (size_t)k * n_mu + j] = w;
+        }
+    }
+    return TPCF_OK;
+}
+
 }  // extern "C"

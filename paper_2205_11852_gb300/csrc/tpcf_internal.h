@@ -149,4 +149,12 @@ cudaError_t launch_combine(const double *G, int nbin, int n_mock, int M_a, doubl
 // C = G / (n_mock - 1) for one Gram block
 cudaError_t launch_scale(const double *G, int nbin, int n_mock, double *C, cudaStream_t s);
 
+// ---- linear maps before the covariance (project.cu) ----
+// out[rows][n_s/f_s][n_mu/f_mu] = group sums of in[rows][n_s][n_mu] (int64)
+cudaError_t launch_rebin(const long long *in, long long rows, int n_s, int n_mu, int f_s, int f_mu, long long *out,
+                         cudaStream_t s);
+// y[n_mock][n_out] = x[n_mock][nbin] P^T, P [n_out][nbin] (float64)
+cudaError_t launch_project(const double *P, int n_out, int nbin, const double *x, int n_mock, double *y,
+                           cudaStream_t s);
+
 }  // namespace tpcf

@@ -71,3 +71,14 @@ def test_bad_binning_rejected_on_host(tp):
         tp.tpcf_thresholds(tp.make_binning([0.0, 2.0, 1.0], 1, tp.TPCF_PERIODIC, 100.0))
     with pytest.raises(tp.TpcfError):
         tp.tpcf_thresholds(tp.make_binning([0.0, 40.0], 1, tp.TPCF_PERIODIC, 100.0))  # s_max > L/3
+
+
+def test_multipole_matrix_matches_oracle(tp):
+    """The host-side Legendre multipole matrix of the C ABI against the oracle's (no GPU needed)."""
+    for n_s, n_mu, ells in ((1, 1, (0,)), (2, 4, (0, 2, 4)), (40, 10, (0, 2, 4)), (3, 100, (4, 0, 8))):
+        P = tp.tpcf_multipole_matrix(n_s, n_mu, ells)
+        ref = oracle.multipole_matrix(n_s, n_mu, ells)
+        assert np.max(np.abs(P - ref)) <= 1e-13
+    for bad in ((1,), (0, 3), (-2,), (66,)):
+        with pytest.raises(tp.TpcfError):
+            tp.tpcf_multipole_matrix(2, 4, bad)

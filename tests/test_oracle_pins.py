@@ -407,3 +407,67 @@ def test_lc_matches_poisson_theory():
     for mat, M, tol in ((lc["Ca"], 1, 0.16), (lc["Cb"], 2, 0.16), (lc["A"], math.inf, 0.35)):
         ratio = np.diag(mat) / (theory(M) if M != math.inf else 2.0 / (n * (n - 1)) / Gp)
         assert abs(ratio.mean() - 1.0) < tol, (M, ratio)
+
+
+# ---------------------------------------------------------------------------
+# linear maps: wider bins and Legendre multipoles (Sect. 2.4, Sect. 4.3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("f_s,f_mu", [(1, 1), (2, 3), (3, 6), (4, 1), (1, 2), (12, 6)])
+def test_rebin_counts_equals_counting_with_merged_edges(f_s, f_mu):
+    """Combining f_s consecutive half-open s bins and f_mu uniform |mu| bins must give exactly the counts
+    of a direct brute-force count with the merged edges (the bins partition the same integer ranges)."""
+    rng = np.random.default_rng(12)
+    L = 200.0
+    x = rng.random((700, 3)) * L
+    y = rng.random((500, 3)) * L
+    n_s, n_mu = 12, 6
+    fine = np.linspace(0.0, 48.0, n_s + 1)
+    bf = oracle.Binning(fine, n_mu, oracle.PERIODIC, L)
+    bc = oracle.Binning(fine[::f_s], n_mu // f_mu, oracle.PERIODIC, L)
+    qx, qy = oracle.quantize(x, oracle.PERIODIC, L), oracle.quantize(y, oracle.PERIODIC, L)
+    for ub in (None, qy):
+        h_f = oracle.count_pairs(qx, ub, bf)[0]
+        h_c = oracle.count_pairs(qx, ub, bc)[0]
+        assert h_c.sum() > 0
+        assert np.array_equal(oracle.rebin_counts(h_f, n_s, n_mu, f_s, f_mu), h_c)
+    stacked = np.stack([h_f, 2 * h_f])
+    assert np.array_equal(oracle.rebin_counts(stacked, n_s, n_mu, f_s, f_mu)[1], 2 * h_c)
+
+
+def test_multipole_matrix_closed_forms():
+    """Entries against the explicit polynomials P_2 = (3mu^2 - 1)/2, P_4 = (35mu^4 - 30mu^2 + 3)/8:
+    for |mu| bins, (2l+1)/2 int_{-1}^{1} doubles the [0, 1] integral."""
+    n_mu = 4
+    P = oracle.multipole_matrix(1, n_mu, (0, 2, 4))
+    a2 = lambda m: (m ** 3 - m) / 2.0                         # int_0^m P_2
+    a4 = lambda m: (7 * m ** 5 - 10 * m ** 3 + 3 * m) / 8.0    # int_0^m P_4
+    e = np.arange(n_mu + 1) / n_mu
+    for j in range(n_mu):
+        assert P[0, j] == pytest.approx(e[j + 1] - e[j], abs=1e-15)
+        assert P[1, j] == pytest.approx(5.0 * (a2(e[j + 1]) - a2(e[j])), abs=1e-14)
+        assert P[2, j] == pytest.approx(9.0 * (a4(e[j + 1]) - a4(e[j])), abs=1e-14)
+    assert P[1, 0] == pytest.approx(-0.5859375, abs=1e-15)    # 5 (1/64 - 1/4) / 2
+
+
+def test_multipole_matrix_invariants():
+    """A constant xi has only a monopole; odd multipoles of an |mu|-binned xi vanish; a xi made of the
+    bin averages of A_0 + A_2 P_2 + A_4 P_4 gives back (A_0, A_2, A_4) as the bins shrink."""
+    n_s, n_mu = 3, 200
+    P = oracle.multipole_matrix(n_s, n_mu, (0, 1, 2, 3, 4))
+    const = np.full(n_s * n_mu, 2.5)
+    m = P @ const
+    assert np.allclose(m[:n_s], 2.5, atol=1e-14) and np.allclose(m[n_s:], 0.0, atol=1e-13)
+    from numpy.polynomial import legendre as npl
+    A = {0: [1.0, -0.3, 4.0], 2: [0.5, 2.0, -1.0], 4: [-0.25, 0.1, 3.0]}
+    e = np.arange(n_mu + 1) / n_mu
+    xi = np.zeros(n_s * n_mu)
+    for ell, amps in A.items():
+        anti = npl.Legendre.basis(ell).integ()
+        avg = (anti(e[1:]) - anti(e[:-1])) * n_mu               # bin average of P_l on [mu_j, mu_j+1]
+        for k in range(n_s):
+            xi[k * n_mu:(k + 1) * n_mu] += amps[k] * avg
+    m = P @ xi
+    for i, ell in enumerate((0, 1, 2, 3, 4)):
+        want = np.array(A.get(ell, [0.0] * n_s))
+        assert np.allclose(m[i * n_s:(i + 1) * n_s], want, rtol=5e-4, atol=1e-4), ell   # O(dmu^2) error
