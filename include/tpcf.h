@@ -184,7 +184,7 @@ int tpcf_lc_cov(tpcf_ctx *ctx, const double *xi_a1, const double *xi_a2, const d
  * Sample covariance of one correlation-function variant over the mocks,
  * Eq. (bruteforce): C = 1/(N-1) sum_m (xi_m - mean)(xi_m - mean)^T.  This is
  * the brute-force (Smp) estimate the LC covariance is compared with: xi from
- * tpcf_ls over all M random subsets (Sect. 2.1, Sect. 3.2).
+ * tpcf_ls over all M random subsets (Sect. 2.1, Sect. 2.2).
  * Input xi: device float64 [n_mock][nbin]; output C: device float64
  * [nbin][nbin] (caller-owned, fully overwritten).  `precision` as in
  * tpcf_lc_cov.  Needs n_mock >= 2 and 1 <= nbin <= 65536 (TPCF_ERR_ARG
@@ -196,7 +196,7 @@ int tpcf_sample_cov(tpcf_ctx *ctx, const double *xi, int n_mock, int nbin, int p
 
 /*
  * Linear maps applied before the covariance.  The LC construction holds for
- * any linear function of the correlation function (Sect. 2.4): multipoles,
+ * any linear function of the correlation function (Sect. 2.3): multipoles,
  * the projected function, wider bins.  Apply the same map to xi_a1, xi_a2
  * and xi_b, then call tpcf_lc_cov; the result is P C^LC P^T.
  */
@@ -235,6 +235,50 @@ int tpcf_project(tpcf_ctx *ctx, const double *P, int n_out, int nbin, const doub
  * [0, 64] (odd multipoles vanish for |mu| bins); TPCF_ERR_ARG otherwise.
  */
 int tpcf_multipole_matrix(int n_s, int n_mu, const int *ells, int n_ell, double *P);
+
+/*
+ * Accuracy of a covariance estimate (Sect. 3), for Gaussian xi.
+ *
+ * tpcf_covcov_var: var[i][j] = Var(C_ij), the diagonal k = i, l = j of the
+ * covariance of covariance.
+ *   B != NULL -- LC covariance, Eq. (covcov_fast):
+ *     (N-1) Var = D_ii D_jj + D_ij^2 + (1/(2 M_a) - 1/M)^2 (B_ii B_jj + B_ij^2)
+ *     with A, B the LC components (Eq. CABdef; their estimates stand in for
+ *     the ensemble values, Sect. 3.3) and D = A + B / (2 M_a).  The paper
+ *     prints D = A + B / M_a; the form here follows from Eq. (covcov)
+ *     applied to Eq. (Cfastx) term by term, and is the one for which the two
+ *     forms (covcov_fast) and (covcov_fast2) agree and LC equals the sample
+ *     covariance at M = 2 M_a.
+ *   B == NULL -- sample covariance, Eq. (covcov_brute): A is the covariance C,
+ *     (N-1) Var = C_ii C_jj + C_ij^2.
+ * A, B: device float64 [nbin][nbin]; var: device float64 [nbin][nbin];
+ * n_mock = N >= 2.  With B: M_a >= 1 and M >= M_a (M = +INFINITY allowed).
+ *
+ * tpcf_chi2_predict: *chi2_2 (device float64 scalar) = the predicted
+ * <chi^2_2> of Sect. 5.3, (1/N_bin^2) sum_ij (N-1) Var(C_ij) / (R_ii R_jj),
+ * with (A, B) as in tpcf_covcov_var (B = NULL: sample covariance) and R =
+ * C_ref the normalising covariance.  <chi^2_N> = <chi^2_2> / (N - 1).
+ *
+ * tpcf_chi2: *chi2 (device scalar) = Eq. (chi2),
+ *   (1/N_bin^2) sum_ij (C_est,ij - C_true,ij)^2 / (C_ref,ii C_ref,jj).
+ *
+ * tpcf_eigvalsh: the eigenvalues w[n] (device float64, ascending) of the
+ * symmetric matrix C[n][n] (device float64; only symmetric input is
+ * meaningful), for checking that an LC covariance is positive definite
+ * before it is inverted (Sect. 3.4).  Householder reduction to tridiagonal
+ * form, then bisection on Sturm counts; absolute accuracy about n * 1e-16 *
+ * max|w|.  Needs 1 <= n <= 1024 (TPCF_ERR_ARG otherwise).
+ *
+ * All four enqueue on `stream` and return without waiting; they share the
+ * context's workspace, so calls on different streams must not overlap.
+ */
+int tpcf_covcov_var(tpcf_ctx *ctx, const double *A, const double *B, int nbin, int M_a, double M, int n_mock,
+                    double *var, void *stream);
+int tpcf_chi2_predict(tpcf_ctx *ctx, const double *A, const double *B, const double *C_ref, int nbin, int M_a,
+                      double M, double *chi2_2, void *stream);
+int tpcf_chi2(tpcf_ctx *ctx, const double *C_est, const double *C_true, const double *C_ref, int nbin, double *chi2,
+              void *stream);
+int tpcf_eigvalsh(tpcf_ctx *ctx, const double *C, int n, double *w, void *stream);
 
 /*
  * tpcf_lc_cov_noalloc -- tpcf_lc_cov in TPCF_FP64 that allocates nothing.

@@ -20,14 +20,18 @@ checkability rather than speed:
 * ``sample_cov`` -- the sample covariance, Eq. (bruteforce), two-pass float64.
 * ``lc_cov``     -- the linear construction: Eqs. (R1R2) and (LCdef).
 * ``cov_ab``     -- the two-size decomposition of Eq. (CovAB).
+* ``covcov_var`` / ``chi2_predict`` / ``chi2`` / ``eigvalsh`` -- accuracy of
+                    the covariance estimates (Sect. 3, Sect. 5.3).
 * ``rebin_counts`` / ``multipole_matrix`` / ``project`` -- the linear maps
-                    applied before the covariance (Sect. 2.4, Sect. 4.3):
+                    applied before the covariance (Sect. 2.3, Sect. 4.3):
                     bins combined into wider ones, the Legendre multipoles.
 
 Readings of the paper where it is silent (all listed in the design notes):
 bins are half-open [e_k, e_{k+1}); mu is |cos| in [0, 1] with the top bin
 closed; the random normalisations use the actual subset sizes N_r,i, which
-equals the paper's N_d form when N_r,i = N_d; rr = 0 gives xi = NaN.
+equals the paper's N_d form when N_r,i = N_d; rr = 0 gives xi = NaN.  In
+Eq. (covcov_fast) D = A + B / (2 M_a) (derived from Eqs. covcov and Cfastx;
+the printed D = A + B / M_a contradicts Eq. covcov_fast2).
 """
 from __future__ import annotations
 
@@ -310,7 +314,7 @@ def cov_ab(C_Ma, C_Mb, M_a: float, M_b: float):
 
 
 # ---------------------------------------------------------------------------
-# Linear maps of the correlation function (Sect. 2.4, Sect. 4.3)
+# Linear maps of the correlation function (Sect. 2.3, Sect. 4.3)
 # ---------------------------------------------------------------------------
 
 def rebin_counts(counts, n_s: int, n_mu: int, f_s: int, f_mu: int) -> np.ndarray:
@@ -353,3 +357,54 @@ def multipole_matrix(n_s: int, n_mu: int, ells=(0, 2, 4)) -> np.ndarray:
 def project(P, xi) -> np.ndarray:
     """Every mock's xi row mapped by P: y[m] = P xi[m]."""
     return np.asarray(xi, dtype=np.float64) @ np.asarray(P, dtype=np.float64).T
+
+
+# ---------------------------------------------------------------------------
+# Accuracy of the covariance estimates (Sect. 3, Sect. 5.3)
+# ---------------------------------------------------------------------------
+
+def covcov_var(A, B, n_mock: int, M_a: int = 1, M: float = math.inf) -> np.ndarray:
+    """Variance of every covariance element for Gaussian xi (k = i, l = j of the
+    covariance of covariance).
+
+    B given: the LC covariance, Eq. (covcov_fast),
+      (N-1) Var(C_ij) = D_ii D_jj + D_ij^2 + (1/(2 M_a) - 1/M)^2 (B_ii B_jj + B_ij^2).
+    D is the covariance of (x + x')/2, the xi of the 2 M_a random catalogue:
+    applying Eq. (covcov) to the four terms of Eq. (Cfastx) gives
+    D = A + B / (2 M_a) (the printed A + B / M_a disagrees with Eq.
+    covcov_fast2 and with the M = 2 M_a limit).
+    B None: the sample covariance C = A, Eq. (covcov_brute),
+      (N-1) Var(C_ij) = C_ii C_jj + C_ij^2.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    if B is None:
+        D = A
+        extra = np.zeros_like(A)
+    else:
+        B = np.asarray(B, dtype=np.float64)
+        D = A + B / (2.0 * M_a)
+        c = 1.0 / (2.0 * M_a) - 1.0 / float(M)
+        extra = c * c * (np.outer(np.diag(B), np.diag(B)) + B * B)
+    return (np.outer(np.diag(D), np.diag(D)) + D * D + extra) / (n_mock - 1)
+
+
+def chi2_predict(A, B, C_ref, M_a: int = 1, M: float = math.inf) -> float:
+    """Predicted <chi^2_2> (Sect. 5.3): (1/N_bin^2) sum_ij (N-1) Var(C_ij) / (R_ii R_jj)."""
+    R = np.asarray(C_ref, dtype=np.float64)
+    r = np.diag(R)
+    v = covcov_var(A, B, 2, M_a, M)       # N = 2: (N - 1) Var
+    return float(np.sum(v / np.outer(r, r)) / R.shape[0] ** 2)
+
+
+def chi2(C_est, C_true, C_ref) -> float:
+    """Eq. (chi2): (1/N_bin^2) sum_ij (C_est - C_true)_ij^2 / (C_ref,ii C_ref,jj)."""
+    E = np.asarray(C_est, dtype=np.float64)
+    T = np.asarray(C_true, dtype=np.float64)
+    r = np.diag(np.asarray(C_ref, dtype=np.float64))
+    return float(np.sum((E - T) ** 2 / np.outer(r, r)) / E.shape[0] ** 2)
+
+
+def eigvalsh(C) -> np.ndarray:
+    """Ascending eigenvalues of a symmetric matrix (LAPACK through numpy), the
+    eigenspectrum check recommended before inverting an LC covariance (Sect. 3.4)."""
+    return np.linalg.eigvalsh(np.asarray(C, dtype=np.float64))

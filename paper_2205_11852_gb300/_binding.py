@@ -35,7 +35,7 @@ TPCF_OPT_GRAPHS, TPCF_OPT_AUTOTUNE = 1, 2
 EXPORTED = ("tpcf_create", "tpcf_destroy", "tpcf_sync", "tpcf_last_error", "tpcf_count", "tpcf_ls",
             "tpcf_lc_cov", "tpcf_last_count_info", "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds",
             "tpcf_lc_cov_noalloc", "tpcf_set_option", "tpcf_sample_cov", "tpcf_rebin_counts", "tpcf_project",
-            "tpcf_multipole_matrix")
+            "tpcf_multipole_matrix", "tpcf_covcov_var", "tpcf_chi2_predict", "tpcf_chi2", "tpcf_eigvalsh")
 
 
 class TpcfError(RuntimeError):
@@ -98,6 +98,12 @@ def load_library() -> ctypes.CDLL:
     lib.tpcf_project.restype = ctypes.c_int
     lib.tpcf_multipole_matrix.argtypes = [I, I, P, I, P]
     lib.tpcf_multipole_matrix.restype = ctypes.c_int
+    lib.tpcf_covcov_var.argtypes = [P, P, P, I, I, D, I, P, P]
+    lib.tpcf_chi2_predict.argtypes = [P, P, P, P, I, I, D, P, P]
+    lib.tpcf_chi2.argtypes = [P, P, P, P, I, P, P]
+    lib.tpcf_eigvalsh.argtypes = [P, P, I, P, P]
+    for name in ("tpcf_covcov_var", "tpcf_chi2_predict", "tpcf_chi2", "tpcf_eigvalsh"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("tpcf_create", "tpcf_sync", "tpcf_count", "tpcf_ls", "tpcf_lc_cov", "tpcf_last_count_info",
                  "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds"):
         getattr(lib, name).restype = ctypes.c_int
@@ -292,6 +298,35 @@ class Context:
         self._check(self._lib.tpcf_project(self.handle, _ptr(P), n_out, nbin, _ptr(xi), n_mock, _ptr(y),
                                            _stream(stream)))
         return y
+
+    def tpcf_covcov_var(self, A, B, n_mock, M_a=1, M=math.inf, stream=None):
+        """Var(C_ij) [nbin, nbin]: LC form from (A, B), or the sample-covariance form from C = A when B is None."""
+        nbin = A.shape[0]
+        var = torch.empty((nbin, nbin), dtype=torch.float64, device=A.device)
+        self._check(self._lib.tpcf_covcov_var(self.handle, _ptr(A), _ptr(B), nbin, int(M_a), float(M), int(n_mock),
+                                              _ptr(var), _stream(stream)))
+        return var
+
+    def tpcf_chi2_predict(self, A, B, C_ref, M_a=1, M=math.inf, stream=None):
+        """Predicted <chi^2_2> (device scalar tensor) of the LC (B given) or sample (B None) covariance."""
+        out = torch.empty((), dtype=torch.float64, device=A.device)
+        self._check(self._lib.tpcf_chi2_predict(self.handle, _ptr(A), _ptr(B), _ptr(C_ref), A.shape[0], int(M_a),
+                                                float(M), _ptr(out), _stream(stream)))
+        return out
+
+    def tpcf_chi2(self, C_est, C_true, C_ref, stream=None):
+        """chi^2 of Eq. (chi2) (device scalar tensor)."""
+        out = torch.empty((), dtype=torch.float64, device=C_est.device)
+        self._check(self._lib.tpcf_chi2(self.handle, _ptr(C_est), _ptr(C_true), _ptr(C_ref), C_est.shape[0],
+                                        _ptr(out), _stream(stream)))
+        return out
+
+    def tpcf_eigvalsh(self, C, stream=None):
+        """Ascending eigenvalues of the symmetric float64 CUDA matrix C."""
+        n = C.shape[0]
+        w = torch.empty((n,), dtype=torch.float64, device=C.device)
+        self._check(self._lib.tpcf_eigvalsh(self.handle, _ptr(C), n, _ptr(w), _stream(stream)))
+        return w
 
     def tpcf_sample_cov(self, xi, precision=TPCF_FP64, stream=None):
         """Sample covariance of xi [n_mock, nbin] over the mocks (Eq. bruteforce); float64 CUDA [nbin, nbin]."""

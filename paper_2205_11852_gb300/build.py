@@ -20,7 +20,7 @@ BUILD = PKG / "_build"
 LIB = BUILD / "libtpcf.so"
 
 SOURCES = ["api.cpp", "count.cpp", "plan.cpp", "mesh.cu", "paircount.cu", "estimator.cu", "gram_split.cu", "noalloc.cu",
-           "project.cu"]
+           "project.cu", "covcov.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -428,6 +428,57 @@ int tpcf_project(tpcf_ctx *ctx, const double *P, int n_out, int nbin, const doub
     return TPCF_OK;
 }
 
+int tpcf_covcov_var(tpcf_ctx *ctx, const double *A, const double *B, int nbin, int M_a, double M, int n_mock,
+                    double *var, void *stream)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!A || !var) return fail(ctx, TPCF_ERR_ARG, "NULL argument");
+    if (nbin < 1 || nbin > 65536 || n_mock < 2) return fail(ctx, TPCF_ERR_ARG, "bad shape");
+    if (B && (M_a < 1 || !(M >= (double)M_a))) return fail(ctx, TPCF_ERR_ARG, "need M_a >= 1 and M >= M_a");
+    CK(launch_covcov(A, B, nbin, M_a, M, n_mock, var, (cudaStream_t)stream));
+    return TPCF_OK;
+}
+
+int tpcf_chi2_predict(tpcf_ctx *ctx, const double *A, const double *B, const double *C_ref, int nbin, int M_a,
+                      double M, double *chi2_2, void *stream)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!A || !C_ref || !chi2_2) return fail(ctx, TPCF_ERR_ARG, "NULL argument");
+    if (nbin < 1 || nbin > 65536) return fail(ctx, TPCF_ERR_ARG, "bad nbin");
+    if (B && (M_a < 1 || !(M >= (double)M_a))) return fail(ctx, TPCF_ERR_ARG, "need M_a >= 1 and M >= M_a");
+    void *w;
+    if ((rc = ensure(ctx, "chi2_work", chi2_work_bytes(), &w))) return rc;
+    CK(launch_chi2(0, A, B, C_ref, nbin, M_a, M, (double *)w, chi2_2, (cudaStream_t)stream));
+    return TPCF_OK;
+}
+
+int tpcf_chi2(tpcf_ctx *ctx, const double *C_est, const double *C_true, const double *C_ref, int nbin, double *chi2,
+              void *stream)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!C_est || !C_true || !C_ref || !chi2) return fail(ctx, TPCF_ERR_ARG, "NULL argument");
+    if (nbin < 1 || nbin > 65536) return fail(ctx, TPCF_ERR_ARG, "bad nbin");
+    void *w;
+    if ((rc = ensure(ctx, "chi2_work", chi2_work_bytes(), &w))) return rc;
+    CK(launch_chi2(1, C_est, C_true, C_ref, nbin, 1, 2.0, (double *)w, chi2, (cudaStream_t)stream));
+    return TPCF_OK;
+}
+
+int tpcf_eigvalsh(tpcf_ctx *ctx, const double *C, int n, double *w, void *stream)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!C || !w) return fail(ctx, TPCF_ERR_ARG, "NULL argument");
+    if (n < 1 || n > 1024) return fail(ctx, TPCF_ERR_ARG, "eigenvalues need 1 <= n <= 1024");
+    void *wk;
+    if ((rc = ensure(ctx, "eig_work", eig_work_bytes(n), &wk))) return rc;
+    CK(launch_eigvalsh(C, n, (double *)wk, w, (cudaStream_t)stream));
+    return TPCF_OK;
+}
+
 int tpcf_multipole_matrix(int n_s, int n_mu, const int *ells, int n_ell, double *P)
 {
     if (n_s < 1 || n_mu < 1 || n_ell < 1 || !ells || !P) return TPCF_ERR_ARG;

@@ -1,0 +1,263 @@
+// Accuracy of the covariance estimates (Sect. 3): the covariance of the
+// sample and LC covariances for Gaussian xi (Eqs. covcov, covcov_brute,
+// covcov_fast), the chi^2 accuracy measure of Eq. (chi2) and its predicted
+// value, and the eigenvalues of a symmetric matrix, used to check whether an
+// LC covariance is positive definite before it is inverted (Sect. 3.4).
+#include <algorithm>
+#include <cmath>
+
+#include "tpcf_internal.h"
+
+namespace tpcf {
+namespace {
+
+// Variance of each covariance element, Eq. (covcov_fast) at k = i, l = j:
+//   (N-1) Var(C_ij) = D_ii D_jj + D_ij^2 + c^2 (B_ii B_jj + B_ij^2)
+// D = A + w B.  LC: w = 1/(2 M_a), c = 1/(2 M_a) - 1/M.  Sample covariance,
+// Eq. (covcov_brute): B absent (c = 0) and A = C.
+__device__ __forceinline__ double covcov_term(const double *A, const double *B, int n, int i, int j, double w,
+                                              double c2)
+{
+    const size_t ii = (size_t)i * n + i, jj = (size_t)j * n + j, ij = (size_t)i * n + j;
+    double dii = A[ii], djj = A[jj], dij = A[ij];
+    double t = 0.0;
+    if (B) {
+        const double bii = B[ii], bjj = B[jj], bij = B[ij];
+        dii = fma(w, bii, dii);
+        djj = fma(w, bjj, djj);
+        dij = fma(w, bij, dij);
+        t = c2 * fma(bii, bjj, bij * bij);
+    }
+    return fma(dii, djj, dij * dij) + t;
+}
+
+__global__ void covcov_kernel(const double *__restrict__ A, const double *__restrict__ B, int n, double w, double c2,
+                              double inv_nm1, double *__restrict__ var)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x)
+        var[t] = covcov_term(A, B, n, (int)(t / n), (int)(t % n), w, c2) * inv_nm1;
+}
+
+constexpr int RED_BLOCKS = 152 * 2, RED_THREADS = 256;
+
+// sum over the block (blockDim.x a multiple of 32, at most 1024), in a fixed
+// order; the result is valid in thread 0
+__device__ double block_sum(double v)
+{
+    __shared__ double part[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += part[k];
+    __syncthreads();
+    return s;
+}
+
+// per-block partial sums over (i, j) of a normalised term:
+//   mode 0: covcov_term / (R_ii R_jj)                 (predicted chi^2_2)
+//   mode 1: (X_ij - Y_ij)^2 / (R_ii R_jj)             (measured chi^2, Eq. chi2)
+__global__ void __launch_bounds__(RED_THREADS) chi2_partial(int mode, const double *__restrict__ X,
+                                                            const double *__restrict__ Y, const double *__restrict__ R,
+                                                            int n, double w, double c2, double *__restrict__ part)
+{
+    const size_t nn = (size_t)n * n;
+    double s = 0.0;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n), j = (int)(t % n);
+        const double norm = R[(size_t)i * n + i] * R[(size_t)j * n + j];
+        double v;
+        if (mode == 0) {
+            v = covcov_term(X, Y, n, i, j, w, c2);
+        } else {
+            const double d = X[t] - Y[t];
+            v = d * d;
+        }
+        s += v / norm;
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(RED_THREADS) chi2_final(const double *__restrict__ part, int n_part, double scale,
+                                                          double *__restrict__ out)
+{
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n_part; k += blockDim.x) s += part[k];
+    s = block_sum(s);
+    if (threadIdx.x == 0) *out = s * scale;
+}
+
+// ---- eigenvalues of a symmetric matrix ----
+constexpr int EIG_THREADS = 1024;
+
+// Householder reduction of the symmetric matrix a[n][n] (overwritten) to
+// tridiagonal form d[n], e[n-1], by one thread block: for each column k the
+// reflector H = I - beta v v^T zeroes a[k+2.., k] and the trailing block B
+// becomes H B H = B - v w^T - w v^T with p = beta B v, w = p - (beta p.v / 2) v.
+__global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double *__restrict__ a, int n, double *__restrict__ d,
+                                                              double *__restrict__ e)
+{
+    extern __shared__ double sh[];
+    double *v = sh;            // [n]
+    double *p = sh + n;        // [n]
+    __shared__ double s_alpha, s_beta, s_k;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k + 2 < n; k++) {
+        const int m0 = k + 1;   // the reflector acts on rows/cols m0..n-1
+        // x = a[m0.., k]; alpha = -sign(x0) |x|
+        double ss = 0.0;
+        for (int i = m0 + 1 + tid; i < n; i += blockDim.x) {
+            const double x = a[(size_t)i * n + k];
+            ss = fma(x, x, ss);
+        }
+        const double tail = block_sum(ss);
+        if (tid == 0) {
+            const double x0 = a[(size_t)m0 * n + k];
+            if (tail == 0.0) {
+                s_alpha = x0;      // column already reduced: H = I
+                s_beta = 0.0;
+            } else {
+                const double nx = sqrt(fma(x0, x0, tail));
+                const double alpha = x0 > 0.0 ? -nx : nx;
+                const double v0 = x0 - alpha;
+                s_alpha = alpha;
+                s_beta = 2.0 / fma(v0, v0, tail);   // 2 / (v.v)
+                v[m0] = v0;
+            }
+        }
+        __syncthreads();
+        const double beta = s_beta;
+        if (tid == 0) {
+            d[k] = a[(size_t)k * n + k];
+            e[k] = s_alpha;
+        }
+        if (beta == 0.0) {
+            __syncthreads();
+            continue;
+        }
+        for (int i = m0 + 1 + tid; i < n; i += blockDim.x) v[i] = a[(size_t)i * n + k];
+        __syncthreads();
+        // p = beta B v, one warp per row
+        for (int i = m0 + warp; i < n; i += nw) {
+            const double *row = a + (size_t)i * n;
+            double s = 0.0;
+            for (int j = m0 + lane; j < n; j += 32) s = fma(row[j], v[j], s);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) p[i] = beta * s;
+        }
+        __syncthreads();
+        double pv = 0.0;
+        for (int i = m0 + tid; i < n; i += blockDim.x) pv = fma(p[i], v[i], pv);
+        pv = block_sum(pv);
+        if (tid == 0) s_k = 0.5 * beta * pv;
+        __syncthreads();
+        const double K = s_k;
+        for (int i = m0 + tid; i < n; i += blockDim.x) p[i] = fma(-K, v[i], p[i]);   // p becomes w
+        __syncthreads();
+        const int m = n - m0;
+        for (int t = tid; t < m * m; t += blockDim.x) {
+            const int i = m0 + t / m, j = m0 + t % m;
+            double *x = a + (size_t)i * n + j;
+            *x = fma(-v[i], p[j], fma(-p[i], v[j], *x));
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (n >= 2) {
+            d[n - 2] = a[(size_t)(n - 2) * n + (n - 2)];
+            e[n - 2] = a[(size_t)(n - 1) * n + (n - 2)];
+        }
+        d[n - 1] = a[(size_t)(n - 1) * n + (n - 1)];
+    }
+}
+
+// number of eigenvalues of the tridiagonal (d, e) below x (Sturm sequence)
+__device__ int sturm_count(const double *d, const double *e, int n, double x, double tiny)
+{
+    int c = 0;
+    double q = d[0] - x;
+    if (q == 0.0) q = -tiny;
+    c += q < 0.0;
+    for (int i = 1; i < n; i++) {
+        q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
+        if (q == 0.0) q = -tiny;
+        c += q < 0.0;
+    }
+    return c;
+}
+
+// eigenvalue i (ascending) by bisection on the Sturm count within the
+// Gershgorin interval; at most 200 halvings
+__global__ void bisect_kernel(const double *__restrict__ d, const double *__restrict__ e, int n,
+                              double *__restrict__ w)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double lo = INFINITY, hi = -INFINITY, nrm = 0.0;
+    for (int k = 0; k < n; k++) {
+        const double r = (k > 0 ? fabs(e[k - 1]) : 0.0) + (k + 1 < n ? fabs(e[k]) : 0.0);
+        lo = fmin(lo, d[k] - r);
+        hi = fmax(hi, d[k] + r);
+        nrm = fmax(nrm, fabs(d[k]) + r);
+    }
+    const double tiny = fmax(nrm, 1e-300) * 1e-300;
+    const double pad = fmax(nrm, 1e-300) * 4e-16 * n;
+    lo -= pad;
+    hi += pad;
+    for (int it = 0; it < 200; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_count(d, e, n, mid, tiny) > i)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    w[i] = 0.5 * (lo + hi);
+}
+
+int blocks_for(size_t n, int threads) { return (int)std::max<size_t>(1, std::min<size_t>((n + threads - 1) / threads, 152 * 16)); }
+
+}  // namespace
+
+cudaError_t launch_covcov(const double *A, const double *B, int nbin, int M_a, double M, int n_mock, double *var,
+                          cudaStream_t s)
+{
+    const double w = B ? 0.5 / M_a : 0.0;
+    const double c = B ? 0.5 / M_a - 1.0 / M : 0.0;
+    covcov_kernel<<<blocks_for((size_t)nbin * nbin, 256), 256, 0, s>>>(A, B, nbin, w, c * c,
+                                                                        1.0 / (double)(n_mock - 1), var);
+    return cudaGetLastError();
+}
+
+size_t chi2_work_bytes() { return RED_BLOCKS * sizeof(double); }
+
+cudaError_t launch_chi2(int mode, const double *X, const double *Y, const double *R, int nbin, int M_a, double M,
+                        double *work, double *out, cudaStream_t s)
+{
+    double w = 0.0, c = 0.0;
+    if (mode == 0 && Y) {
+        w = 0.5 / M_a;
+        c = 0.5 / M_a - 1.0 / M;
+    }
+    const int nb = std::min(RED_BLOCKS, blocks_for((size_t)nbin * nbin, RED_THREADS));
+    chi2_partial<<<nb, RED_THREADS, 0, s>>>(mode, X, Y, R, nbin, w, c * c, work);
+    chi2_final<<<1, RED_THREADS, 0, s>>>(work, nb, 1.0 / ((double)nbin * nbin), out);
+    return cudaGetLastError();
+}
+
+size_t eig_work_bytes(int n) { return ((size_t)n * n + 2 * (size_t)n) * sizeof(double); }
+
+cudaError_t launch_eigvalsh(const double *C, int n, double *work, double *w, cudaStream_t s)
+{
+    double *a = work, *d = work + (size_t)n * n, *e = d + n;
+    cudaError_t err = cudaMemcpyAsync(a, C, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (err != cudaSuccess) return err;
+    tridiag_kernel<<<1, EIG_THREADS, 2 * (size_t)n * sizeof(double), s>>>(a, n, d, e);
+    bisect_kernel<<<(n + 127) / 128, 128, 0, s>>>(d, e, n, w);
+    return cudaGetLastError();
+}
+
+}  // namespace tpcf

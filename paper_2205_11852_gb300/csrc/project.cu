@@ -1,4 +1,4 @@
-// Linear maps applied before the covariance (Sect. 2.4: the LC construction
+// Linear maps applied before the covariance (Sect. 2.3: the LC construction
 // holds for any linear function of the correlation function): re-binning of
 // the pair counts into wider (s, mu) bins, and projection of xi rows with a
 // matrix, e.g. onto the Legendre multipoles of Sect. 4.3.

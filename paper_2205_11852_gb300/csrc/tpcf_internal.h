@@ -157,4 +157,16 @@ cudaError_t launch_rebin(const long long *in, long long rows, int n_s, int n_mu,
 cudaError_t launch_project(const double *P, int n_out, int nbin, const double *x, int n_mock, double *y,
                            cudaStream_t s);
 
+// ---- accuracy of the covariance estimates (covcov.cu) ----
+// var[i][j] = Var(C_ij): LC form with B (D = A + B / (2 M_a)), sample-covariance form with B = NULL (A = C)
+cudaError_t launch_covcov(const double *A, const double *B, int nbin, int M_a, double M, int n_mock, double *var,
+                          cudaStream_t s);
+size_t chi2_work_bytes();
+// mode 0: predicted chi^2_2 from (X = A, Y = B or NULL); mode 1: measured chi^2 of X against Y; R normalises
+cudaError_t launch_chi2(int mode, const double *X, const double *Y, const double *R, int nbin, int M_a, double M,
+                        double *work, double *out, cudaStream_t s);
+size_t eig_work_bytes(int n);
+// ascending eigenvalues w[n] of the symmetric C[n][n] (n <= 1024)
+cudaError_t launch_eigvalsh(const double *C, int n, double *work, double *w, cudaStream_t s);
+
 }  // namespace tpcf

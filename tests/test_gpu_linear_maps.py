@@ -1,4 +1,4 @@
-"""Linear maps before the covariance on the GPU (Sect. 2.4, Sect. 4.3): wider
+"""Linear maps before the covariance on the GPU (Sect. 2.3, Sect. 4.3): wider
 bins from the pair counts, xi rows mapped by a matrix (the Legendre
 multipoles), and the LC covariance of the mapped xi."""
 import math

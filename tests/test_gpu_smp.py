@@ -1,6 +1,6 @@
 """The brute-force (Smp) covariance path on the GPU, against the oracle.
 
-Smp is the estimate the LC covariance replaces (Sect. 2.1, Sect. 3.2): every
+Smp is the estimate the LC covariance replaces (Sect. 2.1, Sect. 2.2): every
 mock is counted against all M = 50 random subsets in one batched launch,
 the split Landy-Szalay estimator runs over all of them, and the covariance is
 the plain sample covariance of Eq. (bruteforce) over the mocks.

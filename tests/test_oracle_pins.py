@@ -410,7 +410,7 @@ def test_lc_matches_poisson_theory():
 
 
 # ---------------------------------------------------------------------------
-# linear maps: wider bins and Legendre multipoles (Sect. 2.4, Sect. 4.3)
+# linear maps: wider bins and Legendre multipoles (Sect. 2.3, Sect. 4.3)
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("f_s,f_mu", [(1, 1), (2, 3), (3, 6), (4, 1), (1, 2), (12, 6)])
@@ -471,3 +471,76 @@ def test_multipole_matrix_invariants():
     for i, ell in enumerate((0, 1, 2, 3, 4)):
         want = np.array(A.get(ell, [0.0] * n_s))
         assert np.allclose(m[i * n_s:(i + 1) * n_s], want, rtol=5e-4, atol=1e-4), ell   # O(dmu^2) error
+
+
+# ---------------------------------------------------------------------------
+# covariance of covariance and chi^2 (Sect. 3, Sect. 5.3), pinned by Monte Carlo
+# ---------------------------------------------------------------------------
+
+def _mc_lc(M_a, M, N, T, seed):
+    """Simulate the LC construction for Gaussian xi: x and x' (the estimates with the two M_a random
+    catalogues) share the data part s (covariance S) and carry independent random-catalogue parts
+    (covariance R); xi of the joint catalogue is (x + x') / 2, as in the derivation of Eq. (Cfastx)."""
+    rng = np.random.default_rng(seed)
+    S = np.array([[2.0, 0.5, 0.2], [0.5, 1.5, 0.3], [0.2, 0.3, 1.0]])
+    R = np.array([[1.0, 0.4, 0.0], [0.4, 2.0, 0.5], [0.0, 0.5, 0.8]])
+    Ls, Lr = np.linalg.cholesky(S), np.linalg.cholesky(R)
+    est_lc, est_smp = [], []
+    for _ in range(T):
+        s = rng.standard_normal((N, 3)) @ Ls.T
+        x = s + rng.standard_normal((N, 3)) @ Lr.T
+        xp = s + rng.standard_normal((N, 3)) @ Lr.T
+        Ca = 0.5 * oracle.sample_cov(x) + 0.5 * oracle.sample_cov(xp)
+        Cb = oracle.sample_cov(0.5 * (x + xp))
+        A = 2 * Cb - Ca
+        B = 2 * M_a * (Ca - Cb)
+        est_lc.append(A + B / M)
+        est_smp.append(oracle.sample_cov(x))
+    # ensemble values: cov(x) = S + R = A + B / M_a, cov(x, x') = S = A
+    return np.array(est_lc), np.array(est_smp), S, M_a * R
+
+
+@pytest.mark.parametrize("M_a,M", [(1, 5.0), (1, 50.0), (2, 3.0), (1, 2.0)])
+def test_covcov_lc_and_smp_against_monte_carlo(M_a, M):
+    """Var(C_ij) of Eqs. (covcov_brute) and (covcov_fast) against the scatter of simulated estimates:
+    the reading D = A + B / (2 M_a) matches, the printed A + B / M_a would be off by up to 2x."""
+    N, T = 8, 12000
+    lc, smp, A, B = _mc_lc(M_a, M, N, T, seed=int(10 * M) + M_a)
+    v_lc = oracle.covcov_var(A, B, N, M_a, M)
+    v_smp = oracle.covcov_var(A + B / M_a, None, N)
+    # relative standard error of a variance from T samples ~ sqrt(2 / T) (1.3 %), plus heavier tails
+    assert np.allclose(lc.var(axis=0, ddof=1), v_lc, rtol=0.07), (lc.var(axis=0, ddof=1), v_lc)
+    assert np.allclose(smp.var(axis=0, ddof=1), v_smp, rtol=0.07)
+    if M != 2.0 * M_a:
+        wrong = oracle.covcov_var(A - B / (2.0 * M_a) + B / M_a, B, N, M_a, M)   # D = A + B / M_a
+        assert np.max(np.abs(lc.var(axis=0, ddof=1) / wrong - 1.0)) > 0.2
+    # chi^2: the mean measured chi^2_N times (N - 1) is the predicted chi^2_2
+    C_true = A + B / M
+    m = np.mean([oracle.chi2(c, C_true, C_true) for c in lc]) * (N - 1)
+    assert m == pytest.approx(oracle.chi2_predict(A, B, C_true, M_a, M), rel=0.05)
+
+
+def test_covcov_special_cases():
+    """LC at M = 2 M_a equals the sample-covariance form of C(2 M_a); identity covariance gives
+    <chi^2_2> = 1 + 1/n for the sample covariance."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((6, 6))
+    A = X @ X.T
+    Y = rng.standard_normal((6, 6))
+    B = Y @ Y.T
+    for M_a in (1, 3):
+        lc = oracle.covcov_var(A, B, 11, M_a, 2.0 * M_a)
+        smp = oracle.covcov_var(A + B / (2.0 * M_a), None, 11)
+        assert np.allclose(lc, smp, rtol=1e-13)
+    for n in (1, 4, 40):
+        eye = np.eye(n)
+        assert oracle.chi2_predict(eye, None, eye) == pytest.approx(1.0 + 1.0 / n, rel=1e-14)
+    assert oracle.chi2(A, A, A) == 0.0
+
+
+def test_eigvalsh_known_spectrum():
+    rng = np.random.default_rng(6)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    lam = np.sort(np.concatenate([rng.uniform(-2, 5, 27), [1.5, 1.5, 1.5]]))
+    C = (Q * lam) @ Q.T
+    assert np.allclose(oracle.eigvalsh(0.5 * (C + C.T)), lam, atol=1e-12)
