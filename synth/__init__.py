@@ -48,6 +48,15 @@ def uniform_box(rng: np.random.Generator, n: int, L: float) -> np.ndarray:
     return x
 
 
+def uniform_slab(rng: np.random.Generator, n: int, dims=(1500.0, 1500.0, 300.0)) -> np.ndarray:
+    """n points uniform in the slab [0, dims[0]) x [0, dims[1]) x [0, dims[2]) (the paper's simulation
+    slab is 1500 x 1500 x 300 (Mpc/h)^3), float64 [n][3]."""
+    d = np.asarray(dims, dtype=np.float64)
+    x = rng.random((n, 3)) * d
+    x[x >= d] = 0.0
+    return x
+
+
 def neyman_scott(rng: np.random.Generator, n: int, L: float, n_parent: float,
                  sigma: float) -> np.ndarray:
     """n children of a Neyman-Scott process in a periodic cube of side L.

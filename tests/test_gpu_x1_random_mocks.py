@@ -1,0 +1,93 @@
+"""Random mocks in the paper's slab (Sect. 4.2, Sect. 5.1), at reduced N.
+
+Uniform points stand in for the data catalogue, N_d = 155 250 per mock in the
+1500 x 1500 x 300 (Mpc/h)^3 slab, with two random catalogues of N_d points each
+(M_a = 1), 20 separation bins of 10 Mpc/h to 200 Mpc/h, open geometry.  The
+true covariance is then known: Eq. (randomtheory) with G_p the pair-volume
+fraction of each bin (measured here as the mean RR / (N_r (N_r - 1) / 2)).
+The LC covariance at M = 50 and its M -> infinity limit (A) must agree with
+it within the error bars of Eq. (covcov_fast), and the predicted LC / Smp
+error ratio on the diagonal must be the paper's 2.7.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+DEV = "cuda:0"
+N_D = 155_250
+N_MOCK = 300
+DIMS = (1500.0, 1500.0, 300.0)
+
+
+@pytest.fixture(scope="module")
+def tp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2205_11852_gb300 as tp
+    return tp
+
+
+def test_x1_lc_diagonal_matches_random_theory(tp):
+    ctx = tp.Context(0)
+    edges = np.linspace(0.0, 200.0, 21)
+    b = tp.make_binning(edges, 1, tp.TPCF_OPEN, 1500.0, los=tp.TPCF_LOS_X)
+    nbin = 20
+    xi = {k: torch.empty((N_MOCK, nbin), dtype=torch.float64, device=DEV) for k in ("a1", "a2", "b")}
+    rr_norm = []
+    batch = 50
+    for m0 in range(0, N_MOCK, batch):
+        dm = []
+        for m in range(m0, m0 + batch):
+            d = synth.uniform_slab(synth.rng_for(908, m, 0), N_D, DIMS)
+            r = np.concatenate([synth.uniform_slab(synth.rng_for(908, m, 1 + i), N_D, DIMS) for i in range(2)])
+            dm.append({"data": torch.from_numpy(d).to(DEV), "randoms": torch.from_numpy(r).to(DEV),
+                       "offsets": [0, N_D, 2 * N_D]})
+        c = ctx.tpcf_count(dm, b, mode=tp.TPCF_BATCHED)
+        nd, nr = [N_D] * batch, [[N_D, N_D]] * batch
+        for k, sel in (("a1", [0]), ("a2", [1]), ("b", [0, 1])):
+            xi[k][m0:m0 + batch] = ctx.tpcf_ls(c["dd"], c["dr"], c["rr"], nd, nr, sel)
+        assert ctx.tpcf_sync() == tp.TPCF_OK
+        rr_norm.append((c["rr"].double() / (N_D * (N_D - 1) / 2.0)).mean(dim=(0, 1)).cpu().numpy())
+        del dm, c
+    Gp = np.mean(rr_norm, axis=0)
+    T0 = 2.0 / (N_D * (N_D - 1)) / Gp                 # M -> infinity
+    M = 50.0
+    nr = M * N_D
+    T50 = (2.0 / (N_D * (N_D - 1)) + 4.0 / (N_D * nr) + 2.0 / (nr * (N_D - 1))) / Gp
+
+    out = ctx.tpcf_lc_cov(xi["a1"], xi["a2"], xi["b"], 1, M, tp.TPCF_FP64)
+    var50 = ctx.tpcf_covcov_var(out["A"], out["B"], N_MOCK, 1, M)
+    varinf = ctx.tpcf_covcov_var(out["A"], out["B"], N_MOCK, 1, math.inf)
+    assert ctx.tpcf_sync() == tp.TPCF_OK
+    c50 = np.diag(out["C_lc"].cpu().numpy())
+    cinf = np.diag(out["A"].cpu().numpy())
+    s50 = np.sqrt(np.diag(var50.cpu().numpy()))
+    sinf = np.sqrt(np.diag(varinf.cpu().numpy()))
+    z50, zinf = (c50 - T50) / s50, (cinf - T0) / sinf
+    # every bin within 5 sigma, and the scatter consistent with the predicted error bars
+    assert np.all(np.abs(z50) < 5.0) and np.all(np.abs(zinf) < 5.0), (z50, zinf)
+    assert 0.15 < np.mean(z50 ** 2) < 3.0 and 0.15 < np.mean(zinf ** 2) < 3.0, (z50, zinf)
+    # the bin-averaged ratio to theory within 4 sigma of its own error
+    for c, t, s in ((c50, T50, s50), (cinf, T0, sinf)):
+        r = c / t
+        assert abs(r.mean() - 1.0) < 4.0 * np.sqrt(np.mean((s / t) ** 2) / len(r)), r
+    # M = infinity lies below M = 50 (B > 0 on the diagonal: the random-catalogue noise)
+    assert np.mean(cinf) < np.mean(c50)
+    # LC / sample-covariance error ratio on the diagonal, Eqs. (covcov_fast) and (covcov_brute), in units
+    # of the M -> infinity theory: A = 1 exactly for random mocks, B = the bin-averaged measured B (3 from
+    # the 1 + 3/M of Eq. randomtheory); the paper measures 2.7 for this set-up
+    bb = float(np.mean(np.diag(out["B"].cpu().numpy()) / T0))
+    c = 0.5 - 1.0 / M
+    D, C = 1.0 + bb / 2.0, 1.0 + bb / M
+    ratio = math.sqrt((D * D + c * c * bb * bb) / (C * C))
+    assert 2.4 < bb < 3.6 and 2.55 < ratio < 2.9, (bb, ratio)
+    ctx.close()
