@@ -233,6 +233,51 @@ def smp_measure(tp, ctx, dev, b, prec, n_mock, n_d, M=50, reps=2):
             "status": rc}
 
 
+def next_rows_measure(tp, ctx, dev, reps=20):
+    """Timings of the steps after the LC covariance, on the covariance workload shape: the brute-force
+    sample covariance, the multipole projection, the covariance-of-covariance variances, the predicted
+    chi^2 and the eigenvalue check."""
+    import torch
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    n_s, n_mu, n_mock = 40, 5, 3500
+    xs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in synth.synthetic_xi_variants(3, n_mock, n_s * n_mu)]
+    P = torch.from_numpy(tp.tpcf_multipole_matrix(n_s, n_mu, (0, 2, 4))).to(dev)
+    out = {"workload": f"{n_mock} mocks x {n_s} s x {n_mu} mu bins; multipoles l=0,2,4 (120 rows)"}
+    out["sample_cov_ms"] = {name: timed(lambda pr=pr: ctx.tpcf_sample_cov(xs[2], pr))
+                            for name, pr in (("fp64", tp.TPCF_FP64), ("tf32x3", tp.TPCF_TF32X3))}
+    out["project_multipoles_ms"] = timed(lambda: ctx.tpcf_project(P, xs[0]))
+    ys = [ctx.tpcf_project(P, x) for x in xs]
+    lc = ctx.tpcf_lc_cov(*ys, 1, M_FINAL, tp.TPCF_FP64)
+    out["lc_cov_multipoles_fp64_ms"] = timed(lambda: ctx.tpcf_lc_cov(*ys, 1, M_FINAL, tp.TPCF_FP64))
+    big = ctx.tpcf_lc_cov(*xs, 1, M_FINAL, tp.TPCF_FP64)
+    for tag, parts in (("120", lc), ("200", big)):
+        out[f"covcov_var_{tag}_ms"] = timed(lambda parts=parts: ctx.tpcf_covcov_var(parts["A"], parts["B"], n_mock,
+                                                                                     1, M_FINAL))
+        out[f"chi2_predict_{tag}_ms"] = timed(lambda parts=parts: ctx.tpcf_chi2_predict(parts["A"], parts["B"],
+                                                                                         parts["C_lc"], 1, M_FINAL))
+        out[f"eigvalsh_{tag}_ms"] = timed(lambda parts=parts: ctx.tpcf_eigvalsh(parts["C_lc"]))
+    w = ctx.tpcf_eigvalsh(lc["C_lc"])
+    out["lc_multipole_cov_min_eigenvalue_over_max"] = float(w[0] / w[-1])
+    out["chi2_2_predicted_multipoles"] = {
+        "lc": float(ctx.tpcf_chi2_predict(lc["A"], lc["B"], lc["C_lc"], 1, M_FINAL)),
+        "smp": float(ctx.tpcf_chi2_predict(lc["C_lc"], None, lc["C_lc"]))}
+    out["status"] = ctx.tpcf_sync()
+    return out
+
+
 def measured_traffic(n_mock):
     """DRAM bytes of one pair-count launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
@@ -494,6 +539,10 @@ def main():
                "lc_over_smp_binned_pairs": (r["n_binned"] / args.smp_mocks) / (n_binned / n_mock),
                "paper_cost_ratio_1p3M_over_7": (1 + 3 * 50) / 7, "status": r["status"]}
 
+    nxt = None
+    if rank == 0 and not args.no_precision_config:
+        nxt = next_rows_measure(tp, ctx, dev)
+
     kernels_per_step = info["n_kernels"] + 3 + 4   # count + 3 LS + 4 covariance kernels
     if rank == 0:
         line = {
@@ -516,6 +565,7 @@ def main():
                       "unit_chunk": info["unit_chunk"], "graph_replay": bool(info["graph_replay"])},
             "precision_config": prec_cfg,
             "smp_comparison": smp,
+            "after_covariance": nxt,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-op/s",
                          "frac": achieved / peak, "traffic": measured_traffic(n_mock),
                          "traffic_note": "ncu DRAM bytes of 2 mocks scaled to the launch's mocks",

@@ -359,10 +359,10 @@ int tpcf_lc_cov(tpcf_ctx *ctx, const double *xi_a1, const double *xi_a2, const d
     if (M_a < 1) return fail(ctx, TPCF_ERR_ARG, "M_a must be >= 1");
     if (!(M >= (double)M_a)) return fail(ctx, TPCF_ERR_ARG, "M must be >= M_a (or +inf)");
     if (precision == TPCF_FP64) {
-        const size_t elems = 3 * (size_t)n_mock * nbin + 3 * (size_t)nbin + 3 * (size_t)nbin * nbin;
+        const int ns = fp64_splits(n_mock, nbin, 3);
         void *w;
-        if ((rc = ensure(ctx, "lc_work", elems * 8, &w))) return rc;
-        CK(launch_lc_fp64(xi_a1, xi_a2, xi_b, n_mock, nbin, (double *)w, M_a, M, C_lc, Ca, Cb, A, B, s));
+        if ((rc = ensure(ctx, "lc_work", fp64_work_elems(n_mock, nbin, 3, ns) * 8, &w))) return rc;
+        CK(launch_lc_fp64_split(xi_a1, xi_a2, xi_b, n_mock, nbin, (double *)w, ns, M_a, M, C_lc, Ca, Cb, A, B, s));
         return TPCF_OK;
     }
     if (precision == TPCF_TF32X3 || precision == TPCF_BF16X3) {
@@ -387,10 +387,10 @@ int tpcf_sample_cov(tpcf_ctx *ctx, const double *xi, int n_mock, int nbin, int p
     if (n_mock < 2) return fail(ctx, TPCF_ERR_ARG, "n_mock must be >= 2");
     if (nbin < 1 || nbin > 65536) return fail(ctx, TPCF_ERR_ARG, "bad nbin");
     if (precision == TPCF_FP64) {
-        const size_t elems = (size_t)n_mock * nbin + (size_t)nbin + (size_t)nbin * nbin;
+        const int ns = fp64_splits(n_mock, nbin, 1);
         void *w;
-        if ((rc = ensure(ctx, "lc_work", elems * 8, &w))) return rc;
-        CK(launch_cov_fp64(xi, n_mock, nbin, (double *)w, C, s));
+        if ((rc = ensure(ctx, "lc_work", fp64_work_elems(n_mock, nbin, 1, ns) * 8, &w))) return rc;
+        CK(launch_cov_fp64(xi, n_mock, nbin, (double *)w, C, s, ns));
         return TPCF_OK;
     }
     if (precision == TPCF_TF32X3 || precision == TPCF_BF16X3) {

@@ -71,26 +71,31 @@ __global__ void centre_kernel(const double *__restrict__ x0, const double *__res
         Y[(size_t)v * total + t] = x[t] - mean[(size_t)v * nbin + (t % nbin)];
 }
 
-// G[v] = Y[v]^T Y[v] (nbin x nbin), float64, 64x64 tiles, 4x4 per thread
+// G[v] = Y[v]^T Y[v] (nbin x nbin), float64, 64x64 tiles, 4x4 per thread.
+// With n_split > 1, blockIdx.z = v * n_split + split and the block sums the
+// mocks [split * k_len, (split + 1) * k_len) into its own partial Gram
+// G + (v * n_split + split) * nbin^2 (summed afterwards in a fixed order).
 constexpr int GT = 64, GK = 16;
 __global__ void __launch_bounds__(256) gram_fp64_kernel(const double *__restrict__ Y, int n_mock, int nbin,
-                                                         double *__restrict__ G)
+                                                         double *__restrict__ G, int n_split = 1, int k_len = 0)
 {
     __shared__ double As[GK][GT + 1];
     __shared__ double Bs[GK][GT + 1];
-    const int v = blockIdx.z;
+    const int v = blockIdx.z / n_split, split = blockIdx.z % n_split;
     const double *y = Y + (size_t)v * n_mock * nbin;
-    double *g = G + (size_t)v * nbin * nbin;
+    double *g = G + (size_t)blockIdx.z * nbin * nbin;
     const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
     if (j0 + GT <= i0) return;  // below the diagonal block row: filled by symmetry
+    const int k_begin = n_split > 1 ? split * k_len : 0;
+    const int k_end = n_split > 1 ? min(n_mock, k_begin + k_len) : n_mock;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     double acc[4][4] = {};
-    for (int k0 = 0; k0 < n_mock; k0 += GK) {
+    for (int k0 = k_begin; k0 < k_end; k0 += GK) {
         for (int e = threadIdx.x; e < GK * GT; e += 256) {
             const int kk = e / GT, c = e % GT;
             const int k = k0 + kk;
-            As[kk][c] = (k < n_mock && i0 + c < nbin) ? y[(size_t)k * nbin + i0 + c] : 0.0;
-            Bs[kk][c] = (k < n_mock && j0 + c < nbin) ? y[(size_t)k * nbin + j0 + c] : 0.0;
+            As[kk][c] = (k < k_end && i0 + c < nbin) ? y[(size_t)k * nbin + i0 + c] : 0.0;
+            Bs[kk][c] = (k < k_end && j0 + c < nbin) ? y[(size_t)k * nbin + j0 + c] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -117,6 +122,20 @@ __global__ void __launch_bounds__(256) gram_fp64_kernel(const double *__restrict
                 g[(size_t)j * nbin + i] = acc[r][c];
             }
         }
+}
+
+// G[v] = sum over the splits of the partial Grams, in split order
+__global__ void split_sum_kernel(const double *__restrict__ part, int n_var, int n_split, size_t nn,
+                                 double *__restrict__ G)
+{
+    const size_t total = (size_t)n_var * nn;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = t / nn, e = t % nn;
+        const double *p = part + v * n_split * nn + e;
+        double s = 0.0;
+        for (int k = 0; k < n_split; k++) s += p[(size_t)k * nn];
+        G[t] = s;
+    }
 }
 
 // LC combination in float64 (Eqs. R1R2, LCdef):
@@ -151,9 +170,10 @@ __global__ void scale_kernel(const double *__restrict__ G, size_t nn, int n_mock
 
 int blocks_for(size_t n, int threads) { return (int)std::min<size_t>((n + threads - 1) / threads, 152 * 16); }
 
-// float64 Gram products of n_var centred variants; returns G [n_var][nbin][nbin] inside work
+// float64 Gram products of n_var centred variants; returns G [n_var][nbin][nbin] inside work.
+// n_split > 1 splits the mocks into n_split ranges (partials after G in work, summed in split order).
 double *gram_fp64(const double *x0, const double *x1, const double *x2, int n_var, int n_mock, int nbin,
-                  double *work, cudaStream_t s)
+                  double *work, cudaStream_t s, int n_split = 1)
 {
     double *Y = work;
     double *mean = Y + (size_t)n_var * n_mock * nbin;
@@ -162,7 +182,15 @@ double *gram_fp64(const double *x0, const double *x1, const double *x2, int n_va
     centre_kernel<<<dim3(std::max(1, blocks_for((size_t)n_mock * nbin, 256)), n_var), 256, 0, s>>>(
         x0, x1, x2, n_mock, nbin, mean, Y);
     const int nt = (nbin + GT - 1) / GT;
-    gram_fp64_kernel<<<dim3(nt, nt, n_var), 256, 0, s>>>(Y, n_mock, nbin, G);
+    if (n_split <= 1) {
+        gram_fp64_kernel<<<dim3(nt, nt, n_var), 256, 0, s>>>(Y, n_mock, nbin, G);
+        return G;
+    }
+    const int k_len = ((n_mock + n_split - 1) / n_split + GK - 1) / GK * GK;
+    double *part = G + (size_t)n_var * nbin * nbin;
+    gram_fp64_kernel<<<dim3(nt, nt, n_var * n_split), 256, 0, s>>>(Y, n_mock, nbin, part, n_split, k_len);
+    const size_t nn = (size_t)nbin * nbin;
+    split_sum_kernel<<<blocks_for((size_t)n_var * nn, 256), 256, 0, s>>>(part, n_var, n_split, nn, G);
     return G;
 }
 
@@ -188,9 +216,36 @@ cudaError_t launch_lc_fp64(const double *xi_a1, const double *xi_a2, const doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_cov_fp64(const double *xi, int n_mock, int nbin, double *work, double *C, cudaStream_t s)
+int fp64_splits(int n_mock, int nbin, int n_var)
 {
-    const double *G = gram_fp64(xi, xi, xi, 1, n_mock, nbin, work, s);
+    // enough blocks to fill the GPU: (upper-triangle tiles x variants x splits) ~ 2 per SM, splits of >= 64 mocks
+    const int nt = (nbin + GT - 1) / GT;
+    const int tiles = n_var * nt * (nt + 1) / 2;
+    const int want = std::max(1, (2 * 152 + tiles - 1) / tiles);
+    return std::max(1, std::min(want, n_mock / 64));
+}
+
+size_t fp64_work_elems(int n_mock, int nbin, int n_var, int n_split)
+{
+    const size_t nn = (size_t)nbin * nbin;
+    return (size_t)n_var * n_mock * nbin + (size_t)n_var * nbin + (size_t)n_var * nn +
+           (n_split > 1 ? (size_t)n_var * n_split * nn : 0);
+}
+
+cudaError_t launch_lc_fp64_split(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
+                                 double *work, int n_split, int M_a, double M, double *C_lc, double *Ca, double *Cb,
+                                 double *A, double *B, cudaStream_t s)
+{
+    const double *G = gram_fp64(xi_a1, xi_a2, xi_b, 3, n_mock, nbin, work, s, n_split);
+    combine_kernel<<<std::max(1, blocks_for((size_t)nbin * nbin, 256)), 256, 0, s>>>(G, nbin, n_mock, M_a, M, C_lc,
+                                                                                     Ca, Cb, A, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cov_fp64(const double *xi, int n_mock, int nbin, double *work, double *C, cudaStream_t s,
+                            int n_split)
+{
+    const double *G = gram_fp64(xi, xi, xi, 1, n_mock, nbin, work, s, n_split);
     scale_kernel<<<std::max(1, blocks_for((size_t)nbin * nbin, 256)), 256, 0, s>>>(G, (size_t)nbin * nbin, n_mock,
                                                                                   C);
     return cudaGetLastError();

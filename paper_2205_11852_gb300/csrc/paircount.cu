@@ -250,7 +250,9 @@ struct Ctx {
             const float mf = __fadd_rn(u, big);
             const int ki = __float_as_int(mf) - 0x4B400000;
             const float ds = __fsub_rn(u, __fsub_rn(mf, big));
-            amb = (fabsf(ds) < __fmaf_rn(c.s_c1, u, c.s_c0)) && ((unsigned)(ki - 1) < (unsigned)c.n_s);
+            // near an edge (or NaN: d2 = 0).  The s = 0 edge needs no recheck
+            // but costs nothing to include; s_max is an edge like the others.
+            amb = !(fabsf(ds) >= __fmaf_rn(c.s_c1, u, c.s_c0));
             k = ki - (ds < 0.0f ? 1 : 0);
             valid = (unsigned)k < (unsigned)c.n_s;
         } else {
@@ -283,17 +285,15 @@ struct Ctx {
                 t = __fmul_rn(__fmul_rn(__fmul_rn(fabsf(dot), rs), rl), (float)c.n_mu);
                 beta = __fmaf_rn(c.mu_c1, rs, __fmaf_rn(c.mu_c3, rl, c.mu_c2));
             }
-            // the pair is ambiguous when t = n_mu |mu| lies within beta of an
-            // interior mu edge 1..n_mu-1
+            // the pair is ambiguous when t = n_mu |mu| (>= 0) lies within beta
+            // of an integer (a mu edge; 0 and n_mu need no recheck but cost
+            // nothing to include), or is NaN (d2 = 0)
             const float mf = __fadd_rn(t, big);
             const int mi = __float_as_int(mf) - 0x4B400000;
             const float d = __fsub_rn(t, __fsub_rn(mf, big));
-            amb |= !(beta < 0.05f);
-            amb |= (fabsf(d) < beta) && ((unsigned)(mi - 1) < (unsigned)(c.n_mu - 1));
-            const int j = min(max(mi - (d < 0.0f ? 1 : 0), 0), c.n_mu - 1);
+            amb |= !(fabsf(d) >= beta);
+            const int j = min(mi - (d < 0.0f ? 1 : 0), c.n_mu - 1);   // mu = 1 in the top bin
             bin = k * c.n_mu + j;
-        } else if (LIN) {
-            amb |= !(r < 3.0e38f);   // d2 == 0: r = inf, u = NaN
         }
         return amb ? -2 : (valid ? bin : -1);
     }
@@ -310,8 +310,8 @@ struct Ctx {
         const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
         for (uint32_t k = 0; k < nmax; k++) {
             const bool mine = k < n;
-            const uint32_t v = lds16_if(q + k * 64u, mine);   // a index | p << 8
-            sts16_if(cq + 2u * (pos + k), (v & 255u) | ((((v >> 8) << 5) | (uint32_t)lane) << 8), mine);
+            const uint32_t v = lds16_if(q + k * 64u, mine);   // a index | (p * 32 + lane) << 8
+            sts16_if(cq + 2u * (pos + k), v, mine);
         }
         __syncwarp();
         uint32_t n_amb = 0;
@@ -414,6 +414,7 @@ struct Ctx {
         uint32_t head = q;
         const uint32_t lim = q + (uint32_t)(QN - 2 * P) * 64u;
         const uint32_t ib0 = base + lane;   // used by SELF tiles only
+        const uint32_t lane8 = (uint32_t)lane << 8;
         uint32_t ai = 0;
         for (; ai + 1 < na; ai += 2) {
             const float4 a = lds128(abase + 16u * ai), cc = lds128(abase + 16u * (ai + 1));
@@ -422,7 +423,7 @@ struct Ctx {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                sts16(head, ai | (p << 8));   // kept only on a hit
+                sts16(head, (ai | lane8) | (uint32_t)(p << 13));   // kept only on a hit
                 head += hit ? 64u : 0u;
             }
 #pragma unroll
@@ -430,7 +431,7 @@ struct Ctx {
                 const float t = __fmaf_rn(cc.x, bx[p], __fmaf_rn(cc.y, by[p], __fmaf_rn(cc.z, bz[p], cc.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai + 1 < ib0 + 32u * p);
-                sts16(head, (ai + 1) | (p << 8));
+                sts16(head, ((ai + 1) | lane8) | (uint32_t)(p << 13));
                 head += hit ? 64u : 0u;
             }
             if (__any_sync(0xffffffffu, head > lim)) {
@@ -445,7 +446,7 @@ struct Ctx {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
                 bool hit = t >= hb[p];
                 if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                sts16(head, ai | (p << 8));
+                sts16(head, (ai | lane8) | (uint32_t)(p << 13));
                 head += hit ? 64u : 0u;
             }
         }
@@ -545,7 +546,7 @@ __device__ void build_segments(const CountParams &prm, const Smem &sm, const Mes
 }
 
 template <bool MU, bool MID, bool LIN>
-__global__ void __launch_bounds__(WARPS * 32) paircount_kernel(const __grid_constant__ CountParams prm, const Mesh m,
+__global__ void __launch_bounds__(WARPS * 32, 3) paircount_kernel(const __grid_constant__ CountParams prm, const Mesh m,
                                                                 const Term *__restrict__ terms,
                                                                 const Unit *__restrict__ units,
                                                                 const uint32_t *__restrict__ n_units_p,

@@ -135,9 +135,16 @@ cudaError_t launch_lc_split(const double *xi_a1, const double *xi_a2, const doub
                             double *C_lc, double *Ca, double *Cb, double *A, double *B, int *status, cudaStream_t s);
 // work bytes of the split-precision path for n_var variants (3: LC, 1: one sample covariance)
 size_t lc_split_work_bytes(int n_mock, int nbin, int precision, int n_var = 3);
+// float64 covariance paths with the mocks split into n_split ranges (fp64_splits picks a count that fills
+// the GPU); work holds fp64_work_elems(n_mock, nbin, n_var, n_split) doubles
+int fp64_splits(int n_mock, int nbin, int n_var);
+size_t fp64_work_elems(int n_mock, int nbin, int n_var, int n_split);
+cudaError_t launch_lc_fp64_split(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
+                                 double *work, int n_split, int M_a, double M, double *C_lc, double *Ca, double *Cb,
+                                 double *A, double *B, cudaStream_t s);
 // sample covariance C[nbin][nbin] of one variant xi[n_mock][nbin], Eq. (bruteforce)
-cudaError_t launch_cov_fp64(const double *xi, int n_mock, int nbin,
-                            double *work /* n_mock*nbin + nbin + nbin*nbin */, double *C, cudaStream_t s);
+cudaError_t launch_cov_fp64(const double *xi, int n_mock, int nbin, double *work, double *C, cudaStream_t s,
+                            int n_split);
 cudaError_t launch_cov_split(const double *xi, int n_mock, int nbin, int precision, void *work, size_t work_bytes,
                              double *C, int *status, cudaStream_t s);
 // column means mean[n_var][nbin] of the first n_var xi variants
