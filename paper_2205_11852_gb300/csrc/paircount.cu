@@ -154,15 +154,30 @@ __device__ __forceinline__ float rsqrt_approx(float x)
 
 // 32-bit shared-memory accesses (addresses from __cvta_generic_to_shared)
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// 16-bit shared accesses through 32-bit registers (the load zero-extends,
+// the store keeps the low half)
 __device__ __forceinline__ void sts16(uint32_t a, uint32_t v)
 {
-    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((unsigned short)v) : "memory");
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 __device__ __forceinline__ uint32_t lds16(uint32_t a)
 {
-    unsigned short v;
-    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
+    uint32_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
     return v;
+}
+// queue push: store v at the head slot; advance the head (one 64-byte slot
+// row) only when t >= h
+__device__ __forceinline__ void push_if_ge(uint32_t &head, uint32_t v, float t, float h)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ge.f32 p, %1, %2;\n\t"
+        "st.shared.u16 [%0], %3;\n\t"
+        "@p add.u32 %0, %0, 64;\n\t}"
+        : "+r"(head)
+        : "f"(t), "f"(h), "r"(v)
+        : "memory");
 }
 __device__ __forceinline__ float4 lds128(uint32_t a)
 {
@@ -189,13 +204,13 @@ __device__ __forceinline__ void red_inc_if(uint32_t base, int bin)
 // 16-bit shared load when live (else 0), without a branch
 __device__ __forceinline__ uint32_t lds16_if(uint32_t a, bool live)
 {
-    unsigned short v;
+    uint32_t v;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %2, 0;\n\t"
-        "mov.u16 %0, 0;\n\t"
+        "mov.u32 %0, 0;\n\t"
         "@p ld.shared.u16 %0, [%1];\n\t}"
-        : "=h"(v)
+        : "=r"(v)
         : "r"(a), "r"((int)live)
         : "memory");
     return v;
@@ -207,7 +222,7 @@ __device__ __forceinline__ void sts16_if(uint32_t a, uint32_t v, bool pred)
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %2, 0;\n\t"
         "@p st.shared.u16 [%0], %1;\n\t}" ::"r"(a),
-        "h"((unsigned short)v), "r"((int)pred)
+        "r"(v), "r"((int)pred)
         : "memory");
 }
 
@@ -327,7 +342,6 @@ struct Ctx {
             int bin = classify(d2, dx, a, b);
             bin = live ? bin : -1;
             red_inc_if(hbase, bin);
-            n_binned += (bin >= 0) ? 1u : 0u;
             const unsigned am = __ballot_sync(0xffffffffu, bin == -2);
             if (am) {
                 // rare: keep the entry for the exact recheck, written over
@@ -343,10 +357,7 @@ struct Ctx {
             const float4 b = lds128(bc + 16u * (v >> 8));
             const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + (v & 255u), __float_as_uint(b.w));
             n_exact++;
-            if (bin >= 0) {
-                red_inc(hbase + 4u * (uint32_t)bin);
-                n_binned++;
-            }
+            if (bin >= 0) red_inc(hbase + 4u * (uint32_t)bin);
         }
         __syncwarp();
     }
@@ -421,18 +432,14 @@ struct Ctx {
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
-                bool hit = t >= hb[p];
-                if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                sts16(head, (ai | lane8) | (uint32_t)(p << 13));   // kept only on a hit
-                head += hit ? 64u : 0u;
+                const float h = (!SELF || a0 + ai < ib0 + 32u * p) ? hb[p] : INFINITY;
+                push_if_ge(head, (ai | lane8) | (uint32_t)(p << 13), t, h);   // kept only on a hit
             }
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const float t = __fmaf_rn(cc.x, bx[p], __fmaf_rn(cc.y, by[p], __fmaf_rn(cc.z, bz[p], cc.w)));
-                bool hit = t >= hb[p];
-                if (SELF) hit = hit && (a0 + ai + 1 < ib0 + 32u * p);
-                sts16(head, ((ai + 1) | lane8) | (uint32_t)(p << 13));
-                head += hit ? 64u : 0u;
+                const float h = (!SELF || a0 + ai + 1 < ib0 + 32u * p) ? hb[p] : INFINITY;
+                push_if_ge(head, ((ai + 1) | lane8) | (uint32_t)(p << 13), t, h);
             }
             if (__any_sync(0xffffffffu, head > lim)) {
                 flush((head - q) >> 6);
@@ -444,10 +451,8 @@ struct Ctx {
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const float t = __fmaf_rn(a.x, bx[p], __fmaf_rn(a.y, by[p], __fmaf_rn(a.z, bz[p], a.w)));
-                bool hit = t >= hb[p];
-                if (SELF) hit = hit && (a0 + ai < ib0 + 32u * p);
-                sts16(head, (ai | lane8) | (uint32_t)(p << 13));
-                head += hit ? 64u : 0u;
+                const float h = (!SELF || a0 + ai < ib0 + 32u * p) ? hb[p] : INFINITY;
+                push_if_ge(head, (ai | lane8) | (uint32_t)(p << 13), t, h);
             }
         }
         if (__any_sync(0xffffffffu, head != q)) flush((head - q) >> 6);
@@ -668,6 +673,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) paircount_kernel(const __grid_c
         // drain the block histogram into the term's int64 histogram
         for (int b = tid; b < prm.nbin; b += blockDim.x) {
             const int v = sm.hist[b];
+            cx.n_binned += (unsigned)v;   // every binned pair passes through the block histogram
             if (v) {
                 atomicAdd((unsigned long long *)&tm.hist[b], (unsigned long long)(long long)v);
                 sm.hist[b] = 0;
