@@ -313,6 +313,16 @@ struct Ctx {
         return amb ? -2 : (valid ? bin : -1);
     }
 
+    // Bin of queue entry v (a index | b copy index << 8).
+    __device__ __forceinline__ int bin_of(uint32_t v) const
+    {
+        const float4 a = lds128(abase + 16u * (v & 255u));
+        const float4 b = lds128(bc + 16u * (v >> 8));
+        const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
+        const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+        return classify(d2, dx, a, b);
+    }
+
     // Bin every queued pair.  The lanes' queues are first packed into one
     // warp-contiguous list (a index | b copy index << 8), so that the binning
     // loop runs with all lanes busy whatever the spread of per-lane counts.
@@ -330,25 +340,28 @@ struct Ctx {
         }
         __syncwarp();
         uint32_t n_amb = 0;
-        for (uint32_t w0 = 0; w0 < total; w0 += 32) {
-            const uint32_t e = w0 + lane;
-            const bool live = e < total;
-            const uint32_t v = lds16_if(cq + 2u * e, live);
-            const uint32_t ai = v & 255u, bi = v >> 8;   // bi = p * 32 + owner lane
-            const float4 a = lds128(abase + 16u * ai);
-            const float4 b = lds128(bc + 16u * bi);
-            const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
-            const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-            int bin = classify(d2, dx, a, b);
-            bin = live ? bin : -1;
-            red_inc_if(hbase, bin);
-            const unsigned am = __ballot_sync(0xffffffffu, bin == -2);
-            if (am) {
-                // rare: keep the entry for the exact recheck, written over
+        const uint32_t lt = (1u << lane) - 1u;
+        // two entries per lane per pass (independent work for the scheduler)
+        for (uint32_t w0 = 0; w0 < total; w0 += 64) {
+            const uint32_t e0 = w0 + lane, e1 = e0 + 32u;
+            const bool live0 = e0 < total, live1 = e1 < total;
+            const uint32_t v0 = lds16_if(cq + 2u * e0, live0);
+            const uint32_t v1 = lds16_if(cq + 2u * e1, live1);
+            int bin0 = bin_of(v0), bin1 = bin_of(v1);   // dead slots read entry 0: in bounds, discarded
+            bin0 = live0 ? bin0 : -1;
+            bin1 = live1 ? bin1 : -1;
+            red_inc_if(hbase, bin0);
+            red_inc_if(hbase, bin1);
+            const unsigned am0 = __ballot_sync(0xffffffffu, bin0 == -2);
+            const unsigned am1 = __ballot_sync(0xffffffffu, bin1 == -2);
+            if (am0 | am1) {
+                // rare: keep the entries for the exact recheck, written over
                 // entries this loop has already consumed
                 __syncwarp();
-                sts16_if(cq + 2u * (n_amb + __popc(am & ((1u << lane) - 1u))), v, bin == -2);
-                n_amb += __popc(am);
+                sts16_if(cq + 2u * (n_amb + __popc(am0 & lt)), v0, bin0 == -2);
+                n_amb += __popc(am0);
+                sts16_if(cq + 2u * (n_amb + __popc(am1 & lt)), v1, bin1 == -2);
+                n_amb += __popc(am1);
             }
         }
         __syncwarp();
