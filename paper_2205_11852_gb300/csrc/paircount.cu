@@ -31,7 +31,7 @@ namespace {
 
 constexpr int P = 4;            // b-points per lane
 constexpr int TILE = 32 * P;    // b-points per warp tile
-constexpr int QN = 40;          // queue slots per lane (16-bit entries)
+constexpr int QN = 24;          // queue slots per lane (16-bit entries)
 constexpr int WARPS = 8;        // warps per block
 constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 
@@ -564,7 +564,7 @@ __device__ void build_segments(const CountParams &prm, const Smem &sm, const Mes
 }
 
 template <bool MU, bool MID, bool LIN>
-__global__ void __launch_bounds__(WARPS * 32, 3) paircount_kernel(const __grid_constant__ CountParams prm, const Mesh m,
+__global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_constant__ CountParams prm, const Mesh m,
                                                                 const Term *__restrict__ terms,
                                                                 const Unit *__restrict__ units,
                                                                 const uint32_t *__restrict__ n_units_p,
