@@ -456,7 +456,7 @@ int autotune(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binni
 {
     const int n_try = std::min(n_mock, 6);
     static const int subdivs[] = {2, 3, 4};
-    static const int chunks[] = {128, 256};
+    static const int chunks[] = {64, 128};
     cudaEvent_t t0, t1;
     CK(cudaEventCreate(&t0));
     CK(cudaEventCreate(&t1));

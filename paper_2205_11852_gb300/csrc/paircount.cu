@@ -1,7 +1,7 @@
 // Binned pair counting on the chaining mesh (Sect. 2.1: DD, DR_i, RR_i
 // counts; Sect. 4.3: bins in separation s and in mu).
 //
-// Work decomposition.  A unit is a chunk of at most 256 sorted points of one
+// Work decomposition.  A unit is a chunk of at most 128 sorted points of one
 // mesh cell A of catalogue a, to be paired with every point of catalogue b in
 // the neighbourhood of A.  A thread block owns a unit: the a-chunk and the
 // histogram live in shared memory, and the warps share the b side.  The
@@ -11,18 +11,24 @@
 // once, one P-vector per lane, shifted into A's frame, then streams the
 // a-chunk past it by broadcast shared-memory loads.
 //
-// Per pair, a dot-product form of the range test,
-//     a.b' - |a|^2/2  >=  (|b'|^2 - H)/2 - margin,
-// costs three FMAs and one compare (|a|^2/2 is stored with the point,
-// (|b'|^2 - H)/2 is per lane), with a margin that makes it a superset of the
-// direct FP32 test d2 < H.  A passing pair appends a 16-bit entry (a index,
-// b slot) to a lane-private queue in shared memory, branch-free.  Queues are
-// binned in bulk: the direct FP32 d2 and dx are recomputed, the s bin comes
-// from a table indexed by the bit pattern of d2 (one compare against the
-// band of the next edge), the mu bin from n_mu |dx| / sqrt(d2).  A pair whose
-// d2 or mu lies within the rigorous FP32 error band of a bin edge is rebinned
-// exactly from the integer grid coordinates (64-bit squared distances,
-// 128-bit mu test), so every count equals the integer definition bit for bit.
+// Line of sight along x (every periodic box).  Per pair the lane forms the
+// FP32 differences and d2 = dx^2 + dy^2 + dz^2 and appends (d2, dx) to its
+// own queue column in shared memory, branch-free: the store always happens
+// and only a pair with d2 below the last edge's band advances the column
+// head.  A flush bins the columns in place, two entries per lane per pass:
+// the s and mu bins are floors of FP32 estimates, each bracketed by a
+// rigorous error interval, so no point is read back from shared memory.  A
+// pair whose interval contains a bin edge (about 3 in 10^4) is identified by
+// replaying its lane's pushes since the flush window began, set aside, and
+// rechecked exactly from the integer grid coordinates (64-bit squared
+// distances, 128-bit mu test), 32 at a time, so every count equals the
+// integer definition bit for bit.
+//
+// Midpoint line of sight (cut-sky).  The mu of a pair needs both points, so
+// the queue holds 16-bit (a index, b slot) entries, pushed after a
+// dot-product range test (a.b' - |a|^2/2 >= (|b'|^2 - H)/2 - margin: three
+// FMAs and a compare), compacted per warp and binned from the a-chunk and
+// the tile's b copies.
 #include "plan.h"
 
 namespace tpcf {
@@ -31,9 +37,12 @@ namespace {
 
 constexpr int P = 4;            // b-points per lane
 constexpr int TILE = 32 * P;    // b-points per warp tile
-constexpr int QN = 24;          // queue slots per lane (16-bit entries)
+constexpr int QN = 24;          // queue slots per lane, midpoint path (16-bit entries)
+constexpr int QX = 18;          // queue slots per lane, x line of sight (8-byte entries)
+constexpr int XCAP = 96;        // per-warp list of pairs awaiting the exact recheck
 constexpr int WARPS = 8;        // warps per block
 constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
+static_assert(P == 4, "tile_x unrolls four b-points per lane");
 
 typedef unsigned __int128 u128;
 typedef __int128 i128;
@@ -48,11 +57,13 @@ struct Seg {
 };
 
 struct Smem {
-    float4 *a;                 // [UNIT_CHUNK]
-    int *hist;                 // [nbin]
-    uint16_t *queue;           // [WARPS][QN][32]
-    uint16_t *compact;         // [WARPS][QN * 32]
-    float4 *bcopy;             // [WARPS][P][32]: b' in A's frame, .w = b index (bits)
+    float4 *a;                 // [UNIT_CHUNK]; .w: -|a|^2/2
+    int *hist;                 // [nbin] (+ 32 spare words, x path)
+    unsigned char *queue;      // x path: [WARPS][QX + 1][32] (d2, dx) pairs;
+                               // midpoint path: [WARPS][QN][32] + [WARPS][QN * 32] 16-bit entries
+    float4 *bcopy;             // midpoint path: [WARPS][P][32] b' in A's frame, .w = b index (bits)
+    uint32_t *bidx;            // x path: [WARPS][P][32] b index of each tile slot
+    uint2 *xlist;              // x path: [WARPS][XCAP] (a index, b index) awaiting the exact recheck
     int16_t *table;            // [tab_n]
     float2 *lohi;              // [n_s + 2]
     uint32_t *orig;            // [n_c + 1]
@@ -63,19 +74,25 @@ struct Smem {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+__host__ __device__ inline bool uses_midpoint(const CountParams &p) { return p.n_mu > 1 && p.los == TPCF_LOS_MIDPOINT; }
+
 __host__ __device__ inline size_t smem_layout(const CountParams &p, size_t *off)
 {
+    const bool mid = uses_midpoint(p);
     size_t o = 0;
     off[0] = o; o = align16(o + sizeof(unsigned long long) * (p.n_s + 1));  // T
     off[1] = o; o = align16(o + sizeof(float4) * UNIT_CHUNK);              // a chunk
-    off[2] = o; o = align16(o + sizeof(float4) * WARPS * P * 32);           // b copies
-    off[3] = o; o = align16(o + sizeof(uint16_t) * WARPS * QN * 32 * 2);    // queues + compacted copies
-    off[4] = o; o = align16(o + sizeof(int) * p.nbin);                      // histogram
+    off[2] = o; o = align16(o + (mid ? sizeof(float4) * WARPS * P * 32      // b copies
+                                     : sizeof(uint32_t) * WARPS * P * 32)); // b indices
+    off[3] = o; o = align16(o + (mid ? sizeof(uint16_t) * WARPS * QN * 32 * 2  // queues + compacted
+                                     : sizeof(float2) * WARPS * (QX + 1) * 32));
+    off[4] = o; o = align16(o + sizeof(int) * (p.nbin + (mid ? 0 : 32)));   // histogram (+ spare words)
     off[5] = o; o = align16(o + sizeof(float2) * (p.n_s + 2));              // edge bands
     off[6] = o; o = align16(o + sizeof(uint32_t) * (p.n_c + 1));            // cell corners
     off[7] = o; o = align16(o + sizeof(int16_t) * (p.linear ? 0 : p.tab_n)); // s table
     off[8] = o; o = align16(o + sizeof(Seg) * (MAX_SEGS + 1));              // segments
     off[9] = o; o = align16(o + sizeof(int) * 8);
+    off[10] = o; o = align16(o + (mid ? 0 : sizeof(uint2) * WARPS * XCAP)); // recheck lists
     return o;
 }
 
@@ -154,12 +171,7 @@ __device__ __forceinline__ float rsqrt_approx(float x)
 
 // 32-bit shared-memory accesses (addresses from __cvta_generic_to_shared)
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// 16-bit shared accesses through 32-bit registers (the load zero-extends,
-// the store keeps the low half)
-__device__ __forceinline__ void sts16(uint32_t a, uint32_t v)
-{
-    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
+// 16-bit shared load through a 32-bit register (zero-extended)
 __device__ __forceinline__ uint32_t lds16(uint32_t a)
 {
     uint32_t v;
@@ -190,15 +202,14 @@ __device__ __forceinline__ void red_inc(uint32_t a)
 {
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a) : "memory");
 }
-// histogram increment when bin >= 0, without a branch
-__device__ __forceinline__ void red_inc_if(uint32_t base, int bin)
+// histogram increment when ok != 0, without a branch
+__device__ __forceinline__ void red_inc_if(uint32_t addr, int ok)
 {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .u32 a;\n\t"
-        "setp.ge.s32 p, %1, 0;\n\t"
-        "mad.lo.u32 a, %1, 4, %0;\n\t"
-        "@p red.shared.add.u32 [a], 1;\n\t}" ::"r"(base),
-        "r"(bin)
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.s32 p, %1, 0;\n\t"
+        "@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(addr),
+        "r"(ok)
         : "memory");
 }
 // 16-bit shared load when live (else 0), without a branch
@@ -226,11 +237,31 @@ __device__ __forceinline__ void sts16_if(uint32_t a, uint32_t v, bool pred)
         : "memory");
 }
 
-// Binning constants, copied from the launch parameters into registers once.
-struct BinConst {
-    float tab_bias, inv_nmu2, s_scale, s_c0, s_c1, mu_c1, mu_c2, mu_c3, hit_max, dot_margin;
-    uint32_t tab_key0, tab_last;
-    int tab_shift, n_s, n_mu;
+// x path push: store (d2, e) at the column head; advance the head (one slot
+// row of 32 lanes x 8 bytes) only when d2 < h.  NaN never passes.
+__device__ __forceinline__ void push_if_lt(uint32_t &head, float d2, uint32_t e, float h)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.lt.f32 p, %1, %2;\n\t"
+        "st.shared.v2.b32 [%0], {%3, %4};\n\t"
+        "@p add.u32 %0, %0, 256;\n\t}"
+        : "+r"(head)
+        : "f"(d2), "f"(h), "r"(__float_as_uint(d2)), "r"(e)
+        : "memory");
+}
+__device__ __forceinline__ float2 lds64(uint32_t a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+// Classification of a queued pair: its histogram slot as a shared address
+// (meaningful when good), good = binned and outside every error band, amb =
+// inside an error band (recheck exactly).  Neither: beyond the last edge.
+struct Cls {
+    uint32_t addr;
+    bool good, amb;
 };
 
 template <bool MU, bool MID, bool LIN>
@@ -238,57 +269,68 @@ struct Ctx {
     const CountParams &prm;
     const Smem &sm;
     const Mesh &m;
-    BinConst c;
     int lane, warp;
     uint32_t q;                // this lane's queue column (shared address of slot 0)
     uint32_t cq;               // this warp's compacted queue (shared address)
-    uint32_t bc;               // this warp's b copies (shared address; .w: b index)
+    uint32_t bc;               // this warp's b copies (midpoint path; .w: b index) or b indices (x path)
+    uint32_t xl;               // this warp's recheck list (x path, shared address)
+    uint32_t n_list;           // entries in it (warp-uniform)
+    uint32_t hdum;             // this lane's spare word after the histogram (x path)
     uint32_t abase;            // the a-chunk (shared address)
     uint32_t hbase;            // the block histogram (shared address)
+    uint32_t hadj;             // hbase minus the bias of the encoded bin keys (see classify)
     uint32_t a0, na;           // current unit's a-chunk
     float gx, gy, gz;          // 2 (corner(A) - observer), midpoint line of sight
     unsigned n_exact, n_binned;
 
-    // Bin of a queued pair: >= 0, -1 (not binned) or -2 (recheck exactly).
-    // Straight-line code: every lane runs the same instructions.
-    __device__ __forceinline__ int classify(float d2, float dx, const float4 &a, const float4 &b) const
+    // Every bin decision is a floor of an FP32 estimate x of an exact value
+    // x* whose error bound gives an interval [x_lo, x_hi] around it, computed
+    // with directed roundings so that it certainly holds x*.  With
+    // B = 1.5 * 2^23, fadd_rd(x, B) = floor(x) + B exactly for |x| < 2^22, so
+    // the floors of both ends are compared as floats: equal means the bin is
+    // certain, different means an edge (or NaN, from d2 = 0) lies inside the
+    // interval and the pair is rechecked exactly.  The bit pattern of
+    // floor(x_lo) + B is the bin plus the pattern of B; the histogram address
+    // absorbs that bias (hadj).  Straight-line code: every lane runs the same
+    // instructions.
+    __device__ __forceinline__ Cls classify(float d2, float dx, const float4 &a, const float4 &b) const
     {
-        const float big = 12582912.0f;   // 1.5 * 2^23: x + big rounds x to an integer
-        bool amb = false, valid;
-        int k;
+        const float big = 12582912.0f;   // 1.5 * 2^23
+        Cls o;
+        bool amb, valid;
+        uint32_t ks;                      // s bin, biased (LIN: + bits of B)
         float r = 0.0f;
         if (LIN) {
-            // s bin = floor(u), u = sqrt(d2) / (q ds); ambiguous near an interior
-            // edge or near s_max
-            r = rsqrt_approx(__fmul_rn(d2, c.inv_nmu2));      // n_mu / sqrt(d2)
-            const float u = __fmul_rn(__fmul_rn(d2, r), c.s_scale);
-            const float mf = __fadd_rn(u, big);
-            const int ki = __float_as_int(mf) - 0x4B400000;
-            const float ds = __fsub_rn(u, __fsub_rn(mf, big));
-            // near an edge (or NaN: d2 = 0).  The s = 0 edge needs no recheck
-            // but costs nothing to include; s_max is an edge like the others.
-            amb = !(fabsf(ds) >= __fmaf_rn(c.s_c1, u, c.s_c0));
-            k = ki - (ds < 0.0f ? 1 : 0);
-            valid = (unsigned)k < (unsigned)c.n_s;
+            // u* = sqrt(D2) / (q ds); v = n_mu sqrt(d2) and u = v * s_scale
+            r = rsqrt_approx(__fmul_rn(d2, prm.inv_nmu2));   // n_mu / sqrt(d2)
+            const float v = __fmul_rn(d2, r);
+            const float flo = __fadd_rd(__fmaf_rd(v, prm.s_lo_mul, -prm.s_c0), big);
+            const float fhi = __fadd_rd(__fmaf_ru(v, prm.s_hi_mul, prm.s_c0), big);
+            amb = !(flo == fhi);
+            valid = flo < prm.s_top;
+            ks = __float_as_uint(flo);
         } else {
-            const uint32_t key = min((__float_as_uint(__fadd_rn(d2, c.tab_bias)) >> c.tab_shift) - c.tab_key0,
-                                     c.tab_last);
-            k = sm.table[key];
+            const uint32_t key = min((__float_as_uint(__fadd_rn(d2, prm.tab_bias)) >> prm.tab_shift) - prm.tab_key0,
+                                     (uint32_t)(prm.tab_n - 1));
+            int k = sm.table[key];
             amb = (k == CODE_AMBIG);
             k = amb ? -1 : k;
             const float2 lh = sm.lohi[k + 1];
             const bool ge_hi = d2 >= lh.y;
             amb |= (d2 >= lh.x) && !ge_hi;
             k += ge_hi ? 1 : 0;
-            valid = (unsigned)k < (unsigned)c.n_s;
+            valid = (unsigned)k < (unsigned)prm.n_s;
+            ks = (uint32_t)k;
         }
-        int bin = k;
         if (MU) {
-            float t, beta;
+            // t* = n_mu |mu|; the top edge t* = n_mu (mu = 1) is an edge like the
+            // others, so a pair there is rechecked and never needs a clamp
+            float tlo, thi;
             if (!MID) {
-                if (!LIN) r = rsqrt_approx(__fmul_rn(d2, c.inv_nmu2));   // n_mu / sqrt(d2)
-                t = __fmul_rn(fabsf(dx), r);
-                beta = __fmaf_rn(c.mu_c1, r, c.mu_c2);
+                if (!LIN) r = rsqrt_approx(__fmul_rn(d2, prm.inv_nmu2));   // n_mu / sqrt(d2)
+                const float bt = __fmaf_ru(prm.mu_c1, r, prm.mu_c2);
+                tlo = __fmaf_rd(fabsf(dx), r, -bt);
+                thi = __fmaf_ru(fabsf(dx), r, bt);
             } else {
                 const float ex = __fsub_rn(a.x, b.x), ey = __fsub_rn(a.y, b.y), ez = __fsub_rn(a.z, b.z);
                 const float lx = __fadd_rn(__fadd_rn(gx, a.x), b.x);
@@ -297,24 +339,24 @@ struct Ctx {
                 const float dot = __fmaf_rn(ez, lz, __fmaf_rn(ey, ly, __fmul_rn(ex, lx)));
                 const float l2 = __fmaf_rn(lz, lz, __fmaf_rn(ly, ly, __fmul_rn(lx, lx)));
                 const float rs = rsqrt_approx(d2), rl = rsqrt_approx(l2);
-                t = __fmul_rn(__fmul_rn(__fmul_rn(fabsf(dot), rs), rl), (float)c.n_mu);
-                beta = __fmaf_rn(c.mu_c1, rs, __fmaf_rn(c.mu_c3, rl, c.mu_c2));
+                const float t = __fmul_rn(__fmul_rn(__fmul_rn(fabsf(dot), rs), rl), prm.f_nmu);
+                const float bt = __fmaf_ru(prm.mu_c1, rs, __fmaf_ru(prm.mu_c3, rl, prm.mu_c2));
+                tlo = __fsub_rd(t, bt);
+                thi = __fadd_ru(t, bt);
             }
-            // the pair is ambiguous when t = n_mu |mu| (>= 0) lies within beta
-            // of an integer (a mu edge; 0 and n_mu need no recheck but cost
-            // nothing to include), or is NaN (d2 = 0)
-            const float mf = __fadd_rn(t, big);
-            const int mi = __float_as_int(mf) - 0x4B400000;
-            const float d = __fsub_rn(t, __fsub_rn(mf, big));
-            amb |= !(fabsf(d) >= beta);
-            const int j = min(mi - (d < 0.0f ? 1 : 0), c.n_mu - 1);   // mu = 1 in the top bin
-            bin = k * c.n_mu + j;
+            const float jlo = __fadd_rd(tlo, big), jhi = __fadd_rd(thi, big);
+            amb |= !(jlo == jhi);
+            o.addr = hadj + 4u * (ks * (uint32_t)prm.n_mu + __float_as_uint(jlo));
+        } else {
+            o.addr = hadj + 4u * ks;
         }
-        return amb ? -2 : (valid ? bin : -1);
+        o.amb = amb;
+        o.good = valid && !amb;
+        return o;
     }
 
-    // Bin of queue entry v (a index | b copy index << 8).
-    __device__ __forceinline__ int bin_of(uint32_t v) const
+    // Classification of queue entry v (a index | b copy index << 8).
+    __device__ __forceinline__ Cls bin_of(uint32_t v) const
     {
         const float4 a = lds128(abase + 16u * (v & 255u));
         const float4 b = lds128(bc + 16u * (v >> 8));
@@ -323,12 +365,12 @@ struct Ctx {
         return classify(d2, dx, a, b);
     }
 
-    // Bin every queued pair.  The lanes' queues are first packed into one
+    // Midpoint path: bin every queued pair.  The lanes' queues are first packed into one
     // warp-contiguous list (a index | b copy index << 8), so that the binning
     // loop runs with all lanes busy whatever the spread of per-lane counts.
     // Pairs that need the exact recheck are rechecked at the end.  n = this
     // lane's count.
-    __device__ __forceinline__ void flush(uint32_t n)
+    __device__ __forceinline__ void flush_mid(uint32_t n)
     {
         uint32_t total;
         const uint32_t pos = warp_exclusive_sum(n, lane, total);
@@ -347,20 +389,19 @@ struct Ctx {
             const bool live0 = e0 < total, live1 = e1 < total;
             const uint32_t v0 = lds16_if(cq + 2u * e0, live0);
             const uint32_t v1 = lds16_if(cq + 2u * e1, live1);
-            int bin0 = bin_of(v0), bin1 = bin_of(v1);   // dead slots read entry 0: in bounds, discarded
-            bin0 = live0 ? bin0 : -1;
-            bin1 = live1 ? bin1 : -1;
-            red_inc_if(hbase, bin0);
-            red_inc_if(hbase, bin1);
-            const unsigned am0 = __ballot_sync(0xffffffffu, bin0 == -2);
-            const unsigned am1 = __ballot_sync(0xffffffffu, bin1 == -2);
+            const Cls c0 = bin_of(v0), c1 = bin_of(v1);   // dead slots read entry 0: in bounds, discarded
+            red_inc_if(c0.addr, live0 && c0.good);
+            red_inc_if(c1.addr, live1 && c1.good);
+            const bool x0 = live0 && c0.amb, x1 = live1 && c1.amb;
+            const unsigned am0 = __ballot_sync(0xffffffffu, x0);
+            const unsigned am1 = __ballot_sync(0xffffffffu, x1);
             if (am0 | am1) {
                 // rare: keep the entries for the exact recheck, written over
                 // entries this loop has already consumed
                 __syncwarp();
-                sts16_if(cq + 2u * (n_amb + __popc(am0 & lt)), v0, bin0 == -2);
+                sts16_if(cq + 2u * (n_amb + __popc(am0 & lt)), v0, x0);
                 n_amb += __popc(am0);
-                sts16_if(cq + 2u * (n_amb + __popc(am1 & lt)), v1, bin1 == -2);
+                sts16_if(cq + 2u * (n_amb + __popc(am1 & lt)), v1, x1);
                 n_amb += __popc(am1);
             }
         }
@@ -375,6 +416,221 @@ struct Ctx {
         __syncwarp();
     }
 
+    // ---- x line of sight ----
+
+    // Exact recheck of the set-aside pairs, one per lane.
+    __device__ __forceinline__ void recheck_list()
+    {
+        __syncwarp();
+        for (uint32_t e = lane; e < n_list; e += 32) {
+            uint2 pr;
+            asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(pr.x), "=r"(pr.y) : "r"(xl + 8u * e) : "memory");
+            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, pr.x, pr.y);
+            n_exact++;
+            if (bin >= 0) red_inc(hbase + 4u * (uint32_t)bin);
+        }
+        __syncwarp();
+        n_list = 0;
+    }
+
+    // d2 and dx of (a-chunk point a, this lane's b-point p), FP32 in A's frame.
+    template <int p>
+    __device__ __forceinline__ float d2_x(const float4 &a, const float (&bx)[P], const float (&by)[P],
+                                          const float (&bz)[P], float &dx) const
+    {
+        dx = __fsub_rn(a.x, bx[p]);
+        const float dy = __fsub_rn(a.y, by[p]), dz = __fsub_rn(a.z, bz[p]);
+        return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    }
+
+    // Push threshold of (a-chunk point ai, b slot p): the last edge's band,
+    // or 0 (never passes) for a self-cell pair that is not a < b.
+    template <bool SELF>
+    __device__ __forceinline__ float thr_x(uint32_t ai, uint32_t ib) const
+    {
+        return (!SELF || a0 + ai < ib) ? prm.hit_max : 0.0f;
+    }
+
+    // The pair behind this lane's queue entry k (the k-th push that advanced
+    // its head since the flush window began at a-chunk index a_lo): the
+    // window's pushes are replayed in push order (a ascending, then p) with
+    // the same FP32 arithmetic.  Rare (ambiguous pairs only) and divergent.
+    template <bool SELF>
+    __device__ __forceinline__ void find_pair(uint32_t k, uint32_t a_lo, uint32_t ib0, const float (&bx)[P],
+                                              const float (&by)[P], const float (&bz)[P], uint32_t &ai_out,
+                                              uint32_t &p_out) const
+    {
+        uint32_t j = 0;
+        ai_out = a_lo;
+        p_out = 0;
+        for (uint32_t ai = a_lo; ai < na; ai++) {
+            const float4 a = lds128(abase + 16u * ai);
+            float dx;
+            const float d0 = d2_x<0>(a, bx, by, bz, dx), d1 = d2_x<1>(a, bx, by, bz, dx);
+            const float d2v = d2_x<2>(a, bx, by, bz, dx), d3 = d2_x<3>(a, bx, by, bz, dx);
+            const bool h0 = d0 < thr_x<SELF>(ai, ib0), h1 = d1 < thr_x<SELF>(ai, ib0 + 32u);
+            const bool h2 = d2v < thr_x<SELF>(ai, ib0 + 64u), h3 = d3 < thr_x<SELF>(ai, ib0 + 96u);
+            const uint32_t c = (uint32_t)h0 + (uint32_t)h1 + (uint32_t)h2 + (uint32_t)h3;
+            if (j + c > k) {
+                uint32_t r = k - j, p = 0;
+                if (h0) { if (r == 0) { p = 0; goto done; } r--; }
+                if (h1) { if (r == 0) { p = 1; goto done; } r--; }
+                if (h2) { if (r == 0) { p = 2; goto done; } r--; }
+                p = 3;
+            done:
+                ai_out = ai;
+                p_out = p;
+                return;
+            }
+            j += c;
+        }
+    }
+
+    // Append this lane's entry k (when x) to the recheck list at its ballot rank.
+    template <bool SELF>
+    __device__ __forceinline__ void set_aside(bool x, uint32_t k, unsigned am, uint32_t lt, uint32_t a_lo, uint32_t ib0,
+                                              const float (&bx)[P], const float (&by)[P], const float (&bz)[P])
+    {
+        if (x) {
+            uint32_t ai, p, ib;
+            find_pair<SELF>(k, a_lo, ib0, bx, by, bz, ai, p);
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(ib) : "r"(bc + 4u * (p * 32u + (uint32_t)lane)) : "memory");
+            const uint32_t at = xl + 8u * (n_list + __popc(am & lt));
+            asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(at), "r"(a0 + ai), "r"(ib) : "memory");
+        }
+        n_list += __popc(am);
+    }
+
+    // Histogram increment when ok, as an unpredicated add of ok: a lane with
+    // nothing to count adds 0 to its own spare word after the histogram.
+    __device__ __forceinline__ void red_x(uint32_t addr, bool ok) const
+    {
+        const uint32_t at = ok ? addr : hdum;
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(at), "r"((uint32_t)ok) : "memory");
+    }
+
+    // Bin this lane's column (n entries; the window's pushes began at a-chunk
+    // index a_lo), two entries per lane per pass.  All lanes run the same
+    // passes; a lane past its count reads a stale slot and discards it (slot
+    // QX exists and is never written: always in bounds).
+    template <bool SELF>
+    __device__ __forceinline__ void flush_x(uint32_t n, uint32_t a_lo, uint32_t ib0, const float (&bx)[P],
+                                            const float (&by)[P], const float (&bz)[P])
+    {
+        const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
+        const uint32_t lt = (1u << lane) - 1u;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (uint32_t k = 0; k < nmax; k += 2) {
+            const bool live0 = k < n, live1 = k + 1 < n;
+            const float2 e0 = lds64(q + k * 256u), e1 = lds64(q + (k + 1u) * 256u);
+            const Cls c0 = classify(e0.x, e0.y, z, z), c1 = classify(e1.x, e1.y, z, z);
+            red_x(c0.addr, live0 && c0.good);
+            red_x(c1.addr, live1 && c1.good);
+            const bool x0 = live0 && c0.amb, x1 = live1 && c1.amb;
+            const unsigned am0 = __ballot_sync(0xffffffffu, x0);
+            const unsigned am1 = __ballot_sync(0xffffffffu, x1);
+            if (am0 | am1) {
+                // rare: at most 31 + 64 entries after this, within XCAP
+                set_aside<SELF>(x0, k, am0, lt, a_lo, ib0, bx, by, bz);
+                set_aside<SELF>(x1, k + 1, am1, lt, a_lo, ib0, bx, by, bz);
+                if (n_list >= 32) recheck_list();
+            }
+        }
+    }
+
+    // One pair: push (d2, dx) when d2 < h.
+    template <int p>
+    __device__ __forceinline__ void push_x(uint32_t &head, const float4 &a, const float (&bx)[P], const float (&by)[P],
+                                           const float (&bz)[P], float h) const
+    {
+        float dx;
+        const float d2 = d2_x<p>(a, bx, by, bz, dx);
+        push_if_lt(head, d2, __float_as_uint(dx), h);
+    }
+
+    // Load one b-point (shifted into A's frame) into lane registers and its
+    // index into the warp's slot table; a missing point sits at 1e30, where
+    // d2 overflows to +inf and never passes.
+    __device__ __forceinline__ void load_bx(int p, bool ok, uint32_t i, float sy, float sz, uint32_t orig_ax,
+                                            float (&bx)[P], float (&by)[P], float (&bz)[P]) const
+    {
+        if (ok) {
+            const float4 v = __ldg(m.pf + i);
+            const int cx = m.pcx[i];
+            const float sx = (float)(int)(sm.orig[cx] - orig_ax);
+            bx[p] = __fadd_rn(v.x, sx);
+            by[p] = __fadd_rn(v.y, sy);
+            bz[p] = __fadd_rn(v.z, sz);
+        } else {
+            bx[p] = by[p] = bz[p] = 1e30f;
+            i = 0;
+        }
+        asm volatile("st.shared.u32 [%0], %1;" ::"r"(bc + 4u * (uint32_t)(p * 32 + lane)), "r"(i) : "memory");
+    }
+
+    // all pairs of the a-chunk with one tile of b-points: the self cell of an
+    // auto count (SELF, indices base..s1) or a packed tile at offset o_base of
+    // the concatenated runs (n_seg runs, total points).
+    template <bool SELF>
+    __device__ __forceinline__ void tile_x(uint32_t base, uint32_t s1, uint32_t o_base, int n_seg, uint32_t total,
+                                           uint32_t orig_ax)
+    {
+        float bx[P], by[P], bz[P];
+        if (SELF) {
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                const uint32_t i = base + lane + 32u * p;
+                load_bx(p, i < s1, i, 0.0f, 0.0f, orig_ax, bx, by, bz);
+            }
+        } else {
+            const uint32_t o0 = o_base + lane;
+            int lo = 0, hi = n_seg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sm.segs[mid].off0 <= o0) lo = mid; else hi = mid - 1;
+            }
+            int g = lo;
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                const uint32_t o = o0 + 32u * p;
+                while (g + 1 < n_seg && sm.segs[g + 1].off0 <= o) g++;
+                const Seg sg = sm.segs[g];
+                load_bx(p, o < total, sg.s0 + (o - sg.off0), sg.sy, sg.sz, orig_ax, bx, by, bz);
+            }
+        }
+        // A flush comes before 2P more pushes could run past QX slots.
+        uint32_t head = q, a_lo = 0;
+        const uint32_t lim = q + (uint32_t)(QX - 2 * P) * 256u;
+        const uint32_t ib0 = base + lane;   // used by SELF tiles only
+        uint32_t ai = 0;
+        for (; ai + 1 < na; ai += 2) {
+            const float4 a = lds128(abase + 16u * ai), c = lds128(abase + 16u * (ai + 1));
+            push_x<0>(head, a, bx, by, bz, thr_x<SELF>(ai, ib0));
+            push_x<1>(head, a, bx, by, bz, thr_x<SELF>(ai, ib0 + 32u));
+            push_x<2>(head, a, bx, by, bz, thr_x<SELF>(ai, ib0 + 64u));
+            push_x<3>(head, a, bx, by, bz, thr_x<SELF>(ai, ib0 + 96u));
+            push_x<0>(head, c, bx, by, bz, thr_x<SELF>(ai + 1, ib0));
+            push_x<1>(head, c, bx, by, bz, thr_x<SELF>(ai + 1, ib0 + 32u));
+            push_x<2>(head, c, bx, by, bz, thr_x<SELF>(ai + 1, ib0 + 64u));
+            push_x<3>(head, c, bx, by, bz, thr_x<SELF>(ai + 1, ib0 + 96u));
+            if (__any_sync(0xffffffffu, head > lim)) {
+                flush_x<SELF>((head - q) >> 8, a_lo, ib0, bx, by, bz);
+                head = q;
+                a_lo = ai + 2;
+            }
+        }
+        if (ai < na) {
+            const float4 a = lds128(abase + 16u * ai);
+            push_x<0>(head, a, bx, by, bz, thr_x<SELF>(ai, ib0));
+            push_x<1>(head, a, bx, by, bz, thr_x<SELF>(ai, ib0 + 32u));
+            push_x<2>(head, a, bx, by, bz, thr_x<SELF>(ai, ib0 + 64u));
+            push_x<3>(head, a, bx, by, bz, thr_x<SELF>(ai, ib0 + 96u));
+        }
+        if (__any_sync(0xffffffffu, head != q)) flush_x<SELF>((head - q) >> 8, a_lo, ib0, bx, by, bz);
+    }
+
+    // ---- midpoint line of sight ----
+
     // Load one b-point into lane registers (shifted into A's frame) and into
     // the warp's b copies used by the flush.
     __device__ __forceinline__ void load_b(int p, bool ok, uint32_t i, float sy, float sz, uint32_t orig_ax,
@@ -388,7 +644,7 @@ struct Ctx {
             by[p] = __fadd_rn(v.y, sy);
             bz[p] = __fadd_rn(v.z, sz);
             const float b2 = __fmaf_rn(bz[p], bz[p], __fmaf_rn(by[p], by[p], __fmul_rn(bx[p], bx[p])));
-            hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, c.hit_max)), c.dot_margin);
+            hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, prm.hit_max)), prm.dot_margin);
         } else {
             bx[p] = by[p] = bz[p] = 0.0f;
             hb[p] = __int_as_float(0x7f800000);   // +inf: never passes
@@ -403,7 +659,7 @@ struct Ctx {
     // auto count (SELF, indices base..s1) or a packed tile at offset o_base of
     // the concatenated runs (n_seg runs, total points).
     template <bool SELF>
-    __device__ __forceinline__ void tile(uint32_t base, uint32_t s1, uint32_t o_base, int n_seg, uint32_t total,
+    __device__ __forceinline__ void tile_mid(uint32_t base, uint32_t s1, uint32_t o_base, int n_seg, uint32_t total,
                                          uint32_t orig_ax)
     {
         float bx[P], by[P], bz[P], hb[P];
@@ -455,7 +711,7 @@ struct Ctx {
                 push_if_ge(head, ((ai + 1) | lane8) | (uint32_t)(p << 13), t, h);
             }
             if (__any_sync(0xffffffffu, head > lim)) {
-                flush((head - q) >> 6);
+                flush_mid((head - q) >> 6);
                 head = q;
             }
         }
@@ -468,7 +724,7 @@ struct Ctx {
                 push_if_ge(head, (ai | lane8) | (uint32_t)(p << 13), t, h);
             }
         }
-        if (__any_sync(0xffffffffu, head != q)) flush((head - q) >> 6);
+        if (__any_sync(0xffffffffu, head != q)) flush_mid((head - q) >> 6);
     }
 };
 
@@ -574,13 +830,15 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
                                                                 int persistent, int term_pl, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    size_t off[10];
+    size_t off[11];
     smem_layout(prm, off);
     Smem sm;
     sm.T = (unsigned long long *)(smem_raw + off[0]);
     sm.a = (float4 *)(smem_raw + off[1]);
     sm.bcopy = (float4 *)(smem_raw + off[2]);
-    sm.queue = (uint16_t *)(smem_raw + off[3]);
+    sm.bidx = (uint32_t *)(smem_raw + off[2]);
+    sm.queue = smem_raw + off[3];
+    sm.xlist = (uint2 *)(smem_raw + off[10]);
     sm.hist = (int *)(smem_raw + off[4]);
     sm.lohi = (float2 *)(smem_raw + off[5]);
     sm.orig = (uint32_t *)(smem_raw + off[6]);
@@ -595,29 +853,27 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
     for (int i = tid; i < prm.nbin; i += blockDim.x) sm.hist[i] = 0;
 
-    BinConst bcst;
-    bcst.tab_bias = prm.tab_bias;
-    bcst.inv_nmu2 = prm.inv_nmu2;
-    bcst.s_scale = prm.s_scale;
-    bcst.s_c0 = prm.s_c0;
-    bcst.s_c1 = prm.s_c1;
-    bcst.mu_c1 = prm.mu_c1;
-    bcst.mu_c2 = prm.mu_c2;
-    bcst.mu_c3 = prm.mu_c3;
-    bcst.hit_max = prm.hit_max;
-    bcst.dot_margin = prm.dot_margin;
-    bcst.tab_key0 = prm.tab_key0;
-    bcst.tab_last = (uint32_t)(prm.tab_n - 1);
-    bcst.tab_shift = prm.tab_shift;
-    bcst.n_s = prm.n_s;
-    bcst.n_mu = prm.n_mu;
-    Ctx<MU, MID, LIN> cx{prm, sm, m, bcst, tid & 31, tid >> 5, 0u, 0u, 0u, 0u, 0u, 0, 0, 0.f, 0.f, 0.f, 0u, 0u};
-    const uint32_t qw = saddr(sm.queue) + (uint32_t)cx.warp * (QN * 32 * 2 * 2);
-    cx.q = qw + 2u * (uint32_t)cx.lane;
-    cx.cq = qw + QN * 32 * 2;
-    cx.bc = saddr(sm.bcopy) + (uint32_t)cx.warp * (P * 32 * 16);
+    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0.f, 0.f, 0.f, 0u, 0u};
+    if (MID) {
+        const uint32_t qw = saddr(sm.queue) + (uint32_t)cx.warp * (QN * 32 * 2 * 2);
+        cx.q = qw + 2u * (uint32_t)cx.lane;
+        cx.cq = qw + QN * 32 * 2;
+        cx.bc = saddr(sm.bcopy) + (uint32_t)cx.warp * (P * 32 * 16);
+    } else {
+        cx.q = saddr(sm.queue) + (uint32_t)cx.warp * ((QX + 1) * 32 * 8) + 8u * (uint32_t)cx.lane;
+        cx.bc = saddr(sm.bidx) + (uint32_t)cx.warp * (P * 32 * 4);
+        cx.xl = saddr(sm.xlist) + (uint32_t)cx.warp * (XCAP * 8);
+        cx.hdum = saddr(sm.hist) + 4u * ((uint32_t)prm.nbin + (uint32_t)cx.lane);
+    }
     cx.abase = saddr(sm.a);
     cx.hbase = saddr(sm.hist);
+    {
+        // classify encodes the s bin with the bias of B's bit pattern on the
+        // linear path, the mu bin always (see classify)
+        const uint32_t kB = 0x4B400000u;
+        const uint32_t sb = LIN ? kB : 0u;
+        cx.hadj = cx.hbase - 4u * (MU ? sb * (uint32_t)prm.n_mu + kB : sb);
+    }
     unsigned long long n_cand = 0;
 
     // per-launch mode: this block walks the chunks of one cell of one term
@@ -672,16 +928,19 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
             if (ti < n_self) {
                 const uint32_t base = self0 + ti * TILE;
                 n_cand += (unsigned long long)min(self1 - base, (uint32_t)TILE) * cx.na;
-                cx.template tile<true>(base, self1, 0u, ns, total, oax);
+                if (MID) cx.template tile_mid<true>(base, self1, 0u, ns, total, oax);
+                else cx.template tile_x<true>(base, self1, 0u, ns, total, oax);
             } else {
                 const uint32_t ob = (ti - n_self) * TILE;
                 n_cand += (unsigned long long)min(total - ob, (uint32_t)TILE) * cx.na;
-                cx.template tile<false>(0u, 0u, ob, ns, total, oax);
+                if (MID) cx.template tile_mid<false>(0u, 0u, ob, ns, total, oax);
+                else cx.template tile_x<false>(0u, 0u, ob, ns, total, oax);
             }
             uint32_t nx = 0;
             if (cx.lane == 0) nx = (uint32_t)atomicAdd(&sm.misc[3], 1) + WARPS;
             ti = __shfl_sync(0xffffffffu, nx, 0);
         }
+        if (!MID && cx.n_list) cx.recheck_list();   // the list refers to this unit's histogram
         __syncthreads();
         // drain the block histogram into the term's int64 histogram
         for (int b = tid; b < prm.nbin; b += blockDim.x) {
@@ -730,7 +989,7 @@ void *select_kernel(const CountParams &p)
 int paircount_smem_bytes(const CountParams &p, int warps_per_block)
 {
     (void)warps_per_block;
-    size_t off[10];
+    size_t off[11];
     return (int)smem_layout(p, off);
 }
 

@@ -272,7 +272,9 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
     if (b.los == TPCF_LOS_X) {
         // beta = mu_c1 * r + mu_c2, r = n_mu / sqrt(d2)
         p.mu_c1 = (float)(1.1 * (1.0 + std::sqrt(3.0)) * E);
-        p.mu_c2 = (float)(b.n_mu * std::ldexp(1.0, -19));
+        // the kernel bounds t* by fma(|dx|, r, -/+beta), i.e. around the exact
+        // product |dx| r rather than its rounding: one more ulp of n_mu
+        p.mu_c2 = (float)(b.n_mu * (std::ldexp(1.0, -19) + std::ldexp(1.0, -23)));
     } else {
         // observer in open grid units; l = u_a + u_b - 2 u_obs
         for (int c = 0; c < 3; c++)
@@ -302,7 +304,14 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
         p.s_scale = (float)(1.0 / ((double)b.n_mu * qds));
         p.s_c0 = (float)(1.5 * (std::sqrt(3.0) * E / qds + 1.5 * E * E / (qds * qds)) + 1e-6);
         p.s_c1 = (float)std::ldexp(1.0, -19);
+        // u = fl(v s_scale) with v = fl(d2 r); |u - u*| <= s_c0 + s_c1 u gives
+        // v s_scale (1 - 2^-24)(1 - s_c1) - s_c0 <= u* <= v s_scale (1 + 2^-24)(1 + s_c1) + s_c0
+        const double sc = (double)p.s_scale, r24 = std::ldexp(1.0, -24);
+        p.s_lo_mul = down_f(sc * (1.0 - (double)p.s_c1) * (1.0 - r24) * (1.0 - r24));
+        p.s_hi_mul = up_f(sc * (1.0 + (double)p.s_c1) * (1.0 + r24) * (1.0 + r24));
     }
+    p.s_top = 12582912.0f + (float)b.n_s;
+    p.f_nmu = (float)b.n_mu;
 
     // s-bin table over FP32 bit patterns of d2 + bias.  The bias (a power of
     // two well below the first positive edge band) keeps every key at or

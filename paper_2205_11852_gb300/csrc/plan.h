@@ -8,7 +8,7 @@
 
 namespace tpcf {
 
-constexpr int UNIT_CHUNK = 256;   // a-points per work unit
+constexpr int UNIT_CHUNK = 128;   // a-points per work unit (at most 128: 7-bit a index in the pair key)
 
 struct Plan {
     CountParams prm;

@@ -68,6 +68,10 @@ struct CountParams {
     int linear;            // edges e_k = k * ds exactly: s bin = floor(sqrt(D2) / (q ds))
     float s_scale;         // 1 / (n_mu q ds): u = d2 * (n_mu / sqrt(d2)) * s_scale = sqrt(d2) / (q ds)
     float s_c0, s_c1;      // s band for the linear path: beta_s = s_c0 + s_c1 * u
+    float s_lo_mul, s_hi_mul;  // linear path, v = d2 * (n_mu / sqrt(d2)): u* lies in
+                               // [v s_lo_mul - s_c0, v s_hi_mul + s_c0] (directed roundings)
+    float s_top;           // 1.5 * 2^23 + n_s: floor(u_lo) + 1.5 * 2^23 < s_top <=> s bin < n_s
+    float f_nmu;           // n_mu as a float
     long long obs[3];      // observer in grid units (midpoint line of sight)
     unsigned long long T[MAX_NS + 1];        // exact squared edges in grid units
     float lo[MAX_NS + 2], hi[MAX_NS + 2];    // float bands: d2 < lo => D2 < T; d2 >= hi => D2 >= T;

@@ -403,7 +403,7 @@ def test_autotuner_choice_is_exact(tp):
     out = c.tpcf_count(_mocks_to_device(mocks), tb)
     c.tpcf_sync()
     info = c.tpcf_last_count_info()
-    assert info["cell_subdiv"] in (2, 3, 4) and info["unit_chunk"] in (128, 256)
+    assert info["cell_subdiv"] in (2, 3, 4) and info["unit_chunk"] in (64, 128)
     for m in (0, 7):
         o = oracle.count_mock(mocks[m].data, mocks[m].randoms, ob)
         assert np.array_equal(out["dd"][m].cpu().numpy(), o["DD"])
