@@ -49,7 +49,7 @@ struct Setup {
     // workspace
     void *uq = nullptr, *keys = nullptr, *us = nullptr, *pf = nullptr, *pcx = nullptr, *cc = nullptr,
          *cs = nullptr, *tmp = nullptr, *uc = nullptr, *ust = nullptr, *units = nullptr, *claim = nullptr,
-         *rqbuf = nullptr;
+         *rqbuf = nullptr, *bscr = nullptr;
     // small tables (host bytes and layout)
     std::vector<unsigned char> small;
     size_t o_cats = 0, o_terms = 0, o_orig = 0, o_tab = 0;
@@ -234,6 +234,7 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
     cudaError_t e = paircount_set_attrs(prm, S.smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "paircount_set_attrs");
     S.blocks = ctx->n_sm * paircount_max_blocks_per_sm(prm, 8, S.smem);
+    if ((rc = ensure(ctx, "pairscratch", paircount_scratch_bytes(S.blocks), &S.bscr))) return rc;
     return TPCF_OK;
 }
 
@@ -284,6 +285,7 @@ int enqueue(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, void *small
     L.warps_per_block = 8;
     L.smem_bytes = S.smem;
     L.chunk = S.chunk;
+    L.scratch = S.bscr;
     if (mode == TPCF_BATCHED) {
         CK(cudaMemsetAsync(uc + (S.ntc - 1), 0, 4, s));
         CK(launch_unit_count(d_terms, n_terms, d_cats, prm.n_cells, cs, S.chunk, uc, s));
@@ -305,7 +307,7 @@ int enqueue(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, void *small
         for (int t = 0; t < n_terms; t++) {
             L.persistent = 0;
             L.term = t;
-            L.blocks = prm.n_cells;
+            L.blocks = std::min(S.blocks, prm.n_cells);   // blocks stride over the cells
             CK(launch_paircount(prm, mesh, d_terms, d_cats, nullptr, nullptr, nullptr, d_tab, ctx->stats,
                                 ctx->status, L, s));
         }
@@ -358,7 +360,7 @@ std::string graph_key(const Setup &S, int mode, tpcf_ctx *ctx)
     put(S.small.data(), S.small.size());   // catalogue pointers, sizes, outputs, cell corners, table
     for (const RqCopy &c : S.rq) put(&c, sizeof(c));
     const void *ws[] = {S.uq, S.keys, S.us, S.pf, S.pcx, S.cc, S.cs, S.tmp, S.uc, S.ust, S.units, S.claim,
-                        S.rqbuf, S.dd, S.dr, S.rr, ctx->stats, ctx->stats_host, ctx->status};
+                        S.rqbuf, S.bscr, S.dd, S.dr, S.rr, ctx->stats, ctx->stats_host, ctx->status};
     put(ws, sizeof(ws));
     return k;
 }

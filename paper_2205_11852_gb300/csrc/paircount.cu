@@ -41,8 +41,15 @@ constexpr int QN = 24;          // queue slots per lane, midpoint path (16-bit e
 constexpr int QX = 18;          // queue slots per lane, x line of sight (8-byte entries)
 constexpr int XCAP = 96;        // per-warp list of pairs awaiting the exact recheck
 constexpr int WARPS = 8;        // warps per block
+constexpr int CAP = 12288;      // raw neighbour points filtered per window
+constexpr int SCR = CAP + 8 * 32;   // float4 scratch entries per block (window + per-warp rounding)
+// misc[] layout
+constexpr int M_CNT = 8;        // [WARPS] survivors per warp in the current window
+constexpr int M_BOX = 16;       // [6] a-chunk bounding box (float bits): lo xyz, hi xyz
+constexpr int M_N = 24;
 constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 static_assert(P == 4, "tile_x unrolls four b-points per lane");
+static_assert(UNIT_CHUNK % 32 == 0 && UNIT_CHUNK <= 128 && UNIT_CHUNK <= WARPS * 32, "a-chunk load and box");
 
 typedef unsigned __int128 u128;
 typedef __int128 i128;
@@ -57,7 +64,7 @@ struct Seg {
 };
 
 struct Smem {
-    float4 *a;                 // [UNIT_CHUNK]; .w: -|a|^2/2
+    float4 *a;                 // [UNIT_CHUNK + 8]; .w: -|a|^2/2; then per-warp bounding-box partials
     int *hist;                 // [nbin] (+ 32 spare words, x path)
     unsigned char *queue;      // x path: [WARPS][QX + 1][32] (d2, dx) pairs;
                                // midpoint path: [WARPS][QN][32] + [WARPS][QN * 32] 16-bit entries
@@ -69,7 +76,7 @@ struct Smem {
     uint32_t *orig;            // [n_c + 1]
     unsigned long long *T;     // [n_s + 1]
     Seg *segs;                 // [MAX_SEGS + 1], the last one a sentinel
-    int *misc;                 // [8]: unit, n_segs, packed points, next tile, self s0, self s1
+    int *misc;                 // [M_N]: unit, n_segs, packed points, next tile, self s0, self s1, counts, box
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -81,7 +88,7 @@ __host__ __device__ inline size_t smem_layout(const CountParams &p, size_t *off)
     const bool mid = uses_midpoint(p);
     size_t o = 0;
     off[0] = o; o = align16(o + sizeof(unsigned long long) * (p.n_s + 1));  // T
-    off[1] = o; o = align16(o + sizeof(float4) * UNIT_CHUNK);              // a chunk
+    off[1] = o; o = align16(o + sizeof(float4) * (UNIT_CHUNK + 8));        // a chunk + box partials
     off[2] = o; o = align16(o + (mid ? sizeof(float4) * WARPS * P * 32      // b copies
                                      : sizeof(uint32_t) * WARPS * P * 32)); // b indices
     off[3] = o; o = align16(o + (mid ? sizeof(uint16_t) * WARPS * QN * 32 * 2  // queues + compacted
@@ -91,7 +98,7 @@ __host__ __device__ inline size_t smem_layout(const CountParams &p, size_t *off)
     off[6] = o; o = align16(o + sizeof(uint32_t) * (p.n_c + 1));            // cell corners
     off[7] = o; o = align16(o + sizeof(int16_t) * (p.linear ? 0 : p.tab_n)); // s table
     off[8] = o; o = align16(o + sizeof(Seg) * (MAX_SEGS + 1));              // segments
-    off[9] = o; o = align16(o + sizeof(int) * 8);
+    off[9] = o; o = align16(o + sizeof(int) * M_N);
     off[10] = o; o = align16(o + (mid ? 0 : sizeof(uint2) * WARPS * XCAP)); // recheck lists
     return o;
 }
@@ -276,6 +283,9 @@ struct Ctx {
     uint32_t xl;               // this warp's recheck list (x path, shared address)
     uint32_t n_list;           // entries in it (warp-uniform)
     uint32_t hdum;             // this lane's spare word after the histogram (x path)
+    float4 *scr;               // this block's scratch: the current window's surviving b-points
+    uint32_t R;                // per-warp region length of the current window (entries)
+    uint32_t pk[WARPS];        // region starts in the filtered order (pk[0] = 0)
     uint32_t abase;            // the a-chunk (shared address)
     uint32_t hbase;            // the block histogram (shared address)
     uint32_t hadj;             // hbase minus the bias of the encoded bin keys (see classify)
@@ -414,6 +424,87 @@ struct Ctx {
             if (bin >= 0) red_inc(hbase + 4u * (uint32_t)bin);
         }
         __syncwarp();
+    }
+
+    // ---- neighbour filtering ----
+
+    // Filter raw neighbour points [w0, w0 + win) of the unit's concatenated
+    // runs: a point enters the window's list only if its distance to the
+    // a-chunk's bounding box is below the last edge's band (with a relative
+    // margin of 2^-16 over the FP32 box distance), so no pair the push test
+    // could pass is lost.  Warp w filters the w-th slice of the window and
+    // appends survivors (b' in A's frame, .w = b index) to its own region of
+    // the block's scratch, in order; the survivor count goes to misc.
+    __device__ __forceinline__ void filter_window(uint32_t w0, uint32_t win, int n_seg, uint32_t orig_ax)
+    {
+        R = (((win + WARPS - 1) / WARPS) + 31u) & ~31u;
+        const uint32_t r0 = w0 + (uint32_t)warp * R, r1 = min(r0 + R, w0 + win);
+        const float lox = __int_as_float(sm.misc[M_BOX + 0]), loy = __int_as_float(sm.misc[M_BOX + 1]);
+        const float loz = __int_as_float(sm.misc[M_BOX + 2]), hix = __int_as_float(sm.misc[M_BOX + 3]);
+        const float hiy = __int_as_float(sm.misc[M_BOX + 4]), hiz = __int_as_float(sm.misc[M_BOX + 5]);
+        const float hf = prm.hit_max * (1.0f + 1.0f / 65536.0f);
+        float4 *dst = scr + (size_t)warp * R;
+        uint32_t cnt = 0;
+        if (r0 < r1) {
+            const uint32_t o_first = r0 + lane;
+            int lo = 0, hi = n_seg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sm.segs[mid].off0 <= o_first) lo = mid; else hi = mid - 1;
+            }
+            int g = lo;
+            const uint32_t lt = (1u << lane) - 1u;
+            for (uint32_t c = r0; c < r1; c += 32) {
+                const uint32_t o = c + (uint32_t)lane;
+                while (g + 1 < n_seg && sm.segs[g + 1].off0 <= o) g++;
+                bool keep = false;
+                float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (o < r1) {
+                    const Seg sg = sm.segs[g];
+                    const uint32_t i = sg.s0 + (o - sg.off0);
+                    const float4 v = __ldg(m.pf + i);
+                    const float sx = (float)(int)(sm.orig[m.pcx[i]] - orig_ax);
+                    e.x = __fadd_rn(v.x, sx);
+                    e.y = __fadd_rn(v.y, sg.sy);
+                    e.z = __fadd_rn(v.z, sg.sz);
+                    e.w = __uint_as_float(i);
+                    const float qx = fmaxf(fmaxf(__fsub_rn(lox, e.x), __fsub_rn(e.x, hix)), 0.0f);
+                    const float qy = fmaxf(fmaxf(__fsub_rn(loy, e.y), __fsub_rn(e.y, hiy)), 0.0f);
+                    const float qz = fmaxf(fmaxf(__fsub_rn(loz, e.z), __fsub_rn(e.z, hiz)), 0.0f);
+                    keep = __fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmul_rn(qx, qx))) < hf;
+                }
+                const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                if (keep) dst[cnt + __popc(mk & lt)] = e;
+                cnt += __popc(mk);
+            }
+        }
+        if (lane == 0) sm.misc[M_CNT + warp] = (int)cnt;
+    }
+
+    // After the window's filter and a barrier: the region starts of the
+    // filtered order; returns the number of survivors.
+    __device__ __forceinline__ uint32_t window_regions()
+    {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int k = 0; k < WARPS; k++) {
+            pk[k] = acc;
+            acc += (uint32_t)sm.misc[M_CNT + k];
+        }
+        return acc;
+    }
+
+    // Surviving b-point at filtered position f (< the window's count).
+    __device__ __forceinline__ float4 fetch_f(uint32_t f) const
+    {
+        uint32_t w = 0, base = 0;
+#pragma unroll
+        for (int k = 1; k < WARPS; k++)
+            if (pk[k] <= f) {
+                w = (uint32_t)k;
+                base = pk[k];
+            }
+        return scr[(size_t)w * R + (f - base)];   // written by this block: plain (coherent) load
     }
 
     // ---- x line of sight ----
@@ -583,19 +674,20 @@ struct Ctx {
                 load_bx(p, i < s1, i, 0.0f, 0.0f, orig_ax, bx, by, bz);
             }
         } else {
-            const uint32_t o0 = o_base + lane;
-            int lo = 0, hi = n_seg - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sm.segs[mid].off0 <= o0) lo = mid; else hi = mid - 1;
-            }
-            int g = lo;
 #pragma unroll
             for (int p = 0; p < P; p++) {
-                const uint32_t o = o0 + 32u * p;
-                while (g + 1 < n_seg && sm.segs[g + 1].off0 <= o) g++;
-                const Seg sg = sm.segs[g];
-                load_bx(p, o < total, sg.s0 + (o - sg.off0), sg.sy, sg.sz, orig_ax, bx, by, bz);
+                const uint32_t f = o_base + (uint32_t)lane + 32u * p;
+                uint32_t i = 0;
+                if (f < total) {
+                    const float4 e = fetch_f(f);
+                    bx[p] = e.x;
+                    by[p] = e.y;
+                    bz[p] = e.z;
+                    i = __float_as_uint(e.w);
+                } else {
+                    bx[p] = by[p] = bz[p] = 1e30f;
+                }
+                asm volatile("st.shared.u32 [%0], %1;" ::"r"(bc + 4u * (uint32_t)(p * 32 + lane)), "r"(i) : "memory");
             }
         }
         // A flush comes before 2P more pushes could run past QX slots.
@@ -633,16 +725,13 @@ struct Ctx {
 
     // Load one b-point into lane registers (shifted into A's frame) and into
     // the warp's b copies used by the flush.
-    __device__ __forceinline__ void load_b(int p, bool ok, uint32_t i, float sy, float sz, uint32_t orig_ax,
-                                           float (&bx)[P], float (&by)[P], float (&bz)[P], float (&hb)[P]) const
+    __device__ __forceinline__ void put_b(int p, bool ok, float x, float y, float z, uint32_t i, float (&bx)[P],
+                                          float (&by)[P], float (&bz)[P], float (&hb)[P]) const
     {
         if (ok) {
-            const float4 v = __ldg(m.pf + i);
-            const int cx = m.pcx[i];
-            const float sx = (float)(int)(sm.orig[cx] - orig_ax);
-            bx[p] = __fadd_rn(v.x, sx);
-            by[p] = __fadd_rn(v.y, sy);
-            bz[p] = __fadd_rn(v.z, sz);
+            bx[p] = x;
+            by[p] = y;
+            bz[p] = z;
             const float b2 = __fmaf_rn(bz[p], bz[p], __fmaf_rn(by[p], by[p], __fmul_rn(bx[p], bx[p])));
             hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, prm.hit_max)), prm.dot_margin);
         } else {
@@ -664,26 +753,21 @@ struct Ctx {
     {
         float bx[P], by[P], bz[P], hb[P];
         if (SELF) {
+            // the self cell: A's own frame, no shift
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const uint32_t i = base + lane + 32u * p;
-                load_b(p, i < s1, i, 0.0f, 0.0f, orig_ax, bx, by, bz, hb);
+                const bool ok = i < s1;
+                const float4 v = ok ? __ldg(m.pf + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+                put_b(p, ok, v.x, v.y, v.z, i, bx, by, bz, hb);
             }
         } else {
-            // locate the run of this lane's first point, then walk forward
-            const uint32_t o0 = o_base + lane;
-            int lo = 0, hi = n_seg - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sm.segs[mid].off0 <= o0) lo = mid; else hi = mid - 1;
-            }
-            int g = lo;
 #pragma unroll
             for (int p = 0; p < P; p++) {
-                const uint32_t o = o0 + 32u * p;
-                while (g + 1 < n_seg && sm.segs[g + 1].off0 <= o) g++;
-                const Seg sg = sm.segs[g];
-                load_b(p, o < total, sg.s0 + (o - sg.off0), sg.sy, sg.sz, orig_ax, bx, by, bz, hb);
+                const uint32_t f = o_base + (uint32_t)lane + 32u * p;
+                const bool ok = f < total;
+                const float4 e = ok ? fetch_f(f) : make_float4(0.f, 0.f, 0.f, 0.f);
+                put_b(p, ok, e.x, e.y, e.z, __float_as_uint(e.w), bx, by, bz, hb);
             }
         }
         __syncwarp();
@@ -827,6 +911,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
                                                                 unsigned *__restrict__ claim,
                                                                 const int16_t *__restrict__ table_g,
                                                                 unsigned long long *__restrict__ stats,
+                                                                float4 *__restrict__ scratch,
                                                                 int persistent, int term_pl, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -853,7 +938,9 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
     for (int i = tid; i < prm.nbin; i += blockDim.x) sm.hist[i] = 0;
 
-    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0.f, 0.f, 0.f, 0u, 0u};
+    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, 0u, 0u, 0u, 0u, 0u, 0u, nullptr, 0u, {}, 0u, 0u, 0u, 0u, 0u,
+                         0.f, 0.f, 0.f, 0u, 0u};
+    cx.scr = scratch + (size_t)blockIdx.x * SCR;
     if (MID) {
         const uint32_t qw = saddr(sm.queue) + (uint32_t)cx.warp * (QN * 32 * 2 * 2);
         cx.q = qw + 2u * (uint32_t)cx.lane;
@@ -876,14 +963,10 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
     }
     unsigned long long n_cand = 0;
 
-    // per-launch mode: this block walks the chunks of one cell of one term
+    // per-launch mode: this block walks the chunks of cells blockIdx.x,
+    // blockIdx.x + gridDim.x, ... of one term
     const uint32_t n_units = persistent ? *n_units_p : 0u;
-    uint32_t pl_a = 0, pl_end = 0;
-    if (!persistent) {
-        const size_t gk = (size_t)terms[term_pl].cat_a * prm.n_cells + blockIdx.x;
-        pl_a = m.cellstart[gk];
-        pl_end = m.cellstart[gk + 1];
-    }
+    uint32_t pl_a = 0, pl_end = 0, pl_next = blockIdx.x, pl_cell = 0;
     __syncthreads();
 
     for (;;) {
@@ -895,9 +978,16 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
             if (u >= n_units) break;
             un = units[u];
         } else {
+            while (pl_a >= pl_end && pl_next < (uint32_t)prm.n_cells) {
+                const size_t gk = (size_t)terms[term_pl].cat_a * prm.n_cells + pl_next;
+                pl_a = m.cellstart[gk];
+                pl_end = m.cellstart[gk + 1];
+                pl_cell = pl_next;
+                pl_next += gridDim.x;
+            }
             if (pl_a >= pl_end) break;
             un.term = term_pl;
-            un.cell = blockIdx.x;
+            un.cell = (int)pl_cell;
             un.a0 = pl_a;
             un.a1 = min(pl_end, pl_a + (uint32_t)chunk);
             pl_a = un.a1;
@@ -905,9 +995,32 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         const Term tm = terms[un.term];
         cx.a0 = un.a0;
         cx.na = un.a1 - un.a0;
-        for (uint32_t i = tid; i < cx.na; i += blockDim.x) sm.a[i] = __ldg(m.pf + un.a0 + i);
+        {
+            // the a-chunk and its bounding box (cell-relative coordinates are
+            // >= 0, so float bit patterns order as unsigned integers)
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool ok = (uint32_t)tid < cx.na;   // na <= UNIT_CHUNK <= blockDim.x
+            if (ok) {
+                v = __ldg(m.pf + un.a0 + tid);
+                sm.a[tid] = v;
+            }
+            if (tid < UNIT_CHUNK) {
+                const unsigned bx = __float_as_uint(v.x), by = __float_as_uint(v.y), bz = __float_as_uint(v.z);
+                const unsigned lx = __reduce_min_sync(0xffffffffu, ok ? bx : 0xFFFFFFFFu);
+                const unsigned ly = __reduce_min_sync(0xffffffffu, ok ? by : 0xFFFFFFFFu);
+                const unsigned lz = __reduce_min_sync(0xffffffffu, ok ? bz : 0xFFFFFFFFu);
+                const unsigned hx = __reduce_max_sync(0xffffffffu, ok ? bx : 0u);
+                const unsigned hy = __reduce_max_sync(0xffffffffu, ok ? by : 0u);
+                const unsigned hz = __reduce_max_sync(0xffffffffu, ok ? bz : 0u);
+                // per-warp partial boxes after the a-chunk, reduced by thread 0 below
+                if (cx.lane == 0) {
+                    sm.a[UNIT_CHUNK + cx.warp] = make_float4(__uint_as_float(lx), __uint_as_float(ly),
+                                                             __uint_as_float(lz), __uint_as_float(hx));
+                    sm.a[UNIT_CHUNK + 4 + cx.warp] = make_float4(__uint_as_float(hy), __uint_as_float(hz), 0.f, 0.f);
+                }
+            }
+        }
         if (cx.warp == 0) build_segments(prm, sm, m, tm, un.cell, cx.lane);
-        if (tid == 0) sm.misc[3] = 0;
         const int n_c = prm.n_c;
         const int ax = un.cell % n_c, ay = (un.cell / n_c) % n_c, az = un.cell / (n_c * n_c);
         const uint32_t oax = sm.orig[ax];
@@ -917,28 +1030,56 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
             cx.gz = 2.0f * (float)((long long)sm.orig[az] - prm.obs[2]);
         }
         __syncthreads();
+        if (tid == 0) {
+            unsigned b[6] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u};
+            for (int w = 0; w < UNIT_CHUNK / 32; w++) {
+                const float4 p0 = sm.a[UNIT_CHUNK + w], p1 = sm.a[UNIT_CHUNK + 4 + w];
+                b[0] = min(b[0], __float_as_uint(p0.x));
+                b[1] = min(b[1], __float_as_uint(p0.y));
+                b[2] = min(b[2], __float_as_uint(p0.z));
+                b[3] = max(b[3], __float_as_uint(p0.w));
+                b[4] = max(b[4], __float_as_uint(p1.x));
+                b[5] = max(b[5], __float_as_uint(p1.y));
+            }
+            for (int k = 0; k < 6; k++) sm.misc[M_BOX + k] = (int)b[k];
+            sm.misc[3] = 0;
+        }
         const int ns = sm.misc[1];
         const uint32_t total = (uint32_t)sm.misc[2];
         const uint32_t self0 = (uint32_t)sm.misc[4], self1 = (uint32_t)sm.misc[5];
         const uint32_t n_self = (self1 - self0 + TILE - 1) / TILE;
-        const uint32_t nt = n_self + (total + TILE - 1) / TILE;
-        // tiles are claimed one at a time from a shared counter (its first
-        // WARPS values are implicit), so warps finish a unit together
-        for (uint32_t ti = cx.warp; ti < nt;) {
-            if (ti < n_self) {
-                const uint32_t base = self0 + ti * TILE;
-                n_cand += (unsigned long long)min(self1 - base, (uint32_t)TILE) * cx.na;
-                if (MID) cx.template tile_mid<true>(base, self1, 0u, ns, total, oax);
-                else cx.template tile_x<true>(base, self1, 0u, ns, total, oax);
-            } else {
-                const uint32_t ob = (ti - n_self) * TILE;
-                n_cand += (unsigned long long)min(total - ob, (uint32_t)TILE) * cx.na;
-                if (MID) cx.template tile_mid<false>(0u, 0u, ob, ns, total, oax);
-                else cx.template tile_x<false>(0u, 0u, ob, ns, total, oax);
+        __syncthreads();
+        // The neighbour runs are filtered window by window into the block's
+        // scratch and tiled densely; the self cell (auto counts) is tiled
+        // directly in the first window.
+        for (uint32_t w0 = 0;; w0 += CAP) {
+            const uint32_t win = min((uint32_t)CAP, total - min(total, w0));
+            cx.filter_window(w0, win, ns, oax);
+            __syncthreads();
+            const uint32_t F = cx.window_regions();
+            const uint32_t ns_w = (w0 == 0) ? n_self : 0u;
+            const uint32_t nt = ns_w + (F + TILE - 1) / TILE;
+            // tiles are claimed one at a time from a shared counter (its first
+            // WARPS values are implicit), so warps finish a window together
+            for (uint32_t ti = cx.warp; ti < nt;) {
+                if (ti < ns_w) {
+                    const uint32_t base = self0 + ti * TILE;
+                    n_cand += (unsigned long long)min(self1 - base, (uint32_t)TILE) * cx.na;
+                    if (MID) cx.template tile_mid<true>(base, self1, 0u, ns, F, oax);
+                    else cx.template tile_x<true>(base, self1, 0u, ns, F, oax);
+                } else {
+                    const uint32_t ob = (ti - ns_w) * TILE;
+                    n_cand += (unsigned long long)min(F - ob, (uint32_t)TILE) * cx.na;
+                    if (MID) cx.template tile_mid<false>(0u, 0u, ob, ns, F, oax);
+                    else cx.template tile_x<false>(0u, 0u, ob, ns, F, oax);
+                }
+                uint32_t nx = 0;
+                if (cx.lane == 0) nx = (uint32_t)atomicAdd(&sm.misc[3], 1) + WARPS;
+                ti = __shfl_sync(0xffffffffu, nx, 0);
             }
-            uint32_t nx = 0;
-            if (cx.lane == 0) nx = (uint32_t)atomicAdd(&sm.misc[3], 1) + WARPS;
-            ti = __shfl_sync(0xffffffffu, nx, 0);
+            __syncthreads();   // every warp is done with this window's scratch and counter
+            if (tid == 0) sm.misc[3] = 0;
+            if (w0 + CAP >= total) break;
         }
         if (!MID && cx.n_list) cx.recheck_list();   // the list refers to this unit's histogram
         __syncthreads();
@@ -993,6 +1134,8 @@ int paircount_smem_bytes(const CountParams &p, int warps_per_block)
     return (int)smem_layout(p, off);
 }
 
+size_t paircount_scratch_bytes(int blocks) { return (size_t)blocks * SCR * sizeof(float4); }
+
 cudaError_t paircount_set_attrs(const CountParams &p, int smem_bytes)
 {
     return cudaFuncSetAttribute(select_kernel(p), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
@@ -1013,8 +1156,9 @@ cudaError_t launch_paircount(const CountParams &p, const Mesh &m, const Term *te
 {
     (void)cats;
     (void)status;
-    void *args[] = {(void *)&p,     (void *)&m,     (void *)&terms,         (void *)&units,   (void *)&n_units,
-                    (void *)&claim, (void *)&table, (void *)&stats,         (void *)&pl.persistent,
+    float4 *scratch = (float4 *)pl.scratch;
+    void *args[] = {(void *)&p,     (void *)&m,     (void *)&terms, (void *)&units,        (void *)&n_units,
+                    (void *)&claim, (void *)&table, (void *)&stats, (void *)&scratch,      (void *)&pl.persistent,
                     (void *)&pl.term, (void *)&pl.chunk};
     return cudaLaunchKernel(select_kernel(p), dim3(pl.blocks), dim3(WARPS * 32), args, (size_t)pl.smem_bytes, s);
 }

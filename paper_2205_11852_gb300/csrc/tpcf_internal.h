@@ -117,12 +117,14 @@ struct PairLaunch {
     int term;              // per-launch mode: the term
     int smem_bytes;
     int chunk;             // a-points per work unit (per-launch mode)
+    void *scratch;         // paircount_scratch_bytes(blocks) of device memory: filtered neighbour windows
 };
 cudaError_t launch_paircount(const CountParams &p, const Mesh &m, const Term *terms, const Cat *cats,
                              const Unit *units, const uint32_t *n_units, unsigned *claim,
                              const int16_t *table, unsigned long long *stats, int *status,
                              const PairLaunch &pl, cudaStream_t s);
 int paircount_smem_bytes(const CountParams &p, int warps_per_block);
+size_t paircount_scratch_bytes(int blocks);
 cudaError_t paircount_set_attrs(const CountParams &p, int smem_bytes);
 int paircount_max_blocks_per_sm(const CountParams &p, int warps_per_block, int smem_bytes);
 
