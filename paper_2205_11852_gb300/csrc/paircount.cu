@@ -63,44 +63,53 @@ struct Seg {
     float sy, sz;          // row shift into A's frame
 };
 
-struct Smem {
-    float4 *a;                 // [UNIT_CHUNK + 8]; .w: -|a|^2/2; then per-warp bounding-box partials
-    int *hist;                 // [nbin] (+ 32 spare words, x path)
-    unsigned char *queue;      // x path: [WARPS][QX + 1][32] (d2, dx) pairs;
-                               // midpoint path: [WARPS][QN][32] + [WARPS][QN * 32] 16-bit entries
-    float4 *bcopy;             // midpoint path: [WARPS][P][32] b' in A's frame, .w = b index (bits)
-    uint32_t *bidx;            // x path: [WARPS][P][32] b index of each tile slot
-    uint2 *xlist;              // x path: [WARPS][XCAP] (a index, b index) awaiting the exact recheck
-    int16_t *table;            // [tab_n]
-    float2 *lohi;              // [n_s + 2]
-    uint32_t *orig;            // [n_c + 1]
-    unsigned long long *T;     // [n_s + 1]
-    Seg *segs;                 // [MAX_SEGS + 1], the last one a sentinel
-    int *misc;                 // [M_N]: unit, n_segs, packed points, next tile, self s0, self s1, counts, box
-};
+// Shared memory.  Fixed-size arrays sit at compile-time offsets (first the
+// ones both paths use, then the path's own), so their addresses fold into
+// the instructions; the arrays sized by the binning follow.
+__host__ __device__ constexpr uint32_t al16(uint32_t x) { return (x + 15u) & ~15u; }
+constexpr uint32_t O_MISC = 0;                                          // int [M_N]
+constexpr uint32_t O_STAT = al16(O_MISC + 4 * M_N);                     // u64 [3][WARPS]: candidates, binned, exact
+constexpr uint32_t O_A = al16(O_STAT + 8 * 3 * WARPS);                  // float4 [UNIT_CHUNK + 8]: a-chunk
+                                                                        // (.w = -|a|^2/2), per-warp box partials
+constexpr uint32_t O_SEG = al16(O_A + 16 * (UNIT_CHUNK + 8));           // Seg [MAX_SEGS + 1]
+constexpr uint32_t O_B = al16(O_SEG + 16 * (MAX_SEGS + 1));             // midpoint: float4 [WARPS][P][32] b copies
+                                                                        // (.w = b index); x: u32 [WARPS][P][32] b index
+__host__ __device__ constexpr uint32_t o_q(bool mid) { return al16(O_B + (mid ? 16u : 4u) * WARPS * P * 32); }
+// queues: x: (d2, dx) [WARPS][QX + 1][32]; midpoint: u16 [WARPS][QN][32] + compacted [WARPS][QN * 32]
+__host__ __device__ constexpr uint32_t o_x(bool mid) { return al16(o_q(mid) + (mid ? 2u * WARPS * QN * 32 * 2 : 8u * WARPS * (QX + 1) * 32)); }
+// x path: recheck lists uint2 [WARPS][XCAP]
+__host__ __device__ constexpr uint32_t o_var(bool mid) { return al16(o_x(mid) + (mid ? 0u : 8u * WARPS * XCAP)); }
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+// offsets of the arrays sized by the binning: T u64 [n_s + 1], hist int
+// [nbin + 32] (32 spare words, x path), lohi float2 [n_s + 2], orig u32
+// [n_c + 1], table i16 [tab_n]
+struct VarOff {
+    uint32_t T, hist, lohi, orig, table, end;
+};
+__host__ __device__ inline VarOff var_offsets(const CountParams &p, bool mid)
+{
+    VarOff v;
+    v.T = o_var(mid);
+    v.hist = al16(v.T + 8u * (uint32_t)(p.n_s + 1));
+    v.lohi = al16(v.hist + 4u * (uint32_t)(p.nbin + 32));
+    v.orig = al16(v.lohi + 8u * (uint32_t)(p.n_s + 2));
+    v.table = al16(v.orig + 4u * (uint32_t)(p.n_c + 1));
+    v.end = al16(v.table + (p.linear ? 0u : 2u * (uint32_t)p.tab_n));
+    return v;
+}
 
 __host__ __device__ inline bool uses_midpoint(const CountParams &p) { return p.n_mu > 1 && p.los == TPCF_LOS_MIDPOINT; }
 
-__host__ __device__ inline size_t smem_layout(const CountParams &p, size_t *off)
+extern __shared__ __align__(16) unsigned char smem_raw[];
+
+__device__ __forceinline__ int *sh_misc() { return (int *)(smem_raw + O_MISC); }
+__device__ __forceinline__ unsigned long long *sh_stat() { return (unsigned long long *)(smem_raw + O_STAT); }
+__device__ __forceinline__ float4 *sh_a() { return (float4 *)(smem_raw + O_A); }
+__device__ __forceinline__ Seg *sh_segs() { return (Seg *)(smem_raw + O_SEG); }
+template <bool MID>
+__device__ __forceinline__ uint32_t *sh_orig(const CountParams &p)
 {
-    const bool mid = uses_midpoint(p);
-    size_t o = 0;
-    off[0] = o; o = align16(o + sizeof(unsigned long long) * (p.n_s + 1));  // T
-    off[1] = o; o = align16(o + sizeof(float4) * (UNIT_CHUNK + 8));        // a chunk + box partials
-    off[2] = o; o = align16(o + (mid ? sizeof(float4) * WARPS * P * 32      // b copies
-                                     : sizeof(uint32_t) * WARPS * P * 32)); // b indices
-    off[3] = o; o = align16(o + (mid ? sizeof(uint16_t) * WARPS * QN * 32 * 2  // queues + compacted
-                                     : sizeof(float2) * WARPS * (QX + 1) * 32));
-    off[4] = o; o = align16(o + sizeof(int) * (p.nbin + (mid ? 0 : 32)));   // histogram (+ spare words)
-    off[5] = o; o = align16(o + sizeof(float2) * (p.n_s + 2));              // edge bands
-    off[6] = o; o = align16(o + sizeof(uint32_t) * (p.n_c + 1));            // cell corners
-    off[7] = o; o = align16(o + sizeof(int16_t) * (p.linear ? 0 : p.tab_n)); // s table
-    off[8] = o; o = align16(o + sizeof(Seg) * (MAX_SEGS + 1));              // segments
-    off[9] = o; o = align16(o + sizeof(int) * M_N);
-    off[10] = o; o = align16(o + (mid ? 0 : sizeof(uint2) * WARPS * XCAP)); // recheck lists
-    return o;
+    return (uint32_t *)(smem_raw + var_offsets(p, MID).orig);
 }
 
 // Exact bin of the pair (ia, ib) from integer grid coordinates; -1 if unbinned.
@@ -274,7 +283,6 @@ struct Cls {
 template <bool MU, bool MID, bool LIN>
 struct Ctx {
     const CountParams &prm;
-    const Smem &sm;
     const Mesh &m;
     int lane, warp;
     uint32_t q;                // this lane's queue column (shared address of slot 0)
@@ -285,7 +293,6 @@ struct Ctx {
     uint32_t hdum;             // this lane's spare word after the histogram (x path)
     float4 *scr;               // this block's scratch: the current window's surviving b-points
     uint32_t R;                // per-warp region length of the current window (entries)
-    uint32_t pk[WARPS];        // region starts in the filtered order (pk[0] = 0)
     uint32_t abase;            // the a-chunk (shared address)
     uint32_t hbase;            // the block histogram (shared address)
     uint32_t hadj;             // hbase minus the bias of the encoded bin keys (see classify)
@@ -322,10 +329,10 @@ struct Ctx {
         } else {
             const uint32_t key = min((__float_as_uint(__fadd_rn(d2, prm.tab_bias)) >> prm.tab_shift) - prm.tab_key0,
                                      (uint32_t)(prm.tab_n - 1));
-            int k = sm.table[key];
+            int k = ((const int16_t *)(smem_raw + var_offsets(prm, MID).table))[key];
             amb = (k == CODE_AMBIG);
             k = amb ? -1 : k;
-            const float2 lh = sm.lohi[k + 1];
+            const float2 lh = ((const float2 *)(smem_raw + var_offsets(prm, MID).lohi))[k + 1];
             const bool ge_hi = d2 >= lh.y;
             amb |= (d2 >= lh.x) && !ge_hi;
             k += ge_hi ? 1 : 0;
@@ -419,7 +426,7 @@ struct Ctx {
         for (uint32_t e = lane; e < n_amb; e += 32) {
             const uint32_t v = lds16(cq + 2u * e);
             const float4 b = lds128(bc + 16u * (v >> 8));
-            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, a0 + (v & 255u), __float_as_uint(b.w));
+            const int bin = exact_bin(prm, (const unsigned long long *)(smem_raw + var_offsets(prm, MID).T), m.us, m.n_total, a0 + (v & 255u), __float_as_uint(b.w));
             n_exact++;
             if (bin >= 0) red_inc(hbase + 4u * (uint32_t)bin);
         }
@@ -439,9 +446,9 @@ struct Ctx {
     {
         R = (((win + WARPS - 1) / WARPS) + 31u) & ~31u;
         const uint32_t r0 = w0 + (uint32_t)warp * R, r1 = min(r0 + R, w0 + win);
-        const float lox = __int_as_float(sm.misc[M_BOX + 0]), loy = __int_as_float(sm.misc[M_BOX + 1]);
-        const float loz = __int_as_float(sm.misc[M_BOX + 2]), hix = __int_as_float(sm.misc[M_BOX + 3]);
-        const float hiy = __int_as_float(sm.misc[M_BOX + 4]), hiz = __int_as_float(sm.misc[M_BOX + 5]);
+        const float lox = __int_as_float(sh_misc()[M_BOX + 0]), loy = __int_as_float(sh_misc()[M_BOX + 1]);
+        const float loz = __int_as_float(sh_misc()[M_BOX + 2]), hix = __int_as_float(sh_misc()[M_BOX + 3]);
+        const float hiy = __int_as_float(sh_misc()[M_BOX + 4]), hiz = __int_as_float(sh_misc()[M_BOX + 5]);
         const float hf = prm.hit_max * (1.0f + 1.0f / 65536.0f);
         float4 *dst = scr + (size_t)warp * R;
         uint32_t cnt = 0;
@@ -450,20 +457,20 @@ struct Ctx {
             int lo = 0, hi = n_seg - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (sm.segs[mid].off0 <= o_first) lo = mid; else hi = mid - 1;
+                if (sh_segs()[mid].off0 <= o_first) lo = mid; else hi = mid - 1;
             }
             int g = lo;
             const uint32_t lt = (1u << lane) - 1u;
             for (uint32_t c = r0; c < r1; c += 32) {
                 const uint32_t o = c + (uint32_t)lane;
-                while (g + 1 < n_seg && sm.segs[g + 1].off0 <= o) g++;
+                while (g + 1 < n_seg && sh_segs()[g + 1].off0 <= o) g++;
                 bool keep = false;
                 float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (o < r1) {
-                    const Seg sg = sm.segs[g];
+                    const Seg sg = sh_segs()[g];
                     const uint32_t i = sg.s0 + (o - sg.off0);
                     const float4 v = __ldg(m.pf + i);
-                    const float sx = (float)(int)(sm.orig[m.pcx[i]] - orig_ax);
+                    const float sx = (float)(int)(sh_orig<MID>(prm)[m.pcx[i]] - orig_ax);
                     e.x = __fadd_rn(v.x, sx);
                     e.y = __fadd_rn(v.y, sg.sy);
                     e.z = __fadd_rn(v.z, sg.sz);
@@ -478,24 +485,24 @@ struct Ctx {
                 cnt += __popc(mk);
             }
         }
-        if (lane == 0) sm.misc[M_CNT + warp] = (int)cnt;
+        if (lane == 0) sh_misc()[M_CNT + warp] = (int)cnt;
     }
 
     // After the window's filter and a barrier: the region starts of the
-    // filtered order; returns the number of survivors.
-    __device__ __forceinline__ uint32_t window_regions()
+    // filtered order (pk[0] = 0); returns the number of survivors.
+    __device__ __forceinline__ uint32_t window_regions(uint32_t (&pk)[WARPS]) const
     {
         uint32_t acc = 0;
 #pragma unroll
         for (int k = 0; k < WARPS; k++) {
             pk[k] = acc;
-            acc += (uint32_t)sm.misc[M_CNT + k];
+            acc += (uint32_t)sh_misc()[M_CNT + k];
         }
         return acc;
     }
 
     // Surviving b-point at filtered position f (< the window's count).
-    __device__ __forceinline__ float4 fetch_f(uint32_t f) const
+    __device__ __forceinline__ float4 fetch_f(uint32_t f, const uint32_t (&pk)[WARPS]) const
     {
         uint32_t w = 0, base = 0;
 #pragma unroll
@@ -516,7 +523,7 @@ struct Ctx {
         for (uint32_t e = lane; e < n_list; e += 32) {
             uint2 pr;
             asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(pr.x), "=r"(pr.y) : "r"(xl + 8u * e) : "memory");
-            const int bin = exact_bin(prm, sm.T, m.us, m.n_total, pr.x, pr.y);
+            const int bin = exact_bin(prm, (const unsigned long long *)(smem_raw + var_offsets(prm, MID).T), m.us, m.n_total, pr.x, pr.y);
             n_exact++;
             if (bin >= 0) red_inc(hbase + 4u * (uint32_t)bin);
         }
@@ -648,7 +655,7 @@ struct Ctx {
         if (ok) {
             const float4 v = __ldg(m.pf + i);
             const int cx = m.pcx[i];
-            const float sx = (float)(int)(sm.orig[cx] - orig_ax);
+            const float sx = (float)(int)(sh_orig<MID>(prm)[cx] - orig_ax);
             bx[p] = __fadd_rn(v.x, sx);
             by[p] = __fadd_rn(v.y, sy);
             bz[p] = __fadd_rn(v.z, sz);
@@ -674,12 +681,14 @@ struct Ctx {
                 load_bx(p, i < s1, i, 0.0f, 0.0f, orig_ax, bx, by, bz);
             }
         } else {
+            uint32_t pk[WARPS];
+            window_regions(pk);
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const uint32_t f = o_base + (uint32_t)lane + 32u * p;
                 uint32_t i = 0;
                 if (f < total) {
-                    const float4 e = fetch_f(f);
+                    const float4 e = fetch_f(f, pk);
                     bx[p] = e.x;
                     by[p] = e.y;
                     bz[p] = e.z;
@@ -762,11 +771,13 @@ struct Ctx {
                 put_b(p, ok, v.x, v.y, v.z, i, bx, by, bz, hb);
             }
         } else {
+            uint32_t pk[WARPS];
+            window_regions(pk);
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const uint32_t f = o_base + (uint32_t)lane + 32u * p;
                 const bool ok = f < total;
-                const float4 e = ok ? fetch_f(f) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 e = ok ? fetch_f(f, pk) : make_float4(0.f, 0.f, 0.f, 0.f);
                 put_b(p, ok, e.x, e.y, e.z, __float_as_uint(e.w), bx, by, bz, hb);
             }
         }
@@ -815,18 +826,19 @@ struct Ctx {
 // The unit's b runs, built by one warp (one lane per neighbour row): the
 // self cell of an auto count apart, every other run concatenated in row order
 // with its offset in the concatenation.
-__device__ void build_segments(const CountParams &prm, const Smem &sm, const Mesh &m, const Term &tm, int cell,
+template <bool MID>
+__device__ void build_segments(const CountParams &prm, const Mesh &m, const Term &tm, int cell,
                                int lane)
 {
     const int n_c = prm.n_c;
     const int ax = cell % n_c, ay = (cell / n_c) % n_c, az = cell / (n_c * n_c);
     const bool periodic = prm.geometry == TPCF_PERIODIC;
     const uint32_t *cs = m.cellstart + (size_t)tm.cat_b * prm.n_cells;
-    const uint32_t oay = sm.orig[ay], oaz = sm.orig[az];
+    const uint32_t oay = sh_orig<MID>(prm)[ay], oaz = sh_orig<MID>(prm)[az];
     uint32_t ns_total = 0, pts_total = 0;
     if (lane == 0) {
-        sm.misc[4] = 0;
-        sm.misc[5] = 0;
+        sh_misc()[4] = 0;
+        sh_misc()[5] = 0;
     }
     __syncwarp();
     for (int r0 = 0; r0 < prm.n_rows; r0 += 32) {
@@ -845,8 +857,8 @@ __device__ void build_segments(const CountParams &prm, const Smem &sm, const Mes
                 use = false;
             }
             if (use) {
-                sy = (float)(int)(sm.orig[y] - oay);
-                sz = (float)(int)(sm.orig[z] - oaz);
+                sy = (float)(int)(sh_orig<MID>(prm)[y] - oay);
+                sz = (float)(int)(sh_orig<MID>(prm)[z] - oaz);
                 const uint32_t rowkey = ((uint32_t)z * n_c + (uint32_t)y) * n_c;
                 int xlo = ax - kx, xhi = ax + kx;
                 auto add = [&](uint32_t a, uint32_t b) {
@@ -857,8 +869,8 @@ __device__ void build_segments(const CountParams &prm, const Smem &sm, const Mes
                     }
                 };
                 if (tm.auto_pairs && dz == 0 && dy == 0) {
-                    sm.misc[4] = (int)cs[rowkey + ax];
-                    sm.misc[5] = (int)cs[rowkey + ax + 1];
+                    sh_misc()[4] = (int)cs[rowkey + ax];
+                    sh_misc()[5] = (int)cs[rowkey + ax + 1];
                     xlo = ax + 1;
                 }
                 if (xlo <= xhi) {
@@ -891,15 +903,15 @@ __device__ void build_segments(const CountParams &prm, const Smem &sm, const Mes
             g.off0 = pts_total + p_ex;
             g.sy = sy;
             g.sz = sz;
-            sm.segs[ns_total + n_ex + i] = g;
+            sh_segs()[ns_total + n_ex + i] = g;
             p_ex += s1[i] - s0[i];
         }
         ns_total += n_all;
         pts_total += p_all;
     }
     if (lane == 0) {
-        sm.misc[1] = (int)ns_total;
-        sm.misc[2] = (int)pts_total;
+        sh_misc()[1] = (int)ns_total;
+        sh_misc()[2] = (int)pts_total;
     }
 }
 
@@ -914,46 +926,41 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
                                                                 float4 *__restrict__ scratch,
                                                                 int persistent, int term_pl, int chunk)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    size_t off[11];
-    smem_layout(prm, off);
-    Smem sm;
-    sm.T = (unsigned long long *)(smem_raw + off[0]);
-    sm.a = (float4 *)(smem_raw + off[1]);
-    sm.bcopy = (float4 *)(smem_raw + off[2]);
-    sm.bidx = (uint32_t *)(smem_raw + off[2]);
-    sm.queue = smem_raw + off[3];
-    sm.xlist = (uint2 *)(smem_raw + off[10]);
-    sm.hist = (int *)(smem_raw + off[4]);
-    sm.lohi = (float2 *)(smem_raw + off[5]);
-    sm.orig = (uint32_t *)(smem_raw + off[6]);
-    sm.table = (int16_t *)(smem_raw + off[7]);
-    sm.segs = (Seg *)(smem_raw + off[8]);
-    sm.misc = (int *)(smem_raw + off[9]);
+    const VarOff vo = var_offsets(prm, MID);
     const int tid = threadIdx.x;
-    for (int i = tid; i <= prm.n_s; i += blockDim.x) sm.T[i] = prm.T[i];
-    for (int i = tid; i <= prm.n_s + 1; i += blockDim.x) sm.lohi[i] = make_float2(prm.lo[i], prm.hi[i]);
-    for (int i = tid; i <= prm.n_c; i += blockDim.x) sm.orig[i] = m.orig[i];
-    if (!LIN)
-        for (int i = tid; i < prm.tab_n; i += blockDim.x) sm.table[i] = table_g[i];
-    for (int i = tid; i < prm.nbin; i += blockDim.x) sm.hist[i] = 0;
+    {
+        unsigned long long *T = (unsigned long long *)(smem_raw + vo.T);
+        float2 *lohi = (float2 *)(smem_raw + vo.lohi);
+        uint32_t *orig = (uint32_t *)(smem_raw + vo.orig);
+        int *hist = (int *)(smem_raw + vo.hist);
+        for (int i = tid; i <= prm.n_s; i += blockDim.x) T[i] = prm.T[i];
+        for (int i = tid; i <= prm.n_s + 1; i += blockDim.x) lohi[i] = make_float2(prm.lo[i], prm.hi[i]);
+        for (int i = tid; i <= prm.n_c; i += blockDim.x) orig[i] = m.orig[i];
+        if (!LIN) {
+            int16_t *table = (int16_t *)(smem_raw + vo.table);
+            for (int i = tid; i < prm.tab_n; i += blockDim.x) table[i] = table_g[i];
+        }
+        for (int i = tid; i < prm.nbin; i += blockDim.x) hist[i] = 0;
+        if (tid < 3 * WARPS) sh_stat()[tid] = 0ull;
+    }
 
-    Ctx<MU, MID, LIN> cx{prm, sm, m, tid & 31, tid >> 5, 0u, 0u, 0u, 0u, 0u, 0u, nullptr, 0u, {}, 0u, 0u, 0u, 0u, 0u,
+    Ctx<MU, MID, LIN> cx{prm, m, tid & 31, tid >> 5, 0u, 0u, 0u, 0u, 0u, 0u, nullptr, 0u, 0u, 0u, 0u, 0u, 0u,
                          0.f, 0.f, 0.f, 0u, 0u};
     cx.scr = scratch + (size_t)blockIdx.x * SCR;
+    const uint32_t sbase = saddr(smem_raw);
     if (MID) {
-        const uint32_t qw = saddr(sm.queue) + (uint32_t)cx.warp * (QN * 32 * 2 * 2);
+        const uint32_t qw = sbase + o_q(true) + (uint32_t)cx.warp * (QN * 32 * 2 * 2);
         cx.q = qw + 2u * (uint32_t)cx.lane;
         cx.cq = qw + QN * 32 * 2;
-        cx.bc = saddr(sm.bcopy) + (uint32_t)cx.warp * (P * 32 * 16);
+        cx.bc = sbase + O_B + (uint32_t)cx.warp * (P * 32 * 16);
     } else {
-        cx.q = saddr(sm.queue) + (uint32_t)cx.warp * ((QX + 1) * 32 * 8) + 8u * (uint32_t)cx.lane;
-        cx.bc = saddr(sm.bidx) + (uint32_t)cx.warp * (P * 32 * 4);
-        cx.xl = saddr(sm.xlist) + (uint32_t)cx.warp * (XCAP * 8);
-        cx.hdum = saddr(sm.hist) + 4u * ((uint32_t)prm.nbin + (uint32_t)cx.lane);
+        cx.q = sbase + o_q(false) + (uint32_t)cx.warp * ((QX + 1) * 32 * 8) + 8u * (uint32_t)cx.lane;
+        cx.bc = sbase + O_B + (uint32_t)cx.warp * (P * 32 * 4);
+        cx.xl = sbase + o_x(false) + (uint32_t)cx.warp * (XCAP * 8);
+        cx.hdum = sbase + vo.hist + 4u * ((uint32_t)prm.nbin + (uint32_t)cx.lane);
     }
-    cx.abase = saddr(sm.a);
-    cx.hbase = saddr(sm.hist);
+    cx.abase = sbase + O_A;
+    cx.hbase = sbase + vo.hist;
     {
         // classify encodes the s bin with the bias of B's bit pattern on the
         // linear path, the mu bin always (see classify)
@@ -961,7 +968,6 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         const uint32_t sb = LIN ? kB : 0u;
         cx.hadj = cx.hbase - 4u * (MU ? sb * (uint32_t)prm.n_mu + kB : sb);
     }
-    unsigned long long n_cand = 0;
 
     // per-launch mode: this block walks the chunks of cells blockIdx.x,
     // blockIdx.x + gridDim.x, ... of one term
@@ -972,9 +978,9 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
     for (;;) {
         Unit un;
         if (persistent) {
-            if (tid == 0) sm.misc[0] = (int)atomicAdd(claim, 1u);
+            if (tid == 0) sh_misc()[0] = (int)atomicAdd(claim, 1u);
             __syncthreads();
-            const uint32_t u = (uint32_t)sm.misc[0];
+            const uint32_t u = (uint32_t)sh_misc()[0];
             if (u >= n_units) break;
             un = units[u];
         } else {
@@ -992,7 +998,6 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
             un.a1 = min(pl_end, pl_a + (uint32_t)chunk);
             pl_a = un.a1;
         }
-        const Term tm = terms[un.term];
         cx.a0 = un.a0;
         cx.na = un.a1 - un.a0;
         {
@@ -1002,7 +1007,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
             const bool ok = (uint32_t)tid < cx.na;   // na <= UNIT_CHUNK <= blockDim.x
             if (ok) {
                 v = __ldg(m.pf + un.a0 + tid);
-                sm.a[tid] = v;
+                sh_a()[tid] = v;
             }
             if (tid < UNIT_CHUNK) {
                 const unsigned bx = __float_as_uint(v.x), by = __float_as_uint(v.y), bz = __float_as_uint(v.z);
@@ -1014,26 +1019,26 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
                 const unsigned hz = __reduce_max_sync(0xffffffffu, ok ? bz : 0u);
                 // per-warp partial boxes after the a-chunk, reduced by thread 0 below
                 if (cx.lane == 0) {
-                    sm.a[UNIT_CHUNK + cx.warp] = make_float4(__uint_as_float(lx), __uint_as_float(ly),
+                    sh_a()[UNIT_CHUNK + cx.warp] = make_float4(__uint_as_float(lx), __uint_as_float(ly),
                                                              __uint_as_float(lz), __uint_as_float(hx));
-                    sm.a[UNIT_CHUNK + 4 + cx.warp] = make_float4(__uint_as_float(hy), __uint_as_float(hz), 0.f, 0.f);
+                    sh_a()[UNIT_CHUNK + 4 + cx.warp] = make_float4(__uint_as_float(hy), __uint_as_float(hz), 0.f, 0.f);
                 }
             }
         }
-        if (cx.warp == 0) build_segments(prm, sm, m, tm, un.cell, cx.lane);
+        if (cx.warp == 0) build_segments<MID>(prm, m, terms[un.term], un.cell, cx.lane);
         const int n_c = prm.n_c;
         const int ax = un.cell % n_c, ay = (un.cell / n_c) % n_c, az = un.cell / (n_c * n_c);
-        const uint32_t oax = sm.orig[ax];
+        const uint32_t oax = sh_orig<MID>(prm)[ax];
         if (MID) {
             cx.gx = 2.0f * (float)((long long)oax - prm.obs[0]);
-            cx.gy = 2.0f * (float)((long long)sm.orig[ay] - prm.obs[1]);
-            cx.gz = 2.0f * (float)((long long)sm.orig[az] - prm.obs[2]);
+            cx.gy = 2.0f * (float)((long long)sh_orig<MID>(prm)[ay] - prm.obs[1]);
+            cx.gz = 2.0f * (float)((long long)sh_orig<MID>(prm)[az] - prm.obs[2]);
         }
         __syncthreads();
         if (tid == 0) {
             unsigned b[6] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u};
             for (int w = 0; w < UNIT_CHUNK / 32; w++) {
-                const float4 p0 = sm.a[UNIT_CHUNK + w], p1 = sm.a[UNIT_CHUNK + 4 + w];
+                const float4 p0 = sh_a()[UNIT_CHUNK + w], p1 = sh_a()[UNIT_CHUNK + 4 + w];
                 b[0] = min(b[0], __float_as_uint(p0.x));
                 b[1] = min(b[1], __float_as_uint(p0.y));
                 b[2] = min(b[2], __float_as_uint(p0.z));
@@ -1041,12 +1046,12 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
                 b[4] = max(b[4], __float_as_uint(p1.x));
                 b[5] = max(b[5], __float_as_uint(p1.y));
             }
-            for (int k = 0; k < 6; k++) sm.misc[M_BOX + k] = (int)b[k];
-            sm.misc[3] = 0;
+            for (int k = 0; k < 6; k++) sh_misc()[M_BOX + k] = (int)b[k];
+            sh_misc()[3] = 0;
         }
-        const int ns = sm.misc[1];
-        const uint32_t total = (uint32_t)sm.misc[2];
-        const uint32_t self0 = (uint32_t)sm.misc[4], self1 = (uint32_t)sm.misc[5];
+        const int ns = sh_misc()[1];
+        const uint32_t total = (uint32_t)sh_misc()[2];
+        const uint32_t self0 = (uint32_t)sh_misc()[4], self1 = (uint32_t)sh_misc()[5];
         const uint32_t n_self = (self1 - self0 + TILE - 1) / TILE;
         __syncthreads();
         // The neighbour runs are filtered window by window into the block's
@@ -1056,7 +1061,9 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
             const uint32_t win = min((uint32_t)CAP, total - min(total, w0));
             cx.filter_window(w0, win, ns, oax);
             __syncthreads();
-            const uint32_t F = cx.window_regions();
+            uint32_t F = 0;
+#pragma unroll
+            for (int k = 0; k < WARPS; k++) F += (uint32_t)sh_misc()[M_CNT + k];
             const uint32_t ns_w = (w0 == 0) ? n_self : 0u;
             const uint32_t nt = ns_w + (F + TILE - 1) / TILE;
             // tiles are claimed one at a time from a shared counter (its first
@@ -1064,38 +1071,39 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
             for (uint32_t ti = cx.warp; ti < nt;) {
                 if (ti < ns_w) {
                     const uint32_t base = self0 + ti * TILE;
-                    n_cand += (unsigned long long)min(self1 - base, (uint32_t)TILE) * cx.na;
+                    if (cx.lane == 0) sh_stat()[cx.warp] += (unsigned long long)min(self1 - base, (uint32_t)TILE) * cx.na;
                     if (MID) cx.template tile_mid<true>(base, self1, 0u, ns, F, oax);
                     else cx.template tile_x<true>(base, self1, 0u, ns, F, oax);
                 } else {
                     const uint32_t ob = (ti - ns_w) * TILE;
-                    n_cand += (unsigned long long)min(F - ob, (uint32_t)TILE) * cx.na;
+                    if (cx.lane == 0) sh_stat()[cx.warp] += (unsigned long long)min(F - ob, (uint32_t)TILE) * cx.na;
                     if (MID) cx.template tile_mid<false>(0u, 0u, ob, ns, F, oax);
                     else cx.template tile_x<false>(0u, 0u, ob, ns, F, oax);
                 }
                 uint32_t nx = 0;
-                if (cx.lane == 0) nx = (uint32_t)atomicAdd(&sm.misc[3], 1) + WARPS;
+                if (cx.lane == 0) nx = (uint32_t)atomicAdd(&sh_misc()[3], 1) + WARPS;
                 ti = __shfl_sync(0xffffffffu, nx, 0);
             }
             __syncthreads();   // every warp is done with this window's scratch and counter
-            if (tid == 0) sm.misc[3] = 0;
+            if (tid == 0) sh_misc()[3] = 0;
             if (w0 + CAP >= total) break;
         }
         if (!MID && cx.n_list) cx.recheck_list();   // the list refers to this unit's histogram
         __syncthreads();
         // drain the block histogram into the term's int64 histogram
+        long long *const th = terms[un.term].hist;
         for (int b = tid; b < prm.nbin; b += blockDim.x) {
-            const int v = sm.hist[b];
+            const int v = ((int *)(smem_raw + vo.hist))[b];
             cx.n_binned += (unsigned)v;   // every binned pair passes through the block histogram
             if (v) {
-                atomicAdd((unsigned long long *)&tm.hist[b], (unsigned long long)(long long)v);
-                sm.hist[b] = 0;
+                atomicAdd((unsigned long long *)&th[b], (unsigned long long)(long long)v);
+                ((int *)(smem_raw + vo.hist))[b] = 0;
             }
         }
         __syncthreads();
     }
-    // work statistics (per-lane candidate counts are warp-uniform: count lane 0 only)
-    unsigned long long ex = cx.n_exact, bn = cx.n_binned, cd = (cx.lane == 0) ? n_cand : 0ull;
+    // work statistics (candidate counts are kept per warp in shared memory)
+    unsigned long long ex = cx.n_exact, bn = cx.n_binned, cd = (cx.lane == 0) ? sh_stat()[cx.warp] : 0ull;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ex += __shfl_down_sync(0xffffffffu, ex, o);
@@ -1130,8 +1138,7 @@ void *select_kernel(const CountParams &p)
 int paircount_smem_bytes(const CountParams &p, int warps_per_block)
 {
     (void)warps_per_block;
-    size_t off[11];
-    return (int)smem_layout(p, off);
+    return (int)var_offsets(p, uses_midpoint(p)).end;
 }
 
 size_t paircount_scratch_bytes(int blocks) { return (size_t)blocks * SCR * sizeof(float4); }
