@@ -38,11 +38,12 @@ namespace {
 constexpr int P = 4;            // b-points per lane
 constexpr int TILE = 32 * P;    // b-points per warp tile
 constexpr int QN = 24;          // queue slots per lane, midpoint path (16-bit entries)
-constexpr int QX = 18;          // queue slots per lane, x line of sight (8-byte entries)
-constexpr int XCAP = 96;        // per-warp list of pairs awaiting the exact recheck
+constexpr int QX = 23;          // queue slots per lane, x line of sight (8-byte entries)
+constexpr int XCAP = 64;        // per-warp list of pairs awaiting the exact recheck (x path, global scratch)
 constexpr int WARPS = 8;        // warps per block
 constexpr int CAP = 12288;      // raw neighbour points filtered per window
-constexpr int SCR = CAP + 8 * 32;   // float4 scratch entries per block (window + per-warp rounding)
+constexpr int SCR_W = CAP + 8 * 32;                 // float4 scratch entries per block window (+ per-warp rounding)
+constexpr int SCR = SCR_W + WARPS * XCAP * 8 / 16;   // + the warps' recheck lists
 // misc[] layout
 constexpr int M_CNT = 8;        // [WARPS] survivors per warp in the current window
 constexpr int M_BOX = 16;       // [6] a-chunk bounding box (float bits): lo xyz, hi xyz
@@ -73,12 +74,11 @@ constexpr uint32_t O_A = al16(O_STAT + 8 * 3 * WARPS);                  // float
                                                                         // (.w = -|a|^2/2), per-warp box partials
 constexpr uint32_t O_SEG = al16(O_A + 16 * (UNIT_CHUNK + 8));           // Seg [MAX_SEGS + 1]
 constexpr uint32_t O_B = al16(O_SEG + 16 * (MAX_SEGS + 1));             // midpoint: float4 [WARPS][P][32] b copies
-                                                                        // (.w = b index); x: u32 [WARPS][P][32] b index
-__host__ __device__ constexpr uint32_t o_q(bool mid) { return al16(O_B + (mid ? 16u : 4u) * WARPS * P * 32); }
+                                                                        // (.w = b index)
+__host__ __device__ constexpr uint32_t o_q(bool mid) { return al16(O_B + (mid ? 16u * WARPS * P * 32 : 0u)); }
 // queues: x: (d2, dx) [WARPS][QX + 1][32]; midpoint: u16 [WARPS][QN][32] + compacted [WARPS][QN * 32]
 __host__ __device__ constexpr uint32_t o_x(bool mid) { return al16(o_q(mid) + (mid ? 2u * WARPS * QN * 32 * 2 : 8u * WARPS * (QX + 1) * 32)); }
-// x path: recheck lists uint2 [WARPS][XCAP]
-__host__ __device__ constexpr uint32_t o_var(bool mid) { return al16(o_x(mid) + (mid ? 0u : 8u * WARPS * XCAP)); }
+__host__ __device__ constexpr uint32_t o_var(bool mid) { return o_x(mid); }
 
 // offsets of the arrays sized by the binning: T u64 [n_s + 1], hist int
 // [nbin + 32] (32 spare words, x path), lohi float2 [n_s + 2], orig u32
@@ -287,8 +287,7 @@ struct Ctx {
     int lane, warp;
     uint32_t q;                // this lane's queue column (shared address of slot 0)
     uint32_t cq;               // this warp's compacted queue (shared address)
-    uint32_t bc;               // this warp's b copies (midpoint path; .w: b index) or b indices (x path)
-    uint32_t xl;               // this warp's recheck list (x path, shared address)
+    uint32_t bc;               // this warp's b copies (midpoint path; .w: b index)
     uint32_t n_list;           // entries in it (warp-uniform)
     uint32_t hdum;             // this lane's spare word after the histogram (x path)
     float4 *scr;               // this block's scratch: the current window's surviving b-points
@@ -516,13 +515,17 @@ struct Ctx {
 
     // ---- x line of sight ----
 
+    // This warp's list of pairs set aside for the exact recheck (global
+    // scratch after the block's window; written and read by this warp only).
+    __device__ __forceinline__ uint2 *xlist() const { return (uint2 *)(scr + SCR_W) + (size_t)warp * XCAP; }
+
     // Exact recheck of the set-aside pairs, one per lane.
     __device__ __forceinline__ void recheck_list()
     {
         __syncwarp();
         for (uint32_t e = lane; e < n_list; e += 32) {
             uint2 pr;
-            asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(pr.x), "=r"(pr.y) : "r"(xl + 8u * e) : "memory");
+            pr = xlist()[e];
             const int bin = exact_bin(prm, (const unsigned long long *)(smem_raw + var_offsets(prm, MID).T), m.us, m.n_total, pr.x, pr.y);
             n_exact++;
             if (bin >= 0) red_inc(hbase + 4u * (uint32_t)bin);
@@ -584,7 +587,9 @@ struct Ctx {
         }
     }
 
-    // Append this lane's entry k (when x) to the recheck list at its ballot rank.
+    // Append this lane's entry k (when x) to the recheck list at its ballot
+    // rank.  The b index of slot p: the self cell's sorted index ib0 + 32 p,
+    // or the point at filtered position ib0 + 32 p of the window.
     template <bool SELF>
     __device__ __forceinline__ void set_aside(bool x, uint32_t k, unsigned am, uint32_t lt, uint32_t a_lo, uint32_t ib0,
                                               const float (&bx)[P], const float (&by)[P], const float (&bz)[P])
@@ -592,9 +597,14 @@ struct Ctx {
         if (x) {
             uint32_t ai, p, ib;
             find_pair<SELF>(k, a_lo, ib0, bx, by, bz, ai, p);
-            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(ib) : "r"(bc + 4u * (p * 32u + (uint32_t)lane)) : "memory");
-            const uint32_t at = xl + 8u * (n_list + __popc(am & lt));
-            asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(at), "r"(a0 + ai), "r"(ib) : "memory");
+            if (SELF) {
+                ib = ib0 + 32u * p;
+            } else {
+                uint32_t pk[WARPS];
+                window_regions(pk);
+                ib = __float_as_uint(fetch_f(ib0 + 32u * p, pk).w);
+            }
+            xlist()[n_list + __popc(am & lt)] = make_uint2(a0 + ai, ib);
         }
         n_list += __popc(am);
     }
@@ -616,21 +626,28 @@ struct Ctx {
                                             const float (&by)[P], const float (&bz)[P])
     {
         const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
-        const uint32_t lt = (1u << lane) - 1u;
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t amask = 0;   // bit k: entry k lies in an error band (QX < 32 slots)
         for (uint32_t k = 0; k < nmax; k += 2) {
             const bool live0 = k < n, live1 = k + 1 < n;
             const float2 e0 = lds64(q + k * 256u), e1 = lds64(q + (k + 1u) * 256u);
             const Cls c0 = classify(e0.x, e0.y, z, z), c1 = classify(e1.x, e1.y, z, z);
             red_x(c0.addr, live0 && c0.good);
             red_x(c1.addr, live1 && c1.good);
-            const bool x0 = live0 && c0.amb, x1 = live1 && c1.amb;
-            const unsigned am0 = __ballot_sync(0xffffffffu, x0);
-            const unsigned am1 = __ballot_sync(0xffffffffu, x1);
-            if (am0 | am1) {
-                // rare: at most 31 + 64 entries after this, within XCAP
-                set_aside<SELF>(x0, k, am0, lt, a_lo, ib0, bx, by, bz);
-                set_aside<SELF>(x1, k + 1, am1, lt, a_lo, ib0, bx, by, bz);
+            amask |= ((live0 && c0.amb) ? 1u : 0u) << k;
+            amask |= ((live1 && c1.amb) ? 2u : 0u) << k;
+        }
+        if (__any_sync(0xffffffffu, amask != 0)) {
+            // rare: set the ambiguous entries aside, one per lane per round
+            // (at most 31 + 32 in the list after a round, within XCAP)
+            const uint32_t lt = (1u << lane) - 1u;
+            for (;;) {
+                const bool x = amask != 0;
+                const unsigned am = __ballot_sync(0xffffffffu, x);
+                if (!am) break;
+                const uint32_t k = x ? (uint32_t)(__ffs(amask) - 1) : 0u;
+                set_aside<SELF>(x, k, am, lt, a_lo, ib0, bx, by, bz);
+                amask &= amask - 1u;
                 if (n_list >= 32) recheck_list();
             }
         }
@@ -661,9 +678,7 @@ struct Ctx {
             bz[p] = __fadd_rn(v.z, sz);
         } else {
             bx[p] = by[p] = bz[p] = 1e30f;
-            i = 0;
         }
-        asm volatile("st.shared.u32 [%0], %1;" ::"r"(bc + 4u * (uint32_t)(p * 32 + lane)), "r"(i) : "memory");
     }
 
     // all pairs of the a-chunk with one tile of b-points: the self cell of an
@@ -686,23 +701,22 @@ struct Ctx {
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const uint32_t f = o_base + (uint32_t)lane + 32u * p;
-                uint32_t i = 0;
                 if (f < total) {
                     const float4 e = fetch_f(f, pk);
                     bx[p] = e.x;
                     by[p] = e.y;
                     bz[p] = e.z;
-                    i = __float_as_uint(e.w);
                 } else {
                     bx[p] = by[p] = bz[p] = 1e30f;
                 }
-                asm volatile("st.shared.u32 [%0], %1;" ::"r"(bc + 4u * (uint32_t)(p * 32 + lane)), "r"(i) : "memory");
             }
         }
         // A flush comes before 2P more pushes could run past QX slots.
         uint32_t head = q, a_lo = 0;
         const uint32_t lim = q + (uint32_t)(QX - 2 * P) * 256u;
-        const uint32_t ib0 = base + lane;   // used by SELF tiles only
+        // SELF: the sorted index of slot 0 (the a < b test and the rechecks);
+        // else the filtered position of slot 0 (the rechecks)
+        const uint32_t ib0 = (SELF ? base : o_base) + lane;
         uint32_t ai = 0;
         for (; ai + 1 < na; ai += 2) {
             const float4 a = lds128(abase + 16u * ai), c = lds128(abase + 16u * (ai + 1));
@@ -944,7 +958,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         if (tid < 3 * WARPS) sh_stat()[tid] = 0ull;
     }
 
-    Ctx<MU, MID, LIN> cx{prm, m, tid & 31, tid >> 5, 0u, 0u, 0u, 0u, 0u, 0u, nullptr, 0u, 0u, 0u, 0u, 0u, 0u,
+    Ctx<MU, MID, LIN> cx{prm, m, tid & 31, tid >> 5, 0u, 0u, 0u, 0u, 0u, nullptr, 0u, 0u, 0u, 0u, 0u, 0u,
                          0.f, 0.f, 0.f, 0u, 0u};
     cx.scr = scratch + (size_t)blockIdx.x * SCR;
     const uint32_t sbase = saddr(smem_raw);
@@ -955,8 +969,6 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         cx.bc = sbase + O_B + (uint32_t)cx.warp * (P * 32 * 16);
     } else {
         cx.q = sbase + o_q(false) + (uint32_t)cx.warp * ((QX + 1) * 32 * 8) + 8u * (uint32_t)cx.lane;
-        cx.bc = sbase + O_B + (uint32_t)cx.warp * (P * 32 * 4);
-        cx.xl = sbase + o_x(false) + (uint32_t)cx.warp * (XCAP * 8);
         cx.hdum = sbase + vo.hist + 4u * ((uint32_t)prm.nbin + (uint32_t)cx.lane);
     }
     cx.abase = sbase + O_A;
