@@ -44,9 +44,8 @@ constexpr int WARPS = 8;        // warps per block
 constexpr int CAP = 12288;      // raw neighbour points filtered per window
 constexpr int SCR_W = CAP + 8 * 32;                 // float4 scratch entries per block window (+ per-warp rounding)
 constexpr int SCR = SCR_W + WARPS * XCAP * 8 / 16;   // + the warps' recheck lists
-// misc[] layout
+// misc[]: [0] unit, [1] runs, [2] run points, [3] tile counter, [4..5] self range, [M_CNT..] window counts
 constexpr int M_CNT = 8;        // [WARPS] survivors per warp in the current window
-constexpr int M_BOX = 16;       // [6] a-chunk bounding box (float bits): lo xyz, hi xyz
 constexpr int M_N = 24;
 constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 static_assert(P == 4, "tile_x unrolls four b-points per lane");
@@ -272,6 +271,11 @@ __device__ __forceinline__ float2 lds64(uint32_t a)
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
     return v;
 }
+// Bounding box of an a-chunk (cell-relative coordinates).
+struct Box {
+    float lx, ly, lz, hx, hy, hz;
+};
+
 // Classification of a queued pair: its histogram slot as a shared address
 // (meaningful when good), good = binned and outside every error band, amb =
 // inside an error band (recheck exactly).  Neither: beyond the last edge.
@@ -434,6 +438,26 @@ struct Ctx {
 
     // ---- neighbour filtering ----
 
+    // The a-chunk's bounding box from the per-warp partials stored after it
+    // (cell-relative coordinates are >= 0, so float bit patterns order as
+    // unsigned integers).
+    __device__ __forceinline__ Box chunk_box() const
+    {
+        unsigned b[6] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u};
+#pragma unroll
+        for (int w = 0; w < UNIT_CHUNK / 32; w++) {
+            const float4 p0 = sh_a()[UNIT_CHUNK + w], p1 = sh_a()[UNIT_CHUNK + 4 + w];
+            b[0] = min(b[0], __float_as_uint(p0.x));
+            b[1] = min(b[1], __float_as_uint(p0.y));
+            b[2] = min(b[2], __float_as_uint(p0.z));
+            b[3] = max(b[3], __float_as_uint(p0.w));
+            b[4] = max(b[4], __float_as_uint(p1.x));
+            b[5] = max(b[5], __float_as_uint(p1.y));
+        }
+        return {__uint_as_float(b[0]), __uint_as_float(b[1]), __uint_as_float(b[2]),
+                __uint_as_float(b[3]), __uint_as_float(b[4]), __uint_as_float(b[5])};
+    }
+
     // Filter raw neighbour points [w0, w0 + win) of the unit's concatenated
     // runs: a point enters the window's list only if its distance to the
     // a-chunk's bounding box is below the last edge's band (with a relative
@@ -443,11 +467,10 @@ struct Ctx {
     // the block's scratch, in order; the survivor count goes to misc.
     __device__ __forceinline__ void filter_window(uint32_t w0, uint32_t win, int n_seg, uint32_t orig_ax)
     {
+        const Box bb = chunk_box();
         R = (((win + WARPS - 1) / WARPS) + 31u) & ~31u;
         const uint32_t r0 = w0 + (uint32_t)warp * R, r1 = min(r0 + R, w0 + win);
-        const float lox = __int_as_float(sh_misc()[M_BOX + 0]), loy = __int_as_float(sh_misc()[M_BOX + 1]);
-        const float loz = __int_as_float(sh_misc()[M_BOX + 2]), hix = __int_as_float(sh_misc()[M_BOX + 3]);
-        const float hiy = __int_as_float(sh_misc()[M_BOX + 4]), hiz = __int_as_float(sh_misc()[M_BOX + 5]);
+        const float lox = bb.lx, loy = bb.ly, loz = bb.lz, hix = bb.hx, hiy = bb.hy, hiz = bb.hz;
         const float hf = prm.hit_max * (1.0f + 1.0f / 65536.0f);
         float4 *dst = scr + (size_t)warp * R;
         uint32_t cnt = 0;
@@ -663,9 +686,8 @@ struct Ctx {
         push_if_lt(head, d2, __float_as_uint(dx), h);
     }
 
-    // Load one b-point (shifted into A's frame) into lane registers and its
-    // index into the warp's slot table; a missing point sits at 1e30, where
-    // d2 overflows to +inf and never passes.
+    // Load one b-point (shifted into A's frame) into lane registers; a
+    // missing point sits at 1e30, where d2 overflows to +inf and never passes.
     __device__ __forceinline__ void load_bx(int p, bool ok, uint32_t i, float sy, float sz, uint32_t orig_ax,
                                             float (&bx)[P], float (&by)[P], float (&bz)[P]) const
     {
@@ -985,13 +1007,17 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
     // blockIdx.x + gridDim.x, ... of one term
     const uint32_t n_units = persistent ? *n_units_p : 0u;
     uint32_t pl_a = 0, pl_end = 0, pl_next = blockIdx.x, pl_cell = 0;
+    // the first unit is claimed here, every later one during the previous
+    // unit's drain (the barrier that ends a unit publishes it)
+    if (tid == 0) {
+        sh_misc()[0] = persistent ? (int)atomicAdd(claim, 1u) : 0;
+        sh_misc()[3] = 0;
+    }
     __syncthreads();
 
     for (;;) {
         Unit un;
         if (persistent) {
-            if (tid == 0) sh_misc()[0] = (int)atomicAdd(claim, 1u);
-            __syncthreads();
             const uint32_t u = (uint32_t)sh_misc()[0];
             if (u >= n_units) break;
             un = units[u];
@@ -1029,7 +1055,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
                 const unsigned hx = __reduce_max_sync(0xffffffffu, ok ? bx : 0u);
                 const unsigned hy = __reduce_max_sync(0xffffffffu, ok ? by : 0u);
                 const unsigned hz = __reduce_max_sync(0xffffffffu, ok ? bz : 0u);
-                // per-warp partial boxes after the a-chunk, reduced by thread 0 below
+                // per-warp partial boxes after the a-chunk (chunk_box)
                 if (cx.lane == 0) {
                     sh_a()[UNIT_CHUNK + cx.warp] = make_float4(__uint_as_float(lx), __uint_as_float(ly),
                                                              __uint_as_float(lz), __uint_as_float(hx));
@@ -1047,25 +1073,10 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
             cx.gz = 2.0f * (float)((long long)sh_orig<MID>(prm)[az] - prm.obs[2]);
         }
         __syncthreads();
-        if (tid == 0) {
-            unsigned b[6] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u};
-            for (int w = 0; w < UNIT_CHUNK / 32; w++) {
-                const float4 p0 = sh_a()[UNIT_CHUNK + w], p1 = sh_a()[UNIT_CHUNK + 4 + w];
-                b[0] = min(b[0], __float_as_uint(p0.x));
-                b[1] = min(b[1], __float_as_uint(p0.y));
-                b[2] = min(b[2], __float_as_uint(p0.z));
-                b[3] = max(b[3], __float_as_uint(p0.w));
-                b[4] = max(b[4], __float_as_uint(p1.x));
-                b[5] = max(b[5], __float_as_uint(p1.y));
-            }
-            for (int k = 0; k < 6; k++) sh_misc()[M_BOX + k] = (int)b[k];
-            sh_misc()[3] = 0;
-        }
         const int ns = sh_misc()[1];
         const uint32_t total = (uint32_t)sh_misc()[2];
         const uint32_t self0 = (uint32_t)sh_misc()[4], self1 = (uint32_t)sh_misc()[5];
         const uint32_t n_self = (self1 - self0 + TILE - 1) / TILE;
-        __syncthreads();
         // The neighbour runs are filtered window by window into the block's
         // scratch and tiled densely; the self cell (auto counts) is tiled
         // directly in the first window.
@@ -1096,13 +1107,14 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
                 if (cx.lane == 0) nx = (uint32_t)atomicAdd(&sh_misc()[3], 1) + WARPS;
                 ti = __shfl_sync(0xffffffffu, nx, 0);
             }
-            __syncthreads();   // every warp is done with this window's scratch and counter
+            const bool last = w0 + CAP >= total;
+            if (!MID && last && cx.n_list) cx.recheck_list();   // the list refers to this unit's histogram
+            __syncthreads();   // every warp is done with this window's scratch, counter and histogram adds
             if (tid == 0) sh_misc()[3] = 0;
-            if (w0 + CAP >= total) break;
+            if (last) break;
         }
-        if (!MID && cx.n_list) cx.recheck_list();   // the list refers to this unit's histogram
-        __syncthreads();
         // drain the block histogram into the term's int64 histogram
+        if (persistent && tid == 0) sh_misc()[0] = (int)atomicAdd(claim, 1u);   // the next unit
         long long *const th = terms[un.term].hist;
         for (int b = tid; b < prm.nbin; b += blockDim.x) {
             const int v = ((int *)(smem_raw + vo.hist))[b];
