@@ -80,7 +80,8 @@ __host__ __device__ constexpr uint32_t o_x(bool mid) { return al16(o_q(mid) + (m
 __host__ __device__ constexpr uint32_t o_var(bool mid) { return o_x(mid); }
 
 // offsets of the arrays sized by the binning: T u64 [n_s + 1], hist int
-// [nbin + 32] (32 spare words, x path), lohi float2 [n_s + 2], orig u32
+// [nbin + max(32, n_mu)] (spare words: per-lane dummies of the x path's adds,
+// and the bins past the last edge of the linear path), lohi float2 [n_s + 2], orig u32
 // [n_c + 1], table i16 [tab_n]
 struct VarOff {
     uint32_t T, hist, lohi, orig, table, end;
@@ -90,7 +91,7 @@ __host__ __device__ inline VarOff var_offsets(const CountParams &p, bool mid)
     VarOff v;
     v.T = o_var(mid);
     v.hist = al16(v.T + 8u * (uint32_t)(p.n_s + 1));
-    v.lohi = al16(v.hist + 4u * (uint32_t)(p.nbin + 32));
+    v.lohi = al16(v.hist + 4u * (uint32_t)(p.nbin + (p.n_mu > 32 ? p.n_mu : 32)));
     v.orig = al16(v.lohi + 8u * (uint32_t)(p.n_s + 2));
     v.table = al16(v.orig + 4u * (uint32_t)(p.n_c + 1));
     v.end = al16(v.table + (p.linear ? 0u : 2u * (uint32_t)p.tab_n));
@@ -371,7 +372,10 @@ struct Ctx {
             o.addr = hadj + 4u * ks;
         }
         o.amb = amb;
-        o.good = valid && !amb;
+        // linear bins: an unambiguous pair past the last edge has s bin n_s
+        // exactly (d2 is below the last edge's band), so its address falls
+        // in the spare words after the histogram and needs no test
+        o.good = LIN ? !amb : (valid && !amb);
         return o;
     }
 
@@ -632,12 +636,12 @@ struct Ctx {
         n_list += __popc(am);
     }
 
-    // Histogram increment when ok, as an unpredicated add of ok: a lane with
-    // nothing to count adds 0 to its own spare word after the histogram.
+    // Histogram increment when ok, as an unpredicated add: a lane with
+    // nothing to count adds to its own spare word after the histogram.
     __device__ __forceinline__ void red_x(uint32_t addr, bool ok) const
     {
         const uint32_t at = ok ? addr : hdum;
-        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(at), "r"((uint32_t)ok) : "memory");
+        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(at) : "memory");
     }
 
     // Bin this lane's column (n entries; the window's pushes began at a-chunk
@@ -657,8 +661,9 @@ struct Ctx {
             const Cls c0 = classify(e0.x, e0.y, z, z), c1 = classify(e1.x, e1.y, z, z);
             red_x(c0.addr, live0 && c0.good);
             red_x(c1.addr, live1 && c1.good);
-            amask |= ((live0 && c0.amb) ? 1u : 0u) << k;
-            amask |= ((live1 && c1.amb) ? 2u : 0u) << k;
+            const uint32_t bit = 1u << k;
+            if (live0 && c0.amb) amask |= bit;
+            if (live1 && c1.amb) amask |= bit << 1;
         }
         if (__any_sync(0xffffffffu, amask != 0)) {
             // rare: set the ambiguous entries aside, one per lane per round
