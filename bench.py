@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--subdiv", type=int, default=0, help="pin the mesh subdivision (0: library choice)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--batching-mocks", type=int, default=8,
+                   help="mocks of the cut-sky batching shape timed as context (0: skip)")
     p.add_argument("--smp-mocks", type=int, default=4,
                    help="mocks of the brute-force (Smp, M=50) comparison run; 0 skips it")
     p.add_argument("--cov-only", action="store_true",
@@ -231,6 +233,45 @@ def smp_measure(tp, ctx, dev, b, prec, n_mock, n_d, M=50, reps=2):
     rc = ctx.tpcf_sync()
     return {"ms": e0.elapsed_time(e1) / reps, "n_binned": info["n_binned"], "n_candidates": info["n_candidates"],
             "status": rc}
+
+
+def batching_measure(tp, ctx, dev, n_mock, reps=2):
+    """The cut-sky batching workload's shape on a sample of its mocks: uneven N_d (Poisson-scattered in
+    50k-400k), octant shell 1200-2400 Mpc/h, midpoint line of sight, R1 + R2 of N_d each, 40 s x 5 mu
+    bins; all mocks and terms in one batched call.  Returns ms per call and the pair totals."""
+    import torch
+    w = synth.BATCHING
+    mks = [w.make_mock(m) for m in range(n_mock)]
+    dm = [{"data": torch.from_numpy(mk.data).to(dev),
+           "randoms": torch.from_numpy(np.concatenate(mk.randoms)).to(dev),
+           "offsets": [0, len(mk.randoms[0]), len(mk.randoms[0]) + len(mk.randoms[1])]} for mk in mks]
+    b = tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_OPEN, w.L, los=tp.TPCF_LOS_MIDPOINT, observer=w.observer)
+    nbin = w.n_s * w.n_mu
+    out = {"dd": torch.empty((n_mock, nbin), dtype=torch.int64, device=dev),
+           "dr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev),
+           "rr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev)}
+    for _ in range(2):
+        ctx.tpcf_count(dm, b, mode=tp.TPCF_BATCHED, out=out)
+    torch.cuda.synchronize()
+    ctx.tpcf_set_timing(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.tpcf_count(dm, b, mode=tp.TPCF_BATCHED, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    info = ctx.tpcf_last_count_info()
+    ctx.tpcf_set_timing(False)
+    rc = ctx.tpcf_sync()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": (f"batching shape, {n_mock} mocks (N_d {min(len(mk.data) for mk in mks)}-"
+                         f"{max(len(mk.data) for mk in mks)}), cut-sky octant shell, midpoint line of sight, "
+                         "40 s x 5 mu bins: counts only, one batched call"),
+            "value": n_mock / (ms * 1e-3), "unit": "mocks/s", "ms_per_call": ms,
+            "gpairs_binned_per_s": info["n_binned"] / (ms * 1e-3) / 1e9,
+            "pairs_binned_per_call": info["n_binned"], "candidate_pairs_per_call": info["n_candidates"],
+            "pair_kernel_ms": info["paircount_ms"] / max(1, info["timed_calls"]), "status": rc}
 
 
 def next_rows_measure(tp, ctx, dev, reps=20):
@@ -543,6 +584,10 @@ def main():
     if rank == 0 and not args.no_precision_config:
         nxt = next_rows_measure(tp, ctx, dev)
 
+    bat = None
+    if rank == 0 and world == 1 and args.batching_mocks > 0:
+        bat = batching_measure(tp, ctx, dev, args.batching_mocks)
+
     kernels_per_step = info["n_kernels"] + 3 + 4   # count + 3 LS + 4 covariance kernels
     if rank == 0:
         line = {
@@ -566,6 +611,7 @@ def main():
             "precision_config": prec_cfg,
             "smp_comparison": smp,
             "after_covariance": nxt,
+            "batching_sample": bat,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-op/s",
                          "frac": achieved / peak, "traffic": measured_traffic(n_mock),
                          "traffic_note": "ncu DRAM bytes of 2 mocks scaled to the launch's mocks",

@@ -75,8 +75,13 @@ constexpr uint32_t O_SEG = al16(O_A + 16 * (UNIT_CHUNK + 8));           // Seg [
 constexpr uint32_t O_B = al16(O_SEG + 16 * (MAX_SEGS + 1));             // midpoint: float4 [WARPS][P][32] b copies
                                                                         // (.w = b index)
 __host__ __device__ constexpr uint32_t o_q(bool mid) { return al16(O_B + (mid ? 16u * WARPS * P * 32 : 0u)); }
-// queues: x: (d2, dx) [WARPS][QX + 1][32]; midpoint: u16 [WARPS][QN][32] + compacted [WARPS][QN * 32]
-__host__ __device__ constexpr uint32_t o_x(bool mid) { return al16(o_q(mid) + (mid ? 2u * WARPS * QN * 32 * 2 : 8u * WARPS * (QX + 1) * 32)); }
+// queues: x: (d2, dx) [WARPS][QX + 1][32] + 2 padding rows (a flush pass reads
+// up to 3 rows past a lane's count: the next warp's column, or the padding);
+// midpoint: u16 [WARPS][QN][32] + compacted [WARPS][QN * 32]
+__host__ __device__ constexpr uint32_t o_x(bool mid)
+{
+    return al16(o_q(mid) + (mid ? 2u * WARPS * QN * 32 * 2 : 8u * 32 * (WARPS * (QX + 1) + 2)));
+}
 __host__ __device__ constexpr uint32_t o_var(bool mid) { return o_x(mid); }
 
 // offsets of the arrays sized by the binning: T u64 [n_s + 1], hist int
@@ -645,9 +650,10 @@ struct Ctx {
     }
 
     // Bin this lane's column (n entries; the window's pushes began at a-chunk
-    // index a_lo), two entries per lane per pass.  All lanes run the same
-    // passes; a lane past its count reads a stale slot and discards it (slot
-    // QX exists and is never written: always in bounds).
+    // index a_lo), four entries per lane per pass.  All lanes run the same
+    // passes; a lane past its count reads a stale slot and discards it (rows
+    // up to QX + 2 lie inside the queue region: the next warp's column, or
+    // the padding after the last warp's).
     template <bool SELF>
     __device__ __forceinline__ void flush_x(uint32_t n, uint32_t a_lo, uint32_t ib0, const float (&bx)[P],
                                             const float (&by)[P], const float (&bz)[P])
@@ -655,15 +661,18 @@ struct Ctx {
         const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         uint32_t amask = 0;   // bit k: entry k lies in an error band (QX < 32 slots)
-        for (uint32_t k = 0; k < nmax; k += 2) {
-            const bool live0 = k < n, live1 = k + 1 < n;
-            const float2 e0 = lds64(q + k * 256u), e1 = lds64(q + (k + 1u) * 256u);
-            const Cls c0 = classify(e0.x, e0.y, z, z), c1 = classify(e1.x, e1.y, z, z);
-            red_x(c0.addr, live0 && c0.good);
-            red_x(c1.addr, live1 && c1.good);
+        for (uint32_t k = 0; k < nmax; k += 4) {
             const uint32_t bit = 1u << k;
-            if (live0 && c0.amb) amask |= bit;
-            if (live1 && c1.amb) amask |= bit << 1;
+#pragma unroll
+            for (uint32_t h = 0; h < 4; h += 2) {
+                const bool live0 = k + h < n, live1 = k + h + 1 < n;
+                const float2 e0 = lds64(q + (k + h) * 256u), e1 = lds64(q + (k + h + 1u) * 256u);
+                const Cls c0 = classify(e0.x, e0.y, z, z), c1 = classify(e1.x, e1.y, z, z);
+                red_x(c0.addr, live0 && c0.good);
+                red_x(c1.addr, live1 && c1.good);
+                if (live0 && c0.amb) amask |= bit << h;
+                if (live1 && c1.amb) amask |= bit << (h + 1);
+            }
         }
         if (__any_sync(0xffffffffu, amask != 0)) {
             // rare: set the ambiguous entries aside, one per lane per round
