@@ -49,6 +49,7 @@ constexpr int M_CNT = 8;        // [WARPS] survivors per warp in the current win
 constexpr int M_N = 24;
 constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 static_assert(P == 4, "tile_x unrolls four b-points per lane");
+static_assert((QX + 1) % 4 == 0, "x-path flush passes read four rows and stay in the lane's column");
 static_assert(UNIT_CHUNK % 32 == 0 && UNIT_CHUNK <= 128 && UNIT_CHUNK <= WARPS * 32, "a-chunk load and box");
 
 typedef unsigned __int128 u128;
@@ -75,12 +76,10 @@ constexpr uint32_t O_SEG = al16(O_A + 16 * (UNIT_CHUNK + 8));           // Seg [
 constexpr uint32_t O_B = al16(O_SEG + 16 * (MAX_SEGS + 1));             // midpoint: float4 [WARPS][P][32] b copies
                                                                         // (.w = b index)
 __host__ __device__ constexpr uint32_t o_q(bool mid) { return al16(O_B + (mid ? 16u * WARPS * P * 32 : 0u)); }
-// queues: x: (d2, dx) [WARPS][QX + 1][32] + 2 padding rows (a flush pass reads
-// up to 3 rows past a lane's count: the next warp's column, or the padding);
-// midpoint: u16 [WARPS][QN][32] + compacted [WARPS][QN * 32]
+// queues: x: (d2, dx) [WARPS][QX + 1][32]; midpoint: u16 [WARPS][QN][32] + compacted [WARPS][QN * 32]
 __host__ __device__ constexpr uint32_t o_x(bool mid)
 {
-    return al16(o_q(mid) + (mid ? 2u * WARPS * QN * 32 * 2 : 8u * 32 * (WARPS * (QX + 1) + 2)));
+    return al16(o_q(mid) + (mid ? 2u * WARPS * QN * 32 * 2 : 8u * WARPS * (QX + 1) * 32));
 }
 __host__ __device__ constexpr uint32_t o_var(bool mid) { return o_x(mid); }
 
@@ -271,6 +270,10 @@ __device__ __forceinline__ void push_if_lt(uint32_t &head, float d2, uint32_t e,
         : "f"(d2), "f"(h), "r"(__float_as_uint(d2)), "r"(e)
         : "memory");
 }
+__device__ __forceinline__ void sts64(uint32_t a, float x, float y)
+{
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
+}
 __device__ __forceinline__ float2 lds64(uint32_t a)
 {
     float2 v;
@@ -345,7 +348,11 @@ struct Ctx {
             const bool ge_hi = d2 >= lh.y;
             amb |= (d2 >= lh.x) && !ge_hi;
             k += ge_hi ? 1 : 0;
-            valid = (unsigned)k < (unsigned)prm.n_s;
+            // at or beyond the last edge's band a pair is certainly not binned
+            // (the x-path queue sentinel lies there)
+            const bool beyond = d2 >= prm.hit_max;
+            amb = amb && !beyond;
+            valid = !beyond && (unsigned)k < (unsigned)prm.n_s;
             ks = (uint32_t)k;
         }
         if (MU) {
@@ -650,28 +657,35 @@ struct Ctx {
     }
 
     // Bin this lane's column (n entries; the window's pushes began at a-chunk
-    // index a_lo), four entries per lane per pass.  All lanes run the same
-    // passes; a lane past its count reads a stale slot and discards it (rows
-    // up to QX + 2 lie inside the queue region: the next warp's column, or
-    // the padding after the last warp's).
+    // index a_lo), four entries per lane per pass.  Every slot that holds no
+    // pending entry holds the sentinel (prm.sent_d2, prm.sent_dx), which
+    // classifies as a certain pair half a bin past the last edge (its add
+    // lands in a spare word), so no pass needs a per-lane count test: the
+    // head slot, which the last miss overwrote, is reset here, and every
+    // slot is reset after it is read.  QX + 1 is a multiple of 4, so the
+    // passes never leave the lane's own column.
     template <bool SELF>
     __device__ __forceinline__ void flush_x(uint32_t n, uint32_t a_lo, uint32_t ib0, const float (&bx)[P],
                                             const float (&by)[P], const float (&bz)[P])
     {
         const uint32_t nmax = __reduce_max_sync(0xffffffffu, n);
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float sd2 = prm.sent_d2, sdx = prm.sent_dx;
+        sts64(q + n * 256u, sd2, sdx);
         uint32_t amask = 0;   // bit k: entry k lies in an error band (QX < 32 slots)
         for (uint32_t k = 0; k < nmax; k += 4) {
             const uint32_t bit = 1u << k;
 #pragma unroll
             for (uint32_t h = 0; h < 4; h += 2) {
-                const bool live0 = k + h < n, live1 = k + h + 1 < n;
-                const float2 e0 = lds64(q + (k + h) * 256u), e1 = lds64(q + (k + h + 1u) * 256u);
+                const uint32_t a0s = q + (k + h) * 256u, a1s = a0s + 256u;
+                const float2 e0 = lds64(a0s), e1 = lds64(a1s);
+                sts64(a0s, sd2, sdx);
+                sts64(a1s, sd2, sdx);
                 const Cls c0 = classify(e0.x, e0.y, z, z), c1 = classify(e1.x, e1.y, z, z);
-                red_x(c0.addr, live0 && c0.good);
-                red_x(c1.addr, live1 && c1.good);
-                if (live0 && c0.amb) amask |= bit << h;
-                if (live1 && c1.amb) amask |= bit << (h + 1);
+                red_x(c0.addr, c0.good);
+                red_x(c1.addr, c1.good);
+                if (c0.amb) amask |= bit << h;
+                if (c1.amb) amask |= bit << (h + 1);
             }
         }
         if (__any_sync(0xffffffffu, amask != 0)) {
@@ -1009,6 +1023,8 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
     }
     cx.abase = sbase + O_A;
     cx.hbase = sbase + vo.hist;
+    if (!MID)
+        for (uint32_t k = 0; k <= (uint32_t)QX; k++) sts64(cx.q + k * 256u, prm.sent_d2, prm.sent_dx);
     {
         // classify encodes the s bin with the bias of B's bit pattern on the
         // linear path, the mu bin always (see classify)

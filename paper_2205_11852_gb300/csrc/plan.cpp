@@ -312,6 +312,14 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
     }
     p.s_top = 12582912.0f + (float)b.n_s;
     p.f_nmu = (float)b.n_mu;
+    // queue sentinel: separation (n_s + 1/2) / n_s times the last edge (past
+    // its band, half a bin past it for linear bins), |mu| = 1 / (2 n_mu)
+    {
+        const double smax_q = b.s_edges[b.n_s] * std::ldexp(1.0, p.bits) / L;
+        const double s_sent = smax_q * (b.n_s + 0.5) / b.n_s;
+        p.sent_d2 = (float)(s_sent * s_sent);
+        p.sent_dx = (float)(0.5 * s_sent / b.n_mu);
+    }
 
     // s-bin table over FP32 bit patterns of d2 + bias.  The bias (a power of
     // two well below the first positive edge band) keeps every key at or

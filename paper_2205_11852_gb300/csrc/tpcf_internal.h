@@ -72,6 +72,7 @@ struct CountParams {
                                // [v s_lo_mul - s_c0, v s_hi_mul + s_c0] (directed roundings)
     float s_top;           // 1.5 * 2^23 + n_s: floor(u_lo) + 1.5 * 2^23 < s_top <=> s bin < n_s
     float f_nmu;           // n_mu as a float
+    float sent_d2, sent_dx;    // x-path queue sentinel: s half a bin past the last edge, mu mid-bin
     long long obs[3];      // observer in grid units (midpoint line of sight)
     unsigned long long T[MAX_NS + 1];        // exact squared edges in grid units
     float lo[MAX_NS + 2], hi[MAX_NS + 2];    // float bands: d2 < lo => D2 < T; d2 >= hi => D2 >= T;
