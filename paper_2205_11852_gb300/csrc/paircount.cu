@@ -39,7 +39,7 @@ constexpr int P = 4;            // b-points per lane
 constexpr int TILE = 32 * P;    // b-points per warp tile
 constexpr int QN = 24;          // queue slots per lane, midpoint path (16-bit entries)
 constexpr int QX = 23;          // queue slots per lane, x line of sight (8-byte entries)
-constexpr int XCAP = 64;        // per-warp list of pairs awaiting the exact recheck (x path, global scratch)
+constexpr int XCAP = 96;        // per-warp list of pairs awaiting the exact recheck (global scratch)
 constexpr int WARPS = 8;        // warps per block
 constexpr int CAP = 12288;      // raw neighbour points filtered per window
 constexpr int SCR_W = CAP + 8 * 32;                 // float4 scratch entries per block window (+ per-warp rounding)
@@ -75,7 +75,9 @@ constexpr uint32_t O_A = al16(O_STAT + 8 * 3 * WARPS);                  // float
 constexpr uint32_t O_SEG = al16(O_A + 16 * (UNIT_CHUNK + 8));           // Seg [MAX_SEGS + 1]
 constexpr uint32_t O_B = al16(O_SEG + 16 * (MAX_SEGS + 1));             // midpoint: float4 [WARPS][P][32] b copies
                                                                         // (.w = b index)
-__host__ __device__ constexpr uint32_t o_q(bool mid) { return al16(O_B + (mid ? 16u * WARPS * P * 32 : 0u)); }
+// (midpoint: slot s = p * 32 + lane is stored at s + s / 32, so that one
+// lane's P slots fall in different bank groups)
+__host__ __device__ constexpr uint32_t o_q(bool mid) { return al16(O_B + (mid ? 16u * WARPS * P * 33 : 0u)); }
 // queues: x: (d2, dx) [WARPS][QX + 1][32]; midpoint: u16 [WARPS][QN][32] + compacted [WARPS][QN * 32]
 __host__ __device__ constexpr uint32_t o_x(bool mid)
 {
@@ -191,13 +193,6 @@ __device__ __forceinline__ float rsqrt_approx(float x)
 
 // 32-bit shared-memory accesses (addresses from __cvta_generic_to_shared)
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// 16-bit shared load through a 32-bit register (zero-extended)
-__device__ __forceinline__ uint32_t lds16(uint32_t a)
-{
-    uint32_t v;
-    asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
 // queue push: store v at the head slot; advance the head (one 64-byte slot
 // row) only when t >= h
 __device__ __forceinline__ void push_if_ge(uint32_t &head, uint32_t v, float t, float h)
@@ -221,16 +216,6 @@ __device__ __forceinline__ float4 lds128(uint32_t a)
 __device__ __forceinline__ void red_inc(uint32_t a)
 {
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a) : "memory");
-}
-// histogram increment when ok != 0, without a branch
-__device__ __forceinline__ void red_inc_if(uint32_t addr, int ok)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.s32 p, %1, 0;\n\t"
-        "@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(addr),
-        "r"(ok)
-        : "memory");
 }
 // 16-bit shared load when live (else 0), without a branch
 __device__ __forceinline__ uint32_t lds16_if(uint32_t a, bool live)
@@ -302,7 +287,7 @@ struct Ctx {
     uint32_t cq;               // this warp's compacted queue (shared address)
     uint32_t bc;               // this warp's b copies (midpoint path; .w: b index)
     uint32_t n_list;           // entries in it (warp-uniform)
-    uint32_t hdum;             // this lane's spare word after the histogram (x path)
+    uint32_t hdum;             // this lane's spare word after the histogram
     float4 *scr;               // this block's scratch: the current window's surviving b-points
     uint32_t R;                // per-warp region length of the current window (entries)
     uint32_t abase;            // the a-chunk (shared address)
@@ -391,11 +376,14 @@ struct Ctx {
         return o;
     }
 
+    // Padded position of b copy slot s (see o_q).
+    __device__ __forceinline__ uint32_t bslot(uint32_t s) const { return s + (s >> 5); }
+
     // Classification of queue entry v (a index | b copy index << 8).
     __device__ __forceinline__ Cls bin_of(uint32_t v) const
     {
         const float4 a = lds128(abase + 16u * (v & 255u));
-        const float4 b = lds128(bc + 16u * (v >> 8));
+        const float4 b = lds128(bc + 16u * bslot(v >> 8));
         const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
         const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
         return classify(d2, dx, a, b);
@@ -404,8 +392,8 @@ struct Ctx {
     // Midpoint path: bin every queued pair.  The lanes' queues are first packed into one
     // warp-contiguous list (a index | b copy index << 8), so that the binning
     // loop runs with all lanes busy whatever the spread of per-lane counts.
-    // Pairs that need the exact recheck are rechecked at the end.  n = this
-    // lane's count.
+    // Pairs that need the exact recheck go to the warp's recheck list, which
+    // is rechecked 32 at a time.  n = this lane's count.
     __device__ __forceinline__ void flush_mid(uint32_t n)
     {
         uint32_t total;
@@ -417,7 +405,6 @@ struct Ctx {
             sts16_if(cq + 2u * (pos + k), v, mine);
         }
         __syncwarp();
-        uint32_t n_amb = 0;
         const uint32_t lt = (1u << lane) - 1u;
         // two entries per lane per pass (independent work for the scheduler)
         for (uint32_t w0 = 0; w0 < total; w0 += 64) {
@@ -426,30 +413,29 @@ struct Ctx {
             const uint32_t v0 = lds16_if(cq + 2u * e0, live0);
             const uint32_t v1 = lds16_if(cq + 2u * e1, live1);
             const Cls c0 = bin_of(v0), c1 = bin_of(v1);   // dead slots read entry 0: in bounds, discarded
-            red_inc_if(c0.addr, live0 && c0.good);
-            red_inc_if(c1.addr, live1 && c1.good);
+            red_x(c0.addr, live0 && c0.good);
+            red_x(c1.addr, live1 && c1.good);
             const bool x0 = live0 && c0.amb, x1 = live1 && c1.amb;
             const unsigned am0 = __ballot_sync(0xffffffffu, x0);
             const unsigned am1 = __ballot_sync(0xffffffffu, x1);
             if (am0 | am1) {
-                // rare: keep the entries for the exact recheck, written over
-                // entries this loop has already consumed
-                __syncwarp();
-                sts16_if(cq + 2u * (n_amb + __popc(am0 & lt)), v0, x0);
-                n_amb += __popc(am0);
-                sts16_if(cq + 2u * (n_amb + __popc(am1 & lt)), v1, x1);
-                n_amb += __popc(am1);
+                // rare: the pair (a index, b index) goes to the recheck list
+                // (at most 31 + 64 entries after this, within XCAP)
+                if (x0) xlist()[n_list + __popc(am0 & lt)] = make_uint2(a0 + (v0 & 255u), b_index(v0 >> 8));
+                n_list += __popc(am0);
+                if (x1) xlist()[n_list + __popc(am1 & lt)] = make_uint2(a0 + (v1 & 255u), b_index(v1 >> 8));
+                n_list += __popc(am1);
+                if (n_list >= 32) recheck_list();
             }
         }
-        __syncwarp();
-        for (uint32_t e = lane; e < n_amb; e += 32) {
-            const uint32_t v = lds16(cq + 2u * e);
-            const float4 b = lds128(bc + 16u * (v >> 8));
-            const int bin = exact_bin(prm, (const unsigned long long *)(smem_raw + var_offsets(prm, MID).T), m.us, m.n_total, a0 + (v & 255u), __float_as_uint(b.w));
-            n_exact++;
-            if (bin >= 0) red_inc(hbase + 4u * (uint32_t)bin);
-        }
-        __syncwarp();
+    }
+
+    // b index of b copy slot s (its .w).
+    __device__ __forceinline__ uint32_t b_index(uint32_t s) const
+    {
+        uint32_t i;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(i) : "r"(bc + 16u * bslot(s) + 12u) : "memory");
+        return i;
     }
 
     // ---- neighbour filtering ----
@@ -812,7 +798,7 @@ struct Ctx {
             hb[p] = __int_as_float(0x7f800000);   // +inf: never passes
             i = 0;
         }
-        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(bc + 16u * (uint32_t)(p * 32 + lane)),
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(bc + 16u * bslot((uint32_t)(p * 32 + lane))),
                      "f"(bx[p]), "f"(by[p]), "f"(bz[p]), "f"(__uint_as_float(i))
                      : "memory");
     }
@@ -1012,14 +998,14 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
                          0.f, 0.f, 0.f, 0u, 0u};
     cx.scr = scratch + (size_t)blockIdx.x * SCR;
     const uint32_t sbase = saddr(smem_raw);
+    cx.hdum = sbase + vo.hist + 4u * ((uint32_t)prm.nbin + (uint32_t)cx.lane);
     if (MID) {
         const uint32_t qw = sbase + o_q(true) + (uint32_t)cx.warp * (QN * 32 * 2 * 2);
         cx.q = qw + 2u * (uint32_t)cx.lane;
         cx.cq = qw + QN * 32 * 2;
-        cx.bc = sbase + O_B + (uint32_t)cx.warp * (P * 32 * 16);
+        cx.bc = sbase + O_B + (uint32_t)cx.warp * (P * 33 * 16);
     } else {
         cx.q = sbase + o_q(false) + (uint32_t)cx.warp * ((QX + 1) * 32 * 8) + 8u * (uint32_t)cx.lane;
-        cx.hdum = sbase + vo.hist + 4u * ((uint32_t)prm.nbin + (uint32_t)cx.lane);
     }
     cx.abase = sbase + O_A;
     cx.hbase = sbase + vo.hist;
@@ -1138,7 +1124,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
                 ti = __shfl_sync(0xffffffffu, nx, 0);
             }
             const bool last = w0 + CAP >= total;
-            if (!MID && last && cx.n_list) cx.recheck_list();   // the list refers to this unit's histogram
+            if (last && cx.n_list) cx.recheck_list();   // the list refers to this unit's histogram
             __syncthreads();   // every warp is done with this window's scratch, counter and histogram adds
             if (tid == 0) sh_misc()[3] = 0;
             if (last) break;
