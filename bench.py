@@ -65,6 +65,8 @@ def parse():
                    help="two split-precision LC covariances of 3500 mocks x 200 bins, then exit (profiler captures)")
     p.add_argument("--count-only", action="store_true",
                    help="one warm-up and one batched tpcf_count of the workload, then exit (profiler captures)")
+    p.add_argument("--count-only-batching", type=int, default=0, metavar="N",
+                   help="like --count-only on N mocks of the cut-sky batching shape (midpoint line of sight)")
     return p.parse_args()
 
 
@@ -434,6 +436,22 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    if args.count_only_batching:
+        w = synth.BATCHING
+        mks = [w.make_mock(m) for m in range(args.count_only_batching)]
+        dm = [{"data": torch.from_numpy(mk.data).to(dev),
+               "randoms": torch.from_numpy(np.concatenate(mk.randoms)).to(dev),
+               "offsets": [0, len(mk.randoms[0]), len(mk.randoms[0]) + len(mk.randoms[1])]} for mk in mks]
+        bb = tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_OPEN, w.L, los=tp.TPCF_LOS_MIDPOINT, observer=w.observer)
+        for _ in range(2):
+            ctx.tpcf_count(dm, bb, mode=tp.TPCF_BATCHED)
+        ctx.tpcf_sync()
+        info = ctx.tpcf_last_count_info()
+        print(json.dumps({"count_only": True, "workload": "batching", "mocks": len(mks),
+                          "n_candidates": info["n_candidates"], "n_binned": info["n_binned"],
+                          "n_exact": info["n_exact"]}))
+        ctx.close()
+        return
     if args.count_only:
         for _ in range(2):
             ctx.tpcf_count(mocks, b, mode=tp.TPCF_BATCHED, out=outc)
