@@ -117,6 +117,24 @@ def test_counts_any_mesh_subdivision(tp, ctx, subdiv):
         ctx.tpcf_set_cell_subdiv(0)
 
 
+def test_counts_neighbourhood_beyond_one_filter_window(tp, ctx):
+    """Dense periodic box: about 44 points per mesh cell at subdivision 3, so the neighbour runs of a cell hold
+    ~13 700 raw points, more than one filter window (12 288), and every unit's b side is filtered and tiled in two
+    windows.  D x R counts must still equal the brute-force oracle bit for bit."""
+    L = 150.0
+    rng = np.random.default_rng(20261203)
+    n = 150_000
+    d = synth.neyman_scott(rng, n, L, 2e-3, 1.0)
+    r = synth.uniform_box(np.random.default_rng(7), n, L)
+    mocks = [synth.Mock(d, [r])]
+    tb, ob = _periodic(L, np.linspace(0, 30.0, 16), 4)
+    ctx.tpcf_set_cell_subdiv(3)
+    try:
+        _check_counts(ctx, tp, mocks, tb, ob, modes=(0,), terms=2)
+    finally:
+        ctx.tpcf_set_cell_subdiv(0)
+
+
 def test_counts_open_midpoint(tp, ctx):
     """Cut-sky octant shell, observer at the origin, midpoint line of sight (batching shape, scaled)."""
     L = 600.0
