@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--batching-mocks", type=int, default=8,
                    help="mocks of the cut-sky batching shape timed as context (0: skip)")
+    p.add_argument("--scale-mocks", type=int, default=2,
+                   help="mocks of the scale shape (1e6 points) timed as context (0: skip)")
     p.add_argument("--smp-mocks", type=int, default=4,
                    help="mocks of the brute-force (Smp, M=50) comparison run; 0 skips it")
     p.add_argument("--cov-only", action="store_true",
@@ -274,6 +276,44 @@ def batching_measure(tp, ctx, dev, n_mock, reps=2):
             "gpairs_binned_per_s": info["n_binned"] / (ms * 1e-3) / 1e9,
             "pairs_binned_per_call": info["n_binned"], "candidate_pairs_per_call": info["n_candidates"],
             "pair_kernel_ms": info["paircount_ms"] / max(1, info["timed_calls"]), "status": rc}
+
+
+def scale_measure(tp, ctx, dev, n_mock, reps=2):
+    """The scale workload's shape on a sample of its mocks: periodic L=2000 Mpc/h, N_d=1e6 Neyman-Scott,
+    R1 + R2 of N_d each, 40 s x 10 mu bins, x line of sight; all mocks and terms in one batched call."""
+    import torch
+    w = synth.SCALE
+    mks = [w.make_mock(m) for m in range(n_mock)]
+    dm = [{"data": torch.from_numpy(mk.data).to(dev),
+           "randoms": torch.from_numpy(np.concatenate(mk.randoms)).to(dev),
+           "offsets": [0, w.n_d, 2 * w.n_d]} for mk in mks]
+    b = tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_PERIODIC, w.L)
+    nbin = w.n_s * w.n_mu
+    out = {"dd": torch.empty((n_mock, nbin), dtype=torch.int64, device=dev),
+           "dr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev),
+           "rr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev)}
+    for _ in range(2):
+        ctx.tpcf_count(dm, b, mode=tp.TPCF_BATCHED, out=out)
+    torch.cuda.synchronize()
+    ctx.tpcf_set_timing(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.tpcf_count(dm, b, mode=tp.TPCF_BATCHED, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    info = ctx.tpcf_last_count_info()
+    ctx.tpcf_set_timing(False)
+    rc = ctx.tpcf_sync()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": (f"scale shape, {n_mock} mocks: periodic L=2000 Mpc/h, N_d=1e6 Neyman-Scott (n_p=2e-6, "
+                         "sigma=3), R1 + R2 of 1e6 each, 40 s x 10 mu bins, x line of sight: counts only, one "
+                         "batched call"),
+            "value": n_mock / (ms * 1e-3), "unit": "mocks/s", "ms_per_call": ms,
+            "gpairs_binned_per_s": info["n_binned"] / (ms * 1e-3) / 1e9,
+            "pairs_binned_per_call": info["n_binned"], "candidate_pairs_per_call": info["n_candidates"],
+            "status": rc}
 
 
 def next_rows_measure(tp, ctx, dev, reps=20):
@@ -605,6 +645,9 @@ def main():
     bat = None
     if rank == 0 and world == 1 and args.batching_mocks > 0:
         bat = batching_measure(tp, ctx, dev, args.batching_mocks)
+    scl = None
+    if rank == 0 and world == 1 and args.scale_mocks > 0:
+        scl = scale_measure(tp, ctx, dev, args.scale_mocks)
 
     kernels_per_step = info["n_kernels"] + 3 + 4   # count + 3 LS + 4 covariance kernels
     if rank == 0:
@@ -630,6 +673,7 @@ def main():
             "smp_comparison": smp,
             "after_covariance": nxt,
             "batching_sample": bat,
+            "scale_sample": scl,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-op/s",
                          "frac": achieved / peak, "traffic": measured_traffic(n_mock),
                          "traffic_note": "ncu DRAM bytes of 2 mocks scaled to the launch's mocks",

@@ -307,7 +307,7 @@ struct Ctx {
     // floor(x_lo) + B is the bin plus the pattern of B; the histogram address
     // absorbs that bias (hadj).  Straight-line code: every lane runs the same
     // instructions.
-    __device__ __forceinline__ Cls classify(float d2, float dx, const float4 &a, const float4 &b) const
+    __device__ __forceinline__ Cls classify(float d2, float dx, float dy, float dz, const float4 &a, const float4 &b) const
     {
         const float big = 12582912.0f;   // 1.5 * 2^23
         Cls o;
@@ -350,15 +350,17 @@ struct Ctx {
                 tlo = __fmaf_rd(fabsf(dx), r, -bt);
                 thi = __fmaf_ru(fabsf(dx), r, bt);
             } else {
-                const float ex = __fsub_rn(a.x, b.x), ey = __fsub_rn(a.y, b.y), ez = __fsub_rn(a.z, b.z);
+                // t = n_mu |dot| / (|d| |l|) = |dot| r rl with r = n_mu / |d| (the
+                // s path's rsqrt); the band's 1/|d| term is mu_c1 rs = mu_c1r r
+                if (!LIN) r = rsqrt_approx(__fmul_rn(d2, prm.inv_nmu2));
                 const float lx = __fadd_rn(__fadd_rn(gx, a.x), b.x);
                 const float ly = __fadd_rn(__fadd_rn(gy, a.y), b.y);
                 const float lz = __fadd_rn(__fadd_rn(gz, a.z), b.z);
-                const float dot = __fmaf_rn(ez, lz, __fmaf_rn(ey, ly, __fmul_rn(ex, lx)));
+                const float dot = __fmaf_rn(dz, lz, __fmaf_rn(dy, ly, __fmul_rn(dx, lx)));
                 const float l2 = __fmaf_rn(lz, lz, __fmaf_rn(ly, ly, __fmul_rn(lx, lx)));
-                const float rs = rsqrt_approx(d2), rl = rsqrt_approx(l2);
-                const float t = __fmul_rn(__fmul_rn(__fmul_rn(fabsf(dot), rs), rl), prm.f_nmu);
-                const float bt = __fmaf_ru(prm.mu_c1, rs, __fmaf_ru(prm.mu_c3, rl, prm.mu_c2));
+                const float rl = rsqrt_approx(l2);
+                const float t = __fmul_rn(__fmul_rn(fabsf(dot), r), rl);
+                const float bt = __fmaf_ru(prm.mu_c1r, r, __fmaf_ru(prm.mu_c3, rl, prm.mu_c2));
                 tlo = __fsub_rd(t, bt);
                 thi = __fadd_ru(t, bt);
             }
@@ -386,7 +388,7 @@ struct Ctx {
         const float4 b = lds128(bc + 16u * bslot(v >> 8));
         const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
         const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        return classify(d2, dx, a, b);
+        return classify(d2, dx, dy, dz, a, b);
     }
 
     // Midpoint path: bin every queued pair.  The lanes' queues are first packed into one
@@ -667,7 +669,7 @@ struct Ctx {
                 const float2 e0 = lds64(a0s), e1 = lds64(a1s);
                 sts64(a0s, sd2, sdx);
                 sts64(a1s, sd2, sdx);
-                const Cls c0 = classify(e0.x, e0.y, z, z), c1 = classify(e1.x, e1.y, z, z);
+                const Cls c0 = classify(e0.x, e0.y, 0.f, 0.f, z, z), c1 = classify(e1.x, e1.y, 0.f, 0.f, z, z);
                 red_x(c0.addr, c0.good);
                 red_x(c1.addr, c1.good);
                 if (c0.amb) amask |= bit << h;

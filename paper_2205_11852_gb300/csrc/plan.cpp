@@ -289,6 +289,7 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
         p.mu_c1 = (float)(b.n_mu * 2.2 * std::sqrt(3.0) * E);
         p.mu_c2 = (float)(b.n_mu * std::ldexp(1.0, -18));
         p.mu_c3 = (float)(b.n_mu * 2.2 * std::sqrt(3.0) * El);
+        p.mu_c1r = up_f((double)p.mu_c1 / b.n_mu);
     }
 
     // Linear bins starting at 0 (e_k = k e_1 exactly): the s bin is

@@ -64,6 +64,7 @@ struct CountParams {
     float dot_margin;      // slack of the dot-product candidate test
     float mu_c1, mu_c2;    // mu ambiguity band (see the kernel)
     float mu_c3;
+    float mu_c1r;          // midpoint line of sight: mu_c1 / n_mu (rounded up)
     float inv_nmu2;        // 1 / n_mu^2
     int linear;            // edges e_k = k * ds exactly: s bin = floor(sqrt(D2) / (q ds))
     float s_scale;         // 1 / (n_mu q ds): u = d2 * (n_mu / sqrt(d2)) * s_scale = sqrt(d2) / (q ds)
