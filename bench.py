@@ -361,16 +361,26 @@ def next_rows_measure(tp, ctx, dev, reps=20):
     return out
 
 
+def kernel_code_hash(path):
+    """sha256 prefix of a CUDA source with comments and blank space removed: it changes
+    only when the code does (a profile taken before a comment edit still describes it)."""
+    import hashlib, re
+    src = open(path, encoding="utf-8").read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = "\n".join(line.strip() for line in src.splitlines() if line.strip())
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def measured_traffic(n_mock):
     """DRAM bytes of one pair-count launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    import hashlib
+    taken on the current kernel code (else None)."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "paircount_traffic.json")))
-        src = open(os.path.join(ROOT, "paper_2205_11852_gb300", "csrc", "paircount.cu"), "rb").read()
+        code = kernel_code_hash(os.path.join(ROOT, "paper_2205_11852_gb300", "csrc", "paircount.cu"))
     except OSError:
         return None
-    if hashlib.sha256(src).hexdigest()[:16] != rec.get("kernel_source_sha256_prefix"):
+    if code != rec.get("kernel_code_sha256_prefix"):
         return None
     return rec["dram_bytes_per_mock"] * n_mock
 

@@ -6,18 +6,23 @@
 // the neighbourhood of A.  A thread block owns a unit: the a-chunk and the
 // histogram live in shared memory, and the warps share the b side.  The
 // neighbourhood is walked as rows of cells (dz, dy) whose x-runs are
-// contiguous in the cell-sorted point order; every run is cut into tiles of
-// 32*P b-points, and the tiles are dealt to the warps.  A warp loads its tile
-// once, one P-vector per lane, shifted into A's frame, then streams the
-// a-chunk past it by broadcast shared-memory loads.
+// contiguous in the cell-sorted point order.  The warps first filter the
+// runs: a b-point is kept only if its distance to the a-chunk's bounding box
+// is below the last edge's band, and the survivors (shifted into A's frame)
+// go to the block's scratch window in global memory.  The window is cut into
+// tiles of 32*P points dealt to the warps; a warp loads its tile once, one
+// P-vector per lane, then streams the a-chunk past it by broadcast
+// shared-memory loads.
 //
 // Line of sight along x (every periodic box).  Per pair the lane forms the
 // FP32 differences and d2 = dx^2 + dy^2 + dz^2 and appends (d2, dx) to its
 // own queue column in shared memory, branch-free: the store always happens
 // and only a pair with d2 below the last edge's band advances the column
-// head.  A flush bins the columns in place, two entries per lane per pass:
+// head.  A flush bins the columns in place, four entries per lane per pass:
 // the s and mu bins are floors of FP32 estimates, each bracketed by a
-// rigorous error interval, so no point is read back from shared memory.  A
+// rigorous error interval, so no point is read back from shared memory.
+// Slots without a pending entry hold a sentinel pair that classifies as
+// certain and lands in a spare word, so the passes need no count tests.  A
 // pair whose interval contains a bin edge (about 3 in 10^4) is identified by
 // replaying its lane's pushes since the flush window began, set aside, and
 // rechecked exactly from the integer grid coordinates (64-bit squared
@@ -28,7 +33,7 @@
 // the queue holds 16-bit (a index, b slot) entries, pushed after a
 // dot-product range test (a.b' - |a|^2/2 >= (|b'|^2 - H)/2 - margin: three
 // FMAs and a compare), compacted per warp and binned from the a-chunk and
-// the tile's b copies.
+// the tile's b copies; its rechecks go through the same 32-at-a-time list.
 #include "plan.h"
 
 namespace tpcf {
