@@ -794,20 +794,35 @@ struct Ctx {
     __device__ __forceinline__ void put_b(int p, bool ok, float x, float y, float z, uint32_t i, float (&bx)[P],
                                           float (&by)[P], float (&bz)[P], float (&hb)[P]) const
     {
-        if (ok) {
-            bx[p] = x;
-            by[p] = y;
-            bz[p] = z;
-            const float b2 = __fmaf_rn(bz[p], bz[p], __fmaf_rn(by[p], by[p], __fmul_rn(bx[p], bx[p])));
-            hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, prm.hit_max)), prm.dot_margin);
-        } else {
-            bx[p] = by[p] = bz[p] = 0.0f;
-            hb[p] = __int_as_float(0x7f800000);   // +inf: never passes
+        if (!ok) {
+            // a missing point sits at 1e18 per axis: its threshold (~1.5e36)
+            // exceeds every a.b' (|a| < 2^31, so below 1e28) and never passes
+            x = y = z = 1e18f;
             i = 0;
         }
+        bx[p] = x;
+        by[p] = y;
+        bz[p] = z;
+        const float b2 = __fmaf_rn(z, z, __fmaf_rn(y, y, __fmul_rn(x, x)));
+        hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, prm.hit_max)), prm.dot_margin);
         asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(bc + 16u * bslot((uint32_t)(p * 32 + lane))),
                      "f"(bx[p]), "f"(by[p]), "f"(bz[p]), "f"(__uint_as_float(i))
                      : "memory");
+    }
+
+    // This lane's b-points and push thresholds from the warp's b copies (a
+    // missing point was stored at 1e18 per axis, so its threshold never passes).
+    __device__ __forceinline__ void reload_b(float (&bx)[P], float (&by)[P], float (&bz)[P], float (&hb)[P]) const
+    {
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            const float4 v = lds128(bc + 16u * bslot((uint32_t)(p * 32 + lane)));
+            bx[p] = v.x;
+            by[p] = v.y;
+            bz[p] = v.z;
+            const float b2 = __fmaf_rn(v.z, v.z, __fmaf_rn(v.y, v.y, __fmul_rn(v.x, v.x)));
+            hb[p] = __fsub_rn(__fmul_rn(0.5f, __fsub_rn(b2, prm.hit_max)), prm.dot_margin);
+        }
     }
 
     // all pairs of the a-chunk with one tile of b-points: the self cell of an
@@ -865,6 +880,9 @@ struct Ctx {
             if (__any_sync(0xffffffffu, head > lim)) {
                 flush_mid((head - q) >> 6);
                 head = q;
+                // the b-points come back from the warp's copies: not held in
+                // registers across the flush, whose binning needs them
+                reload_b(bx, by, bz, hb);
             }
         }
         if (ai < na) {
