@@ -93,9 +93,10 @@ __host__ __device__ constexpr uint32_t o_var(bool mid) { return o_x(mid); }
 // offsets of the arrays sized by the binning: T u64 [n_s + 1], hist int
 // [nbin + max(32, n_mu)] (spare words: per-lane dummies of the x path's adds,
 // and the bins past the last edge of the linear path), lohi float2 [n_s + 2], orig u32
-// [n_c + 1], table i16 [tab_n]
+// [n_c + 1], table i16 [tab_n], sxf float [n_c] (x shift of each cell column into
+// the current unit's frame)
 struct VarOff {
-    uint32_t T, hist, lohi, orig, table, end;
+    uint32_t T, hist, lohi, orig, table, sxf, end;
 };
 __host__ __device__ inline VarOff var_offsets(const CountParams &p, bool mid)
 {
@@ -105,7 +106,8 @@ __host__ __device__ inline VarOff var_offsets(const CountParams &p, bool mid)
     v.lohi = al16(v.hist + 4u * (uint32_t)(p.nbin + (p.n_mu > 32 ? p.n_mu : 32)));
     v.orig = al16(v.lohi + 8u * (uint32_t)(p.n_s + 2));
     v.table = al16(v.orig + 4u * (uint32_t)(p.n_c + 1));
-    v.end = al16(v.table + (p.linear ? 0u : 2u * (uint32_t)p.tab_n));
+    v.sxf = al16(v.table + (p.linear ? 0u : 2u * (uint32_t)p.tab_n));
+    v.end = al16(v.sxf + 4u * (uint32_t)p.n_c);
     return v;
 }
 
@@ -474,13 +476,20 @@ struct Ctx {
     // could pass is lost.  Warp w filters the w-th slice of the window and
     // appends survivors (b' in A's frame, .w = b index) to its own region of
     // the block's scratch, in order; the survivor count goes to misc.
-    __device__ __forceinline__ void filter_window(uint32_t w0, uint32_t win, int n_seg, uint32_t orig_ax)
+    __device__ __forceinline__ void filter_window(uint32_t w0, uint32_t win, int n_seg)
     {
         const Box bb = chunk_box();
         R = (((win + WARPS - 1) / WARPS) + 31u) & ~31u;
         const uint32_t r0 = w0 + (uint32_t)warp * R, r1 = min(r0 + R, w0 + win);
-        const float lox = bb.lx, loy = bb.ly, loz = bb.lz, hix = bb.hx, hiy = bb.hy, hiz = bb.hz;
+        // box as centre and half-widths: per axis q = max(|x - c| - h, 0)
+        const float cx = 0.5f * (bb.lx + bb.hx), cy = 0.5f * (bb.ly + bb.hy), cz = 0.5f * (bb.lz + bb.hz);
+        // half-widths rounded up and the centre rounded to nearest: the box
+        // [c - h, c + h] still holds every a-point
+        const float hx = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(bb.hx, bb.lx)), __fmul_ru(1.0f / 8388608.0f, cx));
+        const float hy = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(bb.hy, bb.ly)), __fmul_ru(1.0f / 8388608.0f, cy));
+        const float hz = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(bb.hz, bb.lz)), __fmul_ru(1.0f / 8388608.0f, cz));
         const float hf = prm.hit_max * (1.0f + 1.0f / 65536.0f);
+        const float *sxf = (const float *)(smem_raw + var_offsets(prm, MID).sxf);
         float4 *dst = scr + (size_t)warp * R;
         uint32_t cnt = 0;
         if (r0 < r1) {
@@ -501,14 +510,13 @@ struct Ctx {
                     const Seg sg = sh_segs()[g];
                     const uint32_t i = sg.s0 + (o - sg.off0);
                     const float4 v = __ldg(m.pf + i);
-                    const float sx = (float)(int)(sh_orig<MID>(prm)[m.pcx[i]] - orig_ax);
-                    e.x = __fadd_rn(v.x, sx);
+                    e.x = __fadd_rn(v.x, sxf[m.pcx[i]]);
                     e.y = __fadd_rn(v.y, sg.sy);
                     e.z = __fadd_rn(v.z, sg.sz);
                     e.w = __uint_as_float(i);
-                    const float qx = fmaxf(fmaxf(__fsub_rn(lox, e.x), __fsub_rn(e.x, hix)), 0.0f);
-                    const float qy = fmaxf(fmaxf(__fsub_rn(loy, e.y), __fsub_rn(e.y, hiy)), 0.0f);
-                    const float qz = fmaxf(fmaxf(__fsub_rn(loz, e.z), __fsub_rn(e.z, hiz)), 0.0f);
+                    const float qx = fmaxf(__fsub_rn(fabsf(__fsub_rn(e.x, cx)), hx), 0.0f);
+                    const float qy = fmaxf(__fsub_rn(fabsf(__fsub_rn(e.y, cy)), hy), 0.0f);
+                    const float qz = fmaxf(__fsub_rn(fabsf(__fsub_rn(e.z, cz)), hz), 0.0f);
                     keep = __fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmul_rn(qx, qx))) < hf;
                 }
                 const unsigned mk = __ballot_sync(0xffffffffu, keep);
@@ -1108,6 +1116,11 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         const int n_c = prm.n_c;
         const int ax = un.cell % n_c, ay = (un.cell / n_c) % n_c, az = un.cell / (n_c * n_c);
         const uint32_t oax = sh_orig<MID>(prm)[ax];
+        {
+            // x shift of every cell column into A's frame, for the filter
+            float *sxf = (float *)(smem_raw + vo.sxf);
+            for (int c = tid; c < n_c; c += blockDim.x) sxf[c] = (float)(int)(sh_orig<MID>(prm)[c] - oax);
+        }
         if (MID) {
             cx.gx = 2.0f * (float)((long long)oax - prm.obs[0]);
             cx.gy = 2.0f * (float)((long long)sh_orig<MID>(prm)[ay] - prm.obs[1]);
@@ -1123,7 +1136,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         // directly in the first window.
         for (uint32_t w0 = 0;; w0 += CAP) {
             const uint32_t win = min((uint32_t)CAP, total - min(total, w0));
-            cx.filter_window(w0, win, ns, oax);
+            cx.filter_window(w0, win, ns);
             __syncthreads();
             uint32_t F = 0;
 #pragma unroll
