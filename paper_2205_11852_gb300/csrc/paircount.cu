@@ -47,11 +47,15 @@ constexpr int QX = 23;          // queue slots per lane, x line of sight (8-byte
 constexpr int XCAP = 96;        // per-warp list of pairs awaiting the exact recheck (global scratch)
 constexpr int WARPS = 8;        // warps per block
 constexpr int CAP = 12288;      // raw neighbour points filtered per window
-constexpr int SCR_W = CAP + 8 * 32;                 // float4 scratch entries per block window (+ per-warp rounding)
-constexpr int SCR = SCR_W + WARPS * XCAP * 8 / 16;   // + the warps' recheck lists
-// misc[]: [0] unit, [1] runs, [2] run points, [3] tile counter, [4..5] self range, [M_CNT..] window counts
+constexpr int NB = 16;          // distance buckets of the window order
+constexpr int SCR_W = CAP + 8 * 32;                 // float4 scratch per block: survivors per warp (+ rounding)
+constexpr int SCR = SCR_W + CAP + WARPS * XCAP * 8 / 16;   // + the bucket-ordered window + the recheck lists
+// misc[]: [0] unit, [1] runs, [2] run points, [3] tile counter, [4..5] self range, [M_CNT..] window counts,
+// [M_BKT..] survivors per distance bucket, [M_POS..] next free position of each bucket
 constexpr int M_CNT = 8;        // [WARPS] survivors per warp in the current window
-constexpr int M_N = 24;
+constexpr int M_BKT = 16;       // [NB]
+constexpr int M_POS = M_BKT + NB;   // [NB]
+constexpr int M_N = M_POS + NB;
 constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 static_assert(P == 4, "tile_x unrolls four b-points per lane");
 static_assert((QX + 1) % 4 == 0, "x-path flush passes read four rows and stay in the lane's column");
@@ -469,25 +473,51 @@ struct Ctx {
                 __uint_as_float(b[3]), __uint_as_float(b[4]), __uint_as_float(b[5])};
     }
 
+    // The window's box in the form the filter and the bucket order use:
+    // centre, half-widths (rounded outward, so [c - h, c + h] holds every
+    // a-point) and the bucket scale NB / dmax^2, dmax bounding the distance
+    // of any survivor from the centre.
+    struct WinBox {
+        float cx, cy, cz, hx, hy, hz, kscale;
+    };
+    __device__ __forceinline__ WinBox win_box() const
+    {
+        const Box bb = chunk_box();
+        WinBox w;
+        w.cx = 0.5f * (bb.lx + bb.hx);
+        w.cy = 0.5f * (bb.ly + bb.hy);
+        w.cz = 0.5f * (bb.lz + bb.hz);
+        w.hx = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(bb.hx, bb.lx)), __fmul_ru(1.0f / 8388608.0f, w.cx));
+        w.hy = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(bb.hy, bb.ly)), __fmul_ru(1.0f / 8388608.0f, w.cy));
+        w.hz = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(bb.hz, bb.lz)), __fmul_ru(1.0f / 8388608.0f, w.cz));
+        const float dm = sqrtf(prm.hit_max) + sqrtf(w.hx * w.hx + w.hy * w.hy + w.hz * w.hz);
+        w.kscale = (float)NB / (dm * dm);
+        return w;
+    }
+    // Distance bucket of a survivor (squared distance from the box centre in
+    // NB equal steps): points of one bucket have similar hit rates, so tiles
+    // cut from the bucket order load the lanes evenly.  Only the order
+    // depends on it, never a count.
+    __device__ __forceinline__ uint32_t bucket_of(float ex, float ey, float ez, const WinBox &w) const
+    {
+        const float ux = __fsub_rn(ex, w.cx), uy = __fsub_rn(ey, w.cy), uz = __fsub_rn(ez, w.cz);
+        const float d2c = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
+        return min(__float2uint_rz(__fmul_rn(d2c, w.kscale)), (uint32_t)(NB - 1));
+    }
+
     // Filter raw neighbour points [w0, w0 + win) of the unit's concatenated
     // runs: a point enters the window's list only if its distance to the
     // a-chunk's bounding box is below the last edge's band (with a relative
     // margin of 2^-16 over the FP32 box distance), so no pair the push test
     // could pass is lost.  Warp w filters the w-th slice of the window and
     // appends survivors (b' in A's frame, .w = b index) to its own region of
-    // the block's scratch, in order; the survivor count goes to misc.
+    // the block's scratch, in order, counting them per warp and per distance
+    // bucket in misc.
     __device__ __forceinline__ void filter_window(uint32_t w0, uint32_t win, int n_seg)
     {
-        const Box bb = chunk_box();
+        const WinBox wb = win_box();
         R = (((win + WARPS - 1) / WARPS) + 31u) & ~31u;
         const uint32_t r0 = w0 + (uint32_t)warp * R, r1 = min(r0 + R, w0 + win);
-        // box as centre and half-widths: per axis q = max(|x - c| - h, 0)
-        const float cx = 0.5f * (bb.lx + bb.hx), cy = 0.5f * (bb.ly + bb.hy), cz = 0.5f * (bb.lz + bb.hz);
-        // half-widths rounded up and the centre rounded to nearest: the box
-        // [c - h, c + h] still holds every a-point
-        const float hx = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(bb.hx, bb.lx)), __fmul_ru(1.0f / 8388608.0f, cx));
-        const float hy = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(bb.hy, bb.ly)), __fmul_ru(1.0f / 8388608.0f, cy));
-        const float hz = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(bb.hz, bb.lz)), __fmul_ru(1.0f / 8388608.0f, cz));
         const float hf = prm.hit_max * (1.0f + 1.0f / 65536.0f);
         const float *sxf = (const float *)(smem_raw + var_offsets(prm, MID).sxf);
         float4 *dst = scr + (size_t)warp * R;
@@ -514,50 +544,63 @@ struct Ctx {
                     e.y = __fadd_rn(v.y, sg.sy);
                     e.z = __fadd_rn(v.z, sg.sz);
                     e.w = __uint_as_float(i);
-                    const float qx = fmaxf(__fsub_rn(fabsf(__fsub_rn(e.x, cx)), hx), 0.0f);
-                    const float qy = fmaxf(__fsub_rn(fabsf(__fsub_rn(e.y, cy)), hy), 0.0f);
-                    const float qz = fmaxf(__fsub_rn(fabsf(__fsub_rn(e.z, cz)), hz), 0.0f);
+                    // box as centre and half-widths: per axis q = max(|x - c| - h, 0)
+                    const float qx = fmaxf(__fsub_rn(fabsf(__fsub_rn(e.x, wb.cx)), wb.hx), 0.0f);
+                    const float qy = fmaxf(__fsub_rn(fabsf(__fsub_rn(e.y, wb.cy)), wb.hy), 0.0f);
+                    const float qz = fmaxf(__fsub_rn(fabsf(__fsub_rn(e.z, wb.cz)), wb.hz), 0.0f);
                     keep = __fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmul_rn(qx, qx))) < hf;
                 }
                 const unsigned mk = __ballot_sync(0xffffffffu, keep);
-                if (keep) dst[cnt + __popc(mk & lt)] = e;
+                if (keep) {
+                    dst[cnt + __popc(mk & lt)] = e;
+                    atomicAdd(&sh_misc()[M_BKT + bucket_of(e.x, e.y, e.z, wb)], 1);
+                }
                 cnt += __popc(mk);
             }
         }
         if (lane == 0) sh_misc()[M_CNT + warp] = (int)cnt;
     }
 
-    // After the window's filter and a barrier: the region starts of the
-    // filtered order (pk[0] = 0); returns the number of survivors.
-    __device__ __forceinline__ uint32_t window_regions(uint32_t (&pk)[WARPS]) const
+    // After the filter's barrier: the start of every bucket in the window's
+    // order (warp 0), and the bucket counters cleared for the next window.
+    __device__ __forceinline__ void bucket_starts() const
     {
-        uint32_t acc = 0;
+        const int c = lane < NB ? sh_misc()[M_BKT + lane] : 0;
+        int x = c;
 #pragma unroll
-        for (int k = 0; k < WARPS; k++) {
-            pk[k] = acc;
-            acc += (uint32_t)sh_misc()[M_CNT + k];
+        for (int o = 1; o < NB; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        return acc;
+        if (lane < NB) {
+            sh_misc()[M_POS + lane] = x - c;
+            sh_misc()[M_BKT + lane] = 0;
+        }
     }
 
-    // Surviving b-point at filtered position f (< the window's count).
-    __device__ __forceinline__ float4 fetch_f(uint32_t f, const uint32_t (&pk)[WARPS]) const
+    // The bucket-ordered window list (written by scatter_window).
+    __device__ __forceinline__ float4 *lst() const { return scr + SCR_W; }
+
+    // After bucket_starts' barrier: this warp's survivors move to their
+    // buckets' places in the window list (the order within a bucket is
+    // arbitrary).
+    __device__ __forceinline__ void scatter_window() const
     {
-        uint32_t w = 0, base = 0;
-#pragma unroll
-        for (int k = 1; k < WARPS; k++)
-            if (pk[k] <= f) {
-                w = (uint32_t)k;
-                base = pk[k];
-            }
-        return scr[(size_t)w * R + (f - base)];   // written by this block: plain (coherent) load
+        const WinBox wb = win_box();
+        const uint32_t cnt = (uint32_t)sh_misc()[M_CNT + warp];
+        const float4 *src = scr + (size_t)warp * R;
+        for (uint32_t e = lane; e < cnt; e += 32) {
+            const float4 v = src[e];   // written by this warp: plain (coherent) load
+            const uint32_t pos = (uint32_t)atomicAdd(&sh_misc()[M_POS + bucket_of(v.x, v.y, v.z, wb)], 1);
+            lst()[pos] = v;
+        }
     }
 
     // ---- x line of sight ----
 
     // This warp's list of pairs set aside for the exact recheck (global
     // scratch after the block's window; written and read by this warp only).
-    __device__ __forceinline__ uint2 *xlist() const { return (uint2 *)(scr + SCR_W) + (size_t)warp * XCAP; }
+    __device__ __forceinline__ uint2 *xlist() const { return (uint2 *)(scr + SCR_W + CAP) + (size_t)warp * XCAP; }
 
     // Exact recheck of the set-aside pairs, one per lane.
     __device__ __forceinline__ void recheck_list()
@@ -640,9 +683,7 @@ struct Ctx {
             if (SELF) {
                 ib = ib0 + 32u * p;
             } else {
-                uint32_t pk[WARPS];
-                window_regions(pk);
-                ib = __float_as_uint(fetch_f(ib0 + 32u * p, pk).w);
+                ib = __float_as_uint(lst()[ib0 + 32u * p].w);   // written by this block: plain load
             }
             xlist()[n_list + __popc(am & lt)] = make_uint2(a0 + ai, ib);
         }
@@ -747,13 +788,11 @@ struct Ctx {
                 load_bx(p, i < s1, i, 0.0f, 0.0f, orig_ax, bx, by, bz);
             }
         } else {
-            uint32_t pk[WARPS];
-            window_regions(pk);
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const uint32_t f = o_base + (uint32_t)lane + 32u * p;
                 if (f < total) {
-                    const float4 e = fetch_f(f, pk);
+                    const float4 e = lst()[f];   // written by this block: plain (coherent) load
                     bx[p] = e.x;
                     by[p] = e.y;
                     bz[p] = e.z;
@@ -851,13 +890,11 @@ struct Ctx {
                 put_b(p, ok, v.x, v.y, v.z, i, bx, by, bz, hb);
             }
         } else {
-            uint32_t pk[WARPS];
-            window_regions(pk);
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 const uint32_t f = o_base + (uint32_t)lane + 32u * p;
                 const bool ok = f < total;
-                const float4 e = ok ? fetch_f(f, pk) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 e = ok ? lst()[f] : make_float4(0.f, 0.f, 0.f, 0.f);
                 put_b(p, ok, e.x, e.y, e.z, __float_as_uint(e.w), bx, by, bz, hb);
             }
         }
@@ -1062,6 +1099,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         sh_misc()[0] = persistent ? (int)atomicAdd(claim, 1u) : 0;
         sh_misc()[3] = 0;
     }
+    if (tid < NB) sh_misc()[M_BKT + tid] = 0;
     __syncthreads();
 
     for (;;) {
@@ -1138,9 +1176,13 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
             const uint32_t win = min((uint32_t)CAP, total - min(total, w0));
             cx.filter_window(w0, win, ns);
             __syncthreads();
+            if (cx.warp == 0) cx.bucket_starts();
             uint32_t F = 0;
 #pragma unroll
             for (int k = 0; k < WARPS; k++) F += (uint32_t)sh_misc()[M_CNT + k];
+            __syncthreads();
+            cx.scatter_window();
+            __syncthreads();
             const uint32_t ns_w = (w0 == 0) ? n_self : 0u;
             const uint32_t nt = ns_w + (F + TILE - 1) / TILE;
             // tiles are claimed one at a time from a shared counter (its first
