@@ -59,6 +59,8 @@ constexpr int M_N = M_POS + NB;
 constexpr int MAX_SEGS = 2 * MAX_ROWS + 2;
 static_assert(P == 4, "tile_x unrolls four b-points per lane");
 static_assert((QX + 1) % 4 == 0, "x-path flush passes read four rows and stay in the lane's column");
+static_assert((SCR * 16) % 128 == 0 && (SCR_W * 16) % 128 == 0 && (CAP * 16) % 128 == 0,
+              "per-block scratch regions start on 128-byte lines (discard_l2)");
 static_assert(UNIT_CHUNK % 32 == 0 && UNIT_CHUNK <= 128 && UNIT_CHUNK <= WARPS * 32, "a-chunk load and box");
 
 typedef unsigned __int128 u128;
@@ -276,6 +278,16 @@ __device__ __forceinline__ float2 lds64(uint32_t a)
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
     return v;
 }
+// Drop the 128-byte lines [p, p + bytes) from L2 without writing them back
+// (their data is dead; a later store writes the line afresh).  Thread t of
+// nt takes every nt-th line.  p is 128-byte aligned and the lines belong to
+// the calling block alone.
+__device__ __forceinline__ void discard_l2(const void *p, uint32_t bytes, uint32_t t, uint32_t nt)
+{
+    for (uint32_t o = t * 128u; o < bytes; o += nt * 128u)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"((const char *)p + o) : "memory");
+}
+
 // Bounding box of an a-chunk (cell-relative coordinates).
 struct Box {
     float lx, ly, lz, hx, hy, hz;
@@ -594,6 +606,9 @@ struct Ctx {
             const uint32_t pos = (uint32_t)atomicAdd(&sh_misc()[M_POS + bucket_of(v.x, v.y, v.z, wb)], 1);
             lst()[pos] = v;
         }
+        // this warp's region is spent (each lane has used what it read)
+        __syncwarp();
+        discard_l2(src, (cnt * 16u + 127u) & ~127u, (uint32_t)lane, 32u);
     }
 
     // ---- x line of sight ----
@@ -1207,6 +1222,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
             if (last && cx.n_list) cx.recheck_list();   // the list refers to this unit's histogram
             __syncthreads();   // every warp is done with this window's scratch, counter and histogram adds
             if (tid == 0) sh_misc()[3] = 0;
+            discard_l2(cx.lst(), (F * 16u + 127u) & ~127u, (uint32_t)tid, blockDim.x);   // the window list is spent
             if (last) break;
         }
         // drain the block histogram into the term's int64 histogram
