@@ -96,7 +96,9 @@ const char *tpcf_last_error(const tpcf_ctx *ctx);
  *   histogram index of (k, j) is k * n_mu + j (s-major); nbin = n_s * n_mu.
  * Positions are quantised to integer grid coordinates (2^32 per box side for
  * TPCF_PERIODIC, 2^30 per bounding-cube side for TPCF_OPEN) and every bin
- * decision is exact on those integers.  Limits: n_s <= 256, nbin <= 4096;
+ * decision is exact on those integers.  Limits: n_s <= 256, nbin <= 65536
+ * and the block histogram within shared memory (about 44 000 bins on a
+ * 227 KB device; above about 400 bins fewer blocks share an SM);
  * periodic boxes need s_max <= box_L / 3 and the x line of sight.
  */
 typedef struct {
@@ -140,7 +142,14 @@ typedef struct {
  * Every mock must have the same M when TPCF_DR or TPCF_RR is requested.
  * `terms` is a mask of TPCF_DD | TPCF_DR | TPCF_RR; unrequested outputs may
  * be NULL.  `mode` selects TPCF_BATCHED or TPCF_PER_LAUNCH; both give
- * identical counts.  Returns TPCF_OK or a negative error (nothing enqueued).
+ * identical counts.  Returns TPCF_OK or a negative error (nothing enqueued);
+ * TPCF_ERR_RANGE when the binning cannot be counted exactly on the integer
+ * grid: a squared separation beyond 64 bits, a periodic s_max above L/3, or
+ * (n_mu > 1) n_mu^2 D2_max |l|^2_max >= 2^126 for the exact mu test, where
+ * |l|^2_max = 1 on the x line of sight and, on the midpoint line of sight,
+ * the largest |u_a + u_b - 2 u_obs|^2 over the cube (open grid units), or a
+ * block histogram (4 nbin bytes) that does not fit in the device's shared
+ * memory beside the queues.
  */
 int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *binning,
                unsigned terms, int64_t *dd, int64_t *dr, int64_t *rr, int mode, void *stream);

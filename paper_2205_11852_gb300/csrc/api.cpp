@@ -110,7 +110,7 @@ int validate_binning(tpcf_ctx *ctx, const tpcf_binning *b)
     if (!(b->box_L > 0) || !std::isfinite(b->box_L)) return fail(ctx, TPCF_ERR_ARG, "box_L must be positive");
     if (b->n_s < 1 || b->n_s > MAX_NS) return fail(ctx, TPCF_ERR_ARG, "n_s must be in [1, 256]");
     if (b->n_mu < 1 || (long long)b->n_s * b->n_mu > MAX_NBIN)
-        return fail(ctx, TPCF_ERR_ARG, "n_mu must be >= 1 with n_s * n_mu <= 4096");
+        return fail(ctx, TPCF_ERR_ARG, "n_mu must be >= 1 with n_s * n_mu <= 65536");
     if (!b->s_edges) return fail(ctx, TPCF_ERR_ARG, "s_edges is NULL");
     if (!(b->s_edges[0] >= 0)) return fail(ctx, TPCF_ERR_ARG, "s edges must be >= 0");
     for (int k = 0; k < b->n_s; k++)

@@ -231,6 +231,18 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
 
     // launch shape (host queries, outside any capture)
     S.smem = paircount_smem_bytes(prm, 8);
+    {
+        // the block histogram (4 nbin bytes) sits in shared memory beside the queues
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) != cudaSuccess) {
+            cudaGetLastError();
+            optin = 0;
+        }
+        if (optin > 0 && S.smem > optin)
+            return fail(ctx, TPCF_ERR_RANGE, "the binning needs " + std::to_string(S.smem) +
+                                                 " bytes of shared memory per block; the device allows " +
+                                                 std::to_string(optin));
+    }
     cudaError_t e = paircount_set_attrs(prm, S.smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "paircount_set_attrs");
     S.blocks = ctx->n_sm * paircount_max_blocks_per_sm(prm, 8, S.smem);

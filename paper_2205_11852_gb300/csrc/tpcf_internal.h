@@ -9,7 +9,7 @@
 namespace tpcf {
 
 constexpr int MAX_NS = 256;          // s bins
-constexpr int MAX_NBIN = 4096;       // s bins x mu bins
+constexpr int MAX_NBIN = 65536;      // s bins x mu bins (the block histogram must also fit in shared memory)
 constexpr int MAX_NC = 1024;         // mesh cells per axis
 constexpr int MAX_ROWS = 81;         // (2K+1)^2 neighbour rows, K <= 4
 constexpr int MAX_TABLE = 16384;     // s-bin lookup slots

@@ -160,6 +160,46 @@ def test_counts_open_plane_parallel_slab(tp, ctx):
     _check_counts(ctx, tp, mocks, tb, ob)
 
 
+@pytest.mark.parametrize("los", ["x", "midpoint"])
+def test_counts_paper_binning_200x100(tp, ctx, los):
+    """The paper's own binning (Sect. 4.3: bins of 1 Mpc/h on [0, 200], 100 mu bins, 20 000 bins, a block
+    histogram of 80 KB) in the paper's slab (1500 x 1500 x 300, Sect. 4.1) with 5000 points per catalogue, x
+    line of sight as in the paper; with the midpoint line of sight the binning is beyond the exact mu test's
+    128-bit range and must be refused."""
+    dims = np.array([1500.0, 1500.0, 300.0])
+    d = synth.uniform_slab(synth.rng_for(35, 0, 0), 5000, dims)
+    r = [synth.uniform_slab(synth.rng_for(35, 0, 1 + i), 5000, dims) for i in range(2)]
+    edges = np.linspace(0.0, 200.0, 201)
+    if los == "midpoint":
+        # n_mu^2 D2 |l|^2 passes 2^128 in a 1500 Mpc/h cube at 2^30 grid units: the exact mu test cannot be
+        # formed, and the library refuses the binning as the oracle does
+        with pytest.raises(ValueError):
+            oracle.Binning(edges, 100, oracle.OPEN, 1500.0, los=oracle.LOS_MIDPOINT, observer=(0, 0, 0))
+        tb = tp.make_binning(edges, 100, tp.TPCF_OPEN, 1500.0, los=tp.TPCF_LOS_MIDPOINT, observer=(0, 0, 0))
+        with pytest.raises(tp.TpcfError) as e:
+            ctx.tpcf_count(_mocks_to_device([synth.Mock(d, r)]), tb)
+        assert e.value.code == tp.TPCF_ERR_RANGE
+        return
+    tb = tp.make_binning(edges, 100, tp.TPCF_OPEN, 1500.0, los=tp.TPCF_LOS_X)
+    ob = oracle.Binning(edges, 100, oracle.OPEN, 1500.0, los=oracle.LOS_X)
+    out = _check_counts(ctx, tp, [synth.Mock(d, r)], tb, ob)
+    assert out["dd"].shape[-1] == 20000 and int(out["dd"].sum()) > 100000
+
+
+def test_binning_beyond_shared_memory_refused(tp, ctx):
+    """256 s x 256 mu bins: a 256 KB block histogram cannot sit in shared memory, so the count is refused
+    with TPCF_ERR_RANGE (nothing is enqueued) and the context stays usable."""
+    d = synth.uniform_slab(synth.rng_for(36, 0, 0), 500, (1500.0, 1500.0, 300.0))
+    mk = _mocks_to_device([synth.Mock(d, [d[:250], d[250:]])])
+    tb = tp.make_binning(np.linspace(0.0, 200.0, 257), 256, tp.TPCF_OPEN, 1500.0, los=tp.TPCF_LOS_X)
+    with pytest.raises(tp.TpcfError) as e:
+        ctx.tpcf_count(mk, tb)
+    assert e.value.code == tp.TPCF_ERR_RANGE
+    ok = tp.make_binning(np.linspace(0.0, 200.0, 21), 4, tp.TPCF_OPEN, 1500.0, los=tp.TPCF_LOS_X)
+    ctx.tpcf_count(mk, ok)
+    assert ctx.tpcf_sync() == tp.TPCF_OK
+
+
 def test_counts_golden_edge_pairs(tp, ctx):
     g = json.load(open(os.path.join(GOLDEN, "edge_pairs.json")))
     for section in ("periodic", "open_midpoint"):
