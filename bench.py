@@ -575,6 +575,12 @@ def main():
     res_host = torch.empty((nbin, nbin), dtype=torch.float64).pin_memory()
     pos2 = torch.empty_like(pos)
     mocks2 = mock_views(pos2, layout)
+    # untimed warm-up steps of this path too: new input pointers mean a new
+    # launch plan and graph, built once
+    for _ in range(args.warmup):
+        pos2.copy_(pinned, non_blocking=True)
+        c = step(mocks_in=mocks2)
+        res_host.copy_(c["C_lc"], non_blocking=True)
     barrier()
     q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     q0.record(stream)
