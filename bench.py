@@ -568,25 +568,23 @@ def main():
     ms_pl = p0.elapsed_time(p1) / n_pl
     per_launch = mocks_total / (ms_pl * 1e-3)
 
-    # end to end through the public API: positions from pinned host memory,
-    # C^LC read back, every step
+    # end to end through the public API: the positions are passed as pinned
+    # HOST arrays (the library copies them in on the stream, TPCF_HOST_INPUT)
+    # and C^LC is read back, every step
     h2d = pinned.numel() * pinned.element_size()
     d2h = nbin * nbin * 8
     res_host = torch.empty((nbin, nbin), dtype=torch.float64).pin_memory()
-    pos2 = torch.empty_like(pos)
-    mocks2 = mock_views(pos2, layout)
-    # untimed warm-up steps of this path too: new input pointers mean a new
-    # launch plan and graph, built once
+    mocks_host = mock_views(pinned, layout)
+    # untimed warm-up steps of this path too: its staged inputs sit at new
+    # device addresses, so its first call builds a launch plan and graph
     for _ in range(args.warmup):
-        pos2.copy_(pinned, non_blocking=True)
-        c = step(mocks_in=mocks2)
+        c = step(mocks_in=mocks_host)
         res_host.copy_(c["C_lc"], non_blocking=True)
     barrier()
     q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     q0.record(stream)
     for _ in range(args.steps):
-        pos2.copy_(pinned, non_blocking=True)
-        c = step(mocks_in=mocks2)
+        c = step(mocks_in=mocks_host)
         res_host.copy_(c["C_lc"], non_blocking=True)
     q1.record(stream)
     barrier()

@@ -57,6 +57,7 @@ extern "C" {
 
 #define TPCF_BATCHED     0        /* all mocks and terms in one persistent launch (default) */
 #define TPCF_PER_LAUNCH  1        /* one kernel launch per (mock, term, subset): baseline */
+#define TPCF_HOST_INPUT  2        /* OR into mode: the mocks' position arrays are host memory */
 
 #define TPCF_FP64    0            /* covariance arithmetic entirely in float64 */
 #define TPCF_TF32X3  1            /* Gram products on tensor cores, 3-term TF32 split, FP32 accumulate */
@@ -142,7 +143,12 @@ typedef struct {
  * Every mock must have the same M when TPCF_DR or TPCF_RR is requested.
  * `terms` is a mask of TPCF_DD | TPCF_DR | TPCF_RR; unrequested outputs may
  * be NULL.  `mode` selects TPCF_BATCHED or TPCF_PER_LAUNCH; both give
- * identical counts.  Returns TPCF_OK or a negative error (nothing enqueued);
+ * identical counts.  With TPCF_HOST_INPUT or-ed into `mode`, data_xyz,
+ * data_u32, rand_xyz and rand_u32 are HOST arrays (same layouts): the call
+ * copies them into the context's device workspace on `stream` before
+ * counting (asynchronously from pinned memory, so they must stay unchanged
+ * until the stream has passed the call; pageable memory is copied before the
+ * call returns).  The outputs stay device memory.  Returns TPCF_OK or a negative error (nothing enqueued);
  * TPCF_ERR_RANGE when the binning cannot be counted exactly on the integer
  * grid: a squared separation beyond 64 bits, a periodic s_max above L/3, or
  * (n_mu > 1) n_mu^2 D2_max |l|^2_max >= 2^126 for the exact mu test, where

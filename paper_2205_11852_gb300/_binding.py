@@ -28,7 +28,7 @@ TPCF_ERR_STATE = -6
 TPCF_PERIODIC, TPCF_OPEN = 0, 1
 TPCF_LOS_X, TPCF_LOS_MIDPOINT = 0, 1
 TPCF_DD, TPCF_DR, TPCF_RR = 1, 2, 4
-TPCF_BATCHED, TPCF_PER_LAUNCH = 0, 1
+TPCF_BATCHED, TPCF_PER_LAUNCH, TPCF_HOST_INPUT = 0, 1, 2
 TPCF_FP64, TPCF_TF32X3, TPCF_BF16X3 = 0, 1, 2
 TPCF_OPT_GRAPHS, TPCF_OPT_AUTOTUNE = 1, 2
 
@@ -213,8 +213,11 @@ class Context:
         """Pair counts of every mock.
 
         mocks: sequence of dicts with keys
-          'data' (float64 CUDA [n_d,3]) or 'data_u32' (int32/uint32 CUDA [3,n_d]),
-          'randoms' (float64 CUDA [n_r,3]) or 'randoms_u32' ([3,n_r]), 'offsets' (M+1 ints).
+          'data' (float64 [n_d,3]) or 'data_u32' (int32/uint32 [3,n_d]),
+          'randoms' (float64 [n_r,3]) or 'randoms_u32' ([3,n_r]), 'offsets' (M+1 ints).
+        The catalogues are either all CUDA tensors or all CPU tensors (pinned
+        for an asynchronous copy): CPU tensors are passed as host arrays with
+        TPCF_HOST_INPUT, and the library copies them in on the stream.
         Returns dict of int64 CUDA tensors dd [n_mock,nbin], dr/rr [n_mock,M,nbin].
         """
         n_mock = len(mocks)
@@ -223,6 +226,11 @@ class Context:
         keep = []
         M = 0
         dev = torch.device("cuda", self.device)
+        cats = [t for m in mocks for t in (m.get("data"), m.get("data_u32"), m.get("randoms"), m.get("randoms_u32"))
+                if t is not None]
+        host = bool(cats) and not any(t.is_cuda for t in cats)
+        if host:
+            mode = int(mode) | TPCF_HOST_INPUT
         for i, m in enumerate(mocks):
             d = m.get("data")
             du = m.get("data_u32")
@@ -233,8 +241,8 @@ class Context:
             o = (ctypes.c_int64 * len(offs))(*[int(x) for x in offs])
             keep.append(o)
             for t in (d, du, r, ru):
-                if t is not None and (not t.is_cuda or not t.is_contiguous()):
-                    raise ValueError("catalogues must be contiguous CUDA tensors")
+                if t is not None and (t.is_cuda == host or not t.is_contiguous()):
+                    raise ValueError("catalogues must be contiguous tensors, all on the GPU or all on the host")
             n_d = d.shape[0] if d is not None else (du.shape[1] if du is not None else 0)
             arr[i] = tpcf_mock(_ptr(d), _ptr(du), n_d, _ptr(r), _ptr(ru),
                                ctypes.cast(o, ctypes.POINTER(ctypes.c_int64)), M)

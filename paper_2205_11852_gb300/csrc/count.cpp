@@ -542,12 +542,110 @@ void release_graphs(tpcf_ctx *ctx)
 }  // namespace detail
 }  // namespace tpcf
 
+namespace {
+
+// TPCF_HOST_INPUT: the mocks' position arrays are host memory.  They are
+// checked, then copied into the context's "hostin" workspace on the call's
+// stream (one copy per array), and dm receives the mocks with the staged
+// device pointers.  Nothing is enqueued when a check fails.
+int stage_host_mocks(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, unsigned terms, cudaStream_t s,
+                     std::vector<tpcf_mock> &dm)
+{
+    if (n_mock < 0 || (n_mock > 0 && !mocks)) return fail(ctx, TPCF_ERR_ARG, "mocks is NULL");
+    const bool need_d = terms & (TPCF_DD | TPCF_DR);
+    const bool need_r = terms & (TPCF_DR | TPCF_RR);
+    auto al256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t bytes = 0;
+    for (int m = 0; m < n_mock; m++) {
+        const tpcf_mock &mk = mocks[m];
+        if (need_d) {
+            if (mk.n_d < 0) return fail(ctx, TPCF_ERR_ARG, "n_d < 0");
+            if (mk.n_d > 0 && !mk.data_xyz == !mk.data_u32)
+                return fail(ctx, TPCF_ERR_ARG, "give exactly one of data_xyz / data_u32");
+            if (mk.n_d > 0) bytes += al256((size_t)mk.n_d * (mk.data_xyz ? 24 : 12));
+        }
+        if (need_r) {
+            if (mk.M < 1 || !mk.rand_offsets || mk.rand_offsets[0] != 0)
+                return fail(ctx, TPCF_ERR_ARG, "M >= 1 and rand_offsets starting at 0 are required");
+            for (int i = 0; i < mk.M; i++)
+                if (mk.rand_offsets[i + 1] < mk.rand_offsets[i])
+                    return fail(ctx, TPCF_ERR_ARG, "rand_offsets must be non-decreasing");
+            const int64_t nr = mk.rand_offsets[mk.M];
+            if (nr > 0 && !mk.rand_xyz == !mk.rand_u32)
+                return fail(ctx, TPCF_ERR_ARG, "give exactly one of rand_xyz / rand_u32");
+            if (nr > 0) bytes += al256((size_t)nr * (mk.rand_xyz ? 24 : 12));
+        }
+    }
+    dm.assign(mocks, mocks + n_mock);
+    if (bytes == 0) return TPCF_OK;
+    // every array to stage, in order; arrays that follow one another in host
+    // memory are copied as one run (one copy for a caller's single buffer)
+    struct Item {
+        const char *src;
+        size_t bytes, align;
+        const void **field;   // the staged mock's pointer to redirect
+    };
+    std::vector<Item> items;
+    for (int m = 0; m < n_mock; m++) {
+        tpcf_mock &mk = dm[m];
+        if (need_d && mk.n_d > 0) {
+            if (mk.data_xyz) items.push_back({(const char *)mk.data_xyz, (size_t)mk.n_d * 24, 8, (const void **)&mk.data_xyz});
+            else items.push_back({(const char *)mk.data_u32, (size_t)mk.n_d * 12, 4, (const void **)&mk.data_u32});
+        }
+        if (need_r && mk.rand_offsets[mk.M] > 0) {
+            const size_t nr = (size_t)mk.rand_offsets[mk.M];
+            if (mk.rand_xyz) items.push_back({(const char *)mk.rand_xyz, nr * 24, 8, (const void **)&mk.rand_xyz});
+            else items.push_back({(const char *)mk.rand_u32, nr * 12, 4, (const void **)&mk.rand_u32});
+        }
+    }
+    // device layout: run r starts on a 256-byte boundary; an array inside a
+    // run keeps its host offset from the run's start
+    std::vector<size_t> dev_off(items.size());
+    std::vector<size_t> run_first;   // index of each run's first item
+    size_t cursor = 0, run_dev = 0;
+    const char *run_src = nullptr, *run_end = nullptr;
+    for (size_t k = 0; k < items.size(); k++) {
+        const Item &it = items[k];
+        const bool joins = run_src && it.src == run_end && (run_dev + (size_t)(it.src - run_src)) % it.align == 0;
+        if (!joins) {
+            run_dev = al256(cursor);
+            run_src = it.src;
+            run_first.push_back(k);
+        }
+        dev_off[k] = run_dev + (size_t)(it.src - run_src);
+        run_end = it.src + it.bytes;
+        cursor = dev_off[k] + it.bytes;
+    }
+    void *buf = nullptr;
+    int rc;
+    if ((rc = ensure(ctx, "hostin", cursor, &buf))) return rc;
+    char *dev = (char *)buf;
+    for (size_t r = 0; r < run_first.size(); r++) {
+        const size_t k0 = run_first[r], k1 = (r + 1 < run_first.size()) ? run_first[r + 1] : items.size();
+        const Item &a = items[k0], &b = items[k1 - 1];
+        CK(cudaMemcpyAsync(dev + dev_off[k0], a.src, (size_t)(b.src + b.bytes - a.src), cudaMemcpyHostToDevice, s));
+    }
+    for (size_t k = 0; k < items.size(); k++) *items[k].field = dev + dev_off[k];
+    return TPCF_OK;
+}
+
+}  // namespace
+
 extern "C" int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *binning,
                           unsigned terms, int64_t *dd, int64_t *dr, int64_t *rr, int mode, void *stream)
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    std::vector<tpcf_mock> staged;
+    if (mode & TPCF_HOST_INPUT) {
+        mode &= ~TPCF_HOST_INPUT;
+        if (mode != TPCF_BATCHED && mode != TPCF_PER_LAUNCH) return fail(ctx, TPCF_ERR_ARG, "bad mode");
+        if ((rc = validate_binning(ctx, binning))) return rc;
+        if (terms == 0 || (terms & ~7u)) return fail(ctx, TPCF_ERR_ARG, "terms must be a non-empty mask of DD|DR|RR");
+        if ((rc = stage_host_mocks(ctx, mocks, n_mock, terms, s, staged))) return rc;
+        mocks = staged.data();
+    }
     // shape-level validation first, so that tuning never sees a bad call
     if ((rc = validate_binning(ctx, binning))) return rc;
     Tuned cfg;

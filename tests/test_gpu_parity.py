@@ -257,6 +257,36 @@ def test_u32_input_matches_float_input(tp, ctx):
         assert torch.equal(f[k], u[k])
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_counts_from_host_arrays(tp, ctx, mode):
+    """Host catalogues (TPCF_HOST_INPUT: pinned and pageable, float64 and pre-quantised) give the counts of
+    the same catalogues on the device, bit for bit; mixing host and device catalogues is refused."""
+    L = 400.0
+    mks = [synth.SMALL.make_mock(7 + m, n_d=1200 + 300 * m, M=2) for m in range(2)]
+    tb, _ = _periodic(L, np.linspace(0, 100.0, 11), 4)
+    ref = ctx.tpcf_count(_mocks_to_device(mks), tb, mode=mode)
+    host = []
+    for m, mk in enumerate(mks):
+        h = {"data": torch.from_numpy(np.ascontiguousarray(mk.data)),
+             "randoms": torch.from_numpy(np.ascontiguousarray(np.concatenate(mk.randoms))),
+             "offsets": [0] + list(np.cumsum([len(r) for r in mk.randoms]))}
+        if m == 0:
+            h = {k: (v.pin_memory() if torch.is_tensor(v) else v) for k, v in h.items()}
+        host.append(h)
+    got = ctx.tpcf_count(host, tb, mode=mode)
+    qd = oracle.quantize(mks[1].data, oracle.PERIODIC, L)
+    qr = np.concatenate([oracle.quantize(r, oracle.PERIODIC, L) for r in mks[1].randoms], axis=1)
+    hu = [host[0], {"data_u32": torch.from_numpy(qd.view(np.int32).copy()).pin_memory(),
+                    "randoms_u32": torch.from_numpy(qr.view(np.int32).copy()), "offsets": host[1]["offsets"]}]
+    got_u = ctx.tpcf_count(hu, tb, mode=mode)
+    assert ctx.tpcf_sync() == tp.TPCF_OK
+    for k in ("dd", "dr", "rr"):
+        assert torch.equal(got[k], ref[k]), k
+        assert torch.equal(got_u[k], ref[k]), k
+    with pytest.raises(ValueError):
+        ctx.tpcf_count([_mocks_to_device(mks)[0], host[1]], tb, mode=mode)
+
+
 def test_terms_subset_and_output_untouched(tp, ctx):
     L = 300.0
     mk = synth.SMALL.make_mock(6, n_d=800, M=2)
