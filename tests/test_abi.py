@@ -82,3 +82,14 @@ def test_multipole_matrix_matches_oracle(tp):
     for bad in ((1,), (0, 3), (-2,), (66,)):
         with pytest.raises(tp.TpcfError):
             tp.tpcf_multipole_matrix(2, 4, bad)
+
+
+def test_binding_constants_match_header(tp):
+    """Every TPCF_ constant the binding exports has the value include/tpcf.h defines."""
+    src = open(os.path.join(ROOT, "include", "tpcf.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"^#define\s+(TPCF_\w+)\s+(-?\d+)", src, flags=re.M)}
+    names = [n for n in dir(tp) if n.startswith("TPCF_")]
+    assert {"TPCF_HOST_INPUT", "TPCF_BATCHED", "TPCF_PER_LAUNCH", "TPCF_ERR_RANGE"} <= set(names)
+    for n in names:
+        assert n in defs, n
+        assert getattr(tp, n) == defs[n], n
