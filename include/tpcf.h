@@ -358,6 +358,7 @@ typedef struct {
     int     timed_calls;      /* tpcf_count calls accumulated in paircount_ms */
     int     unit_chunk;       /* a-points per work unit, chosen by the autotuner */
     int     graph_replay;     /* 1: the batched launch was a replay of a captured CUDA graph */
+    int     pair_kernel;      /* TPCF_KERNEL_DIRECT or TPCF_KERNEL_GENERAL: the pair counter that ran */
 } tpcf_count_info;
 
 int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info);
@@ -384,11 +385,22 @@ int tpcf_set_cell_subdiv(tpcf_ctx *ctx, int subdiv);
  *   TPCF_OPT_AUTOTUNE -- on the first batched call of a new workload shape,
  *                        time candidate mesh subdivisions and work-unit sizes on
  *                        a few of the mocks and keep the fastest (cached per
- *                        context).  A pinned subdivision disables it.
+ *                        context and device).  A pinned subdivision disables it.
+ *   TPCF_OPT_KERNEL   -- which pair counter runs: TPCF_KERNEL_AUTO (the direct
+ *                        counter wherever the binning suits it -- s bins linear
+ *                        from 0 with the x line of sight or s only, and a
+ *                        histogram that fits shared memory with its copies --
+ *                        else the general one) or TPCF_KERNEL_GENERAL (always
+ *                        the general counter; the default).  Both give
+ *                        identical counts.
  * Returns TPCF_OK or TPCF_ERR_ARG.
  */
 #define TPCF_OPT_GRAPHS    1
 #define TPCF_OPT_AUTOTUNE  2
+#define TPCF_OPT_KERNEL    3
+#define TPCF_KERNEL_AUTO     0
+#define TPCF_KERNEL_DIRECT   1
+#define TPCF_KERNEL_GENERAL  2
 int tpcf_set_option(tpcf_ctx *ctx, int option, int value);
 
 #ifdef __cplusplus

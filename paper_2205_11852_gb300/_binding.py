@@ -30,7 +30,8 @@ TPCF_LOS_X, TPCF_LOS_MIDPOINT = 0, 1
 TPCF_DD, TPCF_DR, TPCF_RR = 1, 2, 4
 TPCF_BATCHED, TPCF_PER_LAUNCH, TPCF_HOST_INPUT = 0, 1, 2
 TPCF_FP64, TPCF_TF32X3, TPCF_BF16X3 = 0, 1, 2
-TPCF_OPT_GRAPHS, TPCF_OPT_AUTOTUNE = 1, 2
+TPCF_OPT_GRAPHS, TPCF_OPT_AUTOTUNE, TPCF_OPT_KERNEL = 1, 2, 3
+TPCF_KERNEL_AUTO, TPCF_KERNEL_DIRECT, TPCF_KERNEL_GENERAL = 0, 1, 2
 
 EXPORTED = ("tpcf_create", "tpcf_destroy", "tpcf_sync", "tpcf_last_error", "tpcf_count", "tpcf_ls",
             "tpcf_lc_cov", "tpcf_last_count_info", "tpcf_set_timing", "tpcf_set_cell_subdiv", "tpcf_thresholds",
@@ -42,6 +43,90 @@ class TpcfError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"tpcf error {code}: {msg}")
         self.code = code
+
+
+class TpcfArgError(TpcfError, ValueError):
+    """An argument refused by the binding before anything reaches the library or the GPU.
+
+    The C ABI receives raw pointers and cannot know buffer sizes, so the
+    binding checks every tensor's dtype, shape, contiguity and device first."""
+
+    def __init__(self, msg: str):
+        super().__init__(TPCF_ERR_ARG, msg)
+
+
+_U32 = (torch.int32, getattr(torch, "uint32", torch.int32))
+
+
+def _need(t, name, dtypes, shape, device=None, optional=False):
+    """Check one tensor argument: dtype in `dtypes`, exact `shape` (None entries match any size),
+    contiguous, on `device` when given."""
+    if t is None:
+        if optional:
+            return
+        raise TpcfArgError(f"{name} is required")
+    if not isinstance(t, torch.Tensor):
+        raise TpcfArgError(f"{name} must be a torch tensor")
+    if t.dtype not in dtypes:
+        raise TpcfArgError(f"{name} must have dtype {' or '.join(str(d) for d in dtypes)}, got {t.dtype}")
+    if t.dim() != len(shape) or any(w is not None and int(g) != int(w) for g, w in zip(t.shape, shape)):
+        want = "[" + ", ".join("*" if w is None else str(w) for w in shape) + "]"
+        raise TpcfArgError(f"{name} must have shape {want}, got {list(t.shape)}")
+    if not t.is_contiguous():
+        raise TpcfArgError(f"{name} must be contiguous")
+    if device is not None and t.device != device:
+        raise TpcfArgError(f"{name} is on {t.device}, expected {device}")
+
+
+def validate_count_args(mocks, nbin, device, out=None):
+    """Checks tpcf_count's mocks (and `out`) before the call; returns (host, M).
+
+    Each mock: exactly one of 'data' (float64 [n_d, 3]) / 'data_u32' (32-bit [3, n_d]), and for the
+    randoms one of 'randoms' (float64 [n_r, 3]) / 'randoms_u32' (32-bit [3, n_r]) with 'offsets'
+    (M + 1 integers, offsets[0] == 0, non-decreasing, offsets[-1] == n_r).  The catalogues are all
+    on `device` or all on the host; every mock has the same M."""
+    cats = [t for m in mocks for t in (m.get("data"), m.get("data_u32"), m.get("randoms"), m.get("randoms_u32"))
+            if t is not None]
+    for t in cats:
+        if not isinstance(t, torch.Tensor):
+            raise TpcfArgError("catalogues must be torch tensors")
+    host = bool(cats) and not any(t.is_cuda for t in cats)
+    where = torch.device("cpu") if host else device
+    M = None
+    for i, m in enumerate(mocks):
+        d, du, r, ru = m.get("data"), m.get("data_u32"), m.get("randoms"), m.get("randoms_u32")
+        if d is not None and du is not None:
+            raise TpcfArgError(f"mock {i}: give one of 'data' and 'data_u32'")
+        if r is not None and ru is not None:
+            raise TpcfArgError(f"mock {i}: give one of 'randoms' and 'randoms_u32'")
+        if d is not None:
+            _need(d, f"mock {i} data", (torch.float64,), (None, 3), where)
+        if du is not None:
+            _need(du, f"mock {i} data_u32", _U32, (3, None), where)
+        n_r = 0
+        if r is not None:
+            _need(r, f"mock {i} randoms", (torch.float64,), (None, 3), where)
+            n_r = int(r.shape[0])
+        if ru is not None:
+            _need(ru, f"mock {i} randoms_u32", _U32, (3, None), where)
+            n_r = int(ru.shape[1])
+        offs = [int(x) for x in m.get("offsets", [0])]
+        if len(offs) < 1 or offs[0] != 0:
+            raise TpcfArgError(f"mock {i}: offsets must start at 0")
+        if any(b < a for a, b in zip(offs, offs[1:])):
+            raise TpcfArgError(f"mock {i}: offsets must be non-decreasing")
+        if offs[-1] != n_r:
+            raise TpcfArgError(f"mock {i}: offsets[-1] = {offs[-1]} but the randoms hold {n_r} points")
+        if M is not None and len(offs) - 1 != M:
+            raise TpcfArgError(f"mock {i}: every mock needs the same number of random subsets")
+        M = len(offs) - 1
+    M = M or 0
+    if out is not None:
+        n_mock = len(mocks)
+        _need(out.get("dd"), "out['dd']", (torch.int64,), (n_mock, nbin), device, optional=True)
+        for k in ("dr", "rr"):
+            _need(out.get(k), f"out['{k}']", (torch.int64,), (n_mock, max(M, 1), nbin), device, optional=True)
+    return host, M
 
 
 class tpcf_binning(ctypes.Structure):
@@ -61,7 +146,7 @@ class tpcf_count_info(ctypes.Structure):
                 ("n_units", ctypes.c_int64), ("paircount_ms", ctypes.c_double),
                 ("n_paircount_launches", ctypes.c_int), ("cell_subdiv", ctypes.c_int),
                 ("cells_per_axis", ctypes.c_int), ("n_kernels", ctypes.c_int), ("timed_calls", ctypes.c_int),
-                ("unit_chunk", ctypes.c_int), ("graph_replay", ctypes.c_int)]
+                ("unit_chunk", ctypes.c_int), ("graph_replay", ctypes.c_int), ("pair_kernel", ctypes.c_int)]
 
 
 def load_library() -> ctypes.CDLL:
@@ -224,11 +309,8 @@ class Context:
         nbin = binning.n_s * binning.n_mu
         arr = (tpcf_mock * max(1, n_mock))()
         keep = []
-        M = 0
         dev = torch.device("cuda", self.device)
-        cats = [t for m in mocks for t in (m.get("data"), m.get("data_u32"), m.get("randoms"), m.get("randoms_u32"))
-                if t is not None]
-        host = bool(cats) and not any(t.is_cuda for t in cats)
+        host, M = validate_count_args(mocks, nbin, dev, out)
         if host:
             mode = int(mode) | TPCF_HOST_INPUT
         for i, m in enumerate(mocks):
@@ -237,12 +319,8 @@ class Context:
             r = m.get("randoms")
             ru = m.get("randoms_u32")
             offs = m.get("offsets", [0])
-            M = len(offs) - 1
             o = (ctypes.c_int64 * len(offs))(*[int(x) for x in offs])
             keep.append(o)
-            for t in (d, du, r, ru):
-                if t is not None and (t.is_cuda == host or not t.is_contiguous()):
-                    raise ValueError("catalogues must be contiguous tensors, all on the GPU or all on the host")
             n_d = d.shape[0] if d is not None else (du.shape[1] if du is not None else 0)
             arr[i] = tpcf_mock(_ptr(d), _ptr(du), n_d, _ptr(r), _ptr(ru),
                                ctypes.cast(o, ctypes.POINTER(ctypes.c_int64)), M)
@@ -258,8 +336,17 @@ class Context:
 
     def tpcf_ls(self, dd, dr, rr, n_d, n_r, sel, stream=None, out=None):
         """Split Landy-Szalay xi [n_mock, nbin] (float64 CUDA) over random subsets `sel`."""
+        dev = torch.device("cuda", self.device)
+        _need(dd, "dd", (torch.int64,), (None, None), dev)
         n_mock, nbin = dd.shape
+        _need(dr, "dr", (torch.int64,), (n_mock, None, nbin), dev)
         M = dr.shape[1]
+        _need(rr, "rr", (torch.int64,), (n_mock, M, nbin), dev)
+        _need(out, "out", (torch.float64,), (n_mock, nbin), dev, optional=True)
+        if len(n_d) != n_mock or len(n_r) != n_mock or any(len(row) != M for row in n_r):
+            raise TpcfArgError("n_d must have n_mock entries and n_r n_mock rows of M entries")
+        if not sel or any(not 0 <= int(x) < M for x in sel):
+            raise TpcfArgError("sel must name subsets in [0, M)")
         nd = (ctypes.c_int64 * max(1, n_mock))(*[int(x) for x in n_d])
         flat = [int(x) for row in n_r for x in row]
         nr = (ctypes.c_int64 * max(1, len(flat)))(*flat)
@@ -274,8 +361,11 @@ class Context:
     def tpcf_lc_cov(self, xi_a1, xi_a2, xi_b, M_a=1, M=math.inf, precision=TPCF_FP64, stream=None,
                     want_parts=True):
         """LC covariance (Eqs. R1R2, LCdef); returns dict of float64 CUDA [nbin, nbin] tensors."""
+        dev = torch.device("cuda", self.device)
+        _need(xi_a1, "xi_a1", (torch.float64,), (None, None), dev)
         n_mock, nbin = xi_a1.shape
-        dev = xi_a1.device
+        _need(xi_a2, "xi_a2", (torch.float64,), (n_mock, nbin), dev)
+        _need(xi_b, "xi_b", (torch.float64,), (n_mock, nbin), dev)
         mk = lambda: torch.empty((nbin, nbin), dtype=torch.float64, device=dev)
         out = {"C_lc": mk()}
         if want_parts:
@@ -288,6 +378,11 @@ class Context:
 
     def tpcf_rebin_counts(self, counts, n_s, n_mu, f_s, f_mu, stream=None):
         """Counts [..., n_s * n_mu] (int64 CUDA) summed into [..., (n_s/f_s) * (n_mu/f_mu)] wider bins."""
+        if not isinstance(counts, torch.Tensor) or counts.dim() < 1:
+            raise TpcfArgError("counts must be an int64 tensor [..., n_s * n_mu]")
+        _need(counts, "counts", (torch.int64,), (None,) * counts.dim(), torch.device("cuda", self.device))
+        if counts.shape[-1] != int(n_s) * int(n_mu):
+            raise TpcfArgError(f"counts must end in n_s * n_mu = {int(n_s) * int(n_mu)} bins")
         lead = tuple(counts.shape[:-1])
         rows = 1
         for d in lead:
@@ -300,7 +395,10 @@ class Context:
 
     def tpcf_project(self, P, xi, stream=None):
         """xi [n_mock, nbin] mapped by P [n_out, nbin] (float64 CUDA): returns [n_mock, n_out]."""
+        dev = torch.device("cuda", self.device)
+        _need(P, "P", (torch.float64,), (None, None), dev)
         n_out, nbin = P.shape
+        _need(xi, "xi", (torch.float64,), (None, nbin), dev)
         n_mock = xi.shape[0]
         y = torch.empty((n_mock, n_out), dtype=torch.float64, device=xi.device)
         self._check(self._lib.tpcf_project(self.handle, _ptr(P), n_out, nbin, _ptr(xi), n_mock, _ptr(y),
@@ -309,7 +407,11 @@ class Context:
 
     def tpcf_covcov_var(self, A, B, n_mock, M_a=1, M=math.inf, stream=None):
         """Var(C_ij) [nbin, nbin]: LC form from (A, B), or the sample-covariance form from C = A when B is None."""
+        dev = torch.device("cuda", self.device)
+        _need(A, "A", (torch.float64,), (None, None), dev)
         nbin = A.shape[0]
+        _need(A, "A", (torch.float64,), (nbin, nbin), dev)
+        _need(B, "B", (torch.float64,), (nbin, nbin), dev, optional=True)
         var = torch.empty((nbin, nbin), dtype=torch.float64, device=A.device)
         self._check(self._lib.tpcf_covcov_var(self.handle, _ptr(A), _ptr(B), nbin, int(M_a), float(M), int(n_mock),
                                               _ptr(var), _stream(stream)))
@@ -317,6 +419,12 @@ class Context:
 
     def tpcf_chi2_predict(self, A, B, C_ref, M_a=1, M=math.inf, stream=None):
         """Predicted <chi^2_2> (device scalar tensor) of the LC (B given) or sample (B None) covariance."""
+        dev = torch.device("cuda", self.device)
+        _need(A, "A", (torch.float64,), (None, None), dev)
+        nbin = A.shape[0]
+        _need(A, "A", (torch.float64,), (nbin, nbin), dev)
+        _need(B, "B", (torch.float64,), (nbin, nbin), dev, optional=True)
+        _need(C_ref, "C_ref", (torch.float64,), (nbin, nbin), dev)
         out = torch.empty((), dtype=torch.float64, device=A.device)
         self._check(self._lib.tpcf_chi2_predict(self.handle, _ptr(A), _ptr(B), _ptr(C_ref), A.shape[0], int(M_a),
                                                 float(M), _ptr(out), _stream(stream)))
@@ -324,6 +432,11 @@ class Context:
 
     def tpcf_chi2(self, C_est, C_true, C_ref, stream=None):
         """chi^2 of Eq. (chi2) (device scalar tensor)."""
+        dev = torch.device("cuda", self.device)
+        _need(C_est, "C_est", (torch.float64,), (None, None), dev)
+        nbin = C_est.shape[0]
+        for t, nm in ((C_est, "C_est"), (C_true, "C_true"), (C_ref, "C_ref")):
+            _need(t, nm, (torch.float64,), (nbin, nbin), dev)
         out = torch.empty((), dtype=torch.float64, device=C_est.device)
         self._check(self._lib.tpcf_chi2(self.handle, _ptr(C_est), _ptr(C_true), _ptr(C_ref), C_est.shape[0],
                                         _ptr(out), _stream(stream)))
@@ -331,13 +444,17 @@ class Context:
 
     def tpcf_eigvalsh(self, C, stream=None):
         """Ascending eigenvalues of the symmetric float64 CUDA matrix C."""
+        dev = torch.device("cuda", self.device)
+        _need(C, "C", (torch.float64,), (None, None), dev)
         n = C.shape[0]
+        _need(C, "C", (torch.float64,), (n, n), dev)
         w = torch.empty((n,), dtype=torch.float64, device=C.device)
         self._check(self._lib.tpcf_eigvalsh(self.handle, _ptr(C), n, _ptr(w), _stream(stream)))
         return w
 
     def tpcf_sample_cov(self, xi, precision=TPCF_FP64, stream=None):
         """Sample covariance of xi [n_mock, nbin] over the mocks (Eq. bruteforce); float64 CUDA [nbin, nbin]."""
+        _need(xi, "xi", (torch.float64,), (None, None), torch.device("cuda", self.device))
         n_mock, nbin = xi.shape
         C = torch.empty((nbin, nbin), dtype=torch.float64, device=xi.device)
         self._check(self._lib.tpcf_sample_cov(self.handle, _ptr(xi), n_mock, nbin, int(precision), _ptr(C),

@@ -19,8 +19,8 @@ INCLUDE = ROOT / "include"
 BUILD = PKG / "_build"
 LIB = BUILD / "libtpcf.so"
 
-SOURCES = ["api.cpp", "count.cpp", "plan.cpp", "mesh.cu", "paircount.cu", "estimator.cu", "gram_split.cu", "noalloc.cu",
-           "project.cu", "covcov.cu"]
+SOURCES = ["api.cpp", "count.cpp", "plan.cpp", "mesh.cu", "paircount.cu", "pairdirect.cu", "estimator.cu",
+           "gram_split.cu", "noalloc.cu", "project.cu", "covcov.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,7 +40,7 @@ def _stale() -> bool:
     if not LIB.exists():
         return True
     t = LIB.stat().st_mtime
-    deps = [CSRC / s for s in SOURCES] + list(CSRC.glob("*.h")) + list(INCLUDE.glob("*.h")) + [pathlib.Path(__file__)]
+    deps = [CSRC / s for s in SOURCES] + list(CSRC.glob("*.h")) + list(CSRC.glob("*.cuh")) + list(INCLUDE.glob("*.h")) + [pathlib.Path(__file__)]
     return any(p.stat().st_mtime > t for p in deps)
 
 

@@ -276,6 +276,11 @@ int tpcf_set_option(tpcf_ctx *ctx, int option, int value)
     switch (option) {
     case TPCF_OPT_GRAPHS: ctx->use_graphs = value != 0; break;
     case TPCF_OPT_AUTOTUNE: ctx->autotune = value != 0; break;
+    case TPCF_OPT_KERNEL:
+        if (value != TPCF_KERNEL_AUTO && value != TPCF_KERNEL_GENERAL)
+            return fail(ctx, TPCF_ERR_ARG, "TPCF_OPT_KERNEL takes TPCF_KERNEL_AUTO or TPCF_KERNEL_GENERAL");
+        ctx->kernel_pref = value;
+        break;
     default: return fail(ctx, TPCF_ERR_ARG, "unknown option");
     }
     return TPCF_OK;
@@ -298,6 +303,7 @@ int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info)
     info->n_kernels = ctx->last_kernels;
     info->unit_chunk = ctx->last_chunk;
     info->graph_replay = ctx->last_graph ? 1 : 0;
+    info->pair_kernel = ctx->last_direct ? TPCF_KERNEL_DIRECT : TPCF_KERNEL_GENERAL;
     double total = 0.0;
     for (int i = 0; i < ctx->n_timed; i++) {
         float ms = 0;

@@ -42,6 +42,9 @@ struct Setup {
     unsigned long long units_bound = 0;
     int chunk = UNIT_CHUNK;
     int smem = 0, blocks = 0;
+    bool direct = false;            // the direct pair counter (pairdirect.cu) runs
+    DirectParams dp;
+    int claim_units = 1;            // direct counter: units per block claim
     double L = 0, origin[3] = {0, 0, 0};
     // outputs to clear
     int64_t *dd = nullptr, *dr = nullptr, *rr = nullptr;
@@ -119,6 +122,28 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
     if ((rc = check_mu_width(ctx, binning, S.pl.prm))) return rc;
     const CountParams &prm = S.pl.prm;
     S.chunk = std::max(32, std::min(chunk, UNIT_CHUNK));
+    if (ctx->kernel_pref != TPCF_KERNEL_GENERAL) {
+        int sm_sm = 0, sm_blk = 0, resv = 0;
+        if (cudaDeviceGetAttribute(&sm_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sm_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device) != cudaSuccess) {
+            cudaGetLastError();
+            sm_sm = 0;
+        }
+        if (sm_sm > 0 && build_direct(*binning, S.pl, sm_sm, sm_blk, resv, max_cat, S.dp)) {
+            S.direct = true;
+            S.chunk = std::min(S.chunk, DIRECT_ACHUNK);
+        }
+    }
+    // The pair counters add into 32-bit shared-memory counters: one unit adds
+    // at most chunk x (points of one catalogue) pairs to any counter, which
+    // must stay below 2^32 (the direct counter drains before the sum over
+    // units could reach 2^31).
+    if (max_cat > 0) {
+        const unsigned long long cap = ((1ull << 32) - 1) / max_cat;
+        if (cap < 16) return fail(ctx, TPCF_ERR_RANGE, "a catalogue above 2^28 points would overflow the 32-bit pair counters");
+        if ((unsigned long long)S.chunk > cap) S.chunk = (int)(cap & ~15ull);
+    }
     S.L = binning->box_L;
     for (int c = 0; c < 3; c++) S.origin[c] = binning->origin[c];
 
@@ -193,7 +218,7 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
     if ((rc = ensure(ctx, "ucount", S.ntc * 4, &S.uc))) return rc;
     if ((rc = ensure(ctx, "ustart", S.ntc * 4, &S.ust))) return rc;
     if ((rc = ensure(ctx, "units", S.units_bound * sizeof(Unit), &S.units))) return rc;
-    if ((rc = ensure(ctx, "claim", 256, &S.claim))) return rc;
+    if ((rc = ensure(ctx, "claim", std::max<size_t>(256, 4 * (S.terms.size() + 1)), &S.claim))) return rc;
 
     // pre-quantised randoms: one [3][n_r] array per mock, gathered into a
     // compact [3][n] block per subset
@@ -230,6 +255,19 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
     std::memcpy(S.small.data() + S.o_tab, S.pl.table.data(), S.pl.table.size() * 2);
 
     // launch shape (host queries, outside any capture)
+    if (S.direct) {
+        cudaError_t e = pairdirect_set_attrs(prm, S.dp.R, S.dp.W, S.dp.smem);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "pairdirect_set_attrs");
+        const int occ = pairdirect_max_blocks_per_sm(prm, S.dp.R, S.dp.W, S.dp.smem);
+        if (occ < 1) return fail(ctx, TPCF_ERR_CUDA, "the direct pair counter does not fit on an SM");
+        S.smem = S.dp.smem;
+        S.blocks = ctx->n_sm * occ;
+        // units per block claim: a few claims per block, at most 2^30 pairs per counter
+        const unsigned long long by_work = std::max<unsigned long long>(1, S.units_bound / (4ull * S.blocks));
+        const unsigned long long by_wrap = std::max<unsigned long long>(1, (1ull << 30) / S.dp.unit_pair_bound);
+        S.claim_units = (int)std::min<unsigned long long>({by_work, by_wrap, 4096ull});
+        return TPCF_OK;
+    }
     S.smem = paircount_smem_bytes(prm, 8);
     {
         // the block histogram (4 nbin bytes) sits in shared memory beside the queues
@@ -298,19 +336,28 @@ int enqueue(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, void *small
     L.smem_bytes = S.smem;
     L.chunk = S.chunk;
     L.scratch = S.bscr;
-    if (mode == TPCF_BATCHED) {
+    if (mode == TPCF_BATCHED || S.direct) {
+        // the work-unit list (the direct counter uses it in both modes)
         CK(cudaMemsetAsync(uc + (S.ntc - 1), 0, 4, s));
         CK(launch_unit_count(d_terms, n_terms, d_cats, prm.n_cells, cs, S.chunk, uc, s));
         CK(launch_scan_u32(uc, ust, S.ntc, tmp, S.tmp_n, s));
         CK(launch_unit_fill(d_terms, n_terms, d_cats, prm.n_cells, cs, S.chunk, ust, (Unit *)S.units, s));
-        CK(cudaMemsetAsync(S.claim, 0, 4, s));
+        CK(cudaMemsetAsync(S.claim, 0, 4 * (S.terms.size() + 1), s));
         kernels += 5;
+    }
+    if (mode == TPCF_BATCHED) {
         L.persistent = 1;
         L.term = 0;
         L.blocks = S.blocks;
         if (ev0) CK(cudaEventRecordWithFlags(ev0, s, external ? cudaEventRecordExternal : cudaEventRecordDefault));
-        CK(launch_paircount(prm, mesh, d_terms, d_cats, (const Unit *)S.units, ust + (S.ntc - 1),
-                            (unsigned *)S.claim, d_tab, ctx->stats, ctx->status, L, s));
+        if (S.direct) {
+            L.chunk = S.claim_units;
+            CK(launch_pairdirect(prm, S.dp, mesh, d_terms, (const Unit *)S.units, ust + (S.ntc - 1),
+                                 (unsigned *)S.claim, ctx->stats, L, s));
+        } else {
+            CK(launch_paircount(prm, mesh, d_terms, d_cats, (const Unit *)S.units, ust + (S.ntc - 1),
+                                (unsigned *)S.claim, d_tab, ctx->stats, ctx->status, L, s));
+        }
         if (ev1) CK(cudaEventRecordWithFlags(ev1, s, external ? cudaEventRecordExternal : cudaEventRecordDefault));
         kernels += 1;
         CK(cudaMemcpyAsync(ctx->stats + 3, ust + (S.ntc - 1), 4, cudaMemcpyDeviceToDevice, s));
@@ -319,9 +366,17 @@ int enqueue(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, void *small
         for (int t = 0; t < n_terms; t++) {
             L.persistent = 0;
             L.term = t;
-            L.blocks = std::min(S.blocks, prm.n_cells);   // blocks stride over the cells
-            CK(launch_paircount(prm, mesh, d_terms, d_cats, nullptr, nullptr, nullptr, d_tab, ctx->stats,
-                                ctx->status, L, s));
+            if (S.direct) {
+                // one launch per term over that term's units, each with its own claim counter
+                L.blocks = S.blocks;
+                L.chunk = std::max(1, S.claim_units / 8);
+                CK(launch_pairdirect(prm, S.dp, mesh, d_terms, (const Unit *)S.units, ust + (S.ntc - 1),
+                                     (unsigned *)S.claim + 1 + t, ctx->stats, L, s));
+            } else {
+                L.blocks = std::min(S.blocks, prm.n_cells);   // blocks stride over the cells
+                CK(launch_paircount(prm, mesh, d_terms, d_cats, nullptr, nullptr, nullptr, d_tab, ctx->stats,
+                                    ctx->status, L, s));
+            }
         }
         if (ev1) CK(cudaEventRecordWithFlags(ev1, s, external ? cudaEventRecordExternal : cudaEventRecordDefault));
         kernels += n_terms;
@@ -363,6 +418,8 @@ std::string graph_key(const Setup &S, int mode, tpcf_ctx *ctx)
     std::string k;
     auto put = [&](const void *p, size_t n) { k.append((const char *)p, n); };
     put(&S.pl.prm, sizeof(CountParams));
+    put(&S.direct, sizeof(S.direct));
+    put(&S.dp, sizeof(S.dp));
     put(&mode, sizeof(mode));
     put(&S.chunk, sizeof(S.chunk));
     put(&S.blocks, sizeof(S.blocks));
@@ -505,7 +562,7 @@ int autotune(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binni
     return rc;
 }
 
-std::string tune_key(const tpcf_mock *mocks, int n_mock, const tpcf_binning *b, unsigned terms)
+std::string tune_key(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *b, unsigned terms)
 {
     std::string k;
     auto put = [&](const void *p, size_t n) { k.append((const char *)p, n); };
@@ -516,6 +573,8 @@ std::string tune_key(const tpcf_mock *mocks, int n_mock, const tpcf_binning *b, 
     put(&b->n_mu, sizeof(int));
     put(b->s_edges, sizeof(double) * (b->n_s + 1));
     put(&terms, sizeof(terms));
+    put(&ctx->device, sizeof(ctx->device));
+    put(&ctx->kernel_pref, sizeof(ctx->kernel_pref));
     // size class: log2 of the mean catalogue size
     double pts = 0;
     for (int m = 0; m < n_mock; m++) pts += (double)mocks[m].n_d;
@@ -652,7 +711,7 @@ extern "C" int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, con
     if (ctx->subdiv_pin) {
         cfg.subdiv = ctx->subdiv_pin;
     } else if (ctx->autotune && mode == TPCF_BATCHED && n_mock > 0) {
-        const std::string tk = tune_key(mocks, n_mock, binning, terms);
+        const std::string tk = tune_key(ctx, mocks, n_mock, binning, terms);
         auto it = ctx->tune_cache.find(tk);
         if (it == ctx->tune_cache.end()) {
             Setup probe;
@@ -669,6 +728,7 @@ extern "C" int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, con
     ctx->last_subdiv = cfg.subdiv;
     ctx->last_nc = S.pl.prm.n_c;
     ctx->last_chunk = S.chunk;
+    ctx->last_direct = S.direct;
     ctx->last_launches = S.terms.empty() || S.NT == 0 ? 0 : (mode == TPCF_BATCHED ? 1 : (int)S.terms.size());
     const int slot = timing_slot(ctx);
     if (mode == TPCF_BATCHED && ctx->use_graphs && S.NT > 0 && !S.terms.empty())

@@ -67,6 +67,8 @@ struct tpcf_ctx {
     int autotune = 1;
     std::map<std::string, tpcf::Tuned> tune_cache;
     int last_subdiv = 0, last_nc = 0, last_chunk = 0;
+    int kernel_pref = 2;                  // TPCF_KERNEL_AUTO | TPCF_KERNEL_GENERAL (the default)
+    bool last_direct = false;             // the last tpcf_count ran the direct counter
     // graphs
     cudaStream_t cap_stream = nullptr;
     std::vector<tpcf::GraphEntry> graphs;

@@ -34,7 +34,7 @@
 // dot-product range test (a.b' - |a|^2/2 >= (|b'|^2 - H)/2 - margin: three
 // FMAs and a compare), compacted per warp and binned from the a-chunk and
 // the tile's b copies; its rechecks go through the same 32-at-a-time list.
-#include "plan.h"
+#include "pair_device.cuh"
 
 namespace tpcf {
 
@@ -62,9 +62,6 @@ static_assert((QX + 1) % 4 == 0, "x-path flush passes read four rows and stay in
 static_assert((SCR * 16) % 128 == 0 && (SCR_W * 16) % 128 == 0 && (CAP * 16) % 128 == 0,
               "per-block scratch regions start on 128-byte lines (discard_l2)");
 static_assert(UNIT_CHUNK % 32 == 0 && UNIT_CHUNK <= 128 && UNIT_CHUNK <= WARPS * 32, "a-chunk load and box");
-
-typedef unsigned __int128 u128;
-typedef __int128 i128;
 
 // A run of b-points: cells x0..x1 of one neighbour row, contiguous in the
 // cell-sorted order.  Runs are concatenated, and the concatenation is cut
@@ -131,81 +128,6 @@ __device__ __forceinline__ uint32_t *sh_orig(const CountParams &p)
     return (uint32_t *)(smem_raw + var_offsets(p, MID).orig);
 }
 
-// Exact bin of the pair (ia, ib) from integer grid coordinates; -1 if unbinned.
-__device__ __noinline__ int exact_bin(const CountParams &prm, const unsigned long long *T,
-                                      const uint32_t *__restrict__ us, uint32_t N, uint32_t ia, uint32_t ib)
-{
-    long long d[3];
-    uint32_t ua[3], ub[3];
-    unsigned long long D2 = 0;
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        ua[c] = us[(size_t)c * N + ia];
-        ub[c] = us[(size_t)c * N + ib];
-        d[c] = (prm.geometry == TPCF_PERIODIC) ? (long long)(int)(ua[c] - ub[c])
-                                               : (long long)ua[c] - (long long)ub[c];
-        D2 += (unsigned long long)(d[c] * d[c]);
-    }
-    const int n_s = prm.n_s;
-    if (D2 < T[0] || D2 >= T[n_s]) return -1;
-    int lo = 0, hi = n_s - 1;        // largest k with T[k] <= D2
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (T[mid] <= D2) lo = mid; else hi = mid - 1;
-    }
-    const int k = lo;
-    const int n_mu = prm.n_mu;
-    int j = 0;
-    if (n_mu > 1) {
-        u128 num, den;
-        if (prm.los == TPCF_LOS_X) {
-            num = (u128)(unsigned long long)(d[0] * d[0]);
-            den = (u128)D2;
-        } else {
-            i128 dot = 0;
-            u128 l2 = 0;
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const i128 l = (i128)ua[c] + (i128)ub[c] - 2 * (i128)prm.obs[c];
-                dot += (i128)d[c] * l;
-                l2 += (u128)(l * l);
-            }
-            const u128 ad = (u128)(dot < 0 ? -dot : dot);
-            num = ad * ad;
-            den = (u128)D2 * l2;
-        }
-        if (den != 0) {
-            const u128 lhs = (u128)(unsigned)(n_mu * n_mu) * num;
-            j = n_mu - 1;
-            while (j > 0 && lhs < (u128)(unsigned)(j * j) * den) j--;
-        }
-    }
-    return k * n_mu + j;
-}
-
-__device__ __forceinline__ uint32_t warp_exclusive_sum(uint32_t v, int lane, uint32_t &total)
-{
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    total = __shfl_sync(0xffffffffu, x, 31);
-    return x - v;
-}
-
-// MUFU reciprocal square root without denormal handling (relative error
-// within 2 ulp); every use carries that error in its ambiguity band
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// 32-bit shared-memory accesses (addresses from __cvta_generic_to_shared)
-__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 // queue push: store v at the head slot; advance the head (one 64-byte slot
 // row) only when t >= h
 __device__ __forceinline__ void push_if_ge(uint32_t &head, uint32_t v, float t, float h)
@@ -1229,11 +1151,13 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         if (persistent && tid == 0) sh_misc()[0] = (int)atomicAdd(claim, 1u);   // the next unit
         long long *const th = terms[un.term].hist;
         for (int b = tid; b < prm.nbin; b += blockDim.x) {
-            const int v = ((int *)(smem_raw + vo.hist))[b];
-            cx.n_binned += (unsigned)v;   // every binned pair passes through the block histogram
+            // 32-bit counters read as unsigned: a unit adds fewer than 2^32 pairs
+            // to any bin (the host caps the unit size by the largest catalogue)
+            const unsigned v = ((unsigned *)(smem_raw + vo.hist))[b];
+            cx.n_binned += v;   // every binned pair passes through the block histogram
             if (v) {
-                atomicAdd((unsigned long long *)&th[b], (unsigned long long)(long long)v);
-                ((int *)(smem_raw + vo.hist))[b] = 0;
+                atomicAdd((unsigned long long *)&th[b], (unsigned long long)v);
+                ((unsigned *)(smem_raw + vo.hist))[b] = 0u;
             }
         }
         __syncthreads();

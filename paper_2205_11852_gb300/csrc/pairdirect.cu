@@ -1,0 +1,715 @@
+// Direct binned pair counting on the chaining mesh (Sect. 2.1: DD, DR_i and
+// RR_i counts; Sect. 4.3: bins in separation s and in mu) for linear s bins
+// starting at 0, with the line of sight along x or s only.
+//
+// Work decomposition.  A unit is a chunk of at most 64 sorted points of one
+// mesh cell A, paired with the neighbourhood of A in catalogue b.  Each warp
+// owns a unit on its own: it stages the a-chunk in its region of shared
+// memory, streams the b-points of the neighbourhood (the self cell of an
+// auto count as it is, every other neighbour cell through a filter that
+// keeps a point only if its distance to the a-chunk's bounding box is below
+// the last edge) into its own buffer, and counts every full tile of 256
+// b-points (8 per lane) against the a-chunk as soon as it is there.  The
+// warps of a block share one histogram, so a block works through a chunk of
+// consecutive units of one term at a time (units are ordered by term); block
+// barriers come only between such chunks.
+//
+// Arithmetic.  Coordinates are exact integer offsets from A's lower corner,
+// converted once to FP32 in units of one s bin, so the s bin of a pair is
+// floor(u) with u its FP32 separation.  Two pairs run side by side in packed
+// FP32 (f32x2) arithmetic.  Per pair: d2 from the differences, r = rsqrt(d2)
+// (MUFU), S = floor(d2 r) by one round-toward-zero FMA onto a power-of-two
+// offset, the residual d2 r - floor(d2 r) - 1/2 by one more FMA, and the
+// signed mu bin T = floor(n_mu dx r) at both ends of the error interval
+// [n_mu dx - m, n_mu dx + m] r.  A pair is certain when its s residual lies
+// within cs of 1/2 and both mu floors agree; cs and m come from a rigorous
+// bound on the FP32 errors (plan.cpp).  Every pair, certain or not, is added
+// to the histogram at (S, T-) with one shared-memory atomic; a pair at or
+// beyond the last edge lands in the histogram's spare last row.  A group of
+// 8 pairs per lane with any uncertain pair takes the rare path, which
+// recomputes them, takes back the uncertain ones' adds and rechecks them
+// exactly from the integer coordinates (64-bit squared distances, a 128-bit
+// mu test), 32 at a time, so every count equals the integer definition bit
+// for bit.
+//
+// Histogram.  R copies of a (n_s + 1) x C table of 32-bit counters, lane l
+// adding to copy l mod R, so the 32 adds of a warp fall in distinct banks
+// (R = 32) or at most two per bank (R = 16).  mu is binned by sign, C =
+// 2 n_mu + 2 columns from -n_mu - 1 to n_mu, and folded to |mu| when the
+// table is drained into the term's int64 histogram: when the block moves to
+// another term, or before its 32-bit counters could wrap.
+#include "pair_device.cuh"
+
+namespace tpcf {
+
+namespace {
+
+constexpr int NP = 8;               // b-points per lane: four packed pairs
+constexpr int TB = 32 * NP;         // b-points per tile
+constexpr int BUF = TB + 128;       // per-warp b buffer: a tile plus one filter pass
+constexpr int XCAP = 96;            // per-warp list of pairs awaiting the exact recheck
+constexpr float MAG_S = 8388608.0f;       // 2^23: fma.rz(d2, r, MAG_S) = 2^23 + floor(d2 r) for 0 <= d2 r < 2^23
+constexpr uint32_t MAG_S_BITS = 0x4B000000u;
+constexpr float MAG_T = 12582912.0f;      // 1.5 * 2^23: = 1.5 * 2^23 + floor(t) for |t| < 2^22
+constexpr uint32_t MAG_T_BITS = 0x4B400000u;
+constexpr float FAR = 1.0e5f;             // a padding b-point: far beyond every edge, still finite
+static_assert(DIRECT_ACHUNK % 32 == 0 && DIRECT_ACHUNK <= 64, "a-chunk load: two points per lane");
+
+__host__ __device__ constexpr uint32_t al16(uint32_t x) { return (x + 15u) & ~15u; }
+
+// Shared memory: the block's histogram, T, misc words, then one region per
+// warp: a-records (3 float4 per a-point), the b buffer (float4: x, y, z in
+// bins and the b index), the unit's runs (first index, offset in the
+// concatenation) and the recheck list.
+struct DOff {
+    uint32_t hist, T, misc, warp0, wstride;
+    uint32_t arec, buf, runs, xl;   // offsets inside a warp's region
+    uint32_t end;
+};
+__host__ __device__ inline DOff d_off(int n_s, int n_rows, int R, int C, int W)
+{
+    DOff o;
+    o.hist = 0;
+    o.T = al16(4u * (uint32_t)((n_s + 1) * C * R));
+    o.misc = al16(o.T + 8u * (uint32_t)(n_s + 1));
+    o.warp0 = o.misc + 64u;
+    o.arec = 0;
+    o.buf = o.arec + 48u * DIRECT_ACHUNK;
+    o.runs = o.buf + 16u * BUF;
+    o.xl = al16(o.runs + 8u * (uint32_t)(2 * n_rows + 1));
+    o.wstride = al16(o.xl + 8u * XCAP);
+    o.end = o.warp0 + o.wstride * (uint32_t)W;
+    return o;
+}
+
+extern __shared__ __align__(16) unsigned char dsm[];
+
+__device__ __forceinline__ void red_add(uint32_t a, uint32_t v)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// An a-point's record: -a_x, -a_y, -a_z, cp = m - n_mu a_x, cm = -m - n_mu a_x,
+// each duplicated for the packed operands.
+struct ARec {
+    float2 nax, nay, naz, cp, cm;
+};
+
+// The histogram addresses of the pairs (b_p, a), (b_p', a); amb gains the
+// uncertainty of either.  Hot path.
+template <bool MU>
+__device__ __forceinline__ void pair2(const float2 bx, const float2 by, const float2 bz, const ARec &a,
+                                      const DirectParams &dp, uint32_t KS, uint32_t KT, uint32_t Kl, uint32_t &a0,
+                                      uint32_t &a1, bool &amb)
+{
+    const float2 dx = __fadd2_rn(bx, a.nax), dy = __fadd2_rn(by, a.nay), dz = __fadd2_rn(bz, a.naz);
+    float2 d2 = MU ? __fmul2_rn(dx, dx) : __ffma2_rn(dx, dx, make_float2(dp.tiny, dp.tiny));
+    d2 = __ffma2_rn(dy, dy, d2);
+    d2 = __ffma2_rn(dz, dz, d2);
+    if (MU) {
+        d2.x = fmaxf(d2.x, dp.d2min);
+        d2.y = fmaxf(d2.y, dp.d2min);
+    }
+    float2 r;
+    r.x = rsqrt_approx(d2.x);
+    r.y = rsqrt_approx(d2.y);
+    const float2 S = __ffma2_rz(d2, r, make_float2(MAG_S, MAG_S));
+    const float2 H = __ffma2_rn(S, make_float2(-1.0f, -1.0f), make_float2(MAG_S - 0.5f, MAG_S - 0.5f));
+    const float2 fs = __ffma2_rn(d2, r, H);   // u - floor(u) - 1/2
+    a0 = __float_as_uint(fminf(S.x, dp.s_top)) * KS + Kl;
+    a1 = __float_as_uint(fminf(S.y, dp.s_top)) * KS + Kl;
+    bool u = (fabsf(fs.x) > dp.cs) | (fabsf(fs.y) > dp.cs);
+    if (MU) {
+        const float2 nm = make_float2(dp.nmu, dp.nmu);
+        const float2 dxp = __ffma2_rn(bx, nm, a.cp), dxm = __ffma2_rn(bx, nm, a.cm);
+        const float2 Tp = __ffma2_rz(dxp, r, make_float2(MAG_T, MAG_T));
+        const float2 Tm = __ffma2_rz(dxm, r, make_float2(MAG_T, MAG_T));
+        u = u | (Tp.x != Tm.x) | (Tp.y != Tm.y);
+        a0 += __float_as_uint(Tm.x) * KT;
+        a1 += __float_as_uint(Tm.y) * KT;
+    }
+    amb = amb | u;
+}
+
+// The same pair of pairs, per pair: address, uncertain, s bin certain, S.
+// Rare path.
+template <bool MU>
+__device__ __forceinline__ void pair2_flags(const float2 bx, const float2 by, const float2 bz, const ARec &a,
+                                            const DirectParams &dp, uint32_t KS, uint32_t KT, uint32_t Kl,
+                                            uint32_t (&ad)[2], bool (&amb)[2], bool (&sok)[2], float (&Sv)[2])
+{
+    const float2 dx = __fadd2_rn(bx, a.nax), dy = __fadd2_rn(by, a.nay), dz = __fadd2_rn(bz, a.naz);
+    float2 d2 = MU ? __fmul2_rn(dx, dx) : __ffma2_rn(dx, dx, make_float2(dp.tiny, dp.tiny));
+    d2 = __ffma2_rn(dy, dy, d2);
+    d2 = __ffma2_rn(dz, dz, d2);
+    if (MU) {
+        d2.x = fmaxf(d2.x, dp.d2min);
+        d2.y = fmaxf(d2.y, dp.d2min);
+    }
+    float2 r;
+    r.x = rsqrt_approx(d2.x);
+    r.y = rsqrt_approx(d2.y);
+    const float2 S = __ffma2_rz(d2, r, make_float2(MAG_S, MAG_S));
+    const float2 H = __ffma2_rn(S, make_float2(-1.0f, -1.0f), make_float2(MAG_S - 0.5f, MAG_S - 0.5f));
+    const float2 fs = __ffma2_rn(d2, r, H);
+    ad[0] = __float_as_uint(fminf(S.x, dp.s_top)) * KS + Kl;
+    ad[1] = __float_as_uint(fminf(S.y, dp.s_top)) * KS + Kl;
+    sok[0] = !(fabsf(fs.x) > dp.cs);
+    sok[1] = !(fabsf(fs.y) > dp.cs);
+    amb[0] = !sok[0];
+    amb[1] = !sok[1];
+    Sv[0] = S.x;
+    Sv[1] = S.y;
+    if (MU) {
+        const float2 nm = make_float2(dp.nmu, dp.nmu);
+        const float2 dxp = __ffma2_rn(bx, nm, a.cp), dxm = __ffma2_rn(bx, nm, a.cm);
+        const float2 Tp = __ffma2_rz(dxp, r, make_float2(MAG_T, MAG_T));
+        const float2 Tm = __ffma2_rz(dxm, r, make_float2(MAG_T, MAG_T));
+        amb[0] = amb[0] | (Tp.x != Tm.x);
+        amb[1] = amb[1] | (Tp.y != Tm.y);
+        ad[0] += __float_as_uint(Tm.x) * KT;
+        ad[1] += __float_as_uint(Tm.y) * KT;
+    }
+}
+
+// Per-lane histogram address constants: address = bits(S) KS + bits(T-) KT + Kl.
+struct Addr {
+    uint32_t KS, KT, Kl;
+    uint32_t hb;      // histogram base (shared address) + 4 (lane mod R)
+    uint32_t dump;    // this lane's word in the spare last row
+};
+
+// A warp's shared-memory region and its pending exact rechecks.
+struct WarpMem {
+    float4 *arec;     // a-records of the unit's a-chunk
+    float4 *buf;      // b buffer: x, y, z in bins and the b index
+    uint2 *runs;      // the unit's runs: (first b index, offset in their concatenation)
+    uint2 *xl;        // pairs (a index, b index) awaiting the exact recheck
+};
+
+__device__ __forceinline__ ARec load_a(const float4 *arec, uint32_t ai)
+{
+    const float4 r0 = arec[3 * ai], r1 = arec[3 * ai + 1];
+    const float2 r2 = *(const float2 *)&arec[3 * ai + 2];
+    return ARec{make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y), make_float2(r1.z, r1.w),
+                r2};
+}
+
+// exact recheck of the n listed pairs, one per lane; returns the number rechecked by this lane
+template <bool MU, int R>
+__device__ __forceinline__ uint32_t recheck(const CountParams &prm, const DirectParams &dp, const Mesh &m,
+                                            const unsigned long long *T, const uint2 *xl, uint32_t n, uint32_t hb,
+                                            int lane)
+{
+    __syncwarp();
+    uint32_t cnt = 0;
+    for (uint32_t e = (uint32_t)lane; e < n; e += 32) {
+        const uint2 pr = xl[e];
+        const int bin = exact_bin(prm, T, m.us, m.n_total, pr.x, pr.y);
+        cnt++;
+        if (bin >= 0) {
+            const uint32_t k = (uint32_t)bin / (uint32_t)prm.n_mu, j = (uint32_t)bin % (uint32_t)prm.n_mu;
+            const uint32_t col = MU ? j + (uint32_t)prm.n_mu + 1u : 0u;
+            red_add(hb + 4u * (uint32_t)R * (k * (uint32_t)dp.C + col), 1u);
+        }
+    }
+    __syncwarp();
+    return cnt;
+}
+
+// Every pair of the a-chunk (na points from sorted index a0) with the first nb
+// entries of the warp's buffer; CHK: only pairs a < b count (the self cell
+// of an auto count).  The a-points whose group of 8 pairs per lane holds an
+// uncertain pair are marked and handled after the tile: their adds are taken
+// back and they join the recheck list, unless their s bin alone is certainly
+// at or past the last edge (their add went to the spare row).
+template <bool MU, int R, bool CHK>
+__device__ __forceinline__ void tile(const CountParams &prm, const DirectParams &dp, const Mesh &m,
+                                     const unsigned long long *T, const WarpMem &wm, const Addr &ad, uint32_t nb,
+                                     uint32_t na, uint32_t a0, int lane, uint32_t &n_list,
+                                     unsigned long long &n_exact, unsigned long long &n_cand)
+{
+    float2 BX[4], BY[4], BZ[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const uint32_t s = 32u * (uint32_t)(2 * q + h) + (uint32_t)lane;
+            const float4 v = s < nb ? wm.buf[s] : make_float4(FAR, FAR, FAR, 0.0f);
+            if (h) {
+                BX[q].y = v.x;
+                BY[q].y = v.y;
+                BZ[q].y = v.z;
+            } else {
+                BX[q].x = v.x;
+                BY[q].x = v.y;
+                BZ[q].x = v.z;
+            }
+        }
+    }
+    uint32_t IB[NP];
+    if (CHK) {
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+            const uint32_t s = 32u * (uint32_t)p + (uint32_t)lane;
+            IB[p] = s < nb ? __float_as_uint(wm.buf[s].w) : 0u;
+        }
+    }
+    n_cand += (unsigned long long)nb * na;
+    unsigned long long marked = 0;   // a-points with an uncertain pair (warp-uniform)
+#pragma unroll 1
+    for (uint32_t ai = 0; ai < na; ai++) {
+        const ARec a = load_a(wm.arec, ai);
+        bool amb = false;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            uint32_t x0, x1;
+            pair2<MU>(BX[q], BY[q], BZ[q], a, dp, ad.KS, ad.KT, ad.Kl, x0, x1, amb);
+            if (CHK) {
+                const uint32_t ia = a0 + ai;
+                if (!(ia < IB[2 * q])) x0 = ad.dump;
+                if (!(ia < IB[2 * q + 1])) x1 = ad.dump;
+            }
+            red_add(x0, 1u);
+            red_add(x1, 1u);
+        }
+        if (__any_sync(0xffffffffu, amb)) marked |= 1ull << ai;
+    }
+    const uint32_t lt = (1u << lane) - 1u;
+    while (marked) {
+        const uint32_t ai = (uint32_t)(__ffsll((long long)marked) - 1);
+        marked &= marked - 1ull;
+        const ARec a = load_a(wm.arec, ai);
+        const uint32_t ia = a0 + ai;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            uint32_t adr[2];
+            bool amb[2], sok[2];
+            float Sv[2];
+            pair2_flags<MU>(BX[q], BY[q], BZ[q], a, dp, ad.KS, ad.KT, ad.Kl, adr, amb, sok, Sv);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t s = 32u * (uint32_t)(2 * q + h) + (uint32_t)lane;
+                const bool in_tile = s < nb;
+                const uint32_t ib = in_tile ? __float_as_uint(wm.buf[s].w) : 0u;
+                const bool valid = in_tile && (!CHK || ia < ib);
+                const bool beyond = sok[h] && Sv[h] >= dp.s_top;
+                const bool x = valid && amb[h] && !beyond;
+                if (x) red_add(adr[h], 0xFFFFFFFFu);
+                const unsigned mk = __ballot_sync(0xffffffffu, x);
+                if (x) wm.xl[n_list + __popc(mk & lt)] = make_uint2(ia, ib);
+                n_list += __popc(mk);
+                if (n_list >= XCAP - 32) {
+                    n_exact += recheck<MU, R>(prm, dp, m, T, wm.xl, n_list, ad.hb, lane);
+                    n_list = 0;
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// x, y, z of sorted point i in bins relative to the corner (ox, oy, oz)
+__device__ __forceinline__ float4 bpoint(const DirectParams &dp, uint32_t i, uint32_t ux, uint32_t uy, uint32_t uz,
+                                         uint32_t ox, uint32_t oy, uint32_t oz)
+{
+    return make_float4(__fmul_rn(__int2float_rn((int)(ux - ox)), dp.inv_qds),
+                       __fmul_rn(__int2float_rn((int)(uy - oy)), dp.inv_qds),
+                       __fmul_rn(__int2float_rn((int)(uz - oz)), dp.inv_qds), __uint_as_float(i));
+}
+
+// The unit: a-chunk [un.a0, un.a1) of cell un.cell against the term's neighbourhood.
+template <bool MU, int R>
+__device__ __forceinline__ void unit(const CountParams &prm, const DirectParams &dp, const Mesh &m,
+                                     const unsigned long long *T, const WarpMem &wm, const Addr &ad, const Unit &un,
+                                     const Term &tm, int lane, uint32_t &n_list, unsigned long long &n_exact,
+                                     unsigned long long &n_cand)
+{
+    const int n_c = prm.n_c;
+    const int ax = un.cell % n_c, ay = (un.cell / n_c) % n_c, az = un.cell / (n_c * n_c);
+    const uint32_t ox = m.orig[ax], oy = m.orig[ay], oz = m.orig[az];
+    const size_t N = m.n_total;
+    const uint32_t a0 = un.a0, na = un.a1 - un.a0;
+    // the a-chunk in bin units relative to A's corner, as packed records
+    // (-x, -x, -y, -y), (-z, -z, m - n_mu x, ...), (-m - n_mu x, ...), and its box
+    float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+    for (uint32_t i = (uint32_t)lane; i < na; i += 32) {
+        const size_t g = a0 + i;
+        const float4 p = bpoint(dp, (uint32_t)g, m.us[g], m.us[N + g], m.us[2 * N + g], ox, oy, oz);
+        const float fxp = __fmul_rn(p.x, dp.nmu);
+        const float cp = __fsub_rn(dp.m, fxp), cm = __fsub_rn(-dp.m, fxp);
+        wm.arec[3 * i] = make_float4(-p.x, -p.x, -p.y, -p.y);
+        wm.arec[3 * i + 1] = make_float4(-p.z, -p.z, cp, cp);
+        wm.arec[3 * i + 2] = make_float4(cm, cm, 0.f, 0.f);
+        lx = fminf(lx, p.x);
+        ly = fminf(ly, p.y);
+        lz = fminf(lz, p.z);
+        hx = fmaxf(hx, p.x);
+        hy = fmaxf(hy, p.y);
+        hz = fmaxf(hz, p.z);
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, s));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, s));
+        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, s));
+        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, s));
+        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, s));
+        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, s));
+    }
+    // centre and half-widths, rounded outward
+    const float cxb = 0.5f * (lx + hx), cyb = 0.5f * (ly + hy), czb = 0.5f * (lz + hz);
+    const float e = 1.0f / 1048576.0f;
+    const float hxb = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(hx, lx)), __fmul_ru(e, fabsf(cxb) + 1.0f));
+    const float hyb = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(hy, ly)), __fmul_ru(e, fabsf(cyb) + 1.0f));
+    const float hzb = __fadd_ru(__fmul_ru(0.5f, __fsub_ru(hz, lz)), __fmul_ru(e, fabsf(czb) + 1.0f));
+
+    // the unit's b runs, one lane per neighbour row (dz, dy), each a contiguous
+    // x-run of cells; an auto count takes half of the neighbourhood and the
+    // self cell separately
+    const bool periodic = prm.geometry == TPCF_PERIODIC;
+    const uint32_t *cs = m.cellstart + (size_t)tm.cat_b * prm.n_cells;
+    uint32_t n_run = 0, total = 0, self0 = 0, self1 = 0;
+    for (int r0 = 0; r0 < prm.n_rows; r0 += 32) {
+        const int r = r0 + lane;
+        uint32_t s0[2], s1[2];
+        int nl = 0;
+        if (r < prm.n_rows) {
+            const int dz = prm.row_dz[r], dy = prm.row_dy[r], kx = prm.row_kx[r];
+            bool use = !(tm.auto_pairs && (dz < 0 || (dz == 0 && dy < 0)));
+            int z = az + dz, y = ay + dy;
+            if (periodic) {
+                z = z < 0 ? z + n_c : (z >= n_c ? z - n_c : z);
+                y = y < 0 ? y + n_c : (y >= n_c ? y - n_c : y);
+            } else if (z < 0 || z >= n_c || y < 0 || y >= n_c) {
+                use = false;
+            }
+            if (use) {
+                const uint32_t rowkey = ((uint32_t)z * n_c + (uint32_t)y) * n_c;
+                int xlo = ax - kx, xhi = ax + kx;
+                auto add = [&](uint32_t a, uint32_t b) {
+                    if (b > a) {
+                        s0[nl] = a;
+                        s1[nl] = b;
+                        nl++;
+                    }
+                };
+                if (tm.auto_pairs && dz == 0 && dy == 0) {
+                    self0 = cs[rowkey + ax];
+                    self1 = cs[rowkey + ax + 1];
+                    xlo = ax + 1;
+                }
+                if (xlo <= xhi) {
+                    if (periodic) {
+                        if (xlo < 0) {
+                            add(cs[rowkey + xlo + n_c], cs[rowkey + n_c]);
+                            add(cs[rowkey], cs[rowkey + xhi + 1]);
+                        } else if (xhi >= n_c) {
+                            add(cs[rowkey + xlo], cs[rowkey + n_c]);
+                            add(cs[rowkey], cs[rowkey + xhi - n_c + 1]);
+                        } else {
+                            add(cs[rowkey + xlo], cs[rowkey + xhi + 1]);
+                        }
+                    } else {
+                        xlo = max(xlo, 0);
+                        xhi = min(xhi, n_c - 1);
+                        if (xlo <= xhi) add(cs[rowkey + xlo], cs[rowkey + xhi + 1]);
+                    }
+                }
+            }
+        }
+        uint32_t pl = 0;
+        for (int i = 0; i < nl; i++) pl += s1[i] - s0[i];
+        uint32_t n_all, p_all;
+        const uint32_t n_ex = warp_exclusive_sum((uint32_t)nl, lane, n_all);
+        uint32_t p_ex = warp_exclusive_sum(pl, lane, p_all);
+        for (int i = 0; i < nl; i++) {
+            wm.runs[n_run + n_ex + i] = make_uint2(s0[i], total + p_ex);
+            p_ex += s1[i] - s0[i];
+        }
+        n_run += n_all;
+        total += p_all;
+    }
+    self0 = __reduce_max_sync(0xffffffffu, self0);
+    self1 = __reduce_max_sync(0xffffffffu, self1);
+    if (lane == 0) wm.runs[n_run] = make_uint2(0u, total);   // sentinel: the concatenation's end
+    __syncwarp();
+
+    const uint32_t lt = (1u << lane) - 1u;
+    // the self cell (auto counts): every pair a < b, no filter
+    for (uint32_t c = self0; c < self1; c += TB) {
+        const uint32_t nb = min((uint32_t)TB, self1 - c);
+        for (uint32_t e2 = (uint32_t)lane; e2 < nb; e2 += 32) {
+            const size_t g = c + e2;
+            wm.buf[e2] = bpoint(dp, (uint32_t)g, m.us[g], m.us[N + g], m.us[2 * N + g], ox, oy, oz);
+        }
+        __syncwarp();
+        tile<MU, R, true>(prm, dp, m, T, wm, ad, nb, na, a0, lane, n_list, n_exact, n_cand);
+    }
+    // the neighbour runs: four raw points per lane per pass (their twelve
+    // loads in flight together), survivors appended to the buffer, a tile
+    // counted whenever TB of them are there
+    uint32_t nbuf = 0;
+    int g = 0;
+    for (uint32_t c = 0; c < total; c += 128) {
+        uint32_t idx[4];
+        bool ok[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t o2 = c + 32u * (uint32_t)k + (uint32_t)lane;
+            ok[k] = o2 < total;
+            while (g + 1 < (int)n_run && wm.runs[g + 1].y <= o2) g++;
+            idx[k] = ok[k] ? wm.runs[g].x + (o2 - wm.runs[g].y) : 0u;
+        }
+        uint32_t ux[4], uy[4], uz[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            ux[k] = ok[k] ? __ldg(m.us + idx[k]) : 0u;
+            uy[k] = ok[k] ? __ldg(m.us + N + idx[k]) : 0u;
+            uz[k] = ok[k] ? __ldg(m.us + 2 * N + idx[k]) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float4 p = bpoint(dp, idx[k], ux[k], uy[k], uz[k], ox, oy, oz);
+            const float qx = fmaxf(__fsub_rn(fabsf(__fsub_rn(p.x, cxb)), hxb), 0.0f);
+            const float qy = fmaxf(__fsub_rn(fabsf(__fsub_rn(p.y, cyb)), hyb), 0.0f);
+            const float qz = fmaxf(__fsub_rn(fabsf(__fsub_rn(p.z, czb)), hzb), 0.0f);
+            const bool keep = ok[k] && __fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmul_rn(qx, qx))) < dp.hit;
+            const unsigned mk = __ballot_sync(0xffffffffu, keep);
+            if (keep) wm.buf[nbuf + __popc(mk & lt)] = p;
+            nbuf += __popc(mk);
+        }
+        if (nbuf >= TB) {
+            __syncwarp();
+            tile<MU, R, false>(prm, dp, m, T, wm, ad, TB, na, a0, lane, n_list, n_exact, n_cand);
+            // the leftovers (fewer than 128) move to the front
+            const uint32_t left = nbuf - TB;
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t s = 32u * (uint32_t)k + (uint32_t)lane;
+                v[k] = s < left ? wm.buf[TB + s] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t s = 32u * (uint32_t)k + (uint32_t)lane;
+                if (s < left) wm.buf[s] = v[k];
+            }
+            nbuf = left;
+        }
+    }
+    if (nbuf) {
+        __syncwarp();
+        tile<MU, R, false>(prm, dp, m, T, wm, ad, nbuf, na, a0, lane, n_list, n_exact, n_cand);
+    }
+}
+
+// drain the table into term t's int64 histogram and clear it (whole block)
+template <bool MU, int R>
+__device__ __forceinline__ unsigned long long drain(const CountParams &prm, const DirectParams &dp,
+                                                    const Term *terms, uint32_t *hist, uint32_t hwords, int t)
+{
+    __syncthreads();
+    long long *const th = terms[t].hist;
+    const int n_mu = prm.n_mu;
+    unsigned long long binned = 0;
+    for (int b = threadIdx.x; b < prm.nbin; b += blockDim.x) {
+        const int k = b / n_mu, j = b % n_mu;
+        unsigned long long sum = 0;
+        const uint32_t c1 = MU ? (uint32_t)(j + n_mu + 1) : 0u, c2 = MU ? (uint32_t)(n_mu - j) : 0u;
+        const uint4 *w1 = (const uint4 *)(hist + ((uint32_t)k * (uint32_t)dp.C + c1) * (uint32_t)R);
+#pragma unroll
+        for (int c = 0; c < R / 4; c++) {
+            const uint4 v = w1[c];
+            sum += (unsigned long long)v.x + v.y + v.z + v.w;
+        }
+        if (MU) {
+            const uint4 *w2 = (const uint4 *)(hist + ((uint32_t)k * (uint32_t)dp.C + c2) * (uint32_t)R);
+#pragma unroll
+            for (int c = 0; c < R / 4; c++) {
+                const uint4 v = w2[c];
+                sum += (unsigned long long)v.x + v.y + v.z + v.w;
+            }
+        }
+        if (sum) atomicAdd((unsigned long long *)&th[b], sum);
+        binned += sum;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < hwords; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    return binned;
+}
+
+template <bool MU, int R, int W>
+__global__ void __launch_bounds__(W * 32, 1)
+    pairdirect_kernel(const __grid_constant__ CountParams prm, const __grid_constant__ DirectParams dp, const Mesh m,
+                      const Term *__restrict__ terms, const Unit *__restrict__ units,
+                      const uint32_t *__restrict__ n_units_p, unsigned *__restrict__ claim,
+                      unsigned long long *__restrict__ stats, int term_only, int chunk)
+{
+    const DOff o = d_off(prm.n_s, prm.n_rows, R, dp.C, W);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t *hist = (uint32_t *)(dsm + o.hist);
+    unsigned long long *Tsh = (unsigned long long *)(dsm + o.T);
+    unsigned *misc = (unsigned *)(dsm + o.misc);
+    const uint32_t hwords = (uint32_t)(dp.rows * dp.C * R);
+    for (uint32_t i = tid; i < hwords; i += blockDim.x) hist[i] = 0u;
+    for (int i = tid; i <= prm.n_s; i += blockDim.x) Tsh[i] = prm.T[i];
+
+    unsigned char *wr = dsm + o.warp0 + (size_t)warp * o.wstride;
+    const WarpMem wm{(float4 *)(wr + o.arec), (float4 *)(wr + o.buf), (uint2 *)(wr + o.runs), (uint2 *)(wr + o.xl)};
+    Addr ad;
+    ad.hb = saddr(dsm) + o.hist + 4u * ((uint32_t)lane & (uint32_t)(R - 1));
+    if (MU) {
+        ad.KT = 4u * (uint32_t)R;
+        ad.KS = ad.KT * (uint32_t)dp.C;
+        ad.Kl = ad.hb + ad.KT * (uint32_t)(prm.n_mu + 1) - ad.KS * MAG_S_BITS - ad.KT * MAG_T_BITS;
+    } else {
+        ad.KT = 0u;
+        ad.KS = 4u * (uint32_t)R;
+        ad.Kl = ad.hb - ad.KS * MAG_S_BITS;
+    }
+    ad.dump = ad.hb + ad.KS * (uint32_t)prm.n_s;
+    uint32_t n_list = 0;
+    unsigned long long n_exact = 0, n_cand = 0, binned = 0;
+
+    // Chunks of consecutive units are claimed by the block and worked through
+    // term by term, their units claimed one at a time by the warps.  The table
+    // is drained when the term changes, or before the pairs added since the
+    // last drain could reach 2^31 in one counter (a unit adds at most
+    // unit_pair_bound to any counter, and a chunk at most 2^30).  With
+    // term_only >= 0 (one launch per term) only that term's units are claimed.
+    const uint32_t n_all = *n_units_p;
+    uint32_t u_lo = 0, u_hi = n_all;
+    if (term_only >= 0) {
+        uint32_t lo = 0, hi = n_all;   // first unit of a term >= term_only
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (units[mid].term < term_only) lo = mid + 1; else hi = mid;
+        }
+        u_lo = lo;
+        hi = n_all;                    // first unit of a term > term_only
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (units[mid].term <= term_only) lo = mid + 1; else hi = mid;
+        }
+        u_hi = lo;
+    }
+    const uint32_t csize = (uint32_t)chunk;
+    int cur_term = -1;
+    unsigned long long since = 0;
+    __syncthreads();
+    for (;;) {
+        if (tid == 0) misc[0] = u_lo + atomicAdd(claim, csize);
+        __syncthreads();
+        const uint32_t c0 = misc[0];
+        if (c0 >= u_hi) break;
+        const uint32_t c1 = min(u_hi, c0 + csize);
+        uint32_t s = c0;
+        while (s < c1) {
+            const int t = units[s].term;
+            // the end of term t inside [s, c1)
+            uint32_t lo = s, hi = c1;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (units[mid].term == t) lo = mid; else hi = mid;
+            }
+            const uint32_t e = hi;
+            const unsigned long long seg = (unsigned long long)(e - s) * dp.unit_pair_bound;
+            if (cur_term >= 0 && (t != cur_term || since + seg >= (1ull << 31))) {
+                if (n_list) {   // pending rechecks belong to the table being drained
+                    n_exact += recheck<MU, R>(prm, dp, m, Tsh, wm.xl, n_list, ad.hb, lane);
+                    n_list = 0;
+                }
+                binned += drain<MU, R>(prm, dp, terms, hist, hwords, cur_term);
+                since = 0;
+            }
+            cur_term = t;
+            since += seg;
+            if (tid == 0) misc[1] = s;
+            __syncthreads();
+            const Term tm = terms[t];
+            for (;;) {
+                uint32_t u = 0;
+                if (lane == 0) u = atomicAdd(&misc[1], 1u);
+                u = __shfl_sync(0xffffffffu, u, 0);
+                if (u >= e) break;
+                unit<MU, R>(prm, dp, m, Tsh, wm, ad, units[u], tm, lane, n_list, n_exact, n_cand);
+            }
+            __syncthreads();
+            s = e;
+        }
+    }
+    if (cur_term >= 0) {
+        if (n_list) {
+            n_exact += recheck<MU, R>(prm, dp, m, Tsh, wm.xl, n_list, ad.hb, lane);
+            n_list = 0;
+        }
+        binned += drain<MU, R>(prm, dp, terms, hist, hwords, cur_term);
+    }
+    unsigned long long ex = n_exact, bn = binned, cd = lane == 0 ? n_cand : 0ull;
+#pragma unroll
+    for (int s2 = 16; s2 > 0; s2 >>= 1) {
+        ex += __shfl_down_sync(0xffffffffu, ex, s2);
+        bn += __shfl_down_sync(0xffffffffu, bn, s2);
+        cd += __shfl_down_sync(0xffffffffu, cd, s2);
+    }
+    if (lane == 0) {
+        atomicAdd(&stats[0], cd);
+        atomicAdd(&stats[1], bn);
+        atomicAdd(&stats[2], ex);
+    }
+}
+
+template <bool MU, int R, int W>
+void *dkernel()
+{
+    return (void *)pairdirect_kernel<MU, R, W>;
+}
+
+void *select_direct(const CountParams &p, int R, int W)
+{
+    const bool mu = p.n_mu > 1;
+    if (W == 16) {
+        if (R == 32) return mu ? dkernel<true, 32, 16>() : dkernel<false, 32, 16>();
+        return mu ? dkernel<true, 16, 16>() : dkernel<false, 16, 16>();
+    }
+    if (R == 32) return mu ? dkernel<true, 32, 12>() : dkernel<false, 32, 12>();
+    return mu ? dkernel<true, 16, 12>() : dkernel<false, 16, 12>();
+}
+
+}  // namespace
+
+size_t pairdirect_smem_bytes(const CountParams &p, int R, int C, int W)
+{
+    return d_off(p.n_s, p.n_rows, R, C, W).end;
+}
+
+cudaError_t pairdirect_set_attrs(const CountParams &p, int R, int W, int smem_bytes)
+{
+    return cudaFuncSetAttribute(select_direct(p, R, W), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+}
+
+int pairdirect_max_blocks_per_sm(const CountParams &p, int R, int W, int smem_bytes)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_direct(p, R, W), W * 32, smem_bytes) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_pairdirect(const CountParams &p, const DirectParams &d, const Mesh &m, const Term *terms,
+                              const Unit *units, const uint32_t *n_units, unsigned *claim, unsigned long long *stats,
+                              const PairLaunch &pl, cudaStream_t s)
+{
+    const int term_only = pl.persistent ? -1 : pl.term;
+    void *args[] = {(void *)&p,      (void *)&d,     (void *)&m,     (void *)&terms,     (void *)&units,
+                    (void *)&n_units, (void *)&claim, (void *)&stats, (void *)&term_only, (void *)&pl.chunk};
+    return cudaLaunchKernel(select_direct(p, d.R, d.W), dim3(pl.blocks), dim3(d.W * 32), args, (size_t)d.smem, s);
+}
+
+}  // namespace tpcf

@@ -371,4 +371,84 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
     return TPCF_OK;
 }
 
+// Direct pair counter (pairdirect.cu).  Coordinates are x = RN(RN(float(dx_grid)) inv)
+// with inv = RN(1 / (q ds)), dx_grid the exact integer offset from the unit's
+// cell corner, so |x| <= Xb bins.  The bounds below follow every rounding of
+// the kernel's arithmetic, doubled:
+//   E   : one coordinate's error (conversion and scaling; the common relative
+//         error kappa of inv is carried separately),
+//   e_d : a coordinate difference's error for pairs below n_s + 1 bins,
+//   |sqrt(d2) - s*| <= 2 sqrt3 e_d + 6 e_d^2 + gamma_3 (n_s + 2) (d2 from three fused roundings),
+//   u = d2 r exactly inside the FMA, r = rsqrt(d2) within rho = 2^-22.5
+//   (the hardware's measured worst case over all inputs is 2^-22.94).
+// The s residual band is eps_s = that + rho (n_s + 1.5) + kappa (n_s + 1); a pair
+// with |u - floor(u) - 1/2| <= 1/2 - eps_s has s* in the same bin.  The mu
+// interval: n_mu dx -+ m, with one rounding each way, times r brackets
+// n_mu dx* / s* when m >= n_mu 2E + 1.5 ulp(n_mu Xb + 1) + n_mu rho (n_s + 1)
+// + n_mu |sqrt(d2) - s*| (the common scale cancels in mu).  Below
+// d2min = (1.9 m)^2 the interval is wider than one bin, so such pairs (whose
+// clamped d2 would bias r) always go to the exact recheck.
+bool build_direct(const tpcf_binning &b, const Plan &pl, int smem_sm, int smem_block, int reserved,
+                  unsigned long long max_cat, DirectParams &d)
+{
+    const CountParams &p = pl.prm;
+    std::memset(&d, 0, sizeof(d));
+    if (!p.linear) return false;
+    const bool mu = p.n_mu > 1;
+    if (mu && p.los != TPCF_LOS_X) return false;
+    const double L = b.box_L;
+    const double q = std::ldexp(1.0, p.bits) / L;
+    const double qds = q * b.s_edges[1];
+    const float inv = (float)(1.0 / qds);
+    const double u24 = std::ldexp(1.0, -24);
+    const double kappa = std::fabs((double)inv * qds - 1.0);
+    const double Wmax = std::ldexp(1.0, p.bits) / (double)p.n_c + 1.0;
+    const double Xg = (double)(pl.K + 1) * Wmax;
+    const double Xb = Xg / qds * (1.0 + std::ldexp(1.0, -20));
+    const double E = 0.5 * ulp_f32(Xg) / qds * (1.0 + std::ldexp(1.0, -20)) + 0.5 * ulp_f32(Xb);
+    const double n_s = p.n_s, n_mu = p.n_mu;
+    const double e_d = 2.0 * E + 0.5 * ulp_f32(n_s + 2.0);
+    const double g3 = 3.0 * u24 / (1.0 - 3.0 * u24);
+    const double rho = std::pow(2.0, -22.5);
+    const double dsq = 2.0 * std::sqrt(3.0) * e_d + 6.0 * e_d * e_d + g3 * (n_s + 2.0);
+    const float tiny = (float)std::ldexp(1.0, -60);
+    const double eps_s = 2.0 * (dsq + rho * (n_s + 1.5) + kappa * (n_s + 1.0) + (double)tiny) + u24;
+    if (!(eps_s < 0.05)) return false;
+    d.cs = down_f(0.5 - eps_s);
+    if (mu) {
+        const double mm = 2.0 * (n_mu * 2.0 * E + 1.5 * ulp_f32(n_mu * Xb + 1.0) + n_mu * rho * (n_s + 1.0) +
+                                 n_mu * dsq);
+        if (!(mm < 0.05)) return false;
+        d.m = up_f(mm);
+        d.d2min = up_f((1.9 * (double)d.m) * (1.9 * (double)d.m));
+    }
+    d.tiny = tiny;
+    d.inv_qds = inv;
+    d.nmu = (float)p.n_mu;
+    d.hit = up_f((n_s + 0.01) * (n_s + 0.01));
+    d.s_top = (float)(8388608.0 + n_s);
+    d.C = mu ? 2 * p.n_mu + 2 : 1;
+    d.rows = p.n_s + 1;
+    // one block of 12 warps per SM (their registers fill the register file),
+    // with 32 histogram copies when they fit beside the warps' regions, else 16
+    const long long budget = (long long)std::min(smem_block, smem_sm - reserved);
+    for (int W : {12}) {
+        for (int R : {32, 16}) {
+            const long long need = (long long)pairdirect_smem_bytes(p, R, d.C, W);
+            if (need <= budget) {
+                d.R = R;
+                d.W = W;
+                d.smem = (int)need;
+                // in one unit a lane pairs at most 64 a-points with at most
+                // max_cat / 32 + 16 b-points (the tiles' slots), and 32 / R
+                // lanes share a counter copy
+                d.unit_pair_bound = (unsigned long long)DIRECT_ACHUNK *
+                                    (max_cat / (unsigned long long)R + 512ull / (unsigned long long)R + 16ull);
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
 }  // namespace tpcf

@@ -55,15 +55,33 @@ def _mocks_to_device(mocks):
     return out
 
 
-def _check_counts(ctx, tp, mocks, tb, ob, modes=(0, 1), terms=7):
+def _check_counts(ctx, tp, mocks, tb, ob, modes=(0, 1), terms=7, kernels=(0, 2), want_direct=None):
+    """Counts of both pair counters (TPCF_KERNEL_AUTO, which takes the direct counter where the
+    binning suits it, and TPCF_KERNEL_GENERAL) in every mode, bit for bit against the oracle."""
     dm = _mocks_to_device(mocks)
+    refs = [oracle.count_mock(mk.data, mk.randoms, ob) for mk in mocks]
+    out = None
+    for kern in kernels:
+        ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, kern)
+        try:
+            out = _check_counts_once(ctx, tp, refs, dm, modes, terms, tb)
+            info = ctx.tpcf_last_count_info()
+            if kern == tp.TPCF_KERNEL_GENERAL:
+                assert info["pair_kernel"] == tp.TPCF_KERNEL_GENERAL
+            elif want_direct is not None:
+                assert info["pair_kernel"] == (tp.TPCF_KERNEL_DIRECT if want_direct else tp.TPCF_KERNEL_GENERAL)
+        finally:
+            ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, tp.TPCF_KERNEL_AUTO)
+    return out
+
+
+def _check_counts_once(ctx, tp, refs, dm, modes, terms, tb):
     for mode in modes:
         out = ctx.tpcf_count(dm, tb, terms=terms, mode=mode)
         assert ctx.tpcf_sync() == tp.TPCF_OK
         info = ctx.tpcf_last_count_info()
         tot = 0
-        for m, mk in enumerate(mocks):
-            ref = oracle.count_mock(mk.data, mk.randoms, ob)
+        for m, ref in enumerate(refs):
             if terms & 1:
                 assert np.array_equal(out["dd"][m].cpu().numpy(), ref["DD"]), (mode, m, "DD")
                 tot += ref["DD"].sum()
@@ -92,7 +110,7 @@ def test_counts_periodic_s_only(tp, ctx):
     L = 500.0
     mocks = [synth.SMALL.make_mock(m, n_d=2500, M=2) for m in range(3)]
     tb, ob = _periodic(L, np.linspace(0, 100.0, 21), 1)
-    _check_counts(ctx, tp, mocks, tb, ob)
+    _check_counts(ctx, tp, mocks, tb, ob, want_direct=True)
 
 
 def test_counts_periodic_s_mu(tp, ctx):
@@ -101,7 +119,7 @@ def test_counts_periodic_s_mu(tp, ctx):
     w = synth.Workload("t", 31, 2, "periodic", L, (0, 0, 0), 3000, 2, 80.0, 40, 10, "x", n_parent=4e-5, sigma=3.0)
     mocks = [w.make_mock(m) for m in range(2)]
     tb, ob = _periodic(L, w.s_edges, 10)
-    _check_counts(ctx, tp, mocks, tb, ob)
+    _check_counts(ctx, tp, mocks, tb, ob, want_direct=True)
 
 
 @pytest.mark.parametrize("subdiv", [1, 2, 3, 4])
@@ -200,7 +218,18 @@ def test_binning_beyond_shared_memory_refused(tp, ctx):
     assert ctx.tpcf_sync() == tp.TPCF_OK
 
 
-def test_counts_golden_edge_pairs(tp, ctx):
+@pytest.mark.parametrize("kernel", [0, 2])
+def test_counts_golden_edge_pairs(tp, ctx, kernel):
+    """Hand-worked pairs at exact bin edges, through the default counter (the direct one for the periodic
+    section's linear bins) and the general one."""
+    ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, kernel)
+    try:
+        _golden_edge_pairs(tp, ctx)
+    finally:
+        ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, tp.TPCF_KERNEL_AUTO)
+
+
+def _golden_edge_pairs(tp, ctx):
     g = json.load(open(os.path.join(GOLDEN, "edge_pairs.json")))
     for section in ("periodic", "open_midpoint"):
         s = g[section]
@@ -239,6 +268,19 @@ def test_counts_duplicates_tiny_and_empty(tp, ctx):
     cases = [synth.Mock(dup, [dup[:100], base]), synth.Mock(tiny, [tiny, empty]), synth.Mock(empty, [base, tiny]),
              synth.Mock(base, [empty, empty])]
     _check_counts(ctx, tp, cases, tb, ob)
+
+
+def test_counts_duplicates_linear_bins(tp, ctx):
+    """Coincident and near-coincident points (s = 0 and s of a few grid units, where the direct counter's
+    mu interval is widened past one bin) with linear bins and mu bins: both counters against the oracle."""
+    L = 200.0
+    rng = np.random.default_rng(11)
+    base = rng.random((60, 3)) * L
+    near = base + rng.normal(size=base.shape) * 1e-7 * L    # a few hundred grid units apart
+    dup = np.concatenate([np.repeat(base, 5, axis=0), np.mod(near, L)])
+    tb, ob = _periodic(L, np.linspace(0.0, 40.0, 9), 6)
+    cases = [synth.Mock(dup, [dup[:150], np.mod(near, L)]), synth.Mock(base, [np.repeat(base[:10], 3, axis=0), base])]
+    _check_counts(ctx, tp, cases, tb, ob, want_direct=True)
 
 
 def test_u32_input_matches_float_input(tp, ctx):

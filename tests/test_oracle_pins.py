@@ -473,6 +473,40 @@ def test_multipole_matrix_invariants():
         assert np.allclose(m[i * n_s:(i + 1) * n_s], want, rtol=5e-4, atol=1e-4), ell   # O(dmu^2) error
 
 
+def test_project_hand_worked():
+    """A non-square map worked by hand: y[m] = P xi[m] for P of 2 x 3 and two mocks (a transposed
+    or row-swapped product gives other numbers or the wrong shape)."""
+    P = np.array([[1.0, 2.0, 0.0],
+                  [0.0, -1.0, 3.0]])
+    xi = np.array([[1.0, 10.0, 100.0],
+                   [-2.0, 0.5, 4.0]])
+    y = oracle.project(P, xi)
+    assert y.shape == (2, 2)
+    # mock 0: (1 + 20 + 0, 0 - 10 + 300); mock 1: (-2 + 1 + 0, 0 - 0.5 + 12)
+    assert np.array_equal(y, np.array([[21.0, 290.0], [-1.0, 11.5]]))
+
+
+def test_project_recovers_multipole_amplitudes_per_mock():
+    """Mocks whose xi rows are bin averages of sum_l A_l^(m)(s) P_l(|mu|) with their own amplitudes:
+    project(multipole_matrix, xi) returns every mock's (A_0, A_2, A_4) in the (ell, s) row order."""
+    from numpy.polynomial import legendre as npl
+    n_s, n_mu, ells = 2, 400, (0, 2, 4)
+    P = oracle.multipole_matrix(n_s, n_mu, ells)
+    e = np.arange(n_mu + 1) / n_mu
+    rng = np.random.default_rng(7)
+    amps = rng.normal(size=(3, len(ells), n_s))               # [mock][ell][s]
+    xi = np.zeros((3, n_s * n_mu))
+    for m in range(3):
+        for i, ell in enumerate(ells):
+            anti = npl.Legendre.basis(ell).integ()
+            avg = (anti(e[1:]) - anti(e[:-1])) * n_mu
+            for k in range(n_s):
+                xi[m, k * n_mu:(k + 1) * n_mu] += amps[m, i, k] * avg
+    y = oracle.project(P, xi)
+    assert y.shape == (3, len(ells) * n_s)
+    assert np.allclose(y, amps.reshape(3, -1), rtol=1e-4, atol=1e-4)   # O(dmu^2) bin-average error
+
+
 # ---------------------------------------------------------------------------
 # covariance of covariance and chi^2 (Sect. 3, Sect. 5.3), pinned by Monte Carlo
 # ---------------------------------------------------------------------------
