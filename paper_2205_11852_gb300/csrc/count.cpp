@@ -256,14 +256,14 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
 
     // launch shape (host queries, outside any capture)
     if (S.direct) {
-        cudaError_t e = pairdirect_set_attrs(prm, S.dp.R, S.dp.W, S.dp.smem);
+        cudaError_t e = pairdirect_set_attrs(S.dp, prm.n_mu > 1);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "pairdirect_set_attrs");
-        const int occ = pairdirect_max_blocks_per_sm(prm, S.dp.R, S.dp.W, S.dp.smem);
+        const int occ = pairdirect_max_blocks_per_sm(S.dp, prm.n_mu > 1);
         if (occ < 1) return fail(ctx, TPCF_ERR_CUDA, "the direct pair counter does not fit on an SM");
         S.smem = S.dp.smem;
         S.blocks = ctx->n_sm * occ;
         // units per block claim: a few claims per block, at most 2^30 pairs per counter
-        const unsigned long long by_work = std::max<unsigned long long>(1, S.units_bound / (4ull * S.blocks));
+        const unsigned long long by_work = std::max<unsigned long long>(1, S.units_bound / (3ull * S.blocks));
         const unsigned long long by_wrap = std::max<unsigned long long>(1, (1ull << 30) / S.dp.unit_pair_bound);
         S.claim_units = (int)std::min<unsigned long long>({by_work, by_wrap, 4096ull});
         return TPCF_OK;

@@ -8,8 +8,8 @@
 // memory, streams the b-points of the neighbourhood (the self cell of an
 // auto count as it is, every other neighbour cell through a filter that
 // keeps a point only if its distance to the a-chunk's bounding box is below
-// the last edge) into its own buffer, and counts every full tile of 256
-// b-points (8 per lane) against the a-chunk as soon as it is there.  The
+// the last edge) into its own buffer, and counts every full tile of 128
+// b-points (4 per lane) against the a-chunk as soon as it is there.  The
 // warps of a block share one histogram, so a block works through a chunk of
 // consecutive units of one term at a time (units are ordered by term); block
 // barriers come only between such chunks.
@@ -44,7 +44,8 @@ namespace tpcf {
 
 namespace {
 
-constexpr int NP = 8;               // b-points per lane: four packed pairs
+constexpr int NP = 4;               // b-points per lane
+constexpr int NQ = NP / 2;          // packed pairs per lane
 constexpr int TB = 32 * NP;         // b-points per tile
 constexpr int BUF = TB + 128;       // per-warp b buffer: a tile plus one filter pass
 constexpr int XCAP = 96;            // per-warp list of pairs awaiting the exact recheck
@@ -95,86 +96,132 @@ struct ARec {
     float2 nax, nay, naz, cp, cm;
 };
 
-// The histogram addresses of the pairs (b_p, a), (b_p', a); amb gains the
-// uncertainty of either.  Hot path.
-template <bool MU>
-__device__ __forceinline__ void pair2(const float2 bx, const float2 by, const float2 bz, const ARec &a,
-                                      const DirectParams &dp, uint32_t KS, uint32_t KT, uint32_t Kl, uint32_t &a0,
-                                      uint32_t &a1, bool &amb)
+// Histogram address of a pair with s-row word bits(S) and signed-mu-column
+// word bits(T-): (bits(S) << LS) + (bits(T-) << LT) + Kl, with LT = log2(4 R)
+// and LS = LT + log2(C), so that the row and column strides are shifts.
+template <int R, int LOGC>
+struct Sh {
+    static constexpr int LT = R == 32 ? 7 : (R == 16 ? 6 : -1);
+    static constexpr int LS = LT + LOGC;
+    static_assert(LT > 0, "R is 16 or 32");
+};
+
+__device__ __forceinline__ uint64_t u64of(float2 v) { return *reinterpret_cast<uint64_t *>(&v); }
+
+// Constant operand pairs of the packed arithmetic.
+struct K2 {
+    uint64_t tiny, ms, m1, mh, mt, nm;
+};
+
+// One packed pair of pairs (b_p, a), (b_p', a) in hand-written PTX (hot
+// path): the histogram addresses of both, and flag bits 0 and 1 set when the
+// first or the second is uncertain.  With mu bins (MU): the tiny addend, r = rsqrt(d2) (MUFU), S,
+// the s residual, the mu interval floors T+, T-.
+template <bool MU, int LS, int LT>
+__device__ __forceinline__ void pair2(uint64_t bx, uint64_t by, uint64_t bz, const ARec &a, const K2 &k, float cs,
+                                      float stop, uint32_t Kl, uint32_t &a0, uint32_t &a1, uint32_t &flag)
 {
-    const float2 dx = __fadd2_rn(bx, a.nax), dy = __fadd2_rn(by, a.nay), dz = __fadd2_rn(bz, a.naz);
-    float2 d2 = MU ? __fmul2_rn(dx, dx) : __ffma2_rn(dx, dx, make_float2(dp.tiny, dp.tiny));
-    d2 = __ffma2_rn(dy, dy, d2);
-    d2 = __ffma2_rn(dz, dz, d2);
     if (MU) {
-        d2.x = fmaxf(d2.x, dp.d2min);
-        d2.y = fmaxf(d2.y, dp.d2min);
+        asm("{\n\t"
+            ".reg .b64 dx, dy, dz, d2, r, s, h, fs, xp, xm, tp, tm;\n\t"
+            ".reg .f32 d2x, d2y, rx, ry, sx, sy, fx, fy, px, py, mx, my;\n\t"
+            ".reg .pred p, q;\n\t"
+            ".reg .b32 ux, uy, vx, vy, f0, f1;\n\t"
+            "add.rn.f32x2 dx, %3, %6;\n\t"
+            "add.rn.f32x2 dy, %4, %7;\n\t"
+            "add.rn.f32x2 dz, %5, %8;\n\t"
+            "fma.rn.f32x2 d2, dx, dx, %11;\n\t"
+            "fma.rn.f32x2 d2, dy, dy, d2;\n\t"
+            "fma.rn.f32x2 d2, dz, dz, d2;\n\t"
+            "mov.b64 {d2x, d2y}, d2;\n\t"
+            "rsqrt.approx.ftz.f32 rx, d2x;\n\t"
+            "rsqrt.approx.ftz.f32 ry, d2y;\n\t"
+            "mov.b64 r, {rx, ry};\n\t"
+            "fma.rz.f32x2 s, d2, r, %12;\n\t"
+            "fma.rn.f32x2 h, s, %13, %14;\n\t"
+            "fma.rn.f32x2 fs, d2, r, h;\n\t"
+            "fma.rn.f32x2 xp, %3, %16, %9;\n\t"
+            "fma.rn.f32x2 xm, %3, %16, %10;\n\t"
+            "fma.rz.f32x2 tp, xp, r, %15;\n\t"
+            "fma.rz.f32x2 tm, xm, r, %15;\n\t"
+            "mov.b64 {sx, sy}, s;\n\t"
+            "mov.b64 {fx, fy}, fs;\n\t"
+            "mov.b64 {px, py}, tp;\n\t"
+            "mov.b64 {mx, my}, tm;\n\t"
+            "abs.f32 fx, fx;\n\t"
+            "abs.f32 fy, fy;\n\t"
+            "setp.gtu.f32 p, fx, %17;\n\t"
+            "setp.neu.or.f32 p, px, mx, p;\n\t"
+            "setp.gtu.f32 q, fy, %17;\n\t"
+            "setp.neu.or.f32 q, py, my, q;\n\t"
+            "selp.u32 f0, 1, 0, p;\n\t"
+            "selp.u32 f1, 2, 0, q;\n\t"
+            "or.b32 %2, f0, f1;\n\t"
+            "min.f32 sx, sx, %18;\n\t"
+            "min.f32 sy, sy, %18;\n\t"
+            "mov.b32 ux, sx;\n\t"
+            "mov.b32 uy, sy;\n\t"
+            "mov.b32 vx, mx;\n\t"
+            "mov.b32 vy, my;\n\t"
+            "shl.b32 ux, ux, %20;\n\t"
+            "shl.b32 uy, uy, %20;\n\t"
+            "shl.b32 vx, vx, %21;\n\t"
+            "shl.b32 vy, vy, %21;\n\t"
+            "add.u32 ux, ux, vx;\n\t"
+            "add.u32 uy, uy, vy;\n\t"
+            "add.u32 %0, ux, %19;\n\t"
+            "add.u32 %1, uy, %19;\n\t"
+            "}"
+            : "=r"(a0), "=r"(a1), "=r"(flag)
+            : "l"(bx), "l"(by), "l"(bz), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(u64of(a.cp)),
+              "l"(u64of(a.cm)), "l"(k.tiny), "l"(k.ms), "l"(k.m1), "l"(k.mh), "l"(k.mt), "l"(k.nm), "f"(cs), "f"(stop),
+              "r"(Kl), "n"(LS), "n"(LT));
+    } else {
+        asm("{\n\t"
+            ".reg .b64 dx, dy, dz, d2, r, s, h, fs;\n\t"
+            ".reg .f32 d2x, d2y, rx, ry, sx, sy, fx, fy;\n\t"
+            ".reg .pred p, q;\n\t"
+            ".reg .b32 ux, uy, f0, f1;\n\t"
+            "add.rn.f32x2 dx, %3, %6;\n\t"
+            "add.rn.f32x2 dy, %4, %7;\n\t"
+            "add.rn.f32x2 dz, %5, %8;\n\t"
+            "fma.rn.f32x2 d2, dx, dx, %9;\n\t"
+            "fma.rn.f32x2 d2, dy, dy, d2;\n\t"
+            "fma.rn.f32x2 d2, dz, dz, d2;\n\t"
+            "mov.b64 {d2x, d2y}, d2;\n\t"
+            "rsqrt.approx.ftz.f32 rx, d2x;\n\t"
+            "rsqrt.approx.ftz.f32 ry, d2y;\n\t"
+            "mov.b64 r, {rx, ry};\n\t"
+            "fma.rz.f32x2 s, d2, r, %10;\n\t"
+            "fma.rn.f32x2 h, s, %11, %12;\n\t"
+            "fma.rn.f32x2 fs, d2, r, h;\n\t"
+            "mov.b64 {sx, sy}, s;\n\t"
+            "mov.b64 {fx, fy}, fs;\n\t"
+            "abs.f32 fx, fx;\n\t"
+            "abs.f32 fy, fy;\n\t"
+            "setp.gtu.f32 p, fx, %13;\n\t"
+            "setp.gtu.f32 q, fy, %13;\n\t"
+            "selp.u32 f0, 1, 0, p;\n\t"
+            "selp.u32 f1, 2, 0, q;\n\t"
+            "or.b32 %2, f0, f1;\n\t"
+            "min.f32 sx, sx, %14;\n\t"
+            "min.f32 sy, sy, %14;\n\t"
+            "mov.b32 ux, sx;\n\t"
+            "mov.b32 uy, sy;\n\t"
+            "shl.b32 ux, ux, %16;\n\t"
+            "shl.b32 uy, uy, %16;\n\t"
+            "add.u32 %0, ux, %15;\n\t"
+            "add.u32 %1, uy, %15;\n\t"
+            "}"
+            : "=r"(a0), "=r"(a1), "=r"(flag)
+            : "l"(bx), "l"(by), "l"(bz), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(k.tiny),
+              "l"(k.ms), "l"(k.m1), "l"(k.mh), "f"(cs), "f"(stop), "r"(Kl), "n"(LS));
     }
-    float2 r;
-    r.x = rsqrt_approx(d2.x);
-    r.y = rsqrt_approx(d2.y);
-    const float2 S = __ffma2_rz(d2, r, make_float2(MAG_S, MAG_S));
-    const float2 H = __ffma2_rn(S, make_float2(-1.0f, -1.0f), make_float2(MAG_S - 0.5f, MAG_S - 0.5f));
-    const float2 fs = __ffma2_rn(d2, r, H);   // u - floor(u) - 1/2
-    a0 = __float_as_uint(fminf(S.x, dp.s_top)) * KS + Kl;
-    a1 = __float_as_uint(fminf(S.y, dp.s_top)) * KS + Kl;
-    bool u = (fabsf(fs.x) > dp.cs) | (fabsf(fs.y) > dp.cs);
-    if (MU) {
-        const float2 nm = make_float2(dp.nmu, dp.nmu);
-        const float2 dxp = __ffma2_rn(bx, nm, a.cp), dxm = __ffma2_rn(bx, nm, a.cm);
-        const float2 Tp = __ffma2_rz(dxp, r, make_float2(MAG_T, MAG_T));
-        const float2 Tm = __ffma2_rz(dxm, r, make_float2(MAG_T, MAG_T));
-        u = u | (Tp.x != Tm.x) | (Tp.y != Tm.y);
-        a0 += __float_as_uint(Tm.x) * KT;
-        a1 += __float_as_uint(Tm.y) * KT;
-    }
-    amb = amb | u;
 }
 
-// The same pair of pairs, per pair: address, uncertain, s bin certain, S.
-// Rare path.
-template <bool MU>
-__device__ __forceinline__ void pair2_flags(const float2 bx, const float2 by, const float2 bz, const ARec &a,
-                                            const DirectParams &dp, uint32_t KS, uint32_t KT, uint32_t Kl,
-                                            uint32_t (&ad)[2], bool (&amb)[2], bool (&sok)[2], float (&Sv)[2])
-{
-    const float2 dx = __fadd2_rn(bx, a.nax), dy = __fadd2_rn(by, a.nay), dz = __fadd2_rn(bz, a.naz);
-    float2 d2 = MU ? __fmul2_rn(dx, dx) : __ffma2_rn(dx, dx, make_float2(dp.tiny, dp.tiny));
-    d2 = __ffma2_rn(dy, dy, d2);
-    d2 = __ffma2_rn(dz, dz, d2);
-    if (MU) {
-        d2.x = fmaxf(d2.x, dp.d2min);
-        d2.y = fmaxf(d2.y, dp.d2min);
-    }
-    float2 r;
-    r.x = rsqrt_approx(d2.x);
-    r.y = rsqrt_approx(d2.y);
-    const float2 S = __ffma2_rz(d2, r, make_float2(MAG_S, MAG_S));
-    const float2 H = __ffma2_rn(S, make_float2(-1.0f, -1.0f), make_float2(MAG_S - 0.5f, MAG_S - 0.5f));
-    const float2 fs = __ffma2_rn(d2, r, H);
-    ad[0] = __float_as_uint(fminf(S.x, dp.s_top)) * KS + Kl;
-    ad[1] = __float_as_uint(fminf(S.y, dp.s_top)) * KS + Kl;
-    sok[0] = !(fabsf(fs.x) > dp.cs);
-    sok[1] = !(fabsf(fs.y) > dp.cs);
-    amb[0] = !sok[0];
-    amb[1] = !sok[1];
-    Sv[0] = S.x;
-    Sv[1] = S.y;
-    if (MU) {
-        const float2 nm = make_float2(dp.nmu, dp.nmu);
-        const float2 dxp = __ffma2_rn(bx, nm, a.cp), dxm = __ffma2_rn(bx, nm, a.cm);
-        const float2 Tp = __ffma2_rz(dxp, r, make_float2(MAG_T, MAG_T));
-        const float2 Tm = __ffma2_rz(dxm, r, make_float2(MAG_T, MAG_T));
-        amb[0] = amb[0] | (Tp.x != Tm.x);
-        amb[1] = amb[1] | (Tp.y != Tm.y);
-        ad[0] += __float_as_uint(Tm.x) * KT;
-        ad[1] += __float_as_uint(Tm.y) * KT;
-    }
-}
-
-// Per-lane histogram address constants: address = bits(S) KS + bits(T-) KT + Kl.
+// Per-lane histogram address constants (see Sh).
 struct Addr {
-    uint32_t KS, KT, Kl;
+    uint32_t Kl;
     uint32_t hb;      // histogram base (shared address) + 4 (lane mod R)
     uint32_t dump;    // this lane's word in the spare last row
 };
@@ -195,8 +242,10 @@ __device__ __forceinline__ ARec load_a(const float4 *arec, uint32_t ai)
                 r2};
 }
 
+__device__ __forceinline__ void xl_put(uint2 *xl, uint32_t i, uint32_t ia, uint32_t ib) { xl[i] = make_uint2(ia, ib); }
+
 // exact recheck of the n listed pairs, one per lane; returns the number rechecked by this lane
-template <bool MU, int R>
+template <bool MU, int R, int LOGC>
 __device__ __forceinline__ uint32_t recheck(const CountParams &prm, const DirectParams &dp, const Mesh &m,
                                             const unsigned long long *T, const uint2 *xl, uint32_t n, uint32_t hb,
                                             int lane)
@@ -209,33 +258,25 @@ __device__ __forceinline__ uint32_t recheck(const CountParams &prm, const Direct
         cnt++;
         if (bin >= 0) {
             const uint32_t k = (uint32_t)bin / (uint32_t)prm.n_mu, j = (uint32_t)bin % (uint32_t)prm.n_mu;
-            const uint32_t col = MU ? j + (uint32_t)prm.n_mu + 1u : 0u;
-            red_add(hb + 4u * (uint32_t)R * (k * (uint32_t)dp.C + col), 1u);
+            const uint32_t col = MU ? j + (uint32_t)dp.CO : 0u;
+            red_add(hb + (k << Sh<R, LOGC>::LS) + (col << Sh<R, LOGC>::LT), 1u);
         }
     }
     __syncwarp();
     return cnt;
 }
 
-// Every pair of the a-chunk (na points from sorted index a0) with the first nb
-// entries of the warp's buffer; CHK: only pairs a < b count (the self cell
-// of an auto count).  The a-points whose group of 8 pairs per lane holds an
-// uncertain pair are marked and handled after the tile: their adds are taken
-// back and they join the recheck list, unless their s bin alone is certainly
-// at or past the last edge (their add went to the spare row).
-template <bool MU, int R, bool CHK>
-__device__ __forceinline__ void tile(const CountParams &prm, const DirectParams &dp, const Mesh &m,
-                                     const unsigned long long *T, const WarpMem &wm, const Addr &ad, uint32_t nb,
-                                     uint32_t na, uint32_t a0, int lane, uint32_t &n_list,
-                                     unsigned long long &n_exact, unsigned long long &n_cand)
+// this lane's b-points of the tile (buffer slots 32 p + lane, packed in
+// pairs p = 2q, 2q + 1); slots at or past nb are padding
+__device__ __forceinline__ void load_tile(const float4 *buf, uint32_t nb, int lane, float2 (&BX)[NQ], float2 (&BY)[NQ],
+                                          float2 (&BZ)[NQ])
 {
-    float2 BX[4], BY[4], BZ[4];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < NQ; q++) {
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const uint32_t s = 32u * (uint32_t)(2 * q + h) + (uint32_t)lane;
-            const float4 v = s < nb ? wm.buf[s] : make_float4(FAR, FAR, FAR, 0.0f);
+            const float4 v = s < nb ? buf[s] : make_float4(FAR, FAR, FAR, 0.0f);
             if (h) {
                 BX[q].y = v.x;
                 BY[q].y = v.y;
@@ -247,6 +288,21 @@ __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams 
             }
         }
     }
+}
+
+// Every pair of the a-chunk (na points from sorted index a0) with the first nb
+// entries of the warp's buffer; CHK: only pairs a < b count (the self cell
+// of an auto count).  A partial tile skips the packed pairs whose slots are
+// all padding.  An uncertain pair's add is taken back at once (its address is
+// still in registers) and the pair joins the recheck list.
+template <bool MU, int R, int LOGC, bool CHK>
+__device__ __forceinline__ void tile(const CountParams &prm, const DirectParams &dp, const Mesh &m,
+                                     const unsigned long long *T, const WarpMem &wm, const Addr &ad, uint32_t nb,
+                                     uint32_t na, uint32_t a0, int lane, uint32_t &n_list,
+                                     unsigned long long &n_exact, unsigned long long &n_cand)
+{
+    float2 BX[NQ], BY[NQ], BZ[NQ];
+    load_tile(wm.buf, nb, lane, BX, BY, BZ);
     uint32_t IB[NP];
     if (CHK) {
 #pragma unroll
@@ -255,57 +311,79 @@ __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams 
             IB[p] = s < nb ? __float_as_uint(wm.buf[s].w) : 0u;
         }
     }
-    n_cand += (unsigned long long)nb * na;
-    unsigned long long marked = 0;   // a-points with an uncertain pair (warp-uniform)
-#pragma unroll 1
-    for (uint32_t ai = 0; ai < na; ai++) {
-        const ARec a = load_a(wm.arec, ai);
-        bool amb = false;
+    // slot p of this lane holds a b-point (not padding): bit p
+    uint32_t live = 0;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            uint32_t x0, x1;
-            pair2<MU>(BX[q], BY[q], BZ[q], a, dp, ad.KS, ad.KT, ad.Kl, x0, x1, amb);
-            if (CHK) {
-                const uint32_t ia = a0 + ai;
-                if (!(ia < IB[2 * q])) x0 = ad.dump;
-                if (!(ia < IB[2 * q + 1])) x1 = ad.dump;
-            }
-            red_add(x0, 1u);
-            red_add(x1, 1u);
-        }
-        if (__any_sync(0xffffffffu, amb)) marked |= 1ull << ai;
-    }
+    for (int p = 0; p < NP; p++) live |= (32u * (uint32_t)p + (uint32_t)lane < nb ? 1u : 0u) << p;
+    n_cand += (unsigned long long)nb * na;
+    constexpr int LS = Sh<R, LOGC>::LS, LT = Sh<R, LOGC>::LT;
+    const K2 k2{u64of(make_float2(dp.tiny, dp.tiny)), u64of(make_float2(MAG_S, MAG_S)), u64of(make_float2(-1.0f, -1.0f)),
+                u64of(make_float2(MAG_S - 0.5f, MAG_S - 0.5f)), u64of(make_float2(MAG_T, MAG_T)),
+                u64of(make_float2(dp.nmu, dp.nmu))};
+    const uint32_t nq = (nb + 63u) >> 6;   // packed pairs of this lane with any slot below nb
     const uint32_t lt = (1u << lane) - 1u;
-    while (marked) {
-        const uint32_t ai = (uint32_t)(__ffsll((long long)marked) - 1);
-        marked &= marked - 1ull;
-        const ARec a = load_a(wm.arec, ai);
+    // the uncertain pairs of a-point ai (flags fl, addresses xs): each add is
+    // taken back and the pair joins the recheck list
+    auto settle = [&](uint32_t ai, uint32_t fl, const uint32_t (&xs)[NP]) {
         const uint32_t ia = a0 + ai;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            uint32_t adr[2];
-            bool amb[2], sok[2];
-            float Sv[2];
-            pair2_flags<MU>(BX[q], BY[q], BZ[q], a, dp, ad.KS, ad.KT, ad.Kl, adr, amb, sok, Sv);
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const uint32_t s = 32u * (uint32_t)(2 * q + h) + (uint32_t)lane;
-                const bool in_tile = s < nb;
-                const uint32_t ib = in_tile ? __float_as_uint(wm.buf[s].w) : 0u;
-                const bool valid = in_tile && (!CHK || ia < ib);
-                const bool beyond = sok[h] && Sv[h] >= dp.s_top;
-                const bool x = valid && amb[h] && !beyond;
-                if (x) red_add(adr[h], 0xFFFFFFFFu);
-                const unsigned mk = __ballot_sync(0xffffffffu, x);
-                if (x) wm.xl[n_list + __popc(mk & lt)] = make_uint2(ia, ib);
+        for (int p = 0; p < NP; p++) {
+            const bool x = (fl >> p) & 1u;
+            const unsigned mk = __ballot_sync(0xffffffffu, x);
+            if (mk) {
+                if (x) {
+                    red_add(xs[p], 0xFFFFFFFFu);
+                    xl_put(wm.xl, n_list + __popc(mk & lt), ia,
+                           __float_as_uint(wm.buf[32u * (uint32_t)p + (uint32_t)lane].w));
+                }
                 n_list += __popc(mk);
                 if (n_list >= XCAP - 32) {
-                    n_exact += recheck<MU, R>(prm, dp, m, T, wm.xl, n_list, ad.hb, lane);
+                    n_exact += recheck<MU, R, LOGC>(prm, dp, m, T, wm.xl, n_list, ad.hb, lane);
                     n_list = 0;
                 }
             }
         }
+    };
+    // The flags of a-point ai are examined while a-point ai + 1 is computed,
+    // so that no pass waits on its own pairs' chain before the next begins.
+    uint32_t pxs[NP];
+    uint32_t pfl = 0;
+#pragma unroll
+    for (int p = 0; p < NP; p++) pxs[p] = ad.dump;
+#pragma unroll 1
+    for (uint32_t ai = 0; ai < na; ai++) {
+        const ARec a = load_a(wm.arec, ai);
+        uint32_t xs[NP];
+        uint32_t fl = 0;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            xs[2 * q] = xs[2 * q + 1] = ad.dump;
+            if (q == 0 || (uint32_t)q < nq) {
+                uint32_t f;
+                pair2<MU, LS, LT>(u64of(BX[q]), u64of(BY[q]), u64of(BZ[q]), a, k2, dp.cs, dp.s_top, ad.Kl,
+                                  xs[2 * q], xs[2 * q + 1], f);
+                if (CHK) {
+                    const uint32_t ia = a0 + ai;
+                    if (!(ia < IB[2 * q])) {
+                        xs[2 * q] = ad.dump;
+                        f &= 2u;
+                    }
+                    if (!(ia < IB[2 * q + 1])) {
+                        xs[2 * q + 1] = ad.dump;
+                        f &= 1u;
+                    }
+                }
+                red_add(xs[2 * q], 1u);
+                red_add(xs[2 * q + 1], 1u);
+                fl |= f << (2 * q);
+            }
+        }
+        if (__any_sync(0xffffffffu, pfl)) settle(ai - 1, pfl, pxs);
+        pfl = fl & live;
+#pragma unroll
+        for (int p = 0; p < NP; p++) pxs[p] = xs[p];
     }
+    if (__any_sync(0xffffffffu, pfl)) settle(na - 1, pfl, pxs);
     __syncwarp();
 }
 
@@ -319,7 +397,7 @@ __device__ __forceinline__ float4 bpoint(const DirectParams &dp, uint32_t i, uin
 }
 
 // The unit: a-chunk [un.a0, un.a1) of cell un.cell against the term's neighbourhood.
-template <bool MU, int R>
+template <bool MU, int R, int LOGC>
 __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams &dp, const Mesh &m,
                                      const unsigned long long *T, const WarpMem &wm, const Addr &ad, const Unit &un,
                                      const Term &tm, int lane, uint32_t &n_list, unsigned long long &n_exact,
@@ -444,7 +522,7 @@ __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams 
             wm.buf[e2] = bpoint(dp, (uint32_t)g, m.us[g], m.us[N + g], m.us[2 * N + g], ox, oy, oz);
         }
         __syncwarp();
-        tile<MU, R, true>(prm, dp, m, T, wm, ad, nb, na, a0, lane, n_list, n_exact, n_cand);
+        tile<MU, R, LOGC, true>(prm, dp, m, T, wm, ad, nb, na, a0, lane, n_list, n_exact, n_cand);
     }
     // the neighbour runs: four raw points per lane per pass (their twelve
     // loads in flight together), survivors appended to the buffer, a tile
@@ -481,7 +559,7 @@ __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams 
         }
         if (nbuf >= TB) {
             __syncwarp();
-            tile<MU, R, false>(prm, dp, m, T, wm, ad, TB, na, a0, lane, n_list, n_exact, n_cand);
+            tile<MU, R, LOGC, false>(prm, dp, m, T, wm, ad, TB, na, a0, lane, n_list, n_exact, n_cand);
             // the leftovers (fewer than 128) move to the front
             const uint32_t left = nbuf - TB;
             float4 v[4];
@@ -501,12 +579,12 @@ __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams 
     }
     if (nbuf) {
         __syncwarp();
-        tile<MU, R, false>(prm, dp, m, T, wm, ad, nbuf, na, a0, lane, n_list, n_exact, n_cand);
+        tile<MU, R, LOGC, false>(prm, dp, m, T, wm, ad, nbuf, na, a0, lane, n_list, n_exact, n_cand);
     }
 }
 
 // drain the table into term t's int64 histogram and clear it (whole block)
-template <bool MU, int R>
+template <bool MU, int R, int LOGC>
 __device__ __forceinline__ unsigned long long drain(const CountParams &prm, const DirectParams &dp,
                                                     const Term *terms, uint32_t *hist, uint32_t hwords, int t)
 {
@@ -517,15 +595,16 @@ __device__ __forceinline__ unsigned long long drain(const CountParams &prm, cons
     for (int b = threadIdx.x; b < prm.nbin; b += blockDim.x) {
         const int k = b / n_mu, j = b % n_mu;
         unsigned long long sum = 0;
-        const uint32_t c1 = MU ? (uint32_t)(j + n_mu + 1) : 0u, c2 = MU ? (uint32_t)(n_mu - j) : 0u;
-        const uint4 *w1 = (const uint4 *)(hist + ((uint32_t)k * (uint32_t)dp.C + c1) * (uint32_t)R);
+        // mu bin j: signed columns j and -1 - j
+        const uint32_t c1 = MU ? (uint32_t)(j + dp.CO) : 0u, c2 = MU ? (uint32_t)(dp.CO - 1 - j) : 0u;
+        const uint4 *w1 = (const uint4 *)(hist + (((uint32_t)k << LOGC) + c1) * (uint32_t)R);
 #pragma unroll
         for (int c = 0; c < R / 4; c++) {
             const uint4 v = w1[c];
             sum += (unsigned long long)v.x + v.y + v.z + v.w;
         }
         if (MU) {
-            const uint4 *w2 = (const uint4 *)(hist + ((uint32_t)k * (uint32_t)dp.C + c2) * (uint32_t)R);
+            const uint4 *w2 = (const uint4 *)(hist + (((uint32_t)k << LOGC) + c2) * (uint32_t)R);
 #pragma unroll
             for (int c = 0; c < R / 4; c++) {
                 const uint4 v = w2[c];
@@ -541,7 +620,7 @@ __device__ __forceinline__ unsigned long long drain(const CountParams &prm, cons
     return binned;
 }
 
-template <bool MU, int R, int W>
+template <bool MU, int R, int W, int LOGC>
 __global__ void __launch_bounds__(W * 32, 1)
     pairdirect_kernel(const __grid_constant__ CountParams prm, const __grid_constant__ DirectParams dp, const Mesh m,
                       const Term *__restrict__ terms, const Unit *__restrict__ units,
@@ -561,16 +640,12 @@ __global__ void __launch_bounds__(W * 32, 1)
     const WarpMem wm{(float4 *)(wr + o.arec), (float4 *)(wr + o.buf), (uint2 *)(wr + o.runs), (uint2 *)(wr + o.xl)};
     Addr ad;
     ad.hb = saddr(dsm) + o.hist + 4u * ((uint32_t)lane & (uint32_t)(R - 1));
-    if (MU) {
-        ad.KT = 4u * (uint32_t)R;
-        ad.KS = ad.KT * (uint32_t)dp.C;
-        ad.Kl = ad.hb + ad.KT * (uint32_t)(prm.n_mu + 1) - ad.KS * MAG_S_BITS - ad.KT * MAG_T_BITS;
-    } else {
-        ad.KT = 0u;
-        ad.KS = 4u * (uint32_t)R;
-        ad.Kl = ad.hb - ad.KS * MAG_S_BITS;
-    }
-    ad.dump = ad.hb + ad.KS * (uint32_t)prm.n_s;
+    constexpr int LS = Sh<R, LOGC>::LS, LT = Sh<R, LOGC>::LT;
+    if (MU)
+        ad.Kl = ad.hb + ((uint32_t)dp.CO << LT) - (MAG_S_BITS << LS) - (MAG_T_BITS << LT);
+    else
+        ad.Kl = ad.hb - (MAG_S_BITS << LS);
+    ad.dump = ad.hb + ((uint32_t)prm.n_s << LS);
     uint32_t n_list = 0;
     unsigned long long n_exact = 0, n_cand = 0, binned = 0;
 
@@ -619,10 +694,10 @@ __global__ void __launch_bounds__(W * 32, 1)
             const unsigned long long seg = (unsigned long long)(e - s) * dp.unit_pair_bound;
             if (cur_term >= 0 && (t != cur_term || since + seg >= (1ull << 31))) {
                 if (n_list) {   // pending rechecks belong to the table being drained
-                    n_exact += recheck<MU, R>(prm, dp, m, Tsh, wm.xl, n_list, ad.hb, lane);
+                    n_exact += recheck<MU, R, LOGC>(prm, dp, m, Tsh, wm.xl, n_list, ad.hb, lane);
                     n_list = 0;
                 }
-                binned += drain<MU, R>(prm, dp, terms, hist, hwords, cur_term);
+                binned += drain<MU, R, LOGC>(prm, dp, terms, hist, hwords, cur_term);
                 since = 0;
             }
             cur_term = t;
@@ -635,7 +710,7 @@ __global__ void __launch_bounds__(W * 32, 1)
                 if (lane == 0) u = atomicAdd(&misc[1], 1u);
                 u = __shfl_sync(0xffffffffu, u, 0);
                 if (u >= e) break;
-                unit<MU, R>(prm, dp, m, Tsh, wm, ad, units[u], tm, lane, n_list, n_exact, n_cand);
+                unit<MU, R, LOGC>(prm, dp, m, Tsh, wm, ad, units[u], tm, lane, n_list, n_exact, n_cand);
             }
             __syncthreads();
             s = e;
@@ -643,10 +718,10 @@ __global__ void __launch_bounds__(W * 32, 1)
     }
     if (cur_term >= 0) {
         if (n_list) {
-            n_exact += recheck<MU, R>(prm, dp, m, Tsh, wm.xl, n_list, ad.hb, lane);
+            n_exact += recheck<MU, R, LOGC>(prm, dp, m, Tsh, wm.xl, n_list, ad.hb, lane);
             n_list = 0;
         }
-        binned += drain<MU, R>(prm, dp, terms, hist, hwords, cur_term);
+        binned += drain<MU, R, LOGC>(prm, dp, terms, hist, hwords, cur_term);
     }
     unsigned long long ex = n_exact, bn = binned, cd = lane == 0 ? n_cand : 0ull;
 #pragma unroll
@@ -662,21 +737,21 @@ __global__ void __launch_bounds__(W * 32, 1)
     }
 }
 
-template <bool MU, int R, int W>
+template <bool MU, int R, int W, int LOGC>
 void *dkernel()
 {
-    return (void *)pairdirect_kernel<MU, R, W>;
+    return (void *)pairdirect_kernel<MU, R, W, LOGC>;
 }
 
-void *select_direct(const CountParams &p, int R, int W)
+// kernel for (mu bins, copies, warps, column bits); nullptr when not built
+void *select_direct(bool mu, int R, int W, int logC)
 {
-    const bool mu = p.n_mu > 1;
-    if (W == 16) {
-        if (R == 32) return mu ? dkernel<true, 32, 16>() : dkernel<false, 32, 16>();
-        return mu ? dkernel<true, 16, 16>() : dkernel<false, 16, 16>();
-    }
-    if (R == 32) return mu ? dkernel<true, 32, 12>() : dkernel<false, 32, 12>();
-    return mu ? dkernel<true, 16, 12>() : dkernel<false, 16, 12>();
+    if (W != DIRECT_WARPS) return nullptr;
+    constexpr int DW = DIRECT_WARPS;
+    if (!mu) return R == 32 ? dkernel<false, 32, DW, 0>() : dkernel<false, 16, DW, 0>();
+    if (logC == 5) return R == 32 ? dkernel<true, 32, DW, 5>() : dkernel<true, 16, DW, 5>();
+    if (logC == 6) return R == 32 ? dkernel<true, 32, DW, 6>() : dkernel<true, 16, DW, 6>();
+    return nullptr;
 }
 
 }  // namespace
@@ -686,16 +761,18 @@ size_t pairdirect_smem_bytes(const CountParams &p, int R, int C, int W)
     return d_off(p.n_s, p.n_rows, R, C, W).end;
 }
 
-cudaError_t pairdirect_set_attrs(const CountParams &p, int R, int W, int smem_bytes)
+cudaError_t pairdirect_set_attrs(const DirectParams &d, int mu)
 {
-    return cudaFuncSetAttribute(select_direct(p, R, W), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    void *k = select_direct(mu != 0, d.R, d.W, d.logC);
+    if (!k) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem);
 }
 
-int pairdirect_max_blocks_per_sm(const CountParams &p, int R, int W, int smem_bytes)
+int pairdirect_max_blocks_per_sm(const DirectParams &d, int mu)
 {
+    void *k = select_direct(mu != 0, d.R, d.W, d.logC);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_direct(p, R, W), W * 32, smem_bytes) !=
-        cudaSuccess) {
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, d.W * 32, d.smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -706,10 +783,12 @@ cudaError_t launch_pairdirect(const CountParams &p, const DirectParams &d, const
                               const Unit *units, const uint32_t *n_units, unsigned *claim, unsigned long long *stats,
                               const PairLaunch &pl, cudaStream_t s)
 {
+    void *k = select_direct(p.n_mu > 1, d.R, d.W, d.logC);
+    if (!k) return cudaErrorInvalidValue;
     const int term_only = pl.persistent ? -1 : pl.term;
     void *args[] = {(void *)&p,      (void *)&d,     (void *)&m,     (void *)&terms,     (void *)&units,
                     (void *)&n_units, (void *)&claim, (void *)&stats, (void *)&term_only, (void *)&pl.chunk};
-    return cudaLaunchKernel(select_direct(p, d.R, d.W), dim3(pl.blocks), dim3(d.W * 32), args, (size_t)d.smem, s);
+    return cudaLaunchKernel(k, dim3(pl.blocks), dim3(d.W * 32), args, (size_t)d.smem, s);
 }
 
 }  // namespace tpcf

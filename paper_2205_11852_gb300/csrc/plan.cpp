@@ -373,21 +373,24 @@ int build_plan(const tpcf_binning &b, int subdiv, unsigned long long max_cells, 
 
 // Direct pair counter (pairdirect.cu).  Coordinates are x = RN(RN(float(dx_grid)) inv)
 // with inv = RN(1 / (q ds)), dx_grid the exact integer offset from the unit's
-// cell corner, so |x| <= Xb bins.  The bounds below follow every rounding of
-// the kernel's arithmetic, doubled:
-//   E   : one coordinate's error (conversion and scaling; the common relative
-//         error kappa of inv is carried separately),
-//   e_d : a coordinate difference's error for pairs below n_s + 1 bins,
-//   |sqrt(d2) - s*| <= 2 sqrt3 e_d + 6 e_d^2 + gamma_3 (n_s + 2) (d2 from three fused roundings),
-//   u = d2 r exactly inside the FMA, r = rsqrt(d2) within rho = 2^-22.5
-//   (the hardware's measured worst case over all inputs is 2^-22.94).
-// The s residual band is eps_s = that + rho (n_s + 1.5) + kappa (n_s + 1); a pair
-// with |u - floor(u) - 1/2| <= 1/2 - eps_s has s* in the same bin.  The mu
-// interval: n_mu dx -+ m, with one rounding each way, times r brackets
-// n_mu dx* / s* when m >= n_mu 2E + 1.5 ulp(n_mu Xb + 1) + n_mu rho (n_s + 1)
-// + n_mu |sqrt(d2) - s*| (the common scale cancels in mu).  Below
-// d2min = (1.9 m)^2 the interval is wider than one bin, so such pairs (whose
-// clamped d2 would bias r) always go to the exact recheck.
+// cell corner, so |x| <= Xb bins.  The bounds follow every rounding of the
+// kernel's arithmetic:
+//   E    : one coordinate's error (conversion and scaling; the common
+//          relative error kappa of inv is carried separately),
+//   e_d  : a coordinate difference's error for pairs below n_s + 2 bins
+//          (2 E plus the subtraction's rounding),
+//   d2   : |d2 - s*^2| <= 2 sqrt3 e_d s* + 3 e_d^2 + gamma_3 d2 (three fused
+//          roundings, the tiny addend included), and for the s* >= 1/2 near
+//          any edge sqrt(d2) + s* >= 1.99 s*, so
+//          |sqrt(d2) - s*| <= dsq = 1.01 (sqrt3 e_d + 1.5 e_d^2 / 0.5 + gamma_3 (n_s + 2) / 1.99),
+//   u    = d2 r exactly inside the FMA, r = rsqrt(d2) within rho = 2^-22.5 (the
+//          hardware's measured worst case over all inputs is 2^-22.94).
+// The s residual band is eps_s = 1.1 (dsq + rho (n_s + 1.5) + kappa (n_s + 1) +
+// tiny) + 2^-24: a pair with |u - floor(u) - 1/2| <= 1/2 - eps_s has s* in the
+// same bin.  The mu interval: n_mu dx -+ m, one rounding each way from the
+// exact product n_mu b_x, times r, brackets n_mu dx* / s* when m >= m0 =
+// 1.1 (n_mu 2E + 1.5 ulp(n_mu Xb + 1) + n_mu rho (n_s + 1) + n_mu dsq) (the
+// common scale cancels in mu) plus the bias of the d2 addend (see below).
 bool build_direct(const tpcf_binning &b, const Plan &pl, int smem_sm, int smem_block, int reserved,
                   unsigned long long max_cat, DirectParams &d)
 {
@@ -410,29 +413,49 @@ bool build_direct(const tpcf_binning &b, const Plan &pl, int smem_sm, int smem_b
     const double e_d = 2.0 * E + 0.5 * ulp_f32(n_s + 2.0);
     const double g3 = 3.0 * u24 / (1.0 - 3.0 * u24);
     const double rho = std::pow(2.0, -22.5);
-    const double dsq = 2.0 * std::sqrt(3.0) * e_d + 6.0 * e_d * e_d + g3 * (n_s + 2.0);
-    const float tiny = (float)std::ldexp(1.0, -60);
-    const double eps_s = 2.0 * (dsq + rho * (n_s + 1.5) + kappa * (n_s + 1.0) + (double)tiny) + u24;
+    const double dsq = 1.01 * (std::sqrt(3.0) * e_d + 3.0 * e_d * e_d + g3 * (n_s + 2.0) / 1.99);
+    // mu margin (below) and the d2 addend: s only, a negligible 2^-60; with mu
+    // bins, tiny = m0^2 / n_mu, which biases r = rsqrt(d2 + tiny) low by at
+    // most n_mu tiny / (2 s) <= m0 / 4 in the mu interval for s >= 2 m0, and
+    // leaves the interval wider than one bin (always rechecked) below 2 m0
+    double m0 = 0.0;
+    if (mu) {
+        m0 = 1.1 * (n_mu * 2.0 * E + 1.5 * ulp_f32(n_mu * Xb + 1.0) + n_mu * rho * (n_s + 1.0) + n_mu * dsq);
+        if (!(m0 < 0.04)) return false;
+    }
+    const float tiny = mu ? down_f(m0 * m0 / n_mu) : (float)std::ldexp(1.0, -60);
+    if (!(tiny > 0.0f)) return false;
+    const double eps_s = 1.1 * (dsq + rho * (n_s + 1.5) + kappa * (n_s + 1.0) + (double)tiny) + u24;
     if (!(eps_s < 0.05)) return false;
     d.cs = down_f(0.5 - eps_s);
+    d.logC = 0;
+    d.CO = 0;
     if (mu) {
-        const double mm = 2.0 * (n_mu * 2.0 * E + 1.5 * ulp_f32(n_mu * Xb + 1.0) + n_mu * rho * (n_s + 1.0) +
-                                 n_mu * dsq);
-        if (!(mm < 0.05)) return false;
-        d.m = up_f(mm);
-        d.d2min = up_f((1.9 * (double)d.m) * (1.9 * (double)d.m));
+        d.m = up_f(1.25 * m0 * (1.0 + 1e-6));
+        // |t+-| <= n_mu + m / sqrt(tiny): signed columns j in [-CO, CO - 1]
+        const double ext = (double)d.m / std::sqrt((double)tiny);
+        d.CO = p.n_mu + 1 + (int)std::ceil(ext);
+        int lc = 0;
+        while ((1 << lc) < 2 * d.CO) lc++;
+        if (lc < 5) lc = 5;
+        if (lc > 6) return false;
+        d.logC = lc;
     }
     d.tiny = tiny;
     d.inv_qds = inv;
     d.nmu = (float)p.n_mu;
     d.hit = up_f((n_s + 0.01) * (n_s + 0.01));
+    // every pair's d2 is at least tiny, a normal float, so r = rsqrt(d2) is
+    // finite and every histogram address stays inside the table
+    if (!(d.tiny >= 1.0e-30f) || !std::isfinite(d.m) || !(d.cs > 0.4f) || !(inv > 0.0f)) return false;
     d.s_top = (float)(8388608.0 + n_s);
-    d.C = mu ? 2 * p.n_mu + 2 : 1;
+    d.C = 1 << d.logC;
     d.rows = p.n_s + 1;
-    // one block of 12 warps per SM (their registers fill the register file),
-    // with 32 histogram copies when they fit beside the warps' regions, else 16
+    // one block of DIRECT_WARPS warps per SM (their registers fill the
+    // register file), with 32 histogram copies when they fit beside the
+    // warps' regions, else 16
     const long long budget = (long long)std::min(smem_block, smem_sm - reserved);
-    for (int W : {12}) {
+    for (int W : {DIRECT_WARPS}) {
         for (int R : {32, 16}) {
             const long long need = (long long)pairdirect_smem_bytes(p, R, d.C, W);
             if (need <= budget) {
@@ -440,7 +463,7 @@ bool build_direct(const tpcf_binning &b, const Plan &pl, int smem_sm, int smem_b
                 d.W = W;
                 d.smem = (int)need;
                 // in one unit a lane pairs at most 64 a-points with at most
-                // max_cat / 32 + 16 b-points (the tiles' slots), and 32 / R
+                // max_cat / 32 + 16 b-points (its tile slots), and 32 / R
                 // lanes share a counter copy
                 d.unit_pair_bound = (unsigned long long)DIRECT_ACHUNK *
                                     (max_cat / (unsigned long long)R + 512ull / (unsigned long long)R + 16ull);

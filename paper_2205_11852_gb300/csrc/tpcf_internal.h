@@ -87,7 +87,9 @@ struct CountParams {
 struct DirectParams {
     int R;             // histogram copies (lane l adds to copy l mod R)
     int W;             // warps per block (one block per SM)
-    int C;             // histogram columns: 2 n_mu + 2 signed mu columns, or 1 (s only)
+    int C;             // histogram columns, 1 << logC: signed mu columns from -CO, or 1 (s only)
+    int logC;
+    int CO;            // column of mu bin 0 (the signed mu bin j sits in column j + CO)
     int rows;          // n_s + 1: the last row takes every pair at or beyond the last edge
     int smem;          // dynamic shared memory bytes
     int pad;
@@ -96,10 +98,10 @@ struct DirectParams {
     float nmu;         // n_mu
     float m;           // mu margin in units of n_mu bins: t in [dx'- r, dx'+ r] brackets n_mu mu
     float cs;          // s residual bound: floor(u) is the bin when |u - floor(u) - 1/2| <= cs
-    float d2min;       // lower clamp of d2 (bin^2): below it the mu interval is wider than one bin
-    float tiny;        // d2 addend of the s-only path (keeps rsqrt finite)
+    float tiny;        // d2 addend (keeps rsqrt finite; with mu bins it also bounds r)
     float hit;         // filter: squared box distance (bin^2) below which a b-point is kept
     float s_top;       // 2^23 + n_s: the clamped row of pairs beyond the last edge
+    float pad2;
 };
 
 // Workspace layout produced by the mesh build and consumed by the counters.
@@ -152,14 +154,15 @@ size_t paircount_scratch_bytes(int blocks);
 cudaError_t paircount_set_attrs(const CountParams &p, int smem_bytes);
 int paircount_max_blocks_per_sm(const CountParams &p, int warps_per_block, int smem_bytes);
 
-// direct pair counter (pairdirect.cu): one block per SM, no global scratch
+// direct pair counter (pairdirect.cu): one block of DIRECT_WARPS warps per SM, no global scratch
 constexpr int DIRECT_ACHUNK = 64;    // a-points per work unit
+constexpr int DIRECT_WARPS = 16;
 cudaError_t launch_pairdirect(const CountParams &p, const DirectParams &d, const Mesh &m, const Term *terms,
                               const Unit *units, const uint32_t *n_units, unsigned *claim, unsigned long long *stats,
                               const PairLaunch &pl, cudaStream_t s);
 size_t pairdirect_smem_bytes(const CountParams &p, int R, int C, int W);
-cudaError_t pairdirect_set_attrs(const CountParams &p, int R, int W, int smem_bytes);
-int pairdirect_max_blocks_per_sm(const CountParams &p, int R, int W, int smem_bytes);
+cudaError_t pairdirect_set_attrs(const DirectParams &d, int mu);
+int pairdirect_max_blocks_per_sm(const DirectParams &d, int mu);
 
 // ---- estimator launchers ----
 cudaError_t launch_ls(const long long *dd, const long long *dr, const long long *rr,
