@@ -311,8 +311,9 @@ int tpcf_eigvalsh(tpcf_ctx *ctx, const double *C, int n, double *w, void *stream
  * library; every GPU that loads the library holds it until the process exits.
  * Limit: 3*n_mock*nbin + 3*nbin + 3*nbin*nbin <= 2^21, else TPCF_ERR_RANGE
  * (e.g. nbin = 400 with n_mock <= 1347).
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
+ * Every call looks up the array's device address in the current device's
+ * context (so it stays valid after cudaDeviceReset); the first call on a
+ * device may load the library's device code, so make it before any stream
  * capture.  All calls share the one array: calls whose GPU work overlaps (on
  * different streams, or from different threads) race and give wrong results,
  * so serialise them.  The array keeps the last call's contents; nothing in it
@@ -393,11 +394,33 @@ int tpcf_set_cell_subdiv(tpcf_ctx *ctx, int subdiv);
  *                        else the general one) or TPCF_KERNEL_GENERAL (always
  *                        the general counter; the default).  Both give
  *                        identical counts.
+ * and of the split-precision covariances (tpcf_lc_cov, tpcf_sample_cov with
+ * TPCF_TF32X3 / TPCF_BF16X3):
+ *   TPCF_OPT_WAIT_LIMIT    -- bound, in polls of about 64 ns, of the Gram
+ *                        kernel's wait for its tensor-core products before it
+ *                        reads them (0, the default: 2^26).  A wait that runs
+ *                        out makes the next tpcf_sync return TPCF_ERR_TIMEOUT;
+ *                        the kernel frees its tensor memory and returns.  The
+ *                        waits for bulk copies keep the built-in bound.
+ *   TPCF_OPT_TEST_SKIP_MMA -- tests only: when non-zero, one CTA of the Gram
+ *                        kernel waits for its operand copies and then issues
+ *                        no tensor-core product, so that the wait above runs
+ *                        out with nothing in flight (the result is garbage and
+ *                        the status TPCF_ERR_TIMEOUT).  0 by default.
  * Returns TPCF_OK or TPCF_ERR_ARG.
+ *
+ * Test hooks read from the environment when a context is created:
+ * TPCF_TEST_FAIL_ALLOC=n makes the context's n-th device allocation fail
+ * (the call returns TPCF_ERR_NOMEM with nothing enqueued; the context stays
+ * usable), and TPCF_TEST_FAIL_COUNT=n makes the n-th tpcf_count return
+ * TPCF_ERR_CUDA as if a launch had failed, before it enqueues anything (the
+ * context is then unusable, as after a real CUDA error).
  */
 #define TPCF_OPT_GRAPHS    1
 #define TPCF_OPT_AUTOTUNE  2
 #define TPCF_OPT_KERNEL    3
+#define TPCF_OPT_WAIT_LIMIT    4
+#define TPCF_OPT_TEST_SKIP_MMA 5
 #define TPCF_KERNEL_AUTO     0
 #define TPCF_KERNEL_DIRECT   1
 #define TPCF_KERNEL_GENERAL  2

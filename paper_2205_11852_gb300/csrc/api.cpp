@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -43,6 +44,9 @@ int ensure(tpcf_ctx *ctx, const char *name, size_t bytes, void **out)
             b.p = nullptr;
             b.bytes = 0;
         }
+        if (ctx->fail_alloc_at > 0 && ++ctx->n_alloc == ctx->fail_alloc_at)
+            return fail(ctx, TPCF_ERR_NOMEM, std::string("device allocation of ") + name +
+                                                 " failed (TPCF_TEST_FAIL_ALLOC)");
         size_t want = std::max(bytes + bytes / 8, (size_t)256);
         cudaError_t e = cudaMalloc(&b.p, want);
         if (e != cudaSuccess) {
@@ -59,6 +63,15 @@ int ensure(tpcf_ctx *ctx, const char *name, size_t bytes, void **out)
     }
     *out = b.p;
     return TPCF_OK;
+}
+
+GramOpts gram_opts(const tpcf_ctx *ctx)
+{
+    GramOpts o;
+    o.n_sm = ctx->n_sm;
+    o.wait_limit = ctx->gram_wait_limit;
+    o.test_skip_mma = ctx->test_skip_mma;
+    return o;
 }
 
 // pinned staging area for small host->device tables; waits for its previous use
@@ -195,6 +208,8 @@ int tpcf_create(tpcf_ctx **out, int cuda_device)
         return e == cudaErrorMemoryAllocation ? TPCF_ERR_NOMEM : TPCF_ERR_CUDA;
     }
     std::memset(ctx->stats_host, 0, 4 * sizeof(unsigned long long));
+    if (const char *v = std::getenv("TPCF_TEST_FAIL_ALLOC")) ctx->fail_alloc_at = std::atoll(v);
+    if (const char *v = std::getenv("TPCF_TEST_FAIL_COUNT")) ctx->fail_count_at = std::atoll(v);
     *out = ctx;
     return TPCF_OK;
 }
@@ -281,6 +296,11 @@ int tpcf_set_option(tpcf_ctx *ctx, int option, int value)
             return fail(ctx, TPCF_ERR_ARG, "TPCF_OPT_KERNEL takes TPCF_KERNEL_AUTO or TPCF_KERNEL_GENERAL");
         ctx->kernel_pref = value;
         break;
+    case TPCF_OPT_WAIT_LIMIT:
+        if (value < 0) return fail(ctx, TPCF_ERR_ARG, "TPCF_OPT_WAIT_LIMIT must be >= 0");
+        ctx->gram_wait_limit = value;
+        break;
+    case TPCF_OPT_TEST_SKIP_MMA: ctx->test_skip_mma = value != 0; break;
     default: return fail(ctx, TPCF_ERR_ARG, "unknown option");
     }
     return TPCF_OK;
@@ -372,11 +392,11 @@ int tpcf_lc_cov(tpcf_ctx *ctx, const double *xi_a1, const double *xi_a2, const d
         return TPCF_OK;
     }
     if (precision == TPCF_TF32X3 || precision == TPCF_BF16X3) {
-        const size_t bytes = lc_split_work_bytes(n_mock, nbin, precision);
+        const size_t bytes = lc_split_work_bytes(n_mock, nbin, precision, ctx->n_sm);
         void *w;
         if ((rc = ensure(ctx, "lc_split_work", bytes, &w))) return rc;
         cudaError_t e = launch_lc_split(xi_a1, xi_a2, xi_b, n_mock, nbin, precision, w, bytes, M_a, M, C_lc, Ca,
-                                        Cb, A, B, ctx->status, s);
+                                        Cb, A, B, ctx->status, gram_opts(ctx), s);
         if (e == cudaErrorNotSupported) return fail(ctx, TPCF_ERR_ARG, "split-precision covariance unavailable");
         CK(e);
         return TPCF_OK;
@@ -400,10 +420,10 @@ int tpcf_sample_cov(tpcf_ctx *ctx, const double *xi, int n_mock, int nbin, int p
         return TPCF_OK;
     }
     if (precision == TPCF_TF32X3 || precision == TPCF_BF16X3) {
-        const size_t bytes = lc_split_work_bytes(n_mock, nbin, precision, 1);
+        const size_t bytes = lc_split_work_bytes(n_mock, nbin, precision, ctx->n_sm, 1);
         void *w;
         if ((rc = ensure(ctx, "lc_split_work", bytes, &w))) return rc;
-        cudaError_t e = launch_cov_split(xi, n_mock, nbin, precision, w, bytes, C, ctx->status, s);
+        cudaError_t e = launch_cov_split(xi, n_mock, nbin, precision, w, bytes, C, ctx->status, gram_opts(ctx), s);
         if (e == cudaErrorNotSupported) return fail(ctx, TPCF_ERR_ARG, "split-precision covariance unavailable");
         CK(e);
         return TPCF_OK;

@@ -695,6 +695,8 @@ extern "C" int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, con
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
+    if (ctx->fail_count_at > 0 && ++ctx->n_count == ctx->fail_count_at)
+        return cuda_fail(ctx, cudaErrorLaunchFailure, "tpcf_count (TPCF_TEST_FAIL_COUNT)");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<tpcf_mock> staged;
     if (mode & TPCF_HOST_INPUT) {

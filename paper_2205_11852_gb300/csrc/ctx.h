@@ -69,6 +69,14 @@ struct tpcf_ctx {
     int last_subdiv = 0, last_nc = 0, last_chunk = 0;
     int kernel_pref = 2;                  // TPCF_KERNEL_AUTO | TPCF_KERNEL_GENERAL (the default)
     bool last_direct = false;             // the last tpcf_count ran the direct counter
+    // split-precision Gram kernel: bound of its epilogue wait (0: built in), test-only MMA skip
+    long long gram_wait_limit = 0;
+    int test_skip_mma = 0;
+    // test hooks read from the environment at tpcf_create: the n-th device
+    // allocation of ensure() fails (TPCF_TEST_FAIL_ALLOC=n) and the n-th
+    // tpcf_count fails as if a launch had failed (TPCF_TEST_FAIL_COUNT=n)
+    long long fail_alloc_at = 0, n_alloc = 0;
+    long long fail_count_at = 0, n_count = 0;
     // graphs
     cudaStream_t cap_stream = nullptr;
     std::vector<tpcf::GraphEntry> graphs;
@@ -87,6 +95,7 @@ size_t al(size_t x);
 int check_ctx(tpcf_ctx *ctx);
 int validate_binning(tpcf_ctx *ctx, const tpcf_binning *b);
 int check_mu_width(tpcf_ctx *ctx, const tpcf_binning *b, const CountParams &p);
+GramOpts gram_opts(const tpcf_ctx *ctx);
 void release_graphs(tpcf_ctx *ctx);
 
 }  // namespace detail

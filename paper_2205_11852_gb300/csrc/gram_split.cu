@@ -37,6 +37,9 @@ constexpr int TMEM_COLS = 2 * TM; // two FP32 accumulators: leading product, cor
 constexpr int GRAM_SMEM_MIN = 100 * 1024;   // at most two CTAs per SM: their tensor memory fits
 constexpr int GRAM_THREADS = 128;
 constexpr long long SPIN_LIMIT = 1ll << 26;
+constexpr int NSTAGE = 3;                    // K-slices in flight per CTA
+constexpr int MAX_SPC = 16;                  // K-slices (16 mocks each) accumulated in FP32 per chunk
+constexpr long long PARTIAL_BYTES = 256ll << 20;   // bound of the per-chunk partial Grams
 
 template <int PREC>
 struct Split;
@@ -251,18 +254,39 @@ __host__ __device__ constexpr uint32_t instr_desc()
 }
 
 template <int PREC>
+__host__ __device__ constexpr int stage_bytes() { return 2 * Split<PREC>::PIECES * tile_bytes<PREC>(); }
+
+// shared memory: NSTAGE stages | full[NSTAGE], empty[NSTAGE], done barriers | TMEM slot | flags
+template <int PREC>
+constexpr int gram_smem_bytes() { return NSTAGE * stage_bytes<PREC>() + 8 * (2 * NSTAGE + 1) + 16; }
+
+// One CTA: output tile (bi, bj) of variant v over the K-slices [k0, k1) of
+// chunk kc.  Thread 0 keeps NSTAGE slices in flight (bulk copies completing
+// on full[stage]), issues each slice's MMA chain into the two TMEM
+// accumulators and commits it to empty[stage]; once slice i - 1's MMAs have
+// read their stage, that stage is refilled with slice i - 1 + NSTAGE.  A
+// final commit to `done` releases the epilogue, which writes the chunk's
+// partial Gram (both triangles) to P[kc][v] with plain stores.
+//
+// Every wait is bounded.  The epilogue's wait on `done` gives up after
+// done_limit polls (a context option); skip_mma (tests only) makes CTA
+// (0, 0, 0) wait for its first loads and then issue no MMA and no commit, so
+// that this wait runs out with no copy or MMA in flight.
+template <int PREC>
 __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned char *__restrict__ tiles, int nbin,
-                                                              int n_rb, int n_ks, double *__restrict__ G,
-                                                              int *__restrict__ status)
+                                                              int n_rb, int n_ks, int spc, double *__restrict__ P,
+                                                              int *__restrict__ status, long long done_limit,
+                                                              int skip_mma)
 {
     constexpr int TB = tile_bytes<PREC>();
     constexpr int NP = Split<PREC>::PIECES;
+    constexpr int SB = stage_bytes<PREC>();
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *sA = smem;                       // NP tiles of row block bi
-    unsigned char *sB = smem + NP * TB;             // NP tiles of row block bj
-    uint64_t *bar = (uint64_t *)(smem + 2 * NP * TB);
-    uint32_t *slot = (uint32_t *)(bar + 2);
-    int *flag = (int *)(slot + 1);
+    uint64_t *full = (uint64_t *)(smem + NSTAGE * SB);
+    uint64_t *empty = full + NSTAGE;
+    uint64_t *done = empty + NSTAGE;
+    uint32_t *slot = (uint32_t *)(done + 1);
+    int *flag = (int *)(slot + 1);   // [0]: the epilogue waits on done, [1]: every slice arrived and was multiplied
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // blockIdx.x enumerates the upper-triangle tile pairs (bi <= bj) row by row
@@ -272,14 +296,20 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
         bi++;
     }
     const int bj = bi + rest;
-    const int v = blockIdx.y, ks = blockIdx.z;
+    const int v = blockIdx.y, kc = blockIdx.z;
+    const int k0 = kc * spc, n = min(n_ks, k0 + spc) - k0;   // n >= 1 by the host's chunking
+    const bool skip = skip_mma && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
 
     if (warp == 0) tmem_alloc(slot, TMEM_COLS);
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int i = 0; i < NSTAGE; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(done, 1);
         mbar_fence_init();
-        *flag = 1;
+        flag[0] = 0;
+        flag[1] = 0;
     }
     tc_fence_before();
     __syncthreads();
@@ -287,47 +317,73 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
     const uint32_t tmem = *slot;
 
     if (tid == 0) {
-        mbar_expect_tx(&bar[0], (uint32_t)(2 * NP * TB));
-        for (int p = 0; p < NP; p++) {
-            const unsigned char *ga = tiles + ((((size_t)v * NP + p) * n_rb + bi) * n_ks + ks) * TB;
-            const unsigned char *gb = tiles + ((((size_t)v * NP + p) * n_rb + bj) * n_ks + ks) * TB;
-            bulk_g2s(sA + p * TB, ga, TB, &bar[0]);
-            bulk_g2s(sB + p * TB, gb, TB, &bar[0]);
-        }
-        bool ok = mbar_wait(&bar[0], 0, SPIN_LIMIT);
-        if (!ok) ok = mbar_wait(&bar[0], 0, SPIN_LIMIT);   // give copies in flight one more bounded wait
-        if (ok) {
+        auto issue = [&](int i) {   // the operand tiles of slice k0 + i into stage i % NSTAGE
+            unsigned char *sa = smem + (i % NSTAGE) * SB, *sb = sa + NP * TB;
+            mbar_expect_tx(&full[i % NSTAGE], (uint32_t)SB);
+            for (int p = 0; p < NP; p++) {
+                const size_t base = ((size_t)v * NP + p) * n_rb;
+                bulk_g2s(sa + p * TB, tiles + ((base + bi) * n_ks + k0 + i) * TB, TB, &full[i % NSTAGE]);
+                bulk_g2s(sb + p * TB, tiles + ((base + bj) * n_ks + k0 + i) * TB, TB, &full[i % NSTAGE]);
+            }
+        };
+        int issued = 0, waited = 0, mma_slices = 0;
+        bool ok = true;
+        for (; issued < min(NSTAGE, n); issued++) issue(issued);
+        for (int i = 0; i < n; i++) {
+            ok = mbar_wait(&full[i % NSTAGE], (uint32_t)(i / NSTAGE) & 1u, SPIN_LIMIT);
+            if (!ok) break;
+            waited = i + 1;
+            if (skip) {
+                if (waited == issued) break;   // every copy in flight has landed
+                continue;
+            }
             tc_fence_after();
             constexpr uint32_t idesc = instr_desc<PREC>();
             constexpr int steps = KS / Split<PREC>::K_MMA;
+            const uint32_t sa = smem_addr(smem + (i % NSTAGE) * SB), sb = sa + NP * TB;
 #pragma unroll
             for (int q = 0; q < Split<PREC>::N_PROD; q++) {
-                const uint32_t a0 = smem_addr(sA + Split<PREC>::pa(q) * TB);
-                const uint32_t b0 = smem_addr(sB + Split<PREC>::pb(q) * TB);
+                const uint32_t a0 = sa + Split<PREC>::pa(q) * TB;
+                const uint32_t b0 = sb + Split<PREC>::pb(q) * TB;
 #pragma unroll
-                for (int s = 0; s < steps; s++) {
-                    // each MMA step covers two core matrices along K (2 x 128 bytes);
-                    // product 0 accumulates in columns [0, 128), the others in [128, 256)
-                    const uint64_t da = smem_desc(a0 + s * 256, 128, sbo_bytes<PREC>());
-                    const uint64_t db = smem_desc(b0 + s * 256, 128, sbo_bytes<PREC>());
+                for (int st = 0; st < steps; st++) {
+                    // each MMA step covers two core matrices along K (2 x 128 bytes); product 0
+                    // accumulates in columns [0, 128), the others in [128, 256); the first step of
+                    // the chunk's first slice overwrites each accumulator
+                    const uint64_t da = smem_desc(a0 + st * 256, 128, sbo_bytes<PREC>());
+                    const uint64_t db = smem_desc(b0 + st * 256, 128, sbo_bytes<PREC>());
                     const uint32_t d = tmem + (q == 0 ? 0u : (uint32_t)TM);
-                    mma<PREC>(d, da, db, idesc, (q == 0 || q == 1) ? (s > 0 ? 1u : 0u) : 1u);
+                    const bool init = i == 0 && st == 0 && (q == 0 || q == 1);
+                    mma<PREC>(d, da, db, idesc, init ? 0u : 1u);
                 }
             }
-            mma_commit(&bar[1]);
-        } else {
-            *flag = 0;
+            mma_commit(&empty[i % NSTAGE]);
+            mma_slices = i + 1;
+            // refill the stage of slice i - 1 once its MMAs have read it
+            if (i >= 1 && issued < n) {
+                ok = mbar_wait(&empty[(i - 1) % NSTAGE], (uint32_t)((i - 1) / NSTAGE) & 1u, SPIN_LIMIT);
+                if (!ok) break;
+                issue(issued++);
+            }
         }
+        if (mma_slices > 0) mma_commit(done);
+        // copies still in flight after a wait gave up get one more bounded wait each
+        for (int i = waited; i < issued; i++)
+            if (!mbar_wait(&full[i % NSTAGE], (uint32_t)(i / NSTAGE) & 1u, SPIN_LIMIT)) break;
+        flag[0] = (mma_slices > 0 || skip) ? 1 : 0;
+        flag[1] = (ok && mma_slices == n) ? 1 : 0;
     }
     __syncthreads();
-    if (*flag) {
-        bool done = mbar_wait(&bar[1], 0, SPIN_LIMIT);
-        if (!done) done = mbar_wait(&bar[1], 0, SPIN_LIMIT);
-        if (done) {
+    bool good = flag[1] != 0;
+    if (flag[0]) {
+        bool fin = mbar_wait(done, 0, done_limit);
+        if (!fin) fin = mbar_wait(done, 0, done_limit);
+        good = good && fin;
+        if (fin && good) {
             tc_fence_after();
             // warp w reads accumulator rows 32w..32w+31 (its tensor-memory lanes)
             const int row = bi * TM + warp * 32 + lane;
-            double *g = G + (size_t)v * nbin * nbin;
+            double *g = P + ((size_t)kc * gridDim.y + v) * nbin * nbin;
 #pragma unroll 1
             for (int c0 = 0; c0 < TM; c0 += 32) {
                 uint32_t r[32], rc[32];
@@ -339,21 +395,49 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
                         const int col = bj * TM + c0 + j;
                         if (col < nbin) {
                             const double val = (double)__uint_as_float(r[j]) + (double)__uint_as_float(rc[j]);
-                            atomicAdd(&g[(size_t)row * nbin + col], val);
-                            if (bi != bj) atomicAdd(&g[(size_t)col * nbin + row], val);
+                            g[(size_t)row * nbin + col] = val;
+                            if (bi != bj) g[(size_t)col * nbin + row] = val;
                         }
                     }
                 }
             }
-        } else if (tid == 0) {
-            atomicOr(status, STATUS_TIMEOUT);
         }
-    } else if (tid == 0) {
-        atomicOr(status, STATUS_TIMEOUT);
     }
+    if (!good && tid == 0) atomicOr(status, STATUS_TIMEOUT);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// G[v][i][j] = sum over the chunks kc of P[kc][v][i][j], in chunk order (deterministic)
+__global__ void reduce_partials_kernel(const double *__restrict__ P, int n_kc, size_t per, double *__restrict__ G)
+{
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per; e += (size_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < n_kc; k++) acc += P[(size_t)k * per + e];
+        G[e] = acc;
+    }
+}
+
+// K-chunking of the Gram grid: n_kc chunks of spc slices each.  Enough chunks
+// that the grid covers every SM about twice, at most MAX_SPC slices (FP32
+// accumulation of MAX_SPC * KS mocks) per chunk, and the partials within
+// PARTIAL_BYTES.
+struct Chunking {
+    int spc, n_kc;
+};
+
+Chunking chunking(int n_mock, int nbin, int n_var, int n_sm)
+{
+    const int n_rb = (nbin + TM - 1) / TM, n_ks = (n_mock + KS - 1) / KS;
+    const long long np = (long long)n_rb * (n_rb + 1) / 2;
+    long long want = std::max<long long>(1, (2ll * std::max(1, n_sm) + np * n_var - 1) / (np * n_var));
+    want = std::max<long long>(want, (n_ks + MAX_SPC - 1) / MAX_SPC);
+    const long long per = (long long)n_var * nbin * nbin * 8;
+    want = std::min<long long>(want, std::max<long long>(1, PARTIAL_BYTES / per));
+    want = std::min<long long>(want, n_ks);
+    const int spc = (int)((n_ks + want - 1) / want);
+    return Chunking{spc, (n_ks + spc - 1) / spc};
 }
 
 template <int PREC>
@@ -365,19 +449,33 @@ size_t tiles_bytes(int n_mock, int nbin, int n_var)
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+template <int PREC>
+size_t work_bytes_of(int n_mock, int nbin, int n_var, int n_sm)
+{
+    const Chunking c = chunking(n_mock, nbin, n_var, n_sm);
+    const size_t g = (size_t)n_var * nbin * nbin * 8;
+    return al256(tiles_bytes<PREC>(n_mock, nbin, n_var)) + al256(g) + al256((size_t)c.n_kc * g) +
+           al256((size_t)n_var * nbin * 8);
+}
+
 // n_var = 3: the LC covariance of (x0, x1, x2); n_var = 1: the sample covariance of x0 into C_lc
 template <int PREC>
 cudaError_t run(const double *x0, const double *x1, const double *x2, int n_var, int n_mock, int nbin, void *work,
                 size_t work_bytes, int M_a, double M, double *C_lc, double *Ca, double *Cb, double *A, double *B,
-                int *status, cudaStream_t s)
+                int *status, const GramOpts &opt, cudaStream_t s)
 {
     const int n_rb = (nbin + TM - 1) / TM, n_ks = (n_mock + KS - 1) / KS;
-    if (n_ks > 65535 || n_rb > 90) return cudaErrorInvalidValue;
+    if (n_ks > 65535 * MAX_SPC || n_rb > 90) return cudaErrorInvalidValue;
+    const Chunking ch = chunking(n_mock, nbin, n_var, opt.n_sm);
+    if (ch.n_kc > 65535) return cudaErrorInvalidValue;
     unsigned char *w = (unsigned char *)work;
     unsigned char *tiles = w;
+    const size_t g = (size_t)n_var * nbin * nbin;
     size_t o = al256(tiles_bytes<PREC>(n_mock, nbin, n_var));
     double *G = (double *)(w + o);
-    o += al256((size_t)n_var * nbin * nbin * 8);
+    o += al256(g * 8);
+    double *P = (double *)(w + o);
+    o += al256((size_t)ch.n_kc * g * 8);
     double *mean = (double *)(w + o);
     o += al256((size_t)n_var * nbin * 8);
     if (o > work_bytes) return cudaErrorInvalidValue;
@@ -385,12 +483,16 @@ cudaError_t run(const double *x0, const double *x1, const double *x2, int n_var,
     if (e != cudaSuccess) return e;
     split_kernel<PREC><<<dim3(n_ks, n_rb, n_var), 256, 0, s>>>(x0, x1, x2, mean, n_mock, nbin, n_rb, n_ks, tiles);
     const int np = n_rb * (n_rb + 1) / 2;   // upper-triangle tile pairs
-    e = cudaMemsetAsync(G, 0, (size_t)n_var * nbin * nbin * 8, s);
-    if (e != cudaSuccess) return e;
-    const int smem = std::max(2 * Split<PREC>::PIECES * tile_bytes<PREC>() + 64, GRAM_SMEM_MIN);
+    const int smem = std::max(gram_smem_bytes<PREC>(), GRAM_SMEM_MIN);
     e = cudaFuncSetAttribute(gram_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    gram_tc_kernel<PREC><<<dim3(np, n_var, n_ks), GRAM_THREADS, smem, s>>>(tiles, nbin, n_rb, n_ks, G, status);
+    gram_tc_kernel<PREC><<<dim3(np, n_var, ch.n_kc), GRAM_THREADS, smem, s>>>(
+        tiles, nbin, n_rb, n_ks, ch.spc, P, status, opt.wait_limit > 0 ? opt.wait_limit : SPIN_LIMIT,
+        opt.test_skip_mma);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int rb = (int)std::min<size_t>((g + 255) / 256, 4096);
+    reduce_partials_kernel<<<rb, 256, 0, s>>>(P, ch.n_kc, g, G);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (n_var == 1) return launch_scale(G, nbin, n_mock, C_lc, s);
@@ -399,35 +501,35 @@ cudaError_t run(const double *x0, const double *x1, const double *x2, int n_var,
 
 }  // namespace
 
-size_t lc_split_work_bytes(int n_mock, int nbin, int precision, int n_var)
+size_t lc_split_work_bytes(int n_mock, int nbin, int precision, int n_sm, int n_var)
 {
-    const size_t t = precision == TPCF_BF16X3 ? tiles_bytes<TPCF_BF16X3>(n_mock, nbin, n_var)
-                                              : tiles_bytes<TPCF_TF32X3>(n_mock, nbin, n_var);
-    return al256(t) + al256((size_t)n_var * nbin * nbin * 8) + al256((size_t)n_var * nbin * 8);
+    return precision == TPCF_BF16X3 ? work_bytes_of<TPCF_BF16X3>(n_mock, nbin, n_var, n_sm)
+                                    : work_bytes_of<TPCF_TF32X3>(n_mock, nbin, n_var, n_sm);
 }
 
 cudaError_t launch_lc_split(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock, int nbin,
                             int precision, void *work, size_t work_bytes, int M_a, double M, double *C_lc,
-                            double *Ca, double *Cb, double *A, double *B, int *status, cudaStream_t s)
+                            double *Ca, double *Cb, double *A, double *B, int *status, const GramOpts &opt,
+                            cudaStream_t s)
 {
     if (precision == TPCF_TF32X3)
         return run<TPCF_TF32X3>(xi_a1, xi_a2, xi_b, 3, n_mock, nbin, work, work_bytes, M_a, M, C_lc, Ca, Cb, A, B,
-                                status, s);
+                                status, opt, s);
     if (precision == TPCF_BF16X3)
         return run<TPCF_BF16X3>(xi_a1, xi_a2, xi_b, 3, n_mock, nbin, work, work_bytes, M_a, M, C_lc, Ca, Cb, A, B,
-                                status, s);
+                                status, opt, s);
     return cudaErrorNotSupported;
 }
 
 cudaError_t launch_cov_split(const double *xi, int n_mock, int nbin, int precision, void *work, size_t work_bytes,
-                             double *C, int *status, cudaStream_t s)
+                             double *C, int *status, const GramOpts &opt, cudaStream_t s)
 {
     if (precision == TPCF_TF32X3)
         return run<TPCF_TF32X3>(xi, xi, xi, 1, n_mock, nbin, work, work_bytes, 1, 2.0, C, nullptr, nullptr,
-                                nullptr, nullptr, status, s);
+                                nullptr, nullptr, status, opt, s);
     if (precision == TPCF_BF16X3)
         return run<TPCF_BF16X3>(xi, xi, xi, 1, n_mock, nbin, work, work_bytes, 1, 2.0, C, nullptr, nullptr,
-                                nullptr, nullptr, status, s);
+                                nullptr, nullptr, status, opt, s);
     return cudaErrorNotSupported;
 }
 

@@ -172,11 +172,20 @@ cudaError_t launch_lc_fp64(const double *xi_a1, const double *xi_a2, const doubl
                            int nbin, double *work /* 3*n_mock*nbin + 3*nbin + 3*nbin*nbin */,
                            int M_a, double M, double *C_lc, double *Ca, double *Cb, double *A, double *B,
                            cudaStream_t s);
+// Launch options of the split-precision Gram kernel: the SM count its grid is
+// sized for, the bound (polls) of the epilogue's wait for the MMA chain, and a
+// test-only switch under which one CTA issues no MMA so that this wait runs out.
+struct GramOpts {
+    int n_sm = 1;
+    long long wait_limit = 0;   // 0: the built-in bound
+    int test_skip_mma = 0;
+};
 cudaError_t launch_lc_split(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_mock,
                             int nbin, int precision, void *work, size_t work_bytes, int M_a, double M,
-                            double *C_lc, double *Ca, double *Cb, double *A, double *B, int *status, cudaStream_t s);
-// work bytes of the split-precision path for n_var variants (3: LC, 1: one sample covariance)
-size_t lc_split_work_bytes(int n_mock, int nbin, int precision, int n_var = 3);
+                            double *C_lc, double *Ca, double *Cb, double *A, double *B, int *status,
+                            const GramOpts &opt, cudaStream_t s);
+// work bytes of the split-precision path for n_var variants (3: LC, 1: one sample covariance) on n_sm SMs
+size_t lc_split_work_bytes(int n_mock, int nbin, int precision, int n_sm, int n_var = 3);
 // float64 covariance paths with the mocks split into n_split ranges (fp64_splits picks a count that fills
 // the GPU); work holds fp64_work_elems(n_mock, nbin, n_var, n_split) doubles
 int fp64_splits(int n_mock, int nbin, int n_var);
@@ -188,7 +197,7 @@ cudaError_t launch_lc_fp64_split(const double *xi_a1, const double *xi_a2, const
 cudaError_t launch_cov_fp64(const double *xi, int n_mock, int nbin, double *work, double *C, cudaStream_t s,
                             int n_split);
 cudaError_t launch_cov_split(const double *xi, int n_mock, int nbin, int precision, void *work, size_t work_bytes,
-                             double *C, int *status, cudaStream_t s);
+                             double *C, int *status, const GramOpts &opt, cudaStream_t s);
 // column means mean[n_var][nbin] of the first n_var xi variants
 cudaError_t launch_means(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_var, int n_mock,
                          int nbin, double *mean, cudaStream_t s);
