@@ -7,7 +7,6 @@
 // synchronisation that cudaMalloc / cudaFree can cause.  The caller passes
 // only its inputs and outputs; nothing is allocated or freed here.
 #include <cmath>
-#include <mutex>
 
 #include "tpcf_internal.h"
 
@@ -21,27 +20,16 @@ namespace {
 constexpr size_t NOALLOC_SCRATCH_DOUBLES = size_t(1) << 21;   // 16 MiB
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
-constexpr int MAX_DEVICES = 64;
-double *g_scratch_ptr[MAX_DEVICES] = {};
-std::mutex g_scratch_mu;
-
-// Device address of the scratch array on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// Device address of the scratch array in the current device's context.  In
+// host code the array's name is only a host-side stand-in; the address is
+// looked up on every call (a host-side table lookup once the module is
+// loaded), so it stays right after cudaDeviceReset or a context change.
 cudaError_t scratch_on_current_device(double **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = (double *)p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = (double *)p;
     return cudaSuccess;
 }
 

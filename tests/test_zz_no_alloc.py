@@ -3,9 +3,11 @@
 Some callers cannot call cudaMalloc while they run (services that reserve all
 GPU memory at start-up, code that must not trigger cudaMalloc's implicit device
 synchronisation).  The allocation-free entry point keeps its scratch in a fixed
-array inside the library; here it is called through the C ABI and checked
-against tpcf_lc_cov on two calls in a row, within the covariance tolerance of
-the other tests (1e-12, normalised by sqrt(C^a_ii C^a_jj)).  This file is
+array inside the library; here it is called through the C ABI on two calls in
+a row and checked against the float64 oracle (oracle.lc_cov) and against
+tpcf_lc_cov, within the covariance tolerance of the other tests (1e-12,
+normalised by sqrt(C^a_ii C^a_jj)); the device's free memory and torch's
+reserved memory must not change across the second call.  This file is
 collected last so that a run stopping at the first failure has already run
 every other test.
 """
@@ -14,6 +16,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -31,28 +34,35 @@ def tp():
     return tp
 
 
-def _noalloc(tp, xa1, xa2, xb, M_a, M):
-    n_mock, nbin = xa1.shape
-    outs = [torch.full((nbin, nbin), float("nan"), dtype=torch.float64, device="cuda:0") for _ in range(5)]
-    p = lambda t: ctypes.c_void_p(t.data_ptr())
-    rc = tp.lib().tpcf_lc_cov_noalloc(p(xa1), p(xa2), p(xb), n_mock, nbin, M_a, float(M), *[p(o) for o in outs],
-                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    return rc, dict(zip(("C_lc", "Ca", "Cb", "A", "B"), outs))
-
-
-def test_noalloc_matches_lc_cov_twice(tp):
+def test_noalloc_matches_oracle_twice(tp):
     ctx = tp.Context(0)
-    for call, (seed, n_mock, nbin, M) in enumerate(((51, 150, 37, 50.0), (52, 301, 200, float("inf")))):
-        xs = [torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
-              for a in synth.synthetic_xi_variants(seed, n_mock, nbin)]
-        rc, got = _noalloc(tp, *xs, 1, M)
+    cases = ((51, 150, 37, 50.0), (52, 301, 200, float("inf")))
+    host = [synth.synthetic_xi_variants(seed, n_mock, nbin) for seed, n_mock, nbin, _ in cases]
+    dev = [[torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0") for a in xs] for xs in host]
+    # outputs of both calls made up front, so the second call is the only thing between the memory readings
+    outs = [[torch.full((xs[0].shape[1],) * 2, float("nan"), dtype=torch.float64, device="cuda:0")
+             for _ in range(5)] for xs in host]
+    torch.cuda.synchronize()
+    for call, ((seed, n_mock, nbin, M), xs, gx, out) in enumerate(zip(cases, host, dev, outs)):
+        free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        rc = tp.lib().tpcf_lc_cov_noalloc(p(gx[0]), p(gx[1]), p(gx[2]), n_mock, nbin, 1, float(M),
+                                         *[p(o) for o in out], ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert rc == tp.TPCF_OK, call
-        ref = ctx.tpcf_lc_cov(*xs, 1, M, tp.TPCF_FP64)
         torch.cuda.synchronize()
-        d = torch.sqrt(torch.diag(ref["Ca"]))
-        scale = torch.outer(d, d)
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_reserved() == reserved0
+        got = dict(zip(("C_lc", "Ca", "Cb", "A", "B"), (o.cpu().numpy() for o in out)))
+        ref = oracle.lc_cov(*xs, 1, M)
+        d = np.sqrt(np.diag(ref["Ca"]))
+        scale = np.outer(d, d)
         for k in ("C_lc", "Ca", "Cb", "A", "B"):
-            err = (torch.abs(got[k] - ref[k]) / scale).max().item()
+            err = float(np.max(np.abs(got[k] - ref[k]) / scale))
+            assert err <= 1e-12, (call, k, err)
+        lib = ctx.tpcf_lc_cov(*gx, 1, M, tp.TPCF_FP64)
+        for k in ("C_lc", "Ca", "Cb", "A", "B"):
+            err = float(np.max(np.abs(got[k] - lib[k].cpu().numpy()) / scale))
             assert err <= 1e-12, (call, k, err)
     ctx.close()
 
