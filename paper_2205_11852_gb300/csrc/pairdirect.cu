@@ -25,12 +25,13 @@
 // within cs of 1/2 and both mu floors agree; cs and m come from a rigorous
 // bound on the FP32 errors (plan.cpp).  Every pair, certain or not, is added
 // to the histogram at (S, T-) with one shared-memory atomic; a pair at or
-// beyond the last edge lands in the histogram's spare last row.  A group of
-// 8 pairs per lane with any uncertain pair takes the rare path, which
-// recomputes them, takes back the uncertain ones' adds and rechecks them
-// exactly from the integer coordinates (64-bit squared distances, a 128-bit
-// mu test), 32 at a time, so every count equals the integer definition bit
-// for bit.
+// beyond the last edge lands in the histogram's spare last row.  The check
+// costs two compares per pair, or-ed into one predicate per a-point; an
+// a-point with an uncertain pair in any lane takes the rare path, which
+// recomputes its pairs with a flag each, takes back the uncertain ones' adds
+// and rechecks them exactly from the integer coordinates (64-bit squared
+// distances, a 128-bit mu test), 32 at a time, so every count equals the
+// integer definition bit for bit.
 //
 // Histogram.  R copies of a (n_s + 1) x C table of 32-bit counters, lane l
 // adding to copy l mod R, so the 32 adds of a warp fall in distinct banks
@@ -113,111 +114,215 @@ struct K2 {
     uint64_t tiny, ms, m1, mh, mt, nm;
 };
 
-// One packed pair of pairs (b_p, a), (b_p', a) in hand-written PTX (hot
-// path): the histogram addresses of both, and flag bits 0 and 1 set when the
-// first or the second is uncertain.  With mu bins (MU): the tiny addend, r = rsqrt(d2) (MUFU), S,
-// the s residual, the mu interval floors T+, T-.
-template <bool MU, int LS, int LT>
-__device__ __forceinline__ void pair2(uint64_t bx, uint64_t by, uint64_t bz, const ARec &a, const K2 &k, float cs,
-                                      float stop, uint32_t Kl, uint32_t &a0, uint32_t &a1, uint32_t &flag)
+// One packed pair of pairs (b_p, a), (b_p', a) in hand-written PTX: the
+// packed s floor word S, the s residual FS and, with mu bins (MU), the mu
+// interval floor words TP, TM (the tiny addend, r = rsqrt(d2) by MUFU).
+template <bool MU>
+__device__ __forceinline__ void pair2_core(uint64_t bx, uint64_t by, uint64_t bz, const ARec &a, const K2 &k,
+                                           uint64_t &S, uint64_t &FS, uint64_t &TP, uint64_t &TM)
 {
     if (MU) {
         asm("{\n\t"
-            ".reg .b64 dx, dy, dz, d2, r, s, h, fs, xp, xm, tp, tm;\n\t"
-            ".reg .f32 d2x, d2y, rx, ry, sx, sy, fx, fy, px, py, mx, my;\n\t"
-            ".reg .pred p, q;\n\t"
-            ".reg .b32 ux, uy, vx, vy, f0, f1;\n\t"
-            "add.rn.f32x2 dx, %3, %6;\n\t"
-            "add.rn.f32x2 dy, %4, %7;\n\t"
-            "add.rn.f32x2 dz, %5, %8;\n\t"
-            "fma.rn.f32x2 d2, dx, dx, %11;\n\t"
+            ".reg .b64 dx, dy, dz, d2, r, h, xp, xm;\n\t"
+            ".reg .f32 d2x, d2y, rx, ry;\n\t"
+            "add.rn.f32x2 dx, %4, %7;\n\t"
+            "add.rn.f32x2 dy, %5, %8;\n\t"
+            "add.rn.f32x2 dz, %6, %9;\n\t"
+            "fma.rn.f32x2 d2, dx, dx, %12;\n\t"
             "fma.rn.f32x2 d2, dy, dy, d2;\n\t"
             "fma.rn.f32x2 d2, dz, dz, d2;\n\t"
             "mov.b64 {d2x, d2y}, d2;\n\t"
             "rsqrt.approx.ftz.f32 rx, d2x;\n\t"
             "rsqrt.approx.ftz.f32 ry, d2y;\n\t"
             "mov.b64 r, {rx, ry};\n\t"
-            "fma.rz.f32x2 s, d2, r, %12;\n\t"
-            "fma.rn.f32x2 h, s, %13, %14;\n\t"
-            "fma.rn.f32x2 fs, d2, r, h;\n\t"
-            "fma.rn.f32x2 xp, %3, %16, %9;\n\t"
-            "fma.rn.f32x2 xm, %3, %16, %10;\n\t"
-            "fma.rz.f32x2 tp, xp, r, %15;\n\t"
-            "fma.rz.f32x2 tm, xm, r, %15;\n\t"
-            "mov.b64 {sx, sy}, s;\n\t"
-            "mov.b64 {fx, fy}, fs;\n\t"
-            "mov.b64 {px, py}, tp;\n\t"
-            "mov.b64 {mx, my}, tm;\n\t"
-            "abs.f32 fx, fx;\n\t"
-            "abs.f32 fy, fy;\n\t"
-            "setp.gtu.f32 p, fx, %17;\n\t"
-            "setp.neu.or.f32 p, px, mx, p;\n\t"
-            "setp.gtu.f32 q, fy, %17;\n\t"
-            "setp.neu.or.f32 q, py, my, q;\n\t"
-            "selp.u32 f0, 1, 0, p;\n\t"
-            "selp.u32 f1, 2, 0, q;\n\t"
-            "or.b32 %2, f0, f1;\n\t"
-            "min.f32 sx, sx, %18;\n\t"
-            "min.f32 sy, sy, %18;\n\t"
-            "mov.b32 ux, sx;\n\t"
-            "mov.b32 uy, sy;\n\t"
-            "mov.b32 vx, mx;\n\t"
-            "mov.b32 vy, my;\n\t"
-            "shl.b32 ux, ux, %20;\n\t"
-            "shl.b32 uy, uy, %20;\n\t"
-            "shl.b32 vx, vx, %21;\n\t"
-            "shl.b32 vy, vy, %21;\n\t"
-            "add.u32 ux, ux, vx;\n\t"
-            "add.u32 uy, uy, vy;\n\t"
-            "add.u32 %0, ux, %19;\n\t"
-            "add.u32 %1, uy, %19;\n\t"
+            "fma.rz.f32x2 %0, d2, r, %13;\n\t"
+            "fma.rn.f32x2 h, %0, %14, %15;\n\t"
+            "fma.rn.f32x2 %1, d2, r, h;\n\t"
+            "fma.rn.f32x2 xp, %4, %17, %10;\n\t"
+            "fma.rn.f32x2 xm, %4, %17, %11;\n\t"
+            "fma.rz.f32x2 %2, xp, r, %16;\n\t"
+            "fma.rz.f32x2 %3, xm, r, %16;\n\t"
             "}"
-            : "=r"(a0), "=r"(a1), "=r"(flag)
+            : "=&l"(S), "=&l"(FS), "=&l"(TP), "=&l"(TM)
             : "l"(bx), "l"(by), "l"(bz), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(u64of(a.cp)),
-              "l"(u64of(a.cm)), "l"(k.tiny), "l"(k.ms), "l"(k.m1), "l"(k.mh), "l"(k.mt), "l"(k.nm), "f"(cs), "f"(stop),
-              "r"(Kl), "n"(LS), "n"(LT));
+              "l"(u64of(a.cm)), "l"(k.tiny), "l"(k.ms), "l"(k.m1), "l"(k.mh), "l"(k.mt), "l"(k.nm));
     } else {
         asm("{\n\t"
-            ".reg .b64 dx, dy, dz, d2, r, s, h, fs;\n\t"
-            ".reg .f32 d2x, d2y, rx, ry, sx, sy, fx, fy;\n\t"
-            ".reg .pred p, q;\n\t"
-            ".reg .b32 ux, uy, f0, f1;\n\t"
-            "add.rn.f32x2 dx, %3, %6;\n\t"
-            "add.rn.f32x2 dy, %4, %7;\n\t"
-            "add.rn.f32x2 dz, %5, %8;\n\t"
-            "fma.rn.f32x2 d2, dx, dx, %9;\n\t"
+            ".reg .b64 dx, dy, dz, d2, r, h;\n\t"
+            ".reg .f32 d2x, d2y, rx, ry;\n\t"
+            "add.rn.f32x2 dx, %2, %5;\n\t"
+            "add.rn.f32x2 dy, %3, %6;\n\t"
+            "add.rn.f32x2 dz, %4, %7;\n\t"
+            "fma.rn.f32x2 d2, dx, dx, %8;\n\t"
             "fma.rn.f32x2 d2, dy, dy, d2;\n\t"
             "fma.rn.f32x2 d2, dz, dz, d2;\n\t"
             "mov.b64 {d2x, d2y}, d2;\n\t"
             "rsqrt.approx.ftz.f32 rx, d2x;\n\t"
             "rsqrt.approx.ftz.f32 ry, d2y;\n\t"
             "mov.b64 r, {rx, ry};\n\t"
-            "fma.rz.f32x2 s, d2, r, %10;\n\t"
-            "fma.rn.f32x2 h, s, %11, %12;\n\t"
-            "fma.rn.f32x2 fs, d2, r, h;\n\t"
-            "mov.b64 {sx, sy}, s;\n\t"
-            "mov.b64 {fx, fy}, fs;\n\t"
-            "abs.f32 fx, fx;\n\t"
-            "abs.f32 fy, fy;\n\t"
-            "setp.gtu.f32 p, fx, %13;\n\t"
-            "setp.gtu.f32 q, fy, %13;\n\t"
-            "selp.u32 f0, 1, 0, p;\n\t"
-            "selp.u32 f1, 2, 0, q;\n\t"
-            "or.b32 %2, f0, f1;\n\t"
-            "min.f32 sx, sx, %14;\n\t"
-            "min.f32 sy, sy, %14;\n\t"
-            "mov.b32 ux, sx;\n\t"
-            "mov.b32 uy, sy;\n\t"
-            "shl.b32 ux, ux, %16;\n\t"
-            "shl.b32 uy, uy, %16;\n\t"
-            "add.u32 %0, ux, %15;\n\t"
-            "add.u32 %1, uy, %15;\n\t"
+            "fma.rz.f32x2 %0, d2, r, %9;\n\t"
+            "fma.rn.f32x2 h, %0, %10, %11;\n\t"
+            "fma.rn.f32x2 %1, d2, r, h;\n\t"
             "}"
-            : "=r"(a0), "=r"(a1), "=r"(flag)
+            : "=&l"(S), "=&l"(FS)
             : "l"(bx), "l"(by), "l"(bz), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(k.tiny),
-              "l"(k.ms), "l"(k.m1), "l"(k.mh), "f"(cs), "f"(stop), "r"(Kl), "n"(LS));
+              "l"(k.ms), "l"(k.m1), "l"(k.mh));
+        TP = TM = 0;
     }
 }
+
+__device__ __forceinline__ float lo_f(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi_f(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+
+// Histogram addresses of the two pairs: the s row (S clamped to the spare
+// last row) and, with mu bins, the signed mu column of T-.
+template <bool MU, int LS, int LT>
+__device__ __forceinline__ void pair_addr(uint64_t S, uint64_t TM, float stop, uint32_t Kl, uint32_t &a0,
+                                          uint32_t &a1)
+{
+    a0 = Kl + (__float_as_uint(fminf(lo_f(S), stop)) << LS);
+    a1 = Kl + (__float_as_uint(fminf(hi_f(S), stop)) << LS);
+    if (MU) {
+        a0 += (uint32_t)TM << LT;
+        a1 += (uint32_t)(TM >> 32) << LT;
+    }
+}
+
+// Rare path: two pairs recomputed with one uncertainty flag each, by the
+// same instructions as the hot path's PTX block (so bit for bit the same
+// addresses and decisions).
+template <bool MU, int LS, int LT>
+__device__ __forceinline__ void pair2_flags(uint64_t bx, uint64_t by, uint64_t bz, const ARec &a, const K2 &k,
+                                            float cs, float stop, uint32_t Kl, uint32_t &a0, uint32_t &a1, bool &f0,
+                                            bool &f1)
+{
+    uint64_t S, FS, TP, TM;
+    pair2_core<MU>(bx, by, bz, a, k, S, FS, TP, TM);
+    pair_addr<MU, LS, LT>(S, TM, stop, Kl, a0, a1);
+    f0 = fabsf(lo_f(FS)) > cs;
+    f1 = fabsf(hi_f(FS)) > cs;
+    if (MU) {
+        f0 = f0 || lo_f(TP) != lo_f(TM);
+        f1 = f1 || hi_f(TP) != hi_f(TM);
+    }
+}
+
+// One a-point against this lane's four b-points (two packed pairs q = 0, 1),
+// in one block of hand-written PTX so that the uncertainty of all four pairs
+// accumulates in one predicate (setp with .or): the four histogram adds, and
+// the warp's vote on "some pair of this a-point is uncertain".  CHK (self
+// cell): a pair with a >= b goes to the lane's spare word instead.
+// Operands: %0 vote; %1-%6 b (x, y, z) of q = 0, 1; %7-%11 the a-record;
+// %12-%17 constants; %18 cs; %19 the s clamp; %20 Kl; %21, %22 LS, LT;
+// CHK: %23 a index, %24-%27 b indices of slots 0-3, %28 spare word.
+#define PD_DIFF(BX, BY, BZ)                          \
+    "add.rn.f32x2 dx, " BX ", %7;\n\t"                 \
+    "add.rn.f32x2 dy, " BY ", %8;\n\t"                 \
+    "add.rn.f32x2 dz, " BZ ", %9;\n\t"                 \
+    "fma.rn.f32x2 d2, dx, dx, %12;\n\t"                \
+    "fma.rn.f32x2 d2, dy, dy, d2;\n\t"                 \
+    "fma.rn.f32x2 d2, dz, dz, d2;\n\t"                 \
+    "mov.b64 {d2x, d2y}, d2;\n\t"                      \
+    "rsqrt.approx.ftz.f32 rx, d2x;\n\t"                \
+    "rsqrt.approx.ftz.f32 ry, d2y;\n\t"                \
+    "mov.b64 r, {rx, ry};\n\t"                         \
+    "fma.rz.f32x2 s, d2, r, %13;\n\t"                  \
+    "fma.rn.f32x2 h, s, %14, %15;\n\t"                 \
+    "fma.rn.f32x2 fs, d2, r, h;\n\t"                   \
+    "mov.b64 {sx, sy}, s;\n\t"                         \
+    "mov.b64 {fx, fy}, fs;\n\t"                        \
+    "abs.f32 fx, fx;\n\t"                              \
+    "abs.f32 fy, fy;\n\t"                              \
+    "setp.gtu.or.f32 p, fx, %18, p;\n\t"               \
+    "setp.gtu.or.f32 p, fy, %18, p;\n\t"               \
+    "min.f32 sx, sx, %19;\n\t"                         \
+    "min.f32 sy, sy, %19;\n\t"                         \
+    "mov.b32 ux, sx;\n\t"                              \
+    "mov.b32 uy, sy;\n\t"                              \
+    "shl.b32 ux, ux, %21;\n\t"                         \
+    "shl.b32 uy, uy, %21;\n\t"                         \
+    "add.u32 ux, ux, %20;\n\t"                         \
+    "add.u32 uy, uy, %20;\n\t"
+#define PD_MU(BX)                                    \
+    "fma.rn.f32x2 xp, " BX ", %17, %10;\n\t"           \
+    "fma.rn.f32x2 xm, " BX ", %17, %11;\n\t"           \
+    "fma.rz.f32x2 tp, xp, r, %16;\n\t"                 \
+    "fma.rz.f32x2 tm, xm, r, %16;\n\t"                 \
+    "mov.b64 {px, py}, tp;\n\t"                        \
+    "mov.b64 {mx, my}, tm;\n\t"                        \
+    "setp.neu.or.f32 p, px, mx, p;\n\t"                \
+    "setp.neu.or.f32 p, py, my, p;\n\t"                \
+    "mov.b32 vx, mx;\n\t"                              \
+    "mov.b32 vy, my;\n\t"                              \
+    "shl.b32 vx, vx, %22;\n\t"                         \
+    "shl.b32 vy, vy, %22;\n\t"                         \
+    "add.u32 ux, ux, vx;\n\t"                          \
+    "add.u32 uy, uy, vy;\n\t"
+#define PD_CHK(IB0, IB1)                             \
+    "setp.lt.u32 c, %23, " IB0 ";\n\t"                 \
+    "selp.b32 ux, ux, %28, c;\n\t"                     \
+    "setp.lt.u32 c, %23, " IB1 ";\n\t"                 \
+    "selp.b32 uy, uy, %28, c;\n\t"
+#define PD_RED                                       \
+    "red.shared.add.u32 [ux], 1;\n\t"                  \
+    "red.shared.add.u32 [uy], 1;\n\t"
+#define PD_HEAD                                                                     \
+    "{\n\t"                                                                           \
+    ".reg .b64 dx, dy, dz, d2, r, s, h, fs, xp, xm, tp, tm;\n\t"                      \
+    ".reg .f32 d2x, d2y, rx, ry, sx, sy, fx, fy, px, py, mx, my;\n\t"                 \
+    ".reg .b32 ux, uy, vx, vy;\n\t"                                                   \
+    ".reg .pred p, c;\n\t"                                                            \
+    "setp.ne.u32 p, %20, %20;\n\t"
+#define PD_TAIL                                      \
+    "vote.sync.any.pred p, p, 0xffffffff;\n\t"         \
+    "selp.u32 %0, 1, 0, p;\n\t"                        \
+    "}"
+
+template <bool MU, bool CHK, int LS, int LT>
+__device__ __forceinline__ bool apoint(const float2 (&BX)[NQ], const float2 (&BY)[NQ], const float2 (&BZ)[NQ],
+                                       const ARec &a, const K2 &k, float cs, float stop, uint32_t Kl, uint32_t ia,
+                                       const uint32_t (&IB)[NP], uint32_t dump)
+{
+    static_assert(NQ == 2, "the PTX block covers two packed pairs");
+    uint32_t any;
+#define PD_IN                                                                                                     \
+    "l"(u64of(BX[0])), "l"(u64of(BY[0])), "l"(u64of(BZ[0])), "l"(u64of(BX[1])), "l"(u64of(BY[1])),              \
+        "l"(u64of(BZ[1])), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(u64of(a.cp)),            \
+        "l"(u64of(a.cm)), "l"(k.tiny), "l"(k.ms), "l"(k.m1), "l"(k.mh), "l"(k.mt), "l"(k.nm), "f"(cs), "f"(stop), \
+        "r"(Kl), "n"(LS), "n"(LT)
+    if (MU && CHK) {
+        asm volatile(PD_HEAD PD_DIFF("%1", "%2", "%3") PD_MU("%1") PD_CHK("%24", "%25") PD_RED
+                         PD_DIFF("%4", "%5", "%6") PD_MU("%4") PD_CHK("%26", "%27") PD_RED PD_TAIL
+                     : "=r"(any)
+                     : PD_IN, "r"(ia), "r"(IB[0]), "r"(IB[1]), "r"(IB[2]), "r"(IB[3]), "r"(dump)
+                     : "memory");
+    } else if (MU) {
+        asm volatile(PD_HEAD PD_DIFF("%1", "%2", "%3") PD_MU("%1") PD_RED PD_DIFF("%4", "%5", "%6") PD_MU("%4")
+                         PD_RED PD_TAIL
+                     : "=r"(any)
+                     : PD_IN
+                     : "memory");
+    } else if (CHK) {
+        asm volatile(PD_HEAD PD_DIFF("%1", "%2", "%3") PD_CHK("%24", "%25") PD_RED PD_DIFF("%4", "%5", "%6")
+                         PD_CHK("%26", "%27") PD_RED PD_TAIL
+                     : "=r"(any)
+                     : PD_IN, "r"(ia), "r"(IB[0]), "r"(IB[1]), "r"(IB[2]), "r"(IB[3]), "r"(dump)
+                     : "memory");
+    } else {
+        asm volatile(PD_HEAD PD_DIFF("%1", "%2", "%3") PD_RED PD_DIFF("%4", "%5", "%6") PD_RED PD_TAIL
+                     : "=r"(any)
+                     : PD_IN
+                     : "memory");
+    }
+#undef PD_IN
+    return any != 0;
+}
+#undef PD_DIFF
+#undef PD_MU
+#undef PD_CHK
+#undef PD_RED
+#undef PD_HEAD
+#undef PD_TAIL
 
 // Per-lane histogram address constants (see Sh).
 struct Addr {
@@ -292,9 +397,11 @@ __device__ __forceinline__ void load_tile(const float4 *buf, uint32_t nb, int la
 
 // Every pair of the a-chunk (na points from sorted index a0) with the first nb
 // entries of the warp's buffer; CHK: only pairs a < b count (the self cell
-// of an auto count).  A partial tile skips the packed pairs whose slots are
-// all padding.  An uncertain pair's add is taken back at once (its address is
-// still in registers) and the pair joins the recheck list.
+// of an auto count).  Padding slots hold far-away points whose adds land in
+// the spare last row.  The pairs of one a-point or their uncertainty into one
+// predicate per lane; when any lane's is set, the a-point's pairs are
+// recomputed with a flag each, and each uncertain pair's add is taken back
+// and the pair joins the recheck list.
 template <bool MU, int R, int LOGC, bool CHK>
 __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams &dp, const Mesh &m,
                                      const unsigned long long *T, const WarpMem &wm, const Addr &ad, uint32_t nb,
@@ -303,7 +410,7 @@ __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams 
 {
     float2 BX[NQ], BY[NQ], BZ[NQ];
     load_tile(wm.buf, nb, lane, BX, BY, BZ);
-    uint32_t IB[NP];
+    uint32_t IB[NP] = {0u, 0u, 0u, 0u};
     if (CHK) {
 #pragma unroll
         for (int p = 0; p < NP; p++) {
@@ -320,15 +427,22 @@ __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams 
     const K2 k2{u64of(make_float2(dp.tiny, dp.tiny)), u64of(make_float2(MAG_S, MAG_S)), u64of(make_float2(-1.0f, -1.0f)),
                 u64of(make_float2(MAG_S - 0.5f, MAG_S - 0.5f)), u64of(make_float2(MAG_T, MAG_T)),
                 u64of(make_float2(dp.nmu, dp.nmu))};
-    const uint32_t nq = (nb + 63u) >> 6;   // packed pairs of this lane with any slot below nb
     const uint32_t lt = (1u << lane) - 1u;
-    // the uncertain pairs of a-point ai (flags fl, addresses xs): each add is
-    // taken back and the pair joins the recheck list
-    auto settle = [&](uint32_t ai, uint32_t fl, const uint32_t (&xs)[NP]) {
+    // a-point ai had an uncertain pair in some lane: recompute its pairs with
+    // one flag each (padding slots and, in the self cell, pairs a >= b never
+    // count), take back each uncertain pair's add and put it on the recheck list
+    auto settle = [&](uint32_t ai) {
+        const ARec a = load_a(wm.arec, ai);
         const uint32_t ia = a0 + ai;
+        uint32_t xs[NP];
+        bool fl[NP];
+#pragma unroll
+        for (int q = 0; q < NQ; q++)
+            pair2_flags<MU, LS, LT>(u64of(BX[q]), u64of(BY[q]), u64of(BZ[q]), a, k2, dp.cs, dp.s_top, ad.Kl,
+                                    xs[2 * q], xs[2 * q + 1], fl[2 * q], fl[2 * q + 1]);
 #pragma unroll
         for (int p = 0; p < NP; p++) {
-            const bool x = (fl >> p) & 1u;
+            const bool x = fl[p] && ((live >> p) & 1u) && (!CHK || ia < IB[p]);
             const unsigned mk = __ballot_sync(0xffffffffu, x);
             if (mk) {
                 if (x) {
@@ -344,46 +458,11 @@ __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams 
             }
         }
     };
-    // The flags of a-point ai are examined while a-point ai + 1 is computed,
-    // so that no pass waits on its own pairs' chain before the next begins.
-    uint32_t pxs[NP];
-    uint32_t pfl = 0;
-#pragma unroll
-    for (int p = 0; p < NP; p++) pxs[p] = ad.dump;
 #pragma unroll 1
     for (uint32_t ai = 0; ai < na; ai++) {
         const ARec a = load_a(wm.arec, ai);
-        uint32_t xs[NP];
-        uint32_t fl = 0;
-#pragma unroll
-        for (int q = 0; q < NQ; q++) {
-            xs[2 * q] = xs[2 * q + 1] = ad.dump;
-            if (q == 0 || (uint32_t)q < nq) {
-                uint32_t f;
-                pair2<MU, LS, LT>(u64of(BX[q]), u64of(BY[q]), u64of(BZ[q]), a, k2, dp.cs, dp.s_top, ad.Kl,
-                                  xs[2 * q], xs[2 * q + 1], f);
-                if (CHK) {
-                    const uint32_t ia = a0 + ai;
-                    if (!(ia < IB[2 * q])) {
-                        xs[2 * q] = ad.dump;
-                        f &= 2u;
-                    }
-                    if (!(ia < IB[2 * q + 1])) {
-                        xs[2 * q + 1] = ad.dump;
-                        f &= 1u;
-                    }
-                }
-                red_add(xs[2 * q], 1u);
-                red_add(xs[2 * q + 1], 1u);
-                fl |= f << (2 * q);
-            }
-        }
-        if (__any_sync(0xffffffffu, pfl)) settle(ai - 1, pfl, pxs);
-        pfl = fl & live;
-#pragma unroll
-        for (int p = 0; p < NP; p++) pxs[p] = xs[p];
+        if (apoint<MU, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB, ad.dump)) settle(ai);
     }
-    if (__any_sync(0xffffffffu, pfl)) settle(na - 1, pfl, pxs);
     __syncwarp();
 }
 
