@@ -1,32 +1,42 @@
 #!/usr/bin/env python
-"""Benchmark of the LC covariance hot path on the mid workload.
+"""Benchmark of the LC covariance hot path on the scale workload.
 
-Workload (per GPU, weak scaling): 100 mocks in a periodic box L = 1000 Mpc/h,
-N_d = 100 000 Neyman-Scott points (parents 1e-5 (Mpc/h)^-3, sigma = 3 Mpc/h)
-and two uniform random subsets R1, R2 of N_d points each (the M_a = 1 pair of
-the linear construction), 40 linear s bins on [0, 200) Mpc/h x 10 mu bins
-with the x line of sight.
+Headline workload (per GPU, weak scaling): 200 mocks in a periodic box
+L = 2000 Mpc/h, N_d = 1e6 Neyman-Scott points (parents 2e-6 (Mpc/h)^-3,
+sigma = 3 Mpc/h) and two uniform random subsets R1, R2 of N_d points each
+(the M_a = 1 pair of the linear construction), 40 linear s bins on
+[0, 200) Mpc/h x 10 mu bins with the x line of sight.
 
 One step = the whole hot path: quantisation + chaining-mesh build + pair
 counts DD, DR1, DR2, RR1, RR2 of every mock (one persistent launch) + split
 Landy-Szalay for R1, R2 and R1 u R2 + the LC covariance (Eqs. R1R2, LCdef)
 with M = 50.  `value` is mocks/s with inputs resident in HBM; `e2e` is the
 same metric through the public API with the positions copied from pinned
-host memory and C^LC copied back inside every step.
+host memory and C^LC copied back inside every step.  The xi and covariance
+errors of the timed step are measured against the float64 oracle on the
+same counts and the same xi rows.
+
+Extra keys time the mid, batching (all 1000 uneven cut-sky mocks, midpoint
+line of sight) and small workloads through the same whole step, each with
+its own one-launch-per-mock-per-term comparison; the covariance-only
+precision workload; the brute-force (Smp, M = 50) comparison; and the steps
+after the covariance.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
+import re
 import statistics
 import subprocess
 import sys
 import tempfile
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -46,29 +56,29 @@ M_FINAL = 50.0             # random-catalogue size of the target covariance (the
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--mocks", type=int, default=synth.MID.n_mock, help="mocks per GPU")
-    p.add_argument("--nd", type=int, default=synth.MID.n_d, help="data points per mock")
+    p.add_argument("--workload", default="scale", choices=sorted(synth.WORKLOADS),
+                   help="headline workload (the metric is quoted on scale)")
+    p.add_argument("--mocks", type=int, default=0, help="mocks per GPU (0: the workload's count)")
+    p.add_argument("--nd", type=int, default=0, help="data points per mock (0: the workload's N_d)")
     p.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3"])
+    p.add_argument("--extras", default="mid,batching,small",
+                   help="comma list of extra workloads timed through the whole step (empty: none)")
+    p.add_argument("--batching-mocks", type=int, default=synth.BATCHING.n_mock)
     p.add_argument("--no-precision-config", action="store_true",
                    help="skip the covariance-only measurement on 3500 mocks x 200 bins")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--subdiv", type=int, default=0, help="pin the mesh subdivision (0: library choice)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--batching-mocks", type=int, default=8,
-                   help="mocks of the cut-sky batching shape timed as context (0: skip)")
-    p.add_argument("--scale-mocks", type=int, default=2,
-                   help="mocks of the scale shape (1e6 points) timed as context (0: skip)")
     p.add_argument("--smp-mocks", type=int, default=4,
                    help="mocks of the brute-force (Smp, M=50) comparison run; 0 skips it")
     p.add_argument("--cov-only", action="store_true",
                    help="two split-precision LC covariances of 3500 mocks x 200 bins, then exit (profiler captures)")
     p.add_argument("--count-only", action="store_true",
-                   help="one warm-up and one batched tpcf_count of the workload, then exit (profiler captures)")
-    p.add_argument("--count-only-batching", type=int, default=0, metavar="N",
-                   help="like --count-only on N mocks of the cut-sky batching shape (midpoint line of sight)")
+                   help="one warm-up and one batched tpcf_count of the headline workload, then exit "
+                        "(profiler captures)")
     return p.parse_args()
 
 
@@ -127,88 +137,270 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# workload
+# workloads
 # ---------------------------------------------------------------------------
 
-def make_host_inputs(n_mock, n_d, first_mock):
-    """Positions of all mocks in one float64 array; per mock (data, R1, R2) offsets."""
-    w = synth.MID
-    blocks, layout = [], []
-    off = 0
-    for m in range(first_mock, first_mock + n_mock):
-        mk = w.make_mock(m, n_d=n_d, M=2)
-        parts = [mk.data] + mk.randoms
-        sizes = [len(x) for x in parts]
-        layout.append((off, sizes))
-        blocks.extend(parts)
-        off += sum(sizes)
-    return np.concatenate(blocks), layout
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
-def mock_views(pos_dev, layout):
+def workload_desc(w, n_mock, n_d=0):
+    """One wording of a workload, shared by both arms of the benchmark."""
+    if w.shell is None:
+        geo = f"periodic L={w.L:g} Mpc/h"
+    else:
+        geo = f"cut-sky octant shell {w.shell[0]:g}-{w.shell[1]:g} Mpc/h"
+    if w.n_d_range is not None and not n_d:
+        pts = f"N_d Poisson-scattered in {w.n_d_range[0]}-{w.n_d_range[1]}"
+    else:
+        pts = f"N_d={n_d or w.n_d}"
+    return (f"{w.name}: {n_mock} mocks/GPU, {geo}, {pts} Neyman-Scott (n_p={w.n_parent:g}, sigma={w.sigma:g}), "
+            f"R1+R2 uniform of N_d each, {w.n_s} s x {w.n_mu} mu bins to {w.s_max:g} Mpc/h, "
+            f"{'midpoint' if w.los == 'midpoint' else 'x'} line of sight; LS (R1, R2, R1uR2) + LC covariance "
+            f"(M={M_FINAL:g})")
+
+
+def host_inputs(w, first, n_mock, n_d=0, pinned=False):
+    """Positions of mocks first..first+n_mock-1 of workload w in one float64 [n][3] array (a pinned torch
+    tensor when `pinned`), drawn by a thread pool; per mock (offset, (n_d, n_r1, n_r2, ...))."""
+    import torch
+    sizes = [n_d or w.n_d_of(m) for m in range(first, first + n_mock)]
+    layout, off = [], 0
+    for nd in sizes:
+        layout.append((off, (nd,) * (1 + w.M)))
+        off += nd * (1 + w.M)
+    if pinned:
+        buf = torch.empty((off, 3), dtype=torch.float64, pin_memory=True)
+        arr = buf.numpy()
+    else:
+        arr = np.empty((off, 3), dtype=np.float64)
+        buf = torch.from_numpy(arr)
+
+    def fill(i):
+        mk = w.make_mock(first + i, n_d=n_d or None)
+        o, sz = layout[i]
+        for part, n in zip([mk.data] + mk.randoms, sz):
+            if len(part) != n:
+                raise RuntimeError(f"mock {first + i}: catalogue of {len(part)} points, expected {n}")
+            arr[o:o + n] = part
+            o += n
+
+    with ThreadPoolExecutor(max(1, min(32, host_cores()))) as ex:
+        list(ex.map(fill, range(n_mock)))
+    return buf, layout
+
+
+def mock_views(pos, layout):
     mocks = []
-    for off, (nd, n1, n2) in layout:
-        mocks.append({"data": pos_dev[off:off + nd], "randoms": pos_dev[off + nd:off + nd + n1 + n2],
-                      "offsets": [0, n1, n1 + n2]})
+    for off, sz in layout:
+        nd, nr = sz[0], sz[1:]
+        offs = [0]
+        for n in nr:
+            offs.append(offs[-1] + n)
+        mocks.append({"data": pos[off:off + nd], "randoms": pos[off + nd:off + nd + offs[-1]], "offsets": offs})
     return mocks
+
+
+def binning_of(tp, w):
+    if w.geometry == "periodic":
+        return tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_PERIODIC, w.L)
+    return tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_OPEN, w.L, origin=w.origin,
+                           los=tp.TPCF_LOS_MIDPOINT if w.los == "midpoint" else tp.TPCF_LOS_X, observer=w.observer)
+
+
+class Job:
+    """One workload resident on the device: the whole step (counts, three split LS estimates, LC covariance)."""
+
+    SELS = {"a1": [0], "a2": [1], "b": [0, 1]}
+
+    def __init__(self, tp, ctx, dev, w, pos, layout, prec, world):
+        import torch
+        self.tp, self.ctx, self.dev, self.w, self.prec, self.world = tp, ctx, dev, w, prec, world
+        self.layout = layout
+        self.mocks = mock_views(pos, layout)
+        self.n_mock = len(layout)
+        self.nd = [sz[0] for _, sz in layout]
+        self.nr = [list(sz[1:]) for _, sz in layout]
+        self.b = binning_of(tp, w)
+        self.nbin = w.n_s * w.n_mu
+        n, M, nbin = self.n_mock, w.M, self.nbin
+        self.outc = {"dd": torch.empty((n, nbin), dtype=torch.int64, device=dev),
+                     "dr": torch.empty((n, M, nbin), dtype=torch.int64, device=dev),
+                     "rr": torch.empty((n, M, nbin), dtype=torch.int64, device=dev)}
+        self.xi = {k: torch.empty((n, nbin), dtype=torch.float64, device=dev) for k in self.SELS}
+        self.rows = self.xi
+
+    def step(self, mode=None, mocks=None):
+        from paper_2205_11852_gb300 import multi
+        tp, ctx = self.tp, self.ctx
+        ctx.tpcf_count(mocks or self.mocks, self.b, mode=tp.TPCF_BATCHED if mode is None else mode, out=self.outc)
+        for k, sel in self.SELS.items():
+            ctx.tpcf_ls(self.outc["dd"], self.outc["dr"], self.outc["rr"], self.nd, self.nr, sel, out=self.xi[k])
+        self.rows = {k: multi.gather_rows(v, self.world) for k, v in self.xi.items()}
+        return ctx.tpcf_lc_cov(self.rows["a1"], self.rows["a2"], self.rows["b"], 1, M_FINAL, self.prec,
+                               want_parts=False)
+
+    def errors(self, cov):
+        """xi of the last step against the oracle's float64 LS on the same counts, |dxi| / (1 + |xi|), and
+        C^LC against the oracle's float64 construction on the same xi rows, |dC| / sqrt(C^a_ii C^a_jj)."""
+        import oracle
+        dd, dr, rr = (self.outc[k].cpu().numpy() for k in ("dd", "dr", "rr"))
+        rel, nan_mismatch = [], 0
+        for k, sel in self.SELS.items():
+            got = self.xi[k].cpu().numpy()
+            for m in range(self.n_mock):
+                ref = oracle.ls(dd[m], dr[m], rr[m], self.nd[m], self.nr[m], sel)
+                nan_r, nan_g = np.isnan(ref), np.isnan(got[m])
+                nan_mismatch += int(np.count_nonzero(nan_r != nan_g))
+                ok = ~(nan_r | nan_g)
+                rel.append(np.abs(got[m][ok] - ref[ok]) / (1.0 + np.abs(ref[ok])))
+        rel = np.concatenate(rel)
+        rows = {k: v.cpu().numpy() for k, v in self.rows.items()}
+        ref = oracle.lc_cov(rows["a1"], rows["a2"], rows["b"], 1, M_FINAL)
+        d = np.sqrt(np.abs(np.diag(ref["Ca"])))
+        scale = np.outer(d, d)
+        scale[scale == 0] = 1.0
+        ce = np.abs(cov["C_lc"].cpu().numpy() - ref["C_lc"]) / scale
+        return ({"max": float(rel.max()), "rms": float(np.sqrt(np.mean(rel * rel))), "nan_mismatch": nan_mismatch,
+                 "definition": "|xi - oracle.ls(same counts)| / (1 + |xi|) over mocks, bins and R1, R2, R1uR2"},
+                {"max": float(ce.max()), "rms": float(np.sqrt(np.mean(ce * ce))),
+                 "definition": "|C - oracle.lc_cov(same xi)| / sqrt(C^a_ii C^a_jj) over all elements"})
+
+
+def event_time(fn, n, sync):
+    """ms per call of fn over n calls, CUDA events on the current stream, synchronised on both sides."""
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sync()
+    e0.record(stream)
+    out = None
+    for _ in range(n):
+        out = fn()
+    e1.record(stream)
+    sync()
+    return e0.elapsed_time(e1) / n, out
+
+
+def kernel_code_hash(path):
+    """sha256 prefix of a CUDA source with comments and blank space removed: it changes
+    only when the code does (a profile taken before a comment edit still describes it)."""
+    src = open(path, encoding="utf-8").read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = "\n".join(line.strip() for line in src.splitlines() if line.strip())
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
+def kernel_source(pair_kernel):
+    return "pairdirect.cu" if pair_kernel == 1 else "paircount.cu"
+
+
+def measured_traffic(workload, n_mock, pair_kernel):
+    """DRAM bytes of one pair-count launch from the committed ncu summary of this workload, if it was taken
+    on the current kernel code (else None)."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "paircount_traffic.json")))[workload]
+        src = kernel_source(pair_kernel)
+        code = kernel_code_hash(os.path.join(ROOT, "paper_2205_11852_gb300", "csrc", src))
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("kernel") != src or code != rec.get("kernel_code_sha256_prefix"):
+        return None
+    return rec["dram_bytes_per_mock"] * n_mock
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
 
-def oracle_sample_rate(n_d, target_s, seed_mock=0):
-    """Time the oracle's brute-force counts on a row sample of one mid mock.
+def oracle_sample_rate(w, n_d, target_s, seed_mock=0):
+    """Time the oracle's brute-force counts on a row sample of one mock of workload w.
 
     The five terms of one mock cost 3.5 N_d^2 pair tests (DD and RR_i: N_d^2/2
-    each, DR_i: N_d^2 each).  A sample of k a-rows against all b-points runs
-    k N_d tests per term; the rate in mocks/s is the executed fraction of the
-    mock's pair tests divided by the time taken.
+    each, DR_i: N_d^2 each, with N_r,i = N_d).  A sample of k a-rows against all
+    b-points runs k N_d tests per term; the rate in mocks/s is the executed
+    fraction of the mock's pair tests divided by the time taken.
     """
     import oracle
-    w = synth.MID
-    mk = w.make_mock(seed_mock, n_d=n_d, M=2)
-    ob = oracle.Binning(w.s_edges, w.n_mu, oracle.PERIODIC, w.L)
-    qd = oracle.quantize(mk.data, oracle.PERIODIC, w.L)
-    qr = [oracle.quantize(r, oracle.PERIODIC, w.L) for r in mk.randoms]
+    mk = w.make_mock(seed_mock, n_d=n_d or None)
+    n = len(mk.data)
+    geo = oracle.PERIODIC if w.geometry == "periodic" else oracle.OPEN
+    ob = oracle.Binning(w.s_edges, w.n_mu, geo, w.L, origin=w.origin,
+                        los=oracle.LOS_MIDPOINT if w.los == "midpoint" else oracle.LOS_X, observer=w.observer)
+    qd = oracle.quantize(mk.data, geo, w.L, w.origin)
+    qr = [oracle.quantize(r, geo, w.L, w.origin) for r in mk.randoms]
 
     def run(k):
         t0 = time.perf_counter()
         tests = 0
         a = np.ascontiguousarray(qd[:, :k])
         oracle.count_pairs(a, qd, ob)      # DD rows against all points
-        tests += k * n_d
+        tests += k * n
         for r in qr:
             oracle.count_pairs(a, r, ob)   # DR_i rows
-            tests += k * n_d
+            tests += k * r.shape[1]
             ar = np.ascontiguousarray(r[:, :k])
             oracle.count_pairs(ar, r, ob)  # RR_i rows against all points
-            tests += k * n_d
+            tests += k * r.shape[1]
         return time.perf_counter() - t0, tests
 
-    k = max(16, n_d // 2000)
+    k = max(16, n // 20000)
     dt, tests = run(k)
     # grow the sample until it takes at least ~70% of the target time (or the whole mock)
-    while dt < 0.7 * target_s and k < n_d:
-        k = int(min(n_d, max(2 * k, k * 0.9 * target_s / max(dt, 1e-3))))
+    while dt < 0.7 * target_s and k < n:
+        k = int(min(n, max(2 * k, k * 0.9 * target_s / max(dt, 1e-3))))
         dt, tests = run(k)
-    full = 3.5 * n_d * n_d
+    full = 3.5 * float(n) * float(n)
     frac = tests / full
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"mocks_per_s": frac / dt, "seconds": dt, "rows": k, "fraction_of_mock": frac, "cores": cores,
+    return {"mocks_per_s": frac / dt, "seconds": dt, "rows": k, "fraction_of_mock": frac, "cores": host_cores(),
             "pair_tests_per_s": tests / dt}
 
 
-def smp_measure(tp, ctx, dev, b, prec, n_mock, n_d, M=50, reps=2):
+def sample_text(r):
+    return (f"brute-force counts of {r['rows']} a-rows of mock 0 against all points (DD, DR1, DR2, RR1, RR2), "
+            f"{r['fraction_of_mock']:.4%} of one mock's pair tests, {r['seconds']:.1f} s")
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle as it stands, on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[args.workload]
+    n_mock = args.mocks or w.n_mock
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample_rate(w, args.nd, target_s=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
+        if i >= args.warmup:
+            rates.append(r)
+    v = statistics.median([r["mocks_per_s"] for r in rates])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "mocks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * statistics.median([r["seconds"] for r in rates]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": workload_desc(w, n_mock, args.nd), "global_batch": n_mock * world},
+            "cpu_baseline": {"value": v, "unit": "mocks/s", "cores": rates[0]["cores"], "kind": "oracle",
+                             "sample": sample_text(rates[0]) + " per step"},
+            "e2e": {"value": v, "unit": "mocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# extra measurements
+# ---------------------------------------------------------------------------
+
+def smp_measure(tp, ctx, dev, prec, n_mock, M=50, reps=2):
     """Brute-force (Smp) path on the mid shape: every mock against all M random
     subsets in one batched launch, LS over all subsets, sample covariance
     (Eq. bruteforce).  Returns ms per step and the pair totals."""
     import torch
     w = synth.MID
-    mks = [w.make_mock(m, n_d=n_d, M=M) for m in range(n_mock)]
+    n_d = w.n_d
+    mks = [w.make_mock(m, M=M) for m in range(n_mock)]
     dm = [{"data": torch.from_numpy(mk.data).to(dev),
            "randoms": torch.from_numpy(np.concatenate(mk.randoms)).to(dev),
            "offsets": [i * n_d for i in range(M + 1)]} for mk in mks]
+    b = binning_of(tp, w)
     nbin = w.n_s * w.n_mu
     out = {"dd": torch.empty((n_mock, nbin), dtype=torch.int64, device=dev),
            "dr": torch.empty((n_mock, M, nbin), dtype=torch.int64, device=dev),
@@ -223,97 +415,68 @@ def smp_measure(tp, ctx, dev, b, prec, n_mock, n_d, M=50, reps=2):
         return ctx.tpcf_sample_cov(xi, prec)
 
     step()
-    torch.cuda.synchronize()
     ctx.tpcf_set_timing(True)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, _ = event_time(step, reps, torch.cuda.synchronize)
     info = ctx.tpcf_last_count_info()
     ctx.tpcf_set_timing(False)
-    rc = ctx.tpcf_sync()
-    return {"ms": e0.elapsed_time(e1) / reps, "n_binned": info["n_binned"], "n_candidates": info["n_candidates"],
-            "status": rc}
+    return {"ms": ms, "n_binned": info["n_binned"], "n_candidates": info["n_candidates"], "status": ctx.tpcf_sync()}
 
 
-def batching_measure(tp, ctx, dev, n_mock, reps=2):
-    """The cut-sky batching workload's shape on a sample of its mocks: uneven N_d (Poisson-scattered in
-    50k-400k), octant shell 1200-2400 Mpc/h, midpoint line of sight, R1 + R2 of N_d each, 40 s x 5 mu
-    bins; all mocks and terms in one batched call.  Returns ms per call and the pair totals."""
+def extra_workload(tp, dev, w, n_mock, prec, reps=2):
+    """One more workload through the whole step on its own context: batched and one-launch-per-mock-per-term
+    rates, the pair-kernel rate, counts of the two paths compared on 2 mocks, xi and covariance errors."""
     import torch
-    w = synth.BATCHING
-    mks = [w.make_mock(m) for m in range(n_mock)]
-    dm = [{"data": torch.from_numpy(mk.data).to(dev),
-           "randoms": torch.from_numpy(np.concatenate(mk.randoms)).to(dev),
-           "offsets": [0, len(mk.randoms[0]), len(mk.randoms[0]) + len(mk.randoms[1])]} for mk in mks]
-    b = tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_OPEN, w.L, los=tp.TPCF_LOS_MIDPOINT, observer=w.observer)
-    nbin = w.n_s * w.n_mu
-    out = {"dd": torch.empty((n_mock, nbin), dtype=torch.int64, device=dev),
-           "dr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev),
-           "rr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev)}
-    for _ in range(2):
-        ctx.tpcf_count(dm, b, mode=tp.TPCF_BATCHED, out=out)
-    torch.cuda.synchronize()
-    ctx.tpcf_set_timing(True)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        ctx.tpcf_count(dm, b, mode=tp.TPCF_BATCHED, out=out)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    info = ctx.tpcf_last_count_info()
-    ctx.tpcf_set_timing(False)
-    rc = ctx.tpcf_sync()
-    ms = e0.elapsed_time(e1) / reps
-    return {"workload": (f"batching shape, {n_mock} mocks (N_d {min(len(mk.data) for mk in mks)}-"
-                         f"{max(len(mk.data) for mk in mks)}), cut-sky octant shell, midpoint line of sight, "
-                         "40 s x 5 mu bins: counts only, one batched call"),
-            "value": n_mock / (ms * 1e-3), "unit": "mocks/s", "ms_per_call": ms,
-            "gpairs_binned_per_s": info["n_binned"] / (ms * 1e-3) / 1e9,
-            "pairs_binned_per_call": info["n_binned"], "candidate_pairs_per_call": info["n_candidates"],
-            "pair_kernel_ms": info["paircount_ms"] / max(1, info["timed_calls"]), "status": rc}
+    ctx = tp.Context(dev.index)
+    try:
+        pos, layout = host_inputs(w, 0, n_mock)
+        pos = pos.to(dev)
+        job = Job(tp, ctx, dev, w, pos, layout, prec, 1)
+        chk_b = ctx.tpcf_count(job.mocks[:2], job.b, mode=tp.TPCF_BATCHED)
+        chk_p = ctx.tpcf_count(job.mocks[:2], job.b, mode=tp.TPCF_PER_LAUNCH)
+        same = all(torch.equal(chk_b[k], chk_p[k]) for k in ("dd", "dr", "rr"))
+        job.step()
+        ctx.tpcf_set_timing(True)
+        ms, cov = event_time(job.step, reps, torch.cuda.synchronize)
+        info = ctx.tpcf_last_count_info()
+        ctx.tpcf_set_timing(False)
+        xi_err, cov_err = job.errors(cov)
+        k_ms = info["paircount_ms"] / max(1, info["timed_calls"])
+        job.step(mode=tp.TPCF_PER_LAUNCH)
+        ms_pl, _ = event_time(lambda: job.step(mode=tp.TPCF_PER_LAUNCH), 1, torch.cuda.synchronize)
+        rc = ctx.tpcf_sync()
+        return {"workload": workload_desc(w, n_mock), "value": n_mock / (ms * 1e-3), "unit": "mocks/s",
+                "ms_per_step": ms, "steps": reps, "pair_kernel_ms": k_ms,
+                "gpairs_binned_per_s": info["n_binned"] / (k_ms * 1e-3) / 1e9,
+                "pairs_binned_per_step": info["n_binned"], "candidate_pairs_per_step": info["n_candidates"],
+                "pair_kernel": info["pair_kernel"], "cell_subdiv": info["cell_subdiv"],
+                "per_launch": {"value": n_mock / (ms_pl * 1e-3), "unit": "mocks/s", "ms_per_step": ms_pl,
+                               "batched_over_per_launch": ms_pl / ms},
+                "batched_equals_per_launch": bool(same), "xi_err": xi_err, "cov_err": cov_err, "status": rc}
+    finally:
+        ctx.close()
+        torch.cuda.empty_cache()
 
 
-def scale_measure(tp, ctx, dev, n_mock, reps=2):
-    """The scale workload's shape on a sample of its mocks: periodic L=2000 Mpc/h, N_d=1e6 Neyman-Scott,
-    R1 + R2 of N_d each, 40 s x 10 mu bins, x line of sight; all mocks and terms in one batched call."""
+def precision_measure(tp, ctx, dev):
+    """Covariance-only workload: 3500 mocks x 3 variants x 200 (s, mu) bins, float64 vs split precision on the
+    tensor cores, error against the oracle."""
     import torch
-    w = synth.SCALE
-    mks = [w.make_mock(m) for m in range(n_mock)]
-    dm = [{"data": torch.from_numpy(mk.data).to(dev),
-           "randoms": torch.from_numpy(np.concatenate(mk.randoms)).to(dev),
-           "offsets": [0, w.n_d, 2 * w.n_d]} for mk in mks]
-    b = tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_PERIODIC, w.L)
-    nbin = w.n_s * w.n_mu
-    out = {"dd": torch.empty((n_mock, nbin), dtype=torch.int64, device=dev),
-           "dr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev),
-           "rr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev)}
-    for _ in range(2):
-        ctx.tpcf_count(dm, b, mode=tp.TPCF_BATCHED, out=out)
-    torch.cuda.synchronize()
-    ctx.tpcf_set_timing(True)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        ctx.tpcf_count(dm, b, mode=tp.TPCF_BATCHED, out=out)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    info = ctx.tpcf_last_count_info()
-    ctx.tpcf_set_timing(False)
-    rc = ctx.tpcf_sync()
-    ms = e0.elapsed_time(e1) / reps
-    return {"workload": (f"scale shape, {n_mock} mocks: periodic L=2000 Mpc/h, N_d=1e6 Neyman-Scott (n_p=2e-6, "
-                         "sigma=3), R1 + R2 of 1e6 each, 40 s x 10 mu bins, x line of sight: counts only, one "
-                         "batched call"),
-            "value": n_mock / (ms * 1e-3), "unit": "mocks/s", "ms_per_call": ms,
-            "gpairs_binned_per_s": info["n_binned"] / (ms * 1e-3) / 1e9,
-            "pairs_binned_per_call": info["n_binned"], "candidate_pairs_per_call": info["n_candidates"],
-            "status": rc}
+    import oracle
+    xs = synth.synthetic_xi_variants(3, 3500, 200)
+    gx = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in xs]
+    ref = oracle.lc_cov(*xs, 1, M_FINAL)
+    d = np.sqrt(np.diag(ref["Ca"]))
+    scale = np.outer(d, d)
+    out = {"workload": "3500 mocks x 3 variants x 200 (s, mu) bins, LC covariance with M=50"}
+    for name, pr in (("fp64", tp.TPCF_FP64), ("tf32x3", tp.TPCF_TF32X3), ("bf16x3", tp.TPCF_BF16X3)):
+        fn = lambda pr=pr: ctx.tpcf_lc_cov(*gx, 1, M_FINAL, pr, want_parts=False)  # noqa: E731
+        for _ in range(3):
+            fn()
+        ms, res = event_time(fn, 10, torch.cuda.synchronize)
+        e = np.abs(res["C_lc"].cpu().numpy() - ref["C_lc"]) / scale
+        out[name] = {"ms": ms, "max_err_vs_fp64_oracle": float(e.max()),
+                     "rms_err_vs_fp64_oracle": float(np.sqrt(np.mean(e * e)))}
+    return out
 
 
 def next_rows_measure(tp, ctx, dev, reps=20):
@@ -321,19 +484,11 @@ def next_rows_measure(tp, ctx, dev, reps=20):
     sample covariance, the multipole projection, the covariance-of-covariance variances, the predicted
     chi^2 and the eigenvalue check."""
     import torch
-    stream = torch.cuda.current_stream()
 
     def timed(fn):
         for _ in range(3):
             fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
+        return event_time(fn, reps, torch.cuda.synchronize)[0]
 
     n_s, n_mu, n_mock = 40, 5, 3500
     xs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in synth.synthetic_xi_variants(3, n_mock, n_s * n_mu)]
@@ -361,54 +516,6 @@ def next_rows_measure(tp, ctx, dev, reps=20):
     return out
 
 
-def kernel_code_hash(path):
-    """sha256 prefix of a CUDA source with comments and blank space removed: it changes
-    only when the code does (a profile taken before a comment edit still describes it)."""
-    import hashlib, re
-    src = open(path, encoding="utf-8").read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    src = re.sub(r"//[^\n]*", "", src)
-    src = "\n".join(line.strip() for line in src.splitlines() if line.strip())
-    return hashlib.sha256(src.encode()).hexdigest()[:16]
-
-
-def measured_traffic(n_mock):
-    """DRAM bytes of one pair-count launch from the committed ncu summary, if it was
-    taken on the current kernel code (else None)."""
-    try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "paircount_traffic.json")))
-        code = kernel_code_hash(os.path.join(ROOT, "paper_2205_11852_gb300", "csrc", "paircount.cu"))
-    except OSError:
-        return None
-    if code != rec.get("kernel_code_sha256_prefix"):
-        return None
-    return rec["dram_bytes_per_mock"] * n_mock
-
-
-def run_reference(args, rank, world):
-    """--impl reference: the CPU oracle as it stands, on the host cores (rank 0 only)."""
-    if rank != 0:
-        return
-    rates = []
-    for i in range(args.warmup + args.steps):
-        r = oracle_sample_rate(args.nd, target_s=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
-        if i >= args.warmup:
-            rates.append(r)
-    v = statistics.median([r["mocks_per_s"] for r in rates])
-    sample = (f"brute-force counts of {rates[0]['rows']} a-rows of mock 0 against all points "
-              f"(DD, DR1, DR2, RR1, RR2), {rates[0]['fraction_of_mock']:.3%} of one mock's pair tests per step")
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "mocks/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.median(
-                [r["seconds"] for r in rates]), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": f"mid: {args.mocks} mocks/GPU, periodic L=1000, N_d={args.nd} Neyman-Scott, "
-                                   "R1+R2 of N_d each, 40 s x 10 mu bins to 200", "global_batch": args.mocks * world},
-            "cpu_baseline": {"value": v, "unit": "mocks/s", "cores": rates[0]["cores"], "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": v, "unit": "mocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -431,10 +538,9 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     import paper_2205_11852_gb300 as tp
+    from paper_2205_11852_gb300 import multi
 
     dev = torch.device("cuda", local)
-    w = synth.MID
-    n_mock, n_d = args.mocks, args.nd
     prec = {"fp64": tp.TPCF_FP64, "tf32x3": tp.TPCF_TF32X3, "bf16x3": tp.TPCF_BF16X3}[args.precision]
 
     if args.cov_only:
@@ -447,38 +553,28 @@ def main():
         ctx0.close()
         return
 
-    from paper_2205_11852_gb300 import multi
-    host, layout = make_host_inputs(n_mock, n_d, multi.mock_range(rank, n_mock).start)
-    pinned = torch.from_numpy(host).pin_memory()
+    w = synth.WORKLOADS[args.workload]
+    n_mock = args.mocks or w.n_mock
+    t_gen = time.perf_counter()
+    pinned, layout = host_inputs(w, multi.mock_range(rank, n_mock).start, n_mock, args.nd, pinned=True)
+    t_gen = time.perf_counter() - t_gen
     pos = pinned.to(dev)
-    mocks = mock_views(pos, layout)
-    nd_list = [sz[0] for _, sz in layout]
-    nr_list = [[sz[1], sz[2]] for _, sz in layout]
     ctx = tp.Context(local)
     if args.subdiv:
         ctx.tpcf_set_cell_subdiv(args.subdiv)
-    b = tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_PERIODIC, w.L)
-    nbin = w.n_s * w.n_mu
-    outc = {"dd": torch.empty((n_mock, nbin), dtype=torch.int64, device=dev),
-            "dr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev),
-            "rr": torch.empty((n_mock, 2, nbin), dtype=torch.int64, device=dev)}
-    xi = {k: torch.empty((n_mock, nbin), dtype=torch.float64, device=dev) for k in ("a1", "a2", "b")}
-    sels = {"a1": [0], "a2": [1], "b": [0, 1]}
-    gather = None
-    if world > 1:
-        import torch.distributed as dist
-        gather = {k: torch.empty((world * n_mock, nbin), dtype=torch.float64, device=dev) for k in xi}
+    job = Job(tp, ctx, dev, w, pos, layout, prec, world)
 
-    def step(mode=tp.TPCF_BATCHED, mocks_in=None):
-        ctx.tpcf_count(mocks_in or mocks, b, mode=mode, out=outc)
-        for k, sel in sels.items():
-            ctx.tpcf_ls(outc["dd"], outc["dr"], outc["rr"], nd_list, nr_list, sel, out=xi[k])
-        src = xi
-        if gather is not None:
-            src = {k: multi.gather_rows(v, world) for k, v in xi.items()}
-            for k in src:
-                gather[k] = src[k]
-        return ctx.tpcf_lc_cov(src["a1"], src["a2"], src["b"], 1, M_FINAL, prec, want_parts=False)
+    if args.count_only:
+        for _ in range(2):
+            ctx.tpcf_count(job.mocks, job.b, mode=tp.TPCF_BATCHED, out=job.outc)
+        rc = ctx.tpcf_sync()
+        info = ctx.tpcf_last_count_info()
+        print(json.dumps({"count_only": True, "workload": w.name, "mocks": n_mock, "status": rc,
+                          "n_candidates": info["n_candidates"], "n_binned": info["n_binned"],
+                          "n_exact": info["n_exact"], "pair_kernel": info["pair_kernel"],
+                          "cell_subdiv": info["cell_subdiv"]}))
+        ctx.close()
+        return
 
     def barrier():
         if world > 1:
@@ -486,63 +582,34 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    if args.count_only_batching:
-        w = synth.BATCHING
-        mks = [w.make_mock(m) for m in range(args.count_only_batching)]
-        dm = [{"data": torch.from_numpy(mk.data).to(dev),
-               "randoms": torch.from_numpy(np.concatenate(mk.randoms)).to(dev),
-               "offsets": [0, len(mk.randoms[0]), len(mk.randoms[0]) + len(mk.randoms[1])]} for mk in mks]
-        bb = tp.make_binning(w.s_edges, w.n_mu, tp.TPCF_OPEN, w.L, los=tp.TPCF_LOS_MIDPOINT, observer=w.observer)
-        for _ in range(2):
-            ctx.tpcf_count(dm, bb, mode=tp.TPCF_BATCHED)
-        ctx.tpcf_sync()
-        info = ctx.tpcf_last_count_info()
-        print(json.dumps({"count_only": True, "workload": "batching", "mocks": len(mks),
-                          "n_candidates": info["n_candidates"], "n_binned": info["n_binned"],
-                          "n_exact": info["n_exact"]}))
-        ctx.close()
-        return
-    if args.count_only:
-        for _ in range(2):
-            ctx.tpcf_count(mocks, b, mode=tp.TPCF_BATCHED, out=outc)
-        ctx.tpcf_sync()
-        info = ctx.tpcf_last_count_info()
-        print(json.dumps({"count_only": True, "mocks": n_mock, "n_candidates": info["n_candidates"],
-                          "n_binned": info["n_binned"], "n_exact": info["n_exact"]}))
-        ctx.close()
-        return
+    def max_over_ranks(ms):
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
     # correctness of the timed configuration: batched == per-launch on 2 mocks
-    chk_b = ctx.tpcf_count(mocks[:2], b, mode=tp.TPCF_BATCHED)
-    chk_p = ctx.tpcf_count(mocks[:2], b, mode=tp.TPCF_PER_LAUNCH)
+    chk_b = ctx.tpcf_count(job.mocks[:2], job.b, mode=tp.TPCF_BATCHED)
+    chk_p = ctx.tpcf_count(job.mocks[:2], job.b, mode=tp.TPCF_PER_LAUNCH)
     ctx.tpcf_sync()
     same = all(torch.equal(chk_b[k], chk_p[k]) for k in ("dd", "dr", "rr"))
+    del chk_b, chk_p
 
     for _ in range(args.warmup):
-        step()
+        job.step()
     barrier()
     ctx.tpcf_set_timing(True)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(local)
-    barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        cov = step()
-    e1.record(stream)
-    barrier()
+    ms, cov = event_time(job.step, args.steps, barrier)
     clocks = sampler.stop()
     rc = ctx.tpcf_sync()
     info = ctx.tpcf_last_count_info()
     ctx.tpcf_set_timing(False)
-    ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ms)
     mocks_total = n_mock * world
     value = mocks_total / (ms * 1e-3)
+    xi_err, cov_err = job.errors(cov) if rank == 0 else (None, None)
 
     # pair-count kernel roofline (ALU-bound): algorithmic lane-ops / kernel time
     n_cand, n_binned = info["n_candidates"], info["n_binned"]
@@ -555,154 +622,115 @@ def main():
     gpairs = n_binned / (k_ms * 1e-3) / 1e9
 
     # plain per-launch path on the same GPU (one launch per mock, term and subset)
-    for _ in range(1):
-        step(mode=tp.TPCF_PER_LAUNCH)
-    barrier()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_pl = max(1, min(args.steps, 3))
-    p0.record(stream)
-    for _ in range(n_pl):
-        step(mode=tp.TPCF_PER_LAUNCH)
-    p1.record(stream)
-    barrier()
-    ms_pl = p0.elapsed_time(p1) / n_pl
+    job.step(mode=tp.TPCF_PER_LAUNCH)
+    n_pl = max(1, min(args.steps, 2))
+    ms_pl, _ = event_time(lambda: job.step(mode=tp.TPCF_PER_LAUNCH), n_pl, barrier)
+    ms_pl = max_over_ranks(ms_pl)
     per_launch = mocks_total / (ms_pl * 1e-3)
 
     # end to end through the public API: the positions are passed as pinned
     # HOST arrays (the library copies them in on the stream, TPCF_HOST_INPUT)
     # and C^LC is read back, every step
+    del pos
+    job.mocks = None
+    torch.cuda.empty_cache()
     h2d = pinned.numel() * pinned.element_size()
-    d2h = nbin * nbin * 8
-    res_host = torch.empty((nbin, nbin), dtype=torch.float64).pin_memory()
+    d2h = job.nbin * job.nbin * 8
+    res_host = torch.empty((job.nbin, job.nbin), dtype=torch.float64).pin_memory()
     mocks_host = mock_views(pinned, layout)
-    # untimed warm-up steps of this path too: its staged inputs sit at new
-    # device addresses, so its first call builds a launch plan and graph
-    for _ in range(args.warmup):
-        c = step(mocks_in=mocks_host)
-        res_host.copy_(c["C_lc"], non_blocking=True)
-    barrier()
-    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    q0.record(stream)
-    for _ in range(args.steps):
-        c = step(mocks_in=mocks_host)
-        res_host.copy_(c["C_lc"], non_blocking=True)
-    q1.record(stream)
-    barrier()
-    ms_e2e = q0.elapsed_time(q1) / args.steps
-    te = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = mocks_total / (float(te.item()) * 1e-3)
 
-    # covariance error of the timed path against the float64 oracle construction on the same xi
-    cov_err = None
-    if rank == 0:
-        import oracle
-        src = gather if gather is not None else xi
-        ref = oracle.lc_cov(src["a1"].cpu().numpy(), src["a2"].cpu().numpy(), src["b"].cpu().numpy(), 1, M_FINAL)
-        d = np.sqrt(np.abs(np.diag(ref["Ca"])))
-        scale = np.outer(d, d)
-        scale[scale == 0] = 1.0
-        cov_err = float(np.max(np.abs(cov["C_lc"].cpu().numpy() - ref["C_lc"]) / scale))
+    def e2e_step():
+        c = job.step(mocks=mocks_host)
+        res_host.copy_(c["C_lc"], non_blocking=True)
+        return c
+
+    # one untimed call first: its staged inputs sit at new device addresses,
+    # so it builds a launch plan and graph
+    e2e_step()
+    n_e2e = max(1, min(args.steps, 3))
+    ms_e2e, _ = event_time(e2e_step, n_e2e, barrier)
+    ms_e2e = max_over_ranks(ms_e2e)
+    e2e = mocks_total / (ms_e2e * 1e-3)
+    kernels_per_step = info["n_kernels"] + 3 + 4   # count + 3 LS + 4 covariance kernels
+    tuned = {"cell_subdiv": info["cell_subdiv"], "cells_per_axis": info["cells_per_axis"],
+             "unit_chunk": info["unit_chunk"], "graph_replay": bool(info["graph_replay"]),
+             "pair_kernel": info["pair_kernel"]}
+    ctx.close()
+    del job, pinned, mocks_host
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = oracle_sample_rate(n_d, args.cpu_seconds)
+        r = oracle_sample_rate(w, args.nd, args.cpu_seconds)
         cpu = {"value": r["mocks_per_s"], "unit": "mocks/s", "cores": r["cores"], "kind": "oracle",
-               "sample": (f"brute-force counts of {r['rows']} a-rows of mock 0 against all points (DD, DR1, "
-                          f"DR2, RR1, RR2), {r['fraction_of_mock']:.3%} of one mock's pair tests, "
-                          f"{r['seconds']:.1f} s")}
+               "sample": sample_text(r)}
 
-    # covariance-only workload: 3500 mocks x 3 variants x 200 (s, mu) bins,
-    # float64 vs split precision on the tensor cores, error against the oracle
-    prec_cfg = None
-    if rank == 0 and not args.no_precision_config:
-        import oracle
-        xs = synth.synthetic_xi_variants(3, 3500, 200)
-        gx = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in xs]
-        ref = oracle.lc_cov(*xs, 1, M_FINAL)
-        d = np.sqrt(np.diag(ref["Ca"]))
-        scale = np.outer(d, d)
-        prec_cfg = {"workload": "3500 mocks x 3 variants x 200 (s, mu) bins, LC covariance with M=50"}
-        for name, pr in (("fp64", tp.TPCF_FP64), ("tf32x3", tp.TPCF_TF32X3), ("bf16x3", tp.TPCF_BF16X3)):
-            for _ in range(3):
-                out = ctx.tpcf_lc_cov(*gx, 1, M_FINAL, pr, want_parts=False)
-            torch.cuda.synchronize()
-            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 10
-            c0.record(stream)
-            for _ in range(reps):
-                out = ctx.tpcf_lc_cov(*gx, 1, M_FINAL, pr, want_parts=False)
-            c1.record(stream)
-            torch.cuda.synchronize()
-            err = float(np.max(np.abs(out["C_lc"].cpu().numpy() - ref["C_lc"]) / scale))
-            prec_cfg[name] = {"ms": c0.elapsed_time(c1) / reps, "max_err_vs_fp64_oracle": err}
+    extras = {}
+    if rank == 0 and world == 1:
+        for name in [x for x in args.extras.split(",") if x]:
+            ew = synth.WORKLOADS[name]
+            extras[name] = extra_workload(tp, dev, ew, args.batching_mocks if name == "batching" else ew.n_mock,
+                                          tp.TPCF_FP64 if name == "small" else prec)
 
-    # brute-force (Smp) comparison: the same mocks' shape with all M = 50 subsets
-    smp = None
-    if rank == 0 and world == 1 and args.smp_mocks >= 2:
-        r = smp_measure(tp, ctx, dev, b, prec, args.smp_mocks, n_d)
-        smp_rate = args.smp_mocks / (r["ms"] * 1e-3)
-        smp = {"workload": (f"{args.smp_mocks} mocks of the mid shape with M=50 random subsets of N_d each: "
-                            "DD, DR_1..50, RR_1..50 in one batched launch, LS over all 50, sample covariance"),
-               "value": smp_rate, "unit": "mocks/s", "ms_per_step": r["ms"],
-               "pairs_binned_per_mock": r["n_binned"] / args.smp_mocks,
-               "lc_over_smp_speed": value / smp_rate,
-               "lc_over_smp_binned_pairs": (r["n_binned"] / args.smp_mocks) / (n_binned / n_mock),
-               "paper_cost_ratio_1p3M_over_7": (1 + 3 * 50) / 7, "status": r["status"]}
+    prec_cfg = nxt = smp = None
+    if rank == 0 and world == 1:
+        ctx2 = tp.Context(local)
+        if not args.no_precision_config:
+            prec_cfg = precision_measure(tp, ctx2, dev)
+            nxt = next_rows_measure(tp, ctx2, dev)
+        if args.smp_mocks >= 2:
+            r = smp_measure(tp, ctx2, dev, prec, args.smp_mocks)
+            smp_rate = args.smp_mocks / (r["ms"] * 1e-3)
+            smp = {"workload": (f"{args.smp_mocks} mocks of the mid shape with M=50 random subsets of N_d each: "
+                                "DD, DR_1..50, RR_1..50 in one batched launch, LS over all 50, sample covariance"),
+                   "value": smp_rate, "unit": "mocks/s", "ms_per_step": r["ms"],
+                   "pairs_binned_per_mock": r["n_binned"] / args.smp_mocks,
+                   "paper_cost_ratio_1p3M_over_7": (1 + 3 * 50) / 7, "status": r["status"]}
+            mid = extras.get("mid")
+            if mid is not None:
+                smp["lc_over_smp_speed_mid"] = mid["value"] / smp_rate
+                smp["lc_over_smp_binned_pairs"] = ((r["n_binned"] / args.smp_mocks) /
+                                                   (mid["pairs_binned_per_step"] / synth.MID.n_mock))
+        ctx2.close()
 
-    nxt = None
-    if rank == 0 and not args.no_precision_config:
-        nxt = next_rows_measure(tp, ctx, dev)
-
-    bat = None
-    if rank == 0 and world == 1 and args.batching_mocks > 0:
-        bat = batching_measure(tp, ctx, dev, args.batching_mocks)
-    scl = None
-    if rank == 0 and world == 1 and args.scale_mocks > 0:
-        scl = scale_measure(tp, ctx, dev, args.scale_mocks)
-
-    kernels_per_step = info["n_kernels"] + 3 + 4   # count + 3 LS + 4 covariance kernels
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "mocks/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": (f"mid: {n_mock} mocks/GPU, periodic L=1000 Mpc/h, N_d={n_d} Neyman-Scott "
-                                    "(n_p=1e-5, sigma=3), R1+R2 uniform of N_d each, 40 s x 10 mu bins to "
-                                    "200 Mpc/h, LOS x; LS + LC covariance (M=50)"),
-                       "global_batch": mocks_total, "cov_precision": args.precision,
+            "config": {"workload": workload_desc(w, n_mock, args.nd), "global_batch": mocks_total,
+                       "cov_precision": args.precision,
                        "l2": "inputs larger than L2 (positions and mesh > 129 MB)"},
             "gpairs_binned_per_s": gpairs,
             "pairs_binned_per_step": n_binned * world,
             "candidate_pairs_per_step": n_cand * world,
-            "per_launch": {"value": per_launch, "unit": "mocks/s", "ms_per_step": ms_pl,
+            "per_launch": {"value": per_launch, "unit": "mocks/s", "ms_per_step": ms_pl, "steps": n_pl,
                            "batched_over_per_launch": value / per_launch},
             "batched_equals_per_launch": bool(same),
+            "xi_err": xi_err,
             "cov_err_vs_fp64": cov_err,
-            "tuned": {"cell_subdiv": info["cell_subdiv"], "cells_per_axis": info["cells_per_axis"],
-                      "unit_chunk": info["unit_chunk"], "graph_replay": bool(info["graph_replay"])},
+            "tuned": tuned,
+            "host_input_generation_s": t_gen,
+            "extra_workloads": extras,
             "precision_config": prec_cfg,
             "smp_comparison": smp,
             "after_covariance": nxt,
-            "batching_sample": bat,
-            "scale_sample": scl,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-op/s",
-                         "frac": achieved / peak, "traffic": measured_traffic(n_mock),
-                         "traffic_note": "ncu DRAM bytes of 2 mocks scaled to the launch's mocks",
+                         "frac": achieved / peak,
+                         "traffic": measured_traffic(w.name, n_mock, info["pair_kernel"]),
+                         "traffic_note": "ncu DRAM bytes of a 2-mock launch of this workload scaled to the mocks",
                          "frac_at_run_clock": achieved / (n_sm * LANES_PER_SM * f_run * 1e6),
-                         "kernel": "paircount_kernel", "kernel_ms": k_ms,
-                         "lane_ops_per_launch": lane_ops, "exact_rechecks": info["n_exact"]},
+                         "kernel": "pairdirect_kernel" if info["pair_kernel"] == 1 else "paircount_kernel",
+                         "kernel_ms": k_ms, "lane_ops_per_launch": lane_ops, "exact_rechecks": info["n_exact"]},
             "clocks": clocks,
-            "e2e": {"value": e2e, "unit": "mocks/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e, "unit": "mocks/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": ms_e2e, "steps": n_e2e},
             "gpu_launches": kernels_per_step * args.steps,
             "status": rc,
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
