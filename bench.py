@@ -449,6 +449,7 @@ def extra_workload(tp, dev, w, n_mock, prec, reps=2):
                 "gpairs_binned_per_s": info["n_binned"] / (k_ms * 1e-3) / 1e9,
                 "pairs_binned_per_step": info["n_binned"], "candidate_pairs_per_step": info["n_candidates"],
                 "pair_kernel": info["pair_kernel"], "cell_subdiv": info["cell_subdiv"],
+                "last_wave_idle_frac": info["idle_frac"],
                 "per_launch": {"value": n_mock / (ms_pl * 1e-3), "unit": "mocks/s", "ms_per_step": ms_pl,
                                "batched_over_per_launch": ms_pl / ms},
                 "batched_equals_per_launch": bool(same), "xi_err": xi_err, "cov_err": cov_err, "status": rc}
@@ -601,7 +602,9 @@ def main():
     barrier()
     ctx.tpcf_set_timing(True)
     sampler = ClockSampler(local)
+    torch.cuda.nvtx.range_push("timed_step")   # lets a profiler capture exactly the timed steps
     ms, cov = event_time(job.step, args.steps, barrier)
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     rc = ctx.tpcf_sync()
     info = ctx.tpcf_last_count_info()
@@ -654,7 +657,8 @@ def main():
     kernels_per_step = info["n_kernels"] + 3 + 4   # count + 3 LS + 4 covariance kernels
     tuned = {"cell_subdiv": info["cell_subdiv"], "cells_per_axis": info["cells_per_axis"],
              "unit_chunk": info["unit_chunk"], "graph_replay": bool(info["graph_replay"]),
-             "pair_kernel": info["pair_kernel"]}
+             "pair_kernel": info["pair_kernel"], "pair_blocks": info["pair_blocks"],
+             "last_wave_idle_frac": info["idle_frac"]}
     ctx.close()
     del job, pinned, mocks_host
     torch.cuda.empty_cache()

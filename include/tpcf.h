@@ -360,6 +360,10 @@ typedef struct {
     int     unit_chunk;       /* a-points per work unit, chosen by the autotuner */
     int     graph_replay;     /* 1: the batched launch was a replay of a captured CUDA graph */
     int     pair_kernel;      /* TPCF_KERNEL_DIRECT or TPCF_KERNEL_GENERAL: the pair counter that ran */
+    int     pair_blocks;      /* blocks of the persistent pair-count grid (SMs x blocks per SM) */
+    double  idle_frac;        /* one batched launch: share of warp time between the first warp's start and
+                                 the last warp's end that warps spent finished (the last-wave tail);
+                                 -1 when the call made several launches or none */
 } tpcf_count_info;
 
 int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info);
@@ -384,16 +388,25 @@ int tpcf_set_cell_subdiv(tpcf_ctx *ctx, int subdiv);
  *                        outputs of the call stay the same.  The first call of
  *                        a new shape must not itself be under stream capture.
  *   TPCF_OPT_AUTOTUNE -- on the first batched call of a new workload shape,
- *                        time candidate mesh subdivisions and work-unit sizes on
- *                        a few of the mocks and keep the fastest (cached per
- *                        context and device).  A pinned subdivision disables it.
- *   TPCF_OPT_KERNEL   -- which pair counter runs: TPCF_KERNEL_AUTO (the direct
- *                        counter wherever the binning suits it -- s bins linear
- *                        from 0 with the x line of sight or s only, and a
- *                        histogram that fits shared memory with its copies --
- *                        else the general one) or TPCF_KERNEL_GENERAL (always
- *                        the general counter; the default).  Both give
- *                        identical counts.
+ *                        time candidates on a few of the mocks and keep the
+ *                        fastest: the pair counter (both, under
+ *                        TPCF_KERNEL_AUTO), the mesh subdivision {2, 3, 4} and
+ *                        the work-unit size {64, 128}, then fewer blocks per SM
+ *                        for the winner (cached per context, keyed by the
+ *                        binning, the size class and the device's name, SM
+ *                        count and compute capability).  A pinned subdivision
+ *                        disables it.
+ *   TPCF_OPT_KERNEL   -- which pair counter runs: TPCF_KERNEL_DIRECT (the
+ *                        direct counter wherever the binning suits it -- s bins
+ *                        linear from 0 with the x line of sight or s only, and
+ *                        a histogram that fits shared memory with its copies --
+ *                        else the general one), TPCF_KERNEL_GENERAL (always the
+ *                        general counter) or TPCF_KERNEL_AUTO (the default: the
+ *                        autotuner times both and keeps the faster; without a
+ *                        tuned entry, the general counter).  The per-launch
+ *                        mode runs the configuration tuned for the batched
+ *                        call of the same shape.  Both counters give identical
+ *                        counts.
  * and of the split-precision covariances (tpcf_lc_cov, tpcf_sample_cov with
  * TPCF_TF32X3 / TPCF_BF16X3):
  *   TPCF_OPT_WAIT_LIMIT    -- bound, in polls of about 64 ns, of the Gram

@@ -197,17 +197,24 @@ int tpcf_create(tpcf_ctx **out, int cuda_device)
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->scratch_ev[1]);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->stats, 4 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMallocHost(&ctx->stats_host, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->stats, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->stats_host, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaGetLastError();
         tpcf_destroy(ctx);
         return e == cudaErrorMemoryAllocation ? TPCF_ERR_NOMEM : TPCF_ERR_CUDA;
     }
-    std::memset(ctx->stats_host, 0, 4 * sizeof(unsigned long long));
+    std::memset(ctx->stats_host, 0, 8 * sizeof(unsigned long long));
+    {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, cuda_device) == cudaSuccess)
+            ctx->device_id = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "/" +
+                             std::to_string(prop.major) + "." + std::to_string(prop.minor);
+        cudaGetLastError();
+    }
     if (const char *v = std::getenv("TPCF_TEST_FAIL_ALLOC")) ctx->fail_alloc_at = std::atoll(v);
     if (const char *v = std::getenv("TPCF_TEST_FAIL_COUNT")) ctx->fail_count_at = std::atoll(v);
     *out = ctx;
@@ -292,8 +299,8 @@ int tpcf_set_option(tpcf_ctx *ctx, int option, int value)
     case TPCF_OPT_GRAPHS: ctx->use_graphs = value != 0; break;
     case TPCF_OPT_AUTOTUNE: ctx->autotune = value != 0; break;
     case TPCF_OPT_KERNEL:
-        if (value != TPCF_KERNEL_AUTO && value != TPCF_KERNEL_GENERAL)
-            return fail(ctx, TPCF_ERR_ARG, "TPCF_OPT_KERNEL takes TPCF_KERNEL_AUTO or TPCF_KERNEL_GENERAL");
+        if (value != TPCF_KERNEL_AUTO && value != TPCF_KERNEL_DIRECT && value != TPCF_KERNEL_GENERAL)
+            return fail(ctx, TPCF_ERR_ARG, "TPCF_OPT_KERNEL takes TPCF_KERNEL_AUTO, _DIRECT or _GENERAL");
         ctx->kernel_pref = value;
         break;
     case TPCF_OPT_WAIT_LIMIT:
@@ -317,6 +324,13 @@ int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info)
     info->n_binned = (int64_t)ctx->stats_host[1];
     info->n_exact = (int64_t)ctx->stats_host[2];
     info->n_units = (int64_t)ctx->stats_host[3];
+    {
+        const unsigned long long *st = ctx->stats_host;
+        const unsigned long long t0 = ~st[4], span = st[5] > t0 ? st[5] - t0 : 0ull;
+        info->idle_frac = (ctx->last_launches == 1 && st[7] > 0 && span > 0 && st[4] != 0)
+                              ? 1.0 - (double)st[6] / ((double)st[7] * (double)span)
+                              : -1.0;
+    }
     info->n_paircount_launches = ctx->last_launches;
     info->cell_subdiv = ctx->last_subdiv;
     info->cells_per_axis = ctx->last_nc;
@@ -324,6 +338,7 @@ int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info)
     info->unit_chunk = ctx->last_chunk;
     info->graph_replay = ctx->last_graph ? 1 : 0;
     info->pair_kernel = ctx->last_direct ? TPCF_KERNEL_DIRECT : TPCF_KERNEL_GENERAL;
+    info->pair_blocks = ctx->last_blocks;
     double total = 0.0;
     for (int i = 0; i < ctx->n_timed; i++) {
         float ms = 0;

@@ -60,8 +60,12 @@ struct Setup {
 
 // Validate and build everything host-side for one call; allocates workspace.
 int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *binning, unsigned terms,
-            int64_t *dd, int64_t *dr, int64_t *rr, int mode, int subdiv, int chunk, Setup &S)
+            int64_t *dd, int64_t *dr, int64_t *rr, int mode, const Tuned &cfg, Setup &S)
 {
+    const int subdiv = cfg.subdiv, chunk = cfg.chunk;
+    // the tuned counter, else the context's preference (untuned AUTO: the general counter)
+    const int kern = cfg.kernel >= 0 ? cfg.kernel
+                                     : (ctx->kernel_pref == TPCF_KERNEL_AUTO ? TPCF_KERNEL_GENERAL : ctx->kernel_pref);
     int rc;
     if ((rc = validate_binning(ctx, binning))) return rc;
     if (n_mock < 0 || (n_mock > 0 && !mocks)) return fail(ctx, TPCF_ERR_ARG, "mocks is NULL");
@@ -122,7 +126,7 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
     if ((rc = check_mu_width(ctx, binning, S.pl.prm))) return rc;
     const CountParams &prm = S.pl.prm;
     S.chunk = std::max(32, std::min(chunk, UNIT_CHUNK));
-    if (ctx->kernel_pref != TPCF_KERNEL_GENERAL) {
+    if (kern != TPCF_KERNEL_GENERAL) {
         int sm_sm = 0, sm_blk = 0, resv = 0;
         if (cudaDeviceGetAttribute(&sm_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device) != cudaSuccess ||
             cudaDeviceGetAttribute(&sm_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) != cudaSuccess ||
@@ -261,7 +265,7 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
         const int occ = pairdirect_max_blocks_per_sm(S.dp, prm.n_mu > 1);
         if (occ < 1) return fail(ctx, TPCF_ERR_CUDA, "the direct pair counter does not fit on an SM");
         S.smem = S.dp.smem;
-        S.blocks = ctx->n_sm * occ;
+        S.blocks = ctx->n_sm * (cfg.bps > 0 ? std::min(cfg.bps, occ) : occ);
         // units per block claim: a few claims per block, at most 2^30 pairs per counter
         const unsigned long long by_work = std::max<unsigned long long>(1, S.units_bound / (3ull * S.blocks));
         const unsigned long long by_wrap = std::max<unsigned long long>(1, (1ull << 30) / S.dp.unit_pair_bound);
@@ -283,7 +287,8 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
     }
     cudaError_t e = paircount_set_attrs(prm, S.smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "paircount_set_attrs");
-    S.blocks = ctx->n_sm * paircount_max_blocks_per_sm(prm, 8, S.smem);
+    const int occ = paircount_max_blocks_per_sm(prm, 8, S.smem);
+    S.blocks = ctx->n_sm * (cfg.bps > 0 ? std::min(cfg.bps, occ) : occ);
     if ((rc = ensure(ctx, "pairscratch", paircount_scratch_bytes(S.blocks), &S.bscr))) return rc;
     return TPCF_OK;
 }
@@ -299,9 +304,9 @@ int enqueue(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, void *small
     if (S.dd) CK(cudaMemsetAsync(S.dd, 0, S.n_dd * 8, s));
     if (S.dr && S.n_drr) CK(cudaMemsetAsync(S.dr, 0, S.n_drr * 8, s));
     if (S.rr && S.n_drr) CK(cudaMemsetAsync(S.rr, 0, S.n_drr * 8, s));
-    CK(cudaMemsetAsync(ctx->stats, 0, 4 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ctx->stats, 0, 8 * sizeof(unsigned long long), s));
     if (S.NT == 0 || S.terms.empty()) {
-        CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         return TPCF_OK;
     }
     for (const RqCopy &c : S.rq)
@@ -381,7 +386,7 @@ int enqueue(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, void *small
         if (ev1) CK(cudaEventRecordWithFlags(ev1, s, external ? cudaEventRecordExternal : cudaEventRecordDefault));
         kernels += n_terms;
     }
-    CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     return TPCF_OK;
 }
 
@@ -522,41 +527,78 @@ int run_direct(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, int slot
 }
 
 // Autotuner: time candidate (subdivision, unit size) pairs on a few mocks.
+// Autotuner: times one batched count of the first few mocks per candidate.
+// Stage 1: pair counter (both, when the context leaves the choice to the
+// library) x mesh subdivision {2, 3, 4} x unit size {64, 128} (the direct
+// counter's unit is fixed at 64 a-points).  Stage 2, for the winner: fewer
+// blocks per SM than fit (the persistent grid's occupancy).  Each candidate
+// is timed twice and its faster run kept.
 int autotune(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *binning, unsigned terms,
              int64_t *dd, int64_t *dr, int64_t *rr, cudaStream_t s, Tuned &best)
 {
     const int n_try = std::min(n_mock, 6);
     static const int subdivs[] = {2, 3, 4};
     static const int chunks[] = {64, 128};
+    std::vector<int> kernels;
+    if (ctx->kernel_pref == TPCF_KERNEL_AUTO) kernels = {TPCF_KERNEL_GENERAL, TPCF_KERNEL_DIRECT};
+    else kernels = {ctx->kernel_pref};
     cudaEvent_t t0, t1;
     CK(cudaEventCreate(&t0));
     CK(cudaEventCreate(&t1));
     float best_ms = 1e30f;
     int rc = TPCF_OK;
-    for (int sd : subdivs)
-        for (int ch : chunks) {
-            Setup S;
-            if ((rc = prepare(ctx, mocks, n_try, binning, terms, dd, dr, rr, TPCF_BATCHED, sd, ch, S))) {
-                if (rc == TPCF_ERR_RANGE) { rc = TPCF_OK; continue; }   // mesh not possible at this subdivision
-                break;
-            }
-            float ms = 1e30f;
-            for (int rep = 0; rep < 2 && rc == TPCF_OK; rep++) {
-                CK(cudaEventRecord(t0, s));
-                rc = run_direct(ctx, S, TPCF_BATCHED, s, -1);
-                CK(cudaEventRecord(t1, s));
-                CK(cudaEventSynchronize(t1));
-                float x = 0;
-                CK(cudaEventElapsedTime(&x, t0, t1));
-                ms = std::min(ms, x);
-            }
-            if (rc) break;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best.subdiv = sd;
-                best.chunk = ch;
-            }
+    int best_occ = 0;
+    // time candidate c; rc != 0 stops the search, a mesh or counter that does not fit is skipped
+    auto trial = [&](const Tuned &c, int &occ_out) -> float {
+        Setup S;
+        if ((rc = prepare(ctx, mocks, n_try, binning, terms, dd, dr, rr, TPCF_BATCHED, c, S))) {
+            if (rc == TPCF_ERR_RANGE) rc = TPCF_OK;   // mesh not possible at this subdivision
+            return 1e30f;
         }
+        if (c.kernel == TPCF_KERNEL_DIRECT && !S.direct) return 1e30f;   // the general counter's timing is its own
+        occ_out = S.blocks / std::max(1, ctx->n_sm);
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && rc == TPCF_OK; rep++) {
+            cudaError_t e = cudaEventRecord(t0, s);
+            if (e == cudaSuccess) rc = run_direct(ctx, S, TPCF_BATCHED, s, -1);
+            if (e == cudaSuccess && rc == TPCF_OK) e = cudaEventRecord(t1, s);
+            if (e == cudaSuccess && rc == TPCF_OK) e = cudaEventSynchronize(t1);
+            float x = 0;
+            if (e == cudaSuccess && rc == TPCF_OK) e = cudaEventElapsedTime(&x, t0, t1);
+            if (e != cudaSuccess) rc = cuda_fail(ctx, e, "autotune timing");
+            ms = std::min(ms, x);
+        }
+        return ms;
+    };
+    for (int kern : kernels)
+        for (int sd : subdivs)
+            for (int ch : chunks) {
+                if (kern == TPCF_KERNEL_DIRECT && ch != chunks[0]) continue;
+                Tuned c;
+                c.subdiv = sd;
+                c.chunk = ch;
+                c.kernel = kern;
+                int occ = 0;
+                const float ms = trial(c, occ);
+                if (rc) goto done;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                    best_occ = occ;
+                }
+            }
+    for (int bps = best_occ - 1; bps >= 1 && bps >= best_occ - 2; bps--) {
+        Tuned c = best;
+        c.bps = bps;
+        int occ = 0;
+        const float ms = trial(c, occ);
+        if (rc) goto done;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+done:
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     return rc;
@@ -574,6 +616,7 @@ std::string tune_key(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tp
     put(b->s_edges, sizeof(double) * (b->n_s + 1));
     put(&terms, sizeof(terms));
     put(&ctx->device, sizeof(ctx->device));
+    k.append(ctx->device_id);
     put(&ctx->kernel_pref, sizeof(ctx->kernel_pref));
     // size class: log2 of the mean catalogue size
     double pts = 0;
@@ -712,12 +755,16 @@ extern "C" int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, con
     Tuned cfg;
     if (ctx->subdiv_pin) {
         cfg.subdiv = ctx->subdiv_pin;
+    } else if (ctx->autotune && mode == TPCF_PER_LAUNCH && n_mock > 0) {
+        // the per-launch path runs the configuration tuned for the batched one, if any
+        auto it = ctx->tune_cache.find(tune_key(ctx, mocks, n_mock, binning, terms));
+        if (it != ctx->tune_cache.end()) cfg = it->second;
     } else if (ctx->autotune && mode == TPCF_BATCHED && n_mock > 0) {
         const std::string tk = tune_key(ctx, mocks, n_mock, binning, terms);
         auto it = ctx->tune_cache.find(tk);
         if (it == ctx->tune_cache.end()) {
             Setup probe;
-            if ((rc = prepare(ctx, mocks, n_mock, binning, terms, dd, dr, rr, mode, cfg.subdiv, cfg.chunk, probe)))
+            if ((rc = prepare(ctx, mocks, n_mock, binning, terms, dd, dr, rr, mode, cfg, probe)))
                 return rc;
             Tuned t;
             if ((rc = autotune(ctx, mocks, n_mock, binning, terms, dd, dr, rr, s, t))) return rc;
@@ -726,10 +773,11 @@ extern "C" int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, con
         cfg = it->second;
     }
     Setup S;
-    if ((rc = prepare(ctx, mocks, n_mock, binning, terms, dd, dr, rr, mode, cfg.subdiv, cfg.chunk, S))) return rc;
+    if ((rc = prepare(ctx, mocks, n_mock, binning, terms, dd, dr, rr, mode, cfg, S))) return rc;
     ctx->last_subdiv = cfg.subdiv;
     ctx->last_nc = S.pl.prm.n_c;
     ctx->last_chunk = S.chunk;
+    ctx->last_blocks = S.blocks;
     ctx->last_direct = S.direct;
     ctx->last_launches = S.terms.empty() || S.NT == 0 ? 0 : (mode == TPCF_BATCHED ? 1 : (int)S.terms.size());
     const int slot = timing_slot(ctx);

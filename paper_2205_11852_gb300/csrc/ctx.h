@@ -35,6 +35,8 @@ struct GraphEntry {
 struct Tuned {
     int subdiv = 3;
     int chunk = 256;
+    int kernel = -1;   // TPCF_KERNEL_*; -1: the context's preference
+    int bps = 0;       // blocks per SM of the pair counter; 0: as many as fit
 };
 
 }  // namespace tpcf
@@ -66,8 +68,9 @@ struct tpcf_ctx {
     int use_graphs = 1;
     int autotune = 1;
     std::map<std::string, tpcf::Tuned> tune_cache;
-    int last_subdiv = 0, last_nc = 0, last_chunk = 0;
-    int kernel_pref = 2;                  // TPCF_KERNEL_AUTO | TPCF_KERNEL_GENERAL (the default)
+    int last_subdiv = 0, last_nc = 0, last_chunk = 0, last_blocks = 0;
+    std::string device_id;                // name, SM count and compute capability (tune-cache key)
+    int kernel_pref = 0;                  // TPCF_KERNEL_AUTO (the default) | _DIRECT | _GENERAL
     bool last_direct = false;             // the last tpcf_count ran the direct counter
     // split-precision Gram kernel: bound of its epilogue wait (0: built in), test-only MMA skip
     long long gram_wait_limit = 0;

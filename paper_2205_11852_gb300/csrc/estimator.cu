@@ -46,16 +46,41 @@ __global__ void ls_kernel(const long long *__restrict__ dd, const long long *__r
     if (empty) atomicOr(status, STATUS_EMPTY_BIN);
 }
 
-// column means of the three variants: mean[v][b]
-__global__ void mean_kernel(const double *__restrict__ x0, const double *__restrict__ x1,
-                            const double *__restrict__ x2, int n_mock, int nbin, double *__restrict__ mean)
+// column means of the three variants: mean[v][b].  A block of 32 x 32
+// threads takes 32 columns of one variant: thread (tx, ty) sums rows ty,
+// ty + 32, ... of column tx in four interleaved partial sums (so that loads
+// of consecutive rows are in flight together, and a warp reads 32 consecutive
+// columns of a row), then the 32 row groups are added in shared memory in a
+// fixed order.
+constexpr int MEAN_COLS = 32, MEAN_ROWS = 32;
+__global__ void __launch_bounds__(MEAN_COLS * MEAN_ROWS) mean_kernel(const double *__restrict__ x0,
+                                                                     const double *__restrict__ x1,
+                                                                     const double *__restrict__ x2, int n_mock,
+                                                                     int nbin, double *__restrict__ mean)
 {
+    __shared__ double part[MEAN_ROWS][MEAN_COLS + 1];
     const int v = blockIdx.y;
     const double *x = v == 0 ? x0 : (v == 1 ? x1 : x2);
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbin; b += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int m = 0; m < n_mock; m++) s += x[(size_t)m * nbin + b];
-        mean[(size_t)v * nbin + b] = s / (double)n_mock;
+    const int tx = threadIdx.x % MEAN_COLS, ty = threadIdx.x / MEAN_COLS;
+    const int b = blockIdx.x * MEAN_COLS + tx;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    if (b < nbin) {
+        int m = ty;
+        for (; m + 3 * MEAN_ROWS < n_mock; m += 4 * MEAN_ROWS) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) s[k] += x[(size_t)(m + k * MEAN_ROWS) * nbin + b];
+        }
+        // at most three rows remain
+        if (m < n_mock) s[0] += x[(size_t)m * nbin + b];
+        if (m + MEAN_ROWS < n_mock) s[1] += x[(size_t)(m + MEAN_ROWS) * nbin + b];
+        if (m + 2 * MEAN_ROWS < n_mock) s[2] += x[(size_t)(m + 2 * MEAN_ROWS) * nbin + b];
+    }
+    part[ty][tx] = (s[0] + s[1]) + (s[2] + s[3]);
+    __syncthreads();
+    if (ty == 0 && b < nbin) {
+        double t = 0.0;
+        for (int r = 0; r < MEAN_ROWS; r++) t += part[r][tx];
+        mean[(size_t)v * nbin + b] = t / (double)n_mock;
     }
 }
 
@@ -178,7 +203,8 @@ double *gram_fp64(const double *x0, const double *x1, const double *x2, int n_va
     double *Y = work;
     double *mean = Y + (size_t)n_var * n_mock * nbin;
     double *G = mean + (size_t)n_var * nbin;
-    mean_kernel<<<dim3(std::max(1, (nbin + 127) / 128), n_var), 128, 0, s>>>(x0, x1, x2, n_mock, nbin, mean);
+    mean_kernel<<<dim3((nbin + MEAN_COLS - 1) / MEAN_COLS, n_var), MEAN_COLS * MEAN_ROWS, 0, s>>>(x0, x1, x2, n_mock,
+                                                                                              nbin, mean);
     centre_kernel<<<dim3(std::max(1, blocks_for((size_t)n_mock * nbin, 256)), n_var), 256, 0, s>>>(
         x0, x1, x2, n_mock, nbin, mean, Y);
     const int nt = (nbin + GT - 1) / GT;
@@ -254,8 +280,8 @@ cudaError_t launch_cov_fp64(const double *xi, int n_mock, int nbin, double *work
 cudaError_t launch_means(const double *xi_a1, const double *xi_a2, const double *xi_b, int n_var, int n_mock,
                          int nbin, double *mean, cudaStream_t s)
 {
-    mean_kernel<<<dim3(std::max(1, (nbin + 127) / 128), n_var), 128, 0, s>>>(xi_a1, xi_a2, xi_b, n_mock, nbin,
-                                                                              mean);
+    mean_kernel<<<dim3((nbin + MEAN_COLS - 1) / MEAN_COLS, n_var), MEAN_COLS * MEAN_ROWS, 0, s>>>(
+        xi_a1, xi_a2, xi_b, n_mock, nbin, mean);
     return cudaGetLastError();
 }
 

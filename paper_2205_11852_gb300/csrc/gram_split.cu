@@ -7,15 +7,15 @@
 // exactly:
 //   TF32X3: y = hi + lo (tf32 each), G ~ hi.hi + hi.lo + lo.hi         (3 products)
 //   BF16X3: y = h + m + l (bf16 each), G ~ hh + hm + mh + hl + lh + mm  (6 products)
-// A CTA owns one 128 x 128 output tile of one variant and one K-slice of 16
-// mocks: its operand tiles arrive by one bulk copy each (cp.async.bulk, the
-// TMA engine, completing on an mbarrier), one thread issues the tcgen05.mma
-// chain into FP32 accumulators in tensor memory, and the warps read them back
-// with tcgen05.ld and add them into the float64 Gram with atomics.  The
-// leading product (hi.hi) and the much smaller correction products go to two
-// separate accumulators, so the FP32 rounding of the leading sum spans only
-// 16 exact products and the corrections do not round against it; every slice
-// is summed in float64.
+// A CTA owns one 128 x 128 output tile of one variant and a chunk of K-slices
+// of 16 mocks: its operand tiles arrive by bulk copies (cp.async.bulk, the
+// TMA engine, completing on mbarriers) into a ring of stages, one thread
+// issues the tcgen05.mma chains into FP32 accumulators in tensor memory, and
+// the warps read them back with tcgen05.ld and write the chunk's partial Gram,
+// which a reduction kernel sums over the chunks in float64.  The leading
+// product (hi.hi) and the much smaller correction products go to two separate
+// accumulators, so the FP32 rounding of the leading sum spans only the
+// chunk's few exact products and the corrections do not round against it.
 //
 // Operand tiles are written by the split kernel directly in the canonical
 // K-major, non-swizzled layout of the tensor-core descriptors: 8-row x
@@ -38,7 +38,7 @@ constexpr int GRAM_SMEM_MIN = 100 * 1024;   // at most two CTAs per SM: their te
 constexpr int GRAM_THREADS = 128;
 constexpr long long SPIN_LIMIT = 1ll << 26;
 constexpr int NSTAGE = 3;                    // K-slices in flight per CTA
-constexpr int MAX_SPC = 16;                  // K-slices (16 mocks each) accumulated in FP32 per chunk
+constexpr int MAX_SPC = 2;                   // K-slices (16 mocks each) accumulated in FP32 per chunk
 constexpr long long PARTIAL_BYTES = 256ll << 20;   // bound of the per-chunk partial Grams
 
 template <int PREC>
@@ -266,7 +266,9 @@ constexpr int gram_smem_bytes() { return NSTAGE * stage_bytes<PREC>() + 8 * (2 *
 // accumulators and commits it to empty[stage]; once slice i - 1's MMAs have
 // read their stage, that stage is refilled with slice i - 1 + NSTAGE.  A
 // final commit to `done` releases the epilogue, which writes the chunk's
-// partial Gram (both triangles) to P[kc][v] with plain stores.
+// partial Gram (both triangles) to P[kc][v] with plain stores, or, when the
+// partials would not fit their bound (atomic_out), adds it into G[v] with
+// float64 atomics.
 //
 // Every wait is bounded.  The epilogue's wait on `done` gives up after
 // done_limit polls (a context option); skip_mma (tests only) makes CTA
@@ -275,8 +277,8 @@ constexpr int gram_smem_bytes() { return NSTAGE * stage_bytes<PREC>() + 8 * (2 *
 template <int PREC>
 __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned char *__restrict__ tiles, int nbin,
                                                               int n_rb, int n_ks, int spc, double *__restrict__ P,
-                                                              int *__restrict__ status, long long done_limit,
-                                                              int skip_mma)
+                                                              int atomic_out, int *__restrict__ status,
+                                                              long long done_limit, int skip_mma)
 {
     constexpr int TB = tile_bytes<PREC>();
     constexpr int NP = Split<PREC>::PIECES;
@@ -381,25 +383,41 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
         good = good && fin;
         if (fin && good) {
             tc_fence_after();
-            // warp w reads accumulator rows 32w..32w+31 (its tensor-memory lanes)
-            const int row = bi * TM + warp * 32 + lane;
-            double *g = P + ((size_t)kc * gridDim.y + v) * nbin * nbin;
+            // warp w reads accumulator rows 32w..32w+31 (its tensor-memory lanes), 32
+            // columns at a time.  The transposed block (col, row) is written from
+            // registers (lanes = consecutive rows); the block itself (row, col) through
+            // a 32 x 33 transpose in the warp's part of the now idle stage buffers, so
+            // that every store or atomic of a warp covers 32 consecutive doubles.
+            const int row0 = bi * TM + warp * 32;
+            double *g = P + ((atomic_out ? 0 : (size_t)kc * gridDim.y) + v) * nbin * nbin;
+            double *stg = reinterpret_cast<double *>(smem) + warp * 32 * 33;
 #pragma unroll 1
             for (int c0 = 0; c0 < TM; c0 += 32) {
                 uint32_t r[32], rc[32];
                 tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
                 tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(TM + c0), rc);
-                if (row < nbin) {
+                const int row = row0 + lane;
 #pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        const int col = bj * TM + c0 + j;
-                        if (col < nbin) {
-                            const double val = (double)__uint_as_float(r[j]) + (double)__uint_as_float(rc[j]);
-                            g[(size_t)row * nbin + col] = val;
-                            if (bi != bj) g[(size_t)col * nbin + row] = val;
-                        }
+                for (int j = 0; j < 32; j++) {
+                    const double val = (double)__uint_as_float(r[j]) + (double)__uint_as_float(rc[j]);
+                    stg[lane * 33 + j] = val;
+                    const int col = bj * TM + c0 + j;
+                    if (bi != bj && row < nbin && col < nbin) {
+                        if (atomic_out) atomicAdd(&g[(size_t)col * nbin + row], val);
+                        else g[(size_t)col * nbin + row] = val;
                     }
                 }
+                __syncwarp();
+                const int col = bj * TM + c0 + lane;
+#pragma unroll 4
+                for (int j = 0; j < 32; j++) {
+                    const int rr = row0 + j;
+                    if (rr < nbin && col < nbin) {
+                        if (atomic_out) atomicAdd(&g[(size_t)rr * nbin + col], stg[j * 33 + lane]);
+                        else g[(size_t)rr * nbin + col] = stg[j * 33 + lane];
+                    }
+                }
+                __syncwarp();
             }
         }
     }
@@ -422,9 +440,15 @@ __global__ void reduce_partials_kernel(const double *__restrict__ P, int n_kc, s
 // K-chunking of the Gram grid: n_kc chunks of spc slices each.  Enough chunks
 // that the grid covers every SM about twice, at most MAX_SPC slices (FP32
 // accumulation of MAX_SPC * KS mocks) per chunk, and the partials within
-// PARTIAL_BYTES.
+// PARTIAL_BYTES.  The FP32 rounding of a chunk's leading-product sum grows
+// about linearly with the mocks it holds (relative to the final covariance,
+// ~2^-24 k / sqrt(3 N) for k of N mocks, amplified a few times by the LC
+// combination's differences): 16 slices per chunk gave 5.9e-7 on the
+// 3500 x 200 workload against the 1e-6 budget, 1 slice 1.2e-7, so a chunk
+// holds at most 2.
 struct Chunking {
     int spc, n_kc;
+    bool atomic_out;   // partials beyond PARTIAL_BYTES: the chunks add into G with atomics instead
 };
 
 Chunking chunking(int n_mock, int nbin, int n_var, int n_sm)
@@ -433,11 +457,11 @@ Chunking chunking(int n_mock, int nbin, int n_var, int n_sm)
     const long long np = (long long)n_rb * (n_rb + 1) / 2;
     long long want = std::max<long long>(1, (2ll * std::max(1, n_sm) + np * n_var - 1) / (np * n_var));
     want = std::max<long long>(want, (n_ks + MAX_SPC - 1) / MAX_SPC);
-    const long long per = (long long)n_var * nbin * nbin * 8;
-    want = std::min<long long>(want, std::max<long long>(1, PARTIAL_BYTES / per));
     want = std::min<long long>(want, n_ks);
     const int spc = (int)((n_ks + want - 1) / want);
-    return Chunking{spc, (n_ks + spc - 1) / spc};
+    const int n_kc = (n_ks + spc - 1) / spc;
+    const long long per = (long long)n_var * nbin * nbin * 8;
+    return Chunking{spc, n_kc, n_kc > 1 && (long long)n_kc * per > PARTIAL_BYTES};
 }
 
 template <int PREC>
@@ -454,7 +478,7 @@ size_t work_bytes_of(int n_mock, int nbin, int n_var, int n_sm)
 {
     const Chunking c = chunking(n_mock, nbin, n_var, n_sm);
     const size_t g = (size_t)n_var * nbin * nbin * 8;
-    return al256(tiles_bytes<PREC>(n_mock, nbin, n_var)) + al256(g) + al256((size_t)c.n_kc * g) +
+    return al256(tiles_bytes<PREC>(n_mock, nbin, n_var)) + al256(g) + al256(c.atomic_out ? 0 : (size_t)c.n_kc * g) +
            al256((size_t)n_var * nbin * 8);
 }
 
@@ -474,8 +498,8 @@ cudaError_t run(const double *x0, const double *x1, const double *x2, int n_var,
     size_t o = al256(tiles_bytes<PREC>(n_mock, nbin, n_var));
     double *G = (double *)(w + o);
     o += al256(g * 8);
-    double *P = (double *)(w + o);
-    o += al256((size_t)ch.n_kc * g * 8);
+    double *P = ch.atomic_out ? G : (double *)(w + o);
+    o += al256(ch.atomic_out ? 0 : (size_t)ch.n_kc * g * 8);
     double *mean = (double *)(w + o);
     o += al256((size_t)n_var * nbin * 8);
     if (o > work_bytes) return cudaErrorInvalidValue;
@@ -486,15 +510,21 @@ cudaError_t run(const double *x0, const double *x1, const double *x2, int n_var,
     const int smem = std::max(gram_smem_bytes<PREC>(), GRAM_SMEM_MIN);
     e = cudaFuncSetAttribute(gram_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    if (ch.atomic_out) {
+        e = cudaMemsetAsync(G, 0, g * 8, s);
+        if (e != cudaSuccess) return e;
+    }
     gram_tc_kernel<PREC><<<dim3(np, n_var, ch.n_kc), GRAM_THREADS, smem, s>>>(
-        tiles, nbin, n_rb, n_ks, ch.spc, P, status, opt.wait_limit > 0 ? opt.wait_limit : SPIN_LIMIT,
-        opt.test_skip_mma);
+        tiles, nbin, n_rb, n_ks, ch.spc, P, ch.atomic_out ? 1 : 0, status,
+        opt.wait_limit > 0 ? opt.wait_limit : SPIN_LIMIT, opt.test_skip_mma);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int rb = (int)std::min<size_t>((g + 255) / 256, 4096);
-    reduce_partials_kernel<<<rb, 256, 0, s>>>(P, ch.n_kc, g, G);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (!ch.atomic_out) {
+        const int rb = (int)std::min<size_t>((g + 255) / 256, 4096);
+        reduce_partials_kernel<<<rb, 256, 0, s>>>(P, ch.n_kc, g, G);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (n_var == 1) return launch_scale(G, nbin, n_mock, C_lc, s);
     return launch_combine(G, nbin, n_mock, M_a, M, C_lc, Ca, Cb, A, B, s);
 }

@@ -88,4 +88,26 @@ __device__ __forceinline__ float rsqrt_approx(float x)
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 }  // namespace
+// Global nanosecond timer.
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Lane 0 of each warp at the end of a pair-count launch: stats[4] = max of
+// ~start (so ~stats[4] is the earliest start), stats[5] = latest end,
+// stats[6] = sum of the warps' spans, stats[7] = warps.  The launch's idle
+// fraction 1 - stats[6] / (stats[7] (stats[5] - ~stats[4])) is the share of
+// warp time spent finished while others still worked (the last-wave tail).
+__device__ __forceinline__ void record_warp_span(unsigned long long *stats, unsigned long long t0)
+{
+    const unsigned long long t1 = gtimer();
+    atomicMax(&stats[4], ~t0);
+    atomicMax(&stats[5], t1);
+    atomicAdd(&stats[6], t1 - t0);
+    atomicAdd(&stats[7], 1ull);
+}
+
 }  // namespace tpcf

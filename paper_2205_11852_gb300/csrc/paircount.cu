@@ -985,6 +985,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
 {
     const VarOff vo = var_offsets(prm, MID);
     const int tid = threadIdx.x;
+    const unsigned long long t_start = gtimer();
     {
         unsigned long long *T = (unsigned long long *)(smem_raw + vo.T);
         float2 *lohi = (float2 *)(smem_raw + vo.lohi);
@@ -1174,6 +1175,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) paircount_kernel(const __grid_c
         atomicAdd(&stats[0], cd);
         atomicAdd(&stats[1], bn);
         atomicAdd(&stats[2], ex);
+        record_warp_span(stats, t_start);
     }
 }
 

@@ -210,9 +210,10 @@ __device__ __forceinline__ void pair2_flags(uint64_t bx, uint64_t by, uint64_t b
 // One a-point against this lane's four b-points (two packed pairs q = 0, 1),
 // in one block of hand-written PTX so that the uncertainty of all four pairs
 // accumulates in one predicate (setp with .or): the four histogram adds, and
-// the warp's vote on "some pair of this a-point is uncertain".  CHK (self
+// whether some pair of this lane is uncertain.  The loop runs two a-points per
+// iteration (two independent blocks the scheduler interleaves) under one vote.  CHK (self
 // cell): a pair with a >= b goes to the lane's spare word instead.
-// Operands: %0 vote; %1-%6 b (x, y, z) of q = 0, 1; %7-%11 the a-record;
+// Operands: %0 the lane's uncertainty; %1-%6 b (x, y, z) of q = 0, 1; %7-%11 the a-record;
 // %12-%17 constants; %18 cs; %19 the s clamp; %20 Kl; %21, %22 LS, LT;
 // CHK: %23 a index, %24-%27 b indices of slots 0-3, %28 spare word.
 #define PD_DIFF(BX, BY, BZ)                          \
@@ -274,7 +275,6 @@ __device__ __forceinline__ void pair2_flags(uint64_t bx, uint64_t by, uint64_t b
     ".reg .pred p, c;\n\t"                                                            \
     "setp.ne.u32 p, %20, %20;\n\t"
 #define PD_TAIL                                      \
-    "vote.sync.any.pred p, p, 0xffffffff;\n\t"         \
     "selp.u32 %0, 1, 0, p;\n\t"                        \
     "}"
 
@@ -458,10 +458,22 @@ __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams 
             }
         }
     };
+    uint32_t ai = 0;
 #pragma unroll 1
-    for (uint32_t ai = 0; ai < na; ai++) {
+    for (; ai + 1 < na; ai += 2) {
+        const ARec a = load_a(wm.arec, ai), a2 = load_a(wm.arec, ai + 1);
+        const bool u0 = apoint<MU, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB, ad.dump);
+        const bool u1 = apoint<MU, CHK, LS, LT>(BX, BY, BZ, a2, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai + 1, IB, ad.dump);
+        if (__any_sync(0xffffffffu, u0 || u1)) {
+            settle(ai);
+            settle(ai + 1);
+        }
+    }
+    if (ai < na) {
         const ARec a = load_a(wm.arec, ai);
-        if (apoint<MU, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB, ad.dump)) settle(ai);
+        if (__any_sync(0xffffffffu, apoint<MU, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB,
+                                                            ad.dump)))
+            settle(ai);
     }
     __syncwarp();
 }
@@ -708,6 +720,7 @@ __global__ void __launch_bounds__(W * 32, 1)
 {
     const DOff o = d_off(prm.n_s, prm.n_rows, R, dp.C, W);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long t_start = gtimer();
     uint32_t *hist = (uint32_t *)(dsm + o.hist);
     unsigned long long *Tsh = (unsigned long long *)(dsm + o.T);
     unsigned *misc = (unsigned *)(dsm + o.misc);
@@ -813,6 +826,7 @@ __global__ void __launch_bounds__(W * 32, 1)
         atomicAdd(&stats[0], cd);
         atomicAdd(&stats[1], bn);
         atomicAdd(&stats[2], ex);
+        record_warp_span(stats, t_start);
     }
 }
 

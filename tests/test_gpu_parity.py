@@ -55,8 +55,8 @@ def _mocks_to_device(mocks):
     return out
 
 
-def _check_counts(ctx, tp, mocks, tb, ob, modes=(0, 1), terms=7, kernels=(0, 2), want_direct=None):
-    """Counts of both pair counters (TPCF_KERNEL_AUTO, which takes the direct counter where the
+def _check_counts(ctx, tp, mocks, tb, ob, modes=(0, 1), terms=7, kernels=(1, 2), want_direct=None):
+    """Counts of both pair counters (TPCF_KERNEL_DIRECT, which takes the direct counter where the
     binning suits it, and TPCF_KERNEL_GENERAL) in every mode, bit for bit against the oracle."""
     dm = _mocks_to_device(mocks)
     refs = [oracle.count_mock(mk.data, mk.randoms, ob) for mk in mocks]
@@ -218,10 +218,10 @@ def test_binning_beyond_shared_memory_refused(tp, ctx):
     assert ctx.tpcf_sync() == tp.TPCF_OK
 
 
-@pytest.mark.parametrize("kernel", [0, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_counts_golden_edge_pairs(tp, ctx, kernel):
-    """Hand-worked pairs at exact bin edges, through the default counter (the direct one for the periodic
-    section's linear bins) and the general one."""
+    """Hand-worked pairs at exact bin edges, through the default (autotuned) choice, the direct counter
+    (for the periodic section's linear bins) and the general one."""
     ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, kernel)
     try:
         _golden_edge_pairs(tp, ctx)
@@ -475,10 +475,12 @@ def test_full_size_mid_mock_bit_exact(tp, ctx):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("prec_name", ["TPCF_TF32X3", "TPCF_BF16X3"])
-@pytest.mark.parametrize("n_mock,nbin", [(2, 5), (64, 37), (301, 200), (3500, 200), (130, 400)])
+@pytest.mark.parametrize("n_mock,nbin", [(2, 5), (64, 37), (301, 200), (3500, 200), (130, 400), (400, 1000)])
 def test_lc_split_precision_within_1e6(tp, ctx, prec_name, n_mock, nbin):
     """Gram products in TF32x3 / BF16x3 with FP32 accumulation: every covariance element
-    within 1e-6 of the float64 oracle, normalised by sqrt(C^a_ii C^a_jj)."""
+    within 1e-6 of the float64 oracle, normalised by sqrt(C^a_ii C^a_jj).  400 x 1000 takes
+    the path whose per-chunk partial Grams would exceed their memory bound (chunks added with
+    float64 atomics); the others sum the partials in a fixed order."""
     xa1, xa2, xb = synth.synthetic_xi_variants(43, n_mock, nbin)
     g = [torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in (xa1, xa2, xb)]
     out = ctx.tpcf_lc_cov(*g, 1, 50.0, getattr(tp, prec_name))
@@ -530,12 +532,25 @@ def test_autotuner_choice_is_exact(tp):
     mocks = [w.make_mock(m) for m in range(8)]
     tb, ob = _periodic(L, w.s_edges, 5)
     c = tp.Context(0)
-    out = c.tpcf_count(_mocks_to_device(mocks), tb)
+    dm = _mocks_to_device(mocks)
+    out = c.tpcf_count(dm, tb)
     c.tpcf_sync()
     info = c.tpcf_last_count_info()
+    # the tuner chose a counter (linear bins, x line of sight: both apply), a subdivision, a unit size
+    # (the direct counter's is 64) and a grid of whole blocks per SM
+    assert info["pair_kernel"] in (tp.TPCF_KERNEL_DIRECT, tp.TPCF_KERNEL_GENERAL)
     assert info["cell_subdiv"] in (2, 3, 4) and info["unit_chunk"] in (64, 128)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert info["pair_blocks"] > 0 and info["pair_blocks"] % n_sm == 0
     for m in (0, 7):
         o = oracle.count_mock(mocks[m].data, mocks[m].randoms, ob)
         assert np.array_equal(out["dd"][m].cpu().numpy(), o["DD"])
         assert np.array_equal(out["dr"][m].cpu().numpy(), o["DR"])
+    # the per-launch path runs the tuned configuration and gives the same counts
+    pl = c.tpcf_count(dm, tb, mode=tp.TPCF_PER_LAUNCH)
+    c.tpcf_sync()
+    info2 = c.tpcf_last_count_info()
+    assert (info2["pair_kernel"], info2["cell_subdiv"]) == (info["pair_kernel"], info["cell_subdiv"])
+    for k in ("dd", "dr", "rr"):
+        assert torch.equal(out[k], pl[k])
     c.close()
