@@ -71,6 +71,8 @@ def parse():
                    help="skip the covariance-only measurement on 3500 mocks x 200 bins")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--subdiv", type=int, default=0, help="pin the mesh subdivision (0: library choice)")
+    p.add_argument("--pair-kernel", default="auto", choices=["auto", "direct", "general"],
+                   help="pair counter (auto: the autotuner's choice)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--smp-mocks", type=int, default=4,
                    help="mocks of the brute-force (Smp, M=50) comparison run; 0 skips it")
@@ -300,12 +302,12 @@ def measured_traffic(workload, n_mock, pair_kernel):
     """DRAM bytes of one pair-count launch from the committed ncu summary of this workload, if it was taken
     on the current kernel code (else None)."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "paircount_traffic.json")))[workload]
         src = kernel_source(pair_kernel)
+        rec = json.load(open(os.path.join(ROOT, "profiles", "paircount_traffic.json")))[workload][src]
         code = kernel_code_hash(os.path.join(ROOT, "paper_2205_11852_gb300", "csrc", src))
     except (OSError, KeyError, ValueError):
         return None
-    if rec.get("kernel") != src or code != rec.get("kernel_code_sha256_prefix"):
+    if code != rec.get("kernel_code_sha256_prefix"):
         return None
     return rec["dram_bytes_per_mock"] * n_mock
 
@@ -563,6 +565,8 @@ def main():
     ctx = tp.Context(local)
     if args.subdiv:
         ctx.tpcf_set_cell_subdiv(args.subdiv)
+    ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, {"auto": tp.TPCF_KERNEL_AUTO, "direct": tp.TPCF_KERNEL_DIRECT,
+                                             "general": tp.TPCF_KERNEL_GENERAL}[args.pair_kernel])
     job = Job(tp, ctx, dev, w, pos, layout, prec, world)
 
     if args.count_only:

@@ -91,10 +91,11 @@ __device__ __forceinline__ void red_add(uint32_t a, uint32_t v)
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
-// An a-point's record: -a_x, -a_y, -a_z, cp = m - n_mu a_x, cm = -m - n_mu a_x,
-// each duplicated for the packed operands.
+// An a-point's record, each value duplicated for the packed operands: -a_x,
+// -a_y, -a_z, then with the x line of sight p = m - n_mu a_x, q = -m - n_mu a_x,
+// with the midpoint line of sight (p, q, w) = a - 2 o (o: the observer).
 struct ARec {
-    float2 nax, nay, naz, cp, cm;
+    float2 nax, nay, naz, p, q, w;
 };
 
 // Histogram address of a pair with s-row word bits(S) and signed-mu-column
@@ -109,19 +110,67 @@ struct Sh {
 
 __device__ __forceinline__ uint64_t u64of(float2 v) { return *reinterpret_cast<uint64_t *>(&v); }
 
-// Constant operand pairs of the packed arithmetic.
+// Constant operand pairs of the packed arithmetic (the last five: midpoint
+// line of sight only).
 struct K2 {
-    uint64_t tiny, ms, m1, mh, mt, nm;
+    uint64_t tiny, ms, m1, mh, mt, nm, tinyl, mhalf, c1n, c3n, c05;
 };
 
 // One packed pair of pairs (b_p, a), (b_p', a) in hand-written PTX: the
-// packed s floor word S, the s residual FS and, with mu bins (MU), the mu
-// interval floor words TP, TM (the tiny addend, r = rsqrt(d2) by MUFU).
-template <bool MU>
+// packed s floor word S and s residual FS (the tiny addend, r = rsqrt(d2) by
+// MUFU) and, with mu bins, the signed mu floor words.  V = 1 (x line of
+// sight): TP, TM = the floors at both ends of the error interval.  V = 2
+// (midpoint line of sight): l = b + (a - 2 o), mu = (l.d) r rl with
+// rl = rsqrt(|l|^2 + tinyl), TM = floor(n_mu mu), TP = its residual
+// n_mu mu - TM - 1/2, CB = 1/2 - c2 - c1 r - c3 rl (certain when |TP| <= CB).
+template <int V>
 __device__ __forceinline__ void pair2_core(uint64_t bx, uint64_t by, uint64_t bz, const ARec &a, const K2 &k,
-                                           uint64_t &S, uint64_t &FS, uint64_t &TP, uint64_t &TM)
+                                           uint64_t &S, uint64_t &FS, uint64_t &TP, uint64_t &TM, uint64_t &CB)
 {
-    if (MU) {
+    if (V == 2) {
+        asm("{\n\t"
+            ".reg .b64 dx, dy, dz, d2, r, h, lx, ly, lz, q, l2, rl, w, mu, ht, cb;\n\t"
+            ".reg .f32 d2x, d2y, rx, ry, l2x, l2y, rlx, rly;\n\t"
+            "add.rn.f32x2 dx, %5, %8;\n\t"
+            "add.rn.f32x2 dy, %6, %9;\n\t"
+            "add.rn.f32x2 dz, %7, %10;\n\t"
+            "fma.rn.f32x2 d2, dx, dx, %14;\n\t"
+            "fma.rn.f32x2 d2, dy, dy, d2;\n\t"
+            "fma.rn.f32x2 d2, dz, dz, d2;\n\t"
+            "mov.b64 {d2x, d2y}, d2;\n\t"
+            "rsqrt.approx.ftz.f32 rx, d2x;\n\t"
+            "rsqrt.approx.ftz.f32 ry, d2y;\n\t"
+            "mov.b64 r, {rx, ry};\n\t"
+            "fma.rz.f32x2 %0, d2, r, %15;\n\t"
+            "fma.rn.f32x2 h, %0, %16, %17;\n\t"
+            "fma.rn.f32x2 %1, d2, r, h;\n\t"
+            "add.rn.f32x2 lx, %5, %11;\n\t"
+            "add.rn.f32x2 ly, %6, %12;\n\t"
+            "add.rn.f32x2 lz, %7, %13;\n\t"
+            "mul.rn.f32x2 q, lx, dx;\n\t"
+            "fma.rn.f32x2 q, ly, dy, q;\n\t"
+            "fma.rn.f32x2 q, lz, dz, q;\n\t"
+            "fma.rn.f32x2 l2, lx, lx, %20;\n\t"
+            "fma.rn.f32x2 l2, ly, ly, l2;\n\t"
+            "fma.rn.f32x2 l2, lz, lz, l2;\n\t"
+            "mov.b64 {l2x, l2y}, l2;\n\t"
+            "rsqrt.approx.ftz.f32 rlx, l2x;\n\t"
+            "rsqrt.approx.ftz.f32 rly, l2y;\n\t"
+            "mov.b64 rl, {rlx, rly};\n\t"
+            "mul.rn.f32x2 w, r, rl;\n\t"
+            "mul.rn.f32x2 mu, q, w;\n\t"
+            "fma.rz.f32x2 %3, mu, %19, %18;\n\t"
+            "fma.rn.f32x2 ht, %3, %16, %18;\n\t"
+            "fma.rn.f32x2 %2, mu, %19, ht;\n\t"
+            "add.rn.f32x2 %2, %2, %21;\n\t"
+            "fma.rn.f32x2 cb, %23, rl, %24;\n\t"
+            "fma.rn.f32x2 %4, %22, r, cb;\n\t"
+            "}"
+            : "=&l"(S), "=&l"(FS), "=&l"(TP), "=&l"(TM), "=&l"(CB)
+            : "l"(bx), "l"(by), "l"(bz), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(u64of(a.p)),
+              "l"(u64of(a.q)), "l"(u64of(a.w)), "l"(k.tiny), "l"(k.ms), "l"(k.m1), "l"(k.mh), "l"(k.mt), "l"(k.nm),
+              "l"(k.tinyl), "l"(k.mhalf), "l"(k.c1n), "l"(k.c3n), "l"(k.c05));
+    } else if (V == 1) {
         asm("{\n\t"
             ".reg .b64 dx, dy, dz, d2, r, h, xp, xm;\n\t"
             ".reg .f32 d2x, d2y, rx, ry;\n\t"
@@ -144,8 +193,9 @@ __device__ __forceinline__ void pair2_core(uint64_t bx, uint64_t by, uint64_t bz
             "fma.rz.f32x2 %3, xm, r, %16;\n\t"
             "}"
             : "=&l"(S), "=&l"(FS), "=&l"(TP), "=&l"(TM)
-            : "l"(bx), "l"(by), "l"(bz), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(u64of(a.cp)),
-              "l"(u64of(a.cm)), "l"(k.tiny), "l"(k.ms), "l"(k.m1), "l"(k.mh), "l"(k.mt), "l"(k.nm));
+            : "l"(bx), "l"(by), "l"(bz), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(u64of(a.p)),
+              "l"(u64of(a.q)), "l"(k.tiny), "l"(k.ms), "l"(k.m1), "l"(k.mh), "l"(k.mt), "l"(k.nm));
+        CB = 0;
     } else {
         asm("{\n\t"
             ".reg .b64 dx, dy, dz, d2, r, h;\n\t"
@@ -167,7 +217,7 @@ __device__ __forceinline__ void pair2_core(uint64_t bx, uint64_t by, uint64_t bz
             : "=&l"(S), "=&l"(FS)
             : "l"(bx), "l"(by), "l"(bz), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(k.tiny),
               "l"(k.ms), "l"(k.m1), "l"(k.mh));
-        TP = TM = 0;
+        TP = TM = CB = 0;
     }
 }
 
@@ -191,19 +241,22 @@ __device__ __forceinline__ void pair_addr(uint64_t S, uint64_t TM, float stop, u
 // Rare path: two pairs recomputed with one uncertainty flag each, by the
 // same instructions as the hot path's PTX block (so bit for bit the same
 // addresses and decisions).
-template <bool MU, int LS, int LT>
+template <int V, int LS, int LT>
 __device__ __forceinline__ void pair2_flags(uint64_t bx, uint64_t by, uint64_t bz, const ARec &a, const K2 &k,
                                             float cs, float stop, uint32_t Kl, uint32_t &a0, uint32_t &a1, bool &f0,
                                             bool &f1)
 {
-    uint64_t S, FS, TP, TM;
-    pair2_core<MU>(bx, by, bz, a, k, S, FS, TP, TM);
-    pair_addr<MU, LS, LT>(S, TM, stop, Kl, a0, a1);
+    uint64_t S, FS, TP, TM, CB;
+    pair2_core<V>(bx, by, bz, a, k, S, FS, TP, TM, CB);
+    pair_addr<(V > 0), LS, LT>(S, TM, stop, Kl, a0, a1);
     f0 = fabsf(lo_f(FS)) > cs;
     f1 = fabsf(hi_f(FS)) > cs;
-    if (MU) {
+    if (V == 1) {
         f0 = f0 || lo_f(TP) != lo_f(TM);
         f1 = f1 || hi_f(TP) != hi_f(TM);
+    } else if (V == 2) {
+        f0 = f0 || fabsf(lo_f(TP)) > lo_f(CB);
+        f1 = f1 || fabsf(hi_f(TP)) > hi_f(CB);
     }
 }
 
@@ -278,17 +331,123 @@ __device__ __forceinline__ void pair2_flags(uint64_t bx, uint64_t by, uint64_t b
     "selp.u32 %0, 1, 0, p;\n\t"                        \
     "}"
 
-template <bool MU, bool CHK, int LS, int LT>
+// Midpoint line of sight (no self-cell check; the self cell takes the rare
+// path's instructions).  Operands: %0 the lane's uncertainty; %1-%6 b; %7-%9
+// -a; %10-%12 a - 2 o; %13-%23 constants (tiny, ms, m1, mh, mt, nm, tinyl,
+// -1/2, c1n, c3n, c05); %24 cs; %25 the s clamp; %26 Kl; %27, %28 LS, LT.
+// The mu residual is (n_mu mu - floor(n_mu mu)) - 1/2: 1.5 * 2^23 - 1/2 has no
+// FP32 form, so the half is subtracted after the fraction.
+#define PM_PAIR(BX, BY, BZ)                          \
+    "add.rn.f32x2 dx, " BX ", %7;\n\t"                 \
+    "add.rn.f32x2 dy, " BY ", %8;\n\t"                 \
+    "add.rn.f32x2 dz, " BZ ", %9;\n\t"                 \
+    "fma.rn.f32x2 d2, dx, dx, %13;\n\t"                \
+    "fma.rn.f32x2 d2, dy, dy, d2;\n\t"                 \
+    "fma.rn.f32x2 d2, dz, dz, d2;\n\t"                 \
+    "mov.b64 {d2x, d2y}, d2;\n\t"                      \
+    "rsqrt.approx.ftz.f32 rx, d2x;\n\t"                \
+    "rsqrt.approx.ftz.f32 ry, d2y;\n\t"                \
+    "mov.b64 r, {rx, ry};\n\t"                         \
+    "fma.rz.f32x2 s, d2, r, %14;\n\t"                  \
+    "fma.rn.f32x2 h, s, %15, %16;\n\t"                 \
+    "fma.rn.f32x2 fs, d2, r, h;\n\t"                   \
+    "add.rn.f32x2 lx, " BX ", %10;\n\t"                \
+    "add.rn.f32x2 ly, " BY ", %11;\n\t"                \
+    "add.rn.f32x2 lz, " BZ ", %12;\n\t"                \
+    "mul.rn.f32x2 q, lx, dx;\n\t"                      \
+    "fma.rn.f32x2 q, ly, dy, q;\n\t"                   \
+    "fma.rn.f32x2 q, lz, dz, q;\n\t"                   \
+    "fma.rn.f32x2 l2, lx, lx, %19;\n\t"                \
+    "fma.rn.f32x2 l2, ly, ly, l2;\n\t"                 \
+    "fma.rn.f32x2 l2, lz, lz, l2;\n\t"                 \
+    "mov.b64 {l2x, l2y}, l2;\n\t"                      \
+    "rsqrt.approx.ftz.f32 rlx, l2x;\n\t"               \
+    "rsqrt.approx.ftz.f32 rly, l2y;\n\t"               \
+    "mov.b64 rl, {rlx, rly};\n\t"                      \
+    "mul.rn.f32x2 w, r, rl;\n\t"                       \
+    "mul.rn.f32x2 mu, q, w;\n\t"                       \
+    "fma.rz.f32x2 tm, mu, %18, %17;\n\t"               \
+    "fma.rn.f32x2 ht, tm, %15, %17;\n\t"               \
+    "fma.rn.f32x2 fm, mu, %18, ht;\n\t"                \
+    "add.rn.f32x2 fm, fm, %20;\n\t"                    \
+    "fma.rn.f32x2 cb, %22, rl, %23;\n\t"               \
+    "fma.rn.f32x2 cb, %21, r, cb;\n\t"                 \
+    "mov.b64 {sx, sy}, s;\n\t"                         \
+    "mov.b64 {fx, fy}, fs;\n\t"                        \
+    "mov.b64 {gx, gy}, fm;\n\t"                        \
+    "mov.b64 {kx, ky}, cb;\n\t"                        \
+    "mov.b64 {mx, my}, tm;\n\t"                        \
+    "abs.f32 fx, fx;\n\t"                              \
+    "abs.f32 fy, fy;\n\t"                              \
+    "abs.f32 gx, gx;\n\t"                              \
+    "abs.f32 gy, gy;\n\t"                              \
+    "setp.gtu.or.f32 p, fx, %24, p;\n\t"               \
+    "setp.gtu.or.f32 p, fy, %24, p;\n\t"               \
+    "setp.gtu.or.f32 p, gx, kx, p;\n\t"                \
+    "setp.gtu.or.f32 p, gy, ky, p;\n\t"                \
+    "min.f32 sx, sx, %25;\n\t"                         \
+    "min.f32 sy, sy, %25;\n\t"                         \
+    "mov.b32 ux, sx;\n\t"                              \
+    "mov.b32 uy, sy;\n\t"                              \
+    "shl.b32 ux, ux, %27;\n\t"                         \
+    "shl.b32 uy, uy, %27;\n\t"                         \
+    "add.u32 ux, ux, %26;\n\t"                         \
+    "add.u32 uy, uy, %26;\n\t"                         \
+    "mov.b32 vx, mx;\n\t"                              \
+    "mov.b32 vy, my;\n\t"                              \
+    "shl.b32 vx, vx, %28;\n\t"                         \
+    "shl.b32 vy, vy, %28;\n\t"                         \
+    "add.u32 ux, ux, vx;\n\t"                          \
+    "add.u32 uy, uy, vy;\n\t"                          \
+    "red.shared.add.u32 [ux], 1;\n\t"                  \
+    "red.shared.add.u32 [uy], 1;\n\t"
+#define PM_HEAD                                                                                \
+    "{\n\t"                                                                                      \
+    ".reg .b64 dx, dy, dz, d2, r, s, h, fs, lx, ly, lz, q, l2, rl, w, mu, tm, ht, fm, cb;\n\t"   \
+    ".reg .f32 d2x, d2y, rx, ry, l2x, l2y, rlx, rly, sx, sy, fx, fy, gx, gy, kx, ky, mx, my;\n\t" \
+    ".reg .b32 ux, uy, vx, vy;\n\t"                                                              \
+    ".reg .pred p;\n\t"                                                                          \
+    "setp.ne.u32 p, %26, %26;\n\t"
+
+template <int V, bool CHK, int LS, int LT>
 __device__ __forceinline__ bool apoint(const float2 (&BX)[NQ], const float2 (&BY)[NQ], const float2 (&BZ)[NQ],
                                        const ARec &a, const K2 &k, float cs, float stop, uint32_t Kl, uint32_t ia,
                                        const uint32_t (&IB)[NP], uint32_t dump)
 {
     static_assert(NQ == 2, "the PTX block covers two packed pairs");
+    constexpr bool MU = V > 0;
     uint32_t any;
+    if (V == 2) {
+        if (CHK) {
+            // the self cell: the rare path's instructions, pairs a >= b to the spare word
+            bool unc = false;
+#pragma unroll
+            for (int q = 0; q < NQ; q++) {
+                uint32_t x0, x1;
+                bool f0, f1;
+                pair2_flags<2, LS, LT>(u64of(BX[q]), u64of(BY[q]), u64of(BZ[q]), a, k, cs, stop, Kl, x0, x1, f0, f1);
+                if (!(ia < IB[2 * q])) x0 = dump;
+                if (!(ia < IB[2 * q + 1])) x1 = dump;
+                red_add(x0, 1u);
+                red_add(x1, 1u);
+                unc = unc || f0 || f1;
+            }
+            return unc;
+        }
+        asm volatile(PM_HEAD PM_PAIR("%1", "%2", "%3") PM_PAIR("%4", "%5", "%6") "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(any)
+                     : "l"(u64of(BX[0])), "l"(u64of(BY[0])), "l"(u64of(BZ[0])), "l"(u64of(BX[1])),
+                       "l"(u64of(BY[1])), "l"(u64of(BZ[1])), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)),
+                       "l"(u64of(a.p)), "l"(u64of(a.q)), "l"(u64of(a.w)), "l"(k.tiny), "l"(k.ms), "l"(k.m1),
+                       "l"(k.mh), "l"(k.mt), "l"(k.nm), "l"(k.tinyl), "l"(k.mhalf), "l"(k.c1n), "l"(k.c3n),
+                       "l"(k.c05), "f"(cs), "f"(stop), "r"(Kl), "n"(LS), "n"(LT)
+                     : "memory");
+        return any != 0;
+    }
 #define PD_IN                                                                                                     \
     "l"(u64of(BX[0])), "l"(u64of(BY[0])), "l"(u64of(BZ[0])), "l"(u64of(BX[1])), "l"(u64of(BY[1])),              \
-        "l"(u64of(BZ[1])), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(u64of(a.cp)),            \
-        "l"(u64of(a.cm)), "l"(k.tiny), "l"(k.ms), "l"(k.m1), "l"(k.mh), "l"(k.mt), "l"(k.nm), "f"(cs), "f"(stop), \
+        "l"(u64of(BZ[1])), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(u64of(a.p)),             \
+        "l"(u64of(a.q)), "l"(k.tiny), "l"(k.ms), "l"(k.m1), "l"(k.mh), "l"(k.mt), "l"(k.nm), "f"(cs), "f"(stop), \
         "r"(Kl), "n"(LS), "n"(LT)
     if (MU && CHK) {
         asm volatile(PD_HEAD PD_DIFF("%1", "%2", "%3") PD_MU("%1") PD_CHK("%24", "%25") PD_RED
@@ -323,6 +482,8 @@ __device__ __forceinline__ bool apoint(const float2 (&BX)[NQ], const float2 (&BY
 #undef PD_RED
 #undef PD_HEAD
 #undef PD_TAIL
+#undef PM_PAIR
+#undef PM_HEAD
 
 // Per-lane histogram address constants (see Sh).
 struct Addr {
@@ -339,12 +500,18 @@ struct WarpMem {
     uint2 *xl;        // pairs (a index, b index) awaiting the exact recheck
 };
 
+template <bool MID>
 __device__ __forceinline__ ARec load_a(const float4 *arec, uint32_t ai)
 {
     const float4 r0 = arec[3 * ai], r1 = arec[3 * ai + 1];
+    if (MID) {
+        const float4 r2 = arec[3 * ai + 2];
+        return ARec{make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y),
+                    make_float2(r1.z, r1.w), make_float2(r2.x, r2.y), make_float2(r2.z, r2.w)};
+    }
     const float2 r2 = *(const float2 *)&arec[3 * ai + 2];
     return ARec{make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y), make_float2(r1.z, r1.w),
-                r2};
+                r2, make_float2(0.f, 0.f)};
 }
 
 __device__ __forceinline__ void xl_put(uint2 *xl, uint32_t i, uint32_t ia, uint32_t ib) { xl[i] = make_uint2(ia, ib); }
@@ -402,12 +569,13 @@ __device__ __forceinline__ void load_tile(const float4 *buf, uint32_t nb, int la
 // predicate per lane; when any lane's is set, the a-point's pairs are
 // recomputed with a flag each, and each uncertain pair's add is taken back
 // and the pair joins the recheck list.
-template <bool MU, int R, int LOGC, bool CHK>
+template <int V, int R, int LOGC, bool CHK>
 __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams &dp, const Mesh &m,
                                      const unsigned long long *T, const WarpMem &wm, const Addr &ad, uint32_t nb,
                                      uint32_t na, uint32_t a0, int lane, uint32_t &n_list,
                                      unsigned long long &n_exact, unsigned long long &n_cand)
 {
+    constexpr bool MU = V > 0, MID = V == 2;
     float2 BX[NQ], BY[NQ], BZ[NQ];
     load_tile(wm.buf, nb, lane, BX, BY, BZ);
     uint32_t IB[NP] = {0u, 0u, 0u, 0u};
@@ -426,19 +594,24 @@ __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams 
     constexpr int LS = Sh<R, LOGC>::LS, LT = Sh<R, LOGC>::LT;
     const K2 k2{u64of(make_float2(dp.tiny, dp.tiny)), u64of(make_float2(MAG_S, MAG_S)), u64of(make_float2(-1.0f, -1.0f)),
                 u64of(make_float2(MAG_S - 0.5f, MAG_S - 0.5f)), u64of(make_float2(MAG_T, MAG_T)),
-                u64of(make_float2(dp.nmu, dp.nmu))};
+                u64of(make_float2(dp.nmu, dp.nmu)),
+                MID ? u64of(make_float2(dp.tinyl, dp.tinyl)) : 0ull,
+                MID ? u64of(make_float2(-0.5f, -0.5f)) : 0ull,
+                MID ? u64of(make_float2(-dp.c1, -dp.c1)) : 0ull,
+                MID ? u64of(make_float2(-dp.c3, -dp.c3)) : 0ull,
+                MID ? u64of(make_float2(dp.c05, dp.c05)) : 0ull};
     const uint32_t lt = (1u << lane) - 1u;
     // a-point ai had an uncertain pair in some lane: recompute its pairs with
     // one flag each (padding slots and, in the self cell, pairs a >= b never
     // count), take back each uncertain pair's add and put it on the recheck list
     auto settle = [&](uint32_t ai) {
-        const ARec a = load_a(wm.arec, ai);
+        const ARec a = load_a<MID>(wm.arec, ai);
         const uint32_t ia = a0 + ai;
         uint32_t xs[NP];
         bool fl[NP];
 #pragma unroll
         for (int q = 0; q < NQ; q++)
-            pair2_flags<MU, LS, LT>(u64of(BX[q]), u64of(BY[q]), u64of(BZ[q]), a, k2, dp.cs, dp.s_top, ad.Kl,
+            pair2_flags<V, LS, LT>(u64of(BX[q]), u64of(BY[q]), u64of(BZ[q]), a, k2, dp.cs, dp.s_top, ad.Kl,
                                     xs[2 * q], xs[2 * q + 1], fl[2 * q], fl[2 * q + 1]);
 #pragma unroll
         for (int p = 0; p < NP; p++) {
@@ -461,17 +634,17 @@ __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams 
     uint32_t ai = 0;
 #pragma unroll 1
     for (; ai + 1 < na; ai += 2) {
-        const ARec a = load_a(wm.arec, ai), a2 = load_a(wm.arec, ai + 1);
-        const bool u0 = apoint<MU, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB, ad.dump);
-        const bool u1 = apoint<MU, CHK, LS, LT>(BX, BY, BZ, a2, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai + 1, IB, ad.dump);
+        const ARec a = load_a<MID>(wm.arec, ai), a2 = load_a<MID>(wm.arec, ai + 1);
+        const bool u0 = apoint<V, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB, ad.dump);
+        const bool u1 = apoint<V, CHK, LS, LT>(BX, BY, BZ, a2, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai + 1, IB, ad.dump);
         if (__any_sync(0xffffffffu, u0 || u1)) {
             settle(ai);
             settle(ai + 1);
         }
     }
     if (ai < na) {
-        const ARec a = load_a(wm.arec, ai);
-        if (__any_sync(0xffffffffu, apoint<MU, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB,
+        const ARec a = load_a<MID>(wm.arec, ai);
+        if (__any_sync(0xffffffffu, apoint<V, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB,
                                                             ad.dump)))
             settle(ai);
     }
@@ -488,7 +661,7 @@ __device__ __forceinline__ float4 bpoint(const DirectParams &dp, uint32_t i, uin
 }
 
 // The unit: a-chunk [un.a0, un.a1) of cell un.cell against the term's neighbourhood.
-template <bool MU, int R, int LOGC>
+template <int V, int R, int LOGC>
 __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams &dp, const Mesh &m,
                                      const unsigned long long *T, const WarpMem &wm, const Addr &ad, const Unit &un,
                                      const Term &tm, int lane, uint32_t &n_list, unsigned long long &n_exact,
@@ -500,16 +673,30 @@ __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams 
     const size_t N = m.n_total;
     const uint32_t a0 = un.a0, na = un.a1 - un.a0;
     // the a-chunk in bin units relative to A's corner, as packed records
-    // (-x, -x, -y, -y), (-z, -z, m - n_mu x, ...), (-m - n_mu x, ...), and its box
+    // (-x, -x, -y, -y), then (-z, -z, m - n_mu x, ...), (-m - n_mu x, ..., 0, 0)
+    // (x line of sight) or (-z, -z, x - 2 o_x, ...), (y - 2 o_y, ..., z - 2 o_z, ...)
+    // (midpoint line of sight, o the observer in the same frame), and its box
+    float o2x = 0.f, o2y = 0.f, o2z = 0.f;
+    if (V == 2) {
+        o2x = 2.0f * __fmul_rn(__ll2float_rn(prm.obs[0] - (long long)ox), dp.inv_qds);
+        o2y = 2.0f * __fmul_rn(__ll2float_rn(prm.obs[1] - (long long)oy), dp.inv_qds);
+        o2z = 2.0f * __fmul_rn(__ll2float_rn(prm.obs[2] - (long long)oz), dp.inv_qds);
+    }
     float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
     for (uint32_t i = (uint32_t)lane; i < na; i += 32) {
         const size_t g = a0 + i;
         const float4 p = bpoint(dp, (uint32_t)g, m.us[g], m.us[N + g], m.us[2 * N + g], ox, oy, oz);
-        const float fxp = __fmul_rn(p.x, dp.nmu);
-        const float cp = __fsub_rn(dp.m, fxp), cm = __fsub_rn(-dp.m, fxp);
         wm.arec[3 * i] = make_float4(-p.x, -p.x, -p.y, -p.y);
-        wm.arec[3 * i + 1] = make_float4(-p.z, -p.z, cp, cp);
-        wm.arec[3 * i + 2] = make_float4(cm, cm, 0.f, 0.f);
+        if (V == 2) {
+            const float lax = __fsub_rn(p.x, o2x), lay = __fsub_rn(p.y, o2y), laz = __fsub_rn(p.z, o2z);
+            wm.arec[3 * i + 1] = make_float4(-p.z, -p.z, lax, lax);
+            wm.arec[3 * i + 2] = make_float4(lay, lay, laz, laz);
+        } else {
+            const float fxp = __fmul_rn(p.x, dp.nmu);
+            const float cp = __fsub_rn(dp.m, fxp), cm = __fsub_rn(-dp.m, fxp);
+            wm.arec[3 * i + 1] = make_float4(-p.z, -p.z, cp, cp);
+            wm.arec[3 * i + 2] = make_float4(cm, cm, 0.f, 0.f);
+        }
         lx = fminf(lx, p.x);
         ly = fminf(ly, p.y);
         lz = fminf(lz, p.z);
@@ -613,7 +800,7 @@ __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams 
             wm.buf[e2] = bpoint(dp, (uint32_t)g, m.us[g], m.us[N + g], m.us[2 * N + g], ox, oy, oz);
         }
         __syncwarp();
-        tile<MU, R, LOGC, true>(prm, dp, m, T, wm, ad, nb, na, a0, lane, n_list, n_exact, n_cand);
+        tile<V, R, LOGC, true>(prm, dp, m, T, wm, ad, nb, na, a0, lane, n_list, n_exact, n_cand);
     }
     // the neighbour runs: four raw points per lane per pass (their twelve
     // loads in flight together), survivors appended to the buffer, a tile
@@ -650,7 +837,7 @@ __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams 
         }
         if (nbuf >= TB) {
             __syncwarp();
-            tile<MU, R, LOGC, false>(prm, dp, m, T, wm, ad, TB, na, a0, lane, n_list, n_exact, n_cand);
+            tile<V, R, LOGC, false>(prm, dp, m, T, wm, ad, TB, na, a0, lane, n_list, n_exact, n_cand);
             // the leftovers (fewer than 128) move to the front
             const uint32_t left = nbuf - TB;
             float4 v[4];
@@ -670,7 +857,7 @@ __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams 
     }
     if (nbuf) {
         __syncwarp();
-        tile<MU, R, LOGC, false>(prm, dp, m, T, wm, ad, nbuf, na, a0, lane, n_list, n_exact, n_cand);
+        tile<V, R, LOGC, false>(prm, dp, m, T, wm, ad, nbuf, na, a0, lane, n_list, n_exact, n_cand);
     }
 }
 
@@ -711,13 +898,14 @@ __device__ __forceinline__ unsigned long long drain(const CountParams &prm, cons
     return binned;
 }
 
-template <bool MU, int R, int W, int LOGC>
+template <int V, int R, int W, int LOGC>
 __global__ void __launch_bounds__(W * 32, 1)
     pairdirect_kernel(const __grid_constant__ CountParams prm, const __grid_constant__ DirectParams dp, const Mesh m,
                       const Term *__restrict__ terms, const Unit *__restrict__ units,
                       const uint32_t *__restrict__ n_units_p, unsigned *__restrict__ claim,
                       unsigned long long *__restrict__ stats, int term_only, int chunk)
 {
+    constexpr bool MU = V > 0;
     const DOff o = d_off(prm.n_s, prm.n_rows, R, dp.C, W);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long t_start = gtimer();
@@ -802,7 +990,7 @@ __global__ void __launch_bounds__(W * 32, 1)
                 if (lane == 0) u = atomicAdd(&misc[1], 1u);
                 u = __shfl_sync(0xffffffffu, u, 0);
                 if (u >= e) break;
-                unit<MU, R, LOGC>(prm, dp, m, Tsh, wm, ad, units[u], tm, lane, n_list, n_exact, n_cand);
+                unit<V, R, LOGC>(prm, dp, m, Tsh, wm, ad, units[u], tm, lane, n_list, n_exact, n_cand);
             }
             __syncthreads();
             s = e;
@@ -830,22 +1018,27 @@ __global__ void __launch_bounds__(W * 32, 1)
     }
 }
 
-template <bool MU, int R, int W, int LOGC>
+template <int V, int R, int W, int LOGC>
 void *dkernel()
 {
-    return (void *)pairdirect_kernel<MU, R, W, LOGC>;
+    return (void *)pairdirect_kernel<V, R, W, LOGC>;
 }
 
-// kernel for (mu bins, copies, warps, column bits); nullptr when not built
-void *select_direct(bool mu, int R, int W, int logC)
+// kernel for (mode: 0 s only, 1 mu along x, 2 mu from the midpoint; copies, warps,
+// column bits); nullptr when not built
+void *select_direct(int V, int R, int W, int logC)
 {
     if (W != DIRECT_WARPS) return nullptr;
     constexpr int DW = DIRECT_WARPS;
-    if (!mu) return R == 32 ? dkernel<false, 32, DW, 0>() : dkernel<false, 16, DW, 0>();
-    if (logC == 5) return R == 32 ? dkernel<true, 32, DW, 5>() : dkernel<true, 16, DW, 5>();
-    if (logC == 6) return R == 32 ? dkernel<true, 32, DW, 6>() : dkernel<true, 16, DW, 6>();
+    if (V == 0) return R == 32 ? dkernel<0, 32, DW, 0>() : dkernel<0, 16, DW, 0>();
+    if (V == 1 && logC == 5) return R == 32 ? dkernel<1, 32, DW, 5>() : dkernel<1, 16, DW, 5>();
+    if (V == 1 && logC == 6) return R == 32 ? dkernel<1, 32, DW, 6>() : dkernel<1, 16, DW, 6>();
+    if (V == 2 && logC == 5) return R == 32 ? dkernel<2, 32, DW, 5>() : dkernel<2, 16, DW, 5>();
+    if (V == 2 && logC == 6) return R == 32 ? dkernel<2, 32, DW, 6>() : dkernel<2, 16, DW, 6>();
     return nullptr;
 }
+
+int mode_of(const DirectParams &d, bool mu) { return !mu ? 0 : (d.mid ? 2 : 1); }
 
 }  // namespace
 
@@ -856,14 +1049,14 @@ size_t pairdirect_smem_bytes(const CountParams &p, int R, int C, int W)
 
 cudaError_t pairdirect_set_attrs(const DirectParams &d, int mu)
 {
-    void *k = select_direct(mu != 0, d.R, d.W, d.logC);
+    void *k = select_direct(mode_of(d, mu != 0), d.R, d.W, d.logC);
     if (!k) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem);
 }
 
 int pairdirect_max_blocks_per_sm(const DirectParams &d, int mu)
 {
-    void *k = select_direct(mu != 0, d.R, d.W, d.logC);
+    void *k = select_direct(mode_of(d, mu != 0), d.R, d.W, d.logC);
     int nb = 0;
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, d.W * 32, d.smem) != cudaSuccess) {
         cudaGetLastError();
@@ -876,7 +1069,7 @@ cudaError_t launch_pairdirect(const CountParams &p, const DirectParams &d, const
                               const Unit *units, const uint32_t *n_units, unsigned *claim, unsigned long long *stats,
                               const PairLaunch &pl, cudaStream_t s)
 {
-    void *k = select_direct(p.n_mu > 1, d.R, d.W, d.logC);
+    void *k = select_direct(mode_of(d, p.n_mu > 1), d.R, d.W, d.logC);
     if (!k) return cudaErrorInvalidValue;
     const int term_only = pl.persistent ? -1 : pl.term;
     void *args[] = {(void *)&p,      (void *)&d,     (void *)&m,     (void *)&terms,     (void *)&units,

@@ -398,7 +398,8 @@ bool build_direct(const tpcf_binning &b, const Plan &pl, int smem_sm, int smem_b
     std::memset(&d, 0, sizeof(d));
     if (!p.linear) return false;
     const bool mu = p.n_mu > 1;
-    if (mu && p.los != TPCF_LOS_X) return false;
+    const bool mid = mu && p.los == TPCF_LOS_MIDPOINT;
+    if (mu && p.los != TPCF_LOS_X && !mid) return false;
     const double L = b.box_L;
     const double q = std::ldexp(1.0, p.bits) / L;
     const double qds = q * b.s_edges[1];
@@ -419,11 +420,38 @@ bool build_direct(const tpcf_binning &b, const Plan &pl, int smem_sm, int smem_b
     // most n_mu tiny / (2 s) <= m0 / 4 in the mu interval for s >= 2 m0, and
     // leaves the interval wider than one bin (always rechecked) below 2 m0
     double m0 = 0.0;
-    if (mu) {
+    if (mid) {
+        // Midpoint line of sight, l = a + b - 2 o in bin units (o: the observer
+        // relative to the cell's corner).  mu = (l.d) r rl from the computed
+        // vectors differs from the exact one by at most the angle each vector's
+        // rounding turns it, sqrt3 E_l / |l| + sqrt3 e_d / |d|, plus the
+        // arithmetic (the dot product gamma3, d2 and |l|^2 gamma3 and rsqrt rho
+        // each, two products): c1 r + c3 rl + c2 in units of n_mu mu.  The
+        // addends tiny, tinyl bias r, rl low by at most sqrt(tiny) r / 2 (resp.
+        // rl), folded into c1, c3 (x 1.5); below d2 = tiny, c1 r > 1/2 so the
+        // pair is always rechecked.  |mu| <= 1 + 2^-20 by Cauchy-Schwarz on the
+        // computed vectors, so the signed column stays within n_mu + 1.
+        const double Og0 = std::max({std::fabs((double)p.obs[0]), std::fabs((double)p.obs[1]),
+                                     std::fabs((double)p.obs[2])});
+        const double Og = Og0 + std::ldexp(1.0, p.bits) + Wmax;      // |observer - any cell corner|, grid units
+        const double Ob = Og / qds * (1.0 + std::ldexp(1.0, -20));
+        const double E_o = 0.5 * ulp_f32(Og) / qds * (1.0 + std::ldexp(1.0, -20)) + 0.5 * ulp_f32(Ob);
+        const double LAb = Xb + 2.0 * Ob * (1.0 + u24);
+        const double Lb = Xb + LAb;
+        const double E_l = 2.0 * E + 2.0 * E_o + 0.5 * ulp_f32(LAb) + 0.5 * ulp_f32(Lb);
+        const double c1_0 = n_mu * 1.1 * std::sqrt(3.0) * e_d, c3_0 = n_mu * 1.1 * std::sqrt(3.0) * E_l;
+        const double c2 = 1.1 * n_mu * (2.0 * g3 + 2.0 * rho + 2.0 * u24) + std::ldexp(1.0, -22);
+        d.c1 = up_f(1.5 * 1.01 * c1_0);
+        d.c3 = up_f(1.5 * 1.01 * c3_0);
+        d.c05 = down_f(0.5 - c2);
+        d.tinyl = down_f((c3_0 / n_mu) * (c3_0 / n_mu));
+        if (!(d.c1 < 0.05f) || !(d.c3 < 0.05f) || !(d.c05 > 0.45f) || !(d.tinyl >= 1.0e-30f)) return false;
+        m0 = c1_0 / n_mu;   // tiny = (c1_0 / n_mu)^2 below
+    } else if (mu) {
         m0 = 1.1 * (n_mu * 2.0 * E + 1.5 * ulp_f32(n_mu * Xb + 1.0) + n_mu * rho * (n_s + 1.0) + n_mu * dsq);
         if (!(m0 < 0.04)) return false;
     }
-    const float tiny = mu ? down_f(m0 * m0 / n_mu) : (float)std::ldexp(1.0, -60);
+    const float tiny = mid ? down_f(m0 * m0) : (mu ? down_f(m0 * m0 / n_mu) : (float)std::ldexp(1.0, -60));
     if (!(tiny > 0.0f)) return false;
     const double eps_s = 1.1 * (dsq + rho * (n_s + 1.5) + kappa * (n_s + 1.0) + (double)tiny) + u24;
     if (!(eps_s < 0.05)) return false;
@@ -431,10 +459,12 @@ bool build_direct(const tpcf_binning &b, const Plan &pl, int smem_sm, int smem_b
     d.logC = 0;
     d.CO = 0;
     if (mu) {
-        d.m = up_f(1.25 * m0 * (1.0 + 1e-6));
-        // |t+-| <= n_mu + m / sqrt(tiny): signed columns j in [-CO, CO - 1]
-        const double ext = (double)d.m / std::sqrt((double)tiny);
+        d.m = mid ? 0.0f : up_f(1.25 * m0 * (1.0 + 1e-6));
+        // |t+-| <= n_mu + m / sqrt(tiny) (x line of sight), |t| <= n_mu (1 + 2^-20)
+        // (midpoint): signed columns j in [-CO, CO - 1]
+        const double ext = mid ? 1.0 : (double)d.m / std::sqrt((double)tiny);
         d.CO = p.n_mu + 1 + (int)std::ceil(ext);
+        d.mid = mid ? 1 : 0;
         int lc = 0;
         while ((1 << lc) < 2 * d.CO) lc++;
         if (lc < 5) lc = 5;

@@ -92,7 +92,7 @@ struct DirectParams {
     int CO;            // column of mu bin 0 (the signed mu bin j sits in column j + CO)
     int rows;          // n_s + 1: the last row takes every pair at or beyond the last edge
     int smem;          // dynamic shared memory bytes
-    int pad;
+    int mid;           // 1: mu from the midpoint line of sight
     unsigned long long unit_pair_bound;   // pairs one unit can add to one histogram counter
     float inv_qds;     // grid units -> bin units
     float nmu;         // n_mu
@@ -102,6 +102,9 @@ struct DirectParams {
     float hit;         // filter: squared box distance (bin^2) below which a b-point is kept
     float s_top;       // 2^23 + n_s: the clamped row of pairs beyond the last edge
     float pad2;
+    // midpoint line of sight: t = n_mu mu is certain when |t - floor(t) - 1/2| <= c05 - c1 r - c3 rl
+    // (r = 1 / |d|, rl = 1 / |l| as computed); tinyl keeps rl finite
+    float c1, c3, c05, tinyl;
 };
 
 // Workspace layout produced by the mesh build and consumed by the counters.

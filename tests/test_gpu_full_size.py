@@ -63,22 +63,33 @@ def _oracle_sample_terms(mk, ob, origin):
     return out
 
 
-def _check_decomposition(ctx, tp, mocks, tb, ob, origin=(0.0, 0.0, 0.0)):
-    full = ctx.tpcf_count([_dev(mk.data, mk.randoms) for mk in mocks], tb, mode=tp.TPCF_BATCHED)
-    assert ctx.tpcf_sync() == tp.TPCF_OK
-    red = ctx.tpcf_count([_dev(mk.data[S_N:], [r[S_N:] for r in mk.randoms]) for mk in mocks], tb,
-                         mode=tp.TPCF_BATCHED)
-    assert ctx.tpcf_sync() == tp.TPCF_OK
-    for m, mk in enumerate(mocks):
-        ref = _oracle_sample_terms(mk, ob, origin)
-        dd = full["dd"][m].cpu().numpy()
-        assert dd.sum() > 0
-        assert np.array_equal(dd, red["dd"][m].cpu().numpy() + ref["DD"]), (m, "DD")
-        for i in range(len(mk.randoms)):
-            assert np.array_equal(full["dr"][m, i].cpu().numpy(), red["dr"][m, i].cpu().numpy() + ref["DR"][i]), \
-                (m, i, "DR")
-            assert np.array_equal(full["rr"][m, i].cpu().numpy(), red["rr"][m, i].cpu().numpy() + ref["RR"][i]), \
-                (m, i, "RR")
+def _check_decomposition(ctx, tp, mocks, tb, ob, origin=(0.0, 0.0, 0.0), want_direct=True):
+    """Both pair counters (TPCF_KERNEL_DIRECT, which must take the direct counter here, and
+    TPCF_KERNEL_GENERAL) against the same oracle sample counts."""
+    refs = [_oracle_sample_terms(mk, ob, origin) for mk in mocks]
+    full = None
+    for kern in (tp.TPCF_KERNEL_DIRECT, tp.TPCF_KERNEL_GENERAL):
+        ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, kern)
+        try:
+            full = ctx.tpcf_count([_dev(mk.data, mk.randoms) for mk in mocks], tb, mode=tp.TPCF_BATCHED)
+            assert ctx.tpcf_sync() == tp.TPCF_OK
+            ran = ctx.tpcf_last_count_info()["pair_kernel"]
+            assert ran == (kern if want_direct else tp.TPCF_KERNEL_GENERAL), (kern, ran)
+            red = ctx.tpcf_count([_dev(mk.data[S_N:], [r[S_N:] for r in mk.randoms]) for mk in mocks], tb,
+                                 mode=tp.TPCF_BATCHED)
+            assert ctx.tpcf_sync() == tp.TPCF_OK
+        finally:
+            ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, tp.TPCF_KERNEL_AUTO)
+        for m, mk in enumerate(mocks):
+            ref = refs[m]
+            dd = full["dd"][m].cpu().numpy()
+            assert dd.sum() > 0
+            assert np.array_equal(dd, red["dd"][m].cpu().numpy() + ref["DD"]), (kern, m, "DD")
+            for i in range(len(mk.randoms)):
+                assert np.array_equal(full["dr"][m, i].cpu().numpy(),
+                                      red["dr"][m, i].cpu().numpy() + ref["DR"][i]), (kern, m, i, "DR")
+                assert np.array_equal(full["rr"][m, i].cpu().numpy(),
+                                      red["rr"][m, i].cpu().numpy() + ref["RR"][i]), (kern, m, i, "RR")
     return full
 
 

@@ -162,7 +162,26 @@ def test_counts_open_midpoint(tp, ctx):
     edges = np.linspace(0, 50.0, 21)
     tb = tp.make_binning(edges, 5, tp.TPCF_OPEN, L, los=tp.TPCF_LOS_MIDPOINT, observer=(0, 0, 0))
     ob = oracle.Binning(edges, 5, oracle.OPEN, L, los=oracle.LOS_MIDPOINT, observer=(0, 0, 0))
-    _check_counts(ctx, tp, mocks, tb, ob)
+    _check_counts(ctx, tp, mocks, tb, ob, want_direct=True)
+
+
+def test_counts_open_midpoint_observer_inside(tp, ctx):
+    """Midpoint line of sight with the observer inside the catalogues: pairs whose midpoint lies at (or next
+    to) the observer, where the line of sight vanishes (mu = 0 by definition) or is set by a few grid units,
+    plus duplicated points (d = 0) and a pair placed symmetrically about the observer."""
+    L = 200.0
+    rng = synth.rng_for(37, 0, 0)
+    obs = np.array([100.0, 100.0, 100.0])
+    d = rng.random((1500, 3)) * L
+    # pairs placed symmetrically about the observer (l vanishes up to the grid rounding), and a duplicate
+    d[:4] = [obs + [3.0, 1.0, -2.0], obs - [3.0, 1.0, -2.0], obs + [0.5, 0.0, 0.0], obs - [0.5, 0.0, 0.0]]
+    d[4] = d[5]
+    r = [rng.random((1500, 3)) * L for _ in range(2)]
+    mocks = [synth.Mock(d, r)]
+    edges = np.linspace(0, 30.0, 13)
+    tb = tp.make_binning(edges, 4, tp.TPCF_OPEN, L, los=tp.TPCF_LOS_MIDPOINT, observer=tuple(obs))
+    ob = oracle.Binning(edges, 4, oracle.OPEN, L, los=oracle.LOS_MIDPOINT, observer=tuple(obs))
+    _check_counts(ctx, tp, mocks, tb, ob, want_direct=True)
 
 
 def test_counts_open_plane_parallel_slab(tp, ctx):
