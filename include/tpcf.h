@@ -364,6 +364,9 @@ typedef struct {
     double  idle_frac;        /* one batched launch: share of warp time between the first warp's start and
                                  the last warp's end that warps spent finished (the last-wave tail);
                                  -1 when the call made several launches or none */
+    double  call_ms;          /* with timing: the timed calls' whole spans on their streams (events at the
+                                 call's first and last enqueued operation), summed */
+    double  stage_ms;         /* with timing: the host-input copies of the timed TPCF_HOST_INPUT calls, summed */
 } tpcf_count_info;
 
 int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info);

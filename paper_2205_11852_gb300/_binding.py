@@ -147,7 +147,8 @@ class tpcf_count_info(ctypes.Structure):
                 ("n_paircount_launches", ctypes.c_int), ("cell_subdiv", ctypes.c_int),
                 ("cells_per_axis", ctypes.c_int), ("n_kernels", ctypes.c_int), ("timed_calls", ctypes.c_int),
                 ("unit_chunk", ctypes.c_int), ("graph_replay", ctypes.c_int), ("pair_kernel", ctypes.c_int),
-                ("pair_blocks", ctypes.c_int), ("idle_frac", ctypes.c_double)]
+                ("pair_blocks", ctypes.c_int), ("idle_frac", ctypes.c_double), ("call_ms", ctypes.c_double),
+                ("stage_ms", ctypes.c_double)]
 
 
 def load_library() -> ctypes.CDLL:

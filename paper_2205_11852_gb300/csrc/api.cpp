@@ -236,6 +236,8 @@ void tpcf_destroy(tpcf_ctx *ctx)
         if (e) cudaEventDestroy(e);
     if (ctx->done) cudaEventDestroy(ctx->done);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->call_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->stage_ev) cudaEventDestroy(e);
     if (ctx->status) cudaFree(ctx->status);
     if (ctx->stats) cudaFree(ctx->stats);
     if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
@@ -281,6 +283,8 @@ int tpcf_set_timing(tpcf_ctx *ctx, int enable)
     if (!ctx) return TPCF_ERR_ARG;
     ctx->timing = enable != 0;
     ctx->n_timed = 0;
+    ctx->n_call_timed = 0;
+    ctx->n_stage_timed = 0;
     return TPCF_OK;
 }
 
@@ -348,6 +352,19 @@ int tpcf_last_count_info(tpcf_ctx *ctx, tpcf_count_info *info)
     }
     info->paircount_ms = total;
     info->timed_calls = ctx->n_timed;
+    auto span_sum = [&](const std::vector<cudaEvent_t> &ev, int n, double &out) -> cudaError_t {
+        out = 0.0;
+        for (int i = 0; i < n; i++) {
+            float ms = 0;
+            cudaError_t e = cudaEventSynchronize(ev[2 * i + 1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+            if (e != cudaSuccess) return e;
+            out += ms;
+        }
+        return cudaSuccess;
+    };
+    CK(span_sum(ctx->call_ev, ctx->n_call_timed, info->call_ms));
+    CK(span_sum(ctx->stage_ev, ctx->n_stage_timed, info->stage_ms));
     return TPCF_OK;
 }
 

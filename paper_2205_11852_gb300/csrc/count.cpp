@@ -402,6 +402,21 @@ int upload_small(tpcf_ctx *ctx, const Setup &S, cudaStream_t s, void **dev)
     return staging_done(ctx, s);
 }
 
+// an event pair [2 k, 2 k + 1] of v for the k-th timed span, or -1
+int event_pair(std::vector<cudaEvent_t> &v, int k)
+{
+    if (k >= 4096) return -1;
+    while ((int)v.size() < 2 * (k + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        v.push_back(e);
+    }
+    return k;
+}
+
 // timing slot for this call, or -1
 int timing_slot(tpcf_ctx *ctx)
 {
@@ -741,13 +756,22 @@ extern "C" int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, con
     if (ctx->fail_count_at > 0 && ++ctx->n_count == ctx->fail_count_at)
         return cuda_fail(ctx, cudaErrorLaunchFailure, "tpcf_count (TPCF_TEST_FAIL_COUNT)");
     cudaStream_t s = (cudaStream_t)stream;
+    // timing: the call's whole span on its stream, and the host-input copy
+    const int call_slot = ctx->timing ? event_pair(ctx->call_ev, ctx->n_call_timed) : -1;
+    if (call_slot >= 0) CK(cudaEventRecord(ctx->call_ev[2 * call_slot], s));
     std::vector<tpcf_mock> staged;
     if (mode & TPCF_HOST_INPUT) {
         mode &= ~TPCF_HOST_INPUT;
         if (mode != TPCF_BATCHED && mode != TPCF_PER_LAUNCH) return fail(ctx, TPCF_ERR_ARG, "bad mode");
         if ((rc = validate_binning(ctx, binning))) return rc;
         if (terms == 0 || (terms & ~7u)) return fail(ctx, TPCF_ERR_ARG, "terms must be a non-empty mask of DD|DR|RR");
+        const int st = ctx->timing ? event_pair(ctx->stage_ev, ctx->n_stage_timed) : -1;
+        if (st >= 0) CK(cudaEventRecord(ctx->stage_ev[2 * st], s));
         if ((rc = stage_host_mocks(ctx, mocks, n_mock, terms, s, staged))) return rc;
+        if (st >= 0) {
+            CK(cudaEventRecord(ctx->stage_ev[2 * st + 1], s));
+            ctx->n_stage_timed++;
+        }
         mocks = staged.data();
     }
     // shape-level validation first, so that tuning never sees a bad call
@@ -788,5 +812,9 @@ extern "C" int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, con
     if (rc) return rc;
     if (slot >= 0) ctx->n_timed++;
     CK(cudaEventRecord(ctx->done, s));
+    if (call_slot >= 0) {
+        CK(cudaEventRecord(ctx->call_ev[2 * call_slot + 1], s));
+        ctx->n_call_timed++;
+    }
     return TPCF_OK;
 }

@@ -57,6 +57,9 @@ struct tpcf_ctx {
     // timing: one event pair per timed tpcf_count
     bool timing = false;
     std::vector<cudaEvent_t> ev;          // [2 * k]
+    // whole-call spans of timed tpcf_count calls on their stream [2 * k], and the host-input copies [2 * k]
+    std::vector<cudaEvent_t> call_ev, stage_ev;
+    int n_call_timed = 0, n_stage_timed = 0;
     int n_timed = 0;
     cudaEvent_t done = nullptr;           // recorded after the stats copy of the last tpcf_count
     cudaEvent_t scratch_ev[2] = {nullptr, nullptr};   // graph event nodes point here when untimed

@@ -33,13 +33,11 @@ namespace {
 
 constexpr int TM = 128;          // rows (bins) per tile, M = N of the MMA
 constexpr int KS = 16;           // mocks per K-slice
-constexpr int TMEM_COLS = 2 * TM; // two FP32 accumulators: leading product, corrections
-constexpr int GRAM_SMEM_MIN = 100 * 1024;   // at most two CTAs per SM: their tensor memory fits
-constexpr int GRAM_THREADS = 128;
+constexpr int TMEM_COLS = 4 * TM; // two accumulator sets of (leading product, corrections)
+constexpr int GRAM_THREADS = 160; // warps 0-3: the epilogue (TMEM lanes 0-127); warp 4: loads and MMAs
 constexpr long long SPIN_LIMIT = 1ll << 26;
-constexpr int NSTAGE = 3;                    // K-slices in flight per CTA
-constexpr int MAX_SPC = 2;                   // K-slices (16 mocks each) accumulated in FP32 per chunk
-constexpr long long PARTIAL_BYTES = 256ll << 20;   // bound of the per-chunk partial Grams
+constexpr int NSTAGE = 2;                    // K-slices in flight per CTA
+constexpr int TPAD = TM + 1;                 // row stride (floats) of the shared tile
 
 template <int PREC>
 struct Split;
@@ -256,39 +254,52 @@ __host__ __device__ constexpr uint32_t instr_desc()
 template <int PREC>
 __host__ __device__ constexpr int stage_bytes() { return 2 * Split<PREC>::PIECES * tile_bytes<PREC>(); }
 
-// shared memory: NSTAGE stages | full[NSTAGE], empty[NSTAGE], done barriers | TMEM slot | flags
+// shared memory: NSTAGE stages | FP32 tile sums and compensations [2][TM][TPAD] | full[NSTAGE], empty[NSTAGE],
+// accf[2], accfree[2], done barriers | TMEM slot | flags
 template <int PREC>
-constexpr int gram_smem_bytes() { return NSTAGE * stage_bytes<PREC>() + 8 * (2 * NSTAGE + 1) + 16; }
+constexpr int gram_smem_bytes() { return NSTAGE * stage_bytes<PREC>() + 8 * TM * TPAD + 8 * (2 * NSTAGE + 5) + 16; }
 
-// One CTA: output tile (bi, bj) of variant v over the K-slices [k0, k1) of
-// chunk kc.  Thread 0 keeps NSTAGE slices in flight (bulk copies completing
-// on full[stage]), issues each slice's MMA chain into the two TMEM
-// accumulators and commits it to empty[stage]; once slice i - 1's MMAs have
-// read their stage, that stage is refilled with slice i - 1 + NSTAGE.  A
-// final commit to `done` releases the epilogue, which writes the chunk's
-// partial Gram (both triangles) to P[kc][v] with plain stores, or, when the
-// partials would not fit their bound (atomic_out), adds it into G[v] with
-// float64 atomics.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// One CTA (one per SM): output tile (bi, bj) of variant v over the K-slices
+// [k0, k0 + n) of chunk kc.  Warp 4 keeps NSTAGE slices of operand tiles in
+// flight (bulk copies completing on full[stage]) and issues each slice's MMA
+// chain into accumulator set i % 2 of tensor memory (columns 256 (i % 2) +
+// [0, 128): leading product, + [128, 256): corrections), once the epilogue has
+// drained that set's previous slice (accfree).  Warps 0-3 (TMEM lanes = tile
+// rows) read each finished set (accf) and add its two accumulators into a
+// shared [column][row] tile by compensated (Kahan) FP32 summation (the FP64
+// pipe is too slow for this on the SMs), so the tile holds the chunk's sum to
+// about one FP32 rounding while the tensor cores work on slice i + 1.  At the end the
+// tile is written to P[kc][v] (both triangles) with stores of 32 consecutive
+// doubles per warp.
 //
-// Every wait is bounded.  The epilogue's wait on `done` gives up after
+// Every wait is bounded.  The epilogue's waits for the products give up after
 // done_limit polls (a context option); skip_mma (tests only) makes CTA
 // (0, 0, 0) wait for its first loads and then issue no MMA and no commit, so
 // that this wait runs out with no copy or MMA in flight.
 template <int PREC>
-__global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned char *__restrict__ tiles, int nbin,
-                                                              int n_rb, int n_ks, int spc, double *__restrict__ P,
-                                                              int atomic_out, int *__restrict__ status,
-                                                              long long done_limit, int skip_mma)
+__global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const unsigned char *__restrict__ tiles, int nbin,
+                                                                 int n_rb, int n_ks, int spc, double *__restrict__ P,
+                                                                 int *__restrict__ status, long long done_limit,
+                                                                 int skip_mma)
 {
     constexpr int TB = tile_bytes<PREC>();
     constexpr int NP = Split<PREC>::PIECES;
     constexpr int SB = stage_bytes<PREC>();
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = (uint64_t *)(smem + NSTAGE * SB);
+    float *tsum = (float *)(smem + NSTAGE * SB);              // [TM columns][TPAD]
+    float *tcmp = tsum + TM * TPAD;                           // Kahan compensations, same layout
+    uint64_t *full = (uint64_t *)(tcmp + TM * TPAD);
     uint64_t *empty = full + NSTAGE;
-    uint64_t *done = empty + NSTAGE;
+    uint64_t *accf = empty + NSTAGE;
+    uint64_t *accfree = accf + 2;
+    uint64_t *done = accfree + 2;
     uint32_t *slot = (uint32_t *)(done + 1);
-    int *flag = (int *)(slot + 1);   // [0]: the epilogue waits on done, [1]: every slice arrived and was multiplied
+    int *flag = (int *)(slot + 1);   // [0]: a done commit was issued or skipped on purpose, [1]: all slices multiplied
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // blockIdx.x enumerates the upper-triangle tile pairs (bi <= bj) row by row
@@ -308,120 +319,156 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_tc_kernel(const unsigned ch
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
+        for (int k = 0; k < 2; k++) {
+            mbar_init(&accf[k], 1);
+            mbar_init(&accfree[k], 4);
+        }
         mbar_init(done, 1);
         mbar_fence_init();
         flag[0] = 0;
         flag[1] = 0;
     }
+    for (int e = tid; e < 2 * TM * TPAD; e += blockDim.x) tsum[e] = 0.0f;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *slot;
 
-    if (tid == 0) {
-        auto issue = [&](int i) {   // the operand tiles of slice k0 + i into stage i % NSTAGE
-            unsigned char *sa = smem + (i % NSTAGE) * SB, *sb = sa + NP * TB;
-            mbar_expect_tx(&full[i % NSTAGE], (uint32_t)SB);
-            for (int p = 0; p < NP; p++) {
-                const size_t base = ((size_t)v * NP + p) * n_rb;
-                bulk_g2s(sa + p * TB, tiles + ((base + bi) * n_ks + k0 + i) * TB, TB, &full[i % NSTAGE]);
-                bulk_g2s(sb + p * TB, tiles + ((base + bj) * n_ks + k0 + i) * TB, TB, &full[i % NSTAGE]);
-            }
-        };
-        int issued = 0, waited = 0, mma_slices = 0;
-        bool ok = true;
-        for (; issued < min(NSTAGE, n); issued++) issue(issued);
-        for (int i = 0; i < n; i++) {
-            ok = mbar_wait(&full[i % NSTAGE], (uint32_t)(i / NSTAGE) & 1u, SPIN_LIMIT);
-            if (!ok) break;
-            waited = i + 1;
-            if (skip) {
-                if (waited == issued) break;   // every copy in flight has landed
-                continue;
-            }
-            tc_fence_after();
-            constexpr uint32_t idesc = instr_desc<PREC>();
-            constexpr int steps = KS / Split<PREC>::K_MMA;
-            const uint32_t sa = smem_addr(smem + (i % NSTAGE) * SB), sb = sa + NP * TB;
+    if (warp == 4) {
+        if (lane == 0) {
+            auto issue = [&](int i) {   // the operand tiles of slice k0 + i into stage i % NSTAGE
+                unsigned char *sa = smem + (i % NSTAGE) * SB, *sb = sa + NP * TB;
+                mbar_expect_tx(&full[i % NSTAGE], (uint32_t)SB);
+                for (int p = 0; p < NP; p++) {
+                    const size_t base = ((size_t)v * NP + p) * n_rb;
+                    bulk_g2s(sa + p * TB, tiles + ((base + bi) * n_ks + k0 + i) * TB, TB, &full[i % NSTAGE]);
+                    bulk_g2s(sb + p * TB, tiles + ((base + bj) * n_ks + k0 + i) * TB, TB, &full[i % NSTAGE]);
+                }
+            };
+            int issued = 0, waited = 0, mma_slices = 0;
+            bool ok = true;
+            for (; issued < min(NSTAGE, n); issued++) issue(issued);
+            for (int i = 0; i < n; i++) {
+                ok = mbar_wait(&full[i % NSTAGE], (uint32_t)(i / NSTAGE) & 1u, SPIN_LIMIT);
+                if (!ok) break;
+                waited = i + 1;
+                if (skip) {
+                    if (waited == issued) break;   // every copy in flight has landed
+                    continue;
+                }
+                // accumulator set i % 2 is free once the epilogue has drained slice i - 2
+                if (i >= 2) {
+                    ok = mbar_wait(&accfree[i % 2], (uint32_t)((i - 2) / 2) & 1u, SPIN_LIMIT);
+                    if (!ok) break;
+                }
+                tc_fence_after();
+                constexpr uint32_t idesc = instr_desc<PREC>();
+                constexpr int steps = KS / Split<PREC>::K_MMA;
+                const uint32_t sa = smem_addr(smem + (i % NSTAGE) * SB), sb = sa + NP * TB;
+                const uint32_t set = tmem + (uint32_t)((i % 2) * 2 * TM);
 #pragma unroll
-            for (int q = 0; q < Split<PREC>::N_PROD; q++) {
-                const uint32_t a0 = sa + Split<PREC>::pa(q) * TB;
-                const uint32_t b0 = sb + Split<PREC>::pb(q) * TB;
+                for (int q = 0; q < Split<PREC>::N_PROD; q++) {
+                    const uint32_t a0 = sa + Split<PREC>::pa(q) * TB;
+                    const uint32_t b0 = sb + Split<PREC>::pb(q) * TB;
 #pragma unroll
-                for (int st = 0; st < steps; st++) {
-                    // each MMA step covers two core matrices along K (2 x 128 bytes); product 0
-                    // accumulates in columns [0, 128), the others in [128, 256); the first step of
-                    // the chunk's first slice overwrites each accumulator
-                    const uint64_t da = smem_desc(a0 + st * 256, 128, sbo_bytes<PREC>());
-                    const uint64_t db = smem_desc(b0 + st * 256, 128, sbo_bytes<PREC>());
-                    const uint32_t d = tmem + (q == 0 ? 0u : (uint32_t)TM);
-                    const bool init = i == 0 && st == 0 && (q == 0 || q == 1);
-                    mma<PREC>(d, da, db, idesc, init ? 0u : 1u);
+                    for (int st = 0; st < steps; st++) {
+                        // each MMA step covers two core matrices along K (2 x 128 bytes); product 0
+                        // accumulates in the set's columns [0, 128), the others in [128, 256); the first
+                        // step of each accumulator overwrites it
+                        const uint64_t da = smem_desc(a0 + st * 256, 128, sbo_bytes<PREC>());
+                        const uint64_t db = smem_desc(b0 + st * 256, 128, sbo_bytes<PREC>());
+                        const uint32_t d = set + (q == 0 ? 0u : (uint32_t)TM);
+                        const bool init = st == 0 && (q == 0 || q == 1);
+                        mma<PREC>(d, da, db, idesc, init ? 0u : 1u);
+                    }
+                }
+                mma_commit(&empty[i % NSTAGE]);
+                mma_commit(&accf[i % 2]);
+                mma_slices = i + 1;
+                if (issued < n) {   // refill this stage once its products have read it
+                    ok = mbar_wait(&empty[i % NSTAGE], (uint32_t)(i / NSTAGE) & 1u, SPIN_LIMIT);
+                    if (!ok) break;
+                    issue(issued++);
                 }
             }
-            mma_commit(&empty[i % NSTAGE]);
-            mma_slices = i + 1;
-            // refill the stage of slice i - 1 once its MMAs have read it
-            if (i >= 1 && issued < n) {
-                ok = mbar_wait(&empty[(i - 1) % NSTAGE], (uint32_t)((i - 1) / NSTAGE) & 1u, SPIN_LIMIT);
-                if (!ok) break;
-                issue(issued++);
-            }
+            if (mma_slices > 0) mma_commit(done);
+            // copies still in flight after a wait gave up get one more bounded wait each
+            for (int i = waited; i < issued; i++)
+                if (!mbar_wait(&full[i % NSTAGE], (uint32_t)(i / NSTAGE) & 1u, SPIN_LIMIT)) break;
+            flag[0] = (mma_slices > 0 || skip) ? 1 : 0;
+            flag[1] = (ok && mma_slices == n) ? 1 : 0;
+            if (!ok) atomicOr(status, STATUS_TIMEOUT);
         }
-        if (mma_slices > 0) mma_commit(done);
-        // copies still in flight after a wait gave up get one more bounded wait each
-        for (int i = waited; i < issued; i++)
-            if (!mbar_wait(&full[i % NSTAGE], (uint32_t)(i / NSTAGE) & 1u, SPIN_LIMIT)) break;
-        flag[0] = (mma_slices > 0 || skip) ? 1 : 0;
-        flag[1] = (ok && mma_slices == n) ? 1 : 0;
+    } else {
+        // epilogue: row = this thread's TMEM lane
+        const int r = warp * 32 + lane;
+        bool fine = true;
+        for (int i = 0; i < n && fine; i++) {
+            fine = mbar_wait(&accf[i % 2], (uint32_t)(i / 2) & 1u, done_limit);
+            if (!fine) {
+                fine = mbar_wait(&accf[i % 2], (uint32_t)(i / 2) & 1u, done_limit);
+                if (!fine) break;
+            }
+            tc_fence_after();
+            const uint32_t set = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((i % 2) * 2 * TM);
+#pragma unroll 1
+            for (int c0 = 0; c0 < TM; c0 += 32) {
+                uint32_t lo[32], hi[32];
+                tmem_ld32(set + (uint32_t)c0, lo);
+                tmem_ld32(set + (uint32_t)(TM + c0), hi);
+#pragma unroll
+                for (int j = 0; j < 32; j++) {
+                    const int e = (c0 + j) * TPAD + r;
+                    float sum = tsum[e], cmp = tcmp[e];
+                    // two compensated additions (the leading product, then the corrections)
+                    float y = __fsub_rn(__uint_as_float(lo[j]), cmp);
+                    float t = __fadd_rn(sum, y);
+                    cmp = __fsub_rn(__fsub_rn(t, sum), y);
+                    sum = t;
+                    y = __fsub_rn(__uint_as_float(hi[j]), cmp);
+                    t = __fadd_rn(sum, y);
+                    cmp = __fsub_rn(__fsub_rn(t, sum), y);
+                    tsum[e] = t;
+                    tcmp[e] = cmp;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accfree[i % 2]);
+        }
+        if (!fine && lane == 0) atomicOr(status, STATUS_TIMEOUT);
     }
     __syncthreads();
+    // every product has completed before tensor memory is released (bounded)
     bool good = flag[1] != 0;
     if (flag[0]) {
         bool fin = mbar_wait(done, 0, done_limit);
         if (!fin) fin = mbar_wait(done, 0, done_limit);
         good = good && fin;
-        if (fin && good) {
-            tc_fence_after();
-            // warp w reads accumulator rows 32w..32w+31 (its tensor-memory lanes), 32
-            // columns at a time.  The transposed block (col, row) is written from
-            // registers (lanes = consecutive rows); the block itself (row, col) through
-            // a 32 x 33 transpose in the warp's part of the now idle stage buffers, so
-            // that every store or atomic of a warp covers 32 consecutive doubles.
-            const int row0 = bi * TM + warp * 32;
-            double *g = P + ((atomic_out ? 0 : (size_t)kc * gridDim.y) + v) * nbin * nbin;
-            double *stg = reinterpret_cast<double *>(smem) + warp * 32 * 33;
-#pragma unroll 1
-            for (int c0 = 0; c0 < TM; c0 += 32) {
-                uint32_t r[32], rc[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(TM + c0), rc);
-                const int row = row0 + lane;
-#pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    const double val = (double)__uint_as_float(r[j]) + (double)__uint_as_float(rc[j]);
-                    stg[lane * 33 + j] = val;
-                    const int col = bj * TM + c0 + j;
-                    if (bi != bj && row < nbin && col < nbin) {
-                        if (atomic_out) atomicAdd(&g[(size_t)col * nbin + row], val);
-                        else g[(size_t)col * nbin + row] = val;
-                    }
-                }
-                __syncwarp();
-                const int col = bj * TM + c0 + lane;
-#pragma unroll 4
-                for (int j = 0; j < 32; j++) {
-                    const int rr = row0 + j;
-                    if (rr < nbin && col < nbin) {
-                        if (atomic_out) atomicAdd(&g[(size_t)rr * nbin + col], stg[j * 33 + lane]);
-                        else g[(size_t)rr * nbin + col] = stg[j * 33 + lane];
-                    }
-                }
-                __syncwarp();
+    }
+    if (!good && tid == 0) atomicOr(status, STATUS_TIMEOUT);
+    if (good && warp < 4) {
+        double *g = P + ((size_t)kc * gridDim.y + v) * nbin * nbin;
+        const int t = warp * 32 + lane;
+        // the block itself: thread t takes column t (consecutive threads, consecutive doubles)
+        const int col = bj * TM + t;
+        if (col < nbin) {
+            for (int rr = 0; rr < TM; rr++) {
+                const int row = bi * TM + rr;
+                if (row >= nbin) break;
+                g[(size_t)row * nbin + col] = (double)tsum[t * TPAD + rr] - (double)tcmp[t * TPAD + rr];
+            }
+        }
+        // the transposed block of an off-diagonal pair: thread t takes row t
+        const int row = bi * TM + t;
+        if (bi != bj && row < nbin) {
+            for (int c = 0; c < TM; c++) {
+                const int cc = bj * TM + c;
+                if (cc >= nbin) break;
+                g[(size_t)cc * nbin + row] = (double)tsum[c * TPAD + t] - (double)tcmp[c * TPAD + t];
             }
         }
     }
-    if (!good && tid == 0) atomicOr(status, STATUS_TIMEOUT);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
@@ -437,31 +484,23 @@ __global__ void reduce_partials_kernel(const double *__restrict__ P, int n_kc, s
     }
 }
 
-// K-chunking of the Gram grid: n_kc chunks of spc slices each.  Enough chunks
-// that the grid covers every SM about twice, at most MAX_SPC slices (FP32
-// accumulation of MAX_SPC * KS mocks) per chunk, and the partials within
-// PARTIAL_BYTES.  The FP32 rounding of a chunk's leading-product sum grows
-// about linearly with the mocks it holds (relative to the final covariance,
-// ~2^-24 k / sqrt(3 N) for k of N mocks, amplified a few times by the LC
-// combination's differences): 16 slices per chunk gave 5.9e-7 on the
-// 3500 x 200 workload against the 1e-6 budget, 1 slice 1.2e-7, so a chunk
-// holds at most 2.
+// K-chunking of the Gram grid: n_kc chunks of spc slices each, enough that
+// the grid covers every SM (one CTA per SM: 512 TMEM columns and ~200 KB of
+// shared memory each); the FP32 rounding spans one 16-mock slice whatever the
+// chunk length.  The partials then take at most about n_sm x 2 TM^2 x 8 bytes
+// (n_kc x n_var x nbin^2 doubles with n_kc ~ n_sm / (n_var x tile pairs)).
 struct Chunking {
     int spc, n_kc;
-    bool atomic_out;   // partials beyond PARTIAL_BYTES: the chunks add into G with atomics instead
 };
 
 Chunking chunking(int n_mock, int nbin, int n_var, int n_sm)
 {
     const int n_rb = (nbin + TM - 1) / TM, n_ks = (n_mock + KS - 1) / KS;
     const long long np = (long long)n_rb * (n_rb + 1) / 2;
-    long long want = std::max<long long>(1, (2ll * std::max(1, n_sm) + np * n_var - 1) / (np * n_var));
-    want = std::max<long long>(want, (n_ks + MAX_SPC - 1) / MAX_SPC);
+    long long want = std::max<long long>(1, ((long long)std::max(1, n_sm) + np * n_var - 1) / (np * n_var));
     want = std::min<long long>(want, n_ks);
     const int spc = (int)((n_ks + want - 1) / want);
-    const int n_kc = (n_ks + spc - 1) / spc;
-    const long long per = (long long)n_var * nbin * nbin * 8;
-    return Chunking{spc, n_kc, n_kc > 1 && (long long)n_kc * per > PARTIAL_BYTES};
+    return Chunking{spc, (n_ks + spc - 1) / spc};
 }
 
 template <int PREC>
@@ -478,7 +517,7 @@ size_t work_bytes_of(int n_mock, int nbin, int n_var, int n_sm)
 {
     const Chunking c = chunking(n_mock, nbin, n_var, n_sm);
     const size_t g = (size_t)n_var * nbin * nbin * 8;
-    return al256(tiles_bytes<PREC>(n_mock, nbin, n_var)) + al256(g) + al256(c.atomic_out ? 0 : (size_t)c.n_kc * g) +
+    return al256(tiles_bytes<PREC>(n_mock, nbin, n_var)) + al256(g) + al256((size_t)c.n_kc * g) +
            al256((size_t)n_var * nbin * 8);
 }
 
@@ -489,7 +528,7 @@ cudaError_t run(const double *x0, const double *x1, const double *x2, int n_var,
                 int *status, const GramOpts &opt, cudaStream_t s)
 {
     const int n_rb = (nbin + TM - 1) / TM, n_ks = (n_mock + KS - 1) / KS;
-    if (n_ks > 65535 * MAX_SPC || n_rb > 90) return cudaErrorInvalidValue;
+    if (n_rb > 90) return cudaErrorInvalidValue;
     const Chunking ch = chunking(n_mock, nbin, n_var, opt.n_sm);
     if (ch.n_kc > 65535) return cudaErrorInvalidValue;
     unsigned char *w = (unsigned char *)work;
@@ -498,8 +537,8 @@ cudaError_t run(const double *x0, const double *x1, const double *x2, int n_var,
     size_t o = al256(tiles_bytes<PREC>(n_mock, nbin, n_var));
     double *G = (double *)(w + o);
     o += al256(g * 8);
-    double *P = ch.atomic_out ? G : (double *)(w + o);
-    o += al256(ch.atomic_out ? 0 : (size_t)ch.n_kc * g * 8);
+    double *P = (double *)(w + o);
+    o += al256((size_t)ch.n_kc * g * 8);
     double *mean = (double *)(w + o);
     o += al256((size_t)n_var * nbin * 8);
     if (o > work_bytes) return cudaErrorInvalidValue;
@@ -507,24 +546,18 @@ cudaError_t run(const double *x0, const double *x1, const double *x2, int n_var,
     if (e != cudaSuccess) return e;
     split_kernel<PREC><<<dim3(n_ks, n_rb, n_var), 256, 0, s>>>(x0, x1, x2, mean, n_mock, nbin, n_rb, n_ks, tiles);
     const int np = n_rb * (n_rb + 1) / 2;   // upper-triangle tile pairs
-    const int smem = std::max(gram_smem_bytes<PREC>(), GRAM_SMEM_MIN);
+    const int smem = gram_smem_bytes<PREC>();
     e = cudaFuncSetAttribute(gram_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    if (ch.atomic_out) {
-        e = cudaMemsetAsync(G, 0, g * 8, s);
-        if (e != cudaSuccess) return e;
-    }
     gram_tc_kernel<PREC><<<dim3(np, n_var, ch.n_kc), GRAM_THREADS, smem, s>>>(
-        tiles, nbin, n_rb, n_ks, ch.spc, P, ch.atomic_out ? 1 : 0, status,
-        opt.wait_limit > 0 ? opt.wait_limit : SPIN_LIMIT, opt.test_skip_mma);
+        tiles, nbin, n_rb, n_ks, ch.spc, P, status, opt.wait_limit > 0 ? opt.wait_limit : SPIN_LIMIT,
+        opt.test_skip_mma);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (!ch.atomic_out) {
-        const int rb = (int)std::min<size_t>((g + 255) / 256, 4096);
-        reduce_partials_kernel<<<rb, 256, 0, s>>>(P, ch.n_kc, g, G);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    const int rb = (int)std::min<size_t>((g + 255) / 256, 4096);
+    reduce_partials_kernel<<<rb, 256, 0, s>>>(P, ch.n_kc, g, G);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     if (n_var == 1) return launch_scale(G, nbin, n_mock, C_lc, s);
     return launch_combine(G, nbin, n_mock, M_a, M, C_lc, Ca, Cb, A, B, s);
 }

@@ -497,9 +497,8 @@ def test_full_size_mid_mock_bit_exact(tp, ctx):
 @pytest.mark.parametrize("n_mock,nbin", [(2, 5), (64, 37), (301, 200), (3500, 200), (130, 400), (400, 1000)])
 def test_lc_split_precision_within_1e6(tp, ctx, prec_name, n_mock, nbin):
     """Gram products in TF32x3 / BF16x3 with FP32 accumulation: every covariance element
-    within 1e-6 of the float64 oracle, normalised by sqrt(C^a_ii C^a_jj).  400 x 1000 takes
-    the path whose per-chunk partial Grams would exceed their memory bound (chunks added with
-    float64 atomics); the others sum the partials in a fixed order."""
+    within 1e-6 of the float64 oracle, normalised by sqrt(C^a_ii C^a_jj); 400 x 1000 has 36 tile
+    pairs per variant (more CTAs than SMs, one chunk of slices each)."""
     xa1, xa2, xb = synth.synthetic_xi_variants(43, n_mock, nbin)
     g = [torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in (xa1, xa2, xb)]
     out = ctx.tpcf_lc_cov(*g, 1, 50.0, getattr(tp, prec_name))
