@@ -191,6 +191,15 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
                 S.terms.push_back(Term{cr + i, cr + i, 1, 0, (long long *)rr + ((size_t)m * M + i) * nbin});
         }
     }
+    // longest first: terms in decreasing order of their pair count (n_a n_b, or n (n - 1) / 2 for an auto
+    // count), so that the units claimed last, at the end of a launch, belong to the cheapest terms
+    std::stable_sort(S.terms.begin(), S.terms.end(), [&](const Term &x, const Term &y) {
+        auto cost = [&](const Term &t) {
+            const double na = (double)S.cats[t.cat_a].n, nb = (double)S.cats[t.cat_b].n;
+            return t.auto_pairs ? 0.5 * na * (na - 1.0) : na * nb;
+        };
+        return cost(x) > cost(y);
+    });
     S.dd = (terms & TPCF_DD) ? dd : nullptr;
     S.dr = (terms & TPCF_DR) ? dr : nullptr;
     S.rr = (terms & TPCF_RR) ? rr : nullptr;
@@ -266,8 +275,14 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
         if (occ < 1) return fail(ctx, TPCF_ERR_CUDA, "the direct pair counter does not fit on an SM");
         S.smem = S.dp.smem;
         S.blocks = ctx->n_sm * (cfg.bps > 0 ? std::min(cfg.bps, occ) : occ);
-        // units per block claim: a few claims per block, at most 2^30 pairs per counter
-        const unsigned long long by_work = std::max<unsigned long long>(1, S.units_bound / (3ull * S.blocks));
+        // units per block claim, at most 2^30 pairs per counter: about eight claims per block in the
+        // batched launch; in the one-launch-per-term mode one claim per block of the term's share (every
+        // claim ends in a block barrier, which a launch of one term cannot amortise)
+        const unsigned long long by_work =
+            mode == TPCF_PER_LAUNCH
+                ? std::max<unsigned long long>(1, (S.units_bound / std::max<size_t>(1, S.terms.size()) + S.blocks - 1) /
+                                                      (unsigned long long)S.blocks)
+                : std::max<unsigned long long>(1, S.units_bound / (8ull * S.blocks));
         const unsigned long long by_wrap = std::max<unsigned long long>(1, (1ull << 30) / S.dp.unit_pair_bound);
         S.claim_units = (int)std::min<unsigned long long>({by_work, by_wrap, 4096ull});
         return TPCF_OK;
