@@ -191,15 +191,26 @@ int prepare(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binnin
                 S.terms.push_back(Term{cr + i, cr + i, 1, 0, (long long *)rr + ((size_t)m * M + i) * nbin});
         }
     }
-    // longest first: terms in decreasing order of their pair count (n_a n_b, or n (n - 1) / 2 for an auto
-    // count), so that the units claimed last, at the end of a launch, belong to the cheapest terms
-    std::stable_sort(S.terms.begin(), S.terms.end(), [&](const Term &x, const Term &y) {
+    // longest first: mocks in decreasing order of their pair count (the sum over their terms of n_a n_b,
+    // or n (n - 1) / 2 for an auto count), each mock's terms kept together (its catalogues stay in L2), so
+    // that the units claimed last, at the end of a launch, belong to the cheapest mocks
+    {
         auto cost = [&](const Term &t) {
             const double na = (double)S.cats[t.cat_a].n, nb = (double)S.cats[t.cat_b].n;
             return t.auto_pairs ? 0.5 * na * (na - 1.0) : na * nb;
         };
-        return cost(x) > cost(y);
-    });
+        const size_t per = S.terms.size() / std::max(1, n_mock);   // every mock adds the same number of terms
+        std::vector<double> mc(n_mock, 0.0);
+        for (size_t k = 0; k < S.terms.size(); k++) mc[k / std::max<size_t>(1, per)] += cost(S.terms[k]);
+        std::vector<int> order(n_mock);
+        for (int m = 0; m < n_mock; m++) order[m] = m;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return mc[x] > mc[y]; });
+        std::vector<Term> sorted;
+        sorted.reserve(S.terms.size());
+        for (int m : order)
+            for (size_t k = 0; k < per; k++) sorted.push_back(S.terms[(size_t)m * per + k]);
+        S.terms.swap(sorted);
+    }
     S.dd = (terms & TPCF_DD) ? dd : nullptr;
     S.dr = (terms & TPCF_DR) ? dr : nullptr;
     S.rr = (terms & TPCF_RR) ? rr : nullptr;
