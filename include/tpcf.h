@@ -281,8 +281,9 @@ int tpcf_multipole_matrix(int n_s, int n_mu, const int *ells, int n_ell, double 
  * symmetric matrix C[n][n] (device float64; only symmetric input is
  * meaningful), for checking that an LC covariance is positive definite
  * before it is inverted (Sect. 3.4).  Householder reduction to tridiagonal
- * form, then bisection on Sturm counts; absolute accuracy about n * 1e-16 *
- * max|w|.  Needs 1 <= n <= 1024 (TPCF_ERR_ARG otherwise).
+ * form (one cluster of 8 blocks), then 32-way multisection on Sturm counts
+ * (one warp per eigenvalue); absolute accuracy about n * 1e-16 * max|w|.
+ * Needs 1 <= n <= 1024 (TPCF_ERR_ARG otherwise).
  *
  * All four enqueue on `stream` and return without waiting; they share the
  * context's workspace, so calls on different streams must not overlap.

@@ -91,31 +91,51 @@ __global__ void __launch_bounds__(RED_THREADS) chi2_final(const double *__restri
 }
 
 // ---- eigenvalues of a symmetric matrix ----
-constexpr int EIG_THREADS = 1024;
+constexpr int TRI_CTAS = 8, TRI_THREADS = 512;
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// all threads of the cluster; orders this cluster's global-memory writes
+// before the barrier ahead of its reads after it
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 // Householder reduction of the symmetric matrix a[n][n] (overwritten) to
-// tridiagonal form d[n], e[n-1], by one thread block: for each column k the
-// reflector H = I - beta v v^T zeroes a[k+2.., k] and the trailing block B
-// becomes H B H = B - v w^T - w v^T with p = beta B v, w = p - (beta p.v / 2) v.
-__global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double *__restrict__ a, int n, double *__restrict__ d,
-                                                              double *__restrict__ e)
+// tridiagonal form d[n], e[n-1] by one cluster of TRI_CTAS blocks: for each
+// column k the reflector H = I - beta v v^T zeroes a[k+2.., k] and the
+// trailing block B becomes H B H = B - v w^T - w v^T with p = beta B v,
+// w = p - (beta p.v / 2) v.  Block r owns the rows i = r mod TRI_CTAS: it
+// forms p_i for them (to pg in global memory), and after a cluster barrier
+// every block forms w from all of p and updates its own rows; a second
+// barrier ends the column.  v, beta and w are computed by every block alike
+// (the same data and operation order), so every block takes the same branch
+// at each barrier.
+__global__ void __cluster_dims__(TRI_CTAS, 1, 1) __launch_bounds__(TRI_THREADS)
+    tridiag_kernel(double *__restrict__ a, int n, double *__restrict__ d, double *__restrict__ e,
+                   double *__restrict__ pg)
 {
     extern __shared__ double sh[];
     double *v = sh;            // [n]
-    double *p = sh + n;        // [n]
+    double *w = sh + n;        // [n]
     __shared__ double s_alpha, s_beta, s_k;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int rank = (int)cluster_rank();
     for (int k = 0; k + 2 < n; k++) {
         const int m0 = k + 1;   // the reflector acts on rows/cols m0..n-1
-        // x = a[m0.., k]; alpha = -sign(x0) |x|
+        // x = a[m0.., k] = a[k, m0..] (symmetric); alpha = -sign(x0) |x|
+        const double *rk = a + (size_t)k * n;
         double ss = 0.0;
-        for (int i = m0 + 1 + tid; i < n; i += blockDim.x) {
-            const double x = a[(size_t)i * n + k];
-            ss = fma(x, x, ss);
-        }
+        for (int i = m0 + 1 + tid; i < n; i += blockDim.x) ss = fma(rk[i], rk[i], ss);
         const double tail = block_sum(ss);
         if (tid == 0) {
-            const double x0 = a[(size_t)m0 * n + k];
+            const double x0 = rk[m0];
             if (tail == 0.0) {
                 s_alpha = x0;      // column already reduced: H = I
                 s_beta = 0.0;
@@ -127,45 +147,44 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(double *__restrict
                 s_beta = 2.0 / fma(v0, v0, tail);   // 2 / (v.v)
                 v[m0] = v0;
             }
+            if (rank == 0) {
+                d[k] = rk[k];
+                e[k] = s_alpha;
+            }
         }
         __syncthreads();
         const double beta = s_beta;
-        if (tid == 0) {
-            d[k] = a[(size_t)k * n + k];
-            e[k] = s_alpha;
-        }
-        if (beta == 0.0) {
-            __syncthreads();
-            continue;
-        }
-        for (int i = m0 + 1 + tid; i < n; i += blockDim.x) v[i] = a[(size_t)i * n + k];
+        if (beta == 0.0) continue;   // nothing written in this column: no barrier needed
+        for (int i = m0 + 1 + tid; i < n; i += blockDim.x) v[i] = rk[i];
         __syncthreads();
-        // p = beta B v, one warp per row
-        for (int i = m0 + warp; i < n; i += nw) {
+        // p_i = beta (B v)_i for this block's rows, one warp per row
+        const int r0 = m0 + ((rank - m0) % TRI_CTAS + TRI_CTAS) % TRI_CTAS;   // first own row >= m0
+        for (int i = r0 + TRI_CTAS * warp; i < n; i += TRI_CTAS * nw) {
             const double *row = a + (size_t)i * n;
-            double s = 0.0;
-            for (int j = m0 + lane; j < n; j += 32) s = fma(row[j], v[j], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) p[i] = beta * s;
+            double t = 0.0;
+            for (int j = m0 + lane; j < n; j += 32) t = fma(row[j], v[j], t);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) pg[i] = beta * t;
         }
-        __syncthreads();
+        cluster_sync_all();
         double pv = 0.0;
-        for (int i = m0 + tid; i < n; i += blockDim.x) pv = fma(p[i], v[i], pv);
+        for (int i = m0 + tid; i < n; i += blockDim.x) pv = fma(pg[i], v[i], pv);
         pv = block_sum(pv);
         if (tid == 0) s_k = 0.5 * beta * pv;
         __syncthreads();
         const double K = s_k;
-        for (int i = m0 + tid; i < n; i += blockDim.x) p[i] = fma(-K, v[i], p[i]);   // p becomes w
+        for (int i = m0 + tid; i < n; i += blockDim.x) w[i] = fma(-K, v[i], pg[i]);
         __syncthreads();
-        const int m = n - m0;
-        for (int t = tid; t < m * m; t += blockDim.x) {
-            const int i = m0 + t / m, j = m0 + t % m;
+        // this block's rows of B - v w^T - w v^T
+        const int m = n - m0, nr = (n - r0 + TRI_CTAS - 1) / TRI_CTAS;
+        for (int t = tid; t < nr * m; t += blockDim.x) {
+            const int i = r0 + TRI_CTAS * (t / m), j = m0 + t % m;
             double *x = a + (size_t)i * n + j;
-            *x = fma(-v[i], p[j], fma(-p[i], v[j], *x));
+            *x = fma(-v[i], w[j], fma(-w[i], v[j], *x));
         }
-        __syncthreads();
+        cluster_sync_all();
     }
-    if (tid == 0) {
+    if (rank == 0 && tid == 0) {
         if (n >= 2) {
             d[n - 2] = a[(size_t)(n - 2) * n + (n - 2)];
             e[n - 2] = a[(size_t)(n - 1) * n + (n - 2)];
@@ -189,33 +208,50 @@ __device__ int sturm_count(const double *d, const double *e, int n, double x, do
     return c;
 }
 
-// eigenvalue i (ascending) by bisection on the Sturm count within the
-// Gershgorin interval; at most 200 halvings
-__global__ void bisect_kernel(const double *__restrict__ d, const double *__restrict__ e, int n,
-                              double *__restrict__ w)
+// eigenvalue i (ascending) by multisection on the Sturm count, one warp per
+// eigenvalue: from the Gershgorin interval, each step the lanes j < 31 count
+// the eigenvalues below lo + (j + 1)(hi - lo) / 32 and the bracket becomes
+// the first of the 32 sub-intervals whose upper end counts more than i, so a
+// step gains 5 bits where bisection gains 1 (the FP64 Sturm counts are
+// spread over all SMs instead of one thread each); it stops when a step no
+// longer shrinks the bracket (a few ulps), at most 64 steps
+constexpr int EIG_WARPS = 2;   // eigenvalues per block
+
+__global__ void __launch_bounds__(32 * EIG_WARPS) multisect_kernel(const double *__restrict__ d,
+                                                                   const double *__restrict__ e, int n,
+                                                                   double *__restrict__ w)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int lane = threadIdx.x & 31, i = blockIdx.x * EIG_WARPS + (threadIdx.x >> 5);
+    if (i >= n) return;   // whole warps
     double lo = INFINITY, hi = -INFINITY, nrm = 0.0;
-    for (int k = 0; k < n; k++) {
+    for (int k = lane; k < n; k += 32) {
         const double r = (k > 0 ? fabs(e[k - 1]) : 0.0) + (k + 1 < n ? fabs(e[k]) : 0.0);
         lo = fmin(lo, d[k] - r);
         hi = fmax(hi, d[k] + r);
         nrm = fmax(nrm, fabs(d[k]) + r);
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+    }
     const double tiny = fmax(nrm, 1e-300) * 1e-300;
     const double pad = fmax(nrm, 1e-300) * 4e-16 * n;
     lo -= pad;
     hi += pad;
-    for (int it = 0; it < 200; it++) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (sturm_count(d, e, n, mid, tiny) > i)
-            hi = mid;
-        else
-            lo = mid;
+    for (int it = 0; it < 64; it++) {
+        const double step = (hi - lo) * (1.0 / 32.0);
+        const double x = fmin(fma((double)(lane + 1), step, lo), hi);
+        const bool above = lane < 31 && sturm_count(d, e, n, x, tiny) > i;
+        const unsigned mk = __ballot_sync(0xffffffffu, above);
+        const int f = mk ? __ffs(mk) - 1 : 31;   // sub-interval f: (x_{f-1}, x_f]
+        const double xf = __shfl_sync(0xffffffffu, x, f), xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+        const double nlo = f > 0 ? xp : lo, nhi = f < 31 ? xf : hi;
+        if (!(nlo > lo || nhi < hi)) break;
+        lo = nlo;
+        hi = nhi;
     }
-    w[i] = 0.5 * (lo + hi);
+    if (lane == 0) w[i] = 0.5 * (lo + hi);
 }
 
 int blocks_for(size_t n, int threads) { return (int)std::max<size_t>(1, std::min<size_t>((n + threads - 1) / threads, 152 * 16)); }
@@ -248,15 +284,15 @@ cudaError_t launch_chi2(int mode, const double *X, const double *Y, const double
     return cudaGetLastError();
 }
 
-size_t eig_work_bytes(int n) { return ((size_t)n * n + 2 * (size_t)n) * sizeof(double); }
+size_t eig_work_bytes(int n) { return ((size_t)n * n + 3 * (size_t)n) * sizeof(double); }
 
 cudaError_t launch_eigvalsh(const double *C, int n, double *work, double *w, cudaStream_t s)
 {
-    double *a = work, *d = work + (size_t)n * n, *e = d + n;
+    double *a = work, *d = work + (size_t)n * n, *e = d + n, *pg = e + n;
     cudaError_t err = cudaMemcpyAsync(a, C, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (err != cudaSuccess) return err;
-    tridiag_kernel<<<1, EIG_THREADS, 2 * (size_t)n * sizeof(double), s>>>(a, n, d, e);
-    bisect_kernel<<<(n + 127) / 128, 128, 0, s>>>(d, e, n, w);
+    tridiag_kernel<<<TRI_CTAS, TRI_THREADS, 2 * (size_t)n * sizeof(double), s>>>(a, n, d, e, pg);
+    multisect_kernel<<<(n + EIG_WARPS - 1) / EIG_WARPS, 32 * EIG_WARPS, 0, s>>>(d, e, n, w);
     return cudaGetLastError();
 }
 

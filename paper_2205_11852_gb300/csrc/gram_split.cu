@@ -484,10 +484,11 @@ __global__ void reduce_partials_kernel(const double *__restrict__ P, int n_kc, s
     }
 }
 
-// K-chunking of the Gram grid: n_kc chunks of spc slices each, enough that
-// the grid covers every SM (one CTA per SM: 512 TMEM columns and ~200 KB of
-// shared memory each); the FP32 rounding spans one 16-mock slice whatever the
-// chunk length.  The partials then take at most about n_sm x 2 TM^2 x 8 bytes
+// K-chunking of the Gram grid: n_kc chunks of spc slices each, as many as fit
+// in one wave (one CTA per SM: 512 TMEM columns and ~200 KB of shared memory
+// each; one CTA more than the SMs would run a second wave of one CTA and
+// double the kernel's time); the FP32 rounding spans one 16-mock slice
+// whatever the chunk length.  The partials then take at most about n_sm x 2 TM^2 x 8 bytes
 // (n_kc x n_var x nbin^2 doubles with n_kc ~ n_sm / (n_var x tile pairs)).
 struct Chunking {
     int spc, n_kc;
@@ -497,7 +498,7 @@ Chunking chunking(int n_mock, int nbin, int n_var, int n_sm)
 {
     const int n_rb = (nbin + TM - 1) / TM, n_ks = (n_mock + KS - 1) / KS;
     const long long np = (long long)n_rb * (n_rb + 1) / 2;
-    long long want = std::max<long long>(1, ((long long)std::max(1, n_sm) + np * n_var - 1) / (np * n_var));
+    long long want = std::max<long long>(1, (long long)std::max(1, n_sm) / (np * n_var));
     want = std::min<long long>(want, n_ks);
     const int spc = (int)((n_ks + want - 1) / want);
     return Chunking{spc, (n_ks + spc - 1) / spc};

@@ -331,10 +331,10 @@ __device__ __forceinline__ void pair2_flags(uint64_t bx, uint64_t by, uint64_t b
     "selp.u32 %0, 1, 0, p;\n\t"                        \
     "}"
 
-// Midpoint line of sight (no self-cell check; the self cell takes the rare
-// path's instructions).  Operands: %0 the lane's uncertainty; %1-%6 b; %7-%9
-// -a; %10-%12 a - 2 o; %13-%23 constants (tiny, ms, m1, mh, mt, nm, tinyl,
-// -1/2, c1n, c3n, c05); %24 cs; %25 the s clamp; %26 Kl; %27, %28 LS, LT.
+// Midpoint line of sight.  Operands: %0 the lane's uncertainty; %1-%6 b;
+// %7-%9 -a; %10-%12 a - 2 o; %13-%23 constants (tiny, ms, m1, mh, mt, nm,
+// tinyl, -1/2, c1n, c3n, c05); %24 cs; %25 the s clamp; %26 Kl; %27, %28 LS,
+// LT; self-cell tiles: %29 the a index, %30-%33 b limits, %34 the spare word.
 // The mu residual is (n_mu mu - floor(n_mu mu)) - 1/2: 1.5 * 2^23 - 1/2 has no
 // FP32 form, so the half is subtracted after the fraction.
 #define PM_PAIR(BX, BY, BZ)                          \
@@ -398,7 +398,13 @@ __device__ __forceinline__ void pair2_flags(uint64_t bx, uint64_t by, uint64_t b
     "shl.b32 vx, vx, %28;\n\t"                         \
     "shl.b32 vy, vy, %28;\n\t"                         \
     "add.u32 ux, ux, vx;\n\t"                          \
-    "add.u32 uy, uy, vy;\n\t"                          \
+    "add.u32 uy, uy, vy;\n\t"
+#define PM_CHK(IB0, IB1)                             \
+    "setp.lt.u32 c, %29, " IB0 ";\n\t"                 \
+    "selp.b32 ux, ux, %34, c;\n\t"                     \
+    "setp.lt.u32 c, %29, " IB1 ";\n\t"                 \
+    "selp.b32 uy, uy, %34, c;\n\t"
+#define PM_RED                                       \
     "red.shared.add.u32 [ux], 1;\n\t"                  \
     "red.shared.add.u32 [uy], 1;\n\t"
 #define PM_HEAD                                                                                \
@@ -406,7 +412,7 @@ __device__ __forceinline__ void pair2_flags(uint64_t bx, uint64_t by, uint64_t b
     ".reg .b64 dx, dy, dz, d2, r, s, h, fs, lx, ly, lz, q, l2, rl, w, mu, tm, ht, fm, cb;\n\t"   \
     ".reg .f32 d2x, d2y, rx, ry, l2x, l2y, rlx, rly, sx, sy, fx, fy, gx, gy, kx, ky, mx, my;\n\t" \
     ".reg .b32 ux, uy, vx, vy;\n\t"                                                              \
-    ".reg .pred p;\n\t"                                                                          \
+    ".reg .pred p, c;\n\t"                                                                       \
     "setp.ne.u32 p, %26, %26;\n\t"
 
 template <int V, bool CHK, int LS, int LT>
@@ -418,30 +424,25 @@ __device__ __forceinline__ bool apoint(const float2 (&BX)[NQ], const float2 (&BY
     constexpr bool MU = V > 0;
     uint32_t any;
     if (V == 2) {
-        if (CHK) {
-            // the self cell: the rare path's instructions, pairs a >= b to the spare word
-            bool unc = false;
-#pragma unroll
-            for (int q = 0; q < NQ; q++) {
-                uint32_t x0, x1;
-                bool f0, f1;
-                pair2_flags<2, LS, LT>(u64of(BX[q]), u64of(BY[q]), u64of(BZ[q]), a, k, cs, stop, Kl, x0, x1, f0, f1);
-                if (!(ia < IB[2 * q])) x0 = dump;
-                if (!(ia < IB[2 * q + 1])) x1 = dump;
-                red_add(x0, 1u);
-                red_add(x1, 1u);
-                unc = unc || f0 || f1;
-            }
-            return unc;
-        }
-        asm volatile(PM_HEAD PM_PAIR("%1", "%2", "%3") PM_PAIR("%4", "%5", "%6") "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(any)
-                     : "l"(u64of(BX[0])), "l"(u64of(BY[0])), "l"(u64of(BZ[0])), "l"(u64of(BX[1])),
-                       "l"(u64of(BY[1])), "l"(u64of(BZ[1])), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)),
-                       "l"(u64of(a.p)), "l"(u64of(a.q)), "l"(u64of(a.w)), "l"(k.tiny), "l"(k.ms), "l"(k.m1),
-                       "l"(k.mh), "l"(k.mt), "l"(k.nm), "l"(k.tinyl), "l"(k.mhalf), "l"(k.c1n), "l"(k.c3n),
-                       "l"(k.c05), "f"(cs), "f"(stop), "r"(Kl), "n"(LS), "n"(LT)
-                     : "memory");
+#define PM_IN                                                                                                    \
+    "l"(u64of(BX[0])), "l"(u64of(BY[0])), "l"(u64of(BZ[0])), "l"(u64of(BX[1])), "l"(u64of(BY[1])),             \
+        "l"(u64of(BZ[1])), "l"(u64of(a.nax)), "l"(u64of(a.nay)), "l"(u64of(a.naz)), "l"(u64of(a.p)),            \
+        "l"(u64of(a.q)), "l"(u64of(a.w)), "l"(k.tiny), "l"(k.ms), "l"(k.m1), "l"(k.mh), "l"(k.mt), "l"(k.nm),   \
+        "l"(k.tinyl), "l"(k.mhalf), "l"(k.c1n), "l"(k.c3n), "l"(k.c05), "f"(cs), "f"(stop), "r"(Kl), "n"(LS), \
+        "n"(LT)
+        if (CHK)
+            asm volatile(PM_HEAD PM_PAIR("%1", "%2", "%3") PM_CHK("%30", "%31") PM_RED PM_PAIR("%4", "%5", "%6")
+                             PM_CHK("%32", "%33") PM_RED "selp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(any)
+                         : PM_IN, "r"(ia), "r"(IB[0]), "r"(IB[1]), "r"(IB[2]), "r"(IB[3]), "r"(dump)
+                         : "memory");
+        else
+            asm volatile(PM_HEAD PM_PAIR("%1", "%2", "%3") PM_RED PM_PAIR("%4", "%5", "%6") PM_RED
+                         "selp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(any)
+                         : PM_IN
+                         : "memory");
+#undef PM_IN
         return any != 0;
     }
 #define PD_IN                                                                                                     \
@@ -483,6 +484,8 @@ __device__ __forceinline__ bool apoint(const float2 (&BX)[NQ], const float2 (&BY
 #undef PD_HEAD
 #undef PD_TAIL
 #undef PM_PAIR
+#undef PM_CHK
+#undef PM_RED
 #undef PM_HEAD
 
 // Per-lane histogram address constants (see Sh).
@@ -563,27 +566,31 @@ __device__ __forceinline__ void load_tile(const float4 *buf, uint32_t nb, int la
 }
 
 // Every pair of the a-chunk (na points from sorted index a0) with the first nb
-// entries of the warp's buffer; CHK: only pairs a < b count (the self cell
-// of an auto count).  Padding slots hold far-away points whose adds land in
-// the spare last row.  The pairs of one a-point or their uncertainty into one
-// predicate per lane; when any lane's is set, the a-point's pairs are
-// recomputed with a flag each, and each uncertain pair's add is taken back
-// and the pair joins the recheck list.
+// entries of the warp's buffer; CHK: the first nself entries are points of
+// the a-chunk's own cell (an auto count), of whose pairs only a < b count.
+// Padding slots hold far-away points whose adds land in the spare last row.
+// The a-points run two at a time, the last of an odd chunk alone.  The
+// pairs of one a-point or their
+// uncertainty into one predicate per lane; when any lane's is set, the
+// a-points' pairs are recomputed with a flag each, and each uncertain pair's
+// add is taken back and the pair joins the recheck list.
 template <int V, int R, int LOGC, bool CHK>
 __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams &dp, const Mesh &m,
                                      const unsigned long long *T, const WarpMem &wm, const Addr &ad, uint32_t nb,
-                                     uint32_t na, uint32_t a0, int lane, uint32_t &n_list,
+                                     uint32_t nself, uint32_t na, uint32_t a0, int lane, uint32_t &n_list,
                                      unsigned long long &n_exact, unsigned long long &n_cand)
 {
     constexpr bool MU = V > 0, MID = V == 2;
     float2 BX[NQ], BY[NQ], BZ[NQ];
     load_tile(wm.buf, nb, lane, BX, BY, BZ);
+    // CHK: a self-cell slot counts a pair when a < b, any other real slot
+    // always, a padding slot never
     uint32_t IB[NP] = {0u, 0u, 0u, 0u};
     if (CHK) {
 #pragma unroll
         for (int p = 0; p < NP; p++) {
             const uint32_t s = 32u * (uint32_t)p + (uint32_t)lane;
-            IB[p] = s < nb ? __float_as_uint(wm.buf[s].w) : 0u;
+            IB[p] = s < nself ? __float_as_uint(wm.buf[s].w) : (s < nb ? 0xFFFFFFFFu : 0u);
         }
     }
     // slot p of this lane holds a b-point (not padding): bit p
@@ -613,13 +620,17 @@ __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams 
         for (int q = 0; q < NQ; q++)
             pair2_flags<V, LS, LT>(u64of(BX[q]), u64of(BY[q]), u64of(BZ[q]), a, k2, dp.cs, dp.s_top, ad.Kl,
                                     xs[2 * q], xs[2 * q + 1], fl[2 * q], fl[2 * q + 1]);
+        uint32_t xm = 0;
 #pragma unroll
+        for (int p = 0; p < NP; p++) xm |= (fl[p] && (!CHK || ia < IB[p]) ? 1u : 0u) << p;
+        xm &= live;
+#pragma unroll 1
         for (int p = 0; p < NP; p++) {
-            const bool x = fl[p] && ((live >> p) & 1u) && (!CHK || ia < IB[p]);
+            const bool x = (xm >> p) & 1u;
             const unsigned mk = __ballot_sync(0xffffffffu, x);
             if (mk) {
                 if (x) {
-                    red_add(xs[p], 0xFFFFFFFFu);
+                    red_add(p == 0 ? xs[0] : (p == 1 ? xs[1] : (p == 2 ? xs[2] : xs[3])), 0xFFFFFFFFu);
                     xl_put(wm.xl, n_list + __popc(mk & lt), ia,
                            __float_as_uint(wm.buf[32u * (uint32_t)p + (uint32_t)lane].w));
                 }
@@ -638,14 +649,14 @@ __device__ __forceinline__ void tile(const CountParams &prm, const DirectParams 
         const bool u0 = apoint<V, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB, ad.dump);
         const bool u1 = apoint<V, CHK, LS, LT>(BX, BY, BZ, a2, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai + 1, IB, ad.dump);
         if (__any_sync(0xffffffffu, u0 || u1)) {
-            settle(ai);
-            settle(ai + 1);
+#pragma unroll 1
+            for (uint32_t j = ai; j < ai + 2; j++) settle(j);
         }
     }
-    if (ai < na) {
+    if (ai < na) {   // the last a-point of an odd chunk
         const ARec a = load_a<MID>(wm.arec, ai);
-        if (__any_sync(0xffffffffu, apoint<V, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB,
-                                                            ad.dump)))
+        if (__any_sync(0xffffffffu,
+                       apoint<V, CHK, LS, LT>(BX, BY, BZ, a, k2, dp.cs, dp.s_top, ad.Kl, a0 + ai, IB, ad.dump)))
             settle(ai);
     }
     __syncwarp();
@@ -792,54 +803,65 @@ __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams 
     __syncwarp();
 
     const uint32_t lt = (1u << lane) - 1u;
-    // the self cell (auto counts): every pair a < b, no filter
-    for (uint32_t c = self0; c < self1; c += TB) {
-        const uint32_t nb = min((uint32_t)TB, self1 - c);
-        for (uint32_t e2 = (uint32_t)lane; e2 < nb; e2 += 32) {
-            const size_t g = c + e2;
-            wm.buf[e2] = bpoint(dp, (uint32_t)g, m.us[g], m.us[N + g], m.us[2 * N + g], ox, oy, oz);
-        }
-        __syncwarp();
-        tile<V, R, LOGC, true>(prm, dp, m, T, wm, ad, nb, na, a0, lane, n_list, n_exact, n_cand);
-    }
-    // the neighbour runs: four raw points per lane per pass (their twelve
-    // loads in flight together), survivors appended to the buffer, a tile
-    // counted whenever TB of them are there
-    uint32_t nbuf = 0;
+    // The buffer fills with the self cell's points first (auto counts: pairs
+    // a < b, no filter), at most a tile at a time, then with the neighbour
+    // runs' points that pass the filter: four raw points per lane per pass
+    // (their twelve loads in flight together), survivors appended.  A tile is
+    // counted whenever TB points are there, and once more for the rest.  One
+    // call site per kind of tile keeps the kernel's hot code small.
+    uint32_t nbuf = 0, cself = self0, c = 0;
     int g = 0;
-    for (uint32_t c = 0; c < total; c += 128) {
-        uint32_t idx[4];
-        bool ok[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint32_t o2 = c + 32u * (uint32_t)k + (uint32_t)lane;
-            ok[k] = o2 < total;
-            while (g + 1 < (int)n_run && wm.runs[g + 1].y <= o2) g++;
-            idx[k] = ok[k] ? wm.runs[g].x + (o2 - wm.runs[g].y) : 0u;
+    for (;;) {
+        uint32_t nself = 0;
+        if (cself < self1) {   // the buffer is empty here: self points come first
+            nself = min((uint32_t)TB, self1 - cself);
+            for (uint32_t e2 = (uint32_t)lane; e2 < nself; e2 += 32) {
+                const size_t gi = cself + e2;
+                wm.buf[e2] = bpoint(dp, (uint32_t)gi, m.us[gi], m.us[N + gi], m.us[2 * N + gi], ox, oy, oz);
+            }
+            cself += nself;
+            nbuf = nself;
         }
-        uint32_t ux[4], uy[4], uz[4];
+        while (nbuf < TB && c < total) {
+            uint32_t idx[4];
+            bool ok[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            ux[k] = ok[k] ? __ldg(m.us + idx[k]) : 0u;
-            uy[k] = ok[k] ? __ldg(m.us + N + idx[k]) : 0u;
-            uz[k] = ok[k] ? __ldg(m.us + 2 * N + idx[k]) : 0u;
-        }
+            for (int k = 0; k < 4; k++) {
+                const uint32_t o2 = c + 32u * (uint32_t)k + (uint32_t)lane;
+                ok[k] = o2 < total;
+                while (g + 1 < (int)n_run && wm.runs[g + 1].y <= o2) g++;
+                idx[k] = ok[k] ? wm.runs[g].x + (o2 - wm.runs[g].y) : 0u;
+            }
+            uint32_t ux[4], uy[4], uz[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const float4 p = bpoint(dp, idx[k], ux[k], uy[k], uz[k], ox, oy, oz);
-            const float qx = fmaxf(__fsub_rn(fabsf(__fsub_rn(p.x, cxb)), hxb), 0.0f);
-            const float qy = fmaxf(__fsub_rn(fabsf(__fsub_rn(p.y, cyb)), hyb), 0.0f);
-            const float qz = fmaxf(__fsub_rn(fabsf(__fsub_rn(p.z, czb)), hzb), 0.0f);
-            const bool keep = ok[k] && __fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmul_rn(qx, qx))) < dp.hit;
-            const unsigned mk = __ballot_sync(0xffffffffu, keep);
-            if (keep) wm.buf[nbuf + __popc(mk & lt)] = p;
-            nbuf += __popc(mk);
+            for (int k = 0; k < 4; k++) {
+                ux[k] = ok[k] ? __ldg(m.us + idx[k]) : 0u;
+                uy[k] = ok[k] ? __ldg(m.us + N + idx[k]) : 0u;
+                uz[k] = ok[k] ? __ldg(m.us + 2 * N + idx[k]) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const float4 p = bpoint(dp, idx[k], ux[k], uy[k], uz[k], ox, oy, oz);
+                const float qx = fmaxf(__fsub_rn(fabsf(__fsub_rn(p.x, cxb)), hxb), 0.0f);
+                const float qy = fmaxf(__fsub_rn(fabsf(__fsub_rn(p.y, cyb)), hyb), 0.0f);
+                const float qz = fmaxf(__fsub_rn(fabsf(__fsub_rn(p.z, czb)), hzb), 0.0f);
+                const bool keep = ok[k] && __fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmul_rn(qx, qx))) < dp.hit;
+                const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                if (keep) wm.buf[nbuf + __popc(mk & lt)] = p;
+                nbuf += __popc(mk);
+            }
+            c += 128;
         }
-        if (nbuf >= TB) {
-            __syncwarp();
-            tile<V, R, LOGC, false>(prm, dp, m, T, wm, ad, TB, na, a0, lane, n_list, n_exact, n_cand);
-            // the leftovers (fewer than 128) move to the front
-            const uint32_t left = nbuf - TB;
+        if (nbuf == 0) break;
+        const uint32_t nt = min(nbuf, (uint32_t)TB);
+        __syncwarp();
+        if (nself)
+            tile<V, R, LOGC, true>(prm, dp, m, T, wm, ad, nt, nself, na, a0, lane, n_list, n_exact, n_cand);
+        else
+            tile<V, R, LOGC, false>(prm, dp, m, T, wm, ad, nt, 0u, na, a0, lane, n_list, n_exact, n_cand);
+        // the leftovers (fewer than 128) move to the front
+        const uint32_t left = nbuf - nt;
+        if (left) {
             float4 v[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -852,12 +874,9 @@ __device__ __forceinline__ void unit(const CountParams &prm, const DirectParams 
                 const uint32_t s = 32u * (uint32_t)k + (uint32_t)lane;
                 if (s < left) wm.buf[s] = v[k];
             }
-            nbuf = left;
+            __syncwarp();
         }
-    }
-    if (nbuf) {
-        __syncwarp();
-        tile<V, R, LOGC, false>(prm, dp, m, T, wm, ad, nbuf, na, a0, lane, n_list, n_exact, n_cand);
+        nbuf = left;
     }
 }
 
@@ -951,16 +970,29 @@ __global__ void __launch_bounds__(W * 32, 1)
         }
         u_hi = lo;
     }
-    const uint32_t csize = (uint32_t)chunk;
+    // Claims shrink toward the end (guided self-scheduling): a block takes
+    // half of the remaining units' fair share, at most chunk units and at
+    // least chunk / 32 or two per warp (fewer would leave warps idle), so the
+    // last claims, which set the launch's tail, are short.  A stale read of
+    // the counter only changes a claim's length; the atomic add keeps the
+    // claims disjoint and covering.
+    const uint32_t csize = (uint32_t)chunk, span = u_hi - u_lo;
+    const uint32_t cmin = min(csize, max(csize / 32u, 2u * (uint32_t)W));
     int cur_term = -1;
     unsigned long long since = 0;
     __syncthreads();
     for (;;) {
-        if (tid == 0) misc[0] = u_lo + atomicAdd(claim, csize);
+        if (tid == 0) {
+            const uint32_t cur = *(volatile unsigned *)claim;
+            const uint32_t rem = cur < span ? span - cur : 0u;
+            const uint32_t sz = max(cmin, min(csize, rem / (2u * gridDim.x)));
+            misc[0] = u_lo + atomicAdd(claim, sz);
+            misc[2] = sz;
+        }
         __syncthreads();
         const uint32_t c0 = misc[0];
         if (c0 >= u_hi) break;
-        const uint32_t c1 = min(u_hi, c0 + csize);
+        const uint32_t c1 = min(u_hi, c0 + misc[2]);
         uint32_t s = c0;
         while (s < c1) {
             const int t = units[s].term;

@@ -153,6 +153,34 @@ def test_counts_neighbourhood_beyond_one_filter_window(tp, ctx):
         ctx.tpcf_set_cell_subdiv(0)
 
 
+@pytest.mark.parametrize("los", ["s", "x", "midpoint"])
+def test_counts_dense_self_cells(tp, ctx, los):
+    """Clumps of 300, 129, 65 and 63 points in cubes of 1 Mpc/h over a sparse background: self cells with more
+    points than a b-tile (128) and than an a-chunk (64), odd chunk lengths, and tiles that mix a cell's own
+    points with its neighbours'.  Auto and cross counts, both counters, two mesh subdivisions, bit for bit."""
+    L = 200.0
+    rng = synth.rng_for(38, 0, 0)
+    centres = rng.random((4, 3)) * (L - 20.0) + 10.0
+    clumps = [c + rng.random((n, 3)) for c, n in zip(centres, (300, 129, 65, 63))]
+    d = np.concatenate(clumps + [rng.random((700, 3)) * L])
+    r = [np.concatenate([clumps[1] + 0.25, rng.random((600, 3)) * L]), rng.random((555, 3)) * L]
+    mocks = [synth.Mock(d, r)]
+    edges = np.linspace(0, 30.0, 13)
+    n_mu = 1 if los == "s" else 4
+    if los == "midpoint":
+        obs = (-50.0, 20.0, 300.0)
+        tb = tp.make_binning(edges, n_mu, tp.TPCF_OPEN, L + 1.0, los=tp.TPCF_LOS_MIDPOINT, observer=obs)
+        ob = oracle.Binning(edges, n_mu, oracle.OPEN, L + 1.0, los=oracle.LOS_MIDPOINT, observer=obs)
+    else:
+        tb, ob = _periodic(L, edges, n_mu)
+    for sd in (2, 3):
+        ctx.tpcf_set_cell_subdiv(sd)
+        try:
+            _check_counts(ctx, tp, mocks, tb, ob, want_direct=True)
+        finally:
+            ctx.tpcf_set_cell_subdiv(0)
+
+
 def test_counts_open_midpoint(tp, ctx):
     """Cut-sky octant shell, observer at the origin, midpoint line of sight (batching shape, scaled)."""
     L = 600.0
