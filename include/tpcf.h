@@ -148,7 +148,13 @@ typedef struct {
  * copies them into the context's device workspace on `stream` before
  * counting (asynchronously from pinned memory, so they must stay unchanged
  * until the stream has passed the call; pageable memory is copied before the
- * call returns).  The outputs stay device memory.  Returns TPCF_OK or a negative error (nothing enqueued);
+ * call returns).  A batched host-input call whose configuration is already
+ * known (subdivision pinned, autotuning off, or the shape tuned by an earlier
+ * batched call) and whose positions fill at least two groups of
+ * TPCF_OPT_HOST_GROUP_KB runs in up to 8 groups of consecutive mocks: each
+ * group's copy (on a stream of the context's own) overlaps the count of the
+ * previous group, so only the first copy adds to the call's time; the counts
+ * are those of one batched call.  The outputs stay device memory.  Returns TPCF_OK or a negative error (nothing enqueued);
  * TPCF_ERR_RANGE when the binning cannot be counted exactly on the integer
  * grid: a squared separation beyond 64 bits, a periodic s_max above L/3, or
  * (n_mu > 1) n_mu^2 D2_max |l|^2_max >= 2^126 for the exact mu test, where
@@ -419,6 +425,9 @@ int tpcf_set_cell_subdiv(tpcf_ctx *ctx, int subdiv);
  *                        out makes the next tpcf_sync return TPCF_ERR_TIMEOUT;
  *                        the kernel frees its tensor memory and returns.  The
  *                        waits for bulk copies keep the built-in bound.
+ *   TPCF_OPT_HOST_GROUP_KB -- smallest group, in KiB of staged positions, of
+ *                        a grouped host-input count (see tpcf_count; default
+ *                        262144, i.e. 256 MiB; 0 never groups).
  *   TPCF_OPT_TEST_SKIP_MMA -- tests only: when non-zero, one CTA of the Gram
  *                        kernel waits for its operand copies and then issues
  *                        no tensor-core product, so that the wait above runs
@@ -438,6 +447,7 @@ int tpcf_set_cell_subdiv(tpcf_ctx *ctx, int subdiv);
 #define TPCF_OPT_KERNEL    3
 #define TPCF_OPT_WAIT_LIMIT    4
 #define TPCF_OPT_TEST_SKIP_MMA 5
+#define TPCF_OPT_HOST_GROUP_KB 6
 #define TPCF_KERNEL_AUTO     0
 #define TPCF_KERNEL_DIRECT   1
 #define TPCF_KERNEL_GENERAL  2

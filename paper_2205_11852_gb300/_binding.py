@@ -31,6 +31,7 @@ TPCF_DD, TPCF_DR, TPCF_RR = 1, 2, 4
 TPCF_BATCHED, TPCF_PER_LAUNCH, TPCF_HOST_INPUT = 0, 1, 2
 TPCF_FP64, TPCF_TF32X3, TPCF_BF16X3 = 0, 1, 2
 TPCF_OPT_GRAPHS, TPCF_OPT_AUTOTUNE, TPCF_OPT_KERNEL, TPCF_OPT_WAIT_LIMIT, TPCF_OPT_TEST_SKIP_MMA = 1, 2, 3, 4, 5
+TPCF_OPT_HOST_GROUP_KB = 6
 TPCF_KERNEL_AUTO, TPCF_KERNEL_DIRECT, TPCF_KERNEL_GENERAL = 0, 1, 2
 
 EXPORTED = ("tpcf_create", "tpcf_destroy", "tpcf_sync", "tpcf_last_error", "tpcf_count", "tpcf_ls",

@@ -196,6 +196,12 @@ int tpcf_create(tpcf_ctx **out, int cuda_device)
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->scratch_ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->scratch_ev[1]);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 + 2 * tpcf::PIPE_GROUPS_MAX && e == cudaSuccess; k++) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) ctx->pipe_ev.push_back(ev);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&ctx->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->stats, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->stats_host, 8 * sizeof(unsigned long long));
@@ -232,6 +238,8 @@ void tpcf_destroy(tpcf_ctx *ctx)
     if (ctx->staging_free) cudaEventDestroy(ctx->staging_free);
     release_graphs(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (cudaEvent_t e : ctx->pipe_ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->scratch_ev)
         if (e) cudaEventDestroy(e);
     if (ctx->done) cudaEventDestroy(ctx->done);
@@ -312,6 +320,10 @@ int tpcf_set_option(tpcf_ctx *ctx, int option, int value)
         ctx->gram_wait_limit = value;
         break;
     case TPCF_OPT_TEST_SKIP_MMA: ctx->test_skip_mma = value != 0; break;
+    case TPCF_OPT_HOST_GROUP_KB:
+        if (value < 0) return fail(ctx, TPCF_ERR_ARG, "TPCF_OPT_HOST_GROUP_KB must be >= 0");
+        ctx->group_kb = value;
+        break;
     default: return fail(ctx, TPCF_ERR_ARG, "unknown option");
     }
     return TPCF_OK;

@@ -487,7 +487,8 @@ int run_graph(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, int slot)
     for (GraphEntry &e : ctx->graphs)
         if (e.key == key) g = &e;
     if (!g) {
-        if (ctx->graphs.size() >= 8) {
+        // room for every group of a grouped host-input call beside a few other call shapes
+        if (ctx->graphs.size() >= (size_t)(2 * PIPE_GROUPS_MAX + 8)) {
             auto oldest = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
                                            [](const GraphEntry &a, const GraphEntry &b) { return a.last_use < b.last_use; });
             CK(cudaDeviceSynchronize());
@@ -687,40 +688,49 @@ void release_graphs(tpcf_ctx *ctx)
 
 namespace {
 
-// TPCF_HOST_INPUT: the mocks' position arrays are host memory.  They are
-// checked, then copied into the context's "hostin" workspace on the call's
-// stream (one copy per array), and dm receives the mocks with the staged
-// device pointers.  Nothing is enqueued when a check fails.
-int stage_host_mocks(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, unsigned terms, cudaStream_t s,
-                     std::vector<tpcf_mock> &dm)
+// TPCF_HOST_INPUT: the mocks' position arrays are host memory.
+// check_host_mocks checks their fields and returns the bytes each mock
+// stages; stage_host_mocks copies mocks [0, n_mock) into the workspace
+// buffer `name` on stream s (one copy per run of arrays that follow one
+// another in host memory) and dm receives them with the staged device
+// pointers.
+int check_host_mocks(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, unsigned terms, std::vector<size_t> &bytes)
 {
     if (n_mock < 0 || (n_mock > 0 && !mocks)) return fail(ctx, TPCF_ERR_ARG, "mocks is NULL");
     const bool need_d = terms & (TPCF_DD | TPCF_DR);
     const bool need_r = terms & (TPCF_DR | TPCF_RR);
-    auto al256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t bytes = 0;
+    bytes.assign(n_mock, 0);
     for (int m = 0; m < n_mock; m++) {
         const tpcf_mock &mk = mocks[m];
         if (need_d) {
             if (mk.n_d < 0) return fail(ctx, TPCF_ERR_ARG, "n_d < 0");
             if (mk.n_d > 0 && !mk.data_xyz == !mk.data_u32)
                 return fail(ctx, TPCF_ERR_ARG, "give exactly one of data_xyz / data_u32");
-            if (mk.n_d > 0) bytes += al256((size_t)mk.n_d * (mk.data_xyz ? 24 : 12));
+            if (mk.n_d > 0) bytes[m] += (size_t)mk.n_d * (mk.data_xyz ? 24 : 12);
         }
         if (need_r) {
             if (mk.M < 1 || !mk.rand_offsets || mk.rand_offsets[0] != 0)
                 return fail(ctx, TPCF_ERR_ARG, "M >= 1 and rand_offsets starting at 0 are required");
+            if (mk.M != mocks[0].M) return fail(ctx, TPCF_ERR_ARG, "all mocks need the same M");
             for (int i = 0; i < mk.M; i++)
                 if (mk.rand_offsets[i + 1] < mk.rand_offsets[i])
                     return fail(ctx, TPCF_ERR_ARG, "rand_offsets must be non-decreasing");
             const int64_t nr = mk.rand_offsets[mk.M];
             if (nr > 0 && !mk.rand_xyz == !mk.rand_u32)
                 return fail(ctx, TPCF_ERR_ARG, "give exactly one of rand_xyz / rand_u32");
-            if (nr > 0) bytes += al256((size_t)nr * (mk.rand_xyz ? 24 : 12));
+            if (nr > 0) bytes[m] += (size_t)nr * (mk.rand_xyz ? 24 : 12);
         }
     }
+    return TPCF_OK;
+}
+
+int stage_host_mocks(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, unsigned terms, const char *name,
+                     cudaStream_t s, std::vector<tpcf_mock> &dm)
+{
+    const bool need_d = terms & (TPCF_DD | TPCF_DR);
+    const bool need_r = terms & (TPCF_DR | TPCF_RR);
+    auto al256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
     dm.assign(mocks, mocks + n_mock);
-    if (bytes == 0) return TPCF_OK;
     // every array to stage, in order; arrays that follow one another in host
     // memory are copied as one run (one copy for a caller's single buffer)
     struct Item {
@@ -741,6 +751,7 @@ int stage_host_mocks(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, unsigned
             else items.push_back({(const char *)mk.rand_u32, nr * 12, 4, (const void **)&mk.rand_u32});
         }
     }
+    if (items.empty()) return TPCF_OK;
     // device layout: run r starts on a 256-byte boundary; an array inside a
     // run keeps its host offset from the run's start
     std::vector<size_t> dev_off(items.size());
@@ -761,7 +772,7 @@ int stage_host_mocks(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, unsigned
     }
     void *buf = nullptr;
     int rc;
-    if ((rc = ensure(ctx, "hostin", cursor, &buf))) return rc;
+    if ((rc = ensure(ctx, name, cursor, &buf))) return rc;
     char *dev = (char *)buf;
     for (size_t r = 0; r < run_first.size(); r++) {
         const size_t k0 = run_first[r], k1 = (r + 1 < run_first.size()) ? run_first[r + 1] : items.size();
@@ -769,6 +780,88 @@ int stage_host_mocks(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, unsigned
         CK(cudaMemcpyAsync(dev + dev_off[k0], a.src, (size_t)(b.src + b.bytes - a.src), cudaMemcpyHostToDevice, s));
     }
     for (size_t k = 0; k < items.size(); k++) *items[k].field = dev + dev_off[k];
+    return TPCF_OK;
+}
+
+// A batched host-input count in G groups of consecutive mocks (G >= 2):
+// group g is staged into workspace buffer g mod 2 on the context's copy
+// stream while group g - 1 is counted on the call's stream, so only the first
+// group's copy adds to the call's time.  Each group is a whole batched count
+// (plan, mesh, one pair-count launch) of its mocks with the configuration
+// cfg, writing its rows of dd, dr, rr; every count is exact, so the result
+// equals that of one batched call.  The launch counters of the groups are
+// summed for tpcf_last_count_info.
+int count_host_grouped(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *binning,
+                       unsigned terms, int64_t *dd, int64_t *dr, int64_t *rr, const Tuned &cfg,
+                       const std::vector<size_t> &bytes, int G, cudaStream_t s)
+{
+    cudaStream_t cs = ctx->copy_stream;
+    cudaEvent_t *ev = ctx->pipe_ev.data();
+    // group boundaries: equal shares of the staged bytes, every group non-empty
+    size_t total = 0;
+    for (size_t b : bytes) total += b;
+    std::vector<int> first(G + 1, n_mock);
+    first[0] = 0;
+    {
+        size_t acc = 0;
+        int g = 1;
+        for (int m = 0; m < n_mock && g < G; m++) {
+            acc += bytes[m];
+            if (acc * (size_t)G >= total * (size_t)g && m + 1 < n_mock) first[g++] = m + 1;
+        }
+        G = g;
+        first[G] = n_mock;
+    }
+    const bool need_r = terms & (TPCF_DR | TPCF_RR);
+    const size_t nbin = (size_t)binning->n_s * (size_t)binning->n_mu;
+    const size_t M = need_r ? (size_t)mocks[0].M : 0;
+    void *accp = nullptr;
+    int rc;
+    if ((rc = ensure(ctx, "stats_acc", 8 * sizeof(unsigned long long), &accp))) return rc;
+    unsigned long long *acc = (unsigned long long *)accp;
+    // the copies start after the call's earlier work on s and after the
+    // previous grouped call (which may still read the staging buffers)
+    CK(cudaEventRecord(ev[0], s));
+    CK(cudaStreamWaitEvent(cs, ev[0], 0));
+    CK(cudaStreamWaitEvent(cs, ev[1], 0));
+    std::vector<tpcf_mock> staged;
+    Setup S;
+    for (int g = 0; g < G; g++) {
+        const int m0 = first[g], n = first[g + 1] - first[g];
+        if (g >= 2) CK(cudaStreamWaitEvent(cs, ev[3 + 2 * (g - 2)], 0));   // buffer g mod 2 read by group g - 2
+        const int st = ctx->timing ? event_pair(ctx->stage_ev, ctx->n_stage_timed) : -1;
+        if (st >= 0) CK(cudaEventRecord(ctx->stage_ev[2 * st], cs));
+        if ((rc = stage_host_mocks(ctx, mocks + m0, n, terms, (g & 1) ? "hostin1" : "hostin0", cs, staged)))
+            return rc;
+        if (st >= 0) {
+            CK(cudaEventRecord(ctx->stage_ev[2 * st + 1], cs));
+            ctx->n_stage_timed++;
+        }
+        CK(cudaEventRecord(ev[2 + 2 * g], cs));
+        CK(cudaStreamWaitEvent(s, ev[2 + 2 * g], 0));
+        S = Setup();
+        if ((rc = prepare(ctx, staged.data(), n, binning, terms, dd ? dd + (size_t)m0 * nbin : nullptr,
+                          dr ? dr + (size_t)m0 * M * nbin : nullptr, rr ? rr + (size_t)m0 * M * nbin : nullptr,
+                          TPCF_BATCHED, cfg, S)))
+            return rc;
+        const int slot = timing_slot(ctx);
+        if (ctx->use_graphs && S.NT > 0 && !S.terms.empty())
+            rc = run_graph(ctx, S, TPCF_BATCHED, s, slot);
+        else
+            rc = run_direct(ctx, S, TPCF_BATCHED, s, slot);
+        if (rc) return rc;
+        if (slot >= 0) ctx->n_timed++;
+        CK(launch_stats_accum(ctx->stats, acc, g == 0, s));
+        CK(cudaEventRecord(ev[3 + 2 * g], s));
+    }
+    CK(cudaMemcpyAsync(ctx->stats_host, acc, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ev[1], s));
+    ctx->last_subdiv = cfg.subdiv;
+    ctx->last_nc = S.pl.prm.n_c;
+    ctx->last_chunk = S.chunk;
+    ctx->last_blocks = S.blocks;
+    ctx->last_direct = S.direct;
+    ctx->last_launches = G;
     return TPCF_OK;
 }
 
@@ -791,9 +884,40 @@ extern "C" int tpcf_count(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, con
         if (mode != TPCF_BATCHED && mode != TPCF_PER_LAUNCH) return fail(ctx, TPCF_ERR_ARG, "bad mode");
         if ((rc = validate_binning(ctx, binning))) return rc;
         if (terms == 0 || (terms & ~7u)) return fail(ctx, TPCF_ERR_ARG, "terms must be a non-empty mask of DD|DR|RR");
+        std::vector<size_t> bytes;
+        if ((rc = check_host_mocks(ctx, mocks, n_mock, terms, bytes))) return rc;
+        // a batched call whose configuration is already known (pinned, untuned
+        // or in the tune cache) and that stages at least two groups' worth of
+        // positions runs in groups, each copy overlapping the previous group's
+        // count; otherwise everything is staged, then counted (and tuned)
+        size_t total = 0;
+        for (size_t b : bytes) total += b;
+        const size_t gb = (size_t)ctx->group_kb << 10;
+        const int G = gb ? (int)std::min<size_t>({(size_t)PIPE_GROUPS_MAX, total / gb, (size_t)n_mock}) : 1;
+        if (mode == TPCF_BATCHED && G >= 2) {
+            Tuned cfg;
+            bool known = true;
+            if (ctx->subdiv_pin) {
+                cfg.subdiv = ctx->subdiv_pin;
+            } else if (ctx->autotune) {
+                auto it = ctx->tune_cache.find(tune_key(ctx, mocks, n_mock, binning, terms));
+                if (it == ctx->tune_cache.end()) known = false;
+                else cfg = it->second;
+            }
+            if (known) {
+                if ((rc = count_host_grouped(ctx, mocks, n_mock, binning, terms, dd, dr, rr, cfg, bytes, G, s)))
+                    return rc;
+                CK(cudaEventRecord(ctx->done, s));
+                if (call_slot >= 0) {
+                    CK(cudaEventRecord(ctx->call_ev[2 * call_slot + 1], s));
+                    ctx->n_call_timed++;
+                }
+                return TPCF_OK;
+            }
+        }
         const int st = ctx->timing ? event_pair(ctx->stage_ev, ctx->n_stage_timed) : -1;
         if (st >= 0) CK(cudaEventRecord(ctx->stage_ev[2 * st], s));
-        if ((rc = stage_host_mocks(ctx, mocks, n_mock, terms, s, staged))) return rc;
+        if ((rc = stage_host_mocks(ctx, mocks, n_mock, terms, "hostin", s, staged))) return rc;
         if (st >= 0) {
             CK(cudaEventRecord(ctx->stage_ev[2 * st + 1], s));
             ctx->n_stage_timed++;

@@ -31,6 +31,11 @@ struct GraphEntry {
     unsigned long long last_use = 0;
 };
 
+// Host-input counts run in at most this many groups of mocks, each staged
+// while the previous one is counted; a group holds at least the context's
+// group_kb KiB of staged positions (TPCF_OPT_HOST_GROUP_KB).
+constexpr int PIPE_GROUPS_MAX = 8;
+
 // Autotuned configuration of the batched pair count.
 struct Tuned {
     int subdiv = 3;
@@ -83,6 +88,12 @@ struct tpcf_ctx {
     // tpcf_count fails as if a launch had failed (TPCF_TEST_FAIL_COUNT=n)
     long long fail_alloc_at = 0, n_alloc = 0;
     long long fail_count_at = 0, n_count = 0;
+    // host-input counts in groups: the groups' copies run on copy_stream;
+    // pipe_ev holds [0] the call's start, [1] its end (the next call's copies
+    // wait for it), then per group g [2 + 2 g] copied and [3 + 2 g] counted
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> pipe_ev;
+    long long group_kb = 262144;
     // graphs
     cudaStream_t cap_stream = nullptr;
     std::vector<tpcf::GraphEntry> graphs;

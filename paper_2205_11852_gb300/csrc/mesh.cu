@@ -241,6 +241,17 @@ int grid_for(size_t n, int threads, int cap)
     return (int)b;
 }
 
+// Counters of one pair-count launch (stats[8], see record_warp_span) added
+// into a call's running total: sums, except the earliest start and latest end.
+__global__ void stats_accum_kernel(const unsigned long long *__restrict__ st, unsigned long long *__restrict__ acc,
+                                   int first)
+{
+    const int i = threadIdx.x;
+    if (i >= 8) return;
+    const unsigned long long v = st[i];
+    acc[i] = first ? v : ((i == 4 || i == 5) ? (acc[i] > v ? acc[i] : v) : acc[i] + v);
+}
+
 }  // namespace
 
 size_t scan_tmp_elems(size_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
@@ -296,6 +307,12 @@ cudaError_t launch_unit_fill(const Term *terms, int n_terms, const Cat *cats, in
     const size_t total = (size_t)n_terms * n_cells;
     unit_fill_kernel<<<grid_for(total, 256, 152 * 32), 256, 0, s>>>(terms, n_terms, cats, n_cells, cellstart,
                                                                      chunk, ustart, units);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_accum(const unsigned long long *stats, unsigned long long *acc, int first, cudaStream_t s)
+{
+    stats_accum_kernel<<<1, 32, 0, s>>>(stats, acc, first);
     return cudaGetLastError();
 }
 

@@ -135,6 +135,7 @@ cudaError_t launch_scatter(const Cat *cats, int n_cat, uint32_t max_n, const Cou
                            float4 *pf, uint16_t *pcx, cudaStream_t s);
 cudaError_t launch_unit_count(const Term *terms, int n_terms, const Cat *cats, int n_cells,
                               const uint32_t *cellstart, int chunk, uint32_t *ucount, cudaStream_t s);
+cudaError_t launch_stats_accum(const unsigned long long *stats, unsigned long long *acc, int first, cudaStream_t s);
 cudaError_t launch_unit_fill(const Term *terms, int n_terms, const Cat *cats, int n_cells,
                              const uint32_t *cellstart, int chunk, const uint32_t *ustart, Unit *units,
                              cudaStream_t s);

@@ -376,6 +376,46 @@ def test_counts_from_host_arrays(tp, ctx, mode):
         ctx.tpcf_count([_mocks_to_device(mks)[0], host[1]], tb, mode=mode)
 
 
+@pytest.mark.parametrize("kern", [1, 2])
+def test_counts_host_input_in_groups(tp, ctx, kern):
+    """A batched host-input call of a tuned shape runs in groups of consecutive mocks whose copies overlap
+    the previous group's count (here with 1 KiB groups, so every mock is a group up to the limit of 8):
+    counts equal the oracle's and the device-input call's bit for bit, on two calls in a row (the staging
+    buffers reused) and with uneven mocks; the launch counters are the groups' sums."""
+    L = 400.0
+    mks = [synth.SMALL.make_mock(40 + m, n_d=700 + 290 * m, M=2) for m in range(10)]
+    tb, ob = _periodic(L, np.linspace(0, 60.0, 13), 4)
+    refs = [oracle.count_mock(mk.data, mk.randoms, ob) for mk in mks]
+    ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, kern)
+    try:
+        dev = ctx.tpcf_count(_mocks_to_device(mks), tb)          # tunes the shape
+        host = [{"data": torch.from_numpy(np.ascontiguousarray(mk.data)).pin_memory(),
+                 "randoms": torch.from_numpy(np.ascontiguousarray(np.concatenate(mk.randoms))).pin_memory(),
+                 "offsets": [0] + list(np.cumsum([len(r) for r in mk.randoms]))} for mk in mks]
+        ctx.tpcf_set_option(tp.TPCF_OPT_HOST_GROUP_KB, 1)
+        for rep in range(2):
+            got = ctx.tpcf_count(host if rep == 0 else host[::-1], tb)
+            assert ctx.tpcf_sync() == tp.TPCF_OK
+            info = ctx.tpcf_last_count_info()
+            assert 2 <= info["n_paircount_launches"] <= 8
+            order = list(range(10)) if rep == 0 else list(range(9, -1, -1))
+            tot = 0
+            for i, m in enumerate(order):
+                assert np.array_equal(got["dd"][i].cpu().numpy(), refs[m]["DD"]), (rep, m)
+                assert np.array_equal(got["dr"][i].cpu().numpy(), refs[m]["DR"]), (rep, m)
+                assert np.array_equal(got["rr"][i].cpu().numpy(), refs[m]["RR"]), (rep, m)
+                for k in ("dd", "dr", "rr"):
+                    assert torch.equal(got[k][i], dev[k][m]), (rep, m, k)
+                tot += refs[m]["DD"].sum() + refs[m]["DR"].sum() + refs[m]["RR"].sum()
+            assert info["n_binned"] == tot
+            assert info["n_candidates"] >= tot
+    finally:
+        ctx.tpcf_set_option(tp.TPCF_OPT_HOST_GROUP_KB, 262144)
+        ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, tp.TPCF_KERNEL_AUTO)
+    with pytest.raises(tp.TpcfError):
+        ctx.tpcf_set_option(tp.TPCF_OPT_HOST_GROUP_KB, -1)
+
+
 def test_terms_subset_and_output_untouched(tp, ctx):
     L = 300.0
     mk = synth.SMALL.make_mock(6, n_d=800, M=2)
