@@ -569,16 +569,30 @@ int run_direct(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, int slot
 }
 
 // Autotuner: time candidate (subdivision, unit size) pairs on a few mocks.
-// Autotuner: times one batched count of the first few mocks per candidate.
+// Autotuner: times one batched count of the first few mocks per candidate
+// (at least 6, and all the mocks of a workload under 2e6 points).
 // Stage 1: pair counter (both, when the context leaves the choice to the
 // library) x mesh subdivision {2, 3, 4} x unit size {64, 128} (the direct
 // counter's unit is fixed at 64 a-points).  Stage 2, for the winner: fewer
 // blocks per SM than fit (the persistent grid's occupancy).  Each candidate
-// is timed twice and its faster run kept.
+// is timed twice (six times when a run takes under 2 ms) and its fastest run
+// kept.
 int autotune(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binning *binning, unsigned terms,
              int64_t *dd, int64_t *dr, int64_t *rr, cudaStream_t s, Tuned &best)
 {
-    const int n_try = std::min(n_mock, 6);
+    // at least 6 mocks, more while they hold under 2e6 points in all (a tiny
+    // workload is timed whole: its launch latency and tail depend on its size)
+    int n_try = std::min(n_mock, 6);
+    {
+        double pts = 0;
+        for (int m = 0; m < n_mock; m++) {
+            const tpcf_mock &mk = mocks[m];
+            if (terms & (TPCF_DD | TPCF_DR)) pts += (double)std::max<int64_t>(0, mk.n_d);
+            if ((terms & (TPCF_DR | TPCF_RR)) && mk.rand_offsets && mk.M >= 1) pts += (double)mk.rand_offsets[mk.M];
+            if (pts > 2e6) break;
+            n_try = std::max(n_try, m + 1);
+        }
+    }
     static const int subdivs[] = {2, 3, 4};
     static const int chunks[] = {64, 128};
     std::vector<int> kernels;
@@ -600,7 +614,8 @@ int autotune(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tpcf_binni
         if (c.kernel == TPCF_KERNEL_DIRECT && !S.direct) return 1e30f;   // the general counter's timing is its own
         occ_out = S.blocks / std::max(1, ctx->n_sm);
         float ms = 1e30f;
-        for (int rep = 0; rep < 2 && rc == TPCF_OK; rep++) {
+        // two runs, six when they are short (launch latency makes those noisy)
+        for (int rep = 0; rep < (rep >= 2 && ms < 2.0f ? 6 : 2) && rc == TPCF_OK; rep++) {
             cudaError_t e = cudaEventRecord(t0, s);
             if (e == cudaSuccess) rc = run_direct(ctx, S, TPCF_BATCHED, s, -1);
             if (e == cudaSuccess && rc == TPCF_OK) e = cudaEventRecord(t1, s);
