@@ -398,14 +398,16 @@ int tpcf_set_cell_subdiv(tpcf_ctx *ctx, int subdiv);
  *                        outputs of the call stay the same.  The first call of
  *                        a new shape must not itself be under stream capture.
  *   TPCF_OPT_AUTOTUNE -- on the first batched call of a new workload shape,
- *                        time candidates on a few of the mocks and keep the
- *                        fastest: the pair counter (both, under
- *                        TPCF_KERNEL_AUTO), the mesh subdivision {2, 3, 4} and
- *                        the work-unit size {64, 128}, then fewer blocks per SM
- *                        for the winner (cached per context, keyed by the
- *                        binning, the size class and the device's name, SM
- *                        count and compute capability).  A pinned subdivision
- *                        disables it.
+ *                        time candidates on a few of the mocks (all of them
+ *                        below 2e6 points) and keep the fastest: the pair
+ *                        counter (both, under TPCF_KERNEL_AUTO), the mesh
+ *                        subdivision {2, 3, 4} and the work-unit size
+ *                        {64, 128}, then fewer blocks per SM for the winner
+ *                        (cached per context, keyed by the binning, the
+ *                        classes log2 of the mean catalogue size and of the
+ *                        number of mocks, and the device's name, SM count and
+ *                        compute capability).  A pinned subdivision disables
+ *                        it.
  *   TPCF_OPT_KERNEL   -- which pair counter runs: TPCF_KERNEL_DIRECT (the
  *                        direct counter wherever the binning suits it -- s bins
  *                        linear from 0 with the x line of sight or s only, and

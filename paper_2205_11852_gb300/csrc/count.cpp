@@ -675,11 +675,14 @@ std::string tune_key(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const tp
     put(&ctx->device, sizeof(ctx->device));
     k.append(ctx->device_id);
     put(&ctx->kernel_pref, sizeof(ctx->kernel_pref));
-    // size class: log2 of the mean catalogue size
+    // size class: log2 of the mean catalogue size, and of the number of mocks
+    // (a call of a few mocks fills the GPU differently from one of many)
     double pts = 0;
     for (int m = 0; m < n_mock; m++) pts += (double)mocks[m].n_d;
     const int cls = n_mock > 0 ? (int)std::log2(1.0 + pts / n_mock) : 0;
+    const int mcls = (int)std::log2(1.0 + (double)std::max(0, n_mock));
     put(&cls, sizeof(cls));
+    put(&mcls, sizeof(mcls));
     return k;
 }
 
