@@ -815,7 +815,9 @@ int count_host_grouped(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const 
 {
     cudaStream_t cs = ctx->copy_stream;
     cudaEvent_t *ev = ctx->pipe_ev.data();
-    // group boundaries: equal shares of the staged bytes, every group non-empty
+    // group boundaries by staged bytes, every group non-empty: the first group
+    // takes half a share and the others one each, since only the first copy is
+    // not hidden behind a count
     size_t total = 0;
     for (size_t b : bytes) total += b;
     std::vector<int> first(G + 1, n_mock);
@@ -825,7 +827,9 @@ int count_host_grouped(tpcf_ctx *ctx, const tpcf_mock *mocks, int n_mock, const 
         int g = 1;
         for (int m = 0; m < n_mock && g < G; m++) {
             acc += bytes[m];
-            if (acc * (size_t)G >= total * (size_t)g && m + 1 < n_mock) first[g++] = m + 1;
+            // boundary g at (g - 1/2) / (G - 1/2) of the bytes
+            if ((double)acc * (2.0 * G - 1.0) >= (double)total * (2.0 * g - 1.0) && m + 1 < n_mock)
+                first[g++] = m + 1;
         }
         G = g;
         first[G] = n_mock;
