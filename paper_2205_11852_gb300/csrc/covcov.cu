@@ -193,6 +193,119 @@ __global__ void __cluster_dims__(TRI_CTAS, 1, 1) __launch_bounds__(TRI_THREADS)
     }
 }
 
+// a double in block `rank`'s shared memory at the offset of `p` in this block's
+__device__ __forceinline__ double ld_cluster(const double *p, uint32_t rank)
+{
+    const uint32_t la = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t ra;
+    double v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+// Shared-memory bytes of tridiag_smem_kernel for order n: block r's rows
+// (ceil(n / TRI_CTAS) of n doubles), v, w and the p of its rows.
+size_t tri_smem_bytes(int n)
+{
+    const size_t R = ((size_t)n + TRI_CTAS - 1) / TRI_CTAS;
+    return (R * (size_t)n + 2 * (size_t)n + R) * sizeof(double);
+}
+
+// The same reduction with the matrix held in the cluster's shared memory
+// (orders whose rows fit, about n <= 470): block r keeps the rows
+// i = r mod TRI_CTAS (local row t = global row r + TRI_CTAS t), reads row k
+// and the other blocks' p_i from their shared memory through the cluster's
+// address space, and updates its own rows in place; the input C is only read.
+__global__ void __cluster_dims__(TRI_CTAS, 1, 1) __launch_bounds__(TRI_THREADS)
+    tridiag_smem_kernel(const double *__restrict__ C, int n, double *__restrict__ d, double *__restrict__ e)
+{
+    extern __shared__ double sh[];
+    const int R = (n + TRI_CTAS - 1) / TRI_CTAS;
+    double *rows = sh;                    // [R][n]
+    double *v = rows + (size_t)R * n;     // [n]
+    double *w = v + n;                    // [n]
+    double *p = w + n;                    // [R], by local row
+    __shared__ double s_alpha, s_beta, s_k;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int rank = (int)cluster_rank();
+    const int nown = (n - rank + TRI_CTAS - 1) / TRI_CTAS;   // rows of this block (n > rank: n >= 3 here)
+    for (int idx = tid; idx < nown * n; idx += blockDim.x) {
+        const int t = idx / n, j = idx % n;
+        rows[(size_t)t * n + j] = C[(size_t)(rank + TRI_CTAS * t) * n + j];
+    }
+    cluster_sync_all();
+    for (int k = 0; k + 2 < n; k++) {
+        const int m0 = k + 1;
+        const uint32_t ok = (uint32_t)(k % TRI_CTAS);      // the block that holds row k
+        const double *rk = rows + (size_t)(k / TRI_CTAS) * n;   // row k, at its offset in block ok
+        double ss = 0.0;
+        for (int i = m0 + 1 + tid; i < n; i += blockDim.x) {
+            const double x = ld_cluster(rk + i, ok);
+            v[i] = x;
+            ss = fma(x, x, ss);
+        }
+        const double tail = block_sum(ss);
+        if (tid == 0) {
+            const double x0 = ld_cluster(rk + m0, ok);
+            if (tail == 0.0) {
+                s_alpha = x0;      // column already reduced: H = I
+                s_beta = 0.0;
+            } else {
+                const double nx = sqrt(fma(x0, x0, tail));
+                const double alpha = x0 > 0.0 ? -nx : nx;
+                const double v0 = x0 - alpha;
+                s_alpha = alpha;
+                s_beta = 2.0 / fma(v0, v0, tail);   // 2 / (v.v)
+                v[m0] = v0;
+            }
+            if ((uint32_t)rank == ok) d[k] = rk[k];
+            if (rank == 0) e[k] = s_alpha;
+        }
+        __syncthreads();
+        const double beta = s_beta;
+        if (beta == 0.0) continue;   // nothing written in this column: no barrier needed
+        // p_i = beta (B v)_i for this block's rows i >= m0, one warp per row
+        const int t0 = (m0 - rank + TRI_CTAS - 1) / TRI_CTAS > 0 ? (m0 - rank + TRI_CTAS - 1) / TRI_CTAS : 0;
+        for (int t = t0 + warp; t < nown; t += nw) {
+            const double *row = rows + (size_t)t * n;
+            double x = 0.0;
+            for (int j = m0 + lane; j < n; j += 32) x = fma(row[j], v[j], x);
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) p[t] = beta * x;
+        }
+        cluster_sync_all();
+        double pv = 0.0;
+        for (int i = m0 + tid; i < n; i += blockDim.x) {
+            const double pi = ld_cluster(p + i / TRI_CTAS, (uint32_t)(i % TRI_CTAS));
+            w[i] = pi;
+            pv = fma(pi, v[i], pv);
+        }
+        pv = block_sum(pv);
+        if (tid == 0) s_k = 0.5 * beta * pv;
+        __syncthreads();
+        const double K = s_k;
+        for (int i = m0 + tid; i < n; i += blockDim.x) w[i] = fma(-K, v[i], w[i]);   // p becomes w
+        __syncthreads();
+        const int m = n - m0, nr = nown - t0;
+        for (int idx = tid; idx < nr * m; idx += blockDim.x) {
+            const int t = t0 + idx / m, j = m0 + idx % m, i = rank + TRI_CTAS * t;
+            double *x = rows + (size_t)t * n + j;
+            *x = fma(-v[i], w[j], fma(-w[i], v[j], *x));
+        }
+        cluster_sync_all();
+    }
+    cluster_sync_all();   // no block leaves while another may still read its shared memory
+    if (tid == 0) {
+        const int i2 = n - 2, i1 = n - 1;
+        if (i2 % TRI_CTAS == rank) d[i2] = rows[(size_t)(i2 / TRI_CTAS) * n + i2];
+        if (i1 % TRI_CTAS == rank) {
+            e[i2] = rows[(size_t)(i1 / TRI_CTAS) * n + i2];
+            d[i1] = rows[(size_t)(i1 / TRI_CTAS) * n + i1];
+        }
+    }
+}
+
 // number of eigenvalues of the tridiagonal (d, e) below x (Sturm sequence)
 __device__ int sturm_count(const double *d, const double *e, int n, double x, double tiny)
 {
@@ -289,9 +402,18 @@ size_t eig_work_bytes(int n) { return ((size_t)n * n + 3 * (size_t)n) * sizeof(d
 cudaError_t launch_eigvalsh(const double *C, int n, double *work, double *w, cudaStream_t s)
 {
     double *a = work, *d = work + (size_t)n * n, *e = d + n, *pg = e + n;
-    cudaError_t err = cudaMemcpyAsync(a, C, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    if (err != cudaSuccess) return err;
-    tridiag_kernel<<<TRI_CTAS, TRI_THREADS, 2 * (size_t)n * sizeof(double), s>>>(a, n, d, e, pg);
+    cudaError_t err;
+    const size_t sb = tri_smem_bytes(n);
+    if (n >= 3 && sb <= (size_t)(226 << 10)) {
+        // the matrix fits in the cluster's shared memory
+        err = cudaFuncSetAttribute(tridiag_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+        if (err != cudaSuccess) return err;
+        tridiag_smem_kernel<<<TRI_CTAS, TRI_THREADS, sb, s>>>(C, n, d, e);
+    } else {
+        err = cudaMemcpyAsync(a, C, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (err != cudaSuccess) return err;
+        tridiag_kernel<<<TRI_CTAS, TRI_THREADS, 2 * (size_t)n * sizeof(double), s>>>(a, n, d, e, pg);
+    }
     multisect_kernel<<<(n + EIG_WARPS - 1) / EIG_WARPS, 32 * EIG_WARPS, 0, s>>>(d, e, n, w);
     return cudaGetLastError();
 }
