@@ -409,6 +409,12 @@ def test_counts_host_input_in_groups(tp, ctx, kern):
                 tot += refs[m]["DD"].sum() + refs[m]["DR"].sum() + refs[m]["RR"].sum()
             assert info["n_binned"] == tot
             assert info["n_candidates"] >= tot
+        ctx.tpcf_set_option(tp.TPCF_OPT_HOST_GROUP_KB, 0)        # never grouped: one launch
+        got = ctx.tpcf_count(host, tb)
+        assert ctx.tpcf_sync() == tp.TPCF_OK
+        assert ctx.tpcf_last_count_info()["n_paircount_launches"] == 1
+        for k in ("dd", "dr", "rr"):
+            assert torch.equal(got[k], dev[k]), k
     finally:
         ctx.tpcf_set_option(tp.TPCF_OPT_HOST_GROUP_KB, 262144)
         ctx.tpcf_set_option(tp.TPCF_OPT_KERNEL, tp.TPCF_KERNEL_AUTO)
