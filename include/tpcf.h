@@ -288,7 +288,7 @@ int tpcf_multipole_matrix(int n_s, int n_mu, const int *ells, int n_ell, double 
  * meaningful), for checking that an LC covariance is positive definite
  * before it is inverted (Sect. 3.4).  Householder reduction to tridiagonal
  * form (one cluster of 8 blocks, the matrix in their shared memory up to
- * n = 470, in device memory above), then 32-way multisection on Sturm counts
+ * n = 472, in device memory above), then 32-way multisection on Sturm counts
  * (one warp per eigenvalue); absolute accuracy about n * 1e-16 * max|w|.
  * Needs 1 <= n <= 1024 (TPCF_ERR_ARG otherwise).
  *

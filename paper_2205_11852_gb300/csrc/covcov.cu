@@ -213,7 +213,7 @@ size_t tri_smem_bytes(int n)
 }
 
 // The same reduction with the matrix held in the cluster's shared memory
-// (orders whose rows fit, about n <= 470): block r keeps the rows
+// (orders whose rows fit: n <= 472): block r keeps the rows
 // i = r mod TRI_CTAS (local row t = global row r + TRI_CTAS t), reads row k
 // and the other blocks' p_i from their shared memory through the cluster's
 // address space, and updates its own rows in place; the input C is only read.

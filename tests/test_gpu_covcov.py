@@ -70,10 +70,11 @@ def test_chi2_parity(tp, ctx, nbin):
     assert float(meas) == pytest.approx(oracle.chi2(other["C_lc"], ref["C_lc"], ref["C_lc"]), rel=1e-12)
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 37, 200, 600, 1024])
+@pytest.mark.parametrize("n", [1, 2, 3, 37, 200, 472, 473, 600, 1024])
 def test_eigvalsh_parity(tp, ctx, n):
     """Eigenvalues of an LC covariance built from few mocks (indefinite once nbin > n_mock: A is a
-    difference of covariances) against LAPACK."""
+    difference of covariances) against LAPACK; 472 is the largest order whose matrix the reduction keeps in
+    the cluster's shared memory, 473 the smallest it reduces in device memory."""
     ref = _lc_parts(n, max(2, min(n // 2, 400)), 100 + n)
     C = 0.5 * (ref["C_lc"] + ref["C_lc"].T)
     w = ctx.tpcf_eigvalsh(_d(C))
