@@ -34,7 +34,9 @@ namespace {
 constexpr int TM = 128;          // rows (bins) per tile, M = N of the MMA
 constexpr int KS = 16;           // mocks per K-slice
 constexpr int TMEM_COLS = 4 * TM; // two accumulator sets of (leading product, corrections)
-constexpr int GRAM_THREADS = 160; // warps 0-3: the epilogue (TMEM lanes 0-127); warp 4: loads and MMAs
+constexpr int GRAM_EPI_WARPS = 8;  // the epilogue: warp w reads TMEM lanes 32 (w mod 4).. and columns half w / 4
+constexpr int GRAM_THREADS = 32 * (GRAM_EPI_WARPS + 1);   // + one warp for the loads and MMAs
+static_assert(GRAM_EPI_WARPS == 8 && TM == 128, "two warpgroups split a 128-column tile (drain and store)");
 constexpr long long SPIN_LIMIT = 1ll << 26;
 constexpr int NSTAGE = 2;                    // K-slices in flight per CTA
 constexpr int TPAD = TM + 1;                 // row stride (floats) of the shared tile
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const unsigned
         }
         for (int k = 0; k < 2; k++) {
             mbar_init(&accf[k], 1);
-            mbar_init(&accfree[k], 4);
+            mbar_init(&accfree[k], GRAM_EPI_WARPS);
         }
         mbar_init(done, 1);
         mbar_fence_init();
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const unsigned
     tc_fence_after();
     const uint32_t tmem = *slot;
 
-    if (warp == 4) {
+    if (warp == GRAM_EPI_WARPS) {
         if (lane == 0) {
             auto issue = [&](int i) {   // the operand tiles of slice k0 + i into stage i % NSTAGE
                 unsigned char *sa = smem + (i % NSTAGE) * SB, *sb = sa + NP * TB;
@@ -400,8 +402,10 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const unsigned
             if (!ok) atomicOr(status, STATUS_TIMEOUT);
         }
     } else {
-        // epilogue: row = this thread's TMEM lane
-        const int r = warp * 32 + lane;
+        // epilogue: row = this thread's TMEM lane; the two warpgroups take the
+        // columns [0, TM / 2) and [TM / 2, TM) of both accumulators
+        const int wr = warp & 3, c_lo = (warp >> 2) * (TM / 2);
+        const int r = wr * 32 + lane;
         bool fine = true;
         for (int i = 0; i < n && fine; i++) {
             fine = mbar_wait(&accf[i % 2], (uint32_t)(i / 2) & 1u, done_limit);
@@ -410,9 +414,9 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const unsigned
                 if (!fine) break;
             }
             tc_fence_after();
-            const uint32_t set = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((i % 2) * 2 * TM);
+            const uint32_t set = tmem + ((uint32_t)(wr * 32) << 16) + (uint32_t)((i % 2) * 2 * TM);
 #pragma unroll 1
-            for (int c0 = 0; c0 < TM; c0 += 32) {
+            for (int c0 = c_lo; c0 < c_lo + TM / 2; c0 += 32) {
                 uint32_t lo[32], hi[32];
                 tmem_ld32(set + (uint32_t)c0, lo);
                 tmem_ld32(set + (uint32_t)(TM + c0), hi);
@@ -447,13 +451,14 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const unsigned
         good = good && fin;
     }
     if (!good && tid == 0) atomicOr(status, STATUS_TIMEOUT);
-    if (good && warp < 4) {
+    if (good && warp < GRAM_EPI_WARPS) {
         double *g = P + ((size_t)kc * gridDim.y + v) * nbin * nbin;
-        const int t = warp * 32 + lane;
+        // the epilogue warps' 256 threads: t in [0, TM) and a half h of the other index
+        const int t = (warp * 32 + lane) & (TM - 1), h0 = ((warp * 32 + lane) / TM) * (TM / 2);
         // the block itself: thread t takes column t (consecutive threads, consecutive doubles)
         const int col = bj * TM + t;
         if (col < nbin) {
-            for (int rr = 0; rr < TM; rr++) {
+            for (int rr = h0; rr < h0 + TM / 2; rr++) {
                 const int row = bi * TM + rr;
                 if (row >= nbin) break;
                 g[(size_t)row * nbin + col] = (double)tsum[t * TPAD + rr] - (double)tcmp[t * TPAD + rr];
@@ -462,7 +467,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(const unsigned
         // the transposed block of an off-diagonal pair: thread t takes row t
         const int row = bi * TM + t;
         if (bi != bj && row < nbin) {
-            for (int c = 0; c < TM; c++) {
+            for (int c = h0; c < h0 + TM / 2; c++) {
                 const int cc = bj * TM + c;
                 if (cc >= nbin) break;
                 g[(size_t)cc * nbin + row] = (double)tsum[c * TPAD + t] - (double)tcmp[c * TPAD + t];
