@@ -381,7 +381,8 @@ def test_counts_host_input_in_groups(tp, ctx, kern):
     """A batched host-input call of a tuned shape runs in groups of consecutive mocks whose copies overlap
     the previous group's count (here with 1 KiB groups, so every mock is a group up to the limit of 8):
     counts equal the oracle's and the device-input call's bit for bit, on two calls in a row (the staging
-    buffers reused) and with uneven mocks; the launch counters are the groups' sums."""
+    buffers reused; pinned and pageable host memory) and with uneven mocks; the launch counters are the
+    groups' sums."""
     L = 400.0
     mks = [synth.SMALL.make_mock(40 + m, n_d=700 + 290 * m, M=2) for m in range(10)]
     tb, ob = _periodic(L, np.linspace(0, 60.0, 13), 4)
@@ -393,8 +394,12 @@ def test_counts_host_input_in_groups(tp, ctx, kern):
                  "randoms": torch.from_numpy(np.ascontiguousarray(np.concatenate(mk.randoms))).pin_memory(),
                  "offsets": [0] + list(np.cumsum([len(r) for r in mk.randoms]))} for mk in mks]
         ctx.tpcf_set_option(tp.TPCF_OPT_HOST_GROUP_KB, 1)
+        # the second call: the mocks reversed, half of them from pageable memory
+        pageable = [dict(h, data=torch.from_numpy(np.ascontiguousarray(mks[m].data)),
+                         randoms=torch.from_numpy(np.ascontiguousarray(np.concatenate(mks[m].randoms))))
+                    if m % 2 else h for m, h in enumerate(host)]
         for rep in range(2):
-            got = ctx.tpcf_count(host if rep == 0 else host[::-1], tb)
+            got = ctx.tpcf_count(host if rep == 0 else pageable[::-1], tb)
             assert ctx.tpcf_sync() == tp.TPCF_OK
             info = ctx.tpcf_last_count_info()
             assert 2 <= info["n_paircount_launches"] <= 8
