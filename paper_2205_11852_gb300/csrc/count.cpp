@@ -398,9 +398,11 @@ int enqueue(tpcf_ctx *ctx, const Setup &S, int mode, cudaStream_t s, void *small
             L.persistent = 0;
             L.term = t;
             if (S.direct) {
-                // one launch per term over that term's units, each with its own claim counter
+                // one launch per term over that term's units, each with its own claim counter;
+                // claims start at the term's share per block and shrink (guided), so that few
+                // block barriers (each waits for the block's slowest warp) fall in one launch
                 L.blocks = S.blocks;
-                L.chunk = std::max(1, S.claim_units / 8);
+                L.chunk = std::max(1, S.claim_units);
                 CK(launch_pairdirect(prm, S.dp, mesh, d_terms, (const Unit *)S.units, ust + (S.ntc - 1),
                                      (unsigned *)S.claim + 1 + t, ctx->stats, L, s));
             } else {
