@@ -1,6 +1,7 @@
 // Direct binned pair counting on the chaining mesh (Sect. 2.1: DD, DR_i and
 // RR_i counts; Sect. 4.3: bins in separation s and in mu) for linear s bins
-// starting at 0, with the line of sight along x or s only.
+// starting at 0: s only, mu with the line of sight along x, or mu with the
+// line of sight from the observer to the pair's midpoint (cut-sky mocks).
 //
 // Work decomposition.  A unit is a chunk of at most 64 sorted points of one
 // mesh cell A, paired with the neighbourhood of A in catalogue b.  Each warp
@@ -31,7 +32,10 @@
 // recomputes its pairs with a flag each, takes back the uncertain ones' adds
 // and rechecks them exactly from the integer coordinates (64-bit squared
 // distances, a 128-bit mu test), 32 at a time, so every count equals the
-// integer definition bit for bit.
+// integer definition bit for bit.  With the midpoint line of sight the mu
+// bin comes from l = a + b - 2 o (o the observer), mu = (l.d) r rl with
+// rl = rsqrt(|l|^2), its floor and residual against a per-pair bound
+// c2 + c1 r + c3 rl (plan.cpp), the rest as above.
 //
 // Histogram.  R copies of a (n_s + 1) x C table of 32-bit counters, lane l
 // adding to copy l mod R, so the 32 adds of a warp fall in distinct banks
