@@ -8,9 +8,13 @@
 //              cell keys, counting sort by cell, work-unit list, and the pair
 //              count (one persistent launch, or one launch per term);
 //   the batched path captures enqueue() once as a CUDA graph per call shape
-//              and replays it; an autotuner picks the mesh subdivision and
-//              the work-unit size of a new shape by timing candidates on a
-//              few of its mocks.
+//              and replays it; an autotuner picks the pair counter (direct
+//              or general), the mesh subdivision, the work-unit size and the
+//              blocks per SM of a new shape by timing candidates on a few of
+//              its mocks;
+//   host input (TPCF_HOST_INPUT) is staged into the context's workspace,
+//              in groups of mocks whose copies overlap the previous group's
+//              count when the shape is already tuned (count_host_grouped).
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -7,15 +7,18 @@
 // exactly:
 //   TF32X3: y = hi + lo (tf32 each), G ~ hi.hi + hi.lo + lo.hi         (3 products)
 //   BF16X3: y = h + m + l (bf16 each), G ~ hh + hm + mh + hl + lh + mm  (6 products)
-// A CTA owns one 128 x 128 output tile of one variant and a chunk of K-slices
-// of 16 mocks: its operand tiles arrive by bulk copies (cp.async.bulk, the
-// TMA engine, completing on mbarriers) into a ring of stages, one thread
-// issues the tcgen05.mma chains into FP32 accumulators in tensor memory, and
-// the warps read them back with tcgen05.ld and write the chunk's partial Gram,
-// which a reduction kernel sums over the chunks in float64.  The leading
-// product (hi.hi) and the much smaller correction products go to two separate
-// accumulators, so the FP32 rounding of the leading sum spans only the
-// chunk's few exact products and the corrections do not round against it.
+// A CTA (one per SM) owns one 128 x 128 output tile of one variant and a
+// chunk of K-slices of 16 mocks: its operand tiles arrive by bulk copies
+// (cp.async.bulk, the TMA engine, completing on mbarriers) into two stages,
+// one thread issues each slice's tcgen05.mma chains into one of two FP32
+// accumulator sets in tensor memory, and eight warps read each finished set
+// back with tcgen05.ld and add it into a shared FP32 tile by compensated
+// (Kahan) summation while the next slice multiplies; the tile becomes the
+// chunk's partial Gram, which a reduction kernel sums over the chunks in
+// float64, in chunk order.  The leading product (hi.hi) and the much smaller
+// correction products go to two separate accumulators, so the FP32 rounding of
+// an accumulator spans one slice's exact products and the corrections do not
+// round against the leading sum.
 //
 // Operand tiles are written by the split kernel directly in the canonical
 // K-major, non-swizzled layout of the tensor-core descriptors: 8-row x
