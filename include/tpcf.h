@@ -360,11 +360,12 @@ typedef struct {
     int64_t n_exact;
     int64_t n_units;
     double  paircount_ms;
-    int     n_paircount_launches;
+    int     n_paircount_launches;   /* 1 for a batched call, one per term per launch mode, one per group of a
+                                       grouped host-input call (whose counters are the groups' sums) */
     int     cell_subdiv;      /* cells per s_max along an axis */
     int     cells_per_axis;
     int     n_kernels;        /* kernels launched by the last tpcf_count */
-    int     timed_calls;      /* tpcf_count calls accumulated in paircount_ms */
+    int     timed_calls;      /* pair-count spans accumulated in paircount_ms (a grouped call adds one per group) */
     int     unit_chunk;       /* a-points per work unit, chosen by the autotuner */
     int     graph_replay;     /* 1: the batched launch was a replay of a captured CUDA graph */
     int     pair_kernel;      /* TPCF_KERNEL_DIRECT or TPCF_KERNEL_GENERAL: the pair counter that ran */
