@@ -636,7 +636,7 @@ def main():
     per_launch = mocks_total / (ms_pl * 1e-3)
 
     # end to end through the public API: the positions are passed as pinned
-    # HOST arrays (the library copies them in on the stream, TPCF_HOST_INPUT)
+    # HOST arrays (TPCF_HOST_INPUT: the library copies them in, in groups whose copies overlap the counting)
     # and C^LC is read back, every step
     del pos
     job.mocks = None
