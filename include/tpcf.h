@@ -289,7 +289,8 @@ int tpcf_multipole_matrix(int n_s, int n_mu, const int *ells, int n_ell, double 
  * before it is inverted (Sect. 3.4).  Householder reduction to tridiagonal
  * form (one cluster of 8 blocks, the matrix in their shared memory up to
  * n = 472, in device memory above), then 32-way multisection on Sturm counts
- * (one warp per eigenvalue); absolute accuracy about n * 1e-16 * max|w|.
+ * taken on the continuants of T - x I (one warp per eigenvalue); absolute
+ * accuracy about n * 1e-16 * max|w|.
  * Needs 1 <= n <= 1024 (TPCF_ERR_ARG otherwise).
  *
  * All four enqueue on `stream` and return without waiting; they share the

@@ -306,17 +306,35 @@ __global__ void __cluster_dims__(TRI_CTAS, 1, 1) __launch_bounds__(TRI_THREADS)
     }
 }
 
-// number of eigenvalues of the tridiagonal (d, e) below x (Sturm sequence)
-__device__ int sturm_count(const double *d, const double *e, int n, double x, double tiny)
+// Number of eigenvalues below x of the tridiagonal T = (d, e) scaled so that
+// its Gershgorin norm lies in [1, 2) (e2[i] = e[i]^2), without division: the
+// continuants p_i of T - x I (its leading principal minors, p_{-1} = 1,
+// p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2}) change sign exactly where the
+// ratios q_i = p_i / p_{i-1} of the Sturm sequence are negative, and each step
+// rounds like the ratio form's (one relative error on e2 p_{i-2}, one on the
+// result), so the count is that of a matrix within a few ulps of T.  A zero
+// p_i stands for the ratio -pivmin.  p_i and p_{i-1} are rescaled together by
+// a power of two (exactly) whenever p_i leaves [2^-300, 2^300]; with
+// |q_i| in [pivmin, 3 + 1 / pivmin] and pivmin = 2^-400 no step leaves the
+// range of normal doubles.  Three FP64 operations per step where the ratio
+// form needs a division (GB300's FP64 pipe is the bound).
+__device__ int sturm_count(const double *d, const double *e2, int n, double x)
 {
-    int c = 0;
-    double q = d[0] - x;
-    if (q == 0.0) q = -tiny;
-    c += q < 0.0;
+    constexpr double pivmin = 0x1p-400;
+    double pm = 1.0, p = d[0] - x;
+    if (p == 0.0) p = -pivmin;
+    int c = p < 0.0;
     for (int i = 1; i < n; i++) {
-        q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
-        if (q == 0.0) q = -tiny;
-        c += q < 0.0;
+        double pn = fma(d[i] - x, p, -(e2[i - 1] * pm));
+        if (((__double2hiint(pn) & 0x7fffffff) | __double2loint(pn)) == 0) pn = -pivmin * p;
+        c += (__double2hiint(pn) ^ __double2hiint(p)) < 0;   // the signs differ
+        pm = p;
+        p = pn;
+        const int eb = (__double2hiint(p) >> 20) & 0x7ff;
+        if (eb > 1023 + 300 || eb < 1023 - 300) {
+            p = scalbn(p, 1023 - eb);
+            pm = scalbn(pm, 1023 - eb);
+        }
     }
     return c;
 }
@@ -327,15 +345,17 @@ __device__ int sturm_count(const double *d, const double *e, int n, double x, do
 // the first of the 32 sub-intervals whose upper end counts more than i, so a
 // step gains 5 bits where bisection gains 1 (the FP64 Sturm counts are
 // spread over all SMs instead of one thread each); it stops when a step no
-// longer shrinks the bracket (a few ulps), at most 64 steps
+// longer shrinks the bracket (a few ulps), at most 64 steps.  The block stages
+// T scaled by a power of two (exactly) to a norm in [1, 2) in shared memory.
 constexpr int EIG_WARPS = 2;   // eigenvalues per block
 
 __global__ void __launch_bounds__(32 * EIG_WARPS) multisect_kernel(const double *__restrict__ d,
                                                                    const double *__restrict__ e, int n,
                                                                    double *__restrict__ w)
 {
+    extern __shared__ double sde[];
+    double *ds = sde, *e2s = sde + n;   // [n] each
     const int lane = threadIdx.x & 31, i = blockIdx.x * EIG_WARPS + (threadIdx.x >> 5);
-    if (i >= n) return;   // whole warps
     double lo = INFINITY, hi = -INFINITY, nrm = 0.0;
     for (int k = lane; k < n; k += 32) {
         const double r = (k > 0 ? fabs(e[k - 1]) : 0.0) + (k + 1 < n ? fabs(e[k]) : 0.0);
@@ -348,14 +368,21 @@ __global__ void __launch_bounds__(32 * EIG_WARPS) multisect_kernel(const double 
         hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
     }
-    const double tiny = fmax(nrm, 1e-300) * 1e-300;
-    const double pad = fmax(nrm, 1e-300) * 4e-16 * n;
-    lo -= pad;
-    hi += pad;
+    const int ks = nrm > 0.0 ? ilogb(nrm) : 0;   // T / 2^ks has its norm in [1, 2)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        ds[k] = scalbn(d[k], -ks);
+        const double ek = k + 1 < n ? scalbn(e[k], -ks) : 0.0;
+        e2s[k] = ek * ek;
+    }
+    __syncthreads();
+    if (i >= n) return;   // whole warps, after the block's last barrier
+    const double pad = 4e-16 * n;
+    lo = scalbn(lo, -ks) - pad;
+    hi = scalbn(hi, -ks) + pad;
     for (int it = 0; it < 64; it++) {
         const double step = (hi - lo) * (1.0 / 32.0);
         const double x = fmin(fma((double)(lane + 1), step, lo), hi);
-        const bool above = lane < 31 && sturm_count(d, e, n, x, tiny) > i;
+        const bool above = lane < 31 && sturm_count(ds, e2s, n, x) > i;
         const unsigned mk = __ballot_sync(0xffffffffu, above);
         const int f = mk ? __ffs(mk) - 1 : 31;   // sub-interval f: (x_{f-1}, x_f]
         const double xf = __shfl_sync(0xffffffffu, x, f), xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
@@ -364,7 +391,7 @@ __global__ void __launch_bounds__(32 * EIG_WARPS) multisect_kernel(const double 
         lo = nlo;
         hi = nhi;
     }
-    if (lane == 0) w[i] = 0.5 * (lo + hi);
+    if (lane == 0) w[i] = scalbn(0.5 * (lo + hi), ks);
 }
 
 int blocks_for(size_t n, int threads) { return (int)std::max<size_t>(1, std::min<size_t>((n + threads - 1) / threads, 152 * 16)); }
@@ -414,7 +441,8 @@ cudaError_t launch_eigvalsh(const double *C, int n, double *work, double *w, cud
         if (err != cudaSuccess) return err;
         tridiag_kernel<<<TRI_CTAS, TRI_THREADS, 2 * (size_t)n * sizeof(double), s>>>(a, n, d, e, pg);
     }
-    multisect_kernel<<<(n + EIG_WARPS - 1) / EIG_WARPS, 32 * EIG_WARPS, 0, s>>>(d, e, n, w);
+    multisect_kernel<<<(n + EIG_WARPS - 1) / EIG_WARPS, 32 * EIG_WARPS, 2 * (size_t)n * sizeof(double), s>>>(d, e,
+                                                                                                          n, w);
     return cudaGetLastError();
 }
 
